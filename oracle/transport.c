@@ -1,0 +1,535 @@
+/*
+ * Oracle for the photoexcitation-rate transport: a plain, serial, obviously
+ * correct CPU restatement of the method.  TEST INFRASTRUCTURE ONLY: this file
+ * may be used by the tests, by the smoke check and by the benchmark's CPU
+ * baseline leg, and by nothing on the product path.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * What it follows (van Baal & Jerkstrand, ExTraSS):
+ *   - Sobolev optical depth, Eq. (tau_Sobolev), App. A.1; escape probability
+ *     beta_S, Eq. (beta_Sobolev), App. A.1; a line is an interaction point only
+ *     if tau > 1e-4 in the traversed cell (Sec. 2.3.2).
+ *   - Ray path: straight segments to the next cell wall; on every step the
+ *     photon frequency is updated to the comoving frame and the lines whose
+ *     comoving resonance lies between the segment's start and end frequency
+ *     are met in order (Sec. 2.3.2).  Snapshot mode, homologous v = r/t (Sec. 2).
+ *   - Attenuation: the line removes N_phot (1 - e^-tau) photons; the
+ *     photoexcitation estimator counts them divided by the stimulated-emission
+ *     correction f_corr (Sec. 2.3.2); the ray continues while its remaining
+ *     photon energy at the line is >= 1e-6 of its starting energy
+ *     (Secs. 2.3, 2.3.2).
+ *   - Viewing directions: 20 x 20 equal-angle (theta, phi) bins (Sec. 2);
+ *     output on a 0.1 % logarithmic wavelength grid (Sec. 2.3).
+ *   - Line emissivity A_ul dE_ul beta N_u, Eq. (thin_emissivity), App. A.1.
+ * Readings where the paper is silent are documented with each function.
+ *
+ * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no FMA contraction, so the
+ * same source gives the same numbers on x86-64 and aarch64).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* cgs constants */
+#define XO_C 2.99792458e10
+#define XO_H 6.62607015e-27
+#define XO_K 1.380649e-16
+#define XO_E 4.80320471e-10
+#define XO_ME 9.1093837015e-28
+#define XO_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11, "Parallel random
+ * numbers: as easy as 1, 2, 3").  Counter (c0..c3), key (k0,k1); ten rounds
+ * of two 64x64->128 multiplications with the key bumped by the Weyl
+ * constants between rounds. */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void xo_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, x0, &hi0, &lo0);
+        mulhilo64(M1, x2, &hi1, &lo1);
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Uniform double in [0,1) from the top 53 bits of a 64-bit word. */
+static double u01(uint64_t x) { return (double)(x >> 11) * (1.0 / 9007199254740992.0); }
+
+/* Draw e of packet p: four uniforms from counter (p, e, 0, 0), key (seed, 0). */
+static void draw4(uint64_t seed, int64_t p, uint64_t e, double u[4]) {
+    uint64_t ctr[4] = {(uint64_t)p, e, 0, 0}, key[2] = {seed, 0}, x[4];
+    xo_philox4x64_10(ctr, key, x);
+    for (int i = 0; i < 4; i++) u[i] = u01(x[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. (tau_Sobolev): tau = A_ul/(8 pi) (g_u/g_l) lambda^3 n_l (1 - g_l n_u/(g_u n_l)) t.
+ * A_ul from f_lu by the standard oscillator-strength relation
+ * A_ul = 8 pi^2 e^2 / (m_e c lambda^2) (g_l/g_u) f_lu.  For n_l = 0 the bracket
+ * is multiplied out (n_l - g_l n_u / g_u), which gives tau <= 0. */
+double xo_einstein_A(double lambda_cm, double g_l, double g_u, double f_lu) {
+    return 8.0 * XO_PI * XO_PI * XO_E * XO_E / (XO_ME * XO_C * lambda_cm * lambda_cm) * (g_l / g_u) * f_lu;
+}
+
+double xo_tau_sobolev(double A_ul, double g_l, double g_u, double lambda_cm,
+                      double n_l, double n_u, double t) {
+    double pre = A_ul / (8.0 * XO_PI) * (g_u / g_l) * lambda_cm * lambda_cm * lambda_cm;
+    if (n_l > 0.0) return pre * n_l * (1.0 - g_l * n_u / (g_u * n_l)) * t;
+    return pre * (-(g_l / g_u) * n_u) * t;
+}
+
+/* Eq. (beta_Sobolev): beta = (1 - e^-tau)/tau, with beta(0) = 1. */
+double xo_beta_sobolev(double tau) {
+    if (tau == 0.0) return 1.0;
+    return -expm1(-tau) / tau;
+}
+
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int32_t nx, ny, nz;
+    double v_max, t;
+    const double *L_cell;      /* [ncell] erg/s, band emission (emission_mode 0) */
+    double band_lo_A, band_hi_A;
+    int32_t nlev, nline;
+    const double *g;           /* [nlev] */
+    const double *E_level;     /* [nlev] erg */
+    const double *pops;        /* [ncell*nlev] cm^-3 */
+    const int32_t *lo, *up;    /* [nline] */
+    const double *lambda_A, *f_lu; /* [nline] */
+    const double *ne, *Te;     /* [ncell] */
+    const double *ups_down;    /* [nlev] sum over j<u of Upsilon_ju (SCATTER only) */
+} xo_problem;
+
+typedef struct {
+    int64_t n_packets, p_begin, p_end;
+    uint64_t seed;
+    int32_t mode;              /* 0 attenuation (paper), 1 scatter / fluorescence */
+    int32_t emission_mode;     /* 0 flat-in-nu band with L_cell, 1 line emissivity */
+    double tau_min, e_cut;
+    int32_t n_theta, n_phi;
+    double spec_lam0_A, spec_dlog;
+    int32_t spec_nbins;
+    int64_t max_events;
+} xo_params;
+
+enum { L_EMIT_N, L_ESC_N, L_ABS_N, L_DROP_N, L_EMIT_E, L_ESC_E, L_OOB_E, L_EVENTS,
+       L_TESTS, L_GUARD, L_THERMAL_E, L_INTERACT, L_ABS_E_CMF, L_REEMIT_E_CMF, L_NLEDGER };
+
+typedef struct {
+    const xo_problem *pb;
+    const xo_params *pr;
+    int64_t ncell;
+    double R, dx, dy, dz, ct;
+    int32_t *order;      /* sorted position -> original line index */
+    int32_t *pos;        /* original line index -> sorted position */
+    double *nu;          /* [nline] sorted, descending */
+    double *A;           /* [nline] original order */
+    double *Lc;          /* [ncell] cell luminosity */
+    int64_t *qoff;       /* [ncell+1] packet quota prefix */
+    double *wline;       /* [ncell*nline] line emission weights (emission_mode 1) */
+    int32_t *down_off, *down_line;   /* CSR over upper levels of radiative down-lines */
+} prep_t;
+
+static const double *g_sort_nu;
+static int cmp_desc(const void *a, const void *b) {
+    int32_t i = *(const int32_t *)a, j = *(const int32_t *)b;
+    if (g_sort_nu[i] > g_sort_nu[j]) return -1;
+    if (g_sort_nu[i] < g_sort_nu[j]) return 1;
+    return (i < j) ? -1 : (i > j);
+}
+
+/* Largest-remainder integer quota: N L_c / sum(L) rounded down, the remaining
+ * packets to the largest fractional parts (ties to the lower cell index). */
+typedef struct { double frac; int64_t c; } rem_t;
+static int cmp_rem(const void *a, const void *b) {
+    const rem_t *x = a, *y = b;
+    if (x->frac > y->frac) return -1;
+    if (x->frac < y->frac) return 1;
+    return (x->c < y->c) ? -1 : (x->c > y->c);
+}
+
+void xo_packet_quota(const double *L, int64_t ncell, int64_t N, int64_t *qoff) {
+    double tot = 0.0;
+    for (int64_t c = 0; c < ncell; c++) tot += L[c];
+    rem_t *r = malloc(sizeof(rem_t) * (size_t)(ncell > 0 ? ncell : 1));
+    int64_t *n = calloc((size_t)(ncell > 0 ? ncell : 1), sizeof(int64_t));
+    int64_t used = 0;
+    for (int64_t c = 0; c < ncell; c++) {
+        double q = (tot > 0.0) ? ((double)N * L[c]) / tot : 0.0;
+        double fl = floor(q);
+        n[c] = (int64_t)fl;
+        used += n[c];
+        r[c].frac = q - fl;
+        r[c].c = c;
+    }
+    qsort(r, (size_t)ncell, sizeof(rem_t), cmp_rem);
+    for (int64_t k = 0; k < N - used && k < ncell; k++) n[r[k].c] += 1;
+    qoff[0] = 0;
+    for (int64_t c = 0; c < ncell; c++) qoff[c + 1] = qoff[c] + n[c];
+    free(r); free(n);
+}
+
+static int prep(prep_t *P, const xo_problem *pb, const xo_params *pr) {
+    memset(P, 0, sizeof(*P));
+    P->pb = pb; P->pr = pr;
+    P->ncell = (int64_t)pb->nx * pb->ny * pb->nz;
+    P->R = pb->v_max * pb->t;
+    P->dx = 2.0 * P->R / pb->nx; P->dy = 2.0 * P->R / pb->ny; P->dz = 2.0 * P->R / pb->nz;
+    P->ct = XO_C * pb->t;
+    int32_t nl = pb->nline;
+    double *nu_orig = malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
+    P->order = malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    P->pos = malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    P->nu = malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
+    P->A = malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1));
+    for (int32_t l = 0; l < nl; l++) {
+        double lam = pb->lambda_A[l] * 1e-8;
+        nu_orig[l] = XO_C / lam;
+        P->order[l] = l;
+        P->A[l] = xo_einstein_A(lam, pb->g[pb->lo[l]], pb->g[pb->up[l]], pb->f_lu[l]);
+    }
+    g_sort_nu = nu_orig;
+    qsort(P->order, (size_t)nl, sizeof(int32_t), cmp_desc);
+    for (int32_t k = 0; k < nl; k++) { P->pos[P->order[k]] = k; P->nu[k] = nu_orig[P->order[k]]; }
+    free(nu_orig);
+    /* radiative down-lines of every upper level, ascending original index */
+    P->down_off = calloc((size_t)pb->nlev + 1, sizeof(int32_t));
+    P->down_line = malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+    for (int32_t l = 0; l < nl; l++) P->down_off[pb->up[l] + 1]++;
+    for (int32_t u = 0; u < pb->nlev; u++) P->down_off[u + 1] += P->down_off[u];
+    int32_t *fill = calloc((size_t)pb->nlev + 1, sizeof(int32_t));
+    for (int32_t l = 0; l < nl; l++) { int32_t u = pb->up[l]; P->down_line[P->down_off[u] + fill[u]++] = l; }
+    free(fill);
+    /* cell luminosities */
+    P->Lc = calloc((size_t)P->ncell, sizeof(double));
+    if (pr->emission_mode == 0) {
+        for (int64_t c = 0; c < P->ncell; c++) P->Lc[c] = pb->L_cell[c];
+    } else {
+        /* Eq. (thin_emissivity): A_ul dE_ul beta_S N_u, N_u = n_u V_cell */
+        double V = P->dx * P->dy * P->dz;
+        P->wline = calloc((size_t)(P->ncell * nl), sizeof(double));
+        for (int64_t c = 0; c < P->ncell; c++) {
+            const double *n = pb->pops + c * pb->nlev;
+            double sum = 0.0;
+            for (int32_t l = 0; l < nl; l++) {
+                double lam = pb->lambda_A[l] * 1e-8;
+                double tau = xo_tau_sobolev(P->A[l], pb->g[pb->lo[l]], pb->g[pb->up[l]], lam,
+                                            n[pb->lo[l]], n[pb->up[l]], pb->t);
+                double dE = XO_H * XO_C / lam;
+                double w = P->A[l] * dE * xo_beta_sobolev(tau) * n[pb->up[l]] * V;
+                P->wline[c * nl + l] = w;
+                sum += w;
+            }
+            P->Lc[c] = sum;
+        }
+    }
+    P->qoff = malloc(sizeof(int64_t) * (size_t)(P->ncell + 1));
+    xo_packet_quota(P->Lc, P->ncell, pr->n_packets, P->qoff);
+    return 0;
+}
+
+static void unprep(prep_t *P) {
+    free(P->order); free(P->pos); free(P->nu); free(P->A); free(P->Lc); free(P->qoff);
+    free(P->wline); free(P->down_off); free(P->down_line);
+}
+
+static int64_t cell_of_packet(const prep_t *P, int64_t p) {
+    /* last c with qoff[c] <= p (cells with zero quota are skipped) */
+    int64_t lo = 0, hi = P->ncell;   /* invariant qoff[lo] <= p < qoff[hi] */
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (P->qoff[mid] <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* first sorted position whose frequency is <= nu (lines sorted descending) */
+static int32_t cursor_at(const prep_t *P, double nu) {
+    int32_t lo = 0, hi = P->pb->nline;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) / 2;
+        if (P->nu[mid] <= nu) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+static void isotropic(double umu, double uphi, double n[3]) {
+    double mu = 2.0 * umu - 1.0;
+    double phi = 2.0 * XO_PI * uphi;
+    double st = sqrt(1.0 - mu * mu);
+    n[0] = st * cos(phi); n[1] = st * sin(phi); n[2] = mu;
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Viewing-direction bin: theta in [0,pi] and phi in [0,2pi) cut into equal angles. */
+int32_t xo_viewer_bin(const double n[3], int32_t n_theta, int32_t n_phi) {
+    double th = acos(n[2]);
+    double ph = atan2(n[1], n[0]);
+    if (ph < 0.0) ph += 2.0 * XO_PI;
+    int32_t it = (int32_t)floor(th / (XO_PI / n_theta));
+    int32_t ip = (int32_t)floor(ph / (2.0 * XO_PI / n_phi));
+    if (it >= n_theta) it = n_theta - 1;
+    if (ip >= n_phi) ip = n_phi - 1;
+    if (it < 0) it = 0;
+    if (ip < 0) ip = 0;
+    return it * n_phi + ip;
+}
+
+/* Output wavelength bin on the log grid lambda_k = lam0 (1 + dlog)^k; -1 outside. */
+int64_t xo_lambda_bin(double lam_A, double lam0, double dlog, int32_t nbins) {
+    if (!(lam_A >= lam0)) return -1;
+    double k = floor(log(lam_A / lam0) / log1p(dlog));
+    if (k >= (double)nbins) return -1;
+    return (int64_t)k;
+}
+
+/* Optional sparse estimator sink: one record per estimator increment. */
+typedef struct { int64_t cell; int64_t line; double value; } xo_rec;
+static xo_rec *g_rec;
+static int64_t g_rec_cap, g_rec_n;
+
+static void add_estimator(double *S, int64_t cell, int32_t nline, int32_t l, double v) {
+    if (S) S[cell * nline + l] += v;
+    if (g_rec) {
+        if (g_rec_n < g_rec_cap) { g_rec[g_rec_n].cell = cell; g_rec[g_rec_n].line = l; g_rec[g_rec_n].value = v; }
+        g_rec_n++;
+    }
+}
+
+/* packet_out record per packet: fate, events, N_final, escaped lab energy,
+ * viewer, lambda bin, interactions, start cell, N0, nu_cmf at emission,
+ * final nu_lab */
+#define XO_PKT_FIELDS 11
+
+static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec,
+                             double *ledger, double *pkt) {
+    const xo_problem *pb = P->pb;
+    const xo_params *pr = P->pr;
+    int64_t c = cell_of_packet(P, p);
+    int32_t ix = (int32_t)(c % pb->nx), iy = (int32_t)((c / pb->nx) % pb->ny), iz = (int32_t)(c / ((int64_t)pb->nx * pb->ny));
+    int64_t nq = P->qoff[c + 1] - P->qoff[c];
+    double E0 = P->Lc[c] / (double)nq;      /* packet energy, erg/s */
+    double u[4], v[4];
+    draw4(pr->seed, p, 0, u);
+    draw4(pr->seed, p, 1, v);
+    double d[3] = {P->dx, P->dy, P->dz};
+    int32_t idx[3] = {ix, iy, iz}, nn[3] = {pb->nx, pb->ny, pb->nz};
+    double r[3];
+    for (int a = 0; a < 3; a++) r[a] = (-P->R + idx[a] * d[a]) + u[a] * d[a];
+    double n[3];
+    isotropic(u[3], v[0], n);
+    double nu_cmf, nu_lo = XO_C / (pb->band_hi_A * 1e-8), nu_hi = XO_C / (pb->band_lo_A * 1e-8);
+    int32_t cursor;
+    if (pr->emission_mode == 0) {
+        nu_cmf = nu_lo + v[1] * (nu_hi - nu_lo);
+        cursor = cursor_at(P, nu_cmf);
+    } else {
+        /* choose the emitting line by its share of the cell's line emission */
+        const double *w = P->wline + c * pb->nline;
+        double x = v[1] * P->Lc[c], acc = 0.0;
+        int32_t pick = pb->nline - 1;
+        for (int32_t l = 0; l < pb->nline; l++) {
+            acc += w[l];
+            if (x < acc) { pick = l; break; }
+        }
+        nu_cmf = XO_C / (pb->lambda_A[pick] * 1e-8);
+        cursor = P->pos[pick] + 1;           /* start past the emitting line */
+    }
+    double ct = P->ct;
+    double nu_lab = nu_cmf / (1.0 - dot3(n, r) / ct);
+    double N = E0 / (XO_H * nu_cmf);
+    const double N0 = N, nu_cmf0 = nu_cmf;
+    ledger[L_EMIT_N] += N;
+    ledger[L_EMIT_E] += E0;
+    int64_t events = 0, interactions = 0, ndraw = 0;
+    int fate = 0;    /* 0 escaped, 1 dropped below the energy cut, 2 thermalised, 3 event guard */
+    double esc_E = 0.0;
+    int32_t vbin = -1;
+    int64_t lbin = -1;
+    for (;;) {
+        int64_t cell = ((int64_t)idx[2] * pb->ny + idx[1]) * pb->nx + idx[0];
+        const double *pc = pb->pops + cell * pb->nlev;
+        /* distance to the cell walls, ties to the lowest axis */
+        double s_wall = INFINITY;
+        int axis = -1;
+        for (int a = 0; a < 3; a++) {
+            double s;
+            if (n[a] > 0.0) s = ((-P->R + (idx[a] + 1) * d[a]) - r[a]) / n[a];
+            else if (n[a] < 0.0) s = ((-P->R + idx[a] * d[a]) - r[a]) / n[a];
+            else continue;
+            if (s < 0.0) s = 0.0;
+            if (s < s_wall) { s_wall = s; axis = a; }
+        }
+        double r_end[3];
+        for (int a = 0; a < 3; a++) r_end[a] = r[a] + s_wall * n[a];
+        double nu_end = nu_lab * (1.0 - dot3(n, r_end) / ct);
+        int restart = 0;
+        while (cursor < pb->nline && P->nu[cursor] > nu_end) {
+            int32_t l = P->order[cursor];
+            ledger[L_TESTS] += 1.0;
+            double n_l = pc[pb->lo[l]], n_u = pc[pb->up[l]];
+            double g_l = pb->g[pb->lo[l]], g_u = pb->g[pb->up[l]];
+            double lam = pb->lambda_A[l] * 1e-8;
+            double tau = xo_tau_sobolev(P->A[l], g_l, g_u, lam, n_l, n_u, pb->t);
+            if (tau > pr->tau_min) {
+                events++;
+                ledger[L_EVENTS] += 1.0;
+                double f_corr = 1.0 - g_l * n_u / (g_u * n_l);
+                double nu_l = P->nu[cursor];
+                if (pr->mode == 0) {
+                    double dN = N * (-expm1(-tau));
+                    add_estimator(S, cell, pb->nline, l, dN / f_corr);
+                    N -= dN;
+                    ledger[L_ABS_N] += dN;
+                    if (N * XO_H * nu_l < pr->e_cut * E0) {
+                        ledger[L_DROP_N] += N;
+                        fate = 1;
+                        goto done;
+                    }
+                } else {
+                    double w[4];
+                    draw4(pr->seed, p, 2 + (uint64_t)ndraw, w);   /* one draw per active resonance */
+                    ndraw++;
+                    if (w[0] < -expm1(-tau)) {
+                        interactions++;
+                        ledger[L_INTERACT] += 1.0;
+                        add_estimator(S, cell, pb->nline, l, N / f_corr);
+                        ledger[L_ABS_N] += N;
+                        double Ecmf = N * XO_H * nu_l;
+                        ledger[L_ABS_E_CMF] += Ecmf;
+                        /* re-emission channel: radiative down-lines of the upper
+                         * level weighted by A beta, or collisional destruction */
+                        int32_t ulev = pb->up[l];
+                        double Te = pb->Te[cell], ne = pb->ne[cell];
+                        double Ccoll = 8.629e-6 * ne * pb->ups_down[ulev] / (pb->g[ulev] * sqrt(Te));
+                        double Wtot = Ccoll;
+                        for (int32_t k = P->down_off[ulev]; k < P->down_off[ulev + 1]; k++) {
+                            int32_t m = P->down_line[k];
+                            double lm = pb->lambda_A[m] * 1e-8;
+                            double tm = xo_tau_sobolev(P->A[m], pb->g[pb->lo[m]], g_u, lm,
+                                                       pc[pb->lo[m]], pc[ulev], pb->t);
+                            Wtot += P->A[m] * xo_beta_sobolev(tm);
+                        }
+                        double x = w[1] * Wtot, acc = 0.0;
+                        int32_t pick = -1;
+                        for (int32_t k = P->down_off[ulev]; k < P->down_off[ulev + 1]; k++) {
+                            int32_t m = P->down_line[k];
+                            double lm = pb->lambda_A[m] * 1e-8;
+                            double tm = xo_tau_sobolev(P->A[m], pb->g[pb->lo[m]], g_u, lm,
+                                                       pc[pb->lo[m]], pc[ulev], pb->t);
+                            acc += P->A[m] * xo_beta_sobolev(tm);
+                            if (x < acc) { pick = m; break; }
+                        }
+                        if (pick < 0) {
+                            ledger[L_THERMAL_E] += Ecmf;
+                            fate = 2;
+                            goto done;
+                        }
+                        /* move to the resonance point, re-emit isotropically */
+                        double s_l = ct * (1.0 - nu_l / nu_lab) - dot3(n, r);
+                        for (int a = 0; a < 3; a++) r[a] = r[a] + s_l * n[a];
+                        isotropic(w[2], w[3], n);
+                        double nu_new = XO_C / (pb->lambda_A[pick] * 1e-8);
+                        N = Ecmf / (XO_H * nu_new);
+                        ledger[L_REEMIT_E_CMF] += Ecmf;
+                        nu_lab = nu_new / (1.0 - dot3(n, r) / ct);
+                        cursor = P->pos[pick] + 1;
+                        if (events >= pr->max_events) { fate = 3; ledger[L_GUARD] += 1.0; goto done; }
+                        restart = 1;
+                        break;
+                    }
+                }
+                if (events >= pr->max_events) { fate = 3; ledger[L_GUARD] += 1.0; goto done; }
+            }
+            cursor++;
+        }
+        if (restart) continue;
+        /* advance to the wall and step into the next cell */
+        for (int a = 0; a < 3; a++) r[a] = r_end[a];
+        idx[axis] += (n[axis] > 0.0) ? 1 : -1;
+        if (idx[axis] < 0 || idx[axis] >= nn[axis]) {
+            double E = N * XO_H * nu_lab;
+            esc_E = E;
+            ledger[L_ESC_N] += N;
+            ledger[L_ESC_E] += E;
+            vbin = xo_viewer_bin(n, pr->n_theta, pr->n_phi);
+            lbin = xo_lambda_bin(XO_C / nu_lab * 1e8, pr->spec_lam0_A, pr->spec_dlog, pr->spec_nbins);
+            if (lbin >= 0) spec[(int64_t)vbin * pr->spec_nbins + lbin] += E;
+            else ledger[L_OOB_E] += E;
+            fate = 0;
+            goto done;
+        }
+    }
+done:
+    if (pkt) {
+        pkt[0] = fate; pkt[1] = (double)events; pkt[2] = N; pkt[3] = esc_E;
+        pkt[4] = vbin; pkt[5] = (double)lbin; pkt[6] = (double)interactions; pkt[7] = (double)c;
+        pkt[8] = N0; pkt[9] = nu_cmf0; pkt[10] = nu_lab;
+    }
+}
+
+/* Transport packets [p_begin, p_end) of an N-packet emission.  S (natural cell
+ * order x caller line order; may be NULL), spec and ledger are accumulated
+ * into; pkt (optional) receives XO_PKT_FIELDS doubles per packet; rec
+ * (optional) receives one (cell, line, value) record per estimator increment.
+ * Returns 0, or -1 if more than rec_cap records were produced. */
+int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *spec,
+                 double *ledger, double *pkt, xo_rec *rec, int64_t rec_cap, int64_t *rec_n) {
+    prep_t P;
+    g_rec = rec; g_rec_cap = rec_cap; g_rec_n = 0;
+    prep(&P, pb, pr);
+    for (int64_t p = pr->p_begin; p < pr->p_end; p++)
+        transport_packet(&P, p, S, spec, ledger, pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL);
+    unprep(&P);
+    if (rec_n) *rec_n = g_rec_n;
+    g_rec = NULL;
+    return (rec && g_rec_n > rec_cap) ? -1 : 0;
+}
+
+/* Per-cell luminosity and packet quota as the transport sees them. */
+int xo_emission(const xo_problem *pb, const xo_params *pr, double *Lc, int64_t *qoff) {
+    prep_t P;
+    prep(&P, pb, pr);
+    int64_t nc = (int64_t)pb->nx * pb->ny * pb->nz;
+    memcpy(Lc, P.Lc, sizeof(double) * (size_t)nc);
+    memcpy(qoff, P.qoff, sizeof(int64_t) * (size_t)(nc + 1));
+    unprep(&P);
+    return 0;
+}
+
+/* tau_S and beta_S for every (cell, line) of a cell range (caller line order). */
+int xo_tau_beta(const xo_problem *pb, int64_t c0, int64_t nc, double *tau, double *beta) {
+    for (int64_t c = c0; c < c0 + nc; c++) {
+        const double *n = pb->pops + c * pb->nlev;
+        for (int32_t l = 0; l < pb->nline; l++) {
+            double lam = pb->lambda_A[l] * 1e-8;
+            double gl = pb->g[pb->lo[l]], gu = pb->g[pb->up[l]];
+            double A = xo_einstein_A(lam, gl, gu, pb->f_lu[l]);
+            double t = xo_tau_sobolev(A, gl, gu, lam, n[pb->lo[l]], n[pb->up[l]], pb->t);
+            tau[(c - c0) * pb->nline + l] = t;
+            if (beta) beta[(c - c0) * pb->nline + l] = xo_beta_sobolev(t);
+        }
+    }
+    return 0;
+}
+
+/* Comoving frequency along a ray, for brute-force resonance checks. */
+double xo_nu_cmf(double nu_lab, const double n[3], const double r[3], double s, double t) {
+    double q[3] = {r[0] + s * n[0], r[1] + s * n[1], r[2] + s * n[2]};
+    return nu_lab * (1.0 - dot3(n, q) / (XO_C * t));
+}

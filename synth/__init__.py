@@ -1,0 +1,294 @@
+"""Seeded synthetic inputs for the photoexcitation-transport workloads.
+
+This module only *produces inputs*: grids, atomic models, starting level
+populations and emission luminosities.  It holds none of the method's
+arithmetic (no optical depths, escape probabilities, transport, estimators,
+rates or rate-matrix algebra), so both the CPU oracle and the CUDA library
+can consume what it writes without sharing any computation.
+
+Workloads (all cgs, wavelengths in Angstrom):
+
+* ``uniform_sphere`` - 16^3 Cartesian velocity cells of a homologous flow
+  (v = r/t, v_max = 5000 km/s, t = 200 d), uniform density 1e-15 g/cm^3 inside
+  |v| <= v_max, Te = 5000 K, ne = 1e7 cm^-3; one synthetic ion with 20 levels
+  evenly spaced over 0-10 eV; 100 lines with log-uniform wavelengths in
+  3000-10000 A and log-uniform oscillator strengths in 1e-4..1; uniform
+  emissivity flat in frequency over 2900-10000 A; 1e5 packets.
+* ``clumpy_onion`` - 64^3 cells, lognormal density clumps (sigma = 0.5,
+  Gaussian correlation length 4 cells) in four onion zones
+  (Fe-group / O / He / H), 10 synthetic ions of 50-200 levels, 1e5 lines
+  (1000 A - 3 um, f in 1e-6..1), 1e8 packets, 8^3 subdomains.
+
+The paper's explosion models (3D neutrino-driven models, the 1D-turned-3D
+model and the public toy model it compares against) are not available; these
+recipes stand in for their shapes and sizes (Section 3 of the paper: 17,100
+zones, up to 100 levels per ion).
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+# Physical constants (cgs).  Used only to express the input recipes (eV to erg,
+# ion masses, Boltzmann starting populations), never for transport.
+C_LIGHT = 2.99792458e10
+H_PLANCK = 6.62607015e-27
+K_BOLTZ = 1.380649e-16
+EV = 1.602176634e-12
+M_U = 1.66053906660e-24
+DAY = 86400.0
+
+
+@dataclasses.dataclass
+class Workload:
+    """Everything one transport pass (and the rate solves) consumes.
+
+    Cell index c = (iz * ny + iy) * nx + ix ("natural" order).  Level indices
+    are global: level ``level_off[z] + i`` is level i of ion z.  Lines are in
+    generation order (unsorted); ``lo``/``up`` are global level indices.
+    """
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    v_max: float          # cm/s; the cube spans [-v_max t, v_max t]^3
+    t: float              # s since explosion
+    rho: np.ndarray       # [ncell] g/cm^3
+    Te: np.ndarray        # [ncell] K
+    ne: np.ndarray        # [ncell] cm^-3
+    deposition: np.ndarray  # [ncell] erg/s/cm^3 (non-thermal energy input)
+    L_cell: np.ndarray    # [ncell] erg/s emitted by the cell (band emission)
+    band_A: tuple         # (lambda_lo, lambda_hi) of the flat-in-nu emission band
+    n_ion: int
+    level_off: np.ndarray  # [n_ion+1] int32
+    E_level: np.ndarray   # [nlev] erg above the ion's ground level
+    g_level: np.ndarray   # [nlev] statistical weights
+    ion_mass_u: np.ndarray  # [n_ion] mass numbers
+    n_ion_density: np.ndarray  # [ncell, n_ion] cm^-3
+    lo: np.ndarray        # [nline] int32 global lower level
+    up: np.ndarray        # [nline] int32 global upper level
+    lambda_A: np.ndarray  # [nline] line wavelength, Angstrom
+    f_lu: np.ndarray      # [nline] absorption oscillator strength
+    pops: np.ndarray      # [ncell, nlev] cm^-3 starting level populations
+    upsilon_seed: int     # seed for collision strengths (see collision_strengths)
+    n_packets: int
+    seed: int
+    subdomains: tuple     # (sx, sy, sz) number of subdomains per axis
+    spec_band_A: tuple    # (lambda0, n_bins) of the 0.1 % log output grid
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nlev(self) -> int:
+        return int(self.level_off[-1])
+
+    @property
+    def nline(self) -> int:
+        return int(self.lo.shape[0])
+
+
+def cell_centres(n: int, v_max: float) -> np.ndarray:
+    """Velocity of the centres of n equal cells spanning [-v_max, v_max]."""
+    return -v_max + (np.arange(n) + 0.5) * (2.0 * v_max / n)
+
+
+def _speed_grid(n: int, v_max: float) -> np.ndarray:
+    v = cell_centres(n, v_max)
+    vz, vy, vx = np.meshgrid(v, v, v, indexing="ij")   # natural order: x fastest
+    return np.sqrt(vx * vx + vy * vy + vz * vz).reshape(-1)
+
+
+def lte_populations(n_ion_density, level_off, E_level, g_level, Te):
+    """Boltzmann populations within each ion at the cell temperature.
+
+    Starting populations for the transport-only workloads: n_i = n_z g_i
+    exp(-E_i / k Te) / sum_j g_j exp(-E_j / k Te).
+    """
+    ncell, n_ion = n_ion_density.shape
+    nlev = int(level_off[-1])
+    pops = np.zeros((ncell, nlev))
+    kT = K_BOLTZ * np.where(Te > 0, Te, 1.0)
+    for z in range(n_ion):
+        a, b = int(level_off[z]), int(level_off[z + 1])
+        w = g_level[a:b][None, :] * np.exp(-E_level[a:b][None, :] / kT[:, None])
+        pops[:, a:b] = n_ion_density[:, z:z + 1] * w / w.sum(axis=1, keepdims=True)
+    return pops
+
+
+def _synthetic_ion(rng, L, n_lines, lam_range, f_range, unique_pairs):
+    """One synthetic ion: L levels evenly spaced over 0-10 eV, g = 1 + 2 (i mod 4),
+    lines between random (l < u) pairs with log-uniform wavelength and f."""
+    E = 10.0 * EV * np.arange(L) / (L - 1)
+    g = 1.0 + 2.0 * (np.arange(L) % 4)
+    iu, il = np.triu_indices(L, 1)[1], np.triu_indices(L, 1)[0]
+    npairs = il.shape[0]
+    if unique_pairs:
+        pick = rng.choice(npairs, n_lines, replace=False)
+    else:
+        pick = rng.integers(0, npairs, n_lines)
+    lo, up = il[pick], iu[pick]
+    lam = 10.0 ** rng.uniform(np.log10(lam_range[0]), np.log10(lam_range[1]), n_lines)
+    f = 10.0 ** rng.uniform(np.log10(f_range[0]), np.log10(f_range[1]), n_lines)
+    return E, g, lo, up, lam, f
+
+
+def collision_strengths(seed: int, level_off) -> list:
+    """Effective collision strengths Upsilon for every level pair of every ion,
+    log-uniform in [0.1, 10] (one seeded [L, L] upper-triangular array per ion;
+    entry [l, u] with l < u)."""
+    out = []
+    for z in range(len(level_off) - 1):
+        L = int(level_off[z + 1] - level_off[z])
+        rng = np.random.default_rng([seed, 7919, z])
+        ups = np.zeros((L, L))
+        iu = np.triu_indices(L, 1)
+        ups[iu] = 10.0 ** rng.uniform(-1.0, 1.0, iu[0].shape[0])
+        out.append(ups)
+    return out
+
+
+def _spectrum_grid(lam_lo_emit, lam_hi_emit, v_max, dlog=1e-3):
+    """0.1 % log wavelength grid wide enough for every Doppler-shifted escape."""
+    b = v_max / C_LIGHT
+    lam0 = lam_lo_emit * (1.0 - 1.5 * b)
+    lam1 = lam_hi_emit * (1.0 + 1.5 * b)
+    n_bins = int(np.ceil(np.log(lam1 / lam0) / np.log1p(dlog)))
+    return (lam0, n_bins)
+
+
+def uniform_sphere(seed: int = 0, n_packets: int = 100_000, n: int = 16,
+                   n_lines: int = 100, n_levels: int = 20,
+                   f_range=(1e-4, 1.0), subdomains=(1, 1, 1)) -> Workload:
+    """Plain-method workload: uniform sphere in a 16^3 Cartesian velocity grid."""
+    v_max, t = 5.0e8, 200.0 * DAY
+    speed = _speed_grid(n, v_max)
+    active = speed <= v_max
+    ncell = n ** 3
+    rng = np.random.default_rng(seed)
+    E, g, lo, up, lam, f = _synthetic_ion(rng, n_levels, n_lines, (3000.0, 10000.0),
+                                          f_range, unique_pairs=True)
+    rho = np.where(active, 1e-15, 0.0)
+    Te = np.full(ncell, 5000.0)
+    ne = np.where(active, 1e7, 0.0)
+    A = np.array([56.0])
+    n_ion_density = (rho / (A[0] * M_U))[:, None].copy()
+    level_off = np.array([0, n_levels], dtype=np.int32)
+    pops = lte_populations(n_ion_density, level_off, E, g, Te)
+    vol_active = active.astype(np.float64)
+    L_cell = 1e40 * vol_active / vol_active.sum()
+    deposition = L_cell / ((2.0 * v_max * t / n) ** 3)
+    band = (2900.0, 10000.0)
+    return Workload(
+        name=f"uniform_sphere_{n}^3_{n_lines}lines_{n_packets}pk", nx=n, ny=n, nz=n,
+        v_max=v_max, t=t, rho=rho, Te=Te, ne=ne, deposition=deposition, L_cell=L_cell,
+        band_A=band, n_ion=1, level_off=level_off, E_level=E, g_level=g,
+        ion_mass_u=A, n_ion_density=n_ion_density,
+        lo=lo.astype(np.int32), up=up.astype(np.int32), lambda_A=lam, f_lu=f,
+        pops=pops, upsilon_seed=seed, n_packets=n_packets, seed=seed,
+        subdomains=tuple(subdomains), spec_band_A=_spectrum_grid(band[0], band[1], v_max),
+        meta={"active_cells": int(active.sum())})
+
+
+def gaussian_random_field(n: int, corr_len_cells: float, rng) -> np.ndarray:
+    """Unit-variance periodic Gaussian random field on n^3 with correlation
+    exp(-r^2 / (2 l^2)): white noise filtered by a Gaussian of width l/sqrt(2)."""
+    w = rng.standard_normal((n, n, n))
+    k = 2.0 * np.pi * np.fft.fftfreq(n)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    s = corr_len_cells / np.sqrt(2.0)
+    filt = np.exp(-0.5 * (kx * kx + ky * ky + kz * kz) * s * s)
+    field = np.real(np.fft.ifftn(np.fft.fftn(w) * filt))
+    field -= field.mean()
+    field /= field.std()
+    return field.reshape(-1)   # natural order (x fastest)
+
+
+ZONE_OF_ION = np.array([0, 0, 0, 1, 1, 2, 2, 3, 3, 3])   # Fe-group, O, He, H
+MASS_OF_ZONE = np.array([56.0, 16.0, 4.0, 1.0])
+
+
+def clumpy_onion(seed: int = 0, n_packets: int = 100_000_000, n: int = 64,
+                 n_lines: int = 100_000, n_ion: int = 10, level_range=(50, 200),
+                 subdomains=(8, 8, 8), lam_range=(1000.0, 30000.0),
+                 f_range=(1e-6, 1.0), rho_mean=1e-15, sigma=0.5,
+                 corr_len_cells=4.0) -> Workload:
+    """Paper-scale transport workload: onion zones with lognormal clumps."""
+    v_max, t = 5.0e8, 200.0 * DAY
+    ncell = n ** 3
+    speed = _speed_grid(n, v_max)
+    active = speed <= v_max
+    rng = np.random.default_rng(seed)
+    zone = np.minimum((speed / v_max / 0.25).astype(np.int64), 3)
+    grf = gaussian_random_field(n, corr_len_cells, np.random.default_rng([seed, 1]))
+    rho = np.where(active, rho_mean * np.exp(sigma * grf - 0.5 * sigma * sigma), 0.0)
+    Te = np.full(ncell, 5000.0)
+    ne = 1e7 * rho / rho_mean
+    # number shares: native ions of the cell's zone share 97 %, the others 3 %
+    ion_zone = ZONE_OF_ION[:n_ion] if n_ion == 10 else np.arange(n_ion) % 4
+    A = MASS_OF_ZONE[ion_zone]
+    share = np.zeros((ncell, n_ion))
+    for zz in range(4):
+        native = ion_zone == zz
+        cells = zone == zz
+        nn = int(native.sum())
+        share[np.ix_(cells, native)] = 0.97 / nn
+        share[np.ix_(cells, ~native)] = 0.03 / (n_ion - nn)
+    mu = (share * A[None, :]).sum(axis=1)
+    n_tot = np.where(active, rho / (mu * M_U), 0.0)
+    n_ion_density = share * n_tot[:, None]
+    # atoms
+    Ls = rng.integers(level_range[0], level_range[1] + 1, n_ion)
+    level_off = np.zeros(n_ion + 1, dtype=np.int32)
+    level_off[1:] = np.cumsum(Ls)
+    per_ion = np.full(n_ion, n_lines // n_ion)
+    per_ion[: n_lines - per_ion.sum()] += 1
+    Es, gs, los, ups, lams, fs = [], [], [], [], [], []
+    for z in range(n_ion):
+        E, g, lo, up, lam, f = _synthetic_ion(rng, int(Ls[z]), int(per_ion[z]), lam_range,
+                                              f_range, unique_pairs=False)
+        Es.append(E); gs.append(g)
+        los.append(lo + level_off[z]); ups.append(up + level_off[z])
+        lams.append(lam); fs.append(f)
+    E = np.concatenate(Es); g = np.concatenate(gs)
+    pops = lte_populations(n_ion_density, level_off, E, g, Te)
+    L_cell = 1e40 * rho / rho.sum()
+    deposition = L_cell / ((2.0 * v_max * t / n) ** 3)
+    band = (lam_range[0] / (1.0 + 2.0 * v_max / C_LIGHT), lam_range[1])
+    return Workload(
+        name=f"clumpy_onion_{n}^3_{n_ion}ions_{n_lines}lines_{n_packets}pk",
+        nx=n, ny=n, nz=n, v_max=v_max, t=t, rho=rho, Te=Te, ne=ne,
+        deposition=deposition, L_cell=L_cell, band_A=band, n_ion=n_ion,
+        level_off=level_off, E_level=E, g_level=g, ion_mass_u=A,
+        n_ion_density=n_ion_density, lo=np.concatenate(los).astype(np.int32),
+        up=np.concatenate(ups).astype(np.int32), lambda_A=np.concatenate(lams),
+        f_lu=np.concatenate(fs), pops=pops, upsilon_seed=seed, n_packets=n_packets,
+        seed=seed, subdomains=tuple(subdomains),
+        spec_band_A=_spectrum_grid(band[0], band[1], v_max),
+        meta={"active_cells": int(active.sum()), "levels_per_ion": Ls.tolist()})
+
+
+def single_line_sphere(n: int = 16, n_packets: int = 100_000, seed: int = 3,
+                       lam_A: float = 5000.0, f_lu: float = 1e-3,
+                       n_scale: float = 1.0) -> Workload:
+    """Two-level ion with one line inside a uniform sphere; ``n_scale`` rescales
+    the ion density (n_scale -> 0 gives the optically thin limit)."""
+    w = uniform_sphere(seed=seed, n_packets=n_packets, n=n, n_lines=1, n_levels=2)
+    w.lambda_A = np.array([lam_A]); w.f_lu = np.array([f_lu])
+    w.lo = np.array([0], np.int32); w.up = np.array([1], np.int32)
+    w.n_ion_density = w.n_ion_density * n_scale
+    w.pops = lte_populations(w.n_ion_density, w.level_off, w.E_level, w.g_level, w.Te)
+    w.band_A = (lam_A * 0.9, lam_A * 1.1)
+    w.spec_band_A = _spectrum_grid(w.band_A[0], w.band_A[1], w.v_max)
+    w.name = f"single_line_sphere_{n}^3"
+    return w
+
+
+def workload(name: str, **kw) -> Workload:
+    if name == "uniform_sphere":
+        return uniform_sphere(**kw)
+    if name == "clumpy_onion":
+        return clumpy_onion(**kw)
+    raise KeyError(name)
