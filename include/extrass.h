@@ -1,0 +1,169 @@
+/*
+ * extrass.h - C ABI of the GB300 photoexcitation-rate transport library.
+ *
+ * The library computes photoexcitation rates by radiative transfer through a
+ * 3D homologously expanding ejecta grid (van Baal & Jerkstrand, ExTraSS,
+ * Sec. 2.3 "Radiative transfer" and Sec. 2.3.2 "Photoexcitation"), with the
+ * per-cell, per-line estimator store split into Cartesian subdomains
+ * (Sec. 2.4.1 "Domain decomposition").  All compute runs in CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative XT_E* code; xt_last_error() gives a
+ *     message naming the offending argument.  Nothing traps; device-side loops
+ *     are bounded and report overruns as status codes.
+ *   - Array arguments are plain pointers that may point to host memory
+ *     (pageable or pinned) or to device memory of the context's GPU; the
+ *     library tells them apart with cudaPointerGetAttributes.  Inputs are only
+ *     read during the call; outputs are written before the call returns (the
+ *     call synchronises the context's stream).  The caller owns them.
+ *   - Units are cgs; wavelengths are in Angstrom.  Floating point is FP64.
+ *   - Cell index c = (iz * ny + iy) * nx + ix ("natural order").  Level index
+ *     is global over ions: level i of ion z is level_off[z] + i.  Lines are
+ *     addressed in the caller's order (the order given to load_atomic_data).
+ *   - The context owns all device memory it allocates; xt_destroy frees it.
+ *     A context is driven by one host thread at a time.
+ */
+#ifndef EXTRASS_H
+#define EXTRASS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XT_OK 0
+#define XT_EINVAL (-1)    /* bad argument (message names it) */
+#define XT_ENOMEM (-2)    /* device allocation failed */
+#define XT_ECUDA (-3)     /* a CUDA runtime call failed */
+#define XT_ETIMEOUT (-4)  /* a bounded device loop hit its limit */
+#define XT_ENOTCONV (-5)  /* an iterative solve did not converge */
+#define XT_ESTATE (-6)    /* call made before the data it needs was loaded */
+
+typedef struct xt_ctx xt_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (for example torch.cuda.current_stream().cuda_stream) or NULL for the
+ * legacy default stream; every kernel of the context runs on it. */
+int xt_create(xt_ctx **out, int device, void *cuda_stream);
+void xt_destroy(xt_ctx *ctx);
+const char *xt_last_error(const xt_ctx *ctx);
+
+/* ---- grid (Sec. 2: snapshot, homologous v = r/t) ------------------------ */
+typedef struct {
+    int32_t nx, ny, nz;     /* cells per axis; the cube spans [-v_max t, v_max t]^3 */
+    int32_t sx, sy, sz;     /* subdomains per axis (Sec. 2.4.1); must divide nx, ny, nz */
+    double v_max;           /* cm/s */
+    double t;               /* s since explosion */
+    const double *rho;      /* [ncell] g/cm^3 (may be NULL) */
+    const double *Te;       /* [ncell] K */
+    const double *ne;       /* [ncell] cm^-3 */
+    const double *L_cell;   /* [ncell] erg/s emitted in the flat-nu band (may be NULL) */
+    const double *deposition; /* [ncell] erg/s/cm^3 non-thermal input (may be NULL) */
+    double band_lo_A, band_hi_A;  /* emission band of L_cell, flat in frequency */
+} xt_grid_desc;
+int init_grid(xt_ctx *ctx, const xt_grid_desc *g);
+
+/* ---- atomic data (Sec. 2.2, 2.4 jagged level arrays) -------------------- */
+typedef struct {
+    int32_t n_ion;
+    int32_t nline;
+    const int32_t *level_off;   /* [n_ion+1] CSR offsets of each ion's levels */
+    const double *E_level;      /* [nlev] erg above the ion's ground level */
+    const double *g_level;      /* [nlev] statistical weights */
+    const int32_t *lo, *up;     /* [nline] global lower / upper level (lo < up, same ion) */
+    const double *lambda_A;     /* [nline] line wavelength, Angstrom */
+    const double *f_lu;         /* [nline] absorption oscillator strength */
+    const double *n_ion_density;/* [ncell*n_ion] cm^-3 (may be NULL) */
+    const double *ups_down;     /* [nlev] sum_{j<u} Upsilon_ju; scatter mode only (may be NULL) */
+} xt_atom_desc;
+int load_atomic_data(xt_ctx *ctx, const xt_atom_desc *a);
+
+/* Level populations [ncell][nlev] in cm^-3 (natural cell order). */
+int set_populations(xt_ctx *ctx, const double *pops);
+int get_populations(xt_ctx *ctx, double *pops, size_t n_cap);
+
+/* ---- A1: Sobolev optical depth and escape probability ------------------
+ * tau_S, Eq. (tau_Sobolev) (App. A.1), and beta_S = (1 - e^-tau)/tau,
+ * Eq. (beta_Sobolev), for cells [cell_begin, cell_begin + n_cells) x all
+ * lines, written [n_cells][nline] in the caller's line order.  beta may be
+ * NULL. */
+int get_sobolev_tau(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *tau, double *beta);
+
+/* ---- A2-A6: transport (Secs. 2.3, 2.3.2, 2.4.1) ------------------------ */
+#define XT_MODE_ATTEN 0     /* paper: attenuate by 1 - e^-tau at every line (default) */
+#define XT_MODE_SCATTER 1   /* absorb-or-scatter with fluorescent re-emission */
+#define XT_EMIT_BAND 0      /* flat-in-nu band emission with L_cell */
+#define XT_EMIT_LINES 1     /* line emissivity A_ul dE beta N_u, Eq. (thin_emissivity) */
+#define XT_PKT_FIELDS 11    /* per-packet record, see xt_transport_params.packet_records */
+
+typedef struct {
+    int64_t n_packets;      /* N of the whole emission (sets the per-cell quota) */
+    int64_t packet_begin;   /* first packet id transported by this call */
+    int64_t packet_count;   /* number of packets; <0 means all from packet_begin */
+    uint64_t seed;          /* Philox4x64-10 key (seed, 0); counter (packet, draw, 0, 0) */
+    int32_t mode;           /* XT_MODE_* */
+    int32_t emission;       /* XT_EMIT_* */
+    double tau_min;         /* lines are interaction points only above this tau (1e-4) */
+    double e_cut;           /* stop below this fraction of the starting energy (1e-6) */
+    int32_t n_theta, n_phi; /* viewing-direction bins (20, 20) */
+    double spec_lam0_A;     /* first edge of the output grid */
+    double spec_dlog;       /* bin edges lam0 (1 + dlog)^k (1e-3) */
+    int32_t spec_nbins;
+    int32_t accumulate;     /* 0: zero estimators, spectrum and ledger first */
+    int64_t max_events;     /* per-packet event guard (XT_ETIMEOUT when hit) */
+    int32_t subdomain_rounds; /* 0: the whole grid is one resident domain.  1: each
+                             * subdomain of init_grid is a domain of its own; a packet
+                             * that crosses into another subdomain is queued and
+                             * carried on in the next round (Sec. 2.4.1 bundles) */
+    int32_t flags;          /* reserved, 0 */
+    /* Optional [packet_count][XT_PKT_FIELDS] doubles: fate (0 escaped,
+     * 1 dropped below e_cut, 2 collisionally destroyed, 3 guard), events,
+     * N_final, escaped lab energy, viewer, lambda bin, interactions, emitting
+     * cell, N0, comoving emission frequency, final lab frequency. */
+    double *packet_records;
+} xt_transport_params;
+
+/* Ledger and timing of the last run_transport (photons/s and erg/s). */
+typedef struct {
+    double emitted_N, escaped_N, absorbed_N, dropped_N;
+    double emitted_E, escaped_E, out_of_band_E;
+    double events, tests, guard, thermal_E, interactions, abs_E_cmf, reemit_E_cmf;
+    double transport_ms;    /* device time of the transport kernels */
+    double zero_ms;         /* device time spent clearing the estimator store */
+    double rounds;          /* subdomain-group rounds executed */
+    double queued;          /* packets handed between subdomain groups */
+} xt_transport_stats;
+
+int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);
+
+/* Raw estimators S [n_cells][nline] (photons/s absorbed, divided by f_corr),
+ * cells [cell_begin, +n_cells), caller line order. */
+int get_estimators(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *S);
+
+/* ---- A7: rates (Sec. 2.3.2, Sec. 2.3.1 Gamma = N_abs / N_i) ------------
+ * R_lu = S / (n_l V), R_ul = (g_l/g_u) R_lu (detailed balance), Jbar =
+ * R_lu / B_lu with B_lu = 4 pi (pi e^2 / m_e c) f_lu / (h nu).  Each output
+ * [n_cells][nline]; any may be NULL; slots with n_l = 0 give 0. */
+int get_photoexcitation_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells,
+                              double *R_lu, double *R_ul, double *Jbar);
+
+/* ---- A5: spectrum (Secs. 2, 2.3) ----------------------------------------
+ * kind 0: escaped lab-frame energy per (viewer, bin) [n_theta*n_phi][nbins], erg/s
+ * kind 1: isotropic-equivalent L_lambda = 4 pi/dOmega_k E/dlambda, same shape, erg/s/A
+ * kind 2: angle-summed L_lambda [nbins], erg/s/A */
+int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
+
+typedef struct {
+    int64_t ncell, nlev, nline, n_ion;
+    int64_t spec_views, spec_bins;
+    int64_t store_bytes;    /* device bytes of the estimator store */
+} xt_sizes;
+int get_sizes(xt_ctx *ctx, xt_sizes *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXTRASS_H */

@@ -1,0 +1,307 @@
+"""GB300-native photoexcitation-rate transport (ExTraSS method, Secs. 2.3-2.4).
+
+Thin Python binding of the C-ABI library ``libextrass.so`` (declared in
+``include/extrass.h``).  The functions here only marshal arguments: every step
+of the computation runs in the library's CUDA kernels.  There is no CPU
+fallback; if the library has not been built, importing the binding raises.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); they are passed to the library as plain pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libextrass.so")
+
+XT_OK, XT_EINVAL, XT_ENOMEM, XT_ECUDA, XT_ETIMEOUT, XT_ENOTCONV, XT_ESTATE = 0, -1, -2, -3, -4, -5, -6
+XT_MODE_ATTEN, XT_MODE_SCATTER = 0, 1
+XT_EMIT_BAND, XT_EMIT_LINES = 0, 1
+XT_PKT_FIELDS = 11
+PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
+              "N0", "nu_cmf0", "nu_lab"]
+
+
+class XtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("sx", C.c_int32), ("sy", C.c_int32), ("sz", C.c_int32),
+                ("v_max", C.c_double), ("t", C.c_double),
+                ("rho", C.c_void_p), ("Te", C.c_void_p), ("ne", C.c_void_p),
+                ("L_cell", C.c_void_p), ("deposition", C.c_void_p),
+                ("band_lo_A", C.c_double), ("band_hi_A", C.c_double)]
+
+
+class AtomDesc(C.Structure):
+    _fields_ = [("n_ion", C.c_int32), ("nline", C.c_int32),
+                ("level_off", C.c_void_p), ("E_level", C.c_void_p), ("g_level", C.c_void_p),
+                ("lo", C.c_void_p), ("up", C.c_void_p), ("lambda_A", C.c_void_p),
+                ("f_lu", C.c_void_p), ("n_ion_density", C.c_void_p), ("ups_down", C.c_void_p)]
+
+
+class TransportParams(C.Structure):
+    _fields_ = [("n_packets", C.c_int64), ("packet_begin", C.c_int64),
+                ("packet_count", C.c_int64), ("seed", C.c_uint64),
+                ("mode", C.c_int32), ("emission", C.c_int32),
+                ("tau_min", C.c_double), ("e_cut", C.c_double),
+                ("n_theta", C.c_int32), ("n_phi", C.c_int32),
+                ("spec_lam0_A", C.c_double), ("spec_dlog", C.c_double),
+                ("spec_nbins", C.c_int32), ("accumulate", C.c_int32),
+                ("max_events", C.c_int64), ("subdomain_rounds", C.c_int32), ("flags", C.c_int32),
+                ("packet_records", C.c_void_p)]
+
+
+STATS_FIELDS = ["emitted_N", "escaped_N", "absorbed_N", "dropped_N", "emitted_E", "escaped_E",
+                "out_of_band_E", "events", "tests", "guard", "thermal_E", "interactions",
+                "abs_E_cmf", "reemit_E_cmf", "transport_ms", "zero_ms", "rounds", "queued"]
+
+
+class TransportStats(C.Structure):
+    _fields_ = [(f, C.c_double) for f in STATS_FIELDS]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f in STATS_FIELDS}
+
+
+class Sizes(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in
+                ["ncell", "nlev", "nline", "n_ion", "spec_views", "spec_bins", "store_bytes"]]
+
+
+_lib = None
+
+
+def lib():
+    """Load libextrass.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} missing "
+                              "(run python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "xt_create": ([C.POINTER(vp), C.c_int, vp], C.c_int),
+            "xt_destroy": ([vp], None),
+            "xt_last_error": ([vp], C.c_char_p),
+            "init_grid": ([vp, vp], C.c_int),
+            "load_atomic_data": ([vp, vp], C.c_int),
+            "set_populations": ([vp, vp], C.c_int),
+            "get_populations": ([vp, vp, C.c_size_t], C.c_int),
+            "get_sobolev_tau": ([vp, i64, i64, vp, vp], C.c_int),
+            "run_transport": ([vp, vp, vp], C.c_int),
+            "get_estimators": ([vp, i64, i64, vp], C.c_int),
+            "get_photoexcitation_rates": ([vp, i64, i64, vp, vp, vp], C.c_int),
+            "get_spectrum": ([vp, i32, vp, C.c_size_t], C.c_int),
+            "get_sizes": ([vp, vp], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Plain pointer of a numpy array or torch tensor (None stays None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(ctx, rc):
+    if rc != XT_OK:
+        msg = lib().xt_last_error(ctx).decode() if ctx else "xt_create failed"
+        raise XtError(rc, msg)
+
+
+# ---- C-ABI functions under their own names ---------------------------------
+def xt_create(device=0, stream=None):
+    h = C.c_void_p()
+    _check(None, lib().xt_create(C.byref(h), int(device), stream))
+    return h
+
+
+def xt_destroy(ctx):
+    lib().xt_destroy(ctx)
+
+
+def xt_last_error(ctx):
+    return lib().xt_last_error(ctx).decode()
+
+
+def init_grid(ctx, nx, ny, nz, v_max, t, Te, ne, L_cell=None, band_A=(0.0, 0.0), rho=None,
+              deposition=None, subdomains=(1, 1, 1)):
+    keep = [_f64(x) for x in (rho, Te, ne, L_cell, deposition)]
+    d = GridDesc(nx, ny, nz, *subdomains, v_max, t, *[_ptr(x) for x in keep], *band_A)
+    _check(ctx, lib().init_grid(ctx, C.byref(d)))
+
+
+def load_atomic_data(ctx, level_off, E_level, g_level, lo, up, lambda_A, f_lu,
+                     n_ion_density=None, ups_down=None):
+    lo_, up_, off_ = _i32(lo), _i32(up), _i32(level_off)
+    fl = [_f64(x) for x in (E_level, g_level, lambda_A, f_lu, n_ion_density, ups_down)]
+    d = AtomDesc(len(off_) - 1, len(lo_), _ptr(off_), _ptr(fl[0]), _ptr(fl[1]), _ptr(lo_),
+                 _ptr(up_), _ptr(fl[2]), _ptr(fl[3]), _ptr(fl[4]), _ptr(fl[5]))
+    _check(ctx, lib().load_atomic_data(ctx, C.byref(d)))
+
+
+def set_populations(ctx, pops):
+    p = _f64(pops)
+    _check(ctx, lib().set_populations(ctx, _ptr(p)))
+
+
+def get_sizes(ctx):
+    s = Sizes()
+    _check(ctx, lib().get_sizes(ctx, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in Sizes._fields_}
+
+
+def get_populations(ctx, out=None):
+    sz = get_sizes(ctx)
+    if out is None:
+        out = np.zeros((sz["ncell"], sz["nlev"]))
+    _check(ctx, lib().get_populations(ctx, _ptr(out), int(np.prod(out.shape))))
+    return out
+
+
+def get_sobolev_tau(ctx, cell_begin=0, n_cells=None, tau=None, beta=None, want_beta=True):
+    sz = get_sizes(ctx)
+    n_cells = sz["ncell"] - cell_begin if n_cells is None else n_cells
+    if tau is None:
+        tau = np.zeros((n_cells, sz["nline"]))
+    if beta is None and want_beta:
+        beta = np.zeros((n_cells, sz["nline"]))
+    _check(ctx, lib().get_sobolev_tau(ctx, cell_begin, n_cells, _ptr(tau), _ptr(beta)))
+    return tau, beta
+
+
+def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=XT_MODE_ATTEN,
+                  emission=XT_EMIT_BAND, tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
+                  spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1, accumulate=False,
+                  max_events=1_000_000, subdomain_rounds=False, packet_records=None, check=True):
+    p = TransportParams(int(n_packets), int(packet_begin), int(packet_count), int(seed), int(mode),
+                        int(emission), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
+                        int(spec_nbins), int(bool(accumulate)), int(max_events), int(bool(subdomain_rounds)),
+                        0, _ptr(packet_records))
+    st = TransportStats()
+    rc = lib().run_transport(ctx, C.byref(p), C.byref(st))
+    if check:
+        _check(ctx, rc)
+    return st.as_dict() if check else (rc, st.as_dict())
+
+
+def get_estimators(ctx, cell_begin=0, n_cells=None, out=None):
+    sz = get_sizes(ctx)
+    n_cells = sz["ncell"] - cell_begin if n_cells is None else n_cells
+    if out is None:
+        out = np.zeros((n_cells, sz["nline"]))
+    _check(ctx, lib().get_estimators(ctx, cell_begin, n_cells, _ptr(out)))
+    return out
+
+
+def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=None, Jbar=None,
+                              want=("R_lu", "R_ul", "Jbar")):
+    sz = get_sizes(ctx)
+    n_cells = sz["ncell"] - cell_begin if n_cells is None else n_cells
+    shape = (n_cells, sz["nline"])
+    if R_lu is None and "R_lu" in want:
+        R_lu = np.zeros(shape)
+    if R_ul is None and "R_ul" in want:
+        R_ul = np.zeros(shape)
+    if Jbar is None and "Jbar" in want:
+        Jbar = np.zeros(shape)
+    _check(ctx, lib().get_photoexcitation_rates(ctx, cell_begin, n_cells, _ptr(R_lu), _ptr(R_ul),
+                                                _ptr(Jbar)))
+    return R_lu, R_ul, Jbar
+
+
+def get_spectrum(ctx, kind=0, out=None):
+    sz = get_sizes(ctx)
+    if out is None:
+        out = np.zeros(sz["spec_bins"]) if kind == 2 else np.zeros((sz["spec_views"], sz["spec_bins"]))
+    _check(ctx, lib().get_spectrum(ctx, int(kind), _ptr(out), int(np.prod(out.shape))))
+    return out
+
+
+# ---- convenience --------------------------------------------------------------
+class Context:
+    """Owns one library context; methods mirror the C-ABI calls."""
+
+    def __init__(self, device=0, stream=None):
+        self.h = xt_create(device, stream)
+
+    def close(self):
+        if self.h is not None:
+            xt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, w, subdomains=None, pops=None, with_scatter_data=None):
+        """init_grid + load_atomic_data + set_populations from a workload object
+        (attributes as produced by the input generator)."""
+        sd = tuple(subdomains) if subdomains is not None else tuple(w.subdomains)
+        init_grid(self.h, w.nx, w.ny, w.nz, w.v_max, w.t, w.Te, w.ne, w.L_cell, w.band_A,
+                  rho=w.rho, deposition=w.deposition, subdomains=sd)
+        load_atomic_data(self.h, w.level_off, w.E_level, w.g_level, w.lo, w.up, w.lambda_A,
+                         w.f_lu, n_ion_density=w.n_ion_density, ups_down=with_scatter_data)
+        set_populations(self.h, w.pops if pops is None else pops)
+
+    def transport(self, w, **kw):
+        kw.setdefault("n_packets", w.n_packets)
+        kw.setdefault("seed", w.seed)
+        kw.setdefault("spec_lam0_A", w.spec_band_A[0])
+        kw.setdefault("spec_nbins", w.spec_band_A[1])
+        return run_transport(self.h, **kw)
+
+    def __getattr__(self, name):
+        f = globals().get(name)
+        if callable(f) and name in _CTX_FUNCS:
+            return lambda *a, **k: f(self.h, *a, **k)
+        raise AttributeError(name)
+
+
+_CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations",
+              "get_sobolev_tau", "run_transport", "get_estimators", "get_photoexcitation_rates",
+              "get_spectrum", "get_sizes"}

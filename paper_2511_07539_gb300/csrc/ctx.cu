@@ -1,0 +1,538 @@
+// Context, data upload, A1 (Sobolev tau/beta), A7 (rates) and A5 (spectrum
+// normalisation) of the GB300 transport library.  See include/extrass.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "xt_internal.cuh"
+
+namespace xt {
+
+int fail(xt_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(xt_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, XT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int copy(xt_ctx* c, void* dst, const void* src, size_t n, const char* what) {
+  if (n == 0) return XT_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return XT_OK;
+}
+
+int alloc(xt_ctx* c, void** p, size_t bytes, const char* what) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (bytes == 0) return XT_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, XT_ENOMEM, std::string("cudaMalloc failed for ") + what + " (" +
+                                  std::to_string(bytes) + " bytes)");
+  }
+  return XT_OK;
+}
+
+void release(void** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+int ensure_scratch(xt_ctx* c, size_t bytes) {
+  if (bytes <= c->scratch_bytes) return XT_OK;
+  cudaStreamSynchronize(c->stream);
+  int rc = alloc(c, &c->d_scratch, bytes, "scratch");
+  c->scratch_bytes = rc == XT_OK ? bytes : 0;
+  return rc;
+}
+
+// dst[row(c)][j] = src[c][j]  (natural -> blocked rows), width W
+__global__ void k_nat_to_row(Geometry g, const double* __restrict__ src, double* __restrict__ dst,
+                             int64_t W) {
+  int64_t n = g.ncell * W;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = i / W, j = i - c * W;
+    int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    dst[row_of(g, ix, iy, iz) * W + j] = src[i];
+  }
+}
+
+__global__ void k_row_to_nat(Geometry g, const double* __restrict__ src, double* __restrict__ dst,
+                             int64_t W) {
+  int64_t n = g.ncell * W;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = i / W, j = i - c * W;
+    int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    dst[i] = src[row_of(g, ix, iy, iz) * W + j];
+  }
+}
+
+static int grid_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
+}
+
+// Upload a natural-order [ncell][W] array (host or device) into blocked rows.
+static int upload_rows(xt_ctx* c, const double* src, double** dst, int64_t W, const char* what) {
+  size_t bytes = (size_t)c->geo.ncell * W * sizeof(double);
+  int rc = alloc(c, (void**)dst, bytes, what);
+  if (rc) return rc;
+  const double* dsrc = src;
+  if (!is_device_ptr(src)) {
+    if ((rc = ensure_scratch(c, bytes))) return rc;
+    if ((rc = copy(c, c->d_scratch, src, bytes, what))) return rc;
+    dsrc = (const double*)c->d_scratch;
+  }
+  k_nat_to_row<<<grid_blocks(c->geo.ncell * W, 256), 256, 0, c->stream>>>(c->geo, dsrc, *dst, W);
+  XT_CUDA(c, cudaGetLastError());
+  return XT_OK;
+}
+
+// Run `fill(dev_out)` writing `bytes` and deliver them to `user` (host or device).
+template <class F>
+static int deliver(xt_ctx* c, void* user, size_t bytes, F fill) {
+  if (!user) return XT_OK;
+  if (is_device_ptr(user)) {
+    fill(user);
+    XT_CUDA(c, cudaGetLastError());
+    return XT_OK;
+  }
+  int rc = ensure_scratch(c, bytes);
+  if (rc) return rc;
+  fill(c->d_scratch);
+  XT_CUDA(c, cudaGetLastError());
+  return copy(c, user, c->d_scratch, bytes, "device-to-host copy");
+}
+
+template <class T>
+static int to_host(xt_ctx* c, const T* src, size_t n, std::vector<T>& out, const char* what) {
+  out.resize(n);
+  if (n == 0) return XT_OK;
+  cudaError_t e = cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  return XT_OK;
+}
+
+template <class T>
+static int to_device(xt_ctx* c, const std::vector<T>& v, T** dst, const char* what) {
+  int rc = alloc(c, (void**)dst, v.size() * sizeof(T), what);
+  if (rc) return rc;
+  return copy(c, *dst, v.data(), v.size() * sizeof(T), what);
+}
+
+// ---- A1: tau_S, Eq. (tau_Sobolev), and beta_S, Eq. (beta_Sobolev) ----------
+__device__ __forceinline__ double beta_sobolev(double tau) {
+  return tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+}
+
+__global__ void k_tau_beta(Geometry g, LineTable L, const double* __restrict__ pops,
+                           const int* __restrict__ sorted_of, int64_t c0, int64_t nc,
+                           double* __restrict__ tau_out, double* __restrict__ beta_out) {
+  int64_t n = nc * L.nline;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cl = i / L.nline;
+    int l = (int)(i - cl * L.nline);
+    int64_t c = c0 + cl;
+    int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    const double* pc = pops + row_of(g, ix, iy, iz) * L.nlev;
+    int s = sorted_of[l];
+    double tau = L.K[s] * (pc[L.lo[s]] - L.gratio[s] * pc[L.up[s]]);
+    if (tau_out) tau_out[i] = tau;
+    if (beta_out) beta_out[i] = beta_sobolev(tau);
+  }
+}
+
+// ---- A7: rates from estimators -------------------------------------------
+__global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops,
+                        const double* __restrict__ S, const double* __restrict__ invB,
+                        const int* __restrict__ sorted_of, int64_t c0, int64_t nc, double V,
+                        int which, double* __restrict__ out) {
+  int64_t n = nc * L.nline;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cl = i / L.nline;
+    int l = (int)(i - cl * L.nline);
+    int64_t c = c0 + cl;
+    int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    int64_t row = row_of(g, ix, iy, iz);
+    int s = sorted_of[l];
+    double v = S[row * L.nline + s];
+    if (which > 0) {
+      double nl = pops[row * L.nlev + L.lo[s]];
+      double R = nl > 0.0 ? v / (nl * V) : 0.0;
+      v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
+    }
+    out[i] = v;
+  }
+}
+
+// ---- A5: spectrum normalisation -------------------------------------------
+__global__ void k_spectrum(const double* __restrict__ E, int n_theta, int n_phi, int nb,
+                           double lam0, double dlog, int kind, double* __restrict__ out) {
+  int views = n_theta * n_phi;
+  int64_t n = kind == 2 ? nb : (int64_t)views * nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int b = (int)(i % nb);
+    double e0 = lam0 * pow(1.0 + dlog, (double)b), e1 = lam0 * pow(1.0 + dlog, (double)(b + 1));
+    double dlam = e1 - e0;
+    if (kind == 2) {
+      double s = 0.0;
+      for (int k = 0; k < views; ++k) s += E[(int64_t)k * nb + b];
+      out[i] = s / dlam;
+    } else {
+      int k = (int)(i / nb);
+      double th0 = kPi * (k / n_phi) / n_theta, th1 = kPi * (k / n_phi + 1) / n_theta;
+      double dOm = (2.0 * kPi / n_phi) * (cos(th0) - cos(th1));
+      out[i] = kind == 0 ? E[i] : 4.0 * kPi / dOm * E[i] / dlam;
+    }
+  }
+}
+
+}  // namespace xt
+
+using namespace xt;
+
+extern "C" {
+
+int xt_create(xt_ctx** out, int device, void* cuda_stream) {
+  if (!out) return XT_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return XT_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return XT_ECUDA;
+  xt_ctx* c = new xt_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaEventCreate(&c->ev0);
+  cudaEventCreate(&c->ev1);
+  cudaEventCreate(&c->ev2);
+  if (alloc(c, (void**)&c->d_ledger, LG_N * sizeof(double), "ledger")) { delete c; return XT_ENOMEM; }
+  *out = c;
+  return XT_OK;
+}
+
+void xt_destroy(xt_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  void** ptrs[] = {(void**)&c->d_Te, (void**)&c->d_ne, (void**)&c->d_rho, (void**)&c->d_dep,
+                   (void**)&c->d_L, (void**)&c->d_level_off, (void**)&c->d_g, (void**)&c->d_E,
+                   (void**)&c->d_nu, (void**)&c->d_K, (void**)&c->d_gratio, (void**)&c->d_hnu,
+                   (void**)&c->d_A, (void**)&c->d_invB, (void**)&c->d_lo, (void**)&c->d_up,
+                   (void**)&c->d_orig, (void**)&c->d_down_off, (void**)&c->d_down_line,
+                   (void**)&c->d_nion, (void**)&c->d_ups_down, (void**)&c->d_pops, (void**)&c->d_S,
+                   (void**)&c->d_qoff, (void**)&c->d_Lc, (void**)&c->d_wline, (void**)&c->d_spec,
+                   (void**)&c->d_ledger, (void**)&c->d_scratch, (void**)&c->d_lines,
+                   (void**)&c->d_pool_f, (void**)&c->d_pool_i, (void**)&c->d_pool_pid,
+                   (void**)&c->d_counters, (void**)&c->d_hist};
+  for (void** p : ptrs) release(p);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  delete c;
+}
+
+const char* xt_last_error(const xt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int init_grid(xt_ctx* c, const xt_grid_desc* g) {
+  if (!c || !g) return fail(c, XT_EINVAL, "init_grid: null argument");
+  cudaSetDevice(c->device);
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(c, XT_EINVAL, "init_grid: nx, ny, nz must be >= 1");
+  if (g->sx < 1 || g->sy < 1 || g->sz < 1 || g->nx % g->sx || g->ny % g->sy || g->nz % g->sz)
+    return fail(c, XT_EINVAL, "init_grid: sx, sy, sz must be >= 1 and divide nx, ny, nz");
+  if (!(g->v_max > 0) || !(g->t > 0)) return fail(c, XT_EINVAL, "init_grid: v_max and t must be > 0");
+  if (!g->Te || !g->ne) return fail(c, XT_EINVAL, "init_grid: Te and ne are required");
+  if (g->L_cell && !(g->band_hi_A > g->band_lo_A && g->band_lo_A > 0))
+    return fail(c, XT_EINVAL, "init_grid: band_lo_A < band_hi_A required with L_cell");
+  Geometry& G = c->geo;
+  G.nx = g->nx; G.ny = g->ny; G.nz = g->nz;
+  G.bx = g->nx / g->sx; G.by = g->ny / g->sy; G.bz = g->nz / g->sz;
+  G.sx = g->sx; G.sy = g->sy;
+  G.ncell = (int64_t)g->nx * g->ny * g->nz;
+  G.R = g->v_max * g->t;
+  G.dx = 2.0 * G.R / g->nx; G.dy = 2.0 * G.R / g->ny; G.dz = 2.0 * G.R / g->nz;
+  G.ct = kC * g->t;
+  G.inv_ct = 1.0 / G.ct;
+  c->sx = g->sx; c->sy = g->sy; c->sz = g->sz;
+  c->v_max = g->v_max; c->t = g->t;
+  c->band_lo_A = g->band_lo_A; c->band_hi_A = g->band_hi_A;
+  int rc;
+  if ((rc = upload_rows(c, g->Te, &c->d_Te, 1, "Te"))) return rc;
+  if ((rc = upload_rows(c, g->ne, &c->d_ne, 1, "ne"))) return rc;
+  if (g->rho && (rc = upload_rows(c, g->rho, &c->d_rho, 1, "rho"))) return rc;
+  if (g->deposition && (rc = upload_rows(c, g->deposition, &c->d_dep, 1, "deposition"))) return rc;
+  c->h_L.assign(G.ncell, 0.0);
+  if (g->L_cell) {
+    if ((rc = copy(c, c->h_L.data(), g->L_cell, G.ncell * sizeof(double), "L_cell"))) return rc;
+    if ((rc = upload_rows(c, g->L_cell, &c->d_L, 1, "L_cell"))) return rc;
+  }
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int64_t i = 0; i < G.ncell; ++i)
+    if (!(c->h_L[i] >= 0.0) || !std::isfinite(c->h_L[i]))
+      return fail(c, XT_EINVAL, "init_grid: L_cell must be finite and >= 0 (cell " + std::to_string(i) + ")");
+  c->have_grid = true;
+  c->have_atoms = c->have_pops = c->have_S = false;
+  c->qoff_N = -1;
+  return XT_OK;
+}
+
+int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
+  if (!c || !a) return fail(c, XT_EINVAL, "load_atomic_data: null argument");
+  if (!c->have_grid) return fail(c, XT_ESTATE, "load_atomic_data: call init_grid first");
+  cudaSetDevice(c->device);
+  if (a->n_ion < 1 || a->nline < 0 || !a->level_off || !a->E_level || !a->g_level)
+    return fail(c, XT_EINVAL, "load_atomic_data: n_ion >= 1, level_off, E_level, g_level required");
+  if (a->nline > 0 && (!a->lo || !a->up || !a->lambda_A || !a->f_lu))
+    return fail(c, XT_EINVAL, "load_atomic_data: lo, up, lambda_A, f_lu required");
+  int rc;
+  std::vector<int> off(a->n_ion + 1);
+  if ((rc = copy(c, off.data(), a->level_off, off.size() * sizeof(int), "level_off"))) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (off[0] != 0) return fail(c, XT_EINVAL, "load_atomic_data: level_off[0] must be 0");
+  for (int z = 0; z < a->n_ion; ++z)
+    if (off[z + 1] <= off[z]) return fail(c, XT_EINVAL, "load_atomic_data: level_off must increase (ion " + std::to_string(z) + ")");
+  int nlev = off[a->n_ion], nl = a->nline;
+  std::vector<double> E(nlev), g(nlev), lam(nl), f(nl), ups;
+  std::vector<int> lo(nl), up(nl);
+  if ((rc = copy(c, E.data(), a->E_level, nlev * sizeof(double), "E_level"))) return rc;
+  if ((rc = copy(c, g.data(), a->g_level, nlev * sizeof(double), "g_level"))) return rc;
+  if ((rc = copy(c, lo.data(), a->lo, nl * sizeof(int), "lo"))) return rc;
+  if ((rc = copy(c, up.data(), a->up, nl * sizeof(int), "up"))) return rc;
+  if ((rc = copy(c, lam.data(), a->lambda_A, nl * sizeof(double), "lambda_A"))) return rc;
+  if ((rc = copy(c, f.data(), a->f_lu, nl * sizeof(double), "f_lu"))) return rc;
+  if (a->ups_down) {
+    ups.resize(nlev);
+    if ((rc = copy(c, ups.data(), a->ups_down, nlev * sizeof(double), "ups_down"))) return rc;
+  } else {
+    ups.assign(nlev, 0.0);
+  }
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> ion_of(nlev);
+  for (int z = 0; z < a->n_ion; ++z)
+    for (int i = off[z]; i < off[z + 1]; ++i) ion_of[i] = z;
+  for (int i = 0; i < nlev; ++i)
+    if (!(g[i] > 0)) return fail(c, XT_EINVAL, "load_atomic_data: g_level must be > 0 (level " + std::to_string(i) + ")");
+  for (int l = 0; l < nl; ++l) {
+    if (lo[l] < 0 || up[l] >= nlev || lo[l] >= up[l] || ion_of[lo[l]] != ion_of[up[l]])
+      return fail(c, XT_EINVAL, "load_atomic_data: line " + std::to_string(l) + " needs 0 <= lo < up < nlev in one ion");
+    if (!(lam[l] > 0) || !(f[l] > 0))
+      return fail(c, XT_EINVAL, "load_atomic_data: lambda_A and f_lu must be > 0 (line " + std::to_string(l) + ")");
+  }
+  // descending frequency, ties in ascending caller index
+  std::vector<double> nu(nl);
+  for (int l = 0; l < nl; ++l) nu[l] = kC / (lam[l] * 1e-8);
+  std::vector<int> order(nl);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return nu[i] > nu[j]; });
+  c->h_orig_of = order;
+  c->h_sorted_of.assign(nl, 0);
+  for (int s = 0; s < nl; ++s) c->h_sorted_of[order[s]] = s;
+  const double pie2mc = kPi * kE * kE / (kMe * kC);
+  std::vector<double> s_nu(nl), s_K(nl), s_gr(nl), s_hnu(nl), s_A(nl), s_invB(nl);
+  std::vector<int> s_lo(nl), s_up(nl);
+  for (int s = 0; s < nl; ++s) {
+    int l = order[s];
+    double lc = lam[l] * 1e-8;
+    s_nu[s] = nu[l];
+    s_K[s] = pie2mc * f[l] * lc * c->t;
+    s_gr[s] = g[lo[l]] / g[up[l]];
+    s_hnu[s] = kH * nu[l];
+    s_A[s] = 8.0 * kPi * kPi * kE * kE / (kMe * kC * lc * lc) * s_gr[s] * f[l];
+    s_invB[s] = kH * nu[l] / (4.0 * kPi * pie2mc * f[l]);
+    s_lo[s] = lo[l];
+    s_up[s] = up[l];
+  }
+  // radiative down-lines per upper level, ascending caller index
+  std::vector<int> doff(nlev + 1, 0), dline(nl);
+  for (int l = 0; l < nl; ++l) doff[up[l] + 1]++;
+  for (int u = 0; u < nlev; ++u) doff[u + 1] += doff[u];
+  std::vector<int> fill(nlev, 0);
+  for (int l = 0; l < nl; ++l) dline[doff[up[l]] + fill[up[l]]++] = c->h_sorted_of[l];
+  c->n_ion = a->n_ion; c->nlev = nlev; c->nline = nl;
+  c->h_level_off = off; c->h_g = g; c->h_E = E;
+  if ((rc = to_device(c, off, &c->d_level_off, "level_off"))) return rc;
+  if ((rc = to_device(c, g, &c->d_g, "g"))) return rc;
+  if ((rc = to_device(c, E, &c->d_E, "E"))) return rc;
+  std::vector<double> packed(4 * (size_t)nl);
+  for (int s = 0; s < nl; ++s) {
+    packed[4 * s] = s_nu[s];
+    packed[4 * s + 1] = s_K[s];
+    packed[4 * s + 2] = s_gr[s];
+    int64_t lu = (int64_t)(uint32_t)s_lo[s] | ((int64_t)s_up[s] << 32);
+    std::memcpy(&packed[4 * s + 3], &lu, sizeof(lu));
+  }
+  if ((rc = to_device(c, packed, &c->d_lines, "line table"))) return rc;
+  if ((rc = to_device(c, s_nu, &c->d_nu, "nu"))) return rc;
+  if ((rc = to_device(c, s_K, &c->d_K, "K"))) return rc;
+  if ((rc = to_device(c, s_gr, &c->d_gratio, "gratio"))) return rc;
+  if ((rc = to_device(c, s_hnu, &c->d_hnu, "hnu"))) return rc;
+  if ((rc = to_device(c, s_A, &c->d_A, "A"))) return rc;
+  if ((rc = to_device(c, s_invB, &c->d_invB, "invB"))) return rc;
+  if ((rc = to_device(c, s_lo, &c->d_lo, "lo"))) return rc;
+  if ((rc = to_device(c, s_up, &c->d_up, "up"))) return rc;
+  if ((rc = to_device(c, c->h_sorted_of, &c->d_orig, "sorted_of"))) return rc;
+  if ((rc = to_device(c, doff, &c->d_down_off, "down_off"))) return rc;
+  if ((rc = to_device(c, dline, &c->d_down_line, "down_line"))) return rc;
+  if ((rc = to_device(c, ups, &c->d_ups_down, "ups_down"))) return rc;
+  if (a->n_ion_density && (rc = upload_rows(c, a->n_ion_density, &c->d_nion, a->n_ion, "n_ion_density")))
+    return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_atoms = true;
+  c->have_pops = c->have_S = false;
+  c->qoff_N = -1;
+  return XT_OK;
+}
+
+int set_populations(xt_ctx* c, const double* pops) {
+  if (!c || !pops) return fail(c, XT_EINVAL, "set_populations: null argument");
+  if (!c->have_atoms) return fail(c, XT_ESTATE, "set_populations: load_atomic_data first");
+  cudaSetDevice(c->device);
+  int rc;
+  if (c->d_pops) {   // reuse the allocation
+    size_t bytes = (size_t)c->geo.ncell * c->nlev * sizeof(double);
+    const double* src = pops;
+    if (!is_device_ptr(pops)) {
+      if ((rc = ensure_scratch(c, bytes))) return rc;
+      if ((rc = copy(c, c->d_scratch, pops, bytes, "pops"))) return rc;
+      src = (const double*)c->d_scratch;
+    }
+    k_nat_to_row<<<grid_blocks(c->geo.ncell * c->nlev, 256), 256, 0, c->stream>>>(c->geo, src, c->d_pops, c->nlev);
+    XT_CUDA(c, cudaGetLastError());
+  } else if ((rc = upload_rows(c, pops, &c->d_pops, c->nlev, "pops"))) {
+    return rc;
+  }
+  c->have_pops = true;
+  if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;
+  return XT_OK;
+}
+
+int get_populations(xt_ctx* c, double* pops, size_t n_cap) {
+  if (!c || !pops) return fail(c, XT_EINVAL, "get_populations: null argument");
+  if (!c->have_pops) return fail(c, XT_ESTATE, "get_populations: no populations");
+  size_t n = (size_t)c->geo.ncell * c->nlev;
+  if (n_cap < n) return fail(c, XT_EINVAL, "get_populations: n_cap < ncell*nlev");
+  cudaSetDevice(c->device);
+  int rc = deliver(c, pops, n * sizeof(double), [&](void* d) {
+    k_row_to_nat<<<grid_blocks((int64_t)n, 256), 256, 0, c->stream>>>(c->geo, c->d_pops, (double*)d, c->nlev);
+  });
+  if (rc) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
+static LineTable line_table(xt_ctx* c) {
+  LineTable L;
+  L.nline = c->nline; L.nlev = c->nlev;
+  L.nu = c->d_nu; L.K = c->d_K; L.gratio = c->d_gratio; L.hnu = c->d_hnu; L.A = c->d_A;
+  L.lo = c->d_lo; L.up = c->d_up; L.down_off = c->d_down_off; L.down_line = c->d_down_line;
+  return L;
+}
+
+static int check_range(xt_ctx* c, int64_t c0, int64_t nc, const char* who) {
+  if (c0 < 0 || nc < 0 || c0 + nc > c->geo.ncell)
+    return fail(c, XT_EINVAL, std::string(who) + ": cell range outside the grid");
+  return XT_OK;
+}
+
+int get_sobolev_tau(xt_ctx* c, int64_t c0, int64_t nc, double* tau, double* beta) {
+  if (!c) return XT_EINVAL;
+  if (!c->have_pops) return fail(c, XT_ESTATE, "get_sobolev_tau: set_populations first");
+  int rc = check_range(c, c0, nc, "get_sobolev_tau");
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  LineTable L = line_table(c);
+  size_t bytes = (size_t)nc * c->nline * sizeof(double);
+  int64_t n = nc * c->nline;
+  if (tau && (rc = deliver(c, tau, bytes, [&](void* d) {
+        k_tau_beta<<<grid_blocks(n, 256), 256, 0, c->stream>>>(c->geo, L, c->d_pops, c->d_orig, c0, nc, (double*)d, nullptr);
+      }))) return rc;
+  if (beta) {
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if ((rc = deliver(c, beta, bytes, [&](void* d) {
+          k_tau_beta<<<grid_blocks(n, 256), 256, 0, c->stream>>>(c->geo, L, c->d_pops, c->d_orig, c0, nc, nullptr, (double*)d);
+        }))) return rc;
+  }
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
+static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int which) {
+  LineTable L = line_table(c);
+  double V = c->geo.dx * c->geo.dy * c->geo.dz;
+  size_t bytes = (size_t)nc * c->nline * sizeof(double);
+  int64_t n = nc * c->nline;
+  int rc = deliver(c, out, bytes, [&](void* d) {
+    k_rates<<<grid_blocks(n, 256), 256, 0, c->stream>>>(c->geo, L, c->d_pops, c->d_S, c->d_invB, c->d_orig, c0, nc, V, which, (double*)d);
+  });
+  if (rc) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
+int get_estimators(xt_ctx* c, int64_t c0, int64_t nc, double* S) {
+  if (!c || !S) return fail(c, XT_EINVAL, "get_estimators: null argument");
+  if (!c->have_S) return fail(c, XT_ESTATE, "get_estimators: run_transport first");
+  int rc = check_range(c, c0, nc, "get_estimators");
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  return rates_common(c, c0, nc, S, 0);
+}
+
+int get_photoexcitation_rates(xt_ctx* c, int64_t c0, int64_t nc, double* R_lu, double* R_ul, double* Jbar) {
+  if (!c) return XT_EINVAL;
+  if (!c->have_S) return fail(c, XT_ESTATE, "get_photoexcitation_rates: run_transport first");
+  int rc = check_range(c, c0, nc, "get_photoexcitation_rates");
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  if (R_lu && (rc = rates_common(c, c0, nc, R_lu, 1))) return rc;
+  if (R_ul && (rc = rates_common(c, c0, nc, R_ul, 2))) return rc;
+  if (Jbar && (rc = rates_common(c, c0, nc, Jbar, 3))) return rc;
+  return XT_OK;
+}
+
+int get_spectrum(xt_ctx* c, int32_t kind, double* out, size_t n_cap) {
+  if (!c || !out) return fail(c, XT_EINVAL, "get_spectrum: null argument");
+  if (!c->d_spec) return fail(c, XT_ESTATE, "get_spectrum: run_transport first");
+  if (kind < 0 || kind > 2) return fail(c, XT_EINVAL, "get_spectrum: kind must be 0, 1 or 2");
+  size_t n = kind == 2 ? (size_t)c->spec_bins : (size_t)c->spec_views * c->spec_bins;
+  if (n_cap < n) return fail(c, XT_EINVAL, "get_spectrum: n_cap too small");
+  cudaSetDevice(c->device);
+  int rc = deliver(c, out, n * sizeof(double), [&](void* d) {
+    k_spectrum<<<grid_blocks((int64_t)n, 256), 256, 0, c->stream>>>(c->d_spec, c->n_theta, c->n_phi, c->spec_bins, c->spec_lam0, c->spec_dlog, kind, (double*)d);
+  });
+  if (rc) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
+int get_sizes(xt_ctx* c, xt_sizes* o) {
+  if (!c || !o) return XT_EINVAL;
+  o->ncell = c->geo.ncell; o->nlev = c->nlev; o->nline = c->nline; o->n_ion = c->n_ion;
+  o->spec_views = c->spec_views; o->spec_bins = c->spec_bins;
+  o->store_bytes = (int64_t)c->S_bytes;
+  return XT_OK;
+}
+
+}  // extern "C"

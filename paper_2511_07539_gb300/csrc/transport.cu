@@ -1,0 +1,791 @@
+// Packet transport through the homologous Cartesian grid (A2-A6).
+//
+// Three kernels per chunk of packets (Secs. 2.3, 2.3.2 of the paper):
+//   k_emit     one thread per packet, all lanes doing the same work: emitting
+//              cell from the integer packet quota, position uniform in the
+//              cell, isotropic direction, comoving frequency from the cell's
+//              emission (flat-nu band, or lines weighted by A dE beta N_u,
+//              Eq. (thin_emissivity)); lab frequency nu_cmf / (1 - n.r/ct); the
+//              cell-walk state (distance to the next wall along each axis and
+//              the distance between walls).  Written to a packet pool (SoA).
+//   k_trace    persistent: every lane owns one packet; a lane whose packet ends
+//              takes the next pool entry at once (warp-aggregated counter), so
+//              warps never wait for their longest-lived packet.  One loop
+//              iteration is one cell segment: the comoving frequency at the wall,
+//              nu0 - (nu_lab/ct) s_wall, bounds the lines met in the cell (every
+//              line with nu_end < nu_line <= current nu, in descending order).
+//              Lines with tau_S > tau_min (Eq. (tau_Sobolev)) attenuate the
+//              packet by 1 - e^-tau and add dN / f_corr to the estimator; the
+//              packet stops once its photon energy at the line is below e_cut of
+//              its starting energy.  Scatter mode absorbs the whole packet with
+//              probability 1 - e^-tau and re-emits it in a down-line of the upper
+//              level (weights A beta) or destroys it collisionally.
+//   k_escape   escaped packets: lab energy into (viewing direction, log-lambda
+//              bin), done apart so that the trace loop carries no trigonometry.
+// With subdomain rounds (Sec. 2.4.1) a packet that crosses into another
+// subdomain stops and is queued; the queue is sorted by destination subdomain
+// and traced again in the next round, until no packet is left.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "philox.cuh"
+#include "xt_internal.cuh"
+
+namespace xt {
+
+enum PoolField { F_R0X, F_R0Y, F_R0Z, F_NX, F_NY, F_NZ, F_TMX, F_TMY, F_TMZ, F_TDX, F_TDY, F_TDZ,
+                 F_NULAB, F_NU0, F_N, F_T, NF };
+
+struct Pool {           // structure of arrays, capacity cap
+  int64_t cap;
+  double* f;            // [NF][cap]
+  int* cell;            // natural index of the current cell
+  int* cursor;          // next sorted line to test
+  int* events;
+  int* ndraw;           // scatter draws used
+  int* inter;           // scatter interactions
+  int64_t* pid;         // packet id
+  __device__ __forceinline__ double& F(int k, int64_t i) const { return f[(int64_t)k * cap + i]; }
+};
+
+struct EmitArgs {
+  Geometry g;
+  const int64_t* __restrict__ qoff;   // natural [ncell+1]
+  const double* __restrict__ Epk;     // natural [ncell] packet energy L_c / n_c
+  const double* __restrict__ cdf;     // [row][caller line] (line emission)
+  const double* __restrict__ Lc;      // natural [ncell]
+  const int* __restrict__ sorted_of;
+  const double* __restrict__ nu_tab;  // sorted
+  int nline, emission;
+  uint64_t seed;
+  double nu_lo, nu_hi, e_cut;
+  int64_t p_begin, n;
+  Pool pool;
+  double* __restrict__ ledger;
+  double* __restrict__ records;       // record of packet p at (p - rec_base)
+  int64_t rec_base;
+};
+
+struct TraceArgs {
+  Geometry g;
+  const double2* __restrict__ lines;  // per sorted line: nu, K, gratio, (lo, up)
+  int nline, nlev;
+  const double* __restrict__ pops;    // [row][nlev]
+  double* __restrict__ S;             // [row][sorted line]
+  const double* __restrict__ A;       // sorted
+  const int* __restrict__ down_off;
+  const int* __restrict__ down_line;
+  const double* __restrict__ Te;      // row order
+  const double* __restrict__ ne;
+  const double* __restrict__ ups_down;
+  const double* __restrict__ glev;
+  Pool pool;
+  const int* __restrict__ list;       // pool indices to trace (nullptr: 0..n_list-1)
+  int64_t n_list;
+  unsigned long long* __restrict__ counter;
+  int* __restrict__ esc;              // escaped pool indices
+  unsigned long long* __restrict__ n_esc;
+  int* __restrict__ out;              // queued pool indices (subdomain rounds)
+  unsigned long long* __restrict__ n_out;
+  int rounds;                         // 0: no subdomain boundaries
+  uint64_t seed;
+  double tau_min, ct, inv_ct;
+  int64_t max_events;
+  double* __restrict__ ledger;
+  double* __restrict__ records;
+  int64_t rec_base;
+};
+
+struct EscArgs {
+  Pool pool;
+  const int* __restrict__ esc;
+  int64_t n_esc;
+  double* __restrict__ spec;
+  int n_theta, n_phi, nbins;
+  double lam0, log1p_dlog;
+  double* __restrict__ ledger;
+  double* __restrict__ records;
+  int64_t rec_base;
+};
+
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+
+// 32-byte line record: x = nu, y = K, z = g_l/g_u, w = (lo | up << 32) bit pattern
+struct LineRec { double x, y, z, w; };
+__device__ __forceinline__ LineRec ldline(const double2* __restrict__ t, int s) {
+  const double2 a = __ldg(t + 2 * s), b = __ldg(t + 2 * s + 1);
+  return LineRec{a.x, a.y, b.x, b.y};
+}
+
+__device__ __forceinline__ void isotropic(double umu, double uphi, double n[3]) {
+  const double mu = 2.0 * umu - 1.0;
+  const double phi = 2.0 * kPi * uphi;
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  const double st = sqrt(1.0 - mu * mu);
+  n[0] = st * cp; n[1] = st * sp; n[2] = mu;
+}
+
+__device__ __forceinline__ double sobolev_beta(double tau) {
+  return tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+}
+
+// Distance to the next wall along each axis and between walls, from r in cell idx.
+__device__ __forceinline__ void walk_init(const Geometry& g, const int idx[3], const double r[3],
+                                          const double n[3], double tm[3], double td[3]) {
+  const double d[3] = {g.dx, g.dy, g.dz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (n[k] > 0.0) {
+      const double inv = 1.0 / n[k];
+      tm[k] = fmax(((-g.R + (idx[k] + 1) * d[k]) - r[k]) * inv, 0.0);
+      td[k] = d[k] * inv;
+    } else if (n[k] < 0.0) {
+      const double inv = 1.0 / n[k];
+      tm[k] = fmax(((-g.R + idx[k] * d[k]) - r[k]) * inv, 0.0);
+      td[k] = -d[k] * inv;
+    } else {
+      tm[k] = INFINITY;
+      td[k] = INFINITY;
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void warp_flush(double (&acc)[W], double* ledger, const int (&slot)[W]) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(ledger + slot[k], v);
+  }
+}
+
+// Warp-aggregated append of `idx` by the lanes of the current active set that
+// have `want`; returns nothing, writes buf[slot].
+__device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsigned long long* n) {
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, want);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
+  base = __shfl_sync(act, base, leader);
+  if (want) buf[base + __popc(m & ((1u << lane) - 1u))] = idx;
+}
+
+// ---------------------------------------------------------------- emission
+__global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
+  double acc[2] = {0.0, 0.0};
+  const Geometry& g = a.g;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = a.p_begin + i;
+    int64_t lo = 0, hi = g.ncell;         // last c with qoff[c] <= p
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (a.qoff[mid] <= p) lo = mid; else hi = mid;
+    }
+    const int64_t c = lo;
+    const int idx[3] = {(int)(c % g.nx), (int)((c / g.nx) % g.ny), (int)(c / ((int64_t)g.nx * g.ny))};
+    const double d[3] = {g.dx, g.dy, g.dz};
+    const double E0 = a.Epk[c];
+    const U4 u = draw(a.seed, p, 0), v = draw(a.seed, p, 1);
+    double r[3], n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = (-g.R + idx[k] * d[k]) + u.u[k] * d[k];
+    isotropic(u.u[3], v.u[0], n);
+    double nu_cmf;
+    int cursor;
+    if (a.emission == XT_EMIT_BAND) {
+      nu_cmf = a.nu_lo + v.u[1] * (a.nu_hi - a.nu_lo);
+      int l0 = 0, l1 = a.nline;           // first sorted line with nu <= nu_cmf
+      const long long nb = bits(nu_cmf);
+      while (l0 < l1) {
+        const int mid = (l0 + l1) >> 1;
+        if (bits(a.nu_tab[mid]) <= nb) l1 = mid; else l0 = mid + 1;
+      }
+      cursor = l0;
+    } else {
+      const double* cdf = a.cdf + row_of(g, idx[0], idx[1], idx[2]) * a.nline;
+      const double x = v.u[1] * a.Lc[c];
+      int l0 = 0, l1 = a.nline;           // first caller line with x < cdf
+      while (l0 < l1) {
+        const int mid = (l0 + l1) >> 1;
+        if (x < cdf[mid]) l1 = mid; else l0 = mid + 1;
+      }
+      const int s = a.sorted_of[l0 < a.nline ? l0 : a.nline - 1];
+      nu_cmf = a.nu_tab[s];
+      cursor = s + 1;
+    }
+    const double nu_lab = nu_cmf / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
+    const double N = E0 / (kH * nu_cmf);
+    double tm[3], td[3];
+    walk_init(g, idx, r, n, tm, td);
+    const Pool& P = a.pool;
+    P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
+    P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
+    P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
+    P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
+    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * E0;
+    P.cell[i] = (int)c; P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
+    P.pid[i] = p;
+    acc[0] += N;
+    acc[1] += E0;
+    if (a.records) {
+      double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+      rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
+    }
+  }
+  const int slots[2] = {LG_EMIT_N, LG_EMIT_E};
+  warp_flush(acc, a.ledger, slots);
+}
+
+// ---------------------------------------------------------------- trace
+enum { T_TESTS, T_EVENTS, T_ABS, T_DROP, T_GUARD, T_INTER, T_ABSE, T_REEM, T_THERM, T_NACC };
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
+  const Geometry& g = a.g;
+  const Pool& P = a.pool;
+  const int lane = threadIdx.x & 31;
+  const long long taumin_bits = __double_as_longlong(a.tau_min);
+  const long long thick_bits = __double_as_longlong(38.0);   // 1 - e^-tau == 1 exactly beyond
+  double acc[T_NACC];
+#pragma unroll
+  for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+
+  bool have = false;
+  int64_t i = 0;                         // pool slot
+  int idx[3] = {0, 0, 0}, sgn[3] = {1, 1, 1}, cursor = 0, events = 0;
+  int bx0 = 0, bx1 = 0, by0 = 0, by1 = 0, bz0 = 0, bz1 = 0;   // current subdomain box
+  int64_t row = 0;
+  double tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, nu0 = 0, aslope = 0, N = 0, T = 0;
+
+  for (;;) {
+    // ---- refill lanes whose packet ended (warp-aggregated)
+    {
+      const unsigned act = __activemask();
+      const unsigned m = __ballot_sync(act, !have);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(act, base, leader);
+        if (!have) {
+          const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
+          if (my < (unsigned long long)a.n_list) {
+            i = a.list ? a.list[my] : (int64_t)my;
+            const int c = P.cell[i];
+            idx[0] = c % g.nx; idx[1] = (c / g.nx) % g.ny; idx[2] = c / (g.nx * g.ny);
+            const double nx_ = P.F(F_NX, i), ny_ = P.F(F_NY, i), nz_ = P.F(F_NZ, i);
+            sgn[0] = nx_ > 0.0 ? 1 : -1; sgn[1] = ny_ > 0.0 ? 1 : -1; sgn[2] = nz_ > 0.0 ? 1 : -1;
+            tm[0] = P.F(F_TMX, i); tm[1] = P.F(F_TMY, i); tm[2] = P.F(F_TMZ, i);
+            td[0] = P.F(F_TDX, i); td[1] = P.F(F_TDY, i); td[2] = P.F(F_TDZ, i);
+            nu0 = P.F(F_NU0, i);
+            aslope = P.F(F_NULAB, i) * a.inv_ct;
+            N = P.F(F_N, i);
+            T = P.F(F_T, i);
+            cursor = P.cursor[i];
+            events = P.events[i];
+            row = row_of(g, idx[0], idx[1], idx[2]);
+            if (a.rounds) {
+              bx0 = (idx[0] / g.bx) * g.bx; bx1 = bx0 + g.bx;
+              by0 = (idx[1] / g.by) * g.by; by1 = by0 + g.by;
+              bz0 = (idx[2] / g.bz) * g.bz; bz1 = bz0 + g.bz;
+            }
+            have = true;
+          }
+        }
+      }
+    }
+    if (!have) break;
+
+    // ---- one cell segment
+    int axis = 0;
+    double sw = tm[0];
+    if (bits(tm[1]) < bits(sw)) { sw = tm[1]; axis = 1; }   // ties to the lowest axis
+    if (bits(tm[2]) < bits(sw)) { sw = tm[2]; axis = 2; }
+    const long long end_bits = bits(nu0 - aslope * sw);
+    const double* prow = a.pops + row * a.nlev;
+    int fate = -1;                        // -1 alive
+    bool restart = false;
+    while (cursor < a.nline) {
+      const LineRec L = ldline(a.lines, cursor);
+      if (bits(L.x) <= end_bits) break;
+      acc[T_TESTS] += 1.0;
+      const int lo = __double2loint(L.w), up = __double2hiint(L.w);
+      const double n_l = prow[lo], n_u = prow[up];
+      const double net = n_l - L.z * n_u;
+      const double tau = L.y * net;
+      if (bits(tau) > taumin_bits) {
+        ++events;
+        acc[T_EVENTS] += 1.0;
+        const double ome = bits(tau) >= thick_bits ? 1.0 : -expm1(-tau);
+        if (MODE == XT_MODE_ATTEN) {
+          const double dN = N * ome;
+          atomicAdd(a.S + row * a.nline + cursor, dN * n_l / net);   // dN / f_corr
+          N -= dN;
+          acc[T_ABS] += dN;
+          if (N * kH * L.x < T) { acc[T_DROP] += N; fate = 1; break; }
+        } else {
+          const int64_t p = P.pid[i];
+          const int nd = P.ndraw[i];
+          P.ndraw[i] = nd + 1;
+          const U4 w = draw(a.seed, p, 2 + (uint64_t)nd);
+          if (w.u[0] < ome) {
+            P.inter[i] += 1;
+            acc[T_INTER] += 1.0;
+            atomicAdd(a.S + row * a.nline + cursor, N * n_l / net);
+            acc[T_ABS] += N;
+            const double Ecmf = N * kH * L.x;
+            acc[T_ABSE] += Ecmf;
+            const int k0 = a.down_off[up], k1 = a.down_off[up + 1];
+            double Wtot = 8.629e-6 * a.ne[row] * a.ups_down[up] / (a.glev[up] * sqrt(a.Te[row]));
+            for (int k = k0; k < k1; ++k) {
+              const int m = a.down_line[k];
+              const LineRec M = ldline(a.lines, m);
+              Wtot += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+            }
+            const double x = w.u[1] * Wtot;
+            double run = 0.0;
+            int pick = -1;
+            for (int k = k0; k < k1; ++k) {
+              const int m = a.down_line[k];
+              const LineRec M = ldline(a.lines, m);
+              run += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+              if (x < run) { pick = m; break; }
+            }
+            if (pick < 0) { acc[T_THERM] += Ecmf; fate = 2; break; }
+            // move to the resonance point, re-emit isotropically in line `pick`
+            double r[3] = {P.F(F_R0X, i), P.F(F_R0Y, i), P.F(F_R0Z, i)};
+            double n[3] = {P.F(F_NX, i), P.F(F_NY, i), P.F(F_NZ, i)};
+            const double nu_lab = P.F(F_NULAB, i);
+            const double s_l = a.ct * (1.0 - L.x / nu_lab) - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) r[k] = r[k] + s_l * n[k];
+            isotropic(w.u[2], w.u[3], n);
+            const double nu_new = ldline(a.lines, pick).x;
+            N = Ecmf / (kH * nu_new);
+            acc[T_REEM] += Ecmf;
+            const double nl_new = nu_new / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * a.inv_ct);
+            walk_init(g, idx, r, n, tm, td);
+            sgn[0] = n[0] > 0.0 ? 1 : -1; sgn[1] = n[1] > 0.0 ? 1 : -1; sgn[2] = n[2] > 0.0 ? 1 : -1;
+            P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
+            P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
+            P.F(F_NULAB, i) = nl_new;
+            nu0 = nu_new;
+            aslope = nl_new * a.inv_ct;
+            cursor = pick + 1;
+            if (events >= a.max_events) { acc[T_GUARD] += 1.0; fate = 3; break; }
+            restart = true;
+            break;
+          }
+        }
+        if (events >= a.max_events) { acc[T_GUARD] += 1.0; fate = 3; break; }
+      }
+      ++cursor;
+    }
+    bool escaped = false, queued = false;
+    if (fate < 0 && !restart) {
+      idx[axis] += sgn[axis];
+      tm[axis] += td[axis];
+      const int nax = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
+      if (idx[axis] < 0 || idx[axis] >= nax) {
+        escaped = true;
+      } else {
+        row = row_of(g, idx[0], idx[1], idx[2]);
+        if (a.rounds && (idx[0] < bx0 || idx[0] >= bx1 || idx[1] < by0 || idx[1] >= by1 ||
+                         idx[2] < bz0 || idx[2] >= bz1))
+          queued = true;
+      }
+    }
+    // ---- packet leaves this lane: escaped, finished, or handed to another subdomain
+    const bool leave = escaped || queued || fate >= 0;
+    if (leave) {
+      P.F(F_N, i) = N;
+      P.events[i] = events;
+      if (queued || (MODE == XT_MODE_SCATTER && escaped)) {
+        P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
+        P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
+        P.F(F_NU0, i) = nu0;
+        P.cursor[i] = cursor;
+        P.cell[i] = (idx[2] * g.ny + idx[1]) * g.nx + idx[0];
+      }
+      if (fate >= 0 && a.records) {
+        double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
+        rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+        rec[6] = P.inter[i]; rec[10] = P.F(F_NULAB, i);
+      }
+      have = false;
+    }
+    warp_append(escaped, (int)i, a.esc, a.n_esc);
+    warp_append(queued, (int)i, a.out, a.n_out);
+  }
+  const int slots[T_NACC] = {LG_TESTS, LG_EVENTS, LG_ABS_N, LG_DROP_N, LG_GUARD, LG_INTERACT,
+                             LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E};
+  __syncwarp();
+  warp_flush(acc, a.ledger, slots);
+}
+
+// ---------------------------------------------------------------- escape
+__global__ void __launch_bounds__(256) k_escape(const EscArgs a) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const Pool& P = a.pool;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.n_esc;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = a.esc[j];
+    const double N = P.F(F_N, i), nu_lab = P.F(F_NULAB, i);
+    const double n[3] = {P.F(F_NX, i), P.F(F_NY, i), P.F(F_NZ, i)};
+    const double E = N * kH * nu_lab;
+    acc[0] += N;
+    acc[1] += E;
+    const double th = acos(n[2]);
+    double ph = atan2(n[1], n[0]);
+    if (ph < 0.0) ph += 2.0 * kPi;
+    int it = (int)floor(th / (kPi / a.n_theta)), ip = (int)floor(ph / (2.0 * kPi / a.n_phi));
+    it = min(max(it, 0), a.n_theta - 1);
+    ip = min(max(ip, 0), a.n_phi - 1);
+    const int vbin = it * a.n_phi + ip;
+    int64_t lbin = -1;
+    const double lam = kC / nu_lab * 1e8;
+    if (lam >= a.lam0) {
+      const double kb = floor(log(lam / a.lam0) / a.log1p_dlog);
+      if (kb < (double)a.nbins) lbin = (int64_t)kb;
+    }
+    if (lbin >= 0) atomicAdd(a.spec + (int64_t)vbin * a.nbins + lbin, E);
+    else acc[2] += E;
+    if (a.records) {
+      double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
+      rec[0] = 0.0; rec[1] = P.events[i]; rec[2] = N; rec[3] = E; rec[4] = vbin;
+      rec[5] = (double)lbin; rec[6] = P.inter[i]; rec[10] = nu_lab;
+    }
+  }
+  const int slots[3] = {LG_ESC_N, LG_ESC_E, LG_OOB_E};
+  warp_flush(acc, a.ledger, slots);
+}
+
+// ---------------------------------------------------------------- subdomain queue sort
+__global__ void k_sd_hist(Geometry g, const int* __restrict__ cell, const int* __restrict__ q,
+                          int64_t n, int* __restrict__ key, unsigned* __restrict__ hist) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cell[q[j]];
+    const int ix = c % g.nx, iy = (c / g.nx) % g.ny, iz = c / (g.nx * g.ny);
+    const int sd = ((iz / g.bz) * g.sy + iy / g.by) * g.sx + ix / g.bx;
+    key[j] = sd;
+    atomicAdd(hist + sd, 1u);
+  }
+}
+
+__global__ void k_sd_scatter(const int* __restrict__ q, const int* __restrict__ key, int64_t n,
+                             unsigned* __restrict__ fill, int* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[atomicAdd(fill + key[j], 1u)] = q[j];
+}
+
+// ---------------------------------------------------------------- line emission weights
+// A_ul dE_ul beta_S N_u, Eq. (thin_emissivity), as an inclusive prefix over the
+// caller's line order per cell; Lc = the total.
+__global__ void k_line_emission(Geometry g, const double2* __restrict__ lines,
+                                const double* __restrict__ A, int nline, int nlev,
+                                const double* __restrict__ pops, const int* __restrict__ sorted_of,
+                                double V, double* __restrict__ cdf, double* __restrict__ Lc) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    const int64_t row = row_of(g, ix, iy, iz);
+    const double* pc = pops + row * nlev;
+    double* cr = cdf + row * nline;
+    double run = 0.0;
+    for (int l = 0; l < nline; ++l) {
+      const int s = sorted_of[l];
+      const LineRec L = ldline(lines, s);
+      const double nu_ = pc[__double2hiint(L.w)];
+      const double tau = L.y * (pc[__double2loint(L.w)] - L.z * nu_);
+      run += A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * V;
+      cr[l] = run;
+    }
+    Lc[c] = run;
+  }
+}
+
+// Largest-remainder integer quota of N packets over cells by luminosity
+// (serial host arithmetic in natural cell order).
+static void packet_quota(const std::vector<double>& L, int64_t N, std::vector<int64_t>& qoff) {
+  const int64_t nc = (int64_t)L.size();
+  double tot = 0.0;
+  for (int64_t c = 0; c < nc; ++c) tot += L[c];
+  std::vector<int64_t> n(nc);
+  std::vector<double> frac(nc);
+  int64_t used = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    const double q = tot > 0.0 ? ((double)N * L[c]) / tot : 0.0;
+    const double fl = std::floor(q);
+    n[c] = (int64_t)fl;
+    frac[c] = q - fl;
+    used += n[c];
+  }
+  std::vector<int64_t> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  const int64_t extra = std::min<int64_t>(N - used, nc);
+  if (extra > 0) {
+    auto cmp = [&](int64_t x, int64_t y) { return frac[x] > frac[y] || (frac[x] == frac[y] && x < y); };
+    std::partial_sort(order.begin(), order.begin() + extra, order.end(), cmp);
+    for (int64_t k = 0; k < extra; ++k) n[order[k]] += 1;
+  }
+  qoff.assign(nc + 1, 0);
+  for (int64_t c = 0; c < nc; ++c) qoff[c + 1] = qoff[c] + n[c];
+}
+
+static int sm_count() {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+static int blocks_for(int64_t n, int threads, int per_sm) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)sm_count() * per_sm));
+}
+
+}  // namespace xt
+
+using namespace xt;
+
+// Packet pool (NF doubles, 9 ints, one id per slot), counters and the
+// subdomain histogram, grown on demand and kept in the context.
+static int ensure_buffers(xt_ctx* c, int64_t cap, int nsd) {
+  int rc;
+  if (c->pool_cap < cap) {
+    c->pool_cap = 0;
+    if ((rc = alloc(c, (void**)&c->d_pool_f, (size_t)cap * NF * sizeof(double), "packet pool"))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_pool_i, (size_t)cap * 9 * sizeof(int), "packet pool"))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_pool_pid, (size_t)cap * sizeof(int64_t), "packet pool"))) return rc;
+    c->pool_cap = cap;
+  }
+  if (!c->d_counters && (rc = alloc(c, (void**)&c->d_counters, 4 * sizeof(unsigned long long), "counters"))) return rc;
+  if (c->hist_n < nsd) {
+    c->hist_n = 0;
+    if ((rc = alloc(c, (void**)&c->d_hist, (size_t)2 * nsd * sizeof(unsigned), "subdomain histogram"))) return rc;
+    c->hist_n = nsd;
+  }
+  return XT_OK;
+}
+
+extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transport_stats* out) {
+  if (!c || !p) return fail(c, XT_EINVAL, "run_transport: null argument");
+  if (!c->have_pops) return fail(c, XT_ESTATE, "run_transport: set_populations first");
+  cudaSetDevice(c->device);
+  const Geometry& G = c->geo;
+  if (p->n_packets < 0) return fail(c, XT_EINVAL, "run_transport: n_packets < 0");
+  const int64_t count = p->packet_count < 0 ? p->n_packets - p->packet_begin : p->packet_count;
+  if (p->packet_begin < 0 || count < 0 || p->packet_begin + count > p->n_packets)
+    return fail(c, XT_EINVAL, "run_transport: packet range outside [0, n_packets)");
+  if (p->mode != XT_MODE_ATTEN && p->mode != XT_MODE_SCATTER) return fail(c, XT_EINVAL, "run_transport: mode");
+  if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
+  if (p->emission == XT_EMIT_BAND && !c->d_L) return fail(c, XT_ESTATE, "run_transport: band emission needs L_cell in init_grid");
+  if (p->n_theta < 1 || p->n_phi < 1 || p->spec_nbins < 1 || !(p->spec_lam0_A > 0) || !(p->spec_dlog > 0))
+    return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
+  if (p->max_events < 1) return fail(c, XT_EINVAL, "run_transport: max_events must be >= 1");
+  if (!(p->tau_min > 0) || !(p->e_cut >= 0)) return fail(c, XT_EINVAL, "run_transport: tau_min > 0 and e_cut >= 0 required");
+  if (c->nline < 1) return fail(c, XT_ESTATE, "run_transport: no lines loaded");
+  if (G.ncell >= (int64_t)1 << 31) return fail(c, XT_EINVAL, "run_transport: more than 2^31 cells");
+  int rc;
+  // estimator store
+  const size_t Sb = (size_t)G.ncell * c->nline * sizeof(double);
+  if (!c->d_S || c->S_bytes != Sb) {
+    if ((rc = alloc(c, (void**)&c->d_S, Sb, "estimator store"))) return rc;
+    c->S_bytes = Sb;
+    XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
+  }
+  // spectrum
+  const int views = p->n_theta * p->n_phi;
+  const size_t spec_b = (size_t)views * p->spec_nbins * sizeof(double);
+  if (!c->d_spec || views != c->spec_views || p->spec_nbins != c->spec_bins ||
+      p->spec_lam0_A != c->spec_lam0 || p->spec_dlog != c->spec_dlog) {
+    if ((rc = alloc(c, (void**)&c->d_spec, spec_b, "spectrum"))) return rc;
+    c->spec_views = views; c->spec_bins = p->spec_nbins; c->n_theta = p->n_theta; c->n_phi = p->n_phi;
+    c->spec_lam0 = p->spec_lam0_A; c->spec_dlog = p->spec_dlog;
+    XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
+  }
+  // emission: cell luminosities, packet quota, packet energy per cell
+  if (c->qoff_N != p->n_packets || c->qoff_mode != p->emission) {
+    std::vector<double> Lnat;
+    if ((rc = alloc(c, (void**)&c->d_Lc, G.ncell * sizeof(double) * 2, "Lc"))) return rc;
+    if (p->emission == XT_EMIT_BAND) {
+      Lnat = c->h_L;
+    } else {
+      const size_t wb = (size_t)G.ncell * c->nline * sizeof(double);
+      if (!c->d_wline || c->wline_bytes != wb) {
+        if ((rc = alloc(c, (void**)&c->d_wline, wb, "line emission"))) return rc;
+        c->wline_bytes = wb;
+      }
+      k_line_emission<<<blocks_for(G.ncell, 128, 16), 128, 0, c->stream>>>(
+          G, (const double2*)c->d_lines, c->d_A, c->nline, c->nlev, c->d_pops, c->d_orig,
+          G.dx * G.dy * G.dz, c->d_wline, c->d_Lc);
+      XT_CUDA(c, cudaGetLastError());
+      Lnat.resize(G.ncell);
+      XT_CUDA(c, cudaMemcpyAsync(Lnat.data(), c->d_Lc, G.ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    std::vector<int64_t> q;
+    packet_quota(Lnat, p->n_packets, q);
+    std::vector<double> hv(2 * G.ncell, 0.0);     // [Lc | E per packet]
+    for (int64_t k = 0; k < G.ncell; ++k) {
+      hv[k] = Lnat[k];
+      const int64_t nq = q[k + 1] - q[k];
+      hv[G.ncell + k] = nq > 0 ? Lnat[k] / (double)nq : 0.0;
+    }
+    if ((rc = copy(c, c->d_Lc, hv.data(), hv.size() * sizeof(double), "Lc"))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_qoff, q.size() * sizeof(int64_t), "quota"))) return rc;
+    if ((rc = copy(c, c->d_qoff, q.data(), q.size() * sizeof(int64_t), "quota"))) return rc;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->qoff_N = p->n_packets;
+    c->qoff_mode = p->emission;
+  }
+  // packet pool and queues
+  const int nsd = c->sx * c->sy * c->sz;
+  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 24);
+  if ((rc = ensure_buffers(c, chunk, nsd))) return rc;
+  const int64_t cap = c->pool_cap;
+  int* const I = c->d_pool_i;
+  Pool P;
+  P.cap = cap; P.f = c->d_pool_f;
+  P.cell = I; P.cursor = I + cap; P.events = I + 2 * cap; P.ndraw = I + 3 * cap;
+  P.inter = I + 4 * cap; P.pid = c->d_pool_pid;
+  int* esc = I + 5 * cap;
+  int* qA = I + 6 * cap;
+  int* qB = I + 7 * cap;
+  int* key = I + 8 * cap;
+  unsigned long long* const counters = c->d_counters;
+  unsigned* const hist = c->d_hist;
+
+  double* d_rec = nullptr;
+  const size_t rec_bytes = (size_t)count * XT_PKT_FIELDS * sizeof(double);
+  bool rec_host = false;
+  if (p->packet_records) {
+    if (is_device_ptr(p->packet_records)) {
+      d_rec = p->packet_records;
+    } else {
+      if ((rc = ensure_scratch(c, rec_bytes))) return rc;
+      d_rec = (double*)c->d_scratch;
+      rec_host = true;
+    }
+  }
+
+  XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  if (!p->accumulate) {
+    XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
+    XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
+    XT_CUDA(c, cudaMemsetAsync(c->d_ledger, 0, LG_N * sizeof(double), c->stream));
+  }
+  XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+
+  EmitArgs ea;
+  ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell; ea.cdf = c->d_wline;
+  ea.sorted_of = c->d_orig; ea.nu_tab = c->d_nu; ea.nline = c->nline; ea.emission = p->emission;
+  ea.seed = p->seed;
+  ea.nu_lo = c->band_hi_A > 0 ? kC / (c->band_hi_A * 1e-8) : 0.0;
+  ea.nu_hi = c->band_lo_A > 0 ? kC / (c->band_lo_A * 1e-8) : 0.0;
+  ea.e_cut = p->e_cut; ea.pool = P; ea.ledger = c->d_ledger; ea.records = d_rec;
+  ea.rec_base = p->packet_begin;
+
+  TraceArgs ta;
+  ta.g = G; ta.lines = (const double2*)c->d_lines; ta.nline = c->nline; ta.nlev = c->nlev;
+  ta.pops = c->d_pops; ta.S = c->d_S; ta.A = c->d_A; ta.down_off = c->d_down_off;
+  ta.down_line = c->d_down_line; ta.Te = c->d_Te; ta.ne = c->d_ne; ta.ups_down = c->d_ups_down;
+  ta.glev = c->d_g; ta.pool = P; ta.counter = counters; ta.esc = esc; ta.n_esc = counters + 1;
+  ta.n_out = counters + 2; ta.rounds = p->subdomain_rounds ? 1 : 0; ta.seed = p->seed;
+  ta.tau_min = p->tau_min; ta.ct = G.ct; ta.inv_ct = G.inv_ct; ta.max_events = p->max_events;
+  ta.ledger = c->d_ledger; ta.records = d_rec; ta.rec_base = p->packet_begin;
+
+  EscArgs xa;
+  xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
+  xa.nbins = p->spec_nbins; xa.lam0 = p->spec_lam0_A; xa.log1p_dlog = std::log1p(p->spec_dlog);
+  xa.ledger = c->d_ledger; xa.records = d_rec; xa.rec_base = p->packet_begin;
+
+  int occ = 0;
+  if (p->mode == XT_MODE_ATTEN)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_SCATTER>, 256, 0);
+  occ = std::max(occ, 1);
+  const int max_rounds = 1 << 20;
+  int64_t rounds = 0, queued_total = 0;
+  for (int64_t off = 0; off < count; off += chunk) {
+    const int64_t n = std::min(chunk, count - off);
+    ea.p_begin = p->packet_begin + off;
+    ea.n = n;
+    k_emit<<<blocks_for(n, 256, 16), 256, 0, c->stream>>>(ea);
+    XT_CUDA(c, cudaGetLastError());
+    const int* list = nullptr;
+    int64_t n_list = n;
+    for (int round = 0; n_list > 0; ++round) {
+      if (round >= max_rounds) return fail(c, XT_ETIMEOUT, "run_transport: subdomain rounds did not drain");
+      XT_CUDA(c, cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), c->stream));
+      ta.list = list;
+      ta.n_list = n_list;
+      ta.out = (list == qA) ? qB : qA;
+      const int grid = (int)std::min<int64_t>((int64_t)sm_count() * occ, (n_list + 255) / 256);
+      if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+      else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
+      XT_CUDA(c, cudaGetLastError());
+      unsigned long long cnt[4];
+      XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+      ++rounds;
+      if (cnt[1] > 0) {
+        xa.n_esc = (int64_t)cnt[1];
+        k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
+        XT_CUDA(c, cudaGetLastError());
+      }
+      n_list = (int64_t)cnt[2];
+      queued_total += n_list;
+      if (n_list > 0) {
+        // bundle the queued packets by destination subdomain (counting sort)
+        int* q = ta.out;
+        int* sorted = (q == qA) ? qB : qA;
+        XT_CUDA(c, cudaMemsetAsync(hist, 0, (size_t)nsd * sizeof(unsigned), c->stream));
+        k_sd_hist<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(G, P.cell, q, n_list, key, hist);
+        XT_CUDA(c, cudaGetLastError());
+        std::vector<unsigned> h(nsd);
+        XT_CUDA(c, cudaMemcpyAsync(h.data(), hist, nsd * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        XT_CUDA(c, cudaStreamSynchronize(c->stream));
+        std::vector<unsigned> start(nsd);
+        unsigned run = 0;
+        for (int s = 0; s < nsd; ++s) { start[s] = run; run += h[s]; }
+        XT_CUDA(c, cudaMemcpyAsync(hist + nsd, start.data(), nsd * sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+        k_sd_scatter<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(q, key, n_list, hist + nsd, sorted);
+        XT_CUDA(c, cudaGetLastError());
+        list = sorted;
+      }
+    }
+  }
+  XT_CUDA(c, cudaEventRecord(c->ev2, c->stream));
+  double led[LG_N];
+  XT_CUDA(c, cudaMemcpyAsync(led, c->d_ledger, sizeof(led), cudaMemcpyDeviceToHost, c->stream));
+  if (rec_host) XT_CUDA(c, cudaMemcpyAsync(p->packet_records, d_rec, rec_bytes, cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_S = true;
+  if (out) {
+    double* o = &out->emitted_N;
+    for (int k = 0; k < LG_N; ++k) o[k] = led[k];
+    float ms0 = 0, ms1 = 0;
+    cudaEventElapsedTime(&ms0, c->ev0, c->ev1);
+    cudaEventElapsedTime(&ms1, c->ev1, c->ev2);
+    out->zero_ms = ms0;
+    out->transport_ms = ms1;
+    out->rounds = (double)rounds;
+    out->queued = (double)queued_total;
+  }
+  if (led[LG_GUARD] > 0)
+    return fail(c, XT_ETIMEOUT, "run_transport: " + std::to_string((long long)led[LG_GUARD]) + " packets hit max_events");
+  return XT_OK;
+}
+

@@ -1,0 +1,137 @@
+// Internal declarations of the GB300 transport library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/extrass.h"
+
+namespace xt {
+
+// cgs constants (CODATA exact or recommended values)
+constexpr double kC = 2.99792458e10;
+constexpr double kH = 6.62607015e-27;
+constexpr double kE = 4.80320471e-10;
+constexpr double kMe = 9.1093837015e-28;
+constexpr double kPi = 3.14159265358979323846;
+
+// Per-packet ledger slots (device accumulators), same order as xt_transport_stats.
+enum Ledger {
+  LG_EMIT_N, LG_ESC_N, LG_ABS_N, LG_DROP_N, LG_EMIT_E, LG_ESC_E, LG_OOB_E, LG_EVENTS,
+  LG_TESTS, LG_GUARD, LG_THERMAL_E, LG_INTERACT, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_N
+};
+
+// Read-only view of everything the transport kernel needs (passed by value).
+struct Geometry {
+  int nx, ny, nz;        // cells per axis
+  int bx, by, bz;        // cells per subdomain per axis
+  int sx, sy;            // subdomains per axis (x, y)
+  int64_t ncell;
+  double R, dx, dy, dz, ct, inv_ct;
+};
+
+struct LineTable {        // lines in descending-frequency ("sorted") order
+  int nline, nlev;
+  const double* nu;       // Hz
+  const double* K;        // (pi e^2 / m_e c) f lambda t  [cm^3]
+  const double* gratio;   // g_l / g_u
+  const double* hnu;      // h nu [erg]
+  const double* A;        // Einstein A_ul [s^-1]
+  const int* lo;          // global lower level
+  const int* up;          // global upper level
+  const int* down_off;    // [nlev+1] CSR of radiative down-lines per upper level
+  const int* down_line;   //   (sorted line indices, ascending caller order)
+};
+
+// Map natural (ix,iy,iz) to the subdomain-blocked storage row.
+__host__ __device__ inline int64_t row_of(const Geometry& g, int ix, int iy, int iz) {
+  int qx = ix / g.bx, qy = iy / g.by, qz = iz / g.bz;
+  int64_t sd = ((int64_t)qz * g.sy + qy) * g.sx + qx;
+  int64_t loc = ((int64_t)(iz - qz * g.bz) * g.by + (iy - qy * g.by)) * g.bx + (ix - qx * g.bx);
+  return sd * ((int64_t)g.bx * g.by * g.bz) + loc;
+}
+
+}  // namespace xt
+
+struct xt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // grid
+  bool have_grid = false;
+  xt::Geometry geo{};
+  int sx = 1, sy = 1, sz = 1;
+  double v_max = 0, t = 0, band_lo_A = 0, band_hi_A = 0;
+  std::vector<double> h_L;           // natural order, for the packet quota
+  double* d_Te = nullptr;            // row order
+  double* d_ne = nullptr;
+  double* d_rho = nullptr;
+  double* d_dep = nullptr;
+  double* d_L = nullptr;             // row order
+  // atoms
+  bool have_atoms = false;
+  int n_ion = 0, nlev = 0, nline = 0;
+  std::vector<int> h_level_off;
+  std::vector<double> h_g, h_E;
+  std::vector<int> h_sorted_of;      // caller line -> sorted position
+  std::vector<int> h_orig_of;        // sorted position -> caller line
+  int* d_level_off = nullptr;
+  double* d_g = nullptr;
+  double* d_E = nullptr;
+  double *d_nu = nullptr, *d_K = nullptr, *d_gratio = nullptr, *d_hnu = nullptr, *d_A = nullptr;
+  double* d_invB = nullptr;          // 1 / B_lu (sorted)
+  int *d_lo = nullptr, *d_up = nullptr, *d_orig = nullptr;
+  int *d_down_off = nullptr, *d_down_line = nullptr;
+  double* d_nion = nullptr;          // [row][n_ion]
+  double* d_ups_down = nullptr;      // [nlev]
+  // state
+  bool have_pops = false;
+  double* d_pops = nullptr;          // [row][nlev]
+  double* d_S = nullptr;             // [row][sorted line]
+  size_t S_bytes = 0;
+  bool have_S = false;
+  // emission
+  int64_t* d_qoff = nullptr;         // natural order [ncell+1]
+  int64_t qoff_N = -1;               // N the quota was built for
+  int qoff_mode = -1;
+  double* d_Lc = nullptr;            // natural order cell luminosity used by the quota
+  double* d_wline = nullptr;         // [row][sorted line] line emission weights (XT_EMIT_LINES)
+  size_t wline_bytes = 0;
+  // spectrum
+  double* d_spec = nullptr;
+  int spec_views = 0, spec_bins = 0, n_theta = 20, n_phi = 20;
+  double spec_lam0 = 0, spec_dlog = 1e-3;
+  // ledger
+  double* d_ledger = nullptr;        // [LG_N]
+  double* d_lines = nullptr;         // [sorted line] packed nu, K, gratio, (lo, up): 32 B
+  // transport buffers
+  double* d_pool_f = nullptr;
+  int* d_pool_i = nullptr;
+  int64_t* d_pool_pid = nullptr;
+  int64_t pool_cap = 0;
+  unsigned long long* d_counters = nullptr;
+  unsigned* d_hist = nullptr;
+  int hist_n = 0;
+  // scratch
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+namespace xt {
+int fail(xt_ctx* c, int code, const std::string& msg);
+int cuda_fail(xt_ctx* c, cudaError_t e, const char* what);
+bool is_device_ptr(const void* p);
+// Copy n bytes between any host/device pointers on the context stream.
+int copy(xt_ctx* c, void* dst, const void* src, size_t n, const char* what);
+int ensure_scratch(xt_ctx* c, size_t bytes);
+int alloc(xt_ctx* c, void** p, size_t bytes, const char* what);
+void release(void** p);
+}  // namespace xt
+
+#define XT_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return xt::cuda_fail(ctx, e_, #call);  \
+  } while (0)

@@ -1,0 +1,249 @@
+"""GPU transport vs the CPU oracle, through the C ABI (needs a GB300).
+
+Bars: estimators relative 1e-10 and spectra 1e-9 (FP64 transport; the only
+freedom is the summation order of atomics and last-bit differences of the
+math library), per-packet histories identical (fate and event counts exact,
+photon counts relative 1e-12), Sobolev tau/beta relative 1e-13.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+S_TOL = 1e-10
+SPEC_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def xt():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a GPU"
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_07539_gb300 as xt
+    return xt
+
+
+def _ctx(xt):
+    import torch
+    return xt.Context(0, torch.cuda.current_stream().cuda_stream)
+
+
+def _cmp_sparse(got, want, tol, what):
+    mg, mw = got != 0, want != 0
+    assert np.array_equal(mg, mw), f"{what}: support differs ({mg.sum()} vs {mw.sum()})"
+    if mw.any():
+        err = np.max(np.abs(got[mw] / want[mw] - 1))
+        assert err < tol, f"{what}: max rel err {err}"
+
+
+def _records(xt, ctx, w, **kw):
+    n = w.n_packets if kw.get("packet_count", -1) < 0 else kw["packet_count"]
+    rec = np.zeros((n, xt.XT_PKT_FIELDS))
+    st = ctx.transport(w, packet_records=rec, **kw)
+    return st, rec
+
+
+def _cmp_records(rec, pk):
+    assert np.array_equal(rec[:, 0], pk[:, 0]), "fates differ"
+    assert np.array_equal(rec[:, 1], pk[:, 1]), "event counts differ"
+    assert np.array_equal(rec[:, 7], pk[:, 7]), "emitting cells differ"
+    # N_final of a dropped packet is a cancellation remainder (~2^-53 N0) where
+    # CUDA's and glibc's expm1 may differ by one ulp: bound it against N0
+    assert np.all(np.abs(rec[:, 2] - pk[:, 2]) <= 1e-12 * np.abs(pk[:, 2]) + 1e-15 * pk[:, 8])
+    np.testing.assert_allclose(rec[:, 8], pk[:, 8], rtol=1e-13)
+    np.testing.assert_allclose(rec[:, 9], pk[:, 9], rtol=1e-15)
+    np.testing.assert_allclose(rec[:, 10], pk[:, 10], rtol=1e-14)
+    esc = pk[:, 0] == 0
+    assert np.array_equal(rec[esc, 4], pk[esc, 4]), "viewer bins differ"
+    assert np.array_equal(rec[esc, 5], pk[esc, 5]), "wavelength bins differ"
+
+
+def test_uniform_sphere_full(xt):
+    """16^3 grid, 100 lines, 1e5 packets: estimators, spectrum, ledger, histories."""
+    w = synth.uniform_sphere()
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st, rec = _records(xt, ctx, w)
+        S = ctx.get_estimators()
+        spec = ctx.get_spectrum(0)
+        o = oracle.transport(w, per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        _cmp_sparse(S, o["S"], S_TOL, "estimators")
+        _cmp_sparse(spec, o["spec"], SPEC_TOL, "spectrum")
+        L = o["ledger"]
+        assert st["events"] == L["events"] and st["tests"] == L["tests"]
+        for k, kk in [("emitted_N", "emit_N"), ("escaped_N", "esc_N"), ("absorbed_N", "abs_N"),
+                      ("dropped_N", "drop_N"), ("escaped_E", "esc_E")]:
+            assert st[k] == pytest.approx(L[kk], rel=1e-12)
+        assert st["escaped_N"] + st["absorbed_N"] + st["dropped_N"] == pytest.approx(st["emitted_N"], rel=1e-13)
+
+
+def test_sobolev_tau_beta_and_rates(xt):
+    w = synth.uniform_sphere(n=8, n_packets=30_000, seed=2)
+    w.pops = w.pops * np.linspace(1e-9, 1.0, w.ncell)[:, None]
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        tau, beta = ctx.get_sobolev_tau()
+        t_or, b_or = oracle.tau_beta(w)
+        np.testing.assert_allclose(tau, t_or, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(beta, b_or, rtol=1e-13, atol=0)
+        ctx.transport(w)
+        R_lu, R_ul, J = ctx.get_photoexcitation_rates()
+        o = oracle.transport(w)
+        r_or = oracle.rates(w, o["S"])
+        _cmp_sparse(R_lu, r_or[0], S_TOL, "R_lu")
+        _cmp_sparse(R_ul, r_or[1], S_TOL, "R_ul")
+        _cmp_sparse(J, r_or[2], S_TOL, "Jbar")
+        # a cell sub-range through the same call
+        R2, _, _ = ctx.get_photoexcitation_rates(100, 37, want=("R_lu",))
+        assert np.array_equal(R2, R_lu[100:137])
+
+
+@pytest.mark.parametrize("sd,rounds", [((1, 1, 1), False), ((2, 2, 2), False), ((4, 2, 8), True),
+                                       ((16, 16, 16), True), ((2, 2, 2), True)])
+def test_decomposition_invariance(xt, sd, rounds):
+    """P9: the subdomain split of the store, and tracing each subdomain as a
+    domain of its own with packets handed on between rounds, change no history."""
+    w = synth.uniform_sphere(n_packets=40_000, seed=5)
+    w.pops = w.pops * 1e-5
+    with _ctx(xt) as ctx:
+        ctx.load(w, subdomains=sd)
+        st, rec = _records(xt, ctx, w, subdomain_rounds=rounds)
+        if rounds and sd != (1, 1, 1):
+            assert st["rounds"] > 1 and st["queued"] > 0
+        S = ctx.get_estimators()
+        o = oracle.transport(w, per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        _cmp_sparse(S, o["S"], S_TOL, f"estimators sd={sd}")
+
+
+def test_packet_subrange_and_accumulate(xt):
+    w = synth.uniform_sphere(n_packets=50_000, seed=6)
+    w.pops = w.pops * 1e-4
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        ctx.transport(w, packet_begin=0, packet_count=17_001)
+        ctx.transport(w, packet_begin=17_001, packet_count=50_000 - 17_001, accumulate=True)
+        S = ctx.get_estimators()
+        o = oracle.transport(w)
+        _cmp_sparse(S, o["S"], S_TOL, "split run")
+        _, rec = _records(xt, ctx, w, packet_begin=12_345, packet_count=999)
+        o2 = oracle.transport(w, p_begin=12_345, p_end=12_345 + 999, per_packet=True)
+        _cmp_records(rec, o2["pkt"])
+
+
+def test_edge_cases(xt):
+    # zero packets, one packet, odd grid with ragged subdomain blocks, empty matter
+    w = synth.uniform_sphere(n=6, n_packets=1, seed=7, n_lines=30)
+    with _ctx(xt) as ctx:
+        ctx.load(w, subdomains=(3, 2, 1))
+        st = ctx.transport(w, n_packets=0)
+        assert st["emitted_N"] == 0 and ctx.get_estimators().sum() == 0
+        _, rec = _records(xt, ctx, w)
+        o = oracle.transport(w, per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        w0 = synth.uniform_sphere(n=5, n_packets=5000, seed=8, n_lines=30)
+        w0.pops = np.zeros_like(w0.pops)
+        ctx.load(w0)
+        st = ctx.transport(w0)
+        assert st["events"] == 0 and st["escaped_N"] == pytest.approx(st["emitted_N"], rel=1e-13)
+        o = oracle.transport(w0)
+        _cmp_sparse(ctx.get_spectrum(0), o["spec"], SPEC_TOL, "empty-matter spectrum")
+        # invalid arguments are reported, not trapped
+        with pytest.raises(xt.XtError) as e:
+            ctx.transport(w0, packet_begin=10, packet_count=w0.n_packets)
+        assert e.value.code == xt.XT_EINVAL
+        with pytest.raises(xt.XtError) as e:
+            xt.init_grid(ctx.h, 5, 5, 5, w0.v_max, w0.t, w0.Te, w0.ne, w0.L_cell, w0.band_A,
+                         subdomains=(2, 1, 1))
+        assert e.value.code == xt.XT_EINVAL
+
+
+def test_event_guard_reports_timeout(xt):
+    w = synth.uniform_sphere(n=8, n_packets=2000, seed=9)
+    w.pops = w.pops * 1e-5
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        rc, st = ctx.transport(w, max_events=1, check=False)
+        o = oracle.transport(w, max_events=1)
+        assert rc == xt.XT_ETIMEOUT and st["guard"] == o["ledger"]["guard"] > 0
+
+
+def test_line_emission(xt):
+    w = synth.uniform_sphere(n=8, n_packets=30_000, seed=10)
+    w.pops = w.pops * 1e-3
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        _, rec = _records(xt, ctx, w, emission=xt.XT_EMIT_LINES)
+        S = ctx.get_estimators()
+        o = oracle.transport(w, emission="lines", per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        _cmp_sparse(S, o["S"], S_TOL, "line-emission estimators")
+
+
+@pytest.mark.parametrize("rounds", [False, True])
+def test_scatter_mode(xt, rounds):
+    w = synth.uniform_sphere(n_packets=40_000, seed=12, subdomains=(4, 4, 4))
+    ups = oracle.upsilon_down_sums(w)
+    with _ctx(xt) as ctx:
+        ctx.load(w, with_scatter_data=ups)
+        st, rec = _records(xt, ctx, w, mode=xt.XT_MODE_SCATTER, subdomain_rounds=rounds)
+        S = ctx.get_estimators()
+        spec = ctx.get_spectrum(0)
+        o = oracle.transport(w, mode="scatter", per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        assert np.array_equal(rec[:, 6], o["pkt"][:, 6]), "interaction counts differ"
+        _cmp_sparse(S, o["S"], S_TOL, "scatter estimators")
+        _cmp_sparse(spec, o["spec"], SPEC_TOL, "scatter spectrum")
+        assert st["reemit_E_cmf"] + st["thermal_E"] == pytest.approx(st["abs_E_cmf"], rel=1e-13)
+
+
+@pytest.fixture(scope="module")
+def onion():
+    return synth.clumpy_onion()
+
+
+def test_clumpy_onion_full_grid_packet_subset(xt, onion):
+    """Paper-scale grid and line list (64^3 x 1e5 lines, 8^3 subdomains), a
+    contiguous packet subset: every estimator slot the oracle touches, and
+    nothing else in those cells."""
+    w = onion
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        p0, m = 61_234_567, 60_000
+        st, rec = _records(xt, ctx, w, packet_begin=p0, packet_count=m, subdomain_rounds=True)
+        assert st["rounds"] > 1
+        o = oracle.transport(w, p_begin=p0, p_end=p0 + m, per_packet=True)
+        _cmp_records(rec, o["pkt"])
+        slots, vals = o["S_slots"], o["S_values"]
+        cells = np.unique(slots // w.nline)
+        for c0 in range(0, len(cells), 512):
+            cs = cells[c0:c0 + 512]
+            lo_c, hi_c = cs.min(), cs.max() + 1
+            S = ctx.get_estimators(int(lo_c), int(hi_c - lo_c))
+            want = np.zeros_like(S)
+            sel = (slots // w.nline >= lo_c) & (slots // w.nline < hi_c)
+            want.reshape(-1)[slots[sel] - lo_c * w.nline] = vals[sel]
+            _cmp_sparse(S, want, S_TOL, "onion estimators")
+
+
+def test_clumpy_onion_full_run_sampled(xt, onion):
+    """The full 1e8-packet pass in the benchmark's launch configuration:
+    sampled packet histories vs the oracle one by one, and the ledger closes."""
+    w = onion
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        import torch
+        rec = torch.zeros((w.n_packets, xt.XT_PKT_FIELDS), dtype=torch.float64, device="cuda")
+        st = ctx.transport(w, packet_records=rec)
+        assert st["escaped_N"] + st["absorbed_N"] + st["dropped_N"] == pytest.approx(st["emitted_N"], rel=1e-12)
+        rng = np.random.default_rng(0)
+        ids = np.sort(rng.choice(w.n_packets, 300, replace=False))
+        got = rec[torch.as_tensor(ids, device="cuda")].cpu().numpy()
+        for i, p in enumerate(ids):
+            o = oracle.transport(w, p_begin=int(p), p_end=int(p) + 1, per_packet=True, sparse=True)
+            _cmp_records(got[i:i + 1], o["pkt"])
