@@ -38,6 +38,7 @@
 #define XO_E 4.80320471e-10
 #define XO_ME 9.1093837015e-28
 #define XO_PI 3.14159265358979323846
+#define XO_LN2 0.69314718055994530942
 
 /* ------------------------------------------------------------------ */
 /* Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11, "Parallel random
@@ -391,10 +392,14 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
                 ledger[L_EVENTS] += 1.0;
                 double f_corr = 1.0 - g_l * n_u / (g_u * n_l);
                 double nu_l = P->nu[cursor];
+                /* 1 - e^-tau and e^-tau, each without cancellation */
+                double ex, ome;
+                if (tau > XO_LN2) { ex = exp(-tau); ome = 1.0 - ex; }
+                else { ome = -expm1(-tau); ex = 1.0 - ome; }
                 if (pr->mode == 0) {
-                    double dN = N * (-expm1(-tau));
+                    double dN = N * ome;
                     add_estimator(S, cell, pb->nline, l, dN / f_corr);
-                    N -= dN;
+                    N = N * ex;                       /* N_phot - N_PE: what goes on */
                     ledger[L_ABS_N] += dN;
                     if (N * XO_H * nu_l < pr->e_cut * E0) {
                         ledger[L_DROP_N] += N;
@@ -405,7 +410,7 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
                     double w[4];
                     draw4(pr->seed, p, 2 + (uint64_t)ndraw, w);   /* one draw per active resonance */
                     ndraw++;
-                    if (w[0] < -expm1(-tau)) {
+                    if (w[0] < ome) {
                         interactions++;
                         ledger[L_INTERACT] += 1.0;
                         add_estimator(S, cell, pb->nline, l, N / f_corr);

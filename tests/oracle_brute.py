@@ -92,7 +92,7 @@ def brute_packet(w, p, qoff, tau_min=1e-4, e_cut=1e-6):
             fcorr = 1 - w.g_level[lo] * w.pops[cell, up] / (w.g_level[up] * w.pops[cell, lo])
             dN = N * (-np.expm1(-tau))
             out.append((cell, l, dN / fcorr))
-            N -= dN
+            N = N * np.exp(-tau)
             if N * H * lines_nu[l] < e_cut * E0:
                 fate = 1
                 break
