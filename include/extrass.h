@@ -156,6 +156,15 @@ int get_photoexcitation_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells,
  * kind 2: angle-summed L_lambda [nbins], erg/s/A */
 int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 
+/* ---- numerical self-test (no paper counterpart: checks a device primitive) --
+ * The attenuation factors e^-tau and 1 - e^-tau of every line event are
+ * computed by the library's own fixed-point exponential on the integer pipe.
+ * This evaluates it for n values tau > 0 (host or device arrays) on the
+ * current device, and, if ref_ex / ref_ome are not NULL, CUDA's exp(-tau) and
+ * -expm1(-tau) beside it.  Synchronous; allocates its own temporaries. */
+int xt_selftest_expneg(const double *tau, int64_t n, double *ex, double *ome,
+                       double *ref_ex, double *ref_ome);
+
 typedef struct {
     int64_t ncell, nlev, nline, n_ion;
     int64_t spec_views, spec_bins;

@@ -103,6 +103,7 @@ def lib():
             "get_photoexcitation_rates": ([vp, i64, i64, vp, vp, vp], C.c_int),
             "get_spectrum": ([vp, i32, vp, C.c_size_t], C.c_int),
             "get_sizes": ([vp, vp], C.c_int),
+            "xt_selftest_expneg": ([vp, i64, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -251,6 +252,16 @@ def get_spectrum(ctx, kind=0, out=None):
     if out is None:
         out = np.zeros(sz["spec_bins"]) if kind == 2 else np.zeros((sz["spec_views"], sz["spec_bins"]))
     _check(ctx, lib().get_spectrum(ctx, int(kind), _ptr(out), int(np.prod(out.shape))))
+    return out
+
+
+def xt_selftest_expneg(tau):
+    """Device fixed-point e^-tau and 1-e^-tau, and CUDA's exp/expm1 beside them."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    out = [np.zeros_like(tau) for _ in range(4)]
+    rc = lib().xt_selftest_expneg(_ptr(tau), tau.shape[0], *[_ptr(o) for o in out])
+    if rc != XT_OK:
+        raise XtError(rc, "xt_selftest_expneg failed")
     return out
 
 

@@ -5,9 +5,31 @@
 #include <cstring>
 #include <numeric>
 
+#include "fixexp.cuh"
 #include "xt_internal.cuh"
 
 namespace xt {
+
+// Tables of the fixed-point exponential (fixexp.cuh).  ln2 from its series
+// sum 1/(i 2^i) in Q127 integer arithmetic; 1/n! by exact integer division;
+// e^-j/64 from the host's extended-precision expl (64 or more mantissa bits).
+void fixexp_tables(FixExpTables* t) {
+  typedef unsigned __int128 u128;
+  u128 ln2 = 0;
+  for (int i = 1; i < 127; ++i) ln2 += (((u128)1) << (127 - i)) / (u128)i;   // ln2 2^127
+  t->ln2_a = (uint64_t)(ln2 >> 74);                    // ln2 2^53
+  t->ln2_b = (uint64_t)(ln2 >> 10);                    // next 64 bits
+  const u128 one = ((u128)1) << 63;
+  u128 f = 1;
+  for (int n = 0; n < 10; ++n) {
+    if (n > 0) f *= (u128)n;
+    t->fact[n] = (uint64_t)((one + f / 2) / f);
+  }
+  for (int j = 0; j < 48; ++j) {
+    long double v = expl(-(long double)j / 64.0L) * 9223372036854775808.0L;
+    t->tab[j] = (uint64_t)(v + 0.5L);
+  }
+}
 
 int fail(xt_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -174,11 +196,18 @@ __global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops
     int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
     int64_t row = row_of(g, ix, iy, iz);
     int s = sorted_of[l];
-    double v = S[row * L.nline + s];
-    if (which > 0) {
-      double nl = pops[row * L.nlev + L.lo[s]];
-      double R = nl > 0.0 ? v / (nl * V) : 0.0;
-      v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
+    // the store holds net photons absorbed; gross = net / f_corr, f_corr = net_pop / n_l
+    const double Snet = S[row * L.nline + s];
+    double v = 0.0;
+    if (Snet != 0.0) {
+      const double nl = pops[row * L.nlev + L.lo[s]];
+      const double net = nl - L.gratio[s] * pops[row * L.nlev + L.up[s]];
+      if (which == 0) {
+        v = Snet * nl / net;
+      } else {
+        const double R = Snet / (net * V);           // S / (n_l V)
+        v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
+      }
     }
     out[i] = v;
   }
@@ -204,6 +233,16 @@ __global__ void k_spectrum(const double* __restrict__ E, int n_theta, int n_phi,
       double dOm = (2.0 * kPi / n_phi) * (cos(th0) - cos(th1));
       out[i] = kind == 0 ? E[i] : 4.0 * kPi / dOm * E[i] / dlam;
     }
+  }
+}
+
+__global__ void k_selftest_expneg(FixExpTables T, const double* __restrict__ tau, int64_t n,
+                                  double* ex, double* ome, double* rex, double* rome) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    expneg(T, tau[i], ex[i], ome[i]);
+    rex[i] = exp(-tau[i]);
+    rome[i] = -expm1(-tau[i]);
   }
 }
 
@@ -424,6 +463,7 @@ int set_populations(xt_ctx* c, const double* pops) {
     return rc;
   }
   c->have_pops = true;
+  c->have_S = false;     // estimators refer to the populations of their transport pass
   if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;
   return XT_OK;
 }
@@ -525,6 +565,28 @@ int get_spectrum(xt_ctx* c, int32_t kind, double* out, size_t n_cap) {
   if (rc) return rc;
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   return XT_OK;
+}
+
+int xt_selftest_expneg(const double* tau, int64_t n, double* ex, double* ome, double* ref_ex,
+                       double* ref_ome) {
+  if (!tau || n < 0 || !ex || !ome) return XT_EINVAL;
+  FixExpTables T;
+  fixexp_tables(&T);
+  const size_t b = (size_t)n * sizeof(double);
+  double* d = nullptr;
+  if (cudaMalloc(&d, 5 * b + 8) != cudaSuccess) { cudaGetLastError(); return XT_ENOMEM; }
+  cudaMemcpy(d, tau, b, cudaMemcpyDefault);
+  k_selftest_expneg<<<grid_blocks(n, 256), 256>>>(T, d, n, d + n, d + 2 * n, d + 3 * n, d + 4 * n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    cudaMemcpy(ex, d + n, b, cudaMemcpyDefault);
+    cudaMemcpy(ome, d + 2 * n, b, cudaMemcpyDefault);
+    if (ref_ex) cudaMemcpy(ref_ex, d + 3 * n, b, cudaMemcpyDefault);
+    if (ref_ome) cudaMemcpy(ref_ome, d + 4 * n, b, cudaMemcpyDefault);
+  }
+  cudaFree(d);
+  return e == cudaSuccess ? XT_OK : XT_ECUDA;
 }
 
 int get_sizes(xt_ctx* c, xt_sizes* o) {

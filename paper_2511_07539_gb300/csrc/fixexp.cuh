@@ -1,0 +1,105 @@
+// e^-tau and 1 - e^-tau for tau > 0, computed on the integer pipe.
+//
+// GB300 executes FP64 arithmetic at about 1/64 of its FP32 rate, while 64-bit
+// integer multiplies run on the wide integer pipe.  The attenuation factor of
+// every line event is therefore evaluated in 63-bit fixed point:
+//   tau = k ln2 + r,  0 <= r < ln2           (integer range reduction, ln2 to ~2^-117)
+//   r   = j/64 + s,   0 <= s < 1/64          (table of e^-j/64, after Tang's
+//                                             table-driven method, ACM TOMS 15, 1989)
+//   e^-s by its Taylor series to s^9/9! (< 2^-72) in Horner form,
+//   e^-tau = 2^-k e^-j/64 e^-s, rounded once to double.
+// For tau < ln2 the complement 1 - e^-tau = 1 - e^-r is formed exactly in fixed
+// point, so it keeps full relative precision for small tau; for larger tau it
+// is 1 - e^-tau in double (no cancellation, e^-tau < 1/2).  Both results are
+// within about one ulp of the correctly rounded values; tau >= 709 gives
+// e^-tau = 0.  The tables are computed on the host (xt::fixexp_tables).
+#pragma once
+#include <stdint.h>
+
+namespace xt {
+
+struct FixExpTables {
+  uint64_t tab[48];     // e^-j/64, j = 0..47, Q63
+  uint64_t fact[10];    // 1/n!, n = 0..9, Q63
+  uint64_t ln2_a;       // floor(ln2 2^53)
+  uint64_t ln2_b;       // next 64 bits of ln2 2^53
+};
+
+void fixexp_tables(FixExpTables* t);    // host
+
+__device__ __forceinline__ uint64_t mul_q63(uint64_t a, uint64_t b) {
+  const uint64_t hi = __umul64hi(a, b), lo = a * b;
+  return (hi << 1) | (lo >> 63);
+}
+
+// q * 2^-63 * 2^scale as a double, rounded to nearest even; 0 below 2^-1022.
+__device__ __forceinline__ double q63_to_double(uint64_t q, int scale) {
+  if (q == 0) return 0.0;
+  const int b = 63 - __clzll((long long)q);
+  int e = b - 63 + scale;
+  uint64_t m;
+  if (b > 52) {
+    const int sh = b - 52;
+    const uint64_t rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m = q >> sh;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      m += 1ull;
+      if (m >> 53) { m >>= 1; e += 1; }
+    }
+  } else {
+    m = q << (52 - b);
+  }
+  if (e < -1022) return 0.0;
+  return __longlong_as_double((long long)(((uint64_t)(e + 1023) << 52) | (m & ((1ull << 52) - 1ull))));
+}
+
+// tau > 0 (finite).  Writes e^-tau and 1 - e^-tau.
+__device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double& ex, double& ome) {
+  if (tau >= 709.0) { ex = 0.0; ome = 1.0; return; }
+  const uint64_t bits = (uint64_t)__double_as_longlong(tau);
+  const int eb = (int)(bits >> 52);                        // biased exponent (tau normal, > 0)
+  const uint64_t m = (bits & ((1ull << 52) - 1ull)) | (1ull << 52);
+  uint64_t R;                                              // r in Q63
+  int k = 0;
+  if (tau < 0.6931471805599453) {
+    const int sh = eb - 1012;                              // tau 2^63 = m 2^(eb-1012)
+    if (sh >= 0) R = m << sh;
+    else if (sh > -64) R = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);
+    else R = 0;
+  } else {
+    const uint64_t T53 = m << (eb - 1022);                 // tau 2^53, exact (tau >= 0.69)
+    // k = floor(tau / ln2) from a float estimate (off by at most one), then
+    // corrected; r = tau - k ln2 with ln2 carried to 117 bits, in Q63
+    const float tf = __int_as_float((int)((((uint32_t)(eb - 1023 + 127)) << 23) |
+                                          ((uint32_t)(m >> 29) & 0x7FFFFFu)));
+    k = (int)(tf * 1.44269504f);
+    const uint64_t ln2_q63 = (T.ln2_a << 10) | (T.ln2_b >> 54);
+    // r53 and rc below never under-estimate r (the dropped parts of k ln2 are
+    // only subtracted truncated), so a k that is one too small always shows
+    // r >= ln2 and the corrections cannot oscillate.
+    int64_t Rs = 0;
+    for (int it = 0; it < 4; ++it) {
+      const uint64_t kk = (uint64_t)k;
+      const int64_t r53 = (int64_t)(T53 - kk * T.ln2_a) - (int64_t)__umul64hi(kk, T.ln2_b);
+      if (r53 < 0) { --k; continue; }
+      if ((uint64_t)r53 > T.ln2_a + 1) { ++k; continue; }
+      const int64_t rc = (r53 << 10) - (int64_t)((kk * T.ln2_b) >> 54);
+      if (rc < 0) { --k; continue; }
+      if ((uint64_t)rc > ln2_q63) { ++k; continue; }
+      Rs = rc;
+      break;
+    }
+    R = (uint64_t)Rs;
+  }
+  const int j = (int)(R >> 57);                            // R <= ln2 2^63 -> j <= 44
+  const uint64_t s = R & ((1ull << 57) - 1ull);            // s < 2^-6 in Q63
+  uint64_t p = T.fact[9];
+#pragma unroll
+  for (int n = 8; n >= 0; --n) p = T.fact[n] - mul_q63(s, p);   // all partial sums stay positive
+  const uint64_t E = mul_q63(T.tab[j], p);                 // e^-r in Q63, in (1/2, 1]
+  ex = q63_to_double(E, -k);
+  if (k == 0) ome = q63_to_double((1ull << 63) - E, 0);
+  else ome = 1.0 - ex;
+}
+
+}  // namespace xt

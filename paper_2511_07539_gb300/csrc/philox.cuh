@@ -25,12 +25,21 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+// (x >> 11) 2^-53 assembled from its bits with integer operations only (exact).
+__device__ __forceinline__ double u01(uint64_t x) {
+  const uint64_t m = x >> 11;
+  if (m == 0) return 0.0;
+  const int b = 63 - __clzll((long long)m);          // top bit, 0..52
+  const uint64_t bits = ((uint64_t)(b - 53 + 1023) << 52) | ((m << (52 - b)) & ((1ull << 52) - 1ull));
+  return __longlong_as_double((long long)bits);
+}
+
 __device__ __forceinline__ U4 draw(uint64_t seed, int64_t packet, uint64_t e) {
   uint64_t x[4];
   philox4x64_10((uint64_t)packet, e, 0, 0, seed, 0, x);
   U4 r;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) r.u[i] = (double)(x[i] >> 11) * 0x1.0p-53;
+  for (int i = 0; i < 4; ++i) r.u[i] = u01(x[i]);
   return r;
 }
 

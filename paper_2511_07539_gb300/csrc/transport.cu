@@ -29,6 +29,7 @@
 #include <cmath>
 #include <numeric>
 
+#include "fixexp.cuh"
 #include "philox.cuh"
 #include "xt_internal.cuh"
 
@@ -95,6 +96,7 @@ struct TraceArgs {
   double* __restrict__ ledger;
   double* __restrict__ records;
   int64_t rec_base;
+  FixExpTables fx;
 };
 
 struct EscArgs {
@@ -249,11 +251,14 @@ enum { T_TESTS, T_EVENTS, T_ABS, T_DROP, T_GUARD, T_INTER, T_ABSE, T_REEM, T_THE
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
+  __shared__ FixExpTables fx;
+  for (int k = threadIdx.x; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
+    reinterpret_cast<uint64_t*>(&fx)[k] = reinterpret_cast<const uint64_t*>(&a.fx)[k];
+  __syncthreads();
   const Geometry& g = a.g;
   const Pool& P = a.pool;
   const int lane = threadIdx.x & 31;
   const long long taumin_bits = __double_as_longlong(a.tau_min);
-  const long long thick_bits = __double_as_longlong(38.0);   // 1 - e^-tau == 1 exactly beyond
   double acc[T_NACC];
 #pragma unroll
   for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
@@ -324,11 +329,12 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
       if (bits(tau) > taumin_bits) {
         ++events;
         acc[T_EVENTS] += 1.0;
-        const double ome = bits(tau) >= thick_bits ? 1.0 : -expm1(-tau);
+        double ex, ome;
+        expneg(fx, tau, ex, ome);
         if (MODE == XT_MODE_ATTEN) {
           const double dN = N * ome;
-          atomicAdd(a.S + row * a.nline + cursor, dN * n_l / net);   // dN / f_corr
-          N -= dN;
+          atomicAdd(a.S + row * a.nline + cursor, dN);   // net photons; / f_corr at readout
+          N = N * ex;
           acc[T_ABS] += dN;
           if (N * kH * L.x < T) { acc[T_DROP] += N; fate = 1; break; }
         } else {
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
           if (w.u[0] < ome) {
             P.inter[i] += 1;
             acc[T_INTER] += 1.0;
-            atomicAdd(a.S + row * a.nline + cursor, N * n_l / net);
+            atomicAdd(a.S + row * a.nline + cursor, N);
             acc[T_ABS] += N;
             const double Ecmf = N * kH * L.x;
             acc[T_ABSE] += Ecmf;
@@ -704,6 +710,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.n_out = counters + 2; ta.rounds = p->subdomain_rounds ? 1 : 0; ta.seed = p->seed;
   ta.tau_min = p->tau_min; ta.ct = G.ct; ta.inv_ct = G.inv_ct; ta.max_events = p->max_events;
   ta.ledger = c->d_ledger; ta.records = d_rec; ta.rec_base = p->packet_begin;
+  fixexp_tables(&ta.fx);
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
