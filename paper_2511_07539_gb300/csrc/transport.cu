@@ -232,8 +232,10 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
     P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
     P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
     P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
-    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * E0;
-    P.cell[i] = (int)c; P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
+    // stop once N nu_line < e_cut E0 / h (the photon energy at the line below e_cut E0)
+    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * E0 / kH;
+    P.cell[i] = (int)c | (n[0] > 0.0 ? 0 : 1 << 29) | (n[1] > 0.0 ? 0 : 1 << 30) |
+                (n[2] > 0.0 ? 0 : (int)(1u << 31)); P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
     P.pid[i] = p;
     acc[0] += N;
     acc[1] += E0;
@@ -247,10 +249,11 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
 }
 
 // ---------------------------------------------------------------- trace
-enum { T_TESTS, T_EVENTS, T_ABS, T_DROP, T_GUARD, T_INTER, T_ABSE, T_REEM, T_THERM, T_NACC };
+// Per-lane ledger: integer counters, FP64 sums.
+enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_NACC };
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
+__global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
   for (int k = threadIdx.x; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
     reinterpret_cast<uint64_t*>(&fx)[k] = reinterpret_cast<const uint64_t*>(&a.fx)[k];
@@ -262,13 +265,16 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
   double acc[T_NACC];
 #pragma unroll
   for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+  unsigned n_tests = 0, n_events = 0, n_guard = 0, n_inter = 0;
 
-  bool have = false;
+  bool have = false, seg_new = true;
   int64_t i = 0;                         // pool slot
-  int idx[3] = {0, 0, 0}, sgn[3] = {1, 1, 1}, cursor = 0, events = 0;
+  int ix = 0, iy = 0, iz = 0, sx = 1, sy = 1, sz = 1, cursor = 0, events = 0, axis = 0;
   int bx0 = 0, bx1 = 0, by0 = 0, by1 = 0, bz0 = 0, bz1 = 0;   // current subdomain box
   int64_t row = 0;
-  double tm[3] = {0, 0, 0}, td[3] = {0, 0, 0}, nu0 = 0, aslope = 0, N = 0, T = 0;
+  long long end_bits = 0;
+  double tmx = 0, tmy = 0, tmz = 0, tdx = 0, tdy = 0, tdz = 0, nu0 = 0, aslope = 0;
+  double N = 0, N_in = 0, Tq = 0;
 
   for (;;) {
     // ---- refill lanes whose packet ended (warp-aggregated)
@@ -284,24 +290,26 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
           const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
           if (my < (unsigned long long)a.n_list) {
             i = a.list ? a.list[my] : (int64_t)my;
-            const int c = P.cell[i];
-            idx[0] = c % g.nx; idx[1] = (c / g.nx) % g.ny; idx[2] = c / (g.nx * g.ny);
-            const double nx_ = P.F(F_NX, i), ny_ = P.F(F_NY, i), nz_ = P.F(F_NZ, i);
-            sgn[0] = nx_ > 0.0 ? 1 : -1; sgn[1] = ny_ > 0.0 ? 1 : -1; sgn[2] = nz_ > 0.0 ? 1 : -1;
-            tm[0] = P.F(F_TMX, i); tm[1] = P.F(F_TMY, i); tm[2] = P.F(F_TMZ, i);
-            td[0] = P.F(F_TDX, i); td[1] = P.F(F_TDY, i); td[2] = P.F(F_TDZ, i);
+            const int cs = P.cell[i];
+            const int c = cs & 0x1FFFFFFF;
+            ix = c % g.nx; iy = (c / g.nx) % g.ny; iz = c / (g.nx * g.ny);
+            sx = (cs >> 29) & 1 ? -1 : 1; sy = (cs >> 30) & 1 ? -1 : 1; sz = (cs >> 31) & 1 ? -1 : 1;
+            tmx = P.F(F_TMX, i); tmy = P.F(F_TMY, i); tmz = P.F(F_TMZ, i);
+            tdx = P.F(F_TDX, i); tdy = P.F(F_TDY, i); tdz = P.F(F_TDZ, i);
             nu0 = P.F(F_NU0, i);
             aslope = P.F(F_NULAB, i) * a.inv_ct;
             N = P.F(F_N, i);
-            T = P.F(F_T, i);
+            N_in = N;
+            Tq = P.F(F_T, i);
             cursor = P.cursor[i];
             events = P.events[i];
-            row = row_of(g, idx[0], idx[1], idx[2]);
+            row = row_of(g, ix, iy, iz);
             if (a.rounds) {
-              bx0 = (idx[0] / g.bx) * g.bx; bx1 = bx0 + g.bx;
-              by0 = (idx[1] / g.by) * g.by; by1 = by0 + g.by;
-              bz0 = (idx[2] / g.bz) * g.bz; bz1 = bz0 + g.bz;
+              bx0 = (ix / g.bx) * g.bx; bx1 = bx0 + g.bx;
+              by0 = (iy / g.by) * g.by; by1 = by0 + g.by;
+              bz0 = (iz / g.bz) * g.bz; bz1 = bz0 + g.bz;
             }
+            seg_new = true;
             have = true;
           }
         }
@@ -309,63 +317,76 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
     }
     if (!have) break;
 
-    // ---- one cell segment
-    int axis = 0;
-    double sw = tm[0];
-    if (bits(tm[1]) < bits(sw)) { sw = tm[1]; axis = 1; }   // ties to the lowest axis
-    if (bits(tm[2]) < bits(sw)) { sw = tm[2]; axis = 2; }
-    const long long end_bits = bits(nu0 - aslope * sw);
+    // ---- segment bounds on entering a cell: nearest wall, comoving nu there
+    if (seg_new) {
+      double sw = tmx;
+      axis = 0;
+      if (bits(tmy) < bits(sw)) { sw = tmy; axis = 1; }   // ties to the lowest axis
+      if (bits(tmz) < bits(sw)) { sw = tmz; axis = 2; }
+      end_bits = bits(nu0 - aslope * sw);
+      seg_new = false;
+    }
+    // ---- next interaction point in this cell (at most one event per iteration)
     const double* prow = a.pops + row * a.nlev;
-    int fate = -1;                        // -1 alive
-    bool restart = false;
+    bool found = false;
+    LineRec L;
+    double n_l = 0.0, n_u = 0.0, tau = 0.0;
     while (cursor < a.nline) {
-      const LineRec L = ldline(a.lines, cursor);
+      L = ldline(a.lines, cursor);
       if (bits(L.x) <= end_bits) break;
-      acc[T_TESTS] += 1.0;
-      const int lo = __double2loint(L.w), up = __double2hiint(L.w);
-      const double n_l = prow[lo], n_u = prow[up];
-      const double net = n_l - L.z * n_u;
-      const double tau = L.y * net;
-      if (bits(tau) > taumin_bits) {
-        ++events;
-        acc[T_EVENTS] += 1.0;
-        double ex, ome;
-        expneg(fx, tau, ex, ome);
-        if (MODE == XT_MODE_ATTEN) {
-          const double dN = N * ome;
-          atomicAdd(a.S + row * a.nline + cursor, dN);   // net photons; / f_corr at readout
-          N = N * ex;
-          acc[T_ABS] += dN;
-          if (N * kH * L.x < T) { acc[T_DROP] += N; fate = 1; break; }
-        } else {
-          const int64_t p = P.pid[i];
-          const int nd = P.ndraw[i];
-          P.ndraw[i] = nd + 1;
-          const U4 w = draw(a.seed, p, 2 + (uint64_t)nd);
-          if (w.u[0] < ome) {
-            P.inter[i] += 1;
-            acc[T_INTER] += 1.0;
-            atomicAdd(a.S + row * a.nline + cursor, N);
-            acc[T_ABS] += N;
-            const double Ecmf = N * kH * L.x;
-            acc[T_ABSE] += Ecmf;
-            const int k0 = a.down_off[up], k1 = a.down_off[up + 1];
-            double Wtot = 8.629e-6 * a.ne[row] * a.ups_down[up] / (a.glev[up] * sqrt(a.Te[row]));
-            for (int k = k0; k < k1; ++k) {
-              const int m = a.down_line[k];
-              const LineRec M = ldline(a.lines, m);
-              Wtot += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
-            }
-            const double x = w.u[1] * Wtot;
-            double run = 0.0;
-            int pick = -1;
-            for (int k = k0; k < k1; ++k) {
-              const int m = a.down_line[k];
-              const LineRec M = ldline(a.lines, m);
-              run += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
-              if (x < run) { pick = m; break; }
-            }
-            if (pick < 0) { acc[T_THERM] += Ecmf; fate = 2; break; }
+      ++n_tests;
+      n_l = prow[__double2loint(L.w)];
+      n_u = prow[__double2hiint(L.w)];
+      tau = L.y * (n_l - L.z * n_u);
+      if (bits(tau) > taumin_bits) { found = true; break; }
+      ++cursor;
+    }
+    int fate = -1;                        // -1 alive
+    bool escaped = false, queued = false;
+    if (found) {
+      // ---- line event (lanes that found one run this together)
+      ++events;
+      ++n_events;
+      double ex, ome;
+      expneg(fx, tau, ex, ome);
+      if (MODE == XT_MODE_ATTEN) {
+        atomicAdd(a.S + row * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
+        N = N * ex;
+        if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
+        ++cursor;
+      } else {
+        const int64_t p = P.pid[i];
+        const int nd = P.ndraw[i];
+        P.ndraw[i] = nd + 1;
+        const U4 w = draw(a.seed, p, 2 + (uint64_t)nd);
+        if (w.u[0] < ome) {
+          P.inter[i] += 1;
+          ++n_inter;
+          atomicAdd(a.S + row * a.nline + cursor, N);
+          acc[T_ABS] += N;                    // the whole packet is absorbed
+          const double Ecmf = N * kH * L.x;
+          acc[T_ABSE] += Ecmf;
+          const int up = __double2hiint(L.w);
+          const int k0 = a.down_off[up], k1 = a.down_off[up + 1];
+          double Wtot = 8.629e-6 * a.ne[row] * a.ups_down[up] / (a.glev[up] * sqrt(a.Te[row]));
+          for (int k = k0; k < k1; ++k) {
+            const int m = a.down_line[k];
+            const LineRec M = ldline(a.lines, m);
+            Wtot += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+          }
+          const double x = w.u[1] * Wtot;
+          double run = 0.0;
+          int pick = -1;
+          for (int k = k0; k < k1; ++k) {
+            const int m = a.down_line[k];
+            const LineRec M = ldline(a.lines, m);
+            run += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+            if (x < run) { pick = m; break; }
+          }
+          if (pick < 0) {
+            acc[T_THERM] += Ecmf;
+            fate = 2;
+          } else {
             // move to the resonance point, re-emit isotropically in line `pick`
             double r[3] = {P.F(F_R0X, i), P.F(F_R0Y, i), P.F(F_R0Z, i)};
             double n[3] = {P.F(F_NX, i), P.F(F_NY, i), P.F(F_NZ, i)};
@@ -376,50 +397,54 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
             isotropic(w.u[2], w.u[3], n);
             const double nu_new = ldline(a.lines, pick).x;
             N = Ecmf / (kH * nu_new);
+            N_in = N;
             acc[T_REEM] += Ecmf;
             const double nl_new = nu_new / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * a.inv_ct);
+            const int idx[3] = {ix, iy, iz};
+            double tm[3], td[3];
             walk_init(g, idx, r, n, tm, td);
-            sgn[0] = n[0] > 0.0 ? 1 : -1; sgn[1] = n[1] > 0.0 ? 1 : -1; sgn[2] = n[2] > 0.0 ? 1 : -1;
+            tmx = tm[0]; tmy = tm[1]; tmz = tm[2]; tdx = td[0]; tdy = td[1]; tdz = td[2];
+            sx = n[0] > 0.0 ? 1 : -1; sy = n[1] > 0.0 ? 1 : -1; sz = n[2] > 0.0 ? 1 : -1;
             P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
             P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
             P.F(F_NULAB, i) = nl_new;
             nu0 = nu_new;
             aslope = nl_new * a.inv_ct;
             cursor = pick + 1;
-            if (events >= a.max_events) { acc[T_GUARD] += 1.0; fate = 3; break; }
-            restart = true;
-            break;
+            seg_new = true;
           }
+        } else {
+          ++cursor;
         }
-        if (events >= a.max_events) { acc[T_GUARD] += 1.0; fate = 3; break; }
       }
-      ++cursor;
-    }
-    bool escaped = false, queued = false;
-    if (fate < 0 && !restart) {
-      idx[axis] += sgn[axis];
-      tm[axis] += td[axis];
-      const int nax = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
-      if (idx[axis] < 0 || idx[axis] >= nax) {
+      if (fate < 0 && events >= a.max_events) { ++n_guard; fate = 3; }
+    } else {
+      // ---- no further line in this cell: step into the next one
+      int nax;
+      if (axis == 0) { ix += sx; tmx += tdx; nax = ix < 0 || ix >= g.nx; }
+      else if (axis == 1) { iy += sy; tmy += tdy; nax = iy < 0 || iy >= g.ny; }
+      else { iz += sz; tmz += tdz; nax = iz < 0 || iz >= g.nz; }
+      seg_new = true;
+      if (nax) {
         escaped = true;
       } else {
-        row = row_of(g, idx[0], idx[1], idx[2]);
-        if (a.rounds && (idx[0] < bx0 || idx[0] >= bx1 || idx[1] < by0 || idx[1] >= by1 ||
-                         idx[2] < bz0 || idx[2] >= bz1))
+        row = row_of(g, ix, iy, iz);
+        if (a.rounds && (ix < bx0 || ix >= bx1 || iy < by0 || iy >= by1 || iz < bz0 || iz >= bz1))
           queued = true;
       }
     }
     // ---- packet leaves this lane: escaped, finished, or handed to another subdomain
-    const bool leave = escaped || queued || fate >= 0;
-    if (leave) {
+    if (escaped || queued || fate >= 0) {
       P.F(F_N, i) = N;
       P.events[i] = events;
+      if (MODE == XT_MODE_ATTEN) acc[T_ABS] += N_in - N;   // photons this lane absorbed
       if (queued || (MODE == XT_MODE_SCATTER && escaped)) {
-        P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
-        P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
+        P.F(F_TMX, i) = tmx; P.F(F_TMY, i) = tmy; P.F(F_TMZ, i) = tmz;
+        P.F(F_TDX, i) = tdx; P.F(F_TDY, i) = tdy; P.F(F_TDZ, i) = tdz;
         P.F(F_NU0, i) = nu0;
         P.cursor[i] = cursor;
-        P.cell[i] = (idx[2] * g.ny + idx[1]) * g.nx + idx[0];
+        P.cell[i] = ((iz * g.ny + iy) * g.nx + ix) | (sx < 0 ? 1 << 29 : 0) | (sy < 0 ? 1 << 30 : 0) |
+                    (sz < 0 ? (int)(1u << 31) : 0);
       }
       if (fate >= 0 && a.records) {
         double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
@@ -431,9 +456,11 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs a) {
     warp_append(escaped, (int)i, a.esc, a.n_esc);
     warp_append(queued, (int)i, a.out, a.n_out);
   }
-  const int slots[T_NACC] = {LG_TESTS, LG_EVENTS, LG_ABS_N, LG_DROP_N, LG_GUARD, LG_INTERACT,
-                             LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E};
   __syncwarp();
+  double cnt[4] = {(double)n_tests, (double)n_events, (double)n_guard, (double)n_inter};
+  const int cslots[4] = {LG_TESTS, LG_EVENTS, LG_GUARD, LG_INTERACT};
+  warp_flush(cnt, a.ledger, cslots);
+  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E};
   warp_flush(acc, a.ledger, slots);
 }
 
@@ -479,7 +506,7 @@ __global__ void k_sd_hist(Geometry g, const int* __restrict__ cell, const int* _
                           int64_t n, int* __restrict__ key, unsigned* __restrict__ hist) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int c = cell[q[j]];
+    const int c = cell[q[j]] & 0x1FFFFFFF;
     const int ix = c % g.nx, iy = (c / g.nx) % g.ny, iz = c / (g.nx * g.ny);
     const int sd = ((iz / g.bz) * g.sy + iy / g.by) * g.sx + ix / g.bx;
     key[j] = sd;
