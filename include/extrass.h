@@ -131,10 +131,12 @@ typedef struct {
     double emitted_N, escaped_N, absorbed_N, dropped_N;
     double emitted_E, escaped_E, out_of_band_E;
     double events, tests, guard, thermal_E, interactions, abs_E_cmf, reemit_E_cmf;
-    double transport_ms;    /* device time of the transport kernels */
-    double zero_ms;         /* device time spent clearing the estimator store */
-    double rounds;          /* subdomain-group rounds executed */
-    double queued;          /* packets handed between subdomain groups */
+    double transport_ms;    /* device time of the whole pass (clear, emission, trace, escape) */
+    double zero_ms;         /* clearing the estimator store (overlaps the first emission) */
+    double rounds;          /* trace rounds executed (1 per chunk without subdomain rounds) */
+    double queued;          /* packets handed between subdomains */
+    double emit_ms, trace_ms, escape_ms;   /* summed device time per kernel kind */
+    double kernels;         /* kernels launched by this call */
 } xt_transport_stats;
 
 int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);
@@ -156,14 +158,17 @@ int get_photoexcitation_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells,
  * kind 2: angle-summed L_lambda [nbins], erg/s/A */
 int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 
-/* ---- numerical self-test (no paper counterpart: checks a device primitive) --
- * The attenuation factors e^-tau and 1 - e^-tau of every line event are
- * computed by the library's own fixed-point exponential on the integer pipe.
- * This evaluates it for n values tau > 0 (host or device arrays) on the
- * current device, and, if ref_ex / ref_ome are not NULL, CUDA's exp(-tau) and
- * -expm1(-tau) beside it.  Synchronous; allocates its own temporaries. */
-int xt_selftest_expneg(const double *tau, int64_t n, double *ex, double *ome,
-                       double *ref_ex, double *ref_ome);
+/* ---- numerical self-test (no paper counterpart: checks device primitives) --
+ * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so two hot
+ * transcendental steps are the library's own fixed-point routines on the
+ * integer pipe: kind 0, the attenuation factors e^-x and 1 - e^-x of a line
+ * event (x > 0); kind 1, sin(2 pi x) and cos(2 pi x) of a packet's emission
+ * azimuth (0 <= x < 1, x a multiple of 2^-53).  This evaluates them for n
+ * values (host or device arrays) into y0, y1 and, if r0 / r1 are not NULL,
+ * CUDA's own exp(-x), -expm1(-x) or sin, cos beside them.  Runs on the current
+ * device, synchronously, with temporaries of its own. */
+int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, double *y1,
+                      double *r0, double *r1);
 
 typedef struct {
     int64_t ncell, nlev, nline, n_ion;

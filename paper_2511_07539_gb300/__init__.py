@@ -62,7 +62,8 @@ class TransportParams(C.Structure):
 
 STATS_FIELDS = ["emitted_N", "escaped_N", "absorbed_N", "dropped_N", "emitted_E", "escaped_E",
                 "out_of_band_E", "events", "tests", "guard", "thermal_E", "interactions",
-                "abs_E_cmf", "reemit_E_cmf", "transport_ms", "zero_ms", "rounds", "queued"]
+                "abs_E_cmf", "reemit_E_cmf", "transport_ms", "zero_ms", "rounds", "queued",
+                "emit_ms", "trace_ms", "escape_ms", "kernels"]
 
 
 class TransportStats(C.Structure):
@@ -103,7 +104,7 @@ def lib():
             "get_photoexcitation_rates": ([vp, i64, i64, vp, vp, vp], C.c_int),
             "get_spectrum": ([vp, i32, vp, C.c_size_t], C.c_int),
             "get_sizes": ([vp, vp], C.c_int),
-            "xt_selftest_expneg": ([vp, i64, vp, vp, vp, vp], C.c_int),
+            "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -255,13 +256,14 @@ def get_spectrum(ctx, kind=0, out=None):
     return out
 
 
-def xt_selftest_expneg(tau):
-    """Device fixed-point e^-tau and 1-e^-tau, and CUDA's exp/expm1 beside them."""
-    tau = np.ascontiguousarray(tau, dtype=np.float64)
-    out = [np.zeros_like(tau) for _ in range(4)]
-    rc = lib().xt_selftest_expneg(_ptr(tau), tau.shape[0], *[_ptr(o) for o in out])
+def xt_selftest_fixed(kind, x):
+    """Device fixed-point primitives (kind 0: e^-x, 1 - e^-x; kind 1: sin, cos
+    of 2 pi x) and CUDA's exp/expm1 or sin/cos beside them."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = [np.zeros_like(x) for _ in range(4)]
+    rc = lib().xt_selftest_fixed(int(kind), _ptr(x), x.shape[0], *[_ptr(o) for o in out])
     if rc != XT_OK:
-        raise XtError(rc, "xt_selftest_expneg failed")
+        raise XtError(rc, "xt_selftest_fixed failed")
     return out
 
 

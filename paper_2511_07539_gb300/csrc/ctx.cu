@@ -31,6 +31,24 @@ void fixexp_tables(FixExpTables* t) {
   }
 }
 
+// Tables of the fixed-point sine/cosine (fixexp.cuh), from the host's
+// extended-precision sinl/cosl and M_PIl; Taylor factors by integer division.
+void fixtrig_tables(FixTrigTables* t) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double q63 = 9223372036854775808.0L;
+  for (int j = 0; j <= 64; ++j) {
+    t->sin_t[j] = (uint64_t)(sinl(pi * j / 256.0L) * q63 + 0.5L);
+    t->cos_t[j] = (uint64_t)(cosl(pi * j / 256.0L) * q63 + 0.5L);
+  }
+  t->pi4 = (uint64_t)(pi / 4.0L * q63 + 0.5L);
+  typedef unsigned __int128 u128;
+  const u128 one = ((u128)1) << 63;
+  for (int m = 1; m <= 8; ++m) {
+    const u128 den = (u128)m * (u128)(m + 1);
+    t->inv[m - 1] = (uint64_t)((one + den / 2) / den);
+  }
+}
+
 int fail(xt_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -236,13 +254,20 @@ __global__ void k_spectrum(const double* __restrict__ E, int n_theta, int n_phi,
   }
 }
 
-__global__ void k_selftest_expneg(FixExpTables T, const double* __restrict__ tau, int64_t n,
-                                  double* ex, double* ome, double* rex, double* rome) {
+__global__ void k_selftest_fixed(int kind, FixExpTables T, FixTrigTables R,
+                                 const double* __restrict__ x, int64_t n, double* y0, double* y1,
+                                 double* r0, double* r1) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    expneg(T, tau[i], ex[i], ome[i]);
-    rex[i] = exp(-tau[i]);
-    rome[i] = -expm1(-tau[i]);
+    if (kind == 0) {
+      expneg(T, x[i], y0[i], y1[i]);
+      r0[i] = exp(-x[i]);
+      r1[i] = -expm1(-x[i]);
+    } else {
+      const uint64_t U = (uint64_t)(x[i] * 9007199254740992.0);   // exact for u = U 2^-53
+      sincos_2pi(R, U, y0[i], y1[i]);
+      sincos(2.0 * kPi * x[i], &r0[i], &r1[i]);
+    }
   }
 }
 
@@ -267,6 +292,9 @@ int xt_create(xt_ctx** out, int device, void* cuda_stream) {
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
   cudaEventCreate(&c->ev2);
+  cudaEventCreate(&c->ev_side0);
+  cudaEventCreate(&c->ev_side1);
+  cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (alloc(c, (void**)&c->d_ledger, LG_N * sizeof(double), "ledger")) { delete c; return XT_ENOMEM; }
   *out = c;
   return XT_OK;
@@ -290,6 +318,10 @@ void xt_destroy(xt_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
+  if (c->ev_side0) cudaEventDestroy(c->ev_side0);
+  if (c->ev_side1) cudaEventDestroy(c->ev_side1);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -567,23 +599,25 @@ int get_spectrum(xt_ctx* c, int32_t kind, double* out, size_t n_cap) {
   return XT_OK;
 }
 
-int xt_selftest_expneg(const double* tau, int64_t n, double* ex, double* ome, double* ref_ex,
-                       double* ref_ome) {
-  if (!tau || n < 0 || !ex || !ome) return XT_EINVAL;
+int xt_selftest_fixed(int32_t kind, const double* x, int64_t n, double* y0, double* y1,
+                      double* r0, double* r1) {
+  if (!x || n < 0 || !y0 || !y1 || (kind != 0 && kind != 1)) return XT_EINVAL;
   FixExpTables T;
   fixexp_tables(&T);
+  FixTrigTables R;
+  fixtrig_tables(&R);
   const size_t b = (size_t)n * sizeof(double);
   double* d = nullptr;
   if (cudaMalloc(&d, 5 * b + 8) != cudaSuccess) { cudaGetLastError(); return XT_ENOMEM; }
-  cudaMemcpy(d, tau, b, cudaMemcpyDefault);
-  k_selftest_expneg<<<grid_blocks(n, 256), 256>>>(T, d, n, d + n, d + 2 * n, d + 3 * n, d + 4 * n);
+  cudaMemcpy(d, x, b, cudaMemcpyDefault);
+  k_selftest_fixed<<<grid_blocks(n, 256), 256>>>(kind, T, R, d, n, d + n, d + 2 * n, d + 3 * n, d + 4 * n);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) {
-    cudaMemcpy(ex, d + n, b, cudaMemcpyDefault);
-    cudaMemcpy(ome, d + 2 * n, b, cudaMemcpyDefault);
-    if (ref_ex) cudaMemcpy(ref_ex, d + 3 * n, b, cudaMemcpyDefault);
-    if (ref_ome) cudaMemcpy(ref_ome, d + 4 * n, b, cudaMemcpyDefault);
+    cudaMemcpy(y0, d + n, b, cudaMemcpyDefault);
+    cudaMemcpy(y1, d + 2 * n, b, cudaMemcpyDefault);
+    if (r0) cudaMemcpy(r0, d + 3 * n, b, cudaMemcpyDefault);
+    if (r1) cudaMemcpy(r1, d + 4 * n, b, cudaMemcpyDefault);
   }
   cudaFree(d);
   return e == cudaSuccess ? XT_OK : XT_ECUDA;

@@ -25,6 +25,15 @@ struct FixExpTables {
   uint64_t ln2_b;       // next 64 bits of ln2 2^53
 };
 
+struct FixTrigTables {
+  uint64_t sin_t[65];   // sin(j pi/256), j = 0..64, Q63
+  uint64_t cos_t[65];   // cos(j pi/256), Q63
+  uint64_t pi4;         // pi/4 in Q63
+  uint64_t inv[8];      // 1/(m(m+1)) for m = 1..8 (Taylor factors), Q63
+};
+
+void fixtrig_tables(FixTrigTables* t);  // host
+
 void fixexp_tables(FixExpTables* t);    // host
 
 __device__ __forceinline__ uint64_t mul_q63(uint64_t a, uint64_t b) {
@@ -100,6 +109,44 @@ __device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double
   ex = q63_to_double(E, -k);
   if (k == 0) ome = q63_to_double((1ull << 63) - E, 0);
   else ome = 1.0 - ex;
+}
+
+// sin(2 pi u) and cos(2 pi u) for u = U 2^-53, 0 <= U < 2^53, in fixed point.
+// The octant comes from the top three bits of U (exact); within it the angle
+// beta <= pi/4 is split into j pi/256 (tables) plus delta < pi/256, whose sine
+// and cosine are Taylor series to delta^8 (next term < 2^-72), combined by the
+// angle-addition formulas; octant symmetries give the signs.  Results are
+// within about one ulp of sin and cos of the exact angle 2 pi u.
+__device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, double& s, double& c) {
+  const int oct = (int)(U >> 50);
+  uint64_t g = U & ((1ull << 50) - 1ull);                  // fraction of the octant, Q50
+  if (oct & 1) g = (1ull << 50) - g;                       // reflect: beta = pi/4 - theta
+  const int j = (int)(g >> 44);                            // 0..64
+  const uint64_t b = (g & ((1ull << 44) - 1ull)) << 13;    // Q63, < 2^-6
+  const uint64_t d = mul_q63(b, T.pi4);                    // delta, Q63, < pi/256
+  const uint64_t d2 = mul_q63(d, d);
+  // sin delta = d (1 - d2/(2.3) (1 - d2/(4.5) (1 - d2/(6.7) (1 - d2/(8.9)))))
+  uint64_t ps = (1ull << 63) - mul_q63(d2, T.inv[7]);
+  ps = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[5]), ps);
+  ps = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[3]), ps);
+  ps = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[1]), ps);
+  const uint64_t sd = mul_q63(d, ps);
+  // cos delta = 1 - d2/(1.2) (1 - d2/(3.4) (1 - d2/(5.6) (1 - d2/(7.8))))
+  uint64_t pc = (1ull << 63) - mul_q63(d2, T.inv[6]);
+  pc = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[4]), pc);
+  pc = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[2]), pc);
+  const uint64_t cd = (1ull << 63) - mul_q63(mul_q63(d2, T.inv[0]), pc);
+  const uint64_t sb = mul_q63(T.sin_t[j], cd) + mul_q63(T.cos_t[j], sd);   // sin beta
+  const uint64_t cb = mul_q63(T.cos_t[j], cd) - mul_q63(T.sin_t[j], sd);   // cos beta
+  // angle within the quadrant: alpha = beta (even octant) or pi/2 - beta (odd)
+  const uint64_t sa = (oct & 1) ? cb : sb, ca = (oct & 1) ? sb : cb;
+  const double vs = q63_to_double(sa, 0), vc = q63_to_double(ca, 0);
+  switch (oct >> 1) {
+    case 0: s = vs; c = vc; break;
+    case 1: s = vc; c = -vs; break;
+    case 2: s = -vs; c = -vc; break;
+    default: s = -vc; c = vs; break;
+  }
 }
 
 }  // namespace xt

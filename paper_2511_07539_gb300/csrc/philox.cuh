@@ -34,6 +34,11 @@ __device__ __forceinline__ double u01(uint64_t x) {
   return __longlong_as_double((long long)bits);
 }
 
+// Raw words of draw e of a packet (the uniforms are their top 53 bits).
+__device__ __forceinline__ void draw_raw(uint64_t seed, int64_t packet, uint64_t e, uint64_t x[4]) {
+  philox4x64_10((uint64_t)packet, e, 0, 0, seed, 0, x);
+}
+
 __device__ __forceinline__ U4 draw(uint64_t seed, int64_t packet, uint64_t e) {
   uint64_t x[4];
   philox4x64_10((uint64_t)packet, e, 0, 0, seed, 0, x);

@@ -66,6 +66,7 @@ struct EmitArgs {
   double* __restrict__ ledger;
   double* __restrict__ records;       // record of packet p at (p - rec_base)
   int64_t rec_base;
+  FixTrigTables trig;
 };
 
 struct TraceArgs {
@@ -97,6 +98,7 @@ struct TraceArgs {
   double* __restrict__ records;
   int64_t rec_base;
   FixExpTables fx;
+  FixTrigTables trig;
 };
 
 struct EscArgs {
@@ -120,11 +122,13 @@ __device__ __forceinline__ LineRec ldline(const double2* __restrict__ t, int s) 
   return LineRec{a.x, a.y, b.x, b.y};
 }
 
-__device__ __forceinline__ void isotropic(double umu, double uphi, double n[3]) {
+// Isotropic direction: mu = 2u - 1, phi = 2 pi u' (u' = Uphi 2^-53); the sine
+// and cosine of phi come from the fixed-point routine on the integer pipe.
+__device__ __forceinline__ void isotropic(const FixTrigTables& T, double umu, uint64_t Uphi,
+                                          double n[3]) {
   const double mu = 2.0 * umu - 1.0;
-  const double phi = 2.0 * kPi * uphi;
   double sp, cp;
-  sincos(phi, &sp, &cp);
+  sincos_2pi(T, Uphi, sp, cp);
   const double st = sqrt(1.0 - mu * mu);
   n[0] = st * cp; n[1] = st * sp; n[2] = mu;
 }
@@ -134,19 +138,27 @@ __device__ __forceinline__ double sobolev_beta(double tau) {
 }
 
 // Distance to the next wall along each axis and between walls, from r in cell idx.
+// The three reciprocals 1/n_k come from one division, 1/(n_x n_y n_z).
 __device__ __forceinline__ void walk_init(const Geometry& g, const int idx[3], const double r[3],
                                           const double n[3], double tm[3], double td[3]) {
   const double d[3] = {g.dx, g.dy, g.dz};
+  double inv[3];
+  const double pxy = n[0] * n[1], pall = pxy * n[2];
+  if (fabs(pall) > 1e-280) {
+    const double q = 1.0 / pall;
+    inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) inv[k] = n[k] != 0.0 ? 1.0 / n[k] : 0.0;
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     if (n[k] > 0.0) {
-      const double inv = 1.0 / n[k];
-      tm[k] = fmax(((-g.R + (idx[k] + 1) * d[k]) - r[k]) * inv, 0.0);
-      td[k] = d[k] * inv;
+      tm[k] = fmax(((-g.R + (idx[k] + 1) * d[k]) - r[k]) * inv[k], 0.0);
+      td[k] = d[k] * inv[k];
     } else if (n[k] < 0.0) {
-      const double inv = 1.0 / n[k];
-      tm[k] = fmax(((-g.R + idx[k] * d[k]) - r[k]) * inv, 0.0);
-      td[k] = -d[k] * inv;
+      tm[k] = fmax(((-g.R + idx[k] * d[k]) - r[k]) * inv[k], 0.0);
+      td[k] = -d[k] * inv[k];
     } else {
       tm[k] = INFINITY;
       td[k] = INFINITY;
@@ -180,7 +192,16 @@ __device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsign
 }
 
 // ---------------------------------------------------------------- emission
+template <class T>
+__device__ __forceinline__ void stage(T& dst, const T& src) {
+  for (int k = threadIdx.x; k < (int)(sizeof(T) / 8); k += blockDim.x)
+    reinterpret_cast<uint64_t*>(&dst)[k] = reinterpret_cast<const uint64_t*>(&src)[k];
+}
+
 __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
+  __shared__ FixTrigTables trig;
+  stage(trig, a.trig);
+  __syncthreads();
   double acc[2] = {0.0, 0.0};
   const Geometry& g = a.g;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
@@ -195,11 +216,14 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
     const int idx[3] = {(int)(c % g.nx), (int)((c / g.nx) % g.ny), (int)(c / ((int64_t)g.nx * g.ny))};
     const double d[3] = {g.dx, g.dy, g.dz};
     const double E0 = a.Epk[c];
-    const U4 u = draw(a.seed, p, 0), v = draw(a.seed, p, 1);
+    uint64_t xu[4], xv[4];
+    draw_raw(a.seed, p, 0, xu);
+    draw_raw(a.seed, p, 1, xv);
     double r[3], n[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] = (-g.R + idx[k] * d[k]) + u.u[k] * d[k];
-    isotropic(u.u[3], v.u[0], n);
+    for (int k = 0; k < 3; ++k) r[k] = (-g.R + idx[k] * d[k]) + u01(xu[k]) * d[k];
+    isotropic(trig, u01(xu[3]), xv[0] >> 11, n);
+    const U4 v{{u01(xv[0]), u01(xv[1]), u01(xv[2]), u01(xv[3])}};
     double nu_cmf;
     int cursor;
     if (a.emission == XT_EMIT_BAND) {
@@ -251,12 +275,14 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
 // ---------------------------------------------------------------- trace
 // Per-lane ledger: integer counters, FP64 sums.
 enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_NACC };
+constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
 
 template <int MODE>
 __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
-  for (int k = threadIdx.x; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
-    reinterpret_cast<uint64_t*>(&fx)[k] = reinterpret_cast<const uint64_t*>(&a.fx)[k];
+  __shared__ FixTrigTables trig;
+  stage(fx, a.fx);
+  if (MODE == XT_MODE_SCATTER) stage(trig, a.trig);
   __syncthreads();
   const Geometry& g = a.g;
   const Pool& P = a.pool;
@@ -317,32 +343,51 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     }
     if (!have) break;
 
-    // ---- segment bounds on entering a cell: nearest wall, comoving nu there
-    if (seg_new) {
-      double sw = tmx;
-      axis = 0;
-      if (bits(tmy) < bits(sw)) { sw = tmy; axis = 1; }   // ties to the lowest axis
-      if (bits(tmz) < bits(sw)) { sw = tmz; axis = 2; }
-      end_bits = bits(nu0 - aslope * sw);
-      seg_new = false;
-    }
-    // ---- next interaction point in this cell (at most one event per iteration)
+    // ---- search: test lines and walk cells until an interaction point is met,
+    // the packet leaves the grid or its subdomain, or kMaxSteps walls are crossed
+    // (so that no lane keeps its warp waiting long); the event code below then
+    // runs for all lanes that found one together.
     const double* prow = a.pops + row * a.nlev;
-    bool found = false;
+    bool found = false, escaped = false, queued = false;
     LineRec L;
     double n_l = 0.0, n_u = 0.0, tau = 0.0;
-    while (cursor < a.nline) {
-      L = ldline(a.lines, cursor);
-      if (bits(L.x) <= end_bits) break;
-      ++n_tests;
-      n_l = prow[__double2loint(L.w)];
-      n_u = prow[__double2hiint(L.w)];
-      tau = L.y * (n_l - L.z * n_u);
-      if (bits(tau) > taumin_bits) { found = true; break; }
-      ++cursor;
+    long long next_bits = cursor < a.nline ? bits(ldline(a.lines, cursor).x) : 0;
+    for (int steps = 0;;) {
+      if (seg_new) {       // nearest wall and the comoving frequency there
+        double sw = tmx;
+        axis = 0;
+        if (bits(tmy) < bits(sw)) { sw = tmy; axis = 1; }   // ties to the lowest axis
+        if (bits(tmz) < bits(sw)) { sw = tmz; axis = 2; }
+        end_bits = bits(nu0 - aslope * sw);
+        seg_new = false;
+      }
+      while (cursor < a.nline && next_bits > end_bits) {
+        L = ldline(a.lines, cursor);
+        ++n_tests;
+        n_l = prow[__double2loint(L.w)];
+        n_u = prow[__double2hiint(L.w)];
+        tau = L.y * (n_l - L.z * n_u);
+        if (bits(tau) > taumin_bits) { found = true; break; }
+        ++cursor;
+        next_bits = cursor < a.nline ? bits(ldline(a.lines, cursor).x) : 0;
+      }
+      if (found) break;
+      // no further line in this cell: step into the next one
+      int out;
+      if (axis == 0) { ix += sx; tmx += tdx; out = ix < 0 || ix >= g.nx; }
+      else if (axis == 1) { iy += sy; tmy += tdy; out = iy < 0 || iy >= g.ny; }
+      else { iz += sz; tmz += tdz; out = iz < 0 || iz >= g.nz; }
+      seg_new = true;
+      if (out) { escaped = true; break; }
+      row = row_of(g, ix, iy, iz);
+      prow = a.pops + row * a.nlev;
+      if (a.rounds && (ix < bx0 || ix >= bx1 || iy < by0 || iy >= by1 || iz < bz0 || iz >= bz1)) {
+        queued = true;
+        break;
+      }
+      if (++steps >= kMaxSteps) break;
     }
     int fate = -1;                        // -1 alive
-    bool escaped = false, queued = false;
     if (found) {
       // ---- line event (lanes that found one run this together)
       ++events;
@@ -358,7 +403,9 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         const int64_t p = P.pid[i];
         const int nd = P.ndraw[i];
         P.ndraw[i] = nd + 1;
-        const U4 w = draw(a.seed, p, 2 + (uint64_t)nd);
+        uint64_t xw[4];
+        draw_raw(a.seed, p, 2 + (uint64_t)nd, xw);
+        const U4 w{{u01(xw[0]), u01(xw[1]), u01(xw[2]), u01(xw[3])}};
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
@@ -394,7 +441,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             const double s_l = a.ct * (1.0 - L.x / nu_lab) - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) r[k] = r[k] + s_l * n[k];
-            isotropic(w.u[2], w.u[3], n);
+            isotropic(trig, w.u[2], xw[3] >> 11, n);
             const double nu_new = ldline(a.lines, pick).x;
             N = Ecmf / (kH * nu_new);
             N_in = N;
@@ -418,20 +465,6 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         }
       }
       if (fate < 0 && events >= a.max_events) { ++n_guard; fate = 3; }
-    } else {
-      // ---- no further line in this cell: step into the next one
-      int nax;
-      if (axis == 0) { ix += sx; tmx += tdx; nax = ix < 0 || ix >= g.nx; }
-      else if (axis == 1) { iy += sy; tmy += tdy; nax = iy < 0 || iy >= g.ny; }
-      else { iz += sz; tmz += tdz; nax = iz < 0 || iz >= g.nz; }
-      seg_new = true;
-      if (nax) {
-        escaped = true;
-      } else {
-        row = row_of(g, ix, iy, iz);
-        if (a.rounds && (ix < bx0 || ix >= bx1 || iy < by0 || iy >= by1 || iz < bz0 || iz >= bz1))
-          queued = true;
-      }
     }
     // ---- packet leaves this lane: escaped, finished, or handed to another subdomain
     if (escaped || queued || fate >= 0) {
@@ -713,12 +746,37 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
 
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  // The store clear is HBM-bound and the emission FP64-bound: clear on the side
+  // stream while the first chunk is emitted; the first trace waits for it.
+  bool side_pending = false;
   if (!p->accumulate) {
-    XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
+    XT_CUDA(c, cudaStreamWaitEvent(c->side, c->ev0, 0));
+    XT_CUDA(c, cudaEventRecord(c->ev_side0, c->side));
+    XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->side));
+    XT_CUDA(c, cudaEventRecord(c->ev_side1, c->side));
+    side_pending = true;
     XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
     XT_CUDA(c, cudaMemsetAsync(c->d_ledger, 0, LG_N * sizeof(double), c->stream));
   }
   XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  // per-kernel timing: pairs of events around each launch, summed at the end
+  std::vector<std::pair<int, int>> timed;      // (kind, first event index)
+  size_t nev = 0;
+  auto tick = [&](int kind) -> int {
+    if (nev + 2 > c->ev_pool.size()) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      c->ev_pool.push_back(e0);
+      c->ev_pool.push_back(e1);
+    }
+    timed.push_back({kind, (int)nev});
+    cudaEventRecord(c->ev_pool[nev], c->stream);
+    nev += 2;
+    return (int)nev - 1;
+  };
+  auto tock = [&](int slot) { cudaEventRecord(c->ev_pool[slot], c->stream); };
+  int kernels = 0;
 
   EmitArgs ea;
   ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell; ea.cdf = c->d_wline;
@@ -728,6 +786,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ea.nu_hi = c->band_lo_A > 0 ? kC / (c->band_lo_A * 1e-8) : 0.0;
   ea.e_cut = p->e_cut; ea.pool = P; ea.ledger = c->d_ledger; ea.records = d_rec;
   ea.rec_base = p->packet_begin;
+  fixtrig_tables(&ea.trig);
 
   TraceArgs ta;
   ta.g = G; ta.lines = (const double2*)c->d_lines; ta.nline = c->nline; ta.nlev = c->nlev;
@@ -738,6 +797,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.tau_min = p->tau_min; ta.ct = G.ct; ta.inv_ct = G.inv_ct; ta.max_events = p->max_events;
   ta.ledger = c->d_ledger; ta.records = d_rec; ta.rec_base = p->packet_begin;
   fixexp_tables(&ta.fx);
+  ta.trig = ea.trig;
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
@@ -756,8 +816,15 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     const int64_t n = std::min(chunk, count - off);
     ea.p_begin = p->packet_begin + off;
     ea.n = n;
+    int sl = tick(0);
     k_emit<<<blocks_for(n, 256, 16), 256, 0, c->stream>>>(ea);
     XT_CUDA(c, cudaGetLastError());
+    tock(sl);
+    ++kernels;
+    if (side_pending) {
+      XT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_side1, 0));
+      side_pending = false;
+    }
     const int* list = nullptr;
     int64_t n_list = n;
     for (int round = 0; n_list > 0; ++round) {
@@ -767,17 +834,23 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.n_list = n_list;
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>((int64_t)sm_count() * occ, (n_list + 255) / 256);
+      sl = tick(1);
       if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
       XT_CUDA(c, cudaGetLastError());
+      tock(sl);
+      ++kernels;
       unsigned long long cnt[4];
       XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
       XT_CUDA(c, cudaStreamSynchronize(c->stream));
       ++rounds;
       if (cnt[1] > 0) {
         xa.n_esc = (int64_t)cnt[1];
+        sl = tick(2);
         k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
         XT_CUDA(c, cudaGetLastError());
+        tock(sl);
+        ++kernels;
       }
       n_list = (int64_t)cnt[2];
       queued_total += n_list;
@@ -786,6 +859,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
         int* q = ta.out;
         int* sorted = (q == qA) ? qB : qA;
         XT_CUDA(c, cudaMemsetAsync(hist, 0, (size_t)nsd * sizeof(unsigned), c->stream));
+        kernels += 2;
         k_sd_hist<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(G, P.cell, q, n_list, key, hist);
         XT_CUDA(c, cudaGetLastError());
         std::vector<unsigned> h(nsd);
@@ -801,6 +875,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       }
     }
   }
+  if (side_pending) XT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_side1, 0));
   XT_CUDA(c, cudaEventRecord(c->ev2, c->stream));
   double led[LG_N];
   XT_CUDA(c, cudaMemcpyAsync(led, c->d_ledger, sizeof(led), cudaMemcpyDeviceToHost, c->stream));
@@ -810,13 +885,23 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (out) {
     double* o = &out->emitted_N;
     for (int k = 0; k < LG_N; ++k) o[k] = led[k];
-    float ms0 = 0, ms1 = 0;
-    cudaEventElapsedTime(&ms0, c->ev0, c->ev1);
-    cudaEventElapsedTime(&ms1, c->ev1, c->ev2);
-    out->zero_ms = ms0;
-    out->transport_ms = ms1;
+    float ms_all = 0, ms_clear = 0;
+    cudaEventElapsedTime(&ms_all, c->ev0, c->ev2);
+    if (!p->accumulate) cudaEventElapsedTime(&ms_clear, c->ev_side0, c->ev_side1);
+    out->zero_ms = ms_clear;
+    out->transport_ms = ms_all;
     out->rounds = (double)rounds;
     out->queued = (double)queued_total;
+    double kind_ms[3] = {0, 0, 0};
+    for (auto& tp : timed) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, c->ev_pool[tp.second], c->ev_pool[tp.second + 1]);
+      kind_ms[tp.first] += ms;
+    }
+    out->emit_ms = kind_ms[0];
+    out->trace_ms = kind_ms[1];
+    out->escape_ms = kind_ms[2];
+    out->kernels = kernels;
   }
   if (led[LG_GUARD] > 0)
     return fail(c, XT_ETIMEOUT, "run_transport: " + std::to_string((long long)led[LG_GUARD]) + " packets hit max_events");

@@ -117,6 +117,9 @@ struct xt_ctx {
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  cudaStream_t side = nullptr;       // second stream: store clear overlapping emission
+  cudaEvent_t ev_side0 = nullptr, ev_side1 = nullptr;
+  std::vector<cudaEvent_t> ev_pool;  // per-kernel timing events
 };
 
 namespace xt {
