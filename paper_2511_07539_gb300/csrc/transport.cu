@@ -41,7 +41,7 @@ enum PoolField { F_R0X, F_R0Y, F_R0Z, F_NX, F_NY, F_NZ, F_TMX, F_TMY, F_TMZ, F_T
 struct Pool {           // structure of arrays, capacity cap
   int64_t cap;
   double* f;            // [NF][cap]
-  int* cell;            // natural index of the current cell
+  int* cell;            // current cell, packed ix | iy << 10 | iz << 20
   int* cursor;          // next sorted line to test
   int* events;
   int* ndraw;           // scatter draws used
@@ -54,6 +54,7 @@ struct EmitArgs {
   Geometry g;
   const int64_t* __restrict__ qoff;   // natural [ncell+1]
   const double* __restrict__ Epk;     // natural [ncell] packet energy L_c / n_c
+  const double* __restrict__ Eph;     // natural [ncell] packet energy / h
   const double* __restrict__ cdf;     // [row][caller line] (line emission)
   const double* __restrict__ Lc;      // natural [ncell]
   const int* __restrict__ sorted_of;
@@ -99,6 +100,7 @@ struct TraceArgs {
   int64_t rec_base;
   FixExpTables fx;
   FixTrigTables trig;
+  const int* __restrict__ rtab;       // [nx + ny + nz] separable blocked-row offsets
 };
 
 struct EscArgs {
@@ -219,9 +221,12 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
     uint64_t xu[4], xv[4];
     draw_raw(a.seed, p, 0, xu);
     draw_raw(a.seed, p, 1, xv);
-    double r[3], n[3];
+    double r[3], n[3], uu[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] = (-g.R + idx[k] * d[k]) + u01(xu[k]) * d[k];
+    for (int k = 0; k < 3; ++k) {
+      uu[k] = u01(xu[k]);
+      r[k] = (-g.R + idx[k] * d[k]) + uu[k] * d[k];
+    }
     isotropic(trig, u01(xu[3]), xv[0] >> 11, n);
     const U4 v{{u01(xv[0]), u01(xv[1]), u01(xv[2]), u01(xv[3])}};
     double nu_cmf;
@@ -248,18 +253,40 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
       cursor = s + 1;
     }
     const double nu_lab = nu_cmf / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
-    const double N = E0 / (kH * nu_cmf);
+    const double N = a.Eph[c] / nu_cmf;                 // E0 / (h nu_cmf)
+    // cell walk from the position inside the cell: the nearest wall along k is
+    // d (1 - u) / n_k ahead (n_k > 0) or u d / |n_k| (n_k < 0); td carries the sign
+    double inv[3];
+    {
+      const double pxy = n[0] * n[1], pall = pxy * n[2];
+      if (fabs(pall) > 1e-280) {
+        const double q = 1.0 / pall;
+        inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) inv[k] = n[k] != 0.0 ? 1.0 / n[k] : 0.0;
+      }
+    }
     double tm[3], td[3];
-    walk_init(g, idx, r, n, tm, td);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (n[k] != 0.0) {
+        tm[k] = (n[k] > 0.0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
+        td[k] = d[k] * inv[k];
+      } else {
+        tm[k] = INFINITY;
+        td[k] = INFINITY;
+      }
+    }
     const Pool& P = a.pool;
     P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
     P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
     P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
     P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
     // stop once N nu_line < e_cut E0 / h (the photon energy at the line below e_cut E0)
-    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * E0 / kH;
-    P.cell[i] = (int)c | (n[0] > 0.0 ? 0 : 1 << 29) | (n[1] > 0.0 ? 0 : 1 << 30) |
-                (n[2] > 0.0 ? 0 : (int)(1u << 31)); P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
+    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * a.Eph[c];
+    P.cell[i] = idx[0] | (idx[1] << 10) | (idx[2] << 20);
+    P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
     P.pid[i] = p;
     acc[0] += N;
     acc[1] += E0;
@@ -281,9 +308,15 @@ template <int MODE>
 __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
+  __shared__ int rtab[3 * 1024];
   stage(fx, a.fx);
   if (MODE == XT_MODE_SCATTER) stage(trig, a.trig);
+  const int nt = a.g.nx + a.g.ny + a.g.nz;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) rtab[k] = a.rtab[k];
   __syncthreads();
+  const int* RX = rtab;
+  const int* RY = rtab + a.g.nx;
+  const int* RZ = rtab + a.g.nx + a.g.ny;
   const Geometry& g = a.g;
   const Pool& P = a.pool;
   const int lane = threadIdx.x & 31;
@@ -294,10 +327,11 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   unsigned n_tests = 0, n_events = 0, n_guard = 0, n_inter = 0;
 
   bool have = false, seg_new = true;
-  int64_t i = 0;                         // pool slot
+  int i = 0;                             // pool slot
   int ix = 0, iy = 0, iz = 0, sx = 1, sy = 1, sz = 1, cursor = 0, events = 0, axis = 0;
-  int bx0 = 0, bx1 = 0, by0 = 0, by1 = 0, bz0 = 0, bz1 = 0;   // current subdomain box
-  int64_t row = 0;
+  int rx = 0, ry = 0, rz = 0;            // row = rx + ry + rz (separable blocked layout)
+  int box_lo = 0, box_hi = 0;            // current subdomain box, packed like the cell
+  int row = 0;
   long long end_bits = 0;
   double tmx = 0, tmy = 0, tmz = 0, tdx = 0, tdy = 0, tdz = 0, nu0 = 0, aslope = 0;
   double N = 0, N_in = 0, Tq = 0;
@@ -315,13 +349,13 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         if (!have) {
           const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
           if (my < (unsigned long long)a.n_list) {
-            i = a.list ? a.list[my] : (int64_t)my;
+            i = a.list ? a.list[my] : (int)my;
             const int cs = P.cell[i];
-            const int c = cs & 0x1FFFFFFF;
-            ix = c % g.nx; iy = (c / g.nx) % g.ny; iz = c / (g.nx * g.ny);
-            sx = (cs >> 29) & 1 ? -1 : 1; sy = (cs >> 30) & 1 ? -1 : 1; sz = (cs >> 31) & 1 ? -1 : 1;
+            ix = cs & 1023; iy = (cs >> 10) & 1023; iz = cs >> 20;
             tmx = P.F(F_TMX, i); tmy = P.F(F_TMY, i); tmz = P.F(F_TMZ, i);
             tdx = P.F(F_TDX, i); tdy = P.F(F_TDY, i); tdz = P.F(F_TDZ, i);
+            sx = tdx < 0.0 ? -1 : 1; sy = tdy < 0.0 ? -1 : 1; sz = tdz < 0.0 ? -1 : 1;
+            tdx = fabs(tdx); tdy = fabs(tdy); tdz = fabs(tdz);
             nu0 = P.F(F_NU0, i);
             aslope = P.F(F_NULAB, i) * a.inv_ct;
             N = P.F(F_N, i);
@@ -329,11 +363,12 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             Tq = P.F(F_T, i);
             cursor = P.cursor[i];
             events = P.events[i];
-            row = row_of(g, ix, iy, iz);
+            rx = RX[ix]; ry = RY[iy]; rz = RZ[iz];
+            row = rx + ry + rz;
             if (a.rounds) {
-              bx0 = (ix / g.bx) * g.bx; bx1 = bx0 + g.bx;
-              by0 = (iy / g.by) * g.by; by1 = by0 + g.by;
-              bz0 = (iz / g.bz) * g.bz; bz1 = bz0 + g.bz;
+              const int x0 = (ix / g.bx) * g.bx, y0 = (iy / g.by) * g.by, z0 = (iz / g.bz) * g.bz;
+              box_lo = x0 | (y0 << 10) | (z0 << 20);
+              box_hi = (x0 + g.bx) | ((y0 + g.by) << 10) | ((z0 + g.bz) << 20);
             }
             seg_new = true;
             have = true;
@@ -347,7 +382,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     // the packet leaves the grid or its subdomain, or kMaxSteps walls are crossed
     // (so that no lane keeps its warp waiting long); the event code below then
     // runs for all lanes that found one together.
-    const double* prow = a.pops + row * a.nlev;
+    const double* prow = a.pops + (int64_t)row * a.nlev;
     bool found = false, escaped = false, queued = false;
     LineRec L;
     double n_l = 0.0, n_u = 0.0, tau = 0.0;
@@ -372,16 +407,21 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         next_bits = cursor < a.nline ? bits(ldline(a.lines, cursor).x) : 0;
       }
       if (found) break;
-      // no further line in this cell: step into the next one
-      int out;
-      if (axis == 0) { ix += sx; tmx += tdx; out = ix < 0 || ix >= g.nx; }
-      else if (axis == 1) { iy += sy; tmy += tdy; out = iy < 0 || iy >= g.ny; }
-      else { iz += sz; tmz += tdz; out = iz < 0 || iz >= g.nz; }
+      // no further line in this cell: step into the next one (branch-free in axis)
+      const bool a0 = axis == 0, a1 = axis == 1, a2 = axis == 2;
+      const int coord = (a0 ? ix : a1 ? iy : iz) + (a0 ? sx : a1 ? sy : sz);
+      const double tnew = (a0 ? tmx : a1 ? tmy : tmz) + (a0 ? tdx : a1 ? tdy : tdz);
+      ix = a0 ? coord : ix; iy = a1 ? coord : iy; iz = a2 ? coord : iz;
+      tmx = a0 ? tnew : tmx; tmy = a1 ? tnew : tmy; tmz = a2 ? tnew : tmz;
       seg_new = true;
-      if (out) { escaped = true; break; }
-      row = row_of(g, ix, iy, iz);
-      prow = a.pops + row * a.nlev;
-      if (a.rounds && (ix < bx0 || ix >= bx1 || iy < by0 || iy >= by1 || iz < bz0 || iz >= bz1)) {
+      if (coord < 0 || coord >= (a0 ? g.nx : a1 ? g.ny : g.nz)) { escaped = true; break; }
+      const int rnew = rtab[(a0 ? 0 : a1 ? g.nx : g.nx + g.ny) + coord];
+      rx = a0 ? rnew : rx; ry = a1 ? rnew : ry; rz = a2 ? rnew : rz;
+      row = rx + ry + rz;
+      prow = a.pops + (int64_t)row * a.nlev;
+      if (a.rounds && (ix < (box_lo & 1023) || ix >= (box_hi & 1023) ||
+                       iy < ((box_lo >> 10) & 1023) || iy >= ((box_hi >> 10) & 1023) ||
+                       iz < (box_lo >> 20) || iz >= (box_hi >> 20))) {
         queued = true;
         break;
       }
@@ -395,7 +435,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       double ex, ome;
       expneg(fx, tau, ex, ome);
       if (MODE == XT_MODE_ATTEN) {
-        atomicAdd(a.S + row * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
+        atomicAdd(a.S + (int64_t)row * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
         N = N * ex;
         if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
         ++cursor;
@@ -409,7 +449,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
-          atomicAdd(a.S + row * a.nline + cursor, N);
+          atomicAdd(a.S + (int64_t)row * a.nline + cursor, N);
           acc[T_ABS] += N;                    // the whole packet is absorbed
           const double Ecmf = N * kH * L.x;
           acc[T_ABSE] += Ecmf;
@@ -450,7 +490,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             const int idx[3] = {ix, iy, iz};
             double tm[3], td[3];
             walk_init(g, idx, r, n, tm, td);
-            tmx = tm[0]; tmy = tm[1]; tmz = tm[2]; tdx = td[0]; tdy = td[1]; tdz = td[2];
+            tmx = tm[0]; tmy = tm[1]; tmz = tm[2]; tdx = td[0]; tdy = td[1]; tdz = td[2];   // |d / n|
             sx = n[0] > 0.0 ? 1 : -1; sy = n[1] > 0.0 ? 1 : -1; sz = n[2] > 0.0 ? 1 : -1;
             P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
             P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
@@ -473,11 +513,10 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       if (MODE == XT_MODE_ATTEN) acc[T_ABS] += N_in - N;   // photons this lane absorbed
       if (queued || (MODE == XT_MODE_SCATTER && escaped)) {
         P.F(F_TMX, i) = tmx; P.F(F_TMY, i) = tmy; P.F(F_TMZ, i) = tmz;
-        P.F(F_TDX, i) = tdx; P.F(F_TDY, i) = tdy; P.F(F_TDZ, i) = tdz;
+        P.F(F_TDX, i) = sx * tdx; P.F(F_TDY, i) = sy * tdy; P.F(F_TDZ, i) = sz * tdz;
         P.F(F_NU0, i) = nu0;
         P.cursor[i] = cursor;
-        P.cell[i] = ((iz * g.ny + iy) * g.nx + ix) | (sx < 0 ? 1 << 29 : 0) | (sy < 0 ? 1 << 30 : 0) |
-                    (sz < 0 ? (int)(1u << 31) : 0);
+        P.cell[i] = ix | (iy << 10) | (iz << 20);
       }
       if (fate >= 0 && a.records) {
         double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
@@ -486,8 +525,8 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       }
       have = false;
     }
-    warp_append(escaped, (int)i, a.esc, a.n_esc);
-    warp_append(queued, (int)i, a.out, a.n_out);
+    warp_append(escaped, i, a.esc, a.n_esc);
+    warp_append(queued, i, a.out, a.n_out);
   }
   __syncwarp();
   double cnt[4] = {(double)n_tests, (double)n_events, (double)n_guard, (double)n_inter};
@@ -539,8 +578,8 @@ __global__ void k_sd_hist(Geometry g, const int* __restrict__ cell, const int* _
                           int64_t n, int* __restrict__ key, unsigned* __restrict__ hist) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int c = cell[q[j]] & 0x1FFFFFFF;
-    const int ix = c % g.nx, iy = (c / g.nx) % g.ny, iz = c / (g.nx * g.ny);
+    const int cs = cell[q[j]];
+    const int ix = cs & 1023, iy = (cs >> 10) & 1023, iz = cs >> 20;
     const int sd = ((iz / g.bz) * g.sy + iy / g.by) * g.sx + ix / g.bx;
     key[j] = sd;
     atomicAdd(hist + sd, 1u);
@@ -662,6 +701,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (!(p->tau_min > 0) || !(p->e_cut >= 0)) return fail(c, XT_EINVAL, "run_transport: tau_min > 0 and e_cut >= 0 required");
   if (c->nline < 1) return fail(c, XT_ESTATE, "run_transport: no lines loaded");
   if (G.ncell >= (int64_t)1 << 31) return fail(c, XT_EINVAL, "run_transport: more than 2^31 cells");
+  if (G.nx > 1024 || G.ny > 1024 || G.nz > 1024) return fail(c, XT_EINVAL, "run_transport: more than 1024 cells along an axis");
   int rc;
   // estimator store
   const size_t Sb = (size_t)G.ncell * c->nline * sizeof(double);
@@ -683,7 +723,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   // emission: cell luminosities, packet quota, packet energy per cell
   if (c->qoff_N != p->n_packets || c->qoff_mode != p->emission) {
     std::vector<double> Lnat;
-    if ((rc = alloc(c, (void**)&c->d_Lc, G.ncell * sizeof(double) * 2, "Lc"))) return rc;
+    if ((rc = alloc(c, (void**)&c->d_Lc, G.ncell * sizeof(double) * 3, "Lc"))) return rc;
     if (p->emission == XT_EMIT_BAND) {
       Lnat = c->h_L;
     } else {
@@ -702,11 +742,12 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     }
     std::vector<int64_t> q;
     packet_quota(Lnat, p->n_packets, q);
-    std::vector<double> hv(2 * G.ncell, 0.0);     // [Lc | E per packet]
+    std::vector<double> hv(3 * G.ncell, 0.0);     // [Lc | E per packet | E per packet / h]
     for (int64_t k = 0; k < G.ncell; ++k) {
       hv[k] = Lnat[k];
       const int64_t nq = q[k + 1] - q[k];
       hv[G.ncell + k] = nq > 0 ? Lnat[k] / (double)nq : 0.0;
+      hv[2 * G.ncell + k] = hv[G.ncell + k] / kH;
     }
     if ((rc = copy(c, c->d_Lc, hv.data(), hv.size() * sizeof(double), "Lc"))) return rc;
     if ((rc = alloc(c, (void**)&c->d_qoff, q.size() * sizeof(int64_t), "quota"))) return rc;
@@ -717,7 +758,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   // packet pool and queues
   const int nsd = c->sx * c->sy * c->sz;
-  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 24);
+  // one chunk of up to 2^27 packets (23 GB of pool): the whole emission of a
+  // paper-scale pass runs while the estimator store is being cleared
+  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
   if ((rc = ensure_buffers(c, chunk, nsd))) return rc;
   const int64_t cap = c->pool_cap;
   int* const I = c->d_pool_i;
@@ -779,7 +822,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   int kernels = 0;
 
   EmitArgs ea;
-  ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell; ea.cdf = c->d_wline;
+  ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell;
+  ea.Eph = c->d_Lc + 2 * G.ncell; ea.cdf = c->d_wline;
   ea.sorted_of = c->d_orig; ea.nu_tab = c->d_nu; ea.nline = c->nline; ea.emission = p->emission;
   ea.seed = p->seed;
   ea.nu_lo = c->band_hi_A > 0 ? kC / (c->band_hi_A * 1e-8) : 0.0;
@@ -798,6 +842,18 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.ledger = c->d_ledger; ta.records = d_rec; ta.rec_base = p->packet_begin;
   fixexp_tables(&ta.fx);
   ta.trig = ea.trig;
+  {
+    // separable blocked-row offsets: row = RX[ix] + RY[iy] + RZ[iz]
+    const int B = G.bx * G.by * G.bz;
+    std::vector<int> rt(G.nx + G.ny + G.nz);
+    for (int x = 0; x < G.nx; ++x) rt[x] = (x / G.bx) * B + x % G.bx;
+    for (int y = 0; y < G.ny; ++y) rt[G.nx + y] = (y / G.by) * G.sx * B + (y % G.by) * G.bx;
+    for (int z = 0; z < G.nz; ++z)
+      rt[G.nx + G.ny + z] = (z / G.bz) * G.sy * G.sx * B + (z % G.bz) * G.by * G.bx;
+    if ((rc = alloc(c, (void**)&c->d_rtab, rt.size() * sizeof(int), "row tables"))) return rc;
+    if ((rc = copy(c, c->d_rtab, rt.data(), rt.size() * sizeof(int), "row tables"))) return rc;
+  }
+  ta.rtab = c->d_rtab;
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;

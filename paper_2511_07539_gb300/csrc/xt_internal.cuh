@@ -105,6 +105,7 @@ struct xt_ctx {
   // ledger
   double* d_ledger = nullptr;        // [LG_N]
   double* d_lines = nullptr;         // [sorted line] packed nu, K, gratio, (lo, up): 32 B
+  int* d_rtab = nullptr;             // separable blocked-row offsets [nx + ny + nz]
   // transport buffers
   double* d_pool_f = nullptr;
   int* d_pool_i = nullptr;
