@@ -101,6 +101,9 @@ struct TraceArgs {
   FixExpTables fx;
   FixTrigTables trig;
   const int* __restrict__ rtab;       // [nx + ny + nz] separable blocked-row offsets
+  int64_t* __restrict__ slotlog;      // touched estimator slots
+  unsigned long long* __restrict__ n_slotlog;
+  int64_t slotlog_cap;
 };
 
 struct EscArgs {
@@ -191,6 +194,27 @@ __device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsign
   if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
   base = __shfl_sync(act, base, leader);
   if (want) buf[base + __popc(m & ((1u << lane) - 1u))] = idx;
+}
+
+// Warp-aggregated append of a 64-bit slot index; entries past cap are counted, not written.
+__device__ __forceinline__ void log_slot(bool want, int64_t slot, int64_t* buf, unsigned long long* n,
+                                         int64_t cap) {
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, want);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
+  base = __shfl_sync(act, base, leader);
+  const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
+  if (want && k < (unsigned long long)cap) buf[k] = slot;
+}
+
+__global__ void k_unlog(double* __restrict__ S, const int64_t* __restrict__ log, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    S[log[k]] = 0.0;
 }
 
 // ---------------------------------------------------------------- emission
@@ -428,6 +452,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       if (++steps >= kMaxSteps) break;
     }
     int fate = -1;                        // -1 alive
+    log_slot(found, (int64_t)row * a.nline + cursor, a.slotlog, a.n_slotlog, a.slotlog_cap);
     if (found) {
       // ---- line event (lanes that found one run this together)
       ++events;
@@ -674,7 +699,7 @@ static int ensure_buffers(xt_ctx* c, int64_t cap, int nsd) {
     if ((rc = alloc(c, (void**)&c->d_pool_pid, (size_t)cap * sizeof(int64_t), "packet pool"))) return rc;
     c->pool_cap = cap;
   }
-  if (!c->d_counters && (rc = alloc(c, (void**)&c->d_counters, 4 * sizeof(unsigned long long), "counters"))) return rc;
+  if (!c->d_counters && (rc = alloc(c, (void**)&c->d_counters, 8 * sizeof(unsigned long long), "counters"))) return rc;
   if (c->hist_n < nsd) {
     c->hist_n = 0;
     if ((rc = alloc(c, (void**)&c->d_hist, (size_t)2 * nsd * sizeof(unsigned), "subdomain histogram"))) return rc;
@@ -709,6 +734,13 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     if ((rc = alloc(c, (void**)&c->d_S, Sb, "estimator store"))) return rc;
     c->S_bytes = Sb;
     XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
+    c->slotlog_valid = true;        // the store is all zero
+    c->slotlog_n = 0;
+  }
+  if (!c->d_slotlog) {
+    const int64_t want = std::min<int64_t>(std::max<int64_t>(4 * count, (int64_t)1 << 20), (int64_t)1 << 29);
+    if ((rc = alloc(c, (void**)&c->d_slotlog, (size_t)want * sizeof(int64_t), "slot log"))) return rc;
+    c->slotlog_cap = want;
   }
   // spectrum
   const int views = p->n_theta * p->n_phi;
@@ -789,18 +821,25 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
 
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  // The store clear is HBM-bound and the emission FP64-bound: clear on the side
-  // stream while the first chunk is emitted; the first trace waits for it.
-  bool side_pending = false;
+  // Clear the estimator store: only the slots the previous passes wrote (the
+  // touched-slot log) when the log is complete, else the whole store.
+  int kernels_clear = 0;
   if (!p->accumulate) {
-    XT_CUDA(c, cudaStreamWaitEvent(c->side, c->ev0, 0));
-    XT_CUDA(c, cudaEventRecord(c->ev_side0, c->side));
-    XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->side));
-    XT_CUDA(c, cudaEventRecord(c->ev_side1, c->side));
-    side_pending = true;
+    if (c->slotlog_valid) {
+      if (c->slotlog_n > 0) {
+        k_unlog<<<blocks_for(c->slotlog_n, 256, 8), 256, 0, c->stream>>>(c->d_S, c->d_slotlog, c->slotlog_n);
+        XT_CUDA(c, cudaGetLastError());
+        ++kernels_clear;
+      }
+    } else {
+      XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
+    }
+    c->slotlog_n = 0;
+    c->slotlog_valid = true;
     XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
     XT_CUDA(c, cudaMemsetAsync(c->d_ledger, 0, LG_N * sizeof(double), c->stream));
   }
+  XT_CUDA(c, cudaMemcpyAsync(counters + 4, &c->slotlog_n, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   // per-kernel timing: pairs of events around each launch, summed at the end
   std::vector<std::pair<int, int>> timed;      // (kind, first event index)
@@ -819,7 +858,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return (int)nev - 1;
   };
   auto tock = [&](int slot) { cudaEventRecord(c->ev_pool[slot], c->stream); };
-  int kernels = 0;
+  int kernels = kernels_clear;
 
   EmitArgs ea;
   ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell;
@@ -854,6 +893,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     if ((rc = copy(c, c->d_rtab, rt.data(), rt.size() * sizeof(int), "row tables"))) return rc;
   }
   ta.rtab = c->d_rtab;
+  ta.slotlog = c->d_slotlog;
+  ta.n_slotlog = counters + 4;
+  ta.slotlog_cap = c->slotlog_cap;
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
@@ -877,15 +919,12 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     XT_CUDA(c, cudaGetLastError());
     tock(sl);
     ++kernels;
-    if (side_pending) {
-      XT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_side1, 0));
-      side_pending = false;
-    }
+
     const int* list = nullptr;
     int64_t n_list = n;
     for (int round = 0; n_list > 0; ++round) {
       if (round >= max_rounds) return fail(c, XT_ETIMEOUT, "run_transport: subdomain rounds did not drain");
-      XT_CUDA(c, cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), c->stream));
+      XT_CUDA(c, cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), c->stream));
       ta.list = list;
       ta.n_list = n_list;
       ta.out = (list == qA) ? qB : qA;
@@ -931,19 +970,31 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       }
     }
   }
-  if (side_pending) XT_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_side1, 0));
   XT_CUDA(c, cudaEventRecord(c->ev2, c->stream));
   double led[LG_N];
   XT_CUDA(c, cudaMemcpyAsync(led, c->d_ledger, sizeof(led), cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long nlog = 0;
+  XT_CUDA(c, cudaMemcpyAsync(&nlog, counters + 4, sizeof(nlog), cudaMemcpyDeviceToHost, c->stream));
   if (rec_host) XT_CUDA(c, cudaMemcpyAsync(p->packet_records, d_rec, rec_bytes, cudaMemcpyDeviceToHost, c->stream));
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_S = true;
+  c->slotlog_n = (int64_t)nlog;
+  if (c->slotlog_n > c->slotlog_cap) {
+    // the log overflowed: the next pass clears the whole store; grow the log
+    c->slotlog_valid = false;
+    const int64_t want = std::min<int64_t>(2 * c->slotlog_n, (int64_t)1 << 30);
+    if (want > c->slotlog_cap && alloc(c, (void**)&c->d_slotlog, (size_t)want * sizeof(int64_t), "slot log") == XT_OK)
+      c->slotlog_cap = want;
+    else if (!c->d_slotlog)
+      c->slotlog_cap = 0;
+    c->err.clear();
+  }
   if (out) {
     double* o = &out->emitted_N;
     for (int k = 0; k < LG_N; ++k) o[k] = led[k];
     float ms_all = 0, ms_clear = 0;
     cudaEventElapsedTime(&ms_all, c->ev0, c->ev2);
-    if (!p->accumulate) cudaEventElapsedTime(&ms_clear, c->ev_side0, c->ev_side1);
+    cudaEventElapsedTime(&ms_clear, c->ev0, c->ev1);
     out->zero_ms = ms_clear;
     out->transport_ms = ms_all;
     out->rounds = (double)rounds;

@@ -106,6 +106,12 @@ struct xt_ctx {
   double* d_ledger = nullptr;        // [LG_N]
   double* d_lines = nullptr;         // [sorted line] packed nu, K, gratio, (lo, up): 32 B
   int* d_rtab = nullptr;             // separable blocked-row offsets [nx + ny + nz]
+  // touched-slot log: every estimator slot written by the last pass, so the
+  // next pass clears those slots instead of the whole store
+  int64_t* d_slotlog = nullptr;
+  int64_t slotlog_cap = 0;
+  int64_t slotlog_n = 0;             // entries of the last pass (may exceed cap)
+  bool slotlog_valid = false;        // every nonzero slot of the store is in the log
   // transport buffers
   double* d_pool_f = nullptr;
   int* d_pool_i = nullptr;

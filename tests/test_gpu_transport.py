@@ -250,3 +250,19 @@ def test_clumpy_onion_full_run_sampled(xt, onion):
         for i, p in enumerate(ids):
             o = oracle.transport(w, p_begin=int(p), p_end=int(p) + 1, per_packet=True, sparse=True)
             _cmp_records(got[i:i + 1], o["pkt"])
+
+
+def test_consecutive_passes_clear_the_store(xt):
+    """Back-to-back passes on one context: each pass clears what the previous
+    one wrote (the touched-slot log, or the whole store after a log overflow)."""
+    w = synth.uniform_sphere(n_packets=100_000, seed=14)
+    w.pops = w.pops * 3e-6          # thin: many events per packet, overflows the first log
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        for seed in (14, 15, 16, 17):
+            st = ctx.transport(w, seed=seed)
+            S = ctx.get_estimators()
+            o = oracle.transport(w, seed=seed)
+            assert st["events"] == o["ledger"]["events"]
+            _cmp_sparse(S, o["S"], S_TOL, f"pass with seed {seed}")
+        assert st["events"] > 4 * w.n_packets
