@@ -101,9 +101,10 @@ struct TraceArgs {
   FixExpTables fx;
   FixTrigTables trig;
   const int* __restrict__ rtab;       // [nx + ny + nz] separable blocked-row offsets
-  int64_t* __restrict__ slotlog;      // touched estimator slots
-  unsigned long long* __restrict__ n_slotlog;
-  int64_t slotlog_cap;
+  int64_t* __restrict__ slotlog;      // touched estimator slots: one segment per block
+  int64_t* __restrict__ seg_n;        // entries per segment (kept across launches)
+  int64_t seg_len;
+  unsigned long long* __restrict__ log_overflow;
 };
 
 struct EscArgs {
@@ -196,25 +197,12 @@ __device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsign
   if (want) buf[base + __popc(m & ((1u << lane) - 1u))] = idx;
 }
 
-// Warp-aggregated append of a 64-bit slot index; entries past cap are counted, not written.
-__device__ __forceinline__ void log_slot(bool want, int64_t slot, int64_t* buf, unsigned long long* n,
-                                         int64_t cap) {
-  const unsigned act = __activemask();
-  const unsigned m = __ballot_sync(act, want);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
-  base = __shfl_sync(act, base, leader);
-  const unsigned long long k = base + __popc(m & ((1u << lane) - 1u));
-  if (want && k < (unsigned long long)cap) buf[k] = slot;
-}
-
-__global__ void k_unlog(double* __restrict__ S, const int64_t* __restrict__ log, int64_t n) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    S[log[k]] = 0.0;
+// Clear the slots listed in each block's log segment.
+__global__ void k_unlog(double* __restrict__ S, const int64_t* __restrict__ log,
+                        const int64_t* __restrict__ seg_n, int64_t seg_len) {
+  const int64_t n = seg_n[blockIdx.x];
+  const int64_t* l = log + (int64_t)blockIdx.x * seg_len;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) S[l[k]] = 0.0;
 }
 
 // ---------------------------------------------------------------- emission
@@ -327,6 +315,7 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
 // Per-lane ledger: integer counters, FP64 sums.
 enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_NACC };
 constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
+constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
 template <int MODE>
 __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(const TraceArgs a) {
@@ -341,6 +330,10 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   const int* RX = rtab;
   const int* RY = rtab + a.g.nx;
   const int* RZ = rtab + a.g.nx + a.g.ny;
+  __shared__ unsigned long long blk_log;          // entries in this block's log segment
+  if (threadIdx.x == 0) blk_log = (unsigned long long)a.seg_n[blockIdx.x];
+  __syncthreads();
+  int64_t* const my_log = a.slotlog + (int64_t)blockIdx.x * a.seg_len;
   const Geometry& g = a.g;
   const Pool& P = a.pool;
   const int lane = threadIdx.x & 31;
@@ -452,8 +445,9 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       if (++steps >= kMaxSteps) break;
     }
     int fate = -1;                        // -1 alive
-    log_slot(found, (int64_t)row * a.nline + cursor, a.slotlog, a.n_slotlog, a.slotlog_cap);
     if (found) {
+      const unsigned long long k = atomicAdd(&blk_log, 1ull);
+      if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
       // ---- line event (lanes that found one run this together)
       ++events;
       ++n_events;
@@ -554,6 +548,12 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     warp_append(queued, i, a.out, a.n_out);
   }
   __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long nb = blk_log;
+    if (nb > (unsigned long long)a.seg_len) atomicAdd(a.log_overflow, 1ull);
+    a.seg_n[blockIdx.x] = (int64_t)(nb < (unsigned long long)a.seg_len ? nb : a.seg_len);
+  }
   double cnt[4] = {(double)n_tests, (double)n_events, (double)n_guard, (double)n_inter};
   const int cslots[4] = {LG_TESTS, LG_EVENTS, LG_GUARD, LG_INTERACT};
   warp_flush(cnt, a.ledger, cslots);
@@ -738,9 +738,13 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     c->slotlog_n = 0;
   }
   if (!c->d_slotlog) {
-    const int64_t want = std::min<int64_t>(std::max<int64_t>(4 * count, (int64_t)1 << 20), (int64_t)1 << 29);
+    const int64_t want = std::min<int64_t>(std::max<int64_t>(4 * count, (int64_t)1 << 22), (int64_t)1 << 29);
     if ((rc = alloc(c, (void**)&c->d_slotlog, (size_t)want * sizeof(int64_t), "slot log"))) return rc;
     c->slotlog_cap = want;
+  }
+  if (!c->d_seg_n) {
+    if ((rc = alloc(c, (void**)&c->d_seg_n, (kLogSegments + 1) * sizeof(int64_t), "log segments"))) return rc;
+    XT_CUDA(c, cudaMemsetAsync(c->d_seg_n, 0, (kLogSegments + 1) * sizeof(int64_t), c->stream));
   }
   // spectrum
   const int views = p->n_theta * p->n_phi;
@@ -820,6 +824,15 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     }
   }
 
+  int occ = 0;
+  if (p->mode == XT_MODE_ATTEN)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_SCATTER>, 256, 0);
+  occ = std::max(occ, 1);
+  // trace blocks per launch = touched-slot log segments
+  int grid_max = (int)std::min<int64_t>((int64_t)sm_count() * occ, kLogSegments);
+  if (p->accumulate && c->log_nseg > 0) grid_max = std::min(grid_max, c->log_nseg);
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   // Clear the estimator store: only the slots the previous passes wrote (the
   // touched-slot log) when the log is complete, else the whole store.
@@ -827,19 +840,21 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (!p->accumulate) {
     if (c->slotlog_valid) {
       if (c->slotlog_n > 0) {
-        k_unlog<<<blocks_for(c->slotlog_n, 256, 8), 256, 0, c->stream>>>(c->d_S, c->d_slotlog, c->slotlog_n);
+        k_unlog<<<c->log_nseg, 256, 0, c->stream>>>(c->d_S, c->d_slotlog, c->d_seg_n, c->log_seglen);
         XT_CUDA(c, cudaGetLastError());
         ++kernels_clear;
       }
     } else {
       XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
     }
+    XT_CUDA(c, cudaMemsetAsync(c->d_seg_n, 0, (kLogSegments + 1) * sizeof(int64_t), c->stream));
     c->slotlog_n = 0;
     c->slotlog_valid = true;
+    c->log_nseg = grid_max;
+    c->log_seglen = c->slotlog_cap / grid_max;
     XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
     XT_CUDA(c, cudaMemsetAsync(c->d_ledger, 0, LG_N * sizeof(double), c->stream));
   }
-  XT_CUDA(c, cudaMemcpyAsync(counters + 4, &c->slotlog_n, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
   XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   // per-kernel timing: pairs of events around each launch, summed at the end
   std::vector<std::pair<int, int>> timed;      // (kind, first event index)
@@ -894,20 +909,19 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   ta.rtab = c->d_rtab;
   ta.slotlog = c->d_slotlog;
-  ta.n_slotlog = counters + 4;
-  ta.slotlog_cap = c->slotlog_cap;
+  ta.seg_n = c->d_seg_n;
+  if (c->log_nseg <= 0) {         // first pass of an accumulating sequence
+    c->log_nseg = grid_max;
+    c->log_seglen = c->slotlog_cap / grid_max;
+  }
+  ta.seg_len = c->log_seglen;
+  ta.log_overflow = (unsigned long long*)(c->d_seg_n + kLogSegments);
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
   xa.nbins = p->spec_nbins; xa.lam0 = p->spec_lam0_A; xa.log1p_dlog = std::log1p(p->spec_dlog);
   xa.ledger = c->d_ledger; xa.records = d_rec; xa.rec_base = p->packet_begin;
 
-  int occ = 0;
-  if (p->mode == XT_MODE_ATTEN)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_SCATTER>, 256, 0);
-  occ = std::max(occ, 1);
   const int max_rounds = 1 << 20;
   int64_t rounds = 0, queued_total = 0;
   for (int64_t off = 0; off < count; off += chunk) {
@@ -928,7 +942,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.list = list;
       ta.n_list = n_list;
       ta.out = (list == qA) ? qB : qA;
-      const int grid = (int)std::min<int64_t>((int64_t)sm_count() * occ, (n_list + 255) / 256);
+      const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
       if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
@@ -973,20 +987,21 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   XT_CUDA(c, cudaEventRecord(c->ev2, c->stream));
   double led[LG_N];
   XT_CUDA(c, cudaMemcpyAsync(led, c->d_ledger, sizeof(led), cudaMemcpyDeviceToHost, c->stream));
-  unsigned long long nlog = 0;
-  XT_CUDA(c, cudaMemcpyAsync(&nlog, counters + 4, sizeof(nlog), cudaMemcpyDeviceToHost, c->stream));
+  unsigned long long nover = 0;
+  XT_CUDA(c, cudaMemcpyAsync(&nover, c->d_seg_n + kLogSegments, sizeof(nover), cudaMemcpyDeviceToHost, c->stream));
   if (rec_host) XT_CUDA(c, cudaMemcpyAsync(p->packet_records, d_rec, rec_bytes, cudaMemcpyDeviceToHost, c->stream));
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_S = true;
-  c->slotlog_n = (int64_t)nlog;
-  if (c->slotlog_n > c->slotlog_cap) {
-    // the log overflowed: the next pass clears the whole store; grow the log
+  c->slotlog_n += (int64_t)led[LG_EVENTS] + 1;      // nonzero once anything was logged
+  if (nover > 0) {
+    // a segment overflowed: the next pass clears the whole store; grow the log
     c->slotlog_valid = false;
-    const int64_t want = std::min<int64_t>(2 * c->slotlog_n, (int64_t)1 << 30);
+    const int64_t want = std::min<int64_t>(4 * c->slotlog_cap, (int64_t)1 << 31);
     if (want > c->slotlog_cap && alloc(c, (void**)&c->d_slotlog, (size_t)want * sizeof(int64_t), "slot log") == XT_OK)
       c->slotlog_cap = want;
     else if (!c->d_slotlog)
       c->slotlog_cap = 0;
+    c->log_nseg = 0;
     c->err.clear();
   }
   if (out) {

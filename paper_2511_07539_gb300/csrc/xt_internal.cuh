@@ -109,6 +109,9 @@ struct xt_ctx {
   // touched-slot log: every estimator slot written by the last pass, so the
   // next pass clears those slots instead of the whole store
   int64_t* d_slotlog = nullptr;
+  int64_t* d_seg_n = nullptr;        // entries per log segment, then an overflow counter
+  int log_nseg = 0;                  // segments (trace blocks) of the current log layout
+  int64_t log_seglen = 0;
   int64_t slotlog_cap = 0;
   int64_t slotlog_n = 0;             // entries of the last pass (may exceed cap)
   bool slotlog_valid = false;        // every nonzero slot of the store is in the log
