@@ -170,6 +170,61 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, double *y1,
                       double *r0, double *r1);
 
+/* ---- transport without device allocation (no paper counterpart) -----------
+ * For callers that cannot call cudaMalloc: code running while a CUDA stream is
+ * being captured into a graph, programs whose device memory is handed out once
+ * at start-up by another framework's allocator, or embedders held to a fixed
+ * device-memory budget.  run_transport_noalloc does one attenuation-mode pass
+ * (band emission, the whole grid one domain) like run_transport, but it makes
+ * no device allocation: its working memory is a file-scope device array of
+ * XT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits, and it calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   - The caller passes the inputs and the outputs.  pops, S and spec must be
+ *     device memory; the other arrays may be host or device memory.
+ *   - Limits: at most XT_NOALLOC_MAX_CELLS cells, XT_NOALLOC_MAX_LINES lines,
+ *     2..65536 levels, 1..1024 cells per axis; larger sizes return XT_EINVAL
+ *     with a message in errbuf.  Packets are traced in chunks of
+ *     XT_NOALLOC_CHUNK, so n_packets is not limited.
+ *   - On its first call on a device it looks up the device address of the
+ *     array (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture starts.
+ *   - Every call shares the one array (and fixed host staging buffers), which
+ *     keeps the last call's contents; each call clears what must start at zero.
+ *     Calls that overlap on the GPU, or run from several host threads at once,
+ *     race with each other: issue them one after another.
+ *   - Outputs: S [ncell][nline] (natural cell order, caller line order) gets the
+ *     photoexcitation estimators, photons/s absorbed divided by f_corr, as
+ *     get_estimators returns them; spec [n_theta*n_phi][spec_nbins] the escaped
+ *     lab-frame energy per bin, as get_spectrum kind 0; `out` the ledger (the
+ *     timing fields are 0).  Synchronous on `cuda_stream`. */
+#define XT_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define XT_NOALLOC_MAX_CELLS 65536
+#define XT_NOALLOC_MAX_LINES 16384
+#define XT_NOALLOC_CHUNK 131072
+typedef struct {
+    int32_t nx, ny, nz;
+    double v_max, t;
+    const double *L_cell;         /* [ncell] erg/s in the flat-nu band */
+    double band_lo_A, band_hi_A;
+    int32_t nlev, nline;
+    const double *g_level;        /* [nlev] */
+    const int32_t *lo, *up;       /* [nline] */
+    const double *lambda_A, *f_lu;/* [nline] */
+    const double *pops;           /* [ncell][nlev] device, natural order */
+    int64_t n_packets;
+    uint64_t seed;
+    double tau_min, e_cut;
+    int32_t n_theta, n_phi;
+    double spec_lam0_A, spec_dlog;
+    int32_t spec_nbins;
+    int64_t max_events;
+    double *S;                    /* out, device [ncell][nline] */
+    double *spec;                 /* out, device [n_theta*n_phi][spec_nbins] */
+} xt_noalloc_transport;
+int run_transport_noalloc(const xt_noalloc_transport *a, void *cuda_stream,
+                          xt_transport_stats *out, char *errbuf, size_t errlen);
+
 typedef struct {
     int64_t ncell, nlev, nline, n_ion;
     int64_t spec_views, spec_bins;

@@ -73,6 +73,19 @@ class TransportStats(C.Structure):
         return {f: getattr(self, f) for f in STATS_FIELDS}
 
 
+class NoallocTransport(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("v_max", C.c_double), ("t", C.c_double), ("L_cell", C.c_void_p),
+                ("band_lo_A", C.c_double), ("band_hi_A", C.c_double),
+                ("nlev", C.c_int32), ("nline", C.c_int32), ("g_level", C.c_void_p),
+                ("lo", C.c_void_p), ("up", C.c_void_p), ("lambda_A", C.c_void_p),
+                ("f_lu", C.c_void_p), ("pops", C.c_void_p), ("n_packets", C.c_int64),
+                ("seed", C.c_uint64), ("tau_min", C.c_double), ("e_cut", C.c_double),
+                ("n_theta", C.c_int32), ("n_phi", C.c_int32), ("spec_lam0_A", C.c_double),
+                ("spec_dlog", C.c_double), ("spec_nbins", C.c_int32), ("max_events", C.c_int64),
+                ("S", C.c_void_p), ("spec", C.c_void_p)]
+
+
 class Sizes(C.Structure):
     _fields_ = [(f, C.c_int64) for f in
                 ["ncell", "nlev", "nline", "n_ion", "spec_views", "spec_bins", "store_bytes"]]
@@ -105,6 +118,7 @@ def lib():
             "get_spectrum": ([vp, i32, vp, C.c_size_t], C.c_int),
             "get_sizes": ([vp, vp], C.c_int),
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
+            "run_transport_noalloc": ([vp, vp, vp, C.c_char_p, C.c_size_t], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -265,6 +279,26 @@ def xt_selftest_fixed(kind, x):
     if rc != XT_OK:
         raise XtError(rc, "xt_selftest_fixed failed")
     return out
+
+
+def run_transport_noalloc(nx, ny, nz, v_max, t, L_cell, band_A, g_level, lo, up, lambda_A, f_lu,
+                          pops, S, spec, n_packets, seed=0, tau_min=1e-4, e_cut=1e-6, n_theta=20,
+                          n_phi=20, spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1,
+                          max_events=1_000_000, stream=None):
+    """One attenuation-mode pass that makes no device allocation (see
+    include/extrass.h).  pops, S and spec must be CUDA tensors."""
+    keep = [_f64(L_cell), _f64(g_level), _i32(lo), _i32(up), _f64(lambda_A), _f64(f_lu)]
+    a = NoallocTransport(nx, ny, nz, v_max, t, _ptr(keep[0]), band_A[0], band_A[1],
+                         int(len(keep[1])), int(len(keep[2])), _ptr(keep[1]), _ptr(keep[2]),
+                         _ptr(keep[3]), _ptr(keep[4]), _ptr(keep[5]), _ptr(pops), int(n_packets),
+                         int(seed), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
+                         int(spec_nbins), int(max_events), _ptr(S), _ptr(spec))
+    st = TransportStats()
+    err = C.create_string_buffer(512)
+    rc = lib().run_transport_noalloc(C.byref(a), stream, C.byref(st), err, 512)
+    if rc != XT_OK:
+        raise XtError(rc, err.value.decode())
+    return st.as_dict()
 
 
 # ---- convenience --------------------------------------------------------------

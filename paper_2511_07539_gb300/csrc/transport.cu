@@ -27,6 +27,8 @@
 // and traced again in the next round, until no packet is left.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <numeric>
 
 #include "fixexp.cuh"
@@ -1030,3 +1032,304 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   return XT_OK;
 }
 
+
+// ============================================================================
+// Transport without device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
+// being captured into a graph, drivers whose device memory is carved up once
+// at start-up by another framework's allocator, or embedders that must keep a
+// fixed device-memory budget.  run_transport_noalloc gives them one
+// attenuation-mode transport pass that allocates nothing: its working memory
+// (line table, packet quota, packet pool, escape list, counters, ledger) lives
+// in the file-scope array below, of fixed size, which every GPU that loads the
+// library holds until the process exits.  The kernels are the ones
+// run_transport launches; only where their scratch lives differs.
+// ============================================================================
+namespace xt {
+
+constexpr size_t kNaScratch = (size_t)XT_NOALLOC_SCRATCH_BYTES;
+constexpr int64_t kNaChunk = XT_NOALLOC_CHUNK;
+constexpr int kNaMaxCells = XT_NOALLOC_MAX_CELLS;
+constexpr int kNaMaxLines = XT_NOALLOC_MAX_LINES;
+constexpr int kNaSegs = 4096;
+
+// byte offsets of the parts of the scratch array (all 256-byte aligned)
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kNaLines = 0;                                               // 4 doubles per line
+constexpr size_t kNaNu = na_align(kNaLines + 32ull * kNaMaxLines);           // sorted nu
+constexpr size_t kNaSorted = na_align(kNaNu + 8ull * kNaMaxLines);           // caller -> sorted
+constexpr size_t kNaQoff = na_align(kNaSorted + 4ull * kNaMaxLines);         // [ncell+1]
+constexpr size_t kNaCellE = na_align(kNaQoff + 8ull * (kNaMaxCells + 1));    // Lc | Epk | Eph
+constexpr size_t kNaRtab = na_align(kNaCellE + 24ull * kNaMaxCells);         // [nx+ny+nz]
+constexpr size_t kNaCount = na_align(kNaRtab + 4ull * 3 * 1024);             // 8 counters
+constexpr size_t kNaLedger = na_align(kNaCount + 64);                        // [LG_N]
+constexpr size_t kNaSegN = na_align(kNaLedger + 8ull * LG_N);                // [kNaSegs + 1]
+constexpr size_t kNaLog = na_align(kNaSegN + 8ull * (kNaSegs + 1));          // 256 B dummy
+constexpr size_t kNaPoolF = na_align(kNaLog + 256);                          // NF doubles x chunk
+constexpr size_t kNaPoolI = na_align(kNaPoolF + 8ull * NF * kNaChunk);       // 9 ints x chunk
+constexpr size_t kNaPoolP = na_align(kNaPoolI + 4ull * 9 * kNaChunk);        // packet ids
+constexpr size_t kNaEnd = na_align(kNaPoolP + 8ull * kNaChunk);
+static_assert(kNaEnd <= kNaScratch, "no-allocation scratch layout exceeds its array");
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaScratch];
+static void* g_na_ptr[64];            // device address of g_na_scratch, per device
+
+// Device address of the scratch array on the current device.  Looked up once
+// per device with that device current (host code must not use the symbol's
+// name as an address).
+static int na_scratch(void** out, std::string& err) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    err = "run_transport_noalloc: no current CUDA device (or device index >= 64)";
+    return XT_ECUDA;
+  }
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess || !p) {
+      err = std::string("run_transport_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+      return XT_ECUDA;
+    }
+    g_na_ptr[dev] = p;
+  }
+  *out = g_na_ptr[dev];
+  return XT_OK;
+}
+
+// Estimators of one row from descending-frequency order to the caller's line
+// order, and from net photons to photons divided by f_corr (in place; the row
+// is staged in shared memory).
+__global__ void k_na_finish(double* __restrict__ S, const double* __restrict__ pops,
+                            const double* __restrict__ lines, const int* __restrict__ sorted_of,
+                            int nline, int nlev) {
+  extern __shared__ double srow[];
+  double* row = S + (int64_t)blockIdx.x * nline;
+  const double* pc = pops + (int64_t)blockIdx.x * nlev;
+  for (int s = threadIdx.x; s < nline; s += blockDim.x) srow[s] = row[s];
+  __syncthreads();
+  for (int l = threadIdx.x; l < nline; l += blockDim.x) {
+    const int s = sorted_of[l];
+    const double v = srow[s];
+    double out = 0.0;
+    if (v != 0.0) {
+      const double* L = lines + 4 * (int64_t)s;
+      const int64_t lu = __double_as_longlong(L[3]);
+      const double nl = pc[(int)(lu & 0xFFFFFFFF)], nu = pc[(int)(lu >> 32)];
+      out = v * nl / (nl - L[2] * nu);
+    }
+    row[l] = out;
+  }
+}
+
+// host staging, fixed size (no heap allocation on this path)
+static double h_na_L[kNaMaxCells], h_na_cellE[3 * kNaMaxCells];
+static int64_t h_na_q[kNaMaxCells + 1];
+static double h_na_frac[kNaMaxCells];
+static int h_na_ord[kNaMaxCells > kNaMaxLines ? kNaMaxCells : kNaMaxLines];
+static double h_na_lam[kNaMaxLines], h_na_f[kNaMaxLines], h_na_nu[kNaMaxLines];
+static int h_na_lo[kNaMaxLines], h_na_up[kNaMaxLines], h_na_sorted[kNaMaxLines];
+static double h_na_g[1 << 16];
+static double h_na_lines[4 * kNaMaxLines], h_na_nus[kNaMaxLines];
+static int h_na_rtab[3 * 1024];
+
+}  // namespace xt
+
+extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_stream,
+                                     xt_transport_stats* out, char* errbuf, size_t errlen) {
+  using namespace xt;
+  std::string err;
+  auto bad = [&](int code, const std::string& m) {
+    if (errbuf && errlen) { std::snprintf(errbuf, errlen, "%s", m.c_str()); }
+    return code;
+  };
+  if (!a) return bad(XT_EINVAL, "run_transport_noalloc: null argument");
+  const int64_t ncell = (int64_t)a->nx * a->ny * a->nz;
+  if (a->nx < 1 || a->ny < 1 || a->nz < 1 || a->nx > 1024 || a->ny > 1024 || a->nz > 1024)
+    return bad(XT_EINVAL, "run_transport_noalloc: nx, ny, nz must be in 1..1024");
+  if (ncell > kNaMaxCells)
+    return bad(XT_EINVAL, "run_transport_noalloc: " + std::to_string(ncell) + " cells exceed the maximum " +
+                              std::to_string(kNaMaxCells));
+  if (a->nline < 1 || a->nline > kNaMaxLines)
+    return bad(XT_EINVAL, "run_transport_noalloc: nline must be in 1.." + std::to_string(kNaMaxLines));
+  if (a->nlev < 2 || a->nlev > (1 << 16))
+    return bad(XT_EINVAL, "run_transport_noalloc: nlev must be in 2..65536");
+  if (!a->L_cell || !a->g_level || !a->lo || !a->up || !a->lambda_A || !a->f_lu || !a->pops || !a->S || !a->spec)
+    return bad(XT_EINVAL, "run_transport_noalloc: every array argument is required");
+  if (!is_device_ptr(a->pops) || !is_device_ptr(a->S) || !is_device_ptr(a->spec))
+    return bad(XT_EINVAL, "run_transport_noalloc: pops, S and spec must be device memory");
+  if (a->n_packets < 0 || !(a->v_max > 0) || !(a->t > 0) || !(a->band_hi_A > a->band_lo_A) || !(a->band_lo_A > 0))
+    return bad(XT_EINVAL, "run_transport_noalloc: n_packets >= 0, v_max > 0, t > 0, 0 < band_lo_A < band_hi_A");
+  if (a->n_theta < 1 || a->n_phi < 1 || a->spec_nbins < 1 || !(a->spec_lam0_A > 0) || !(a->spec_dlog > 0) ||
+      !(a->tau_min > 0) || !(a->e_cut >= 0) || a->max_events < 1)
+    return bad(XT_EINVAL, "run_transport_noalloc: spectrum grid, tau_min, e_cut or max_events");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  void* base = nullptr;
+  if (int rc = na_scratch(&base, err)) return bad(rc, err);
+  unsigned char* B = (unsigned char*)base;
+  const int nl = a->nline, nlev = a->nlev;
+#define NA_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bad(XT_ECUDA, std::string("run_transport_noalloc: ") + #call + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+  // ---- inputs to host staging (the caller's arrays may be host or device memory)
+  NA_CUDA(cudaMemcpyAsync(h_na_L, a->L_cell, ncell * sizeof(double), cudaMemcpyDefault, st));
+  NA_CUDA(cudaMemcpyAsync(h_na_g, a->g_level, nlev * sizeof(double), cudaMemcpyDefault, st));
+  NA_CUDA(cudaMemcpyAsync(h_na_lo, a->lo, nl * sizeof(int), cudaMemcpyDefault, st));
+  NA_CUDA(cudaMemcpyAsync(h_na_up, a->up, nl * sizeof(int), cudaMemcpyDefault, st));
+  NA_CUDA(cudaMemcpyAsync(h_na_lam, a->lambda_A, nl * sizeof(double), cudaMemcpyDefault, st));
+  NA_CUDA(cudaMemcpyAsync(h_na_f, a->f_lu, nl * sizeof(double), cudaMemcpyDefault, st));
+  NA_CUDA(cudaStreamSynchronize(st));
+  for (int l = 0; l < nl; ++l) {
+    if (h_na_lo[l] < 0 || h_na_up[l] >= nlev || h_na_lo[l] >= h_na_up[l] || !(h_na_lam[l] > 0) || !(h_na_f[l] > 0))
+      return bad(XT_EINVAL, "run_transport_noalloc: line " + std::to_string(l) + " needs 0 <= lo < up < nlev, lambda > 0, f > 0");
+    h_na_nu[l] = kC / (h_na_lam[l] * 1e-8);
+  }
+  for (int64_t k = 0; k < ncell; ++k)
+    if (!(h_na_L[k] >= 0.0) || !std::isfinite(h_na_L[k]))
+      return bad(XT_EINVAL, "run_transport_noalloc: L_cell must be finite and >= 0");
+  // ---- line table in descending frequency (ties: ascending caller index)
+  for (int l = 0; l < nl; ++l) h_na_ord[l] = l;
+  std::sort(h_na_ord, h_na_ord + nl, [](int x, int y) {
+    return h_na_nu[x] > h_na_nu[y] || (h_na_nu[x] == h_na_nu[y] && x < y);
+  });
+  const double pie2mc = kPi * kE * kE / (kMe * kC);
+  for (int s = 0; s < nl; ++s) {
+    const int l = h_na_ord[s];
+    h_na_sorted[l] = s;
+    h_na_nus[s] = h_na_nu[l];
+    h_na_lines[4 * s] = h_na_nu[l];
+    h_na_lines[4 * s + 1] = pie2mc * h_na_f[l] * (h_na_lam[l] * 1e-8) * a->t;
+    h_na_lines[4 * s + 2] = h_na_g[h_na_lo[l]] / h_na_g[h_na_up[l]];
+    const int64_t lu = (int64_t)(uint32_t)h_na_lo[l] | ((int64_t)h_na_up[l] << 32);
+    std::memcpy(&h_na_lines[4 * s + 3], &lu, sizeof(lu));
+  }
+  // ---- packet quota by largest remainder, packet energies
+  double tot = 0.0;
+  for (int64_t k = 0; k < ncell; ++k) tot += h_na_L[k];
+  int64_t used = 0;
+  for (int64_t k = 0; k < ncell; ++k) {
+    const double q = tot > 0.0 ? ((double)a->n_packets * h_na_L[k]) / tot : 0.0;
+    const double fl = std::floor(q);
+    h_na_q[k + 1] = (int64_t)fl;
+    h_na_frac[k] = q - fl;
+    used += (int64_t)fl;
+    h_na_ord[k] = (int)k;
+  }
+  const int64_t extra = std::min<int64_t>(a->n_packets - used, ncell);
+  if (extra > 0) {
+    std::partial_sort(h_na_ord, h_na_ord + extra, h_na_ord + ncell, [](int x, int y) {
+      return h_na_frac[x] > h_na_frac[y] || (h_na_frac[x] == h_na_frac[y] && x < y);
+    });
+    for (int64_t k = 0; k < extra; ++k) h_na_q[h_na_ord[k] + 1] += 1;
+  }
+  h_na_q[0] = 0;
+  for (int64_t k = 0; k < ncell; ++k) {
+    const int64_t nq = h_na_q[k + 1];
+    h_na_cellE[k] = h_na_L[k];
+    h_na_cellE[ncell + k] = nq > 0 ? h_na_L[k] / (double)nq : 0.0;
+    h_na_cellE[2 * ncell + k] = h_na_cellE[ncell + k] / kH;
+    h_na_q[k + 1] += h_na_q[k];
+  }
+  for (int x = 0; x < a->nx; ++x) h_na_rtab[x] = x;
+  for (int y = 0; y < a->ny; ++y) h_na_rtab[a->nx + y] = y * a->nx;
+  for (int z = 0; z < a->nz; ++z) h_na_rtab[a->nx + a->ny + z] = z * a->nx * a->ny;
+  // ---- staged tables into the scratch array; outputs and counters cleared
+  NA_CUDA(cudaMemcpyAsync(B + kNaLines, h_na_lines, 32ull * nl, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(B + kNaNu, h_na_nus, 8ull * nl, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(B + kNaSorted, h_na_sorted, 4ull * nl, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(B + kNaQoff, h_na_q, 8ull * (ncell + 1), cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(B + kNaCellE, h_na_cellE, 24ull * ncell, cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemcpyAsync(B + kNaRtab, h_na_rtab, 4ull * (a->nx + a->ny + a->nz), cudaMemcpyHostToDevice, st));
+  NA_CUDA(cudaMemsetAsync(B + kNaLedger, 0, 8ull * LG_N, st));
+  NA_CUDA(cudaMemsetAsync(B + kNaSegN, 0, 8ull * (kNaSegs + 1), st));
+  const size_t Sb = (size_t)ncell * nl * sizeof(double);
+  const int views = a->n_theta * a->n_phi;
+  NA_CUDA(cudaMemsetAsync(a->S, 0, Sb, st));
+  NA_CUDA(cudaMemsetAsync(a->spec, 0, (size_t)views * a->spec_nbins * sizeof(double), st));
+  // ---- the same kernels as run_transport, with their scratch in the array
+  Geometry G;
+  G.nx = a->nx; G.ny = a->ny; G.nz = a->nz; G.bx = a->nx; G.by = a->ny; G.bz = a->nz; G.sx = 1; G.sy = 1;
+  G.ncell = ncell; G.R = a->v_max * a->t;
+  G.dx = 2.0 * G.R / a->nx; G.dy = 2.0 * G.R / a->ny; G.dz = 2.0 * G.R / a->nz;
+  G.ct = kC * a->t; G.inv_ct = 1.0 / G.ct;
+  unsigned long long* counters = (unsigned long long*)(B + kNaCount);
+  double* ledger = (double*)(B + kNaLedger);
+  int* I = (int*)(B + kNaPoolI);
+  Pool P;
+  P.cap = kNaChunk; P.f = (double*)(B + kNaPoolF);
+  P.cell = I; P.cursor = I + kNaChunk; P.events = I + 2 * kNaChunk; P.ndraw = I + 3 * kNaChunk;
+  P.inter = I + 4 * kNaChunk; P.pid = (int64_t*)(B + kNaPoolP);
+  int* esc = I + 5 * kNaChunk;
+  double* cellE = (double*)(B + kNaCellE);
+  EmitArgs ea{};
+  ea.g = G; ea.qoff = (const int64_t*)(B + kNaQoff); ea.Lc = cellE; ea.Epk = cellE + ncell;
+  ea.Eph = cellE + 2 * ncell; ea.cdf = nullptr; ea.sorted_of = (const int*)(B + kNaSorted);
+  ea.nu_tab = (const double*)(B + kNaNu); ea.nline = nl; ea.emission = XT_EMIT_BAND; ea.seed = a->seed;
+  ea.nu_lo = kC / (a->band_hi_A * 1e-8); ea.nu_hi = kC / (a->band_lo_A * 1e-8); ea.e_cut = a->e_cut;
+  ea.pool = P; ea.ledger = ledger; ea.records = nullptr; ea.rec_base = 0;
+  fixtrig_tables(&ea.trig);
+  TraceArgs ta{};
+  ta.g = G; ta.lines = (const double2*)(B + kNaLines); ta.nline = nl; ta.nlev = nlev; ta.pops = a->pops;
+  ta.S = a->S; ta.pool = P; ta.list = nullptr; ta.counter = counters; ta.esc = esc; ta.n_esc = counters + 1;
+  ta.out = nullptr; ta.n_out = counters + 2; ta.rounds = 0; ta.seed = a->seed; ta.tau_min = a->tau_min;
+  ta.ct = G.ct; ta.inv_ct = G.inv_ct; ta.max_events = a->max_events; ta.ledger = ledger;
+  ta.records = nullptr; ta.rec_base = 0;
+  fixexp_tables(&ta.fx);
+  ta.trig = ea.trig;
+  ta.rtab = (const int*)(B + kNaRtab);
+  ta.slotlog = (int64_t*)(B + kNaLog); ta.seg_n = (int64_t*)(B + kNaSegN); ta.seg_len = 0;
+  ta.log_overflow = (unsigned long long*)(B + kNaSegN + 8ull * kNaSegs);
+  EscArgs xa{};
+  xa.pool = P; xa.esc = esc; xa.spec = a->spec; xa.n_theta = a->n_theta; xa.n_phi = a->n_phi;
+  xa.nbins = a->spec_nbins; xa.lam0 = a->spec_lam0_A; xa.log1p_dlog = std::log1p(a->spec_dlog);
+  xa.ledger = ledger; xa.records = nullptr; xa.rec_base = 0;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
+  const int grid_max = (int)std::min<int64_t>((int64_t)sm_count() * std::max(occ, 1), kNaSegs);
+  int kernels = 0;
+  for (int64_t off = 0; off < a->n_packets; off += kNaChunk) {
+    const int64_t n = std::min(kNaChunk, a->n_packets - off);
+    ea.p_begin = off;
+    ea.n = n;
+    k_emit<<<blocks_for(n, 256, 16), 256, 0, st>>>(ea);
+    NA_CUDA(cudaGetLastError());
+    NA_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), st));
+    ta.n_list = n;
+    k_trace<XT_MODE_ATTEN><<<(int)std::min<int64_t>(grid_max, (n + 255) / 256), 256, 0, st>>>(ta);
+    NA_CUDA(cudaGetLastError());
+    unsigned long long cnt[3];
+    NA_CUDA(cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
+    kernels += 2;
+    if (cnt[1] > 0) {
+      xa.n_esc = (int64_t)cnt[1];
+      k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, st>>>(xa);
+      NA_CUDA(cudaGetLastError());
+      ++kernels;
+    }
+  }
+  // ---- estimators to the caller's line order, divided by f_corr
+  const size_t smem = (size_t)nl * sizeof(double);
+  NA_CUDA(cudaFuncSetAttribute(k_na_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_na_finish<<<(unsigned)ncell, 256, smem, st>>>(a->S, a->pops, (const double*)(B + kNaLines),
+                                                  (const int*)(B + kNaSorted), nl, nlev);
+  NA_CUDA(cudaGetLastError());
+  ++kernels;
+  double led[LG_N];
+  NA_CUDA(cudaMemcpyAsync(led, ledger, sizeof(led), cudaMemcpyDeviceToHost, st));
+  NA_CUDA(cudaStreamSynchronize(st));
+#undef NA_CUDA
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    double* o = &out->emitted_N;
+    for (int k = 0; k < LG_N; ++k) o[k] = led[k];
+    out->rounds = 1;
+    out->kernels = kernels;
+  }
+  if (led[LG_GUARD] > 0) return bad(XT_ETIMEOUT, "run_transport_noalloc: packets hit max_events");
+  return XT_OK;
+}
