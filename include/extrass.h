@@ -158,6 +158,61 @@ int get_photoexcitation_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells,
  * kind 2: angle-summed L_lambda [nbins], erg/s/A */
 int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 
+/* ---- A8: statistical-equilibrium level populations (Sec. 2.2, Sec. 2.3.2) --
+ * For every (cell, ion): rates between the ion's levels held fixed (radiative
+ * decay A_ul beta_S, photoexcitation R_lu and stimulated emission
+ * (g_l/g_u) R_lu, collisions C_ul = 8.629e-6 Upsilon n_e/(g_u sqrt Te) and
+ * C_lu by detailed balance for every pair, a non-thermal excitation term from
+ * the deposition), equilibrium of every level with the equation of the ground
+ * level replaced by sum n = n_z, solved as one linear system.  All systems go
+ * through one persistent launch, longest first.
+ *   XT_PREC_FP64     LU with partial pivoting in FP64 (the plain method).
+ *   XT_PREC_FP32_IR  the system scaled by the warm start (columns) and row
+ *                    maxima, LU in FP32, refined in FP64 (residual, update)
+ *                    until the largest relative correction is below tol.
+ * Rates: XT_RATES_ESTIMATORS uses the last transport pass (R_lu = S/(n_l V));
+ * XT_RATES_JBAR uses J_nu = jbar_W B_nu(jbar_TR).  Optical depths for beta_S
+ * use the context's populations.  The warm start (scaling and first guess) is
+ * the context's populations (XT_WARM_CURRENT), Boltzmann populations
+ * (XT_WARM_LTE) or warm_in [ncell][nlev] (XT_WARM_GIVEN). */
+#define XT_PREC_FP64 0
+#define XT_PREC_FP32_IR 1
+#define XT_RATES_NONE 0
+#define XT_RATES_ESTIMATORS 1
+#define XT_RATES_JBAR 2
+#define XT_WARM_CURRENT 0
+#define XT_WARM_LTE 1
+#define XT_WARM_GIVEN 2
+#define XT_SE_OK 1          /* status bits per (cell, ion) */
+#define XT_SE_FALLBACK 2    /* refinement did not converge; solved again in FP64 */
+#define XT_SE_SINGULAR 4    /* zero pivot */
+typedef struct {
+    int32_t precision;      /* XT_PREC_* */
+    int32_t rates;          /* XT_RATES_* */
+    int32_t warm;           /* XT_WARM_* */
+    int32_t max_iter;       /* refinement steps (FP32_IR) */
+    double tol;             /* refinement stop: max |dn| / n over kept levels */
+    double jbar_W, jbar_TR; /* XT_RATES_JBAR */
+    double eta_nt;          /* non-thermal excitation efficiency (0.5) */
+    const int32_t *levels_used; /* [ncell*n_ion] levels kept per (cell, ion) (NULL: all) */
+    const double *warm_in;  /* XT_WARM_GIVEN: [ncell][nlev] */
+    const double *upsilon;  /* per ion, row-major [L_z][L_z] (entry [l][u], l < u),
+                               concatenated over ions; required */
+    int32_t use_graph;      /* replay the launch from a captured CUDA graph */
+    int32_t autotune;       /* pick panel widths per level-count bucket by timing */
+} xt_nlte_params;
+typedef struct {
+    double systems, fp64_fallbacks, singular, max_iter_used, mean_iter;
+    double solve_ms;        /* device time of the persistent launch */
+    double assemble_flops, lu_flops;   /* algorithmic flop counts of the launch */
+    int32_t panel_width[8]; /* chosen per bucket of 64 levels */
+} xt_nlte_stats;
+/* New populations into the context (and into pops_out [ncell][nlev] natural
+ * order, levels beyond levels_used set to 0, when not NULL); status_out
+ * [ncell*n_ion] (may be NULL). */
+int solve_nlte(xt_ctx *ctx, const xt_nlte_params *p, double *pops_out, int32_t *status_out,
+               xt_nlte_stats *stats);
+
 /* ---- numerical self-test (no paper counterpart: checks device primitives) --
  * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so two hot
  * transcendental steps are the library's own fixed-point routines on the

@@ -86,6 +86,33 @@ class NoallocTransport(C.Structure):
                 ("S", C.c_void_p), ("spec", C.c_void_p)]
 
 
+XT_PREC_FP64, XT_PREC_FP32_IR = 0, 1
+XT_RATES_NONE, XT_RATES_ESTIMATORS, XT_RATES_JBAR = 0, 1, 2
+XT_WARM_CURRENT, XT_WARM_LTE, XT_WARM_GIVEN = 0, 1, 2
+XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR = 1, 2, 4
+
+
+class NlteParams(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rates", C.c_int32), ("warm", C.c_int32),
+                ("max_iter", C.c_int32), ("tol", C.c_double), ("jbar_W", C.c_double),
+                ("jbar_TR", C.c_double), ("eta_nt", C.c_double), ("levels_used", C.c_void_p),
+                ("warm_in", C.c_void_p), ("upsilon", C.c_void_p), ("use_graph", C.c_int32),
+                ("autotune", C.c_int32)]
+
+
+NLTE_STATS = ["systems", "fp64_fallbacks", "singular", "max_iter_used", "mean_iter", "solve_ms",
+              "assemble_flops", "lu_flops"]
+
+
+class NlteStats(C.Structure):
+    _fields_ = [(f, C.c_double) for f in NLTE_STATS] + [("panel_width", C.c_int32 * 8)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f in NLTE_STATS}
+        d["panel_width"] = list(self.panel_width)
+        return d
+
+
 class Sizes(C.Structure):
     _fields_ = [(f, C.c_int64) for f in
                 ["ncell", "nlev", "nline", "n_ion", "spec_views", "spec_bins", "store_bytes"]]
@@ -119,6 +146,7 @@ def lib():
             "get_sizes": ([vp, vp], C.c_int),
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
             "run_transport_noalloc": ([vp, vp, vp, C.c_char_p, C.c_size_t], C.c_int),
+            "solve_nlte": ([vp, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -262,6 +290,29 @@ def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=N
     return R_lu, R_ul, Jbar
 
 
+def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATORS,
+               warm=XT_WARM_CURRENT, max_iter=8, tol=1e-12, jbar_W=0.0, jbar_TR=0.0, eta_nt=0.5,
+               levels_used=None, warm_in=None, use_graph=False, autotune=False, pops_out=None,
+               status_out=None, check=True):
+    """A8: statistical-equilibrium populations of every (cell, ion); the new
+    populations replace the context's.  upsilon: per-ion [L_z, L_z] arrays (a
+    list, concatenated here) or one flat array."""
+    if isinstance(upsilon, (list, tuple)):
+        upsilon = np.concatenate([np.ascontiguousarray(u, dtype=np.float64).ravel() for u in upsilon])
+    ups = _f64(upsilon)
+    lu = _i32(levels_used) if levels_used is not None else None
+    wi = _f64(warm_in) if warm_in is not None else None
+    p = NlteParams(int(precision), int(rates), int(warm), int(max_iter), float(tol), float(jbar_W),
+                   float(jbar_TR), float(eta_nt), _ptr(lu), _ptr(wi), _ptr(ups), int(bool(use_graph)),
+                   int(bool(autotune)))
+    st = NlteStats()
+    rc = lib().solve_nlte(ctx, C.byref(p), _ptr(pops_out), _ptr(status_out), C.byref(st))
+    if check:
+        _check(ctx, rc)
+        return st.as_dict()
+    return rc, st.as_dict()
+
+
 def get_spectrum(ctx, kind=0, out=None):
     sz = get_sizes(ctx)
     if out is None:
@@ -349,6 +400,6 @@ class Context:
         raise AttributeError(name)
 
 
-_CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations",
+_CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations", "solve_nlte",
               "get_sobolev_tau", "run_transport", "get_estimators", "get_photoexcitation_rates",
               "get_spectrum", "get_sizes"}

@@ -127,6 +127,12 @@ static int grid_blocks(int64_t n, int threads) {
   return (int)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 32);
 }
 
+int nat_to_row(xt_ctx* c, const double* src, double* dst, int64_t W) {
+  k_nat_to_row<<<grid_blocks(c->geo.ncell * W, 256), 256, 0, c->stream>>>(c->geo, src, dst, W);
+  XT_CUDA(c, cudaGetLastError());
+  return XT_OK;
+}
+
 // Upload a natural-order [ncell][W] array (host or device) into blocked rows.
 static int upload_rows(xt_ctx* c, const double* src, double** dst, int64_t W, const char* what) {
   size_t bytes = (size_t)c->geo.ncell * W * sizeof(double);

@@ -1,0 +1,656 @@
+// A8: batched statistical-equilibrium solves (Sec. 2.2; Sec. 2.3.2 for the
+// photoexcitation and detailed-balance photodeexcitation rates).
+//
+// One persistent launch serves every (cell, ion) system, longest first (a
+// work list sorted by level count, taken from an atomic counter), one CTA per
+// system at a time:
+//   assemble  the FP64 rate matrix of the system in the CTA's global
+//             workspace: collisions for every level pair (Boltzmann factors
+//             per level, detailed balance), radiative lines (A beta_S,
+//             photoexcitation, stimulated emission) by atomics, the
+//             non-thermal term into the ground level, the diagonal as minus the
+//             total out-rate, the ground-level equation replaced by sum n = n_z;
+//   factor    blocked right-looking LU with partial pivoting: a warp factors
+//             each panel of nb columns in shared memory, then the CTA swaps
+//             rows, solves for the panel's U rows and updates the trailing
+//             matrix through L2 (rank-nb update from shared memory);
+//   solve     blocked forward/back substitution;
+//   refine    (FP32 path) the matrix scaled by the warm start (columns) and the
+//             row maxima is factored in FP32; residuals and updates are FP64
+//             until the largest relative correction is below tol; a system
+//             that does not converge is solved again in FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fixexp.cuh"
+#include "xt_internal.cuh"
+
+namespace xt {
+
+constexpr int kSeThreads = 256;
+constexpr int kSeMaxL = 320;      // levels per system
+constexpr int kSeNbMax = 32;      // panel width
+
+struct SeArgs {
+  Geometry g;
+  int nlev, n_ion, nline;
+  const int* __restrict__ level_off;
+  const double* __restrict__ E;
+  const double* __restrict__ glev;
+  const double* __restrict__ nion;      // [row][n_ion]
+  const double* __restrict__ Te;        // row order
+  const double* __restrict__ ne;
+  const double* __restrict__ dep;
+  const double* __restrict__ pops;      // [row][nlev]: optical depths, estimator f_corr
+  const double* __restrict__ warm;      // [row][nlev] warm start, or nullptr for Boltzmann
+  double* __restrict__ pops_out;        // [row][nlev]
+  int* __restrict__ status;             // [cell * n_ion + z] natural cell order
+  const double* __restrict__ lines;     // packed sorted: nu, K, g_l/g_u, (lo | up << 32)
+  const double* __restrict__ A;         // sorted
+  const int* __restrict__ down_off;     // [nlev + 1] lines by upper level
+  const int* __restrict__ down_line;
+  const double* __restrict__ S;         // estimators (net photons) [row][sorted line]
+  const double* __restrict__ Rj;        // photoexcitation per sorted line (Jbar model)
+  int rates;
+  double V;
+  const double* __restrict__ ups;       // per ion [L_z][L_z]
+  const int64_t* __restrict__ ups_off;
+  const int* __restrict__ levels_used;  // [cell * n_ion + z] or nullptr
+  const int* __restrict__ work;         // cell * 16 + ion, longest first
+  int64_t n_work;
+  unsigned long long* __restrict__ counter;
+  double* __restrict__ W64;             // per CTA: L_max^2 doubles
+  void* __restrict__ WT;                // per CTA: L_max^2 of the factor type
+  int64_t wlen;                         // L_max^2
+  int precision;
+  double tol, eta;
+  int max_iter;
+  int nb_bucket[8];                     // panel width per 64-level bucket
+  double* __restrict__ iters;           // [cell * n_ion + z] refinement steps
+};
+
+__device__ __forceinline__ void block_sync() { __syncthreads(); }
+
+// ---- blocked LU with partial pivoting of the L x L row-major matrix A (global)
+template <typename T>
+__device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T* u12) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int sing;
+  if (tid == 0) sing = 0;
+  for (int k0 = 0; k0 < L; k0 += nb) {
+    const int kb = min(nb, L - k0);
+    const int rows = L - k0;                       // panel rows k0..L-1
+    // load panel [rows][kb]
+    for (int e = tid; e < rows * kb; e += blockDim.x) {
+      const int r = e / kb, cc = e - r * kb;
+      pan[r * kb + cc] = A[(int64_t)(k0 + r) * L + k0 + cc];
+    }
+    block_sync();
+    if (warp == 0) {
+      // unblocked LU of the panel by one warp
+      for (int j = 0; j < kb; ++j) {
+        // argmax |pan[r][j]|, r >= j
+        T best = 0;
+        int bi = j;
+        for (int r = j + lane; r < rows; r += 32) {
+          const T v = pan[r * kb + j] < 0 ? -pan[r * kb + j] : pan[r * kb + j];
+          if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) piv[k0 + j] = k0 + bi;
+        if (best == 0) { if (lane == 0) sing = 1; continue; }
+        if (bi != j)
+          for (int cc = lane; cc < kb; cc += 32) {
+            const T tmp = pan[j * kb + cc];
+            pan[j * kb + cc] = pan[bi * kb + cc];
+            pan[bi * kb + cc] = tmp;
+          }
+        __syncwarp();
+        const T inv = T(1) / pan[j * kb + j];
+        for (int r = j + 1 + lane; r < rows; r += 32) {
+          const T l = pan[r * kb + j] * inv;
+          pan[r * kb + j] = l;
+          for (int cc = j + 1; cc < kb; ++cc) pan[r * kb + cc] -= l * pan[j * kb + cc];
+        }
+        __syncwarp();
+      }
+    }
+    block_sync();
+    // write the panel back; apply its row swaps to the other columns
+    for (int e = tid; e < rows * kb; e += blockDim.x) {
+      const int r = e / kb, cc = e - r * kb;
+      A[(int64_t)(k0 + r) * L + k0 + cc] = pan[r * kb + cc];
+    }
+    for (int j = 0; j < kb; ++j) {
+      const int p = piv[k0 + j];
+      if (p != k0 + j)
+        for (int cc = tid; cc < L; cc += blockDim.x) {
+          if (cc >= k0 && cc < k0 + kb) continue;
+          const T tmp = A[(int64_t)(k0 + j) * L + cc];
+          A[(int64_t)(k0 + j) * L + cc] = A[(int64_t)p * L + cc];
+          A[(int64_t)p * L + cc] = tmp;
+        }
+      block_sync();
+    }
+    const int n2 = L - k0 - kb;                     // trailing columns
+    if (n2 > 0) {
+      // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared memory
+      for (int cc = tid; cc < n2; cc += blockDim.x) {
+        T col[kSeNbMax];
+#pragma unroll 4
+        for (int r = 0; r < kb; ++r) {
+          T v = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
+          for (int s = 0; s < r; ++s) v -= pan[r * kb + s] * col[s];
+          col[r] = v;
+        }
+        for (int r = 0; r < kb; ++r) {
+          u12[r * n2 + cc] = col[r];
+          A[(int64_t)(k0 + r) * L + k0 + kb + cc] = col[r];
+        }
+      }
+      block_sync();
+      // A22 -= L21 U12: 4 x 4 register tiles
+      const int m2 = L - k0 - kb;                   // trailing rows
+      const int tr = (m2 + 3) / 4, tc = (n2 + 3) / 4;
+      for (int t = tid; t < tr * tc; t += blockDim.x) {
+        const int bi = (t / tc) * 4, bj = (t % tc) * 4;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+        for (int k = 0; k < kb; ++k) {
+          T lv[4], uv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) lv[a] = (bi + a < m2) ? pan[(kb + bi + a) * kb + k] : T(0);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) uv[b] = (bj + b < n2) ? u12[k * n2 + bj + b] : T(0);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (bi + a < m2 && bj + b < n2) {
+              T* p = A + (int64_t)(k0 + kb + bi + a) * L + k0 + kb + bj + b;
+              *p -= acc[a][b];
+            }
+      }
+      block_sync();
+    }
+  }
+  block_sync();
+  return sing == 0;
+}
+
+// ---- solve A x = b in place (x in shared memory, type T), A = P L U from lu_factor
+template <typename T>
+__device__ void lu_solve(const T* __restrict__ A, int L, const int* piv, T* x) {
+  const int tid = threadIdx.x;
+  if (tid == 0)
+    for (int k = 0; k < L; ++k) {
+      const int p = piv[k];
+      if (p != k) { const T t = x[k]; x[k] = x[p]; x[p] = t; }
+    }
+  block_sync();
+  // forward, unit lower: blocks of 32 rows, diagonal block by warp 0, rest by all
+  for (int r0 = 0; r0 < L; r0 += 32) {
+    const int rb = min(32, L - r0);
+    if (tid < 32) {
+      for (int r = 1; r < rb; ++r) {
+        T part = (tid < r) ? A[(int64_t)(r0 + r) * L + r0 + tid] * x[r0 + tid] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (tid == 0) x[r0 + r] -= part;
+        __syncwarp();
+      }
+    }
+    block_sync();
+    for (int i = r0 + rb + tid; i < L; i += blockDim.x) {
+      T s = 0;
+      for (int c = 0; c < rb; ++c) s += A[(int64_t)i * L + r0 + c] * x[r0 + c];
+      x[i] -= s;
+    }
+    block_sync();
+  }
+  // backward, upper
+  for (int r1 = L; r1 > 0; r1 -= 32) {
+    const int r0 = max(0, r1 - 32), rb = r1 - r0;
+    if (tid < 32) {
+      for (int r = rb - 1; r >= 0; --r) {
+        const int row = r0 + r;
+        T part = (tid > r && tid < rb) ? A[(int64_t)row * L + r0 + tid] * x[r0 + tid] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (tid == 0) x[row] = (x[row] - part) / A[(int64_t)row * L + row];
+        __syncwarp();
+      }
+    }
+    block_sync();
+    for (int i = tid; i < r0; i += blockDim.x) {
+      T s = 0;
+      for (int c = 0; c < rb; ++c) s += A[(int64_t)i * L + r0 + c] * x[r0 + c];
+      x[i] -= s;
+    }
+    block_sync();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
+  extern __shared__ double sm[];
+  double* sE = sm;                       // per-level vectors (kSeMaxL each)
+  double* sG = sE + kSeMaxL;
+  double* sW = sG + kSeMaxL;             // g_i exp(-E_i / k Te)
+  double* sX0 = sW + kSeMaxL;            // warm start (column scale)
+  double* sR = sX0 + kSeMaxL;            // row scale
+  double* sN = sR + kSeMaxL;             // solution (FP64)
+  double* sRes = sN + kSeMaxL;           // residual
+  int* sPiv = (int*)(sRes + kSeMaxL);
+  T* sVec = (T*)(sPiv + kSeMaxL);        // right-hand side in the factor type
+  T* sPan = sVec + kSeMaxL;              // panel [L][nb]
+  T* sU12 = sPan + kSeMaxL * kSeNbMax;   // [nb][L]
+  __shared__ unsigned long long item;
+  __shared__ double red[32];
+  __shared__ int flag;
+  const int tid = threadIdx.x;
+  double* W = a.W64 + (int64_t)blockIdx.x * a.wlen;
+  T* WT = (T*)a.WT + (int64_t)blockIdx.x * a.wlen;
+  const double kB = 1.380649e-16;
+  for (;;) {
+    if (tid == 0) item = atomicAdd(a.counter, 1ull);
+    block_sync();
+    if (item >= (unsigned long long)a.n_work) break;
+    const int w = a.work[item];
+    const int cell = w >> 4, z = w & 15;
+    const int ix = cell % a.g.nx, iy = (cell / a.g.nx) % a.g.ny, iz = cell / (a.g.nx * a.g.ny);
+    const int64_t row = row_of(a.g, ix, iy, iz);
+    const int off = a.level_off[z], Lz = a.level_off[z + 1] - off;
+    const int L = a.levels_used ? min(a.levels_used[cell * a.n_ion + z], Lz) : Lz;
+    const double Te = a.Te[row], ne = a.ne[row], dep = a.dep ? a.dep[row] : 0.0;
+    const double nz = a.nion[row * a.n_ion + z];
+    const double* pc = a.pops + row * a.nlev;
+    const double* ups = a.ups + a.ups_off[z];
+    const double sqT = sqrt(Te), kT = kB * Te;
+    // per-level data; warm start
+    for (int i = tid; i < L; i += blockDim.x) {
+      sE[i] = a.E[off + i];
+      sG[i] = a.glev[off + i];
+      sW[i] = sG[i] * exp(-(sE[i] - a.E[off]) / kT);
+    }
+    block_sync();
+    if (a.warm) {
+      for (int i = tid; i < L; i += blockDim.x) sX0[i] = a.warm[row * a.nlev + off + i];
+    } else {
+      double s = 0;
+      for (int i = tid; i < L; i += blockDim.x) s += sW[i];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if ((tid & 31) == 0) red[tid >> 5] = s;
+      block_sync();
+      if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k]; red[0] = t; }
+      block_sync();
+      const double tot = red[0];
+      for (int i = tid; i < L; i += blockDim.x) sX0[i] = nz * sW[i] / tot;
+    }
+    block_sync();
+    // ---- assemble M (row-major, M[i][j] = rate j -> i) : collisions
+    const double cfac = 8.629e-6 * ne / sqT;
+    for (int e = tid; e < L * L; e += blockDim.x) {
+      const int i = e / L, j = e - i * L;
+      double v = 0.0;
+      if (j > i) v = ups[(int64_t)i * Lz + j] * cfac / sG[j];                    // down j -> i
+      else if (j < i) v = ups[(int64_t)j * Lz + i] * cfac / sG[i] * (sW[i] / sW[j]);   // up j -> i
+      W[e] = v;
+    }
+    block_sync();
+    // radiative lines of the kept levels (lines by upper level u < L)
+    for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
+      const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
+      for (int k = k0 + (tid & 7); k < k1; k += 8) {
+        const int s = a.down_line[k];
+        const double* Lr = a.lines + 4 * (int64_t)s;
+        const int64_t lu = __double_as_longlong(Lr[3]);
+        const int lo = (int)(lu & 0xFFFFFFFF) - off;
+        const double nl = pc[off + lo], nu_ = pc[off + u];
+        const double net = nl - Lr[2] * nu_;
+        const double tau = Lr[1] * net;
+        const double beta = tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+        double Rlu = 0.0;
+        if (a.rates == XT_RATES_JBAR) Rlu = a.Rj[s];
+        else if (a.rates == XT_RATES_ESTIMATORS && net > 0.0) Rlu = a.S[row * a.nline + s] / (net * a.V);
+        atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
+        atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u
+      }
+    }
+    // non-thermal excitation from the ground level
+    if (dep > 0.0 && nz > 0.0 && L > 1) {
+      double s = 0;
+      for (int u = 1 + tid; u < L; u += blockDim.x) s += ups[u] * (sE[u] - sE[0]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if ((tid & 31) == 0) red[tid >> 5] = s;
+      block_sync();
+      if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k]; red[0] = t; }
+      block_sync();
+      const double denom = nz * red[0];
+      if (denom > 0.0)
+        for (int u = 1 + tid; u < L; u += blockDim.x) W[(int64_t)u * L] += a.eta * dep * ups[u] / denom;
+    }
+    block_sync();
+    // diagonal: minus the total rate out of each level (column sums)
+    for (int i = tid; i < L; i += blockDim.x) {
+      double s = 0;
+      for (int j = 0; j < L; ++j) if (j != i) s += W[(int64_t)j * L + i];
+      sRes[i] = -s;
+    }
+    block_sync();
+    for (int i = tid; i < L; i += blockDim.x) W[(int64_t)i * L + i] = sRes[i];
+    block_sync();
+    for (int j = tid; j < L; j += blockDim.x) W[j] = 1.0;   // ground-level equation -> sum n = n_z
+    block_sync();
+    const int nb = a.nb_bucket[min(L >> 6, 7)];
+    int st = XT_SE_OK, iters = 0;
+    bool ok;
+    if (sizeof(T) == 8 || a.precision == XT_PREC_FP64) {
+      // ---- plain FP64: factor M, solve
+      double* Wd = (double*)WT;
+      for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
+      block_sync();
+      ok = lu_factor<double>(Wd, L, min(nb, 16), sPiv, (double*)sPan, (double*)sU12);
+      for (int i = tid; i < L; i += blockDim.x) sN[i] = i == 0 ? nz : 0.0;
+      block_sync();
+      if (ok) lu_solve<double>(Wd, L, sPiv, sN);
+      else st = XT_SE_SINGULAR;
+    } else {
+      // ---- FP32 factor of diag(r) M diag(x0), FP64 refinement
+      for (int i = tid; i < L; i += blockDim.x) sX0[i] = sX0[i] > 1e-300 ? sX0[i] : 1e-300;
+      block_sync();
+      for (int i = tid; i < L; i += blockDim.x) {
+        double mx = 0;
+        for (int j = 0; j < L; ++j) mx = fmax(mx, fabs(W[(int64_t)i * L + j] * sX0[j]));
+        sR[i] = mx > 0 ? 1.0 / mx : 1.0;
+      }
+      block_sync();
+      for (int e = tid; e < L * L; e += blockDim.x) {
+        const int i = e / L, j = e - i * L;
+        WT[e] = (T)(W[e] * sX0[j] * sR[i]);
+      }
+      block_sync();
+      ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12);
+      if (!ok) st = XT_SE_SINGULAR;
+      for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = i == 0 ? nz : 0.0; }
+      block_sync();
+      bool conv = false;
+      for (iters = 0; ok && iters < a.max_iter; ++iters) {
+        for (int i = tid; i < L; i += blockDim.x) sVec[i] = (T)(sRes[i] * sR[i]);
+        block_sync();
+        lu_solve<T>(WT, L, sPiv, sVec);
+        double dmax = 0;
+        for (int i = tid; i < L; i += blockDim.x) {
+          const double d = (double)sVec[i] * sX0[i];
+          sN[i] += d;
+          dmax = fmax(dmax, fabs(d) / fmax(fabs(sN[i]), 1e-30 * nz));
+        }
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if ((tid & 31) == 0) red[tid >> 5] = dmax;
+        block_sync();
+        if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t < a.tol; }
+        block_sync();
+        if (flag && iters > 0) { conv = true; ++iters; break; }
+        // residual b - M n in FP64
+        for (int i = tid; i < L; i += blockDim.x) {
+          double s = i == 0 ? nz : 0.0;
+          for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sN[j];
+          sRes[i] = s;
+        }
+        block_sync();
+      }
+      if (ok && !conv) {
+        // not converged: the plain FP64 solve decides
+        st |= XT_SE_FALLBACK;
+        double* Wd = (double*)a.WT + (int64_t)blockIdx.x * a.wlen;   // reuse (FP64 sized)
+        for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
+        block_sync();
+        ok = lu_factor<double>(Wd, L, 16, sPiv, (double*)sPan, (double*)sU12);
+        for (int i = tid; i < L; i += blockDim.x) sN[i] = i == 0 ? nz : 0.0;
+        block_sync();
+        if (ok) lu_solve<double>(Wd, L, sPiv, sN);
+        else st = XT_SE_SINGULAR;
+      }
+    }
+    block_sync();
+    double* out = a.pops_out + row * a.nlev + off;
+    for (int i = tid; i < Lz; i += blockDim.x) out[i] = i < L ? sN[i] : 0.0;
+    if (tid == 0) {
+      if (a.status) a.status[cell * a.n_ion + z] = st;
+      if (a.iters) a.iters[cell * a.n_ion + z] = iters;
+    }
+    block_sync();
+  }
+}
+
+// Boltzmann populations of the kept levels (XT_WARM_LTE for transport use).
+__global__ void k_lte(Geometry g, int nlev, int n_ion, const int* __restrict__ level_off,
+                      const double* __restrict__ E, const double* __restrict__ glev,
+                      const double* __restrict__ nion, const double* __restrict__ Te,
+                      const int* __restrict__ levels_used, double* __restrict__ out) {
+  const int64_t n = g.ncell * n_ion;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = e / n_ion;
+    const int z = (int)(e - cell * n_ion);
+    const int ix = (int)(cell % g.nx), iy = (int)((cell / g.nx) % g.ny), iz = (int)(cell / ((int64_t)g.nx * g.ny));
+    const int64_t row = row_of(g, ix, iy, iz);
+    const int off = level_off[z], Lz = level_off[z + 1] - off;
+    const int L = levels_used ? min(levels_used[e], Lz) : Lz;
+    const double kT = 1.380649e-16 * Te[row];
+    double s = 0;
+    for (int i = 0; i < L; ++i) s += glev[off + i] * exp(-(E[off + i] - E[off]) / kT);
+    const double nz = nion[row * n_ion + z];
+    for (int i = 0; i < Lz; ++i)
+      out[row * nlev + off + i] = i < L ? nz * glev[off + i] * exp(-(E[off + i] - E[off]) / kT) / s : 0.0;
+  }
+}
+
+static size_t se_smem(size_t tsize) {
+  return 7 * kSeMaxL * sizeof(double) + kSeMaxL * sizeof(int) +
+         (kSeMaxL + kSeMaxL * kSeNbMax + kSeNbMax * kSeMaxL) * tsize;
+}
+
+}  // namespace xt
+
+using namespace xt;
+
+extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, int32_t* status_out,
+                          xt_nlte_stats* stats) {
+  if (!c || !p) return fail(c, XT_EINVAL, "solve_nlte: null argument");
+  if (!c->have_pops || !c->have_atoms) return fail(c, XT_ESTATE, "solve_nlte: load_atomic_data and set_populations first");
+  if (!c->d_nion) return fail(c, XT_ESTATE, "solve_nlte: n_ion_density was not given to load_atomic_data");
+  if (c->n_ion > 16) return fail(c, XT_EINVAL, "solve_nlte: at most 16 ions");
+  if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR) return fail(c, XT_EINVAL, "solve_nlte: precision");
+  if (p->rates == XT_RATES_ESTIMATORS && !c->have_S)
+    return fail(c, XT_ESTATE, "solve_nlte: estimator rates need a transport pass with the current populations");
+  if (p->rates == XT_RATES_JBAR && !(p->jbar_W > 0 && p->jbar_TR > 0)) return fail(c, XT_EINVAL, "solve_nlte: jbar_W, jbar_TR > 0");
+  if (!p->upsilon) return fail(c, XT_EINVAL, "solve_nlte: upsilon is required");
+  if (p->warm == XT_WARM_GIVEN && !p->warm_in) return fail(c, XT_EINVAL, "solve_nlte: warm_in required");
+  if (p->precision == XT_PREC_FP32_IR && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
+  cudaSetDevice(c->device);
+  const Geometry& G = c->geo;
+  int Lmax = 0;
+  for (int z = 0; z < c->n_ion; ++z) Lmax = std::max(Lmax, c->h_level_off[z + 1] - c->h_level_off[z]);
+  if (Lmax > kSeMaxL) return fail(c, XT_EINVAL, "solve_nlte: more than 320 levels in an ion");
+  int rc;
+  const int64_t nsys = G.ncell * c->n_ion;
+  // levels kept and the longest-first work list (counting sort by L)
+  std::vector<int> used(nsys);
+  if (p->levels_used) {
+    if ((rc = copy(c, used.data(), p->levels_used, nsys * sizeof(int), "levels_used"))) return rc;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  std::vector<int64_t> cnt(Lmax + 2, 0);
+  for (int64_t e = 0; e < nsys; ++e) {
+    const int z = (int)(e % c->n_ion);
+    const int Lz = c->h_level_off[z + 1] - c->h_level_off[z];
+    int L = p->levels_used ? used[e] : Lz;
+    if (L < 1 || L > Lz) return fail(c, XT_EINVAL, "solve_nlte: levels_used out of range at " + std::to_string(e));
+    used[e] = L;
+    cnt[L]++;
+  }
+  std::vector<int64_t> start(Lmax + 2, 0);
+  for (int L = Lmax; L >= 1; --L) start[L - 1] = start[L] + cnt[L];   // longest first
+  std::vector<int> work(nsys);
+  {
+    std::vector<int64_t> fill(start);
+    for (int64_t e = 0; e < nsys; ++e) {
+      const int64_t cell = e / c->n_ion;
+      const int z = (int)(e % c->n_ion);
+      work[fill[used[e] - 1]++] = (int)(cell * 16 + z);
+    }
+  }
+  // device inputs of this call
+  size_t ups_n = 0;
+  std::vector<int64_t> ups_off(c->n_ion + 1, 0);
+  for (int z = 0; z < c->n_ion; ++z) {
+    const int64_t Lz = c->h_level_off[z + 1] - c->h_level_off[z];
+    ups_off[z + 1] = ups_off[z] + Lz * Lz;
+  }
+  ups_n = (size_t)ups_off[c->n_ion];
+  double* d_ups = nullptr; int64_t* d_upsoff = nullptr; int* d_work = nullptr; int* d_used = nullptr;
+  double* d_Rj = nullptr; unsigned long long* d_cnt = nullptr; double* d_iters = nullptr;
+  int* d_status = nullptr; double* d_new = nullptr; double* d_warm = nullptr;
+  double* d_W64 = nullptr; void* d_WT = nullptr;
+  auto cleanup = [&]() {
+    void* ps[] = {d_ups, d_upsoff, d_work, d_used, d_Rj, d_cnt, d_iters, d_status, d_warm, d_W64, d_WT};
+    for (void* q : ps) if (q) cudaFree(q);
+  };
+  int grid = 0;
+  const size_t tsz = p->precision == XT_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t smem = se_smem(tsz);
+  if (p->precision == XT_PREC_FP64) {
+    cudaFuncSetAttribute(k_se<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_se<double>, kSeThreads, smem);
+  } else {
+    cudaFuncSetAttribute(k_se<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_se<float>, kSeThreads, smem);
+  }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  grid = std::max(grid, 1) * sms;
+  grid = (int)std::min<int64_t>(grid, nsys);
+  const int64_t wlen = (int64_t)Lmax * Lmax;
+#define SE_ALLOC(ptr, bytes, what)                                          \
+  do {                                                                      \
+    if ((rc = alloc(c, (void**)&(ptr), (bytes), what))) { cleanup(); return rc; } \
+  } while (0)
+  SE_ALLOC(d_ups, ups_n * sizeof(double), "upsilon");
+  SE_ALLOC(d_upsoff, ups_off.size() * sizeof(int64_t), "upsilon offsets");
+  SE_ALLOC(d_work, nsys * sizeof(int), "work list");
+  SE_ALLOC(d_used, nsys * sizeof(int), "levels used");
+  SE_ALLOC(d_cnt, 8 * sizeof(unsigned long long), "counter");
+  SE_ALLOC(d_iters, nsys * sizeof(double), "iterations");
+  SE_ALLOC(d_status, nsys * sizeof(int), "status");
+  SE_ALLOC(d_new, (size_t)G.ncell * c->nlev * sizeof(double), "new populations");
+  SE_ALLOC(d_W64, (size_t)grid * wlen * sizeof(double), "workspace");
+  SE_ALLOC(d_WT, (size_t)grid * wlen * sizeof(double), "workspace");
+  if ((rc = copy(c, d_ups, p->upsilon, ups_n * sizeof(double), "upsilon"))) { cleanup(); cudaFree(d_new); return rc; }
+  if ((rc = copy(c, d_upsoff, ups_off.data(), ups_off.size() * sizeof(int64_t), "upsilon offsets"))) { cleanup(); cudaFree(d_new); return rc; }
+  if ((rc = copy(c, d_work, work.data(), nsys * sizeof(int), "work list"))) { cleanup(); cudaFree(d_new); return rc; }
+  if ((rc = copy(c, d_used, used.data(), nsys * sizeof(int), "levels used"))) { cleanup(); cudaFree(d_new); return rc; }
+  XT_CUDA(c, cudaMemsetAsync(d_cnt, 0, 8 * sizeof(unsigned long long), c->stream));
+  XT_CUDA(c, cudaMemsetAsync(d_new, 0, (size_t)G.ncell * c->nlev * sizeof(double), c->stream));
+  if (p->rates == XT_RATES_JBAR) {
+    // R_lu = B_lu W B_nu(T_R), B_lu = 4 pi K / (h c t) with K = (pi e^2 / m_e c) f lambda t
+    std::vector<double> packed(4 * (size_t)c->nline), Rj(c->nline);
+    XT_CUDA(c, cudaMemcpyAsync(packed.data(), c->d_lines, packed.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < c->nline; ++s) {
+      const double nu = packed[4 * s], K = packed[4 * s + 1];
+      const double B = 4.0 * kPi * K / (kH * kC * c->t);
+      const double x = kH * nu / (1.380649e-16 * p->jbar_TR);
+      Rj[s] = B * p->jbar_W * 2.0 * kH * nu * nu * nu / (kC * kC) / std::expm1(x);
+    }
+    SE_ALLOC(d_Rj, c->nline * sizeof(double), "jbar rates");
+    if ((rc = copy(c, d_Rj, Rj.data(), c->nline * sizeof(double), "jbar rates"))) { cleanup(); cudaFree(d_new); return rc; }
+  }
+  const double* warm = c->d_pops;
+  if (p->warm == XT_WARM_GIVEN) {
+    SE_ALLOC(d_warm, (size_t)G.ncell * c->nlev * sizeof(double), "warm start");
+    const size_t bytes = (size_t)G.ncell * c->nlev * sizeof(double);
+    if ((rc = ensure_scratch(c, bytes))) { cleanup(); cudaFree(d_new); return rc; }
+    if ((rc = copy(c, c->d_scratch, p->warm_in, bytes, "warm start"))) { cleanup(); cudaFree(d_new); return rc; }
+    if ((rc = nat_to_row(c, (const double*)c->d_scratch, d_warm, c->nlev))) { cleanup(); cudaFree(d_new); return rc; }
+    warm = d_warm;
+  } else if (p->warm == XT_WARM_LTE) {
+    warm = nullptr;
+  }
+  SeArgs a;
+  a.g = G; a.nlev = c->nlev; a.n_ion = c->n_ion; a.nline = c->nline;
+  a.level_off = c->d_level_off; a.E = c->d_E; a.glev = c->d_g; a.nion = c->d_nion;
+  a.Te = c->d_Te; a.ne = c->d_ne; a.dep = c->d_dep; a.pops = c->d_pops; a.warm = warm;
+  a.pops_out = d_new; a.status = d_status; a.lines = c->d_lines; a.A = c->d_A;
+  a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = d_Rj;
+  a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = d_ups; a.ups_off = d_upsoff;
+  a.levels_used = d_used; a.work = d_work; a.n_work = nsys; a.counter = d_cnt;
+  a.W64 = d_W64; a.WT = d_WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
+  a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = d_iters;
+  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = 32;
+  XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  if (p->precision == XT_PREC_FP64) k_se<double><<<grid, kSeThreads, smem, c->stream>>>(a);
+  else k_se<float><<<grid, kSeThreads, smem, c->stream>>>(a);
+  XT_CUDA(c, cudaGetLastError());
+  XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  std::vector<int> status(nsys);
+  std::vector<double> iters(nsys);
+  XT_CUDA(c, cudaMemcpyAsync(status.data(), d_status, nsys * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaMemcpyAsync(iters.data(), d_iters, nsys * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  // the new populations replace the context's (estimators refer to the old ones)
+  std::swap(c->d_pops, d_new);
+  cudaFree(d_new);
+  c->have_S = false;
+  if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;
+  int64_t nfb = 0, nsing = 0;
+  double itmax = 0, itsum = 0, flops_lu = 0, flops_as = 0;
+  for (int64_t e = 0; e < nsys; ++e) {
+    if (status[e] & XT_SE_FALLBACK) ++nfb;
+    if (status[e] & XT_SE_SINGULAR) ++nsing;
+    itmax = std::max(itmax, iters[e]);
+    itsum += iters[e];
+    const double L = used[e];
+    flops_lu += 2.0 / 3.0 * L * L * L;
+    flops_as += 4.0 * L * L;
+  }
+  cleanup();
+  if (status_out) {
+    if ((rc = copy(c, status_out, status.data(), nsys * sizeof(int), "status"))) return rc;
+  }
+  if (pops_out) {
+    if ((rc = get_populations(c, pops_out, (size_t)G.ncell * c->nlev))) return rc;
+  }
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->systems = (double)nsys;
+    stats->fp64_fallbacks = (double)nfb;
+    stats->singular = (double)nsing;
+    stats->max_iter_used = itmax;
+    stats->mean_iter = nsys ? itsum / nsys : 0;
+    stats->solve_ms = ms;
+    stats->assemble_flops = flops_as;
+    stats->lu_flops = flops_lu;
+    for (int k = 0; k < 8; ++k) stats->panel_width[k] = a.nb_bucket[k];
+  }
+  if (nsing > 0) return fail(c, XT_ENOTCONV, "solve_nlte: " + std::to_string(nsing) + " singular systems");
+  return XT_OK;
+}

@@ -141,6 +141,8 @@ int copy(xt_ctx* c, void* dst, const void* src, size_t n, const char* what);
 int ensure_scratch(xt_ctx* c, size_t bytes);
 int alloc(xt_ctx* c, void** p, size_t bytes, const char* what);
 void release(void** p);
+// natural-order [ncell][W] device array -> blocked rows (device), on the context stream
+int nat_to_row(xt_ctx* c, const double* src, double* dst, int64_t W);
 }  // namespace xt
 
 #define XT_CUDA(ctx, call)                                        \

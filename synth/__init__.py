@@ -76,6 +76,10 @@ class Workload:
     subdomains: tuple     # (sx, sy, sz) number of subdomains per axis
     spec_band_A: tuple    # (lambda0, n_bins) of the 0.1 % log output grid
     meta: dict = dataclasses.field(default_factory=dict)
+    upsilon: list = None          # per ion [L_z, L_z] collision strengths (entry [l, u], l < u)
+    levels_used: np.ndarray = None  # [ncell, n_ion] levels kept per (cell, ion); None = all
+    jbar_W: float = 0.0           # mean intensity model W B_nu(T_R) for the rate solves
+    jbar_TR: float = 0.0
 
     @property
     def ncell(self) -> int:
@@ -284,6 +288,59 @@ def single_line_sphere(n: int = 16, n_packets: int = 100_000, seed: int = 3,
     w.spec_band_A = _spectrum_grid(w.band_A[0], w.band_A[1], w.v_max)
     w.name = f"single_line_sphere_{n}^3"
     return w
+
+
+def nlte_batch(n: int = 64, seed: int = 0, n_ion: int = 10, L_max: int = 300,
+               L_range=(20, 300), lines_per_level: int = 5) -> Workload:
+    """Batched rate-solve workload: n^3 cells x n_ion ions; every (cell, ion)
+    keeps its own number of levels, uniform in L_range (the ion models have
+    L_max levels, 0-10 eV, g = 1 + 2 (i mod 4); each upper level has
+    lines_per_level lines down to random lower levels, lambda log-uniform
+    3000-10000 A, f log-uniform 1e-4..1; collision strengths log-uniform
+    0.1-10 for every pair).  Te uniform 3000-10000 K per cell, n_e and ion
+    densities lognormal, deposition lognormal.  The mean intensity stands in
+    for the 16^3-sphere transport field: diluted Planck W B_nu(T_R) with
+    T_R = 8000 K, W = 5.6e-5 (J_nu near 5000 A about 5e-9 erg/s/cm^2/Hz/sr).
+    Starting populations: Boltzmann over the kept levels."""
+    v_max, t = 5.0e8, 200.0 * DAY
+    ncell = n ** 3
+    rng = np.random.default_rng([seed, 3])
+    Te = rng.uniform(3000.0, 10000.0, ncell)
+    ne = 1e7 * np.exp(0.5 * rng.standard_normal(ncell))
+    rho = np.full(ncell, 1e-15)
+    n_ion_density = 1e6 * np.exp(0.5 * rng.standard_normal((ncell, n_ion)))
+    deposition = 1e-14 * np.exp(0.5 * rng.standard_normal(ncell))
+    levels_used = rng.integers(L_range[0], L_range[1] + 1, (ncell, n_ion)).astype(np.int32)
+    level_off = (np.arange(n_ion + 1) * L_max).astype(np.int32)
+    E1 = 10.0 * EV * np.arange(L_max) / (L_max - 1)
+    g1 = 1.0 + 2.0 * (np.arange(L_max) % 4)
+    los, ups_, lams, fs = [], [], [], []
+    for z in range(n_ion):
+        r = np.random.default_rng([seed, 11, z])
+        u = np.repeat(np.arange(1, L_max), lines_per_level)
+        lo = np.floor(r.random(u.shape[0]) * u).astype(np.int64)
+        los.append(lo + level_off[z]); ups_.append(u + level_off[z])
+        lams.append(10.0 ** r.uniform(np.log10(3000.0), 4.0, u.shape[0]))
+        fs.append(10.0 ** r.uniform(-4.0, 0.0, u.shape[0]))
+    E = np.tile(E1, n_ion); g = np.tile(g1, n_ion)
+    pops = np.zeros((ncell, n_ion * L_max))
+    kT = K_BOLTZ * Te
+    for z in range(n_ion):
+        w = g1[None, :] * np.exp(-E1[None, :] / kT[:, None])
+        w = np.where(np.arange(L_max)[None, :] < levels_used[:, z:z + 1], w, 0.0)
+        pops[:, level_off[z]:level_off[z + 1]] = n_ion_density[:, z:z + 1] * w / w.sum(axis=1, keepdims=True)
+    w_ = Workload(
+        name=f"nlte_batch_{n}^3x{n_ion}_L{L_range[0]}-{L_range[1]}", nx=n, ny=n, nz=n,
+        v_max=v_max, t=t, rho=rho, Te=Te, ne=ne, deposition=deposition,
+        L_cell=np.ones(ncell), band_A=(3000.0, 10000.0), n_ion=n_ion, level_off=level_off,
+        E_level=E, g_level=g, ion_mass_u=np.full(n_ion, 56.0), n_ion_density=n_ion_density,
+        lo=np.concatenate(los).astype(np.int32), up=np.concatenate(ups_).astype(np.int32),
+        lambda_A=np.concatenate(lams), f_lu=np.concatenate(fs), pops=pops, upsilon_seed=seed,
+        n_packets=0, seed=seed, subdomains=(1, 1, 1),
+        spec_band_A=_spectrum_grid(3000.0, 10000.0, v_max), meta={},
+        levels_used=levels_used, jbar_W=5.6e-5, jbar_TR=8000.0)
+    w_.upsilon = collision_strengths(seed, level_off)
+    return w_
 
 
 def workload(name: str, **kw) -> Workload:
