@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
   __shared__ int flag;
   const int tid = threadIdx.x;
   double* W = a.W64 + (int64_t)blockIdx.x * a.wlen;
-  T* WT = (T*)a.WT + (int64_t)blockIdx.x * a.wlen;
+  // each CTA owns L_max^2 doubles of WT, used as T (factor) or double (fallback)
+  T* WT = (T*)((double*)a.WT + (int64_t)blockIdx.x * a.wlen);
   const double kB = 1.380649e-16;
   for (;;) {
     if (tid == 0) item = atomicAdd(a.counter, 1ull);
@@ -505,15 +506,16 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     used[e] = L;
     cnt[L]++;
   }
+  // bucket of L starts after every longer bucket: start[L] = sum_{L' > L} cnt[L']
   std::vector<int64_t> start(Lmax + 2, 0);
-  for (int L = Lmax; L >= 1; --L) start[L - 1] = start[L] + cnt[L];   // longest first
+  for (int L = Lmax - 1; L >= 1; --L) start[L] = start[L + 1] + cnt[L + 1];
   std::vector<int> work(nsys);
   {
     std::vector<int64_t> fill(start);
     for (int64_t e = 0; e < nsys; ++e) {
       const int64_t cell = e / c->n_ion;
       const int z = (int)(e % c->n_ion);
-      work[fill[used[e] - 1]++] = (int)(cell * 16 + z);
+      work[fill[used[e]]++] = (int)(cell * 16 + z);
     }
   }
   // device inputs of this call
