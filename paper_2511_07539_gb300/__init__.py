@@ -291,7 +291,7 @@ def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=N
 
 
 def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATORS,
-               warm=XT_WARM_CURRENT, max_iter=8, tol=1e-12, jbar_W=0.0, jbar_TR=0.0, eta_nt=0.5,
+               warm=XT_WARM_CURRENT, max_iter=8, tol=1e-10, jbar_W=0.0, jbar_TR=0.0, eta_nt=0.5,
                levels_used=None, warm_in=None, use_graph=False, autotune=False, pops_out=None,
                status_out=None, check=True):
     """A8: statistical-equilibrium populations of every (cell, ion); the new

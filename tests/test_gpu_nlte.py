@@ -1,7 +1,8 @@
 """A8 batched statistical-equilibrium solves on the GPU vs the FP64 oracle
-(LAPACK), through the C ABI (needs a GPU).  Bars: plain FP64 LU relative
-1e-10; FP32 LU with FP64 refinement relative 1e-6 (the stated target; the
-refinement stops at 1e-12)."""
+(LAPACK), through the C ABI (needs a GPU).  Bars on every level with
+n_i >= 1e-30 n_z: plain FP64 LU relative 1e-10; FP32 LU with FP64 refinement
+relative 1e-6 (the stated target; with the refinement stop at 1e-10 the
+worst level is also required below 1e-8)."""
 import numpy as np
 import pytest
 
@@ -65,7 +66,7 @@ def test_batch_uneven_levels_vs_oracle(xt, precision, tol):
     assert st["systems"] == 270 and st["singular"] == 0
     if precision == 1:
         assert st["fp64_fallbacks"] == 0 and st["max_iter_used"] <= 8
-        assert worst < 1e-10
+        assert worst < 1e-8
 
 
 def test_lte_warm_start_and_full_levels(xt):
