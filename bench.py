@@ -154,6 +154,57 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def nlte_bench(local, stream_ptr):
+    """A8 on the batched rate-solve workload (64^3 cells x 10 ions, 20-300
+    levels each): FP32 LU + FP64 refinement for all 2.6e6 systems; the plain
+    FP64 LU on the 32^3 sub-batch (1/8 of the systems), scaled by the flop
+    count; the mixed result's deviation from the FP64 one on that sub-batch."""
+    import paper_2511_07539_gb300 as xt
+    import synth
+    out = {}
+    w = synth.nlte_batch(n=64)
+    kw = dict(rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_CURRENT, jbar_W=w.jbar_W,
+              jbar_TR=w.jbar_TR, levels_used=w.levels_used)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, autotune=True, use_graph=True, **kw)
+    best = None
+    for _ in range(3):
+        xt.set_populations(ctx.h, w.pops)
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, use_graph=True, **kw)
+        best = st if best is None or st["solve_ms"] < best["solve_ms"] else best
+    out["mixed"] = {"systems": best["systems"], "solve_ms": best["solve_ms"],
+                    "lu_tflops": best["lu_flops"] / (best["solve_ms"] * 1e-3) / 1e12,
+                    "fp64_fallbacks": best["fp64_fallbacks"], "mean_refinements": best["mean_iter"],
+                    "max_refinements": best["max_iter_used"], "panel_width": best["panel_width"]}
+    ctx.close()
+    del w
+    ws = synth.nlte_batch(n=32)
+    kws = dict(rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_CURRENT, jbar_W=ws.jbar_W,
+               jbar_TR=ws.jbar_TR, levels_used=ws.levels_used)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(ws)
+    p64 = np.zeros((ws.ncell, ws.nlev))
+    st64 = xt.solve_nlte(ctx.h, ws.upsilon, precision=xt.XT_PREC_FP64, pops_out=p64, **kws)
+    xt.set_populations(ctx.h, ws.pops)
+    p32 = np.zeros_like(p64)
+    st32 = xt.solve_nlte(ctx.h, ws.upsilon, precision=xt.XT_PREC_FP32_IR, pops_out=p32,
+                         autotune=True, **kws)
+    ctx.close()
+    nz = np.repeat(ws.n_ion_density, np.diff(ws.level_off), axis=1)
+    sig = p64 >= 1e-30 * nz
+    err = float(np.max(np.abs(p32[sig] / p64[sig] - 1)))
+    scale = best["lu_flops"] / st64["lu_flops"]
+    out["fp64_subbatch"] = {"systems": st64["systems"], "solve_ms": st64["solve_ms"],
+                            "lu_tflops": st64["lu_flops"] / (st64["solve_ms"] * 1e-3) / 1e12,
+                            "full_batch_ms_scaled": st64["solve_ms"] * scale,
+                            "scaling": "by LU flop count of the full batch"}
+    out["mixed_subbatch_ms"] = st32["solve_ms"]
+    out["max_rel_dev_mixed_vs_fp64"] = err
+    out["speedup_vs_fp64"] = st64["solve_ms"] * scale / best["solve_ms"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +215,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="onion", choices=["onion", "onion-small", "sphere"])
+    ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
     ap.add_argument("--rounds-steps", type=int, default=1,
                     help="extra timed passes with subdomain rounds (0 to skip)")
     args = ap.parse_args()
@@ -298,11 +350,13 @@ def main():
         "subdomain_rounds": rounds,
         "gpu_launches": launches,
     }
+    ctx.close()
+    if rank == 0 and not args.no_nlte and args.workload == "onion":
+        line["nlte"] = nlte_bench(local, stream.cuda_stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -327,6 +327,14 @@ void xt_destroy(xt_ctx* c) {
   if (c->ev_side0) cudaEventDestroy(c->ev_side0);
   if (c->ev_side1) cudaEventDestroy(c->ev_side1);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  {
+    auto& s = c->se;
+    void** sp[] = {(void**)&s.ups, (void**)&s.upsoff, (void**)&s.work, (void**)&s.used, (void**)&s.cnt,
+                   (void**)&s.iters, (void**)&s.status, (void**)&s.pops_new, (void**)&s.W64,
+                   (void**)&s.WT, (void**)&s.Rj, (void**)&s.warm};
+    for (void** q : sp) release(q);
+    for (cudaGraphExec_t g : s.graphs) cudaGraphExecDestroy(g);
+  }
   if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }

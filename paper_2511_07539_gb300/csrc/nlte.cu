@@ -518,57 +518,61 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
       work[fill[used[e]]++] = (int)(cell * 16 + z);
     }
   }
-  // device inputs of this call
-  size_t ups_n = 0;
+  // buffers of the solve, kept in the context between calls
+  auto& B = c->se;
   std::vector<int64_t> ups_off(c->n_ion + 1, 0);
   for (int z = 0; z < c->n_ion; ++z) {
     const int64_t Lz = c->h_level_off[z + 1] - c->h_level_off[z];
     ups_off[z + 1] = ups_off[z] + Lz * Lz;
   }
-  ups_n = (size_t)ups_off[c->n_ion];
-  double* d_ups = nullptr; int64_t* d_upsoff = nullptr; int* d_work = nullptr; int* d_used = nullptr;
-  double* d_Rj = nullptr; unsigned long long* d_cnt = nullptr; double* d_iters = nullptr;
-  int* d_status = nullptr; double* d_new = nullptr; double* d_warm = nullptr;
-  double* d_W64 = nullptr; void* d_WT = nullptr;
-  auto cleanup = [&]() {
-    void* ps[] = {d_ups, d_upsoff, d_work, d_used, d_Rj, d_cnt, d_iters, d_status, d_warm, d_W64, d_WT};
-    for (void* q : ps) if (q) cudaFree(q);
-  };
-  int grid = 0;
-  const size_t tsz = p->precision == XT_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t ups_n = (size_t)ups_off[c->n_ion];
+  const int pi = p->precision == XT_PREC_FP64 ? 0 : 1;
+  const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
   const size_t smem = se_smem(tsz);
-  if (p->precision == XT_PREC_FP64) {
+  int per_sm = 0;
+  if (pi == 0) {
     cudaFuncSetAttribute(k_se<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_se<double>, kSeThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<double>, kSeThreads, smem);
   } else {
     cudaFuncSetAttribute(k_se<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid, k_se<float>, kSeThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float>, kSeThreads, smem);
   }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  grid = std::max(grid, 1) * sms;
-  grid = (int)std::min<int64_t>(grid, nsys);
+  const int grid = (int)std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, nsys);
   const int64_t wlen = (int64_t)Lmax * Lmax;
-#define SE_ALLOC(ptr, bytes, what)                                          \
-  do {                                                                      \
-    if ((rc = alloc(c, (void**)&(ptr), (bytes), what))) { cleanup(); return rc; } \
+  const size_t wbytes = (size_t)grid * wlen * sizeof(double);
+  const size_t pops_n = (size_t)G.ncell * c->nlev;
+#define SE_GROW(ptr, have, need, elt, what)                                           \
+  do {                                                                                \
+    if ((have) < (need)) {                                                            \
+      (have) = 0;                                                                     \
+      if ((rc = alloc(c, (void**)&(ptr), (size_t)(need) * (elt), what))) return rc;   \
+      (have) = (need);                                                                \
+    }                                                                                 \
   } while (0)
-  SE_ALLOC(d_ups, ups_n * sizeof(double), "upsilon");
-  SE_ALLOC(d_upsoff, ups_off.size() * sizeof(int64_t), "upsilon offsets");
-  SE_ALLOC(d_work, nsys * sizeof(int), "work list");
-  SE_ALLOC(d_used, nsys * sizeof(int), "levels used");
-  SE_ALLOC(d_cnt, 8 * sizeof(unsigned long long), "counter");
-  SE_ALLOC(d_iters, nsys * sizeof(double), "iterations");
-  SE_ALLOC(d_status, nsys * sizeof(int), "status");
-  SE_ALLOC(d_new, (size_t)G.ncell * c->nlev * sizeof(double), "new populations");
-  SE_ALLOC(d_W64, (size_t)grid * wlen * sizeof(double), "workspace");
-  SE_ALLOC(d_WT, (size_t)grid * wlen * sizeof(double), "workspace");
-  if ((rc = copy(c, d_ups, p->upsilon, ups_n * sizeof(double), "upsilon"))) { cleanup(); cudaFree(d_new); return rc; }
-  if ((rc = copy(c, d_upsoff, ups_off.data(), ups_off.size() * sizeof(int64_t), "upsilon offsets"))) { cleanup(); cudaFree(d_new); return rc; }
-  if ((rc = copy(c, d_work, work.data(), nsys * sizeof(int), "work list"))) { cleanup(); cudaFree(d_new); return rc; }
-  if ((rc = copy(c, d_used, used.data(), nsys * sizeof(int), "levels used"))) { cleanup(); cudaFree(d_new); return rc; }
-  XT_CUDA(c, cudaMemsetAsync(d_cnt, 0, 8 * sizeof(unsigned long long), c->stream));
-  XT_CUDA(c, cudaMemsetAsync(d_new, 0, (size_t)G.ncell * c->nlev * sizeof(double), c->stream));
+  SE_GROW(B.ups, B.ups_n, ups_n, sizeof(double), "upsilon");
+  if (!B.upsoff && (rc = alloc(c, (void**)&B.upsoff, 17 * sizeof(int64_t), "upsilon offsets"))) return rc;
+  if (B.nsys < nsys) {
+    B.nsys = 0;
+    if ((rc = alloc(c, (void**)&B.work, nsys * sizeof(int), "work list"))) return rc;
+    if ((rc = alloc(c, (void**)&B.used, nsys * sizeof(int), "levels used"))) return rc;
+    if ((rc = alloc(c, (void**)&B.iters, nsys * sizeof(double), "iterations"))) return rc;
+    if ((rc = alloc(c, (void**)&B.status, nsys * sizeof(int), "status"))) return rc;
+    B.nsys = nsys;
+  }
+  if (!B.cnt && (rc = alloc(c, (void**)&B.cnt, 8 * sizeof(unsigned long long), "counter"))) return rc;
+  SE_GROW(B.pops_new, B.pops_n, pops_n, sizeof(double), "new populations");
+  if (B.wbytes < wbytes) {
+    B.wbytes = 0;
+    if ((rc = alloc(c, (void**)&B.W64, wbytes, "workspace"))) return rc;
+    if ((rc = alloc(c, (void**)&B.WT, wbytes, "workspace"))) return rc;
+    B.wbytes = wbytes;
+  }
+  if ((rc = copy(c, B.ups, p->upsilon, ups_n * sizeof(double), "upsilon"))) return rc;
+  if ((rc = copy(c, B.upsoff, ups_off.data(), ups_off.size() * sizeof(int64_t), "upsilon offsets"))) return rc;
+  if ((rc = copy(c, B.work, work.data(), nsys * sizeof(int), "work list"))) return rc;
+  if ((rc = copy(c, B.used, used.data(), nsys * sizeof(int), "levels used"))) return rc;
   if (p->rates == XT_RATES_JBAR) {
     // R_lu = B_lu W B_nu(T_R), B_lu = 4 pi K / (h c t) with K = (pi e^2 / m_e c) f lambda t
     std::vector<double> packed(4 * (size_t)c->nline), Rj(c->nline);
@@ -576,50 +580,108 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     XT_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int s = 0; s < c->nline; ++s) {
       const double nu = packed[4 * s], K = packed[4 * s + 1];
-      const double B = 4.0 * kPi * K / (kH * kC * c->t);
+      const double Bl = 4.0 * kPi * K / (kH * kC * c->t);
       const double x = kH * nu / (1.380649e-16 * p->jbar_TR);
-      Rj[s] = B * p->jbar_W * 2.0 * kH * nu * nu * nu / (kC * kC) / std::expm1(x);
+      Rj[s] = Bl * p->jbar_W * 2.0 * kH * nu * nu * nu / (kC * kC) / std::expm1(x);
     }
-    SE_ALLOC(d_Rj, c->nline * sizeof(double), "jbar rates");
-    if ((rc = copy(c, d_Rj, Rj.data(), c->nline * sizeof(double), "jbar rates"))) { cleanup(); cudaFree(d_new); return rc; }
+    SE_GROW(B.Rj, B.Rj_n, c->nline, sizeof(double), "jbar rates");
+    if ((rc = copy(c, B.Rj, Rj.data(), c->nline * sizeof(double), "jbar rates"))) return rc;
   }
   const double* warm = c->d_pops;
   if (p->warm == XT_WARM_GIVEN) {
-    SE_ALLOC(d_warm, (size_t)G.ncell * c->nlev * sizeof(double), "warm start");
-    const size_t bytes = (size_t)G.ncell * c->nlev * sizeof(double);
-    if ((rc = ensure_scratch(c, bytes))) { cleanup(); cudaFree(d_new); return rc; }
-    if ((rc = copy(c, c->d_scratch, p->warm_in, bytes, "warm start"))) { cleanup(); cudaFree(d_new); return rc; }
-    if ((rc = nat_to_row(c, (const double*)c->d_scratch, d_warm, c->nlev))) { cleanup(); cudaFree(d_new); return rc; }
-    warm = d_warm;
+    SE_GROW(B.warm, B.warm_n, pops_n, sizeof(double), "warm start");
+    if ((rc = ensure_scratch(c, pops_n * sizeof(double)))) return rc;
+    if ((rc = copy(c, c->d_scratch, p->warm_in, pops_n * sizeof(double), "warm start"))) return rc;
+    if ((rc = nat_to_row(c, (const double*)c->d_scratch, B.warm, c->nlev))) return rc;
+    warm = B.warm;
   } else if (p->warm == XT_WARM_LTE) {
     warm = nullptr;
   }
   SeArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.g = G; a.nlev = c->nlev; a.n_ion = c->n_ion; a.nline = c->nline;
   a.level_off = c->d_level_off; a.E = c->d_E; a.glev = c->d_g; a.nion = c->d_nion;
   a.Te = c->d_Te; a.ne = c->d_ne; a.dep = c->d_dep; a.pops = c->d_pops; a.warm = warm;
-  a.pops_out = d_new; a.status = d_status; a.lines = c->d_lines; a.A = c->d_A;
-  a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = d_Rj;
-  a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = d_ups; a.ups_off = d_upsoff;
-  a.levels_used = d_used; a.work = d_work; a.n_work = nsys; a.counter = d_cnt;
-  a.W64 = d_W64; a.WT = d_WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
-  a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = d_iters;
-  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = 32;
+  a.pops_out = B.pops_new; a.status = B.status; a.lines = c->d_lines; a.A = c->d_A;
+  a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = B.Rj;
+  a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = B.ups; a.ups_off = B.upsoff;
+  a.levels_used = B.used; a.work = B.work; a.n_work = nsys; a.counter = B.cnt;
+  a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
+  a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
+  auto launch = [&](const SeArgs& args, int g_) {
+    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), c->stream);
+    if (pi == 0) k_se<double><<<g_, kSeThreads, smem, c->stream>>>(args);
+    else k_se<float><<<g_, kSeThreads, smem, c->stream>>>(args);
+  };
+  // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
+  if (p->autotune && !B.tuned[pi]) {
+    const int cand[3] = {8, 16, 32};
+    for (int b = 0; b < 8; ++b) {
+      // systems with L in [64 b, 64 b + 63] are contiguous in the longest-first list
+      int64_t lo = -1, hi = -1;
+      for (int L = std::min(64 * b + 63, Lmax); L >= std::max(1, 64 * b); --L)
+        if (cnt[L] > 0) { if (lo < 0 || start[L] < lo) lo = start[L]; hi = std::max(hi, start[L] + cnt[L]); }
+      if (lo < 0) continue;
+      const int64_t n = std::min<int64_t>(hi - lo, 2048);
+      float best = 1e30f;
+      for (int k = 0; k < 3; ++k) {
+        if (pi == 0 && cand[k] > 16) continue;
+        SeArgs t_ = a;
+        t_.work = B.work + lo;
+        t_.n_work = n;
+        for (int q = 0; q < 8; ++q) t_.nb_bucket[q] = cand[k];
+        launch(t_, (int)std::min<int64_t>(grid, n));       // warm
+        XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+        launch(t_, (int)std::min<int64_t>(grid, n));
+        XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+        XT_CUDA(c, cudaEventSynchronize(c->ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        if (ms < best) { best = ms; B.nb[pi][b] = cand[k]; }
+      }
+    }
+    B.tuned[pi] = true;
+  }
+  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = B.nb[pi][k];
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  if (p->precision == XT_PREC_FP64) k_se<double><<<grid, kSeThreads, smem, c->stream>>>(a);
-  else k_se<float><<<grid, kSeThreads, smem, c->stream>>>(a);
+  if (p->use_graph) {
+    // one captured launch per argument set, replayed on later calls
+    std::vector<unsigned char> key(sizeof(a) + 2 * sizeof(int));
+    std::memcpy(key.data(), &a, sizeof(a));
+    std::memcpy(key.data() + sizeof(a), &grid, sizeof(int));
+    std::memcpy(key.data() + sizeof(a) + sizeof(int), &pi, sizeof(int));
+    int gi = -1;
+    for (size_t k = 0; k < B.graph_keys.size(); ++k) if (B.graph_keys[k] == key) gi = (int)k;
+    if (gi < 0) {
+      cudaGraph_t graph;
+      XT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      launch(a, grid);
+      XT_CUDA(c, cudaStreamEndCapture(c->stream, &graph));
+      cudaGraphExec_t ex;
+      XT_CUDA(c, cudaGraphInstantiate(&ex, graph, 0));
+      cudaGraphDestroy(graph);
+      if (B.graphs.size() >= 4) { cudaGraphExecDestroy(B.graphs.front()); B.graphs.erase(B.graphs.begin()); B.graph_keys.erase(B.graph_keys.begin()); }
+      B.graphs.push_back(ex);
+      B.graph_keys.push_back(key);
+      gi = (int)B.graphs.size() - 1;
+    }
+    XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+    XT_CUDA(c, cudaGraphLaunch(B.graphs[gi], c->stream));
+  } else {
+    launch(a, grid);
+  }
   XT_CUDA(c, cudaGetLastError());
   XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   std::vector<int> status(nsys);
   std::vector<double> iters(nsys);
-  XT_CUDA(c, cudaMemcpyAsync(status.data(), d_status, nsys * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  XT_CUDA(c, cudaMemcpyAsync(iters.data(), d_iters, nsys * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaMemcpyAsync(status.data(), B.status, nsys * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaMemcpyAsync(iters.data(), B.iters, nsys * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   float ms = 0;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  // the new populations replace the context's (estimators refer to the old ones)
-  std::swap(c->d_pops, d_new);
-  cudaFree(d_new);
+  // the new populations replace the context's (estimators refer to the old ones);
+  // the old buffer becomes the next call's output
+  std::swap(c->d_pops, B.pops_new);
   c->have_S = false;
   if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;
   int64_t nfb = 0, nsing = 0;
@@ -633,7 +695,6 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     flops_lu += 2.0 / 3.0 * L * L * L;
     flops_as += 4.0 * L * L;
   }
-  cleanup();
   if (status_out) {
     if ((rc = copy(c, status_out, status.data(), nsys * sizeof(int), "status"))) return rc;
   }

@@ -127,6 +127,23 @@ struct xt_ctx {
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  // statistical-equilibrium solve: buffers kept between calls, tuned panel
+  // widths per precision and 64-level bucket, captured launches
+  struct SeBufs {
+    double* ups = nullptr; size_t ups_n = 0;
+    int64_t* upsoff = nullptr;
+    int* work = nullptr; int* used = nullptr; int64_t nsys = 0;
+    unsigned long long* cnt = nullptr;
+    double* iters = nullptr; int* status = nullptr;
+    double* pops_new = nullptr; size_t pops_n = 0;
+    double* W64 = nullptr; double* WT = nullptr; size_t wbytes = 0;
+    double* Rj = nullptr; int Rj_n = 0;
+    double* warm = nullptr; size_t warm_n = 0;
+    int nb[2][8] = {{16, 16, 16, 16, 16, 16, 16, 16}, {32, 32, 32, 32, 32, 32, 32, 32}};
+    bool tuned[2] = {false, false};
+    std::vector<std::vector<unsigned char>> graph_keys;
+    std::vector<cudaGraphExec_t> graphs;
+  } se;
   cudaStream_t side = nullptr;       // second stream: store clear overlapping emission
   cudaEvent_t ev_side0 = nullptr, ev_side1 = nullptr;
   std::vector<cudaEvent_t> ev_pool;  // per-kernel timing events

@@ -325,10 +325,14 @@ def nlte_batch(n: int = 64, seed: int = 0, n_ion: int = 10, L_max: int = 300,
     E = np.tile(E1, n_ion); g = np.tile(g1, n_ion)
     pops = np.zeros((ncell, n_ion * L_max))
     kT = K_BOLTZ * Te
+    base = g1[None, :] * np.exp(-E1[None, :] / kT[:, None])      # same levels in every ion
+    csum = np.cumsum(base, axis=1)
     for z in range(n_ion):
-        w = g1[None, :] * np.exp(-E1[None, :] / kT[:, None])
-        w = np.where(np.arange(L_max)[None, :] < levels_used[:, z:z + 1], w, 0.0)
-        pops[:, level_off[z]:level_off[z + 1]] = n_ion_density[:, z:z + 1] * w / w.sum(axis=1, keepdims=True)
+        Lz = levels_used[:, z]
+        norm = n_ion_density[:, z] / csum[np.arange(ncell), Lz - 1]
+        blk = pops[:, level_off[z]:level_off[z + 1]]
+        np.multiply(base, norm[:, None], out=blk)
+        blk[np.arange(L_max)[None, :] >= Lz[:, None]] = 0.0
     w_ = Workload(
         name=f"nlte_batch_{n}^3x{n_ion}_L{L_range[0]}-{L_range[1]}", nx=n, ny=n, nz=n,
         v_max=v_max, t=t, rho=rho, Te=Te, ne=ne, deposition=deposition,

@@ -96,3 +96,22 @@ def test_rates_from_transport_estimators(xt):
     cells = act[::7]
     ref = _oracle_batch(w, cells, R_lu_lines=R_lu)
     _check(w, pops, ref, 1e-8)
+
+
+def test_graph_replay_and_autotune_match(xt):
+    """The captured-graph replay and the autotuned panel widths give the same
+    populations as a plain launch, on repeated calls."""
+    w = synth.nlte_batch(n=3, seed=4)
+    kw = dict(precision=1, rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_LTE, jbar_W=w.jbar_W,
+              jbar_TR=w.jbar_TR, levels_used=w.levels_used)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        base = np.zeros((w.ncell, w.nlev))
+        xt.solve_nlte(ctx.h, w.upsilon, pops_out=base, **kw)
+        for k in range(3):
+            xt.set_populations(ctx.h, w.pops)
+            out = np.zeros_like(base)
+            st = xt.solve_nlte(ctx.h, w.upsilon, pops_out=out, use_graph=True, autotune=True, **kw)
+            m = base > 0
+            assert np.max(np.abs(out[m] / base[m] - 1)) < 1e-9
+            assert all(nb in (8, 16, 32) for nb in st["panel_width"])
