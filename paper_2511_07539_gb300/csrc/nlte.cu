@@ -608,11 +608,12 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.levels_used = B.used; a.work = B.work; a.n_work = nsys; a.counter = B.cnt;
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
-  auto launch = [&](const SeArgs& args, int g_) {
-    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), c->stream);
-    if (pi == 0) k_se<double><<<g_, kSeThreads, smem, c->stream>>>(args);
-    else k_se<float><<<g_, kSeThreads, smem, c->stream>>>(args);
+  auto launch_on = [&](const SeArgs& args, int g_, cudaStream_t s_) {
+    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
+    if (pi == 0) k_se<double><<<g_, kSeThreads, smem, s_>>>(args);
+    else k_se<float><<<g_, kSeThreads, smem, s_>>>(args);
   };
+  auto launch = [&](const SeArgs& args, int g_) { launch_on(args, g_, c->stream); };
   // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
   if (p->autotune && !B.tuned[pi]) {
     const int cand[3] = {8, 16, 32};
@@ -653,10 +654,13 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     int gi = -1;
     for (size_t k = 0; k < B.graph_keys.size(); ++k) if (B.graph_keys[k] == key) gi = (int)k;
     if (gi < 0) {
+      // captured on the context's own stream (the caller's may be the legacy
+      // default stream, which cannot be captured); replayed on the caller's
       cudaGraph_t graph;
-      XT_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      launch(a, grid);
-      XT_CUDA(c, cudaStreamEndCapture(c->stream, &graph));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+      XT_CUDA(c, cudaStreamBeginCapture(c->side, cudaStreamCaptureModeThreadLocal));
+      launch_on(a, grid, c->side);
+      XT_CUDA(c, cudaStreamEndCapture(c->side, &graph));
       cudaGraphExec_t ex;
       XT_CUDA(c, cudaGraphInstantiate(&ex, graph, 0));
       cudaGraphDestroy(graph);
