@@ -183,6 +183,7 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 #define XT_WARM_CURRENT 0
 #define XT_WARM_LTE 1
 #define XT_WARM_GIVEN 2
+#define XT_WARM_SURROGATE 3 /* the population surrogate's prediction (see below) */
 #define XT_SE_OK 1          /* status bits per (cell, ion) */
 #define XT_SE_FALLBACK 2    /* refinement did not converge; solved again in FP64 */
 #define XT_SE_SINGULAR 4    /* zero pivot */
@@ -212,6 +213,41 @@ typedef struct {
  * [ncell*n_ion] (may be NULL). */
 int solve_nlte(xt_ctx *ctx, const xt_nlte_params *p, double *pops_out, int32_t *status_out,
                xt_nlte_stats *stats);
+
+/* ---- A9: population surrogate (no paper counterpart: it warm-starts A8) ----
+ * A multilayer perceptron predicts log10(n_i / n_z) / 10 of every level of a
+ * cell from log10 n_e, log10 Te, log10 of the deposition and, per ion, the mean
+ * log10 Jbar of its lines in 32 log-lambda bins (3 + 32 n_ion inputs, nlev
+ * outputs).  Hidden layers GELU (tanh form), linear output, masked mean squared
+ * error, Adam on FP32 master weights; every matrix product in BF16 on the
+ * tensor cores with FP32 accumulation.  Weights are one flat FP32 vector:
+ * W_1 [n_in][h], b_1, W_2, b_2, ..., W_out, b_out (W row-major [fan_in][fan_out]).
+ * A bad prediction costs only refinement steps: solve_nlte refines (or falls
+ * back to FP64) whatever the warm start. */
+int surrogate_init(xt_ctx *ctx, const int32_t *sizes, int32_t n_sizes, uint64_t seed);
+/* set != 0: load weights from flat; else copy them out.  n_cap in floats. */
+int surrogate_weights(xt_ctx *ctx, int32_t set, float *flat, size_t n_cap);
+/* One forward and backward pass on a batch: X [B][n_in], T and mask [B][n_out]
+ * (FP32, host or device); update != 0 applies one Adam step (lr).  Gradients of
+ * the flat parameter vector into grads_out (may be NULL), loss into loss_out. */
+int surrogate_train_step(xt_ctx *ctx, const float *X, const float *T, const float *mask, int64_t B,
+                         double lr, int32_t update, float *grads_out, double *loss_out);
+int surrogate_predict(xt_ctx *ctx, const float *X, int64_t B, float *Y);
+typedef struct {
+    int32_t epochs, batch;
+    double lr;
+    int32_t n_hidden, n_layers;   /* network made on first use: 3 x 256 */
+    uint64_t seed;
+    int32_t rates;                /* how the Jbar inputs are formed (XT_RATES_*) */
+    double jbar_W, jbar_TR;
+    const int32_t *levels_used;   /* [ncell*n_ion] or NULL */
+} xt_train_params;
+typedef struct {
+    double first_loss, last_loss, steps, samples, train_ms;
+} xt_train_stats;
+/* Train on every cell of the context: inputs from its grid and radiation
+ * field, targets its current populations (the result of solve_nlte). */
+int train_surrogate(xt_ctx *ctx, const xt_train_params *p, xt_train_stats *stats);
 
 /* ---- numerical self-test (no paper counterpart: checks device primitives) --
  * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so two hot

@@ -90,6 +90,21 @@ XT_PREC_FP64, XT_PREC_FP32_IR = 0, 1
 XT_RATES_NONE, XT_RATES_ESTIMATORS, XT_RATES_JBAR = 0, 1, 2
 XT_WARM_CURRENT, XT_WARM_LTE, XT_WARM_GIVEN = 0, 1, 2
 XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR = 1, 2, 4
+XT_WARM_SURROGATE = 3
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double),
+                ("n_hidden", C.c_int32), ("n_layers", C.c_int32), ("seed", C.c_uint64),
+                ("rates", C.c_int32), ("jbar_W", C.c_double), ("jbar_TR", C.c_double),
+                ("levels_used", C.c_void_p)]
+
+
+class TrainStats(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ["first_loss", "last_loss", "steps", "samples", "train_ms"]]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class NlteParams(C.Structure):
@@ -147,6 +162,11 @@ def lib():
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
             "run_transport_noalloc": ([vp, vp, vp, C.c_char_p, C.c_size_t], C.c_int),
             "solve_nlte": ([vp, vp, vp, vp, vp], C.c_int),
+            "surrogate_init": ([vp, vp, i32, C.c_uint64], C.c_int),
+            "surrogate_weights": ([vp, i32, vp, C.c_size_t], C.c_int),
+            "surrogate_train_step": ([vp, vp, vp, vp, i64, C.c_double, i32, vp, vp], C.c_int),
+            "surrogate_predict": ([vp, vp, i64, vp], C.c_int),
+            "train_surrogate": ([vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -311,6 +331,54 @@ def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATOR
         _check(ctx, rc)
         return st.as_dict()
     return rc, st.as_dict()
+
+
+def _f32(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def surrogate_init(ctx, sizes, seed=0):
+    s = np.ascontiguousarray(sizes, dtype=np.int32)
+    _check(ctx, lib().surrogate_init(ctx, _ptr(s), len(s), int(seed)))
+
+
+def surrogate_weights(ctx, flat=None, n=None):
+    """Set the flat FP32 weights (flat given) or return them (n floats)."""
+    if flat is not None:
+        f = _f32(flat)
+        _check(ctx, lib().surrogate_weights(ctx, 1, _ptr(f), int(f.size)))
+        return f
+    out = np.zeros(n, dtype=np.float32)
+    _check(ctx, lib().surrogate_weights(ctx, 0, _ptr(out), int(n)))
+    return out
+
+
+def surrogate_train_step(ctx, X, T, mask, lr=1e-3, update=True, n_param=None):
+    X, T, mask = _f32(X), _f32(T), _f32(mask)
+    grads = np.zeros(n_param, dtype=np.float32) if n_param else None
+    loss = C.c_double()
+    _check(ctx, lib().surrogate_train_step(ctx, _ptr(X), _ptr(T), _ptr(mask), int(X.shape[0]),
+                                           float(lr), int(bool(update)), _ptr(grads), C.byref(loss)))
+    return loss.value, grads
+
+
+def surrogate_predict(ctx, X, n_out):
+    X = _f32(X)
+    Y = np.zeros((X.shape[0], n_out), dtype=np.float32)
+    _check(ctx, lib().surrogate_predict(ctx, _ptr(X), int(X.shape[0]), _ptr(Y)))
+    return Y
+
+
+def train_surrogate(ctx, epochs=20, batch=256, lr=1e-3, n_hidden=256, n_layers=3, seed=0,
+                    rates=XT_RATES_JBAR, jbar_W=0.0, jbar_TR=0.0, levels_used=None):
+    lu = _i32(levels_used) if levels_used is not None else None
+    p = TrainParams(int(epochs), int(batch), float(lr), int(n_hidden), int(n_layers), int(seed),
+                    int(rates), float(jbar_W), float(jbar_TR), _ptr(lu))
+    st = TrainStats()
+    _check(ctx, lib().train_surrogate(ctx, C.byref(p), C.byref(st)))
+    return st.as_dict()
 
 
 def get_spectrum(ctx, kind=0, out=None):

@@ -330,12 +330,13 @@ void xt_destroy(xt_ctx* c) {
   {
     auto& s = c->se;
     void** sp[] = {(void**)&s.ups, (void**)&s.upsoff, (void**)&s.work, (void**)&s.used, (void**)&s.cnt,
-                   (void**)&s.iters, (void**)&s.status, (void**)&s.pops_new, (void**)&s.W64,
+                   (void**)&s.iters, (void**)&s.status, (void**)&s.pops_new, (void**)&s.W64, (void**)&s.used_nat,
                    (void**)&s.WT, (void**)&s.Rj, (void**)&s.warm};
     for (void** q : sp) release(q);
     for (cudaGraphExec_t g : s.graphs) cudaGraphExecDestroy(g);
   }
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->mlp) mlp_destroy(c->mlp);
   delete c;
 }
 

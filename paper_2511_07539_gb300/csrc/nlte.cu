@@ -483,6 +483,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (p->rates == XT_RATES_JBAR && !(p->jbar_W > 0 && p->jbar_TR > 0)) return fail(c, XT_EINVAL, "solve_nlte: jbar_W, jbar_TR > 0");
   if (!p->upsilon) return fail(c, XT_EINVAL, "solve_nlte: upsilon is required");
   if (p->warm == XT_WARM_GIVEN && !p->warm_in) return fail(c, XT_EINVAL, "solve_nlte: warm_in required");
+  if (p->warm < XT_WARM_CURRENT || p->warm > XT_WARM_SURROGATE) return fail(c, XT_EINVAL, "solve_nlte: warm");
   if (p->precision == XT_PREC_FP32_IR && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
   cudaSetDevice(c->device);
   const Geometry& G = c->geo;
@@ -573,6 +574,13 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if ((rc = copy(c, B.upsoff, ups_off.data(), ups_off.size() * sizeof(int64_t), "upsilon offsets"))) return rc;
   if ((rc = copy(c, B.work, work.data(), nsys * sizeof(int), "work list"))) return rc;
   if ((rc = copy(c, B.used, used.data(), nsys * sizeof(int), "levels used"))) return rc;
+  if (p->levels_used) {
+    if (!B.used_nat || B.used_nat_n < nsys) {
+      if ((rc = alloc(c, (void**)&B.used_nat, nsys * sizeof(int), "levels used"))) return rc;
+      B.used_nat_n = nsys;
+    }
+    if ((rc = copy(c, B.used_nat, p->levels_used, nsys * sizeof(int), "levels used"))) return rc;
+  }
   if (p->rates == XT_RATES_JBAR) {
     // R_lu = B_lu W B_nu(T_R), B_lu = 4 pi K / (h c t) with K = (pi e^2 / m_e c) f lambda t
     std::vector<double> packed(4 * (size_t)c->nline), Rj(c->nline);
@@ -596,6 +604,12 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     warm = B.warm;
   } else if (p->warm == XT_WARM_LTE) {
     warm = nullptr;
+  } else if (p->warm == XT_WARM_SURROGATE) {
+    SE_GROW(B.warm, B.warm_n, pops_n, sizeof(double), "warm start");
+    int* d_lu = nullptr;
+    if (p->levels_used) d_lu = B.used_nat;
+    if ((rc = surrogate_warm(c, p->rates, p->jbar_W, p->jbar_TR, d_lu, B.warm))) return rc;
+    warm = B.warm;
   }
   SeArgs a;
   std::memset(&a, 0, sizeof(a));

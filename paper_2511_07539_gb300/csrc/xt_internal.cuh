@@ -54,7 +54,10 @@ __host__ __device__ inline int64_t row_of(const Geometry& g, int ix, int iy, int
 
 }  // namespace xt
 
+struct xt_mlp;
+
 struct xt_ctx {
+  xt_mlp* mlp = nullptr;             // population surrogate (mlp.cu)
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -139,6 +142,7 @@ struct xt_ctx {
     double* W64 = nullptr; double* WT = nullptr; size_t wbytes = 0;
     double* Rj = nullptr; int Rj_n = 0;
     double* warm = nullptr; size_t warm_n = 0;
+    int* used_nat = nullptr; int64_t used_nat_n = 0;
     int nb[2][8] = {{16, 16, 16, 16, 16, 16, 16, 16}, {32, 32, 32, 32, 32, 32, 32, 32}};
     bool tuned[2] = {false, false};
     std::vector<std::vector<unsigned char>> graph_keys;
@@ -160,6 +164,11 @@ int alloc(xt_ctx* c, void** p, size_t bytes, const char* what);
 void release(void** p);
 // natural-order [ncell][W] device array -> blocked rows (device), on the context stream
 int nat_to_row(xt_ctx* c, const double* src, double* dst, int64_t W);
+void mlp_destroy(xt_mlp* n);
+// Surrogate warm start: populations [row][nlev] predicted for every cell
+// (levels beyond levels_used zero), into `out` (device).
+int surrogate_warm(xt_ctx* c, int rates, double jbar_W, double jbar_TR, const int* levels_used_dev,
+                   double* out);
 }  // namespace xt
 
 #define XT_CUDA(ctx, call)                                        \
