@@ -87,7 +87,8 @@ int get_populations(xt_ctx *ctx, double *pops, size_t n_cap);
 
 /* ---- A1: Sobolev optical depth and escape probability ------------------
  * tau_S, Eq. (tau_Sobolev) (App. A.1), and beta_S = (1 - e^-tau)/tau,
- * Eq. (beta_Sobolev), for cells [cell_begin, cell_begin + n_cells) x all
+ * Eq. (beta_Sobolev), taken as 1 for tau <= 0 (empty lower level or
+ * population inversion: no trapping), for cells [cell_begin, +n_cells) x all
  * lines, written [n_cells][nline] in the caller's line order.  beta may be
  * NULL. */
 int get_sobolev_tau(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *tau, double *beta);
@@ -171,7 +172,10 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
  *                    maxima, LU in FP32, refined in FP64 (residual, update)
  *                    until the largest relative correction is below tol.
  * Rates: XT_RATES_ESTIMATORS uses the last transport pass (R_lu = S/(n_l V));
- * XT_RATES_JBAR uses J_nu = jbar_W B_nu(jbar_TR).  Optical depths for beta_S
+ * XT_RATES_JBAR illuminates every line with the external field
+ * J_nu = jbar_W B_nu(jbar_TR), of which a Sobolev region absorbs the part
+ * beta_S: R_lu = beta_S B_lu J_nu (the 1 - e^-tau absorbed fraction that the
+ * Sec. 2.3.2 estimator counts).  Optical depths for beta_S
  * use the context's populations.  The warm start (scaling and first guess) is
  * the context's populations (XT_WARM_CURRENT), Boltzmann populations
  * (XT_WARM_LTE) or warm_in [ncell][nlev] (XT_WARM_GIVEN). */

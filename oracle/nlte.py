@@ -9,7 +9,10 @@ transfer held fixed; Sec. 2.3.2: photodeexcitation from detailed balance):
 
   rates i -> j (per atom, s^-1), P[i, j]:
     radiative decay     u -> l : A_ul beta_S(tau_ul)          (Eq. beta_Sobolev)
-    photoexcitation     l -> u : R_lu = B_lu Jbar             (or from the estimators)
+    photoexcitation     l -> u : R_lu from the estimators, or beta_S B_lu J_ext for a
+                                 given external field J_ext (reading: the part of an
+                                 outside field a Sobolev region absorbs, the quantity
+                                 the Sec. 2.3.2 estimator counts, 1 - e^-tau per photon)
     stimulated emission u -> l : R_ul = (g_l / g_u) R_lu
     collisions (every pair)    : C_ul = 8.629e-6 Upsilon n_e / (g_u sqrt(Te)),
                                  C_lu = C_ul (g_u / g_l) exp(-(E_u - E_l) / k Te)
@@ -44,10 +47,11 @@ def sobolev_tau(lam_cm, f_lu, g_l, g_u, n_l, n_u, t):
 
 
 def sobolev_beta(tau):
+    """Eq. (beta_Sobolev) for tau > 0; 1 for tau <= 0 (no trapping)."""
     tau = np.asarray(tau, dtype=np.float64)
     out = np.ones_like(tau)
-    nz = tau != 0
-    out[nz] = -np.expm1(-tau[nz]) / tau[nz]
+    pos = tau > 0
+    out[pos] = -np.expm1(-tau[pos]) / tau[pos]
     return out
 
 
@@ -73,7 +77,7 @@ def rate_matrix(E, g, lo, up, lam_A, f_lu, ups, Te, ne, n_z, dep, t, pops_beta,
     tau = sobolev_tau(lam, f_lu, gl, gu, pops_beta[lo], pops_beta[up], t)
     beta = sobolev_beta(tau)
     if R_lu is None:
-        R_lu = np.zeros_like(lam) if jbar is None else 4.0 * np.pi * PI_E2_MC * f_lu / (H_PLANCK * nu) * jbar(nu)
+        R_lu = np.zeros_like(lam) if jbar is None else beta * 4.0 * np.pi * PI_E2_MC * f_lu / (H_PLANCK * nu) * jbar(nu)
     R_ul = (gl / gu) * R_lu
     np.add.at(P, (up, lo), A * beta + R_ul)
     np.add.at(P, (lo, up), R_lu)
@@ -145,3 +149,4 @@ def system(w, c, z, pops_beta=None, R_lu_lines=None, eta=0.5):
                     float(w.ne[c]), n_z, float(w.deposition[c]), w.t, pb, R_lu=R, jbar=jbar,
                     eta=eta)
     return P, n_z, v
+

@@ -93,9 +93,11 @@ double xo_tau_sobolev(double A_ul, double g_l, double g_u, double lambda_cm,
     return pre * (-(g_l / g_u) * n_u) * t;
 }
 
-/* Eq. (beta_Sobolev): beta = (1 - e^-tau)/tau, with beta(0) = 1. */
+/* Eq. (beta_Sobolev): beta = (1 - e^-tau)/tau for tau > 0.  For tau <= 0
+ * (empty lower level, population inversion) the escape probability is taken
+ * as 1: nothing traps the line (the formula would grow like e^|tau|). */
 double xo_beta_sobolev(double tau) {
-    if (tau == 0.0) return 1.0;
+    if (tau <= 0.0) return 1.0;
     return -expm1(-tau) / tau;
 }
 

@@ -185,7 +185,7 @@ static int to_device(xt_ctx* c, const std::vector<T>& v, T** dst, const char* wh
 
 // ---- A1: tau_S, Eq. (tau_Sobolev), and beta_S, Eq. (beta_Sobolev) ----------
 __device__ __forceinline__ double beta_sobolev(double tau) {
-  return tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+  return tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
 }
 
 __global__ void k_tau_beta(Geometry g, LineTable L, const double* __restrict__ pops,

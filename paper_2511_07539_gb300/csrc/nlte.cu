@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
         const double nl = pc[off + lo], nu_ = pc[off + u];
         const double net = nl - Lr[2] * nu_;
         const double tau = Lr[1] * net;
-        const double beta = tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+        const double beta = tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
         double Rlu = 0.0;
-        if (a.rates == XT_RATES_JBAR) Rlu = a.Rj[s];
+        if (a.rates == XT_RATES_JBAR) Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
         else if (a.rates == XT_RATES_ESTIMATORS && net > 0.0) Rlu = a.S[row * a.nline + s] / (net * a.V);
         atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
         atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u

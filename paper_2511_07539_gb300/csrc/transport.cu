@@ -142,7 +142,7 @@ __device__ __forceinline__ void isotropic(const FixTrigTables& T, double umu, ui
 }
 
 __device__ __forceinline__ double sobolev_beta(double tau) {
-  return tau == 0.0 ? 1.0 : -expm1(-tau) / tau;
+  return tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
 }
 
 // Distance to the next wall along each axis and between walls, from r in cell idx.

@@ -91,3 +91,28 @@ def test_thin_lines_in_planck_field_give_boltzmann():
     n = nlte.solve_se(P, 1.0)
     boltz = g * np.exp(-E / (K * T))
     np.testing.assert_allclose(n, boltz / boltz.sum(), rtol=1e-10)
+
+
+
+def test_external_field_absorption_closed_form():
+    """Net photoexcitations per volume of an isotropic external field J_nu in a
+    homologous flow: every photon that crosses the resonance is absorbed with
+    probability 1 - e^-tau, and the resonance sweeps d nu / ds = nu / (c t), so
+    n_l R_lu - n_u R_ul = 4 pi J_nu (1 - e^-tau) / (h c t), whatever f_lu and
+    the populations (Sobolev geometry, Sec. 2.3.2 absorbed fraction)."""
+    E = np.array([0.0, 3e-12])
+    g = np.array([2.0, 4.0])
+    lo, up = np.array([0]), np.array([1])
+    ups = np.zeros((2, 2))
+    t = 100 * 86400.0
+    J = 3e-9
+    for f, nl, nu_ in ((1e-3, 1.0, 0.1), (0.5, 1e4, 7.0), (0.2, 1e8, 1e7)):
+        lam_A = np.array([6000.0])
+        pops = np.array([nl, nu_])
+        P = nlte.rate_matrix(E, g, lo, up, lam_A, np.array([f]), ups, 5000.0, 0.0, 1.0, 0.0, t,
+                             pops, jbar=lambda nu: np.full_like(nu, J))
+        tau = nlte.sobolev_tau(lam_A * 1e-8, f, 2.0, 4.0, nl, nu_, t)[0]
+        A = nlte.einstein_A(lam_A * 1e-8, 2.0, 4.0, f)[0]
+        net_up = nl * P[0, 1] - nu_ * (P[1, 0] - A * nlte.sobolev_beta(tau))
+        expect = 4 * np.pi * J * -np.expm1(-tau) / (nlte.H_PLANCK * nlte.C_LIGHT * t)
+        assert np.isclose(net_up, expect, rtol=1e-10), (f, nl, nu_, net_up, expect)

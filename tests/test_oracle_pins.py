@@ -36,6 +36,7 @@ def test_beta_sobolev_vs_mpmath():
         worst = max(worst, abs(got - float(exact)) / float(exact))
     assert worst < 5e-16
     assert L.xo_beta_sobolev(0.0) == 1.0
+    assert L.xo_beta_sobolev(-5.0) == 1.0 and L.xo_beta_sobolev(-1e4) == 1.0
     t = 1e-9
     assert abs(L.xo_beta_sobolev(t) - (1 - t / 2 + t * t / 6)) < 1e-16
     # large tau: beta -> 1/tau
