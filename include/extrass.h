@@ -191,6 +191,7 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 #define XT_SE_OK 1          /* status bits per (cell, ion) */
 #define XT_SE_FALLBACK 2    /* refinement did not converge; solved again in FP64 */
 #define XT_SE_SINGULAR 4    /* zero pivot */
+#define XT_SE_NOCONV 8      /* Newton steps ran out (populations: the last iterate) */
 typedef struct {
     int32_t precision;      /* XT_PREC_* */
     int32_t rates;          /* XT_RATES_* */
@@ -205,12 +206,25 @@ typedef struct {
                                concatenated over ions; required */
     int32_t use_graph;      /* replay the launch from a captured CUDA graph */
     int32_t autotune;       /* pick panel widths per level-count bucket by timing */
+    /* Newton-Raphson on the optical depths (Sec. 2.2): newton_max = 0 solves the
+     * linear system with beta_S from the context's populations; > 0 makes beta_S
+     * a function of the solution and takes up to newton_max steps from the warm
+     * start.  Each step factors the Jacobian (M plus every line's derivative of
+     * its net downward flow through beta_S) in the chosen precision, with an
+     * FP64 residual; step n += lam d, lam = min(1, newton_limit * min over
+     * d_i < 0 of n_i / -d_i); stop when max lam |d_i| / n_i <= newton_tol over
+     * levels with n_i >= 1e-30 n_z.  Estimator rates stay fixed per atom. */
+    int32_t newton_max;
+    double newton_tol;      /* 1e-6 */
+    double newton_limit;    /* 0.9 */
 } xt_nlte_params;
 typedef struct {
-    double systems, fp64_fallbacks, singular, max_iter_used, mean_iter;
+    double systems, fp64_fallbacks, singular, max_iter_used, mean_iter;  /* iterations:
+                               refinement steps, or Newton steps when newton_max > 0 */
     double solve_ms;        /* device time of the persistent launch */
     double assemble_flops, lu_flops;   /* algorithmic flop counts of the launch */
     int32_t panel_width[8]; /* chosen per bucket of 64 levels */
+    double not_converged;   /* systems with XT_SE_NOCONV */
 } xt_nlte_stats;
 /* New populations into the context (and into pops_out [ncell][nlev] natural
  * order, levels beyond levels_used set to 0, when not NULL); status_out
@@ -252,6 +266,43 @@ typedef struct {
 /* Train on every cell of the context: inputs from its grid and radiation
  * field, targets its current populations (the result of solve_nlte). */
 int train_surrogate(xt_ctx *ctx, const xt_train_params *p, xt_train_stats *stats);
+
+/* ---- A10: the coupled NLTE / transport loop -------------------------------
+ * Sec. 2 alternates the NLTE solver and the ray tracing; Sec. 2.2 solves the
+ * populations with the transport's photoexcitation rates held fixed; Sec.
+ * 2.3.2 forms those rates from the estimators.  One outer step: a transport
+ * pass (*transport, accumulate forced to 0) from the context's populations
+ * n_k, solve_nlte (*nlte, rates forced to XT_RATES_ESTIMATORS, warm start the
+ * current populations, so newton_max > 0 solves the optical depths with the
+ * populations), then n_{k+1} = n_k^(1-alpha) s_k^alpha (alpha = 1: s_k), and
+ * change = max |n_{k+1} - n_k| / n_k over levels with n >= floor n_z in either
+ * iterate.  Stops when change <= tol or after max_outer steps; the context
+ * keeps n_{k+1}.  Start populations: the context's (XT_WARM_CURRENT),
+ * Boltzmann (XT_WARM_LTE, levels_used of *nlte), start_in [ncell][nlev]
+ * natural order (XT_WARM_GIVEN), or the surrogate's prediction with its Jbar
+ * inputs from nlte->jbar_W, jbar_TR (XT_WARM_SURROGATE).  Synchronous; the
+ * transport keeps its seed every step, so a step is a deterministic map. */
+typedef struct {
+    const xt_transport_params *transport;
+    const xt_nlte_params *nlte;
+    int32_t start;          /* XT_WARM_* */
+    const double *start_in; /* XT_WARM_GIVEN */
+    double alpha;           /* 1 */
+    double tol;             /* 1e-3 */
+    double floor;           /* 1e-20 */
+    int32_t max_outer;
+} xt_coupled_params;
+typedef struct {
+    int32_t outer, converged;
+    double last_change;
+    double wall_ms;         /* host clock over the whole call, start included */
+    double start_ms;        /* start populations (surrogate inference, Boltzmann) */
+    double transport_ms, solve_ms, mix_ms;   /* device time summed over steps */
+    double newton_steps;    /* mean Newton steps per system, summed over steps */
+    double max_newton_steps, not_converged, fp64_fallbacks;
+    double change[64];      /* change after each of the first 64 steps */
+} xt_coupled_stats;
+int run_coupled(xt_ctx *ctx, const xt_coupled_params *p, xt_coupled_stats *stats);
 
 /* ---- numerical self-test (no paper counterpart: checks device primitives) --
  * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so two hot

@@ -150,3 +150,76 @@ def system(w, c, z, pops_beta=None, R_lu_lines=None, eta=0.5):
                     eta=eta)
     return P, n_z, v
 
+
+
+def sobolev_beta_deriv(tau):
+    """d beta_S / d tau = (tau e^-tau - (1 - e^-tau)) / tau^2 for tau > 0, with
+    the limit -1/2 as tau -> 0+; 0 for tau <= 0, where beta_S = 1."""
+    tau = np.asarray(tau, dtype=np.float64)
+    out = np.zeros_like(tau)
+    pos = tau > 1e-8
+    out[pos] = (tau[pos] * np.exp(-tau[pos]) + np.expm1(-tau[pos])) / tau[pos] ** 2
+    out[(tau > 0) & ~pos] = -0.5
+    return out
+
+
+def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=100, limit=0.9,
+              floor=1e-30, eta=0.5):
+    """Populations of ion z in cell c that are consistent with their own Sobolev
+    optical depths (Sec. 2.2: Newton-Raphson on the rate equations with the
+    photoexcitation rates of the transport held fixed per atom).
+
+    G(n) = M(beta(n)) n - b.  The Jacobian is M plus, for every line, the
+    derivative of its net downward flow F = A beta n_u - beta B_lu J_ext
+    (n_l - g_l/g_u n_u) through beta (J_ext: the external-field model; with
+    estimator rates R_lu is fixed per atom and only A beta n_u depends on
+    beta): dF/dn_l = beta' K (A n_u - B_lu J_ext net), dF/dn_u = -g_l/g_u times
+    that; F enters row l with +, row u with - (row 0 is sum n = n_z).
+    Step n += lam d, lam = min(1, limit * min over d_i < 0 of n_i / -d_i), so
+    populations stay positive (reading: the paper damps its steps; a
+    positivity limit of this kind is the damping used here).  Stops when
+    max lam |d_i| / n_i <= tol over levels with n_i >= floor n_z.
+    Returns (n, steps); steps = -1 when max_iter ran out."""
+    L = None if w.levels_used is None else int(w.levels_used[c, z])
+    v = ion_view(w, z, L)
+    L = v["L"]
+    off = v["off"]
+    n = (w.pops[c][off:off + L] if n0 is None else np.asarray(n0, dtype=np.float64)).copy()
+    lo, up, g = v["lo"], v["up"], v["g"]
+    lam_cm = v["lam"] * 1e-8
+    A = einstein_A(lam_cm, g[lo], g[up], v["f"])
+    K = PI_E2_MC * v["f"] * lam_cm * w.t
+    gr = g[lo] / g[up]
+    BJ = np.zeros_like(A)
+    if R_lu_lines is None and w.jbar_W > 0:
+        nu = C_LIGHT / lam_cm
+        BJ = 4.0 * np.pi * PI_E2_MC * v["f"] / (H_PLANCK * nu) * w.jbar_W * planck_nu(nu, w.jbar_TR)
+    for it in range(max_iter):
+        pops = w.pops[c].copy()
+        pops[off:off + L] = n
+        P, n_z, _ = system(w, c, z, pops_beta=pops, R_lu_lines=R_lu_lines, eta=eta)
+        M, b = se_system(P, n_z)
+        G = M @ n - b
+        J = M.copy()
+        net = n[lo] - gr * n[up]
+        t = sobolev_beta_deriv(K * net) * K * (A * n[up] - BJ * net)
+        for k in range(lo.shape[0]):
+            l, u = lo[k], up[k]
+            if l != 0:
+                J[l, l] += t[k]
+                J[l, u] -= gr[k] * t[k]
+            if u != 0:
+                J[u, l] -= t[k]
+                J[u, u] += gr[k] * t[k]
+        d = np.linalg.solve(J, -G)
+        lam = 1.0
+        neg = d < 0
+        if np.any(neg):
+            lam = min(lam, limit * float(np.min(n[neg] / -d[neg])))
+        step = lam * d
+        sig = n >= floor * n_z
+        change = float(np.max(np.abs(step[sig]) / n[sig])) if sig.any() else 0.0
+        n = n + step
+        if change <= tol:
+            return n, it + 1
+    return n, -1

@@ -89,7 +89,7 @@ class NoallocTransport(C.Structure):
 XT_PREC_FP64, XT_PREC_FP32_IR = 0, 1
 XT_RATES_NONE, XT_RATES_ESTIMATORS, XT_RATES_JBAR = 0, 1, 2
 XT_WARM_CURRENT, XT_WARM_LTE, XT_WARM_GIVEN = 0, 1, 2
-XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR = 1, 2, 4
+XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR, XT_SE_NOCONV = 1, 2, 4, 8
 XT_WARM_SURROGATE = 3
 
 
@@ -112,7 +112,8 @@ class NlteParams(C.Structure):
                 ("max_iter", C.c_int32), ("tol", C.c_double), ("jbar_W", C.c_double),
                 ("jbar_TR", C.c_double), ("eta_nt", C.c_double), ("levels_used", C.c_void_p),
                 ("warm_in", C.c_void_p), ("upsilon", C.c_void_p), ("use_graph", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("newton_max", C.c_int32), ("newton_tol", C.c_double),
+                ("newton_limit", C.c_double)]
 
 
 NLTE_STATS = ["systems", "fp64_fallbacks", "singular", "max_iter_used", "mean_iter", "solve_ms",
@@ -120,11 +121,13 @@ NLTE_STATS = ["systems", "fp64_fallbacks", "singular", "max_iter_used", "mean_it
 
 
 class NlteStats(C.Structure):
-    _fields_ = [(f, C.c_double) for f in NLTE_STATS] + [("panel_width", C.c_int32 * 8)]
+    _fields_ = ([(f, C.c_double) for f in NLTE_STATS] + [("panel_width", C.c_int32 * 8)] +
+                [("not_converged", C.c_double)])
 
     def as_dict(self):
         d = {f: getattr(self, f) for f in NLTE_STATS}
         d["panel_width"] = list(self.panel_width)
+        d["not_converged"] = self.not_converged
         return d
 
 
@@ -167,6 +170,7 @@ def lib():
             "surrogate_train_step": ([vp, vp, vp, vp, i64, C.c_double, i32, vp, vp], C.c_int),
             "surrogate_predict": ([vp, vp, i64, vp], C.c_int),
             "train_surrogate": ([vp, vp, vp], C.c_int),
+            "run_coupled": ([vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -313,7 +317,7 @@ def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=N
 def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATORS,
                warm=XT_WARM_CURRENT, max_iter=8, tol=1e-10, jbar_W=0.0, jbar_TR=0.0, eta_nt=0.5,
                levels_used=None, warm_in=None, use_graph=False, autotune=False, pops_out=None,
-               status_out=None, check=True):
+               status_out=None, check=True, newton_max=0, newton_tol=1e-6, newton_limit=0.9):
     """A8: statistical-equilibrium populations of every (cell, ion); the new
     populations replace the context's.  upsilon: per-ion [L_z, L_z] arrays (a
     list, concatenated here) or one flat array."""
@@ -324,9 +328,58 @@ def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATOR
     wi = _f64(warm_in) if warm_in is not None else None
     p = NlteParams(int(precision), int(rates), int(warm), int(max_iter), float(tol), float(jbar_W),
                    float(jbar_TR), float(eta_nt), _ptr(lu), _ptr(wi), _ptr(ups), int(bool(use_graph)),
-                   int(bool(autotune)))
+                   int(bool(autotune)), int(newton_max), float(newton_tol), float(newton_limit))
     st = NlteStats()
     rc = lib().solve_nlte(ctx, C.byref(p), _ptr(pops_out), _ptr(status_out), C.byref(st))
+    if check:
+        _check(ctx, rc)
+        return st.as_dict()
+    return rc, st.as_dict()
+
+
+class CoupledParams(C.Structure):
+    _fields_ = [("transport", C.c_void_p), ("nlte", C.c_void_p), ("start", C.c_int32),
+                ("start_in", C.c_void_p), ("alpha", C.c_double), ("tol", C.c_double),
+                ("floor", C.c_double), ("max_outer", C.c_int32)]
+
+
+COUPLED_STATS = ["last_change", "wall_ms", "start_ms", "transport_ms", "solve_ms", "mix_ms",
+                 "newton_steps", "max_newton_steps", "not_converged", "fp64_fallbacks"]
+
+
+class CoupledStats(C.Structure):
+    _fields_ = ([("outer", C.c_int32), ("converged", C.c_int32)] +
+                [(f, C.c_double) for f in COUPLED_STATS] + [("change", C.c_double * 64)])
+
+    def as_dict(self):
+        d = {"outer": self.outer, "converged": bool(self.converged)}
+        d.update({f: getattr(self, f) for f in COUPLED_STATS})
+        d["change"] = list(self.change)[: min(self.outer, 64)]
+        return d
+
+
+def run_coupled(ctx, upsilon, n_packets, seed=0, start=XT_WARM_LTE, start_in=None, alpha=1.0,
+                tol=1e-3, floor=1e-20, max_outer=30, precision=XT_PREC_FP32_IR, newton_max=60,
+                newton_tol=1e-6, newton_limit=0.9, max_iter=8, ir_tol=1e-10, jbar_W=0.0,
+                jbar_TR=0.0, eta_nt=0.5, levels_used=None, use_graph=False, emission=XT_EMIT_BAND,
+                tau_min=1e-4, e_cut=1e-6, spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1,
+                max_events=1_000_000, subdomain_rounds=False, check=True):
+    """A10: the coupled loop (see include/extrass.h, run_coupled)."""
+    if isinstance(upsilon, (list, tuple)):
+        upsilon = np.concatenate([np.ascontiguousarray(u, dtype=np.float64).ravel() for u in upsilon])
+    ups = _f64(upsilon)
+    lu = _i32(levels_used) if levels_used is not None else None
+    si = _f64(start_in) if start_in is not None else None
+    tp = TransportParams(int(n_packets), 0, -1, int(seed), XT_MODE_ATTEN, int(emission), tau_min, e_cut,
+                         20, 20, spec_lam0_A, spec_dlog, int(spec_nbins), 0, int(max_events),
+                         int(bool(subdomain_rounds)), 0, None)
+    np_ = NlteParams(int(precision), XT_RATES_ESTIMATORS, XT_WARM_CURRENT, int(max_iter), float(ir_tol),
+                     float(jbar_W), float(jbar_TR), float(eta_nt), _ptr(lu), None, _ptr(ups),
+                     int(bool(use_graph)), 0, int(newton_max), float(newton_tol), float(newton_limit))
+    p = CoupledParams(C.addressof(tp), C.addressof(np_), int(start), _ptr(si), float(alpha), float(tol),
+                      float(floor), int(max_outer))
+    st = CoupledStats()
+    rc = lib().run_coupled(ctx, C.byref(p), C.byref(st))
     if check:
         _check(ctx, rc)
         return st.as_dict()
@@ -470,4 +523,4 @@ class Context:
 
 _CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations", "solve_nlte",
               "get_sobolev_tau", "run_transport", "get_estimators", "get_photoexcitation_rates",
-              "get_spectrum", "get_sizes"}
+              "get_spectrum", "get_sizes", "run_coupled"}

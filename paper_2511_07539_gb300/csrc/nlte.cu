@@ -68,7 +68,9 @@ struct SeArgs {
   double tol, eta;
   int max_iter;
   int nb_bucket[8];                     // panel width per 64-level bucket
-  double* __restrict__ iters;           // [cell * n_ion + z] refinement steps
+  double* __restrict__ iters;           // [cell * n_ion + z] refinement (or Newton) steps
+  int newton_max;                       // 0: linear solve with beta_S from pops
+  double newton_tol, newton_limit;
 };
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
@@ -256,7 +258,9 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
   double* sR = sX0 + kSeMaxL;            // row scale
   double* sN = sR + kSeMaxL;             // solution (FP64)
   double* sRes = sN + kSeMaxL;           // residual
-  int* sPiv = (int*)(sRes + kSeMaxL);
+  double* sB = sRes + kSeMaxL;           // right-hand side (b, or -G for a Newton step)
+  double* sNk = sB + kSeMaxL;            // Newton iterate
+  int* sPiv = (int*)(sNk + kSeMaxL);
   T* sVec = (T*)(sPiv + kSeMaxL);        // right-hand side in the factor type
   T* sPan = sVec + kSeMaxL;              // panel [L][nb]
   T* sU12 = sPan + kSeMaxL * kSeNbMax;   // [nb][L]
@@ -283,6 +287,18 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
     const double* pc = a.pops + row * a.nlev;
     const double* ups = a.ups + a.ups_off[z];
     const double sqT = sqrt(Te), kT = kB * Te;
+    const bool newton = a.newton_max > 0;
+    if (!(nz > 0.0)) {
+      // no atoms of this ion here: zero populations, nothing to solve
+      double* out = a.pops_out + row * a.nlev + off;
+      for (int i = tid; i < Lz; i += blockDim.x) out[i] = 0.0;
+      if (tid == 0) {
+        if (a.status) a.status[cell * a.n_ion + z] = XT_SE_OK;
+        if (a.iters) a.iters[cell * a.n_ion + z] = 0;
+      }
+      block_sync();
+      continue;
+    }
     // per-level data; warm start
     for (int i = tid; i < L; i += blockDim.x) {
       sE[i] = a.E[off + i];
@@ -304,129 +320,218 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
       for (int i = tid; i < L; i += blockDim.x) sX0[i] = nz * sW[i] / tot;
     }
     block_sync();
-    // ---- assemble M (row-major, M[i][j] = rate j -> i) : collisions
-    const double cfac = 8.629e-6 * ne / sqT;
-    for (int e = tid; e < L * L; e += blockDim.x) {
-      const int i = e / L, j = e - i * L;
-      double v = 0.0;
-      if (j > i) v = ups[(int64_t)i * Lz + j] * cfac / sG[j];                    // down j -> i
-      else if (j < i) v = ups[(int64_t)j * Lz + i] * cfac / sG[i] * (sW[i] / sW[j]);   // up j -> i
-      W[e] = v;
-    }
-    block_sync();
-    // radiative lines of the kept levels (lines by upper level u < L)
-    for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
-      const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
-      for (int k = k0 + (tid & 7); k < k1; k += 8) {
-        const int s = a.down_line[k];
-        const double* Lr = a.lines + 4 * (int64_t)s;
-        const int64_t lu = __double_as_longlong(Lr[3]);
-        const int lo = (int)(lu & 0xFFFFFFFF) - off;
-        const double nl = pc[off + lo], nu_ = pc[off + u];
-        const double net = nl - Lr[2] * nu_;
-        const double tau = Lr[1] * net;
-        const double beta = tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
-        double Rlu = 0.0;
-        if (a.rates == XT_RATES_JBAR) Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
-        else if (a.rates == XT_RATES_ESTIMATORS && net > 0.0) Rlu = a.S[row * a.nline + s] / (net * a.V);
-        atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
-        atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u
-      }
-    }
-    // non-thermal excitation from the ground level
-    if (dep > 0.0 && nz > 0.0 && L > 1) {
-      double s = 0;
-      for (int u = 1 + tid; u < L; u += blockDim.x) s += ups[u] * (sE[u] - sE[0]);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if ((tid & 31) == 0) red[tid >> 5] = s;
-      block_sync();
-      if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k]; red[0] = t; }
-      block_sync();
-      const double denom = nz * red[0];
-      if (denom > 0.0)
-        for (int u = 1 + tid; u < L; u += blockDim.x) W[(int64_t)u * L] += a.eta * dep * ups[u] / denom;
-    }
-    block_sync();
-    // diagonal: minus the total rate out of each level (column sums)
-    for (int i = tid; i < L; i += blockDim.x) {
-      double s = 0;
-      for (int j = 0; j < L; ++j) if (j != i) s += W[(int64_t)j * L + i];
-      sRes[i] = -s;
-    }
-    block_sync();
-    for (int i = tid; i < L; i += blockDim.x) W[(int64_t)i * L + i] = sRes[i];
-    block_sync();
-    for (int j = tid; j < L; j += blockDim.x) W[j] = 1.0;   // ground-level equation -> sum n = n_z
+    // Newton iterate: the warm start, kept positive
+    if (newton)
+      for (int i = tid; i < L; i += blockDim.x) sNk[i] = fmax(sX0[i], 1e-280 * fmax(nz, 1e-300));
     block_sync();
     const int nb = a.nb_bucket[min(L >> 6, 7)];
-    int st = XT_SE_OK, iters = 0;
-    bool ok;
-    if (sizeof(T) == 8 || a.precision == XT_PREC_FP64) {
-      // ---- plain FP64: factor M, solve
-      double* Wd = (double*)WT;
-      for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
-      block_sync();
-      ok = lu_factor<double>(Wd, L, min(nb, 16), sPiv, (double*)sPan, (double*)sU12);
-      for (int i = tid; i < L; i += blockDim.x) sN[i] = i == 0 ? nz : 0.0;
-      block_sync();
-      if (ok) lu_solve<double>(Wd, L, sPiv, sN);
-      else st = XT_SE_SINGULAR;
-    } else {
-      // ---- FP32 factor of diag(r) M diag(x0), FP64 refinement
-      for (int i = tid; i < L; i += blockDim.x) sX0[i] = sX0[i] > 1e-300 ? sX0[i] : 1e-300;
-      block_sync();
-      for (int i = tid; i < L; i += blockDim.x) {
-        double mx = 0;
-        for (int j = 0; j < L; ++j) mx = fmax(mx, fabs(W[(int64_t)i * L + j] * sX0[j]));
-        sR[i] = mx > 0 ? 1.0 / mx : 1.0;
-      }
-      block_sync();
+    int st = XT_SE_OK, iters = 0, nsteps = 0;
+    bool ok = true;
+    for (;;) {
+      // optical depths from the iterate (Newton) or from the context's populations
+      const double* nbeta = newton ? sNk : pc + off;
+      // ---- assemble M (row-major, M[i][j] = rate j -> i) : collisions
+      const double cfac = 8.629e-6 * ne / sqT;
       for (int e = tid; e < L * L; e += blockDim.x) {
         const int i = e / L, j = e - i * L;
-        WT[e] = (T)(W[e] * sX0[j] * sR[i]);
+        double v = 0.0;
+        if (j > i) v = ups[(int64_t)i * Lz + j] * cfac / sG[j];                    // down j -> i
+        else if (j < i) v = ups[(int64_t)j * Lz + i] * cfac / sG[i] * (sW[i] / sW[j]);   // up j -> i
+        W[e] = v;
       }
       block_sync();
-      ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12);
-      if (!ok) st = XT_SE_SINGULAR;
-      for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = i == 0 ? nz : 0.0; }
-      block_sync();
-      bool conv = false;
-      for (iters = 0; ok && iters < a.max_iter; ++iters) {
-        for (int i = tid; i < L; i += blockDim.x) sVec[i] = (T)(sRes[i] * sR[i]);
-        block_sync();
-        lu_solve<T>(WT, L, sPiv, sVec);
-        double dmax = 0;
-        for (int i = tid; i < L; i += blockDim.x) {
-          const double d = (double)sVec[i] * sX0[i];
-          sN[i] += d;
-          dmax = fmax(dmax, fabs(d) / fmax(fabs(sN[i]), 1e-30 * nz));
+      // radiative lines of the kept levels (lines by upper level u < L)
+      for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
+        const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
+        for (int k = k0 + (tid & 7); k < k1; k += 8) {
+          const int s = a.down_line[k];
+          const double* Lr = a.lines + 4 * (int64_t)s;
+          const int64_t lu = __double_as_longlong(Lr[3]);
+          const int lo = (int)(lu & 0xFFFFFFFF) - off;
+          const double tau = Lr[1] * (nbeta[lo] - Lr[2] * nbeta[u]);
+          const double beta = tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
+          double Rlu = 0.0;
+          if (a.rates == XT_RATES_JBAR) {
+            Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
+          } else if (a.rates == XT_RATES_ESTIMATORS) {
+            // fixed per atom: the populations of the transport pass set it
+            const double net = pc[off + lo] - Lr[2] * pc[off + u];
+            if (net > 0.0) Rlu = a.S[row * a.nline + s] / (net * a.V);
+          }
+          atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
+          atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u
         }
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if ((tid & 31) == 0) red[tid >> 5] = dmax;
+      }
+      // non-thermal excitation from the ground level
+      if (dep > 0.0 && nz > 0.0 && L > 1) {
+        double s = 0;
+        for (int u = 1 + tid; u < L; u += blockDim.x) s += ups[u] * (sE[u] - sE[0]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
         block_sync();
-        if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t < a.tol; }
+        if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k]; red[0] = t; }
         block_sync();
-        if (flag && iters > 0) { conv = true; ++iters; break; }
-        // residual b - M n in FP64
+        const double denom = nz * red[0];
+        if (denom > 0.0)
+          for (int u = 1 + tid; u < L; u += blockDim.x) W[(int64_t)u * L] += a.eta * dep * ups[u] / denom;
+      }
+      block_sync();
+      // diagonal: minus the total rate out of each level (column sums)
+      for (int i = tid; i < L; i += blockDim.x) {
+        double s = 0;
+        for (int j = 0; j < L; ++j) if (j != i) s += W[(int64_t)j * L + i];
+        sRes[i] = -s;
+      }
+      block_sync();
+      for (int i = tid; i < L; i += blockDim.x) W[(int64_t)i * L + i] = sRes[i];
+      block_sync();
+      for (int j = tid; j < L; j += blockDim.x) W[j] = 1.0;   // ground-level equation -> sum n = n_z
+      block_sync();
+      if (newton) {
+        // right-hand side -G = b - M n (FP64), then the Jacobian: for every line
+        // the derivative of its net downward flow F = A beta n_u - beta B J_ext
+        // (n_l - g_l/g_u n_u) through beta: dF/dn_l = t, dF/dn_u = -g_l/g_u t,
+        // t = beta'(tau) K (A n_u - B J_ext net); +F in row l, -F in row u
         for (int i = tid; i < L; i += blockDim.x) {
           double s = i == 0 ? nz : 0.0;
-          for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sN[j];
-          sRes[i] = s;
+          for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sNk[j];
+          sB[i] = s;
         }
         block_sync();
+        for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
+          const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
+          for (int k = k0 + (tid & 7); k < k1; k += 8) {
+            const int s = a.down_line[k];
+            const double* Lr = a.lines + 4 * (int64_t)s;
+            const int64_t lu = __double_as_longlong(Lr[3]);
+            const int lo = (int)(lu & 0xFFFFFFFF) - off;
+            const double net = sNk[lo] - Lr[2] * sNk[u];
+            const double tau = Lr[1] * net;
+            double db = 0.0;
+            if (tau > 1e-8) db = (tau * exp(-tau) + expm1(-tau)) / (tau * tau);
+            else if (tau > 0.0) db = -0.5;
+            if (db == 0.0) continue;
+            const double BJ = a.rates == XT_RATES_JBAR ? a.Rj[s] : 0.0;
+            const double t = db * Lr[1] * (a.A[s] * sNk[u] - BJ * net);
+            if (lo != 0) {
+              atomicAdd(W + (int64_t)lo * L + lo, t);
+              atomicAdd(W + (int64_t)lo * L + u, -Lr[2] * t);
+            }
+            atomicAdd(W + (int64_t)u * L + lo, -t);
+            atomicAdd(W + (int64_t)u * L + u, Lr[2] * t);
+          }
+        }
+        // the column scale of the FP32 factor: the iterate (levels below
+        // 1e-30 n_z need no relative accuracy)
+        for (int i = tid; i < L; i += blockDim.x) sX0[i] = fmax(sNk[i], 1e-30 * nz);
+      } else {
+        for (int i = tid; i < L; i += blockDim.x) sB[i] = i == 0 ? nz : 0.0;
       }
-      if (ok && !conv) {
-        // not converged: the plain FP64 solve decides
-        st |= XT_SE_FALLBACK;
-        double* Wd = (double*)a.WT + (int64_t)blockIdx.x * a.wlen;   // reuse (FP64 sized)
+      block_sync();
+      // ---- solve W x = sB into sN
+      int it_ir = 0;
+      if (sizeof(T) == 8 || a.precision == XT_PREC_FP64) {
+        // plain FP64: factor, solve
+        double* Wd = (double*)WT;
         for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
         block_sync();
-        ok = lu_factor<double>(Wd, L, 16, sPiv, (double*)sPan, (double*)sU12);
-        for (int i = tid; i < L; i += blockDim.x) sN[i] = i == 0 ? nz : 0.0;
+        ok = lu_factor<double>(Wd, L, min(nb, 16), sPiv, (double*)sPan, (double*)sU12);
+        for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[i];
         block_sync();
         if (ok) lu_solve<double>(Wd, L, sPiv, sN);
         else st = XT_SE_SINGULAR;
+      } else {
+        // FP32 factor of diag(r) W diag(x0), FP64 refinement
+        for (int i = tid; i < L; i += blockDim.x) sX0[i] = sX0[i] > 1e-300 ? sX0[i] : 1e-300;
+        block_sync();
+        for (int i = tid; i < L; i += blockDim.x) {
+          double mx = 0;
+          for (int j = 0; j < L; ++j) mx = fmax(mx, fabs(W[(int64_t)i * L + j] * sX0[j]));
+          sR[i] = mx > 0 ? 1.0 / mx : 1.0;
+        }
+        block_sync();
+        for (int e = tid; e < L * L; e += blockDim.x) {
+          const int i = e / L, j = e - i * L;
+          WT[e] = (T)(W[e] * sX0[j] * sR[i]);
+        }
+        block_sync();
+        ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12);
+        if (!ok) st = XT_SE_SINGULAR;
+        for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = sB[i]; }
+        block_sync();
+        bool conv = false;
+        for (it_ir = 0; ok && it_ir < a.max_iter; ++it_ir) {
+          for (int i = tid; i < L; i += blockDim.x) sVec[i] = (T)(sRes[i] * sR[i]);
+          block_sync();
+          lu_solve<T>(WT, L, sPiv, sVec);
+          double dmax = 0;
+          for (int i = tid; i < L; i += blockDim.x) {
+            const double d = (double)sVec[i] * sX0[i];
+            sN[i] += d;
+            // relative to the solution; a Newton correction relative to 1e-8 of the level
+            dmax = fmax(dmax, fabs(d) / fmax(fabs(sN[i]), newton ? 1e-8 * sX0[i] : 1e-30 * nz));
+          }
+          for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          if ((tid & 31) == 0) red[tid >> 5] = dmax;
+          block_sync();
+          if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t < a.tol; }
+          block_sync();
+          if (flag && it_ir > 0) { conv = true; ++it_ir; break; }
+          // residual sB - W x in FP64
+          for (int i = tid; i < L; i += blockDim.x) {
+            double s = sB[i];
+            for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sN[j];
+            sRes[i] = s;
+          }
+          block_sync();
+        }
+        if (ok && !conv) {
+          // not converged: the plain FP64 solve decides
+          st |= XT_SE_FALLBACK;
+          double* Wd = (double*)a.WT + (int64_t)blockIdx.x * a.wlen;   // reuse (FP64 sized)
+          for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
+          block_sync();
+          ok = lu_factor<double>(Wd, L, 16, sPiv, (double*)sPan, (double*)sU12);
+          for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[i];
+          block_sync();
+          if (ok) lu_solve<double>(Wd, L, sPiv, sN);
+          else st = XT_SE_SINGULAR;
+        }
       }
+      block_sync();
+      if (!newton) { iters = it_ir; break; }
+      if (!ok) break;
+      // ---- Newton step: positivity limit, change over the levels that count
+      {
+        double lmin = 1.0;
+        for (int i = tid; i < L; i += blockDim.x)
+          if (sN[i] < 0.0) lmin = fmin(lmin, a.newton_limit * sNk[i] / -sN[i]);
+        for (int o = 16; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+        if ((tid & 31) == 0) red[tid >> 5] = lmin;
+        block_sync();
+        if (tid == 0) { double t = 1.0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmin(t, red[k]); red[0] = t; }
+        block_sync();
+        const double lam = red[0];
+        block_sync();
+        double ch = 0.0;
+        for (int i = tid; i < L; i += blockDim.x) {
+          const double d = lam * sN[i];
+          if (sNk[i] >= 1e-30 * nz) ch = fmax(ch, fabs(d) / sNk[i]);
+          sNk[i] += d;
+        }
+        for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
+        if ((tid & 31) == 0) red[tid >> 5] = ch;
+        block_sync();
+        if (tid == 0) { double t = 0.0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t <= a.newton_tol; }
+        block_sync();
+        ++nsteps;
+        if (flag) break;
+        if (nsteps >= a.newton_max) { st |= XT_SE_NOCONV; break; }
+      }
+    }
+    if (newton) {
+      iters = nsteps;
+      for (int i = tid; i < L; i += blockDim.x) sN[i] = sNk[i];
     }
     block_sync();
     double* out = a.pops_out + row * a.nlev + off;
@@ -462,8 +567,17 @@ __global__ void k_lte(Geometry g, int nlev, int n_ion, const int* __restrict__ l
   }
 }
 
+int lte_fill(xt_ctx* c, const int* levels_used_dev, double* out) {
+  const int64_t n = c->geo.ncell * c->n_ion;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_lte<<<std::max(blocks, 1), 256, 0, c->stream>>>(c->geo, c->nlev, c->n_ion, c->d_level_off, c->d_E, c->d_g,
+                                                  c->d_nion, c->d_Te, levels_used_dev, out);
+  XT_CUDA(c, cudaGetLastError());
+  return XT_OK;
+}
+
 static size_t se_smem(size_t tsize) {
-  return 7 * kSeMaxL * sizeof(double) + kSeMaxL * sizeof(int) +
+  return 9 * kSeMaxL * sizeof(double) + kSeMaxL * sizeof(int) +
          (kSeMaxL + kSeMaxL * kSeNbMax + kSeNbMax * kSeMaxL) * tsize;
 }
 
@@ -485,6 +599,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (p->warm == XT_WARM_GIVEN && !p->warm_in) return fail(c, XT_EINVAL, "solve_nlte: warm_in required");
   if (p->warm < XT_WARM_CURRENT || p->warm > XT_WARM_SURROGATE) return fail(c, XT_EINVAL, "solve_nlte: warm");
   if (p->precision == XT_PREC_FP32_IR && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
+  if (p->newton_max < 0 || (p->newton_max > 0 && (!(p->newton_tol > 0) || !(p->newton_limit > 0 && p->newton_limit < 1))))
+    return fail(c, XT_EINVAL, "solve_nlte: newton_max >= 0, newton_tol > 0, 0 < newton_limit < 1");
   cudaSetDevice(c->device);
   const Geometry& G = c->geo;
   int Lmax = 0;
@@ -622,6 +738,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.levels_used = B.used; a.work = B.work; a.n_work = nsys; a.counter = B.cnt;
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
+  a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_limit = p->newton_limit;
   auto launch_on = [&](const SeArgs& args, int g_, cudaStream_t s_) {
     cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
     if (pi == 0) k_se<double><<<g_, kSeThreads, smem, s_>>>(args);
@@ -702,16 +819,18 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   std::swap(c->d_pops, B.pops_new);
   c->have_S = false;
   if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;
-  int64_t nfb = 0, nsing = 0;
+  int64_t nfb = 0, nsing = 0, nnc = 0;
   double itmax = 0, itsum = 0, flops_lu = 0, flops_as = 0;
   for (int64_t e = 0; e < nsys; ++e) {
     if (status[e] & XT_SE_FALLBACK) ++nfb;
     if (status[e] & XT_SE_SINGULAR) ++nsing;
+    if (status[e] & XT_SE_NOCONV) ++nnc;
     itmax = std::max(itmax, iters[e]);
     itsum += iters[e];
     const double L = used[e];
-    flops_lu += 2.0 / 3.0 * L * L * L;
-    flops_as += 4.0 * L * L;
+    const double solves = p->newton_max > 0 ? std::max(iters[e], 1.0) : 1.0;   // factorizations
+    flops_lu += solves * 2.0 / 3.0 * L * L * L;
+    flops_as += solves * 4.0 * L * L;
   }
   if (status_out) {
     if ((rc = copy(c, status_out, status.data(), nsys * sizeof(int), "status"))) return rc;
@@ -731,6 +850,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     stats->assemble_flops = flops_as;
     stats->lu_flops = flops_lu;
     for (int k = 0; k < 8; ++k) stats->panel_width[k] = a.nb_bucket[k];
+    stats->not_converged = (double)nnc;
   }
   if (nsing > 0) return fail(c, XT_ENOTCONV, "solve_nlte: " + std::to_string(nsing) + " singular systems");
   return XT_OK;

@@ -169,6 +169,8 @@ void mlp_destroy(xt_mlp* n);
 // (levels beyond levels_used zero), into `out` (device).
 int surrogate_warm(xt_ctx* c, int rates, double jbar_W, double jbar_TR, const int* levels_used_dev,
                    double* out);
+// Boltzmann populations [row][nlev] of the kept levels into `out` (device).
+int lte_fill(xt_ctx* c, const int* levels_used_dev, double* out);
 }  // namespace xt
 
 #define XT_CUDA(ctx, call)                                        \

@@ -1,0 +1,99 @@
+"""Newton solves on the optical depths (A8 with beta_S from the solution) and
+the coupled NLTE / transport loop (A10) on the GPU, through the C ABI, against
+the FP64 oracle (needs a GPU).  Bar: populations relative 1e-6 on every level
+with n >= 1e-30 n_z (the refinement target), both Newton iterations run to a
+step of 1e-10."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import coupled, nlte
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xt():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a GPU"
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_07539_gb300 as xt
+    return xt
+
+
+def _ctx(xt):
+    import torch
+    return xt.Context(0, torch.cuda.current_stream().cuda_stream)
+
+
+def _worst(w, got, ref, floor=1e-30):
+    worst = 0.0
+    for z in range(w.n_ion):
+        a, b = int(w.level_off[z]), int(w.level_off[z + 1])
+        nz = w.n_ion_density[:, z:z + 1]
+        m = (ref[:, a:b] >= floor * nz) & (nz > 0)
+        if m.any():
+            worst = max(worst, float(np.max(np.abs(got[:, a:b][m] / ref[:, a:b][m] - 1))))
+    return worst
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_batch_vs_oracle(xt, precision):
+    w = synth.nlte_batch(n=2, seed=5, L_range=(20, 200))       # 8 cells x 10 ions
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        pops = np.zeros((w.ncell, w.nlev))
+        status = np.zeros(w.ncell * w.n_ion, dtype=np.int32)
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=precision, rates=xt.XT_RATES_JBAR,
+                           warm=xt.XT_WARM_CURRENT, jbar_W=w.jbar_W, jbar_TR=w.jbar_TR,
+                           levels_used=w.levels_used, pops_out=pops, status_out=status,
+                           newton_max=100, newton_tol=1e-10)
+    assert st["not_converged"] == 0 and st["singular"] == 0
+    assert np.all(status & xt.XT_SE_OK) and not np.any(status & xt.XT_SE_NOCONV)
+    ref = np.zeros_like(pops)
+    for c in range(w.ncell):
+        for z in range(w.n_ion):
+            n, k = nlte.newton_se(w, c, z, tol=1e-10)
+            assert k > 0
+            L, off = int(w.levels_used[c, z]), int(w.level_off[z])
+            ref[c, off:off + L] = n
+    assert _worst(w, pops, ref) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coupled_loop_vs_oracle(xt, precision):
+    """From Boltzmann populations on an 8^3 sphere: the same number of outer
+    steps and the same converged populations as the oracle's loop."""
+    w = synth.uniform_sphere(seed=4, n=8, n_packets=50_000)
+    w.upsilon = synth.collision_strengths(4, w.level_off)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st = xt.run_coupled(ctx.h, w.upsilon, w.n_packets, seed=w.seed, start=xt.XT_WARM_LTE,
+                            tol=1e-4, precision=precision, newton_tol=1e-10,
+                            spec_lam0_A=w.spec_band_A[0], spec_nbins=w.spec_band_A[1])
+        got = np.zeros((w.ncell, w.nlev))
+        xt.get_populations(ctx.h, got)
+    ref, steps, hist = coupled.coupled_loop(w, tol=1e-4, newton_tol=1e-10)
+    assert st["converged"] and steps == st["outer"], (st, hist)
+    assert st["not_converged"] == 0
+    assert _worst(w, got, ref) < 1e-6
+    np.testing.assert_allclose(st["change"][:-1], hist[:-1], rtol=1e-4)
+
+
+def test_coupled_loop_edge_cases(xt):
+    """One outer step stops at max_outer; an alpha < 1 step is the geometric
+    mean of the oracle's; a grid cell without matter keeps zero populations."""
+    w = synth.uniform_sphere(seed=5, n=6, n_packets=20_000)
+    w.upsilon = synth.collision_strengths(5, w.level_off)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st = xt.run_coupled(ctx.h, w.upsilon, w.n_packets, seed=w.seed, start=xt.XT_WARM_LTE,
+                            alpha=0.5, max_outer=1, tol=1e-12, precision=0, newton_tol=1e-10,
+                            spec_lam0_A=w.spec_band_A[0], spec_nbins=w.spec_band_A[1])
+        got = np.zeros((w.ncell, w.nlev))
+        xt.get_populations(ctx.h, got)
+    assert st["outer"] == 1 and not st["converged"]
+    ref, _ = coupled.outer_step(w, alpha=0.5, newton_tol=1e-10)
+    assert _worst(w, got, ref) < 1e-6
+    assert np.all(got[w.rho == 0] == 0)

@@ -85,19 +85,22 @@ def test_training_lowers_the_loss(xt):
 
 def test_surrogate_warm_start_gains(xt):
     """Trained on the solved populations of one batch, the network warm-starts
-    the solve of a second batch of the same kind: the result is unchanged and
-    the refinement needs fewer steps than from Boltzmann populations."""
+    the Newton solve (optical depths from the populations) of a second batch of
+    the same kind: the result is unchanged and fewer Newton steps are needed
+    than from Boltzmann populations."""
     train = synth.nlte_batch(n=8, seed=5, L_range=(20, 120))
     test = synth.nlte_batch(n=4, seed=6, L_range=(20, 120))
     kw = lambda w: dict(rates=xt.XT_RATES_JBAR, jbar_W=w.jbar_W, jbar_TR=w.jbar_TR,
-                        levels_used=w.levels_used)
+                        levels_used=w.levels_used, newton_max=100, newton_tol=1e-8)
     with _ctx(xt) as ctx:
         ctx.load(train)
-        xt.solve_nlte(ctx.h, train.upsilon, precision=xt.XT_PREC_FP64, **kw(train))
-        st = xt.train_surrogate(ctx.h, epochs=150, batch=128, lr=2e-3, **kw(train))
+        s0 = xt.solve_nlte(ctx.h, train.upsilon, precision=xt.XT_PREC_FP64, **kw(train))
+        assert s0["not_converged"] == 0
+        st = xt.train_surrogate(ctx.h, epochs=150, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
+                                jbar_W=train.jbar_W, jbar_TR=train.jbar_TR,
+                                levels_used=train.levels_used)
         assert st["last_loss"] < 0.1 * st["first_loss"]
         ref = np.zeros((test.ncell, test.nlev))
-        ctx_t = None
         # the second batch in the same context: grid and atoms reloaded, network kept
         ctx.load(test)
         xt.solve_nlte(ctx.h, test.upsilon, precision=xt.XT_PREC_FP64, pops_out=ref, **kw(test))
@@ -107,7 +110,9 @@ def test_surrogate_warm_start_gains(xt):
             out = np.zeros_like(ref)
             s = xt.solve_nlte(ctx.h, test.upsilon, precision=xt.XT_PREC_FP32_IR, warm=warm,
                               pops_out=out, **kw(test))
+            assert s["not_converged"] == 0
             m = ref > 1e-30 * ref.max()
             assert np.max(np.abs(out[m] / ref[m] - 1)) < 1e-6
             res[warm] = s["mean_iter"]
-    assert res[xt.XT_WARM_SURROGATE] <= res[xt.XT_WARM_LTE], res
+    print("mean Newton steps", res)
+    assert res[xt.XT_WARM_SURROGATE] < 0.8 * res[xt.XT_WARM_LTE], res
