@@ -211,12 +211,15 @@ typedef struct {
      * a function of the solution and takes up to newton_max steps from the warm
      * start.  Each step factors the Jacobian (M plus every line's derivative of
      * its net downward flow through beta_S) in the chosen precision, with an
-     * FP64 residual; step n += lam d, lam = min(1, newton_limit * min over
-     * d_i < 0 of n_i / -d_i); stop when max lam |d_i| / n_i <= newton_tol over
-     * levels with n_i >= 1e-30 n_z.  Estimator rates stay fixed per atom. */
+     * FP64 residual, for the correction d.  With r = max |d_i| / n_i over
+     * levels with n_i >= 1e-30 n_z: stop when r <= newton_tol; else every level
+     * moves by the factor 1 + lam d_i / n_i kept within [1/newton_maxvar,
+     * newton_maxvar], lam = 1 once r <= 0.1, before that 0.95, then 0.75, 0.5,
+     * 0.25, 0.05 from steps 10, 35, 50, 90 on (Sec. 2.2).  Estimator rates stay
+     * fixed per atom. */
     int32_t newton_max;
     double newton_tol;      /* 1e-6 */
-    double newton_limit;    /* 0.9 */
+    double newton_maxvar;   /* 10: largest change factor of a population per step */
 } xt_nlte_params;
 typedef struct {
     double systems, fp64_fallbacks, singular, max_iter_used, mean_iter;  /* iterations:

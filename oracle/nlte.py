@@ -163,7 +163,12 @@ def sobolev_beta_deriv(tau):
     return out
 
 
-def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=100, limit=0.9,
+def newton_damping(it):
+    """Damping of Newton step it (0-based), Sec. 2.2."""
+    return 0.95 if it < 10 else 0.75 if it < 35 else 0.5 if it < 50 else 0.25 if it < 90 else 0.05
+
+
+def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=150, max_var=10.0,
               floor=1e-30, eta=0.5):
     """Populations of ion z in cell c that are consistent with their own Sobolev
     optical depths (Sec. 2.2: Newton-Raphson on the rate equations with the
@@ -175,11 +180,15 @@ def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=100, limit=0
     estimator rates R_lu is fixed per atom and only A beta n_u depends on
     beta): dF/dn_l = beta' K (A n_u - B_lu J_ext net), dF/dn_u = -g_l/g_u times
     that; F enters row l with +, row u with - (row 0 is sum n = n_z).
-    Step n += lam d, lam = min(1, limit * min over d_i < 0 of n_i / -d_i), so
-    populations stay positive (reading: the paper damps its steps; a
-    positivity limit of this kind is the damping used here).  Stops when
-    max lam |d_i| / n_i <= tol over levels with n_i >= floor n_z.
-    Returns (n, steps); steps = -1 when max_iter ran out."""
+
+    With d = J^-1 (-G) and r = max |d_i| / n_i over the levels with
+    n_i >= floor n_z: stop when r <= tol; otherwise every level moves by the
+    factor 1 + lam d_i / n_i, kept within [1/max_var, max_var] (Sec. 2.2 bounds
+    the variation of the populations between two steps; readings: a factor 10,
+    which also keeps them positive), lam = 1 once r <= 0.1 and the damping of
+    the step before that (Sec. 2.2: 0.95, then 0.75, 0.5, 0.25 and 0.05 from
+    steps 10, 35, 50 and 90 on).  Returns (n, steps); steps = -1 when max_iter
+    ran out."""
     L = None if w.levels_used is None else int(w.levels_used[c, z])
     v = ion_view(w, z, L)
     L = v["L"]
@@ -194,6 +203,8 @@ def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=100, limit=0
     if R_lu_lines is None and w.jbar_W > 0:
         nu = C_LIGHT / lam_cm
         BJ = 4.0 * np.pi * PI_E2_MC * v["f"] / (H_PLANCK * nu) * w.jbar_W * planck_nu(nu, w.jbar_TR)
+    n_z = float(w.n_ion_density[c, z])
+    n = np.maximum(n, 1e-280 * n_z)
     for it in range(max_iter):
         pops = w.pops[c].copy()
         pops[off:off + L] = n
@@ -212,14 +223,10 @@ def newton_se(w, c, z, n0=None, R_lu_lines=None, tol=1e-6, max_iter=100, limit=0
                 J[u, l] -= t[k]
                 J[u, u] += gr[k] * t[k]
         d = np.linalg.solve(J, -G)
-        lam = 1.0
-        neg = d < 0
-        if np.any(neg):
-            lam = min(lam, limit * float(np.min(n[neg] / -d[neg])))
-        step = lam * d
         sig = n >= floor * n_z
-        change = float(np.max(np.abs(step[sig]) / n[sig])) if sig.any() else 0.0
-        n = n + step
-        if change <= tol:
+        r = float(np.max(np.abs(d[sig]) / n[sig])) if sig.any() else 0.0
+        lam = 1.0 if r <= 0.1 else newton_damping(it)
+        n = n * np.clip(1.0 + lam * d / n, 1.0 / max_var, max_var)
+        if r <= tol:
             return n, it + 1
     return n, -1

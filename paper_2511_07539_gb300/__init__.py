@@ -113,7 +113,7 @@ class NlteParams(C.Structure):
                 ("jbar_TR", C.c_double), ("eta_nt", C.c_double), ("levels_used", C.c_void_p),
                 ("warm_in", C.c_void_p), ("upsilon", C.c_void_p), ("use_graph", C.c_int32),
                 ("autotune", C.c_int32), ("newton_max", C.c_int32), ("newton_tol", C.c_double),
-                ("newton_limit", C.c_double)]
+                ("newton_maxvar", C.c_double)]
 
 
 NLTE_STATS = ["systems", "fp64_fallbacks", "singular", "max_iter_used", "mean_iter", "solve_ms",
@@ -317,7 +317,7 @@ def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=N
 def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATORS,
                warm=XT_WARM_CURRENT, max_iter=8, tol=1e-10, jbar_W=0.0, jbar_TR=0.0, eta_nt=0.5,
                levels_used=None, warm_in=None, use_graph=False, autotune=False, pops_out=None,
-               status_out=None, check=True, newton_max=0, newton_tol=1e-6, newton_limit=0.9):
+               status_out=None, check=True, newton_max=0, newton_tol=1e-6, newton_maxvar=10.0):
     """A8: statistical-equilibrium populations of every (cell, ion); the new
     populations replace the context's.  upsilon: per-ion [L_z, L_z] arrays (a
     list, concatenated here) or one flat array."""
@@ -328,7 +328,7 @@ def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATOR
     wi = _f64(warm_in) if warm_in is not None else None
     p = NlteParams(int(precision), int(rates), int(warm), int(max_iter), float(tol), float(jbar_W),
                    float(jbar_TR), float(eta_nt), _ptr(lu), _ptr(wi), _ptr(ups), int(bool(use_graph)),
-                   int(bool(autotune)), int(newton_max), float(newton_tol), float(newton_limit))
+                   int(bool(autotune)), int(newton_max), float(newton_tol), float(newton_maxvar))
     st = NlteStats()
     rc = lib().solve_nlte(ctx, C.byref(p), _ptr(pops_out), _ptr(status_out), C.byref(st))
     if check:
@@ -359,8 +359,8 @@ class CoupledStats(C.Structure):
 
 
 def run_coupled(ctx, upsilon, n_packets, seed=0, start=XT_WARM_LTE, start_in=None, alpha=1.0,
-                tol=1e-3, floor=1e-20, max_outer=30, precision=XT_PREC_FP32_IR, newton_max=60,
-                newton_tol=1e-6, newton_limit=0.9, max_iter=8, ir_tol=1e-10, jbar_W=0.0,
+                tol=1e-3, floor=1e-20, max_outer=30, precision=XT_PREC_FP32_IR, newton_max=150,
+                newton_tol=1e-6, newton_maxvar=10.0, max_iter=8, ir_tol=1e-10, jbar_W=0.0,
                 jbar_TR=0.0, eta_nt=0.5, levels_used=None, use_graph=False, emission=XT_EMIT_BAND,
                 tau_min=1e-4, e_cut=1e-6, spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1,
                 max_events=1_000_000, subdomain_rounds=False, check=True):
@@ -375,7 +375,7 @@ def run_coupled(ctx, upsilon, n_packets, seed=0, start=XT_WARM_LTE, start_in=Non
                          int(bool(subdomain_rounds)), 0, None)
     np_ = NlteParams(int(precision), XT_RATES_ESTIMATORS, XT_WARM_CURRENT, int(max_iter), float(ir_tol),
                      float(jbar_W), float(jbar_TR), float(eta_nt), _ptr(lu), None, _ptr(ups),
-                     int(bool(use_graph)), 0, int(newton_max), float(newton_tol), float(newton_limit))
+                     int(bool(use_graph)), 0, int(newton_max), float(newton_tol), float(newton_maxvar))
     p = CoupledParams(C.addressof(tp), C.addressof(np_), int(start), _ptr(si), float(alpha), float(tol),
                       float(floor), int(max_outer))
     st = CoupledStats()

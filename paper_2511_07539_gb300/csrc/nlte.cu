@@ -70,7 +70,7 @@ struct SeArgs {
   int nb_bucket[8];                     // panel width per 64-level bucket
   double* __restrict__ iters;           // [cell * n_ion + z] refinement (or Newton) steps
   int newton_max;                       // 0: linear solve with beta_S from pops
-  double newton_tol, newton_limit;
+  double newton_tol, newton_maxvar;
 };
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
     block_sync();
     // Newton iterate: the warm start, kept positive
     if (newton)
-      for (int i = tid; i < L; i += blockDim.x) sNk[i] = fmax(sX0[i], 1e-280 * fmax(nz, 1e-300));
+      for (int i = tid; i < L; i += blockDim.x) sNk[i] = fmax(sX0[i], 1e-280 * nz);
     block_sync();
     const int nb = a.nb_bucket[min(L >> 6, 7)];
     int st = XT_SE_OK, iters = 0, nsteps = 0;
@@ -501,31 +501,29 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
       block_sync();
       if (!newton) { iters = it_ir; break; }
       if (!ok) break;
-      // ---- Newton step: positivity limit, change over the levels that count
+      // ---- Newton step: r = max |d_i| / n_i over the levels that count; every
+      // level moves by the factor 1 + lam d_i / n_i within [1/max_var, max_var]
+      // (Sec. 2.2 bounds the change per step); lam = 1 once r <= 0.1, before
+      // that the damping of the step (Sec. 2.2)
       {
-        double lmin = 1.0;
+        double r = 0.0;
         for (int i = tid; i < L; i += blockDim.x)
-          if (sN[i] < 0.0) lmin = fmin(lmin, a.newton_limit * sNk[i] / -sN[i]);
-        for (int o = 16; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-        if ((tid & 31) == 0) red[tid >> 5] = lmin;
+          if (sNk[i] >= 1e-30 * nz) r = fmax(r, fabs(sN[i]) / sNk[i]);
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if ((tid & 31) == 0) red[tid >> 5] = r;
         block_sync();
-        if (tid == 0) { double t = 1.0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmin(t, red[k]); red[0] = t; }
+        if (tid == 0) { double t = 0.0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); red[0] = t; }
         block_sync();
-        const double lam = red[0];
+        const double rmax = red[0];
         block_sync();
-        double ch = 0.0;
-        for (int i = tid; i < L; i += blockDim.x) {
-          const double d = lam * sN[i];
-          if (sNk[i] >= 1e-30 * nz) ch = fmax(ch, fabs(d) / sNk[i]);
-          sNk[i] += d;
-        }
-        for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
-        if ((tid & 31) == 0) red[tid >> 5] = ch;
-        block_sync();
-        if (tid == 0) { double t = 0.0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t <= a.newton_tol; }
+        const double lam = rmax <= 0.1 ? 1.0
+                         : nsteps < 10 ? 0.95 : nsteps < 35 ? 0.75 : nsteps < 50 ? 0.5 : nsteps < 90 ? 0.25 : 0.05;
+        const double vmax = a.newton_maxvar, vmin = 1.0 / a.newton_maxvar;
+        for (int i = tid; i < L; i += blockDim.x)
+          sNk[i] *= fmin(fmax(1.0 + lam * sN[i] / sNk[i], vmin), vmax);
         block_sync();
         ++nsteps;
-        if (flag) break;
+        if (rmax <= a.newton_tol) break;
         if (nsteps >= a.newton_max) { st |= XT_SE_NOCONV; break; }
       }
     }
@@ -599,8 +597,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (p->warm == XT_WARM_GIVEN && !p->warm_in) return fail(c, XT_EINVAL, "solve_nlte: warm_in required");
   if (p->warm < XT_WARM_CURRENT || p->warm > XT_WARM_SURROGATE) return fail(c, XT_EINVAL, "solve_nlte: warm");
   if (p->precision == XT_PREC_FP32_IR && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
-  if (p->newton_max < 0 || (p->newton_max > 0 && (!(p->newton_tol > 0) || !(p->newton_limit > 0 && p->newton_limit < 1))))
-    return fail(c, XT_EINVAL, "solve_nlte: newton_max >= 0, newton_tol > 0, 0 < newton_limit < 1");
+  if (p->newton_max < 0 || (p->newton_max > 0 && (!(p->newton_tol > 0) || !(p->newton_maxvar > 1))))
+    return fail(c, XT_EINVAL, "solve_nlte: newton_max >= 0, newton_tol > 0, newton_maxvar > 1");
   cudaSetDevice(c->device);
   const Geometry& G = c->geo;
   int Lmax = 0;
@@ -738,7 +736,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.levels_used = B.used; a.work = B.work; a.n_work = nsys; a.counter = B.cnt;
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
-  a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_limit = p->newton_limit;
+  a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_maxvar = p->newton_maxvar;
   auto launch_on = [&](const SeArgs& args, int g_, cudaStream_t s_) {
     cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
     if (pi == 0) k_se<double><<<g_, kSeThreads, smem, s_>>>(args);
