@@ -237,13 +237,14 @@ int solve_nlte(xt_ctx *ctx, const xt_nlte_params *p, double *pops_out, int32_t *
 
 /* ---- A9: population surrogate (no paper counterpart: it warm-starts A8) ----
  * A multilayer perceptron predicts log10(n_i / n_z) / 10 of every level of a
- * cell from log10 n_e, log10 Te, log10 of the deposition and, per ion, the mean
- * log10 Jbar of its lines in 32 log-lambda bins (3 + 32 n_ion inputs, nlev
+ * cell from log10 n_e, log10 Te, log10 of the deposition, per ion the mean
+ * log10 Jbar of its lines in 32 log-lambda bins, and per ion log10 n_z / 10
+ * (3 + 33 n_ion inputs: the 32 n_ion Jbar bins, then the n_ion densities; nlev
  * outputs).  Hidden layers GELU (tanh form), linear output, masked mean squared
  * error, Adam on FP32 master weights; every matrix product in BF16 on the
  * tensor cores with FP32 accumulation.  Weights are one flat FP32 vector:
  * W_1 [n_in][h], b_1, W_2, b_2, ..., W_out, b_out (W row-major [fan_in][fan_out]).
- * A bad prediction costs only refinement steps: solve_nlte refines (or falls
+ * A bad prediction costs only refinement or Newton steps: solve_nlte refines (or falls
  * back to FP64) whatever the warm start. */
 int surrogate_init(xt_ctx *ctx, const int32_t *sizes, int32_t n_sizes, uint64_t seed);
 /* set != 0: load weights from flat; else copy them out.  n_cap in floats. */

@@ -1,7 +1,7 @@
 // A9: the population surrogate network (not in the paper; it warm-starts the
 // statistical-equilibrium solves).  Input: log10 n_e, log10 Te, log10 of the
-// deposition and, per ion, the mean log10 Jbar of its lines in 32 log-lambda
-// bins; output: log10(n_i / n_z) / 10 of every level (clipped at -30 in
+// deposition, per ion the mean log10 Jbar of its lines in 32 log-lambda bins,
+// and per ion log10 n_z / 10 (it sets the optical depths); output: log10(n_i / n_z) / 10 of every level (clipped at -30 in
 // log10, masked beyond the kept levels).  Hidden layers GELU (tanh form,
 // Hendrycks & Gimpel 2016), linear output; masked mean squared error; Adam
 // (Kingma & Ba 2015) on FP32 master weights.  Every matrix product runs in
@@ -461,7 +461,7 @@ __global__ void k_features(const FeatArgs a) {
   const int64_t cell = blockIdx.x;
   const int ix = (int)(cell % a.g.nx), iy = (int)((cell / a.g.nx) % a.g.ny), iz = (int)(cell / ((int64_t)a.g.nx * a.g.ny));
   const int64_t row = row_of(a.g, ix, iy, iz);
-  const int nin = 3 + a.n_ion * a.nbin;
+  const int nin = 3 + a.n_ion * (a.nbin + 1);
   float* x = a.X + cell * nin;
   extern __shared__ float sh[];
   float* sum = sh;                       // [n_ion * nbin]
@@ -493,6 +493,9 @@ __global__ void k_features(const FeatArgs a) {
   }
   for (int k = threadIdx.x; k < a.n_ion * a.nbin; k += blockDim.x)
     x[3 + k] = cnt[k] > 0.f ? sum[k] / cnt[k] + 9.f : -5.f;
+  // the density of every ion: it sets the optical depths of its lines
+  for (int z = threadIdx.x; z < a.n_ion; z += blockDim.x)
+    x[3 + a.n_ion * a.nbin + z] = (float)(log10(fmax(a.nion[row * a.n_ion + z], 1e-30)) / 10.0);
   if (a.T) {
     for (int z = 0; z < a.n_ion; ++z) {
       const int off = a.level_off[z], Lz = a.level_off[z + 1] - off;
@@ -617,7 +620,7 @@ int surrogate_warm(xt_ctx* c, int rates, double jbar_W, double jbar_TR, const in
                    double* out) {
   if (!c->mlp) return fail(c, XT_ESTATE, "surrogate warm start: surrogate_init / train_surrogate first");
   xt_mlp* n = c->mlp;
-  const int nin = 3 + c->n_ion * kJbarBins;
+  const int nin = 3 + c->n_ion * (kJbarBins + 1);
   if (n->sizes.front() != nin || n->sizes.back() != c->nlev)
     return fail(c, XT_EINVAL, "surrogate warm start: network sizes do not match the context");
   const int64_t N = c->geo.ncell;
@@ -653,7 +656,7 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S) return fail(c, XT_ESTATE, "train_surrogate: no estimators for these populations");
   if (p->epochs < 0 || p->batch < 1 || !(p->lr > 0)) return fail(c, XT_EINVAL, "train_surrogate: epochs >= 0, batch >= 1, lr > 0");
   cudaSetDevice(c->device);
-  const int nin = 3 + c->n_ion * kJbarBins, nout = c->nlev;
+  const int nin = 3 + c->n_ion * (kJbarBins + 1), nout = c->nlev;
   int rc;
   if (!c->mlp || c->mlp->sizes.front() != nin || c->mlp->sizes.back() != nout) {
     std::vector<int> sz{nin};

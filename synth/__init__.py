@@ -218,15 +218,18 @@ def clumpy_onion(seed: int = 0, n_packets: int = 100_000_000, n: int = 64,
                  n_lines: int = 100_000, n_ion: int = 10, level_range=(50, 200),
                  subdomains=(8, 8, 8), lam_range=(1000.0, 30000.0),
                  f_range=(1e-6, 1.0), rho_mean=1e-15, sigma=0.5,
-                 corr_len_cells=4.0) -> Workload:
-    """Paper-scale transport workload: onion zones with lognormal clumps."""
+                 corr_len_cells=4.0, field_seed=None) -> Workload:
+    """Paper-scale transport workload: onion zones with lognormal clumps.
+    field_seed (default: seed) draws the clump field alone, so that two
+    realizations can share the same atoms."""
     v_max, t = 5.0e8, 200.0 * DAY
     ncell = n ** 3
     speed = _speed_grid(n, v_max)
     active = speed <= v_max
     rng = np.random.default_rng(seed)
     zone = np.minimum((speed / v_max / 0.25).astype(np.int64), 3)
-    grf = gaussian_random_field(n, corr_len_cells, np.random.default_rng([seed, 1]))
+    grf = gaussian_random_field(n, corr_len_cells,
+                                np.random.default_rng([seed if field_seed is None else field_seed, 1]))
     rho = np.where(active, rho_mean * np.exp(sigma * grf - 0.5 * sigma * sigma), 0.0)
     Te = np.full(ncell, 5000.0)
     ne = 1e7 * rho / rho_mean

@@ -84,35 +84,37 @@ def test_training_lowers_the_loss(xt):
 
 
 def test_surrogate_warm_start_gains(xt):
-    """Trained on the solved populations of one batch, the network warm-starts
-    the Newton solve (optical depths from the populations) of a second batch of
-    the same kind: the result is unchanged and fewer Newton steps are needed
-    than from Boltzmann populations."""
-    train = synth.nlte_batch(n=8, seed=5, L_range=(20, 120))
-    test = synth.nlte_batch(n=4, seed=6, L_range=(20, 120))
-    kw = lambda w: dict(rates=xt.XT_RATES_JBAR, jbar_W=w.jbar_W, jbar_TR=w.jbar_TR,
-                        levels_used=w.levels_used, newton_max=100, newton_tol=1e-8)
+    """Trained on the solved populations of one clumpy ejecta realization, the
+    network warm-starts the Newton solves (optical depths from the
+    populations) of a second realization with the same atoms and new clumps:
+    the result is the same and the solves take far fewer Newton steps than
+    from Boltzmann populations."""
+    kw_w = dict(seed=1, n=12, n_packets=1000, n_lines=2000, level_range=(20, 50),
+                subdomains=(2, 2, 2))
+    train = synth.clumpy_onion(**kw_w)
+    test = synth.clumpy_onion(field_seed=2, **kw_w)
+    ups = synth.collision_strengths(train.upsilon_seed, train.level_off)
+    kw = dict(rates=xt.XT_RATES_JBAR, jbar_W=5.6e-5, jbar_TR=8000.0, newton_max=100,
+              newton_tol=1e-8)
     with _ctx(xt) as ctx:
         ctx.load(train)
-        s0 = xt.solve_nlte(ctx.h, train.upsilon, precision=xt.XT_PREC_FP64, **kw(train))
+        s0 = xt.solve_nlte(ctx.h, ups, precision=xt.XT_PREC_FP64, warm=xt.XT_WARM_LTE, **kw)
         assert s0["not_converged"] == 0
-        st = xt.train_surrogate(ctx.h, epochs=150, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
-                                jbar_W=train.jbar_W, jbar_TR=train.jbar_TR,
-                                levels_used=train.levels_used)
-        assert st["last_loss"] < 0.1 * st["first_loss"]
+        st = xt.train_surrogate(ctx.h, epochs=500, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
+                                jbar_W=5.6e-5, jbar_TR=8000.0)
+        assert st["last_loss"] < 0.02 * st["first_loss"], st
         ref = np.zeros((test.ncell, test.nlev))
-        # the second batch in the same context: grid and atoms reloaded, network kept
+        # the second realization in the same context: grid and atoms reloaded, network kept
         ctx.load(test)
-        xt.solve_nlte(ctx.h, test.upsilon, precision=xt.XT_PREC_FP64, pops_out=ref, **kw(test))
+        xt.solve_nlte(ctx.h, ups, precision=xt.XT_PREC_FP64, warm=xt.XT_WARM_LTE, pops_out=ref, **kw)
         res = {}
         for warm in (xt.XT_WARM_LTE, xt.XT_WARM_SURROGATE):
-            xt.set_populations(ctx.h, test.pops)
             out = np.zeros_like(ref)
-            s = xt.solve_nlte(ctx.h, test.upsilon, precision=xt.XT_PREC_FP32_IR, warm=warm,
-                              pops_out=out, **kw(test))
+            s = xt.solve_nlte(ctx.h, ups, precision=xt.XT_PREC_FP32_IR, warm=warm,
+                              pops_out=out, **kw)
             assert s["not_converged"] == 0
             m = ref > 1e-30 * ref.max()
             assert np.max(np.abs(out[m] / ref[m] - 1)) < 1e-6
-            res[warm] = s["mean_iter"]
-    print("mean Newton steps", res)
-    assert res[xt.XT_WARM_SURROGATE] < 0.8 * res[xt.XT_WARM_LTE], res
+            res[warm] = (s["mean_iter"], s["solve_ms"])
+    print("mean Newton steps, solve ms", res, "training", st)
+    assert res[xt.XT_WARM_SURROGATE][0] < 0.6 * res[xt.XT_WARM_LTE][0], res
