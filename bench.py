@@ -205,6 +205,58 @@ def nlte_bench(local, stream_ptr):
     return out
 
 
+def coupled_bench(local, stream_ptr, n=32):
+    """A10: the coupled loop to a relative population change <= 1e-3 on a
+    clumpy onion of n^3 cells (10 ions of 20-60 levels, 5000 lines, 2e6
+    packets per pass): the plain loop (Newton steps factored in FP64 from
+    Boltzmann populations) against the fast one (FP32 factors with FP64
+    refinement, Newton from the surrogate's prediction).  The surrogate is
+    trained beforehand, and outside the timing, on the converged populations of
+    another clump realization with the same atoms.  Both loops are timed by the
+    host clock around the whole run_coupled call (start populations included)."""
+    import paper_2511_07539_gb300 as xt
+    import synth
+    kw_w = dict(seed=1, n=n, n_packets=2_000_000, n_lines=5000, level_range=(20, 60),
+                subdomains=(4, 4, 4))
+    A = synth.clumpy_onion(**kw_w)
+    B = synth.clumpy_onion(field_seed=2, **kw_w)
+    ups = synth.collision_strengths(A.upsilon_seed, A.level_off)
+    common = dict(tol=1e-3, jbar_W=5.6e-5, jbar_TR=8000.0, spec_lam0_A=A.spec_band_A[0],
+                  spec_nbins=A.spec_band_A[1], seed=A.seed)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(A)
+    stA = xt.run_coupled(ctx.h, ups, A.n_packets, start=xt.XT_WARM_LTE,
+                         precision=xt.XT_PREC_FP32_IR, **common)
+    tr = xt.train_surrogate(ctx.h, epochs=60, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
+                            jbar_W=5.6e-5, jbar_TR=8000.0)
+    ctx.load(B)
+    xt.run_coupled(ctx.h, ups, B.n_packets, start=xt.XT_WARM_LTE, max_outer=1,
+                   precision=xt.XT_PREC_FP32_IR, **common)           # warm-up (buffers)
+    res, pops = {}, {}
+    for name, start, prec in (("plain_fp64", xt.XT_WARM_LTE, xt.XT_PREC_FP64),
+                              ("surrogate_mixed", xt.XT_WARM_SURROGATE, xt.XT_PREC_FP32_IR),
+                              ("lte_mixed", xt.XT_WARM_LTE, xt.XT_PREC_FP32_IR)):
+        ctx.load(B)
+        st = xt.run_coupled(ctx.h, ups, B.n_packets, start=start, precision=prec, **common)
+        p = np.zeros((B.ncell, B.nlev))
+        xt.get_populations(ctx.h, p)
+        pops[name] = p
+        res[name] = {k: st[k] for k in ("outer", "converged", "wall_ms", "start_ms",
+                                        "transport_ms", "solve_ms", "newton_steps",
+                                        "max_newton_steps", "not_converged", "change")}
+    ctx.close()
+    nz = np.repeat(B.n_ion_density, np.diff(B.level_off), axis=1)
+    ref = pops["plain_fp64"]
+    sig = (ref >= 1e-20 * nz) & (nz > 0)
+    dev = {k: float(np.max(np.abs(v[sig] / ref[sig] - 1))) for k, v in pops.items() if k != "plain_fp64"}
+    return {"workload": B.name + " (clump field 2; surrogate trained on clump field 1)",
+            "tol": 1e-3, **res, "max_rel_dev_vs_plain": dev,
+            "speedup_surrogate_mixed_vs_plain": res["plain_fp64"]["wall_ms"] / res["surrogate_mixed"]["wall_ms"],
+            "training": {"realization_1_outer": stA["outer"], "first_loss": tr["first_loss"],
+                         "last_loss": tr["last_loss"], "steps": tr["steps"],
+                         "train_ms": tr["train_ms"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +268,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="onion", choices=["onion", "onion-small", "sphere"])
     ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
+    ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
+    ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
+    ap.add_argument("--coupled-n", type=int, default=32)
     ap.add_argument("--rounds-steps", type=int, default=1,
                     help="extra timed passes with subdomain rounds (0 to skip)")
     args = ap.parse_args()
@@ -245,6 +300,12 @@ def main():
     barrier()
     g.build()
     import paper_2511_07539_gb300 as xt
+
+    if args.only_coupled:
+        if rank == 0:
+            print(json.dumps({"coupled": coupled_bench(local, torch.cuda.current_stream().cuda_stream,
+                                                       args.coupled_n)}), flush=True)
+        return
 
     w = make_workload(args)
     stream = torch.cuda.current_stream()
@@ -353,6 +414,8 @@ def main():
     ctx.close()
     if rank == 0 and not args.no_nlte and args.workload == "onion":
         line["nlte"] = nlte_bench(local, stream.cuda_stream)
+    if rank == 0 and not args.no_coupled and args.workload == "onion":
+        line["coupled"] = coupled_bench(local, stream.cuda_stream, args.coupled_n)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
