@@ -31,6 +31,11 @@ sys.path.insert(0, ROOT)
 METRIC = "packet-line interactions/s"
 UNIT = "interactions/s"
 BYTES_PER_EVENT = 32          # n_l, n_u reads (16 B) + estimator read-modify-write (16 B)
+# DRAM bytes (read + write) per event of the attenuation trace kernel, from an
+# ncu capture of this kernel version on the 32^3 onion case (1531.8 MB over
+# 7,813,774 events); the bench's launch is too large to capture with many
+# passes, and its traffic is taken as proportional to its events.
+TRACE_DRAM_BYTES_PER_EVENT = 1531.8e6 / 7813774
 
 
 def _measured_peaks():
@@ -154,15 +159,16 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def nlte_bench(local, stream_ptr):
-    """A8 on the batched rate-solve workload (64^3 cells x 10 ions, 20-300
-    levels each): FP32 LU + FP64 refinement for all 2.6e6 systems; the plain
-    FP64 LU on the 32^3 sub-batch (1/8 of the systems), scaled by the flop
-    count; the mixed result's deviation from the FP64 one on that sub-batch."""
+def nlte_bench(local, stream_ptr, n=64):
+    """A8 on the batched rate-solve workload (n^3 cells x 10 ions, 20-300
+    levels each; n = 64: 2.6e6 systems): FP32 LU + FP64 refinement for all
+    systems; the plain FP64 LU on the (n/2)^3 sub-batch (1/8 of the systems),
+    scaled by the flop count; the mixed result's deviation from the FP64 one
+    on that sub-batch."""
     import paper_2511_07539_gb300 as xt
     import synth
     out = {}
-    w = synth.nlte_batch(n=64)
+    w = synth.nlte_batch(n=n)
     kw = dict(rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_CURRENT, jbar_W=w.jbar_W,
               jbar_TR=w.jbar_TR, levels_used=w.levels_used)
     ctx = xt.Context(local, stream_ptr)
@@ -179,7 +185,7 @@ def nlte_bench(local, stream_ptr):
                     "max_refinements": best["max_iter_used"], "panel_width": best["panel_width"]}
     ctx.close()
     del w
-    ws = synth.nlte_batch(n=32)
+    ws = synth.nlte_batch(n=max(n // 2, 1))
     kws = dict(rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_CURRENT, jbar_W=ws.jbar_W,
                jbar_TR=ws.jbar_TR, levels_used=ws.levels_used)
     ctx = xt.Context(local, stream_ptr)
@@ -271,6 +277,8 @@ def main():
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
     ap.add_argument("--coupled-n", type=int, default=32)
+    ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
+    ap.add_argument("--nlte-n", type=int, default=64)
     ap.add_argument("--rounds-steps", type=int, default=1,
                     help="extra timed passes with subdomain rounds (0 to skip)")
     args = ap.parse_args()
@@ -301,6 +309,11 @@ def main():
     g.build()
     import paper_2511_07539_gb300 as xt
 
+    if args.only_nlte:
+        if rank == 0:
+            print(json.dumps({"nlte": nlte_bench(local, torch.cuda.current_stream().cuda_stream,
+                                                 args.nlte_n)}), flush=True)
+        return
     if args.only_coupled:
         if rank == 0:
             print(json.dumps({"coupled": coupled_bench(local, torch.cuda.current_stream().cuda_stream,
@@ -384,6 +397,7 @@ def main():
     d2h = spec.nbytes + 18 * 8
     e2e_val = ev_e2e / (min(e2e_ms) * 1e-3) if e2e_ms else None
 
+    store_gb = xt.get_sizes(ctx.h)["store_bytes"] / 1e9
     peaks, src = _measured_peaks()
     # dominant kernel: the trace loop; its device time per launch from CUDA
     # events on the launching stream inside the library
@@ -394,7 +408,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "cells": w.ncell, "lines": w.nline, "levels": w.nlev,
                    "packets_per_gpu": w.n_packets, "subdomains": list(w.subdomains),
-                   "mode": "attenuation", "l2": "estimator store (209.7 GB) cleared every step",
+                   "mode": "attenuation",
+                   "l2": f"inputs larger than L2: estimator store ({store_gb:.1f} GB) cleared every step",
                    "parallelism": f"replicas{world}"},
         "events_per_step": ev / len(stats),
         "tests_per_step": float(np.mean([s["tests"] for s in stats])),
@@ -402,7 +417,9 @@ def main():
         "pass_device_ms": kern_ms, "store_clear_ms": zero_ms, "emit_ms": emit_ms,
         "trace_ms": trace_ms, "escape_ms": escape_ms, "trace_launches_per_pass": trace_launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": TRACE_DRAM_BYTES_PER_EVENT * ev / len(stats),
+                     "traffic_source": "ncu dram bytes per event on the 32^3 onion, scaled by events",
                      "peak_source": src, "kernel": "k_trace",
                      "bytes_per_unit": BYTES_PER_EVENT, "unit_counted": "event"},
         "clocks": clk.summary(),
@@ -413,7 +430,7 @@ def main():
     }
     ctx.close()
     if rank == 0 and not args.no_nlte and args.workload == "onion":
-        line["nlte"] = nlte_bench(local, stream.cuda_stream)
+        line["nlte"] = nlte_bench(local, stream.cuda_stream, args.nlte_n)
     if rank == 0 and not args.no_coupled and args.workload == "onion":
         line["coupled"] = coupled_bench(local, stream.cuda_stream, args.coupled_n)
     if rank == 0 and not args.no_cpu_baseline:
