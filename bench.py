@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--coupled-n", type=int, default=32)
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
     ap.add_argument("--nlte-n", type=int, default=64)
+    ap.add_argument("--nlte-once", action="store_true",
+                    help="with --only-nlte: one plain mixed-precision launch (profiling case)")
     ap.add_argument("--rounds-steps", type=int, default=1,
                     help="extra timed passes with subdomain rounds (0 to skip)")
     args = ap.parse_args()
@@ -309,6 +311,16 @@ def main():
     g.build()
     import paper_2511_07539_gb300 as xt
 
+    if args.only_nlte and args.nlte_once:
+        import synth
+        w = synth.nlte_batch(n=args.nlte_n)
+        ctx = xt.Context(local, torch.cuda.current_stream().cuda_stream)
+        ctx.load(w)
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, rates=xt.XT_RATES_JBAR,
+                           jbar_W=w.jbar_W, jbar_TR=w.jbar_TR, levels_used=w.levels_used)
+        ctx.close()
+        print(json.dumps({"nlte_once": st}), flush=True)
+        return
     if args.only_nlte:
         if rank == 0:
             print(json.dumps({"nlte": nlte_bench(local, torch.cuda.current_stream().cuda_stream,
