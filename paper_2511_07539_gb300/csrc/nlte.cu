@@ -29,9 +29,16 @@
 
 namespace xt {
 
-constexpr int kSeThreads = 256;
+constexpr int kSeThreads = 256;   // CTA of the large systems
 constexpr int kSeMaxL = 320;      // levels per system
+constexpr int kSmallThreads = 64; // CTA of the systems with at most kSmallL levels
+constexpr int kSmallL = 64;
 constexpr int kSeNbMax = 32;      // panel width
+// panel buffer: [maxl][nb + 1] of the factor type, or of doubles with nb <= 16
+__host__ __device__ constexpr size_t se_pan_bytes(int maxl) {
+  return (size_t)maxl * (kSeNbMax + 1) * 4 > (size_t)maxl * 17 * 8 ? (size_t)maxl * (kSeNbMax + 1) * 4
+                                                                    : (size_t)maxl * 17 * 8;
+}
 
 struct SeArgs {
   Geometry g;
@@ -76,59 +83,74 @@ struct SeArgs {
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
 // ---- blocked LU with partial pivoting of the L x L row-major matrix A (global)
+// Panels of nb columns are staged in shared memory with row stride nb + 1 (no
+// bank conflicts between consecutive rows).  Every step of a panel column uses
+// the whole CTA: pivot search (warp reductions, then across warps), row swap,
+// multipliers and the rank-1 update of the panel, one thread per row.  Then
+// the CTA applies the swaps to the other columns, solves for the panel's U
+// rows and updates the trailing matrix through L2 (rank-nb update).
 template <typename T>
 __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T* u12) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  __shared__ int sing, spiv;
+  __shared__ double sbest[32];
+  __shared__ int sidx[32];
   if (tid == 0) sing = 0;
+  const int kbp = nb + 1;
   for (int k0 = 0; k0 < L; k0 += nb) {
     const int kb = min(nb, L - k0);
     const int rows = L - k0;                       // panel rows k0..L-1
-    // load panel [rows][kb]
     for (int e = tid; e < rows * kb; e += blockDim.x) {
       const int r = e / kb, cc = e - r * kb;
-      pan[r * kb + cc] = A[(int64_t)(k0 + r) * L + k0 + cc];
+      pan[r * kbp + cc] = A[(int64_t)(k0 + r) * L + k0 + cc];
     }
     block_sync();
-    if (warp == 0) {
-      // unblocked LU of the panel by one warp
-      for (int j = 0; j < kb; ++j) {
-        // argmax |pan[r][j]|, r >= j
-        T best = 0;
-        int bi = j;
-        for (int r = j + lane; r < rows; r += 32) {
-          const T v = pan[r * kb + j] < 0 ? -pan[r * kb + j] : pan[r * kb + j];
-          if (v > best) { best = v; bi = r; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (lane == 0) piv[k0 + j] = k0 + bi;
-        if (best == 0) { if (lane == 0) sing = 1; continue; }
-        if (bi != j)
-          for (int cc = lane; cc < kb; cc += 32) {
-            const T tmp = pan[j * kb + cc];
-            pan[j * kb + cc] = pan[bi * kb + cc];
-            pan[bi * kb + cc] = tmp;
-          }
-        __syncwarp();
-        const T inv = T(1) / pan[j * kb + j];
-        for (int r = j + 1 + lane; r < rows; r += 32) {
-          const T l = pan[r * kb + j] * inv;
-          pan[r * kb + j] = l;
-          for (int cc = j + 1; cc < kb; ++cc) pan[r * kb + cc] -= l * pan[j * kb + cc];
-        }
-        __syncwarp();
+    for (int j = 0; j < kb; ++j) {
+      // argmax |pan[r][j]| over r >= j, ties to the lowest row
+      T best = 0;
+      int bi = j;
+      for (int r = j + tid; r < rows; r += blockDim.x) {
+        const T v = pan[r * kbp + j] < 0 ? -pan[r * kbp + j] : pan[r * kbp + j];
+        if (v > best) { best = v; bi = r; }
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { sbest[warp] = (double)best; sidx[warp] = bi; }
+      block_sync();
+      if (tid == 0) {
+        double b = sbest[0];
+        int p = sidx[0];
+        for (int w = 1; w < nwarp; ++w)
+          if (sbest[w] > b || (sbest[w] == b && sidx[w] < p)) { b = sbest[w]; p = sidx[w]; }
+        piv[k0 + j] = k0 + p;
+        if (b == 0) { sing = 1; p = -1; }
+        spiv = p;
+      }
+      block_sync();
+      const int p = spiv;
+      if (p < 0) continue;                         // uniform: zero column
+      if (p != j && tid < kb) {
+        const T t = pan[j * kbp + tid];
+        pan[j * kbp + tid] = pan[p * kbp + tid];
+        pan[p * kbp + tid] = t;
+      }
+      block_sync();
+      const T inv = T(1) / pan[j * kbp + j];
+      for (int r = j + 1 + tid; r < rows; r += blockDim.x) {
+        const T l = pan[r * kbp + j] * inv;
+        pan[r * kbp + j] = l;
+        for (int cc = j + 1; cc < kb; ++cc) pan[r * kbp + cc] -= l * pan[j * kbp + cc];
+      }
+      block_sync();
     }
-    block_sync();
     // write the panel back; apply its row swaps to the other columns
     for (int e = tid; e < rows * kb; e += blockDim.x) {
       const int r = e / kb, cc = e - r * kb;
-      A[(int64_t)(k0 + r) * L + k0 + cc] = pan[r * kb + cc];
+      A[(int64_t)(k0 + r) * L + k0 + cc] = pan[r * kbp + cc];
     }
     for (int j = 0; j < kb; ++j) {
       const int p = piv[k0 + j];
@@ -145,16 +167,11 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
     if (n2 > 0) {
       // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared memory
       for (int cc = tid; cc < n2; cc += blockDim.x) {
-        T col[kSeNbMax];
-#pragma unroll 4
         for (int r = 0; r < kb; ++r) {
           T v = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
-          for (int s = 0; s < r; ++s) v -= pan[r * kb + s] * col[s];
-          col[r] = v;
-        }
-        for (int r = 0; r < kb; ++r) {
-          u12[r * n2 + cc] = col[r];
-          A[(int64_t)(k0 + r) * L + k0 + kb + cc] = col[r];
+          for (int s = 0; s < r; ++s) v -= pan[r * kbp + s] * u12[s * n2 + cc];
+          u12[r * n2 + cc] = v;
+          A[(int64_t)(k0 + r) * L + k0 + kb + cc] = v;
         }
       }
       block_sync();
@@ -171,7 +188,7 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
         for (int k = 0; k < kb; ++k) {
           T lv[4], uv[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) lv[a] = (bi + a < m2) ? pan[(kb + bi + a) * kb + k] : T(0);
+          for (int a = 0; a < 4; ++a) lv[a] = (bi + a < m2) ? pan[(kb + bi + a) * kbp + k] : T(0);
 #pragma unroll
           for (int b = 0; b < 4; ++b) uv[b] = (bj + b < n2) ? u12[k * n2 + bj + b] : T(0);
 #pragma unroll
@@ -195,27 +212,41 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
   return sing == 0;
 }
 
-// ---- solve A x = b in place (x in shared memory, type T), A = P L U from lu_factor
-template <typename T>
-__device__ void lu_solve(const T* __restrict__ A, int L, const int* piv, T* x) {
-  const int tid = threadIdx.x;
-  if (tid == 0)
+// The row permutation of lu_factor's pivots as a gather: row i of P b is b[perm[i]].
+__device__ void lu_perm(const int* piv, int L, int* perm) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < L; ++i) perm[i] = i;
     for (int k = 0; k < L; ++k) {
       const int p = piv[k];
-      if (p != k) { const T t = x[k]; x[k] = x[p]; x[p] = t; }
+      if (p != k) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
     }
+  }
   block_sync();
-  // forward, unit lower: blocks of 32 rows, diagonal block by warp 0, rest by all
+}
+
+// ---- solve L U x = y in place (x in shared memory, type T, already permuted)
+// Each 32-row diagonal block is solved by one warp with the block's rows in
+// registers (one row per lane) and the solved values passed by shuffles; the
+// rows outside the block are updated by the whole CTA, one row per thread.
+template <typename T>
+__device__ void lu_solve(const T* __restrict__ A, int L, T* x) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  // forward, unit lower
   for (int r0 = 0; r0 < L; r0 += 32) {
     const int rb = min(32, L - r0);
     if (tid < 32) {
-      for (int r = 1; r < rb; ++r) {
-        T part = (tid < r) ? A[(int64_t)(r0 + r) * L + r0 + tid] * x[r0 + tid] : T(0);
+      const bool on = lane < rb;
+      const T* Ar = A + (int64_t)(r0 + (on ? lane : 0)) * L + r0;
+      T a[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (tid == 0) x[r0 + r] -= part;
-        __syncwarp();
+      for (int c = 0; c < 32; ++c) a[c] = (on && c < lane) ? Ar[c] : T(0);
+      T xv = on ? x[r0 + lane] : T(0);
+#pragma unroll
+      for (int c = 0; c < 31; ++c) {
+        const T xc = __shfl_sync(0xffffffffu, xv, c);
+        xv -= a[c] * xc;                           // a[c] = 0 for c >= lane
       }
+      if (on) x[r0 + lane] = xv;
     }
     block_sync();
     for (int i = r0 + rb + tid; i < L; i += blockDim.x) {
@@ -229,14 +260,22 @@ __device__ void lu_solve(const T* __restrict__ A, int L, const int* piv, T* x) {
   for (int r1 = L; r1 > 0; r1 -= 32) {
     const int r0 = max(0, r1 - 32), rb = r1 - r0;
     if (tid < 32) {
-      for (int r = rb - 1; r >= 0; --r) {
-        const int row = r0 + r;
-        T part = (tid > r && tid < rb) ? A[(int64_t)row * L + r0 + tid] * x[r0 + tid] : T(0);
+      const bool on = lane < rb;
+      const T* Ar = A + (int64_t)(r0 + (on ? lane : 0)) * L + r0;
+      T a[32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (tid == 0) x[row] = (x[row] - part) / A[(int64_t)row * L + row];
-        __syncwarp();
+      for (int c = 0; c < 32; ++c) a[c] = (on && c > lane && c < rb) ? Ar[c] : T(0);
+      const T d = on ? Ar[lane] : T(1);
+      T xv = on ? x[r0 + lane] : T(0);
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < rb) {                              // uniform across the warp
+          if (lane == c) xv = xv / d;
+          const T xc = __shfl_sync(0xffffffffu, xv, c);
+          xv -= a[c] * xc;                         // a[c] = 0 for c <= lane
+        }
       }
+      if (on) x[r0 + lane] = xv;
     }
     block_sync();
     for (int i = tid; i < r0; i += blockDim.x) {
@@ -248,26 +287,31 @@ __device__ void lu_solve(const T* __restrict__ A, int L, const int* piv, T* x) {
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
+// MAXL: largest level count the CTA takes (the large kernel 320 with 256
+// threads, the small one 64 with 64 threads: short block-wide steps cost few
+// warps, and several CTAs share an SM).
+template <typename T, int MAXL, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   extern __shared__ double sm[];
-  double* sE = sm;                       // per-level vectors (kSeMaxL each)
-  double* sG = sE + kSeMaxL;
-  double* sW = sG + kSeMaxL;             // g_i exp(-E_i / k Te)
-  double* sX0 = sW + kSeMaxL;            // warm start (column scale)
-  double* sR = sX0 + kSeMaxL;            // row scale
-  double* sN = sR + kSeMaxL;             // solution (FP64)
-  double* sRes = sN + kSeMaxL;           // residual
-  double* sB = sRes + kSeMaxL;           // right-hand side (b, or -G for a Newton step)
-  double* sNk = sB + kSeMaxL;            // Newton iterate
-  int* sPiv = (int*)(sNk + kSeMaxL);
-  T* sVec = (T*)(sPiv + kSeMaxL);        // right-hand side in the factor type
-  T* sPan = sVec + kSeMaxL;              // panel [L][nb]
-  T* sU12 = sPan + kSeMaxL * kSeNbMax;   // [nb][L]
+  double* sE = sm;                       // per-level vectors (MAXL each)
+  double* sG = sE + MAXL;
+  double* sW = sG + MAXL;                // g_i exp(-E_i / k Te)
+  double* sX0 = sW + MAXL;               // warm start (column scale)
+  double* sR = sX0 + MAXL;               // row scale
+  double* sN = sR + MAXL;                // solution (FP64)
+  double* sRes = sN + MAXL;              // residual
+  double* sB = sRes + MAXL;              // right-hand side (b, or -G for a Newton step)
+  double* sNk = sB + MAXL;               // Newton iterate
+  double* sQ = sNk + MAXL;               // collisional factor of upward rates (per lower level)
+  int* sPiv = (int*)(sQ + MAXL);
+  int* sPerm = sPiv + MAXL;              // the pivots as a gather
+  T* sVec = (T*)(sPerm + MAXL);          // right-hand side in the factor type
+  T* sPan = sVec + MAXL;                 // panel [L][nb + 1]
+  T* sU12 = (T*)((char*)sPan + se_pan_bytes(MAXL));   // [nb][L]
   __shared__ unsigned long long item;
   __shared__ double red[32];
   __shared__ int flag;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   double* W = a.W64 + (int64_t)blockIdx.x * a.wlen;
   // each CTA owns L_max^2 doubles of WT, used as T (factor) or double (fallback)
   T* WT = (T*)((double*)a.WT + (int64_t)blockIdx.x * a.wlen);
@@ -323,6 +367,16 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
     // Newton iterate: the warm start, kept positive
     if (newton)
       for (int i = tid; i < L; i += blockDim.x) sNk[i] = fmax(sX0[i], 1e-280 * nz);
+    // collisional rate factors of the system, with w_i = g_i e^{-(E_i - E_0)/kT}:
+    // down j -> i (j > i) = Y_ij cfac / g_j; up j -> i (j < i) = Y_ji cfac / g_j
+    // e^{-(E_i - E_j)/kT} = Y_ji (cfac / w_j) (w_i / g_i)
+    const double cfac = 8.629e-6 * ne / sqT;
+    for (int i = tid; i < L; i += blockDim.x) {
+      const double gi = a.glev[off + i], wi = sW[i];
+      sQ[i] = cfac / wi;
+      sG[i] = cfac / gi;          // from here on: the downward factor
+      sW[i] = wi / gi;            // from here on: e^{-(E_i - E_0)/kT}
+    }
     block_sync();
     const int nb = a.nb_bucket[min(L >> 6, 7)];
     int st = XT_SE_OK, iters = 0, nsteps = 0;
@@ -330,14 +384,16 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
     for (;;) {
       // optical depths from the iterate (Newton) or from the context's populations
       const double* nbeta = newton ? sNk : pc + off;
-      // ---- assemble M (row-major, M[i][j] = rate j -> i) : collisions
-      const double cfac = 8.629e-6 * ne / sqT;
-      for (int e = tid; e < L * L; e += blockDim.x) {
-        const int i = e / L, j = e - i * L;
-        double v = 0.0;
-        if (j > i) v = ups[(int64_t)i * Lz + j] * cfac / sG[j];                    // down j -> i
-        else if (j < i) v = ups[(int64_t)j * Lz + i] * cfac / sG[i] * (sW[i] / sW[j]);   // up j -> i
-        W[e] = v;
+      // ---- assemble M (row-major, M[i][j] = rate j -> i) : collisions, a warp
+      // per row (the collision strengths are stored symmetric)
+      for (int i = warp; i < L; i += nwarp) {
+        const double* ur = ups + (int64_t)i * Lz;
+        double* Wr = W + (int64_t)i * L;
+        const double ei = sW[i];
+        for (int j = lane; j < L; j += 32) {
+          const double y = ur[j];
+          Wr[j] = j > i ? y * sG[j] : j < i ? y * (sQ[j] * ei) : 0.0;
+        }
       }
       block_sync();
       // radiative lines of the kept levels (lines by upper level u < L)
@@ -392,10 +448,12 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
         // the derivative of its net downward flow F = A beta n_u - beta B J_ext
         // (n_l - g_l/g_u n_u) through beta: dF/dn_l = t, dF/dn_u = -g_l/g_u t,
         // t = beta'(tau) K (A n_u - B J_ext net); +F in row l, -F in row u
-        for (int i = tid; i < L; i += blockDim.x) {
-          double s = i == 0 ? nz : 0.0;
-          for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sNk[j];
-          sB[i] = s;
+        for (int i = warp; i < L; i += nwarp) {
+          const double* Wr = W + (int64_t)i * L;
+          double s = 0.0;
+          for (int j = lane; j < L; j += 32) s += Wr[j] * sNk[j];
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) sB[i] = (i == 0 ? nz : 0.0) - s;
         }
         block_sync();
         for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
@@ -436,34 +494,36 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
         for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
         block_sync();
         ok = lu_factor<double>(Wd, L, min(nb, 16), sPiv, (double*)sPan, (double*)sU12);
-        for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[i];
+        lu_perm(sPiv, L, sPerm);
+        for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[sPerm[i]];
         block_sync();
-        if (ok) lu_solve<double>(Wd, L, sPiv, sN);
+        if (ok) lu_solve<double>(Wd, L, sN);
         else st = XT_SE_SINGULAR;
       } else {
         // FP32 factor of diag(r) W diag(x0), FP64 refinement
         for (int i = tid; i < L; i += blockDim.x) sX0[i] = sX0[i] > 1e-300 ? sX0[i] : 1e-300;
         block_sync();
-        for (int i = tid; i < L; i += blockDim.x) {
+        for (int i = warp; i < L; i += nwarp) {
+          const double* Wr = W + (int64_t)i * L;
           double mx = 0;
-          for (int j = 0; j < L; ++j) mx = fmax(mx, fabs(W[(int64_t)i * L + j] * sX0[j]));
-          sR[i] = mx > 0 ? 1.0 / mx : 1.0;
-        }
-        block_sync();
-        for (int e = tid; e < L * L; e += blockDim.x) {
-          const int i = e / L, j = e - i * L;
-          WT[e] = (T)(W[e] * sX0[j] * sR[i]);
+          for (int j = lane; j < L; j += 32) mx = fmax(mx, fabs(Wr[j] * sX0[j]));
+          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          const double r = mx > 0 ? 1.0 / mx : 1.0;
+          T* Tr = WT + (int64_t)i * L;
+          for (int j = lane; j < L; j += 32) Tr[j] = (T)(Wr[j] * sX0[j] * r);
+          if (lane == 0) sR[i] = r;
         }
         block_sync();
         ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12);
+        lu_perm(sPiv, L, sPerm);
         if (!ok) st = XT_SE_SINGULAR;
         for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = sB[i]; }
         block_sync();
         bool conv = false;
         for (it_ir = 0; ok && it_ir < a.max_iter; ++it_ir) {
-          for (int i = tid; i < L; i += blockDim.x) sVec[i] = (T)(sRes[i] * sR[i]);
+          for (int i = tid; i < L; i += blockDim.x) { const int q = sPerm[i]; sVec[i] = (T)(sRes[q] * sR[q]); }
           block_sync();
-          lu_solve<T>(WT, L, sPiv, sVec);
+          lu_solve<T>(WT, L, sVec);
           double dmax = 0;
           for (int i = tid; i < L; i += blockDim.x) {
             const double d = (double)sVec[i] * sX0[i];
@@ -478,10 +538,12 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
           block_sync();
           if (flag && it_ir > 0) { conv = true; ++it_ir; break; }
           // residual sB - W x in FP64
-          for (int i = tid; i < L; i += blockDim.x) {
-            double s = sB[i];
-            for (int j = 0; j < L; ++j) s -= W[(int64_t)i * L + j] * sN[j];
-            sRes[i] = s;
+          for (int i = warp; i < L; i += nwarp) {
+            const double* Wr = W + (int64_t)i * L;
+            double s = 0.0;
+            for (int j = lane; j < L; j += 32) s += Wr[j] * sN[j];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) sRes[i] = sB[i] - s;
           }
           block_sync();
         }
@@ -492,9 +554,10 @@ __global__ void __launch_bounds__(kSeThreads) k_se(const SeArgs a) {
           for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
           block_sync();
           ok = lu_factor<double>(Wd, L, 16, sPiv, (double*)sPan, (double*)sU12);
-          for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[i];
+          lu_perm(sPiv, L, sPerm);
+          for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[sPerm[i]];
           block_sync();
-          if (ok) lu_solve<double>(Wd, L, sPiv, sN);
+          if (ok) lu_solve<double>(Wd, L, sN);
           else st = XT_SE_SINGULAR;
         }
       }
@@ -574,9 +637,9 @@ int lte_fill(xt_ctx* c, const int* levels_used_dev, double* out) {
   return XT_OK;
 }
 
-static size_t se_smem(size_t tsize) {
-  return 9 * kSeMaxL * sizeof(double) + kSeMaxL * sizeof(int) +
-         (kSeMaxL + kSeMaxL * kSeNbMax + kSeNbMax * kSeMaxL) * tsize;
+static size_t se_smem(size_t tsize, int maxl) {
+  return 10 * (size_t)maxl * sizeof(double) + 2 * (size_t)maxl * sizeof(int) + (size_t)maxl * tsize +
+         se_pan_bytes(maxl) + (size_t)kSeNbMax * maxl * tsize;
 }
 
 }  // namespace xt
@@ -643,20 +706,28 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   const size_t ups_n = (size_t)ups_off[c->n_ion];
   const int pi = p->precision == XT_PREC_FP64 ? 0 : 1;
   const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
-  const size_t smem = se_smem(tsz);
-  int per_sm = 0;
+  // systems with more than kSmallL levels go to the large kernel, the rest
+  // (the tail of the longest-first list) to the small one
+  const int64_t n_big = Lmax > kSmallL ? start[kSmallL] : 0, n_small = nsys - n_big;
+  const size_t smem = se_smem(tsz, kSeMaxL), smem_s = se_smem(tsz, kSmallL);
+  int per_sm = 0, per_sm_s = 0;
   if (pi == 0) {
-    cudaFuncSetAttribute(k_se<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<double>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<double, kSeMaxL, kSeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<double, kSeMaxL, kSeThreads>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<double, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<double, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
   } else {
-    cudaFuncSetAttribute(k_se<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<float, kSeMaxL, kSeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float, kSeMaxL, kSeThreads>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<float, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<float, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
   }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int grid = (int)std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, nsys);
-  const int64_t wlen = (int64_t)Lmax * Lmax;
-  const size_t wbytes = (size_t)grid * wlen * sizeof(double);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, n_big));
+  const int grid_s = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(per_sm_s, 1) * sms, n_small));
+  const int64_t wlen = (int64_t)Lmax * Lmax, wlen_s = (int64_t)kSmallL * kSmallL;
+  const size_t wbytes = ((size_t)grid * wlen + (size_t)grid_s * wlen_s) * sizeof(double);
   const size_t pops_n = (size_t)G.ncell * c->nlev;
 #define SE_GROW(ptr, have, need, elt, what)                                           \
   do {                                                                                \
@@ -684,7 +755,20 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     if ((rc = alloc(c, (void**)&B.WT, wbytes, "workspace"))) return rc;
     B.wbytes = wbytes;
   }
-  if ((rc = copy(c, B.ups, p->upsilon, ups_n * sizeof(double), "upsilon"))) return rc;
+  {
+    // the kernel reads the collision strengths by rows: store them symmetric
+    std::vector<double> ups(ups_n);
+    if ((rc = copy(c, ups.data(), p->upsilon, ups_n * sizeof(double), "upsilon"))) return rc;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int z = 0; z < c->n_ion; ++z) {
+      const int64_t Lz = c->h_level_off[z + 1] - c->h_level_off[z];
+      double* u = ups.data() + ups_off[z];
+      for (int64_t i = 0; i < Lz; ++i)
+        for (int64_t j = 0; j < i; ++j) u[i * Lz + j] = u[j * Lz + i];
+    }
+    if ((rc = copy(c, B.ups, ups.data(), ups_n * sizeof(double), "upsilon"))) return rc;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   if ((rc = copy(c, B.upsoff, ups_off.data(), ups_off.size() * sizeof(int64_t), "upsilon offsets"))) return rc;
   if ((rc = copy(c, B.work, work.data(), nsys * sizeof(int), "work list"))) return rc;
   if ((rc = copy(c, B.used, used.data(), nsys * sizeof(int), "levels used"))) return rc;
@@ -733,16 +817,29 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.pops_out = B.pops_new; a.status = B.status; a.lines = c->d_lines; a.A = c->d_A;
   a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = B.Rj;
   a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = B.ups; a.ups_off = B.upsoff;
-  a.levels_used = B.used; a.work = B.work; a.n_work = nsys; a.counter = B.cnt;
+  a.levels_used = B.used; a.work = B.work; a.n_work = n_big; a.counter = B.cnt;
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
   a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_maxvar = p->newton_maxvar;
-  auto launch_on = [&](const SeArgs& args, int g_, cudaStream_t s_) {
-    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
-    if (pi == 0) k_se<double><<<g_, kSeThreads, smem, s_>>>(args);
-    else k_se<float><<<g_, kSeThreads, smem, s_>>>(args);
+  SeArgs as = a;                         // the small systems: own work range, counter, workspace
+  as.work = B.work + n_big; as.n_work = n_small; as.counter = B.cnt + 1;
+  as.W64 = B.W64 + (size_t)grid * wlen; as.WT = B.WT + (size_t)grid * wlen; as.wlen = wlen_s;
+  // one kernel (small = the 64-level one) on a work range
+  auto launch_one = [&](const SeArgs& args, bool small, int g_, cudaStream_t s_) {
+    if (args.n_work <= 0) return;
+    if (small) {
+      if (pi == 0) k_se<double, kSmallL, kSmallThreads><<<g_, kSmallThreads, smem_s, s_>>>(args);
+      else k_se<float, kSmallL, kSmallThreads><<<g_, kSmallThreads, smem_s, s_>>>(args);
+    } else {
+      if (pi == 0) k_se<double, kSeMaxL, kSeThreads><<<g_, kSeThreads, smem, s_>>>(args);
+      else k_se<float, kSeMaxL, kSeThreads><<<g_, kSeThreads, smem, s_>>>(args);
+    }
   };
-  auto launch = [&](const SeArgs& args, int g_) { launch_on(args, g_, c->stream); };
+  auto launch_on = [&](const SeArgs& big, const SeArgs& small, cudaStream_t s_) {
+    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
+    launch_one(big, false, grid, s_);
+    launch_one(small, true, grid_s, s_);
+  };
   // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
   if (p->autotune && !B.tuned[pi]) {
     const int cand[3] = {8, 16, 32};
@@ -756,13 +853,17 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
       float best = 1e30f;
       for (int k = 0; k < 3; ++k) {
         if (pi == 0 && cand[k] > 16) continue;
-        SeArgs t_ = a;
+        const bool small = lo >= n_big;               // the sample lies in the small range
+        SeArgs t_ = small ? as : a;
         t_.work = B.work + lo;
         t_.n_work = n;
         for (int q = 0; q < 8; ++q) t_.nb_bucket[q] = cand[k];
-        launch(t_, (int)std::min<int64_t>(grid, n));       // warm
+        const int g_ = (int)std::min<int64_t>(small ? grid_s : grid, n);
+        cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), c->stream);
+        launch_one(t_, small, g_, c->stream);           // warm
+        cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), c->stream);
         XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-        launch(t_, (int)std::min<int64_t>(grid, n));
+        launch_one(t_, small, g_, c->stream);
         XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
         XT_CUDA(c, cudaEventSynchronize(c->ev1));
         float ms = 0;
@@ -772,14 +873,16 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     }
     B.tuned[pi] = true;
   }
-  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = B.nb[pi][k];
+  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = as.nb_bucket[k] = B.nb[pi][k];
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   if (p->use_graph) {
-    // one captured launch per argument set, replayed on later calls
-    std::vector<unsigned char> key(sizeof(a) + 2 * sizeof(int));
+    // one captured pair of launches per argument set, replayed on later calls
+    std::vector<unsigned char> key(2 * sizeof(a) + 3 * sizeof(int));
     std::memcpy(key.data(), &a, sizeof(a));
-    std::memcpy(key.data() + sizeof(a), &grid, sizeof(int));
-    std::memcpy(key.data() + sizeof(a) + sizeof(int), &pi, sizeof(int));
+    std::memcpy(key.data() + sizeof(a), &as, sizeof(as));
+    std::memcpy(key.data() + 2 * sizeof(a), &grid, sizeof(int));
+    std::memcpy(key.data() + 2 * sizeof(a) + sizeof(int), &grid_s, sizeof(int));
+    std::memcpy(key.data() + 2 * sizeof(a) + 2 * sizeof(int), &pi, sizeof(int));
     int gi = -1;
     for (size_t k = 0; k < B.graph_keys.size(); ++k) if (B.graph_keys[k] == key) gi = (int)k;
     if (gi < 0) {
@@ -788,7 +891,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
       cudaGraph_t graph;
       XT_CUDA(c, cudaStreamSynchronize(c->stream));
       XT_CUDA(c, cudaStreamBeginCapture(c->side, cudaStreamCaptureModeThreadLocal));
-      launch_on(a, grid, c->side);
+      launch_on(a, as, c->side);
       XT_CUDA(c, cudaStreamEndCapture(c->side, &graph));
       cudaGraphExec_t ex;
       XT_CUDA(c, cudaGraphInstantiate(&ex, graph, 0));
@@ -801,7 +904,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
     XT_CUDA(c, cudaGraphLaunch(B.graphs[gi], c->stream));
   } else {
-    launch(a, grid);
+    launch_on(a, as, c->stream);
   }
   XT_CUDA(c, cudaGetLastError());
   XT_CUDA(c, cudaEventRecord(c->ev1, c->stream));
