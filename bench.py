@@ -183,6 +183,17 @@ def nlte_bench(local, stream_ptr, n=64):
                     "lu_tflops": best["lu_flops"] / (best["solve_ms"] * 1e-3) / 1e12,
                     "fp64_fallbacks": best["fp64_fallbacks"], "mean_refinements": best["mean_iter"],
                     "max_refinements": best["max_iter_used"], "panel_width": best["panel_width"]}
+    # the same with the LU's trailing updates on the tensor cores (TF32)
+    xt.set_populations(ctx.h, w.pops)
+    xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_TF32_IR, autotune=True, use_graph=True, **kw)
+    tb = None
+    for _ in range(3):
+        xt.set_populations(ctx.h, w.pops)
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_TF32_IR, use_graph=True, **kw)
+        tb = st if tb is None or st["solve_ms"] < tb["solve_ms"] else tb
+    out["tf32"] = {"solve_ms": tb["solve_ms"], "fp64_fallbacks": tb["fp64_fallbacks"],
+                   "mean_refinements": tb["mean_iter"], "max_refinements": tb["max_iter_used"],
+                   "panel_width": tb["panel_width"]}
     ctx.close()
     del w
     ws = synth.nlte_batch(n=max(n // 2, 1))
@@ -196,6 +207,9 @@ def nlte_bench(local, stream_ptr, n=64):
     p32 = np.zeros_like(p64)
     st32 = xt.solve_nlte(ctx.h, ws.upsilon, precision=xt.XT_PREC_FP32_IR, pops_out=p32,
                          autotune=True, **kws)
+    xt.set_populations(ctx.h, ws.pops)
+    ptf = np.zeros_like(p64)
+    xt.solve_nlte(ctx.h, ws.upsilon, precision=xt.XT_PREC_TF32_IR, pops_out=ptf, autotune=True, **kws)
     ctx.close()
     nz = np.repeat(ws.n_ion_density, np.diff(ws.level_off), axis=1)
     sig = p64 >= 1e-30 * nz
@@ -207,6 +221,7 @@ def nlte_bench(local, stream_ptr, n=64):
                             "scaling": "by LU flop count of the full batch"}
     out["mixed_subbatch_ms"] = st32["solve_ms"]
     out["max_rel_dev_mixed_vs_fp64"] = err
+    out["max_rel_dev_tf32_vs_fp64"] = float(np.max(np.abs(ptf[sig] / p64[sig] - 1)))
     out["speedup_vs_fp64"] = st64["solve_ms"] * scale / best["solve_ms"]
     return out
 

@@ -171,6 +171,9 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
  *   XT_PREC_FP32_IR  the system scaled by the warm start (columns) and row
  *                    maxima, LU in FP32, refined in FP64 (residual, update)
  *                    until the largest relative correction is below tol.
+ *   XT_PREC_TF32_IR  as XT_PREC_FP32_IR with the rank-nb trailing updates of
+ *                    the blocked LU on the tensor cores (TF32 operands, FP32
+ *                    accumulation); more refinement steps, same FP64 result.
  * Rates: XT_RATES_ESTIMATORS uses the last transport pass (R_lu = S/(n_l V));
  * XT_RATES_JBAR illuminates every line with the external field
  * J_nu = jbar_W B_nu(jbar_TR), of which a Sobolev region absorbs the part
@@ -181,6 +184,7 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
  * (XT_WARM_LTE) or warm_in [ncell][nlev] (XT_WARM_GIVEN). */
 #define XT_PREC_FP64 0
 #define XT_PREC_FP32_IR 1
+#define XT_PREC_TF32_IR 2   /* as FP32_IR, the trailing updates of the LU on the tensor cores (TF32) */
 #define XT_RATES_NONE 0
 #define XT_RATES_ESTIMATORS 1
 #define XT_RATES_JBAR 2

@@ -86,7 +86,7 @@ class NoallocTransport(C.Structure):
                 ("S", C.c_void_p), ("spec", C.c_void_p)]
 
 
-XT_PREC_FP64, XT_PREC_FP32_IR = 0, 1
+XT_PREC_FP64, XT_PREC_FP32_IR, XT_PREC_TF32_IR = 0, 1, 2
 XT_RATES_NONE, XT_RATES_ESTIMATORS, XT_RATES_JBAR = 0, 1, 2
 XT_WARM_CURRENT, XT_WARM_LTE, XT_WARM_GIVEN = 0, 1, 2
 XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR, XT_SE_NOCONV = 1, 2, 4, 8

@@ -82,6 +82,25 @@ struct SeArgs {
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
+// D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
+// accumulators; per lane (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g + 8, t),
+// a2 (g, t + 4), a3 (g + 8, t + 4); b0 (t, g), b1 (t + 4, g); c0, c1 (g, 2t, 2t + 1),
+// c2, c3 (g + 8, 2t, 2t + 1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&c)[4], float a0, float a1, float a2, float a3,
+                                                float b0, float b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(to_tf32(a0)), "r"(to_tf32(a1)), "r"(to_tf32(a2)), "r"(to_tf32(a3)), "r"(to_tf32(b0)),
+        "r"(to_tf32(b1)));
+}
+
 // ---- blocked LU with partial pivoting of the L x L row-major matrix A (global)
 // Panels of nb columns are staged in shared memory with row stride nb + 1 (no
 // bank conflicts between consecutive rows).  Every step of a panel column uses
@@ -90,7 +109,8 @@ __device__ __forceinline__ void block_sync() { __syncthreads(); }
 // the CTA applies the swaps to the other columns, solves for the panel's U
 // rows and updates the trailing matrix through L2 (rank-nb update).
 template <typename T>
-__device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T* u12) {
+__device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T* u12,
+                          bool tc_tf32 = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   __shared__ int sing, spiv;
   __shared__ double sbest[32];
@@ -175,8 +195,38 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
         }
       }
       block_sync();
-      // A22 -= L21 U12: 4 x 4 register tiles
       const int m2 = L - k0 - kb;                   // trailing rows
+      if (tc_tf32) {
+        // A22 -= L21 U12 on the tensor cores: TF32 operands, FP32 accumulation,
+        // one 16 x 8 output tile per warp and step (mma.sync m16n8k8)
+        const int g = lane >> 2, t4 = lane & 3;
+        const int mt = (m2 + 15) >> 4, ntl = (n2 + 7) >> 3;
+        for (int t = warp; t < mt * ntl; t += nwarp) {
+          const int bi = (t / ntl) << 4, bj = (t % ntl) << 3;
+          float c[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int k = 0; k < kb; k += 8) {
+            const int ka = k + t4, kc = k + t4 + 4;
+            const int ra = bi + g, rb = bi + g + 8;
+            const float a0 = (ra < m2 && ka < kb) ? (float)pan[(kb + ra) * kbp + ka] : 0.f;
+            const float a1 = (rb < m2 && ka < kb) ? (float)pan[(kb + rb) * kbp + ka] : 0.f;
+            const float a2 = (ra < m2 && kc < kb) ? (float)pan[(kb + ra) * kbp + kc] : 0.f;
+            const float a3 = (rb < m2 && kc < kb) ? (float)pan[(kb + rb) * kbp + kc] : 0.f;
+            const int cb = bj + g;
+            const float b0 = (cb < n2 && ka < kb) ? (float)u12[ka * n2 + cb] : 0.f;
+            const float b1 = (cb < n2 && kc < kb) ? (float)u12[kc * n2 + cb] : 0.f;
+            mma_tf32_16x8x8(c, a0, a1, a2, a3, b0, b1);
+          }
+          const int r0 = bi + g, cc0 = bj + 2 * t4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = r0 + ((q >> 1) << 3), cc = cc0 + (q & 1);
+            if (r < m2 && cc < n2) A[(int64_t)(k0 + kb + r) * L + k0 + kb + cc] -= (T)c[q];
+          }
+        }
+        block_sync();
+        continue;
+      }
+      // A22 -= L21 U12: 4 x 4 register tiles
       const int tr = (m2 + 3) / 4, tc = (n2 + 3) / 4;
       for (int t = tid; t < tr * tc; t += blockDim.x) {
         const int bi = (t / tc) * 4, bj = (t % tc) * 4;
@@ -514,7 +564,7 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           if (lane == 0) sR[i] = r;
         }
         block_sync();
-        ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12);
+        ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12, sizeof(T) == 4 && a.precision == XT_PREC_TF32_IR);
         lu_perm(sPiv, L, sPerm);
         if (!ok) st = XT_SE_SINGULAR;
         for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = sB[i]; }
@@ -652,14 +702,15 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (!c->have_pops || !c->have_atoms) return fail(c, XT_ESTATE, "solve_nlte: load_atomic_data and set_populations first");
   if (!c->d_nion) return fail(c, XT_ESTATE, "solve_nlte: n_ion_density was not given to load_atomic_data");
   if (c->n_ion > 16) return fail(c, XT_EINVAL, "solve_nlte: at most 16 ions");
-  if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR) return fail(c, XT_EINVAL, "solve_nlte: precision");
+  if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR && p->precision != XT_PREC_TF32_IR)
+    return fail(c, XT_EINVAL, "solve_nlte: precision");
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S)
     return fail(c, XT_ESTATE, "solve_nlte: estimator rates need a transport pass with the current populations");
   if (p->rates == XT_RATES_JBAR && !(p->jbar_W > 0 && p->jbar_TR > 0)) return fail(c, XT_EINVAL, "solve_nlte: jbar_W, jbar_TR > 0");
   if (!p->upsilon) return fail(c, XT_EINVAL, "solve_nlte: upsilon is required");
   if (p->warm == XT_WARM_GIVEN && !p->warm_in) return fail(c, XT_EINVAL, "solve_nlte: warm_in required");
   if (p->warm < XT_WARM_CURRENT || p->warm > XT_WARM_SURROGATE) return fail(c, XT_EINVAL, "solve_nlte: warm");
-  if (p->precision == XT_PREC_FP32_IR && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
+  if (p->precision != XT_PREC_FP64 && (p->max_iter < 1 || !(p->tol > 0))) return fail(c, XT_EINVAL, "solve_nlte: max_iter >= 1, tol > 0");
   if (p->newton_max < 0 || (p->newton_max > 0 && (!(p->newton_tol > 0) || !(p->newton_maxvar > 1))))
     return fail(c, XT_EINVAL, "solve_nlte: newton_max >= 0, newton_tol > 0, newton_maxvar > 1");
   cudaSetDevice(c->device);
@@ -704,7 +755,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     ups_off[z + 1] = ups_off[z] + Lz * Lz;
   }
   const size_t ups_n = (size_t)ups_off[c->n_ion];
-  const int pi = p->precision == XT_PREC_FP64 ? 0 : 1;
+  const int pi = p->precision == XT_PREC_FP64 ? 0 : 1;           // kernel type: double / float
+  const int ti = p->precision == XT_PREC_TF32_IR ? 2 : pi;        // tuning slot
   const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
   // systems with more than kSmallL levels go to the large kernel, the rest
   // (the tail of the longest-first list) to the small one
@@ -841,7 +893,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     launch_one(small, true, grid_s, s_);
   };
   // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
-  if (p->autotune && !B.tuned[pi]) {
+  if (p->autotune && !B.tuned[ti]) {
     const int cand[3] = {8, 16, 32};
     for (int b = 0; b < 8; ++b) {
       // systems with L in [64 b, 64 b + 63] are contiguous in the longest-first list
@@ -868,12 +920,12 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
         XT_CUDA(c, cudaEventSynchronize(c->ev1));
         float ms = 0;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-        if (ms < best) { best = ms; B.nb[pi][b] = cand[k]; }
+        if (ms < best) { best = ms; B.nb[ti][b] = cand[k]; }
       }
     }
-    B.tuned[pi] = true;
+    B.tuned[ti] = true;
   }
-  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = as.nb_bucket[k] = B.nb[pi][k];
+  for (int k = 0; k < 8; ++k) a.nb_bucket[k] = as.nb_bucket[k] = B.nb[ti][k];
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   if (p->use_graph) {
     // one captured pair of launches per argument set, replayed on later calls

@@ -143,8 +143,9 @@ struct xt_ctx {
     double* Rj = nullptr; int Rj_n = 0;
     double* warm = nullptr; size_t warm_n = 0;
     int* used_nat = nullptr; int64_t used_nat_n = 0;
-    int nb[2][8] = {{16, 16, 16, 16, 16, 16, 16, 16}, {32, 32, 32, 32, 32, 32, 32, 32}};
-    bool tuned[2] = {false, false};
+    int nb[3][8] = {{16, 16, 16, 16, 16, 16, 16, 16}, {32, 32, 32, 32, 32, 32, 32, 32},
+                    {32, 32, 32, 32, 32, 32, 32, 32}};   // FP64, FP32, TF32
+    bool tuned[3] = {false, false, false};
     std::vector<std::vector<unsigned char>> graph_keys;
     std::vector<cudaGraphExec_t> graphs;
   } se;

@@ -2,7 +2,8 @@
 (LAPACK), through the C ABI (needs a GPU).  Bars on every level with
 n_i >= 1e-30 n_z: plain FP64 LU relative 1e-10; FP32 LU with FP64 refinement
 relative 1e-6 (the stated target; with the refinement stop at 1e-10 the
-worst level is also required below 1e-8)."""
+worst level is also required below 1e-8); the same for the LU whose trailing
+updates run on the tensor cores in TF32."""
 import numpy as np
 import pytest
 
@@ -50,7 +51,7 @@ def _check(w, pops, ref, tol):
     return worst
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6), (2, 1e-6)])
 def test_batch_uneven_levels_vs_oracle(xt, precision, tol):
     w = synth.nlte_batch(n=3, seed=1)             # 27 cells x 10 ions, L in 20..300
     with _ctx(xt) as ctx:
@@ -64,8 +65,9 @@ def test_batch_uneven_levels_vs_oracle(xt, precision, tol):
     worst = _check(w, pops, ref, tol)
     assert np.all(status & xt.XT_SE_OK)
     assert st["systems"] == 270 and st["singular"] == 0
-    if precision == 1:
-        assert st["fp64_fallbacks"] == 0 and st["max_iter_used"] <= 8
+    if precision >= 1:
+        # FP32 (or TF32 tensor-core) factors refined in FP64 reach the FP64 result
+        assert st["fp64_fallbacks"] == 0 and st["max_iter_used"] <= 8, st
         assert worst < 1e-8
 
 
