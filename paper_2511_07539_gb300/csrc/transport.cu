@@ -1,6 +1,8 @@
 // Packet transport through the homologous Cartesian grid (A2-A6).
 //
-// Three kernels per chunk of packets (Secs. 2.3, 2.3.2 of the paper):
+// Kernels per chunk of packets (Secs. 2.3, 2.3.2 of the paper); in attenuation
+// mode without subdomain rounds the trace kernel emits each packet itself when
+// a lane takes it (no pool round trip), otherwise k_emit fills the pool first:
 //   k_emit     one thread per packet, all lanes doing the same work: emitting
 //              cell from the integer packet quota, position uniform in the
 //              cell, isotropic direction, comoving frequency from the cell's
@@ -107,6 +109,8 @@ struct TraceArgs {
   int64_t* __restrict__ seg_n;        // entries per segment (kept across launches)
   int64_t seg_len;
   unsigned long long* __restrict__ log_overflow;
+  int fused;                          // attenuation without rounds: emit packets in the refill
+  EmitArgs em;                        // (packet p = em.p_begin + pool slot)
 };
 
 struct EscArgs {
@@ -214,99 +218,116 @@ __device__ __forceinline__ void stage(T& dst, const T& src) {
     reinterpret_cast<uint64_t*>(&dst)[k] = reinterpret_cast<const uint64_t*>(&src)[k];
 }
 
+// One packet of the emission: emitting cell from the integer quota, position,
+// direction, comoving and lab frequency, photon number, first resonance cursor
+// and the cell-walk state (td carries the sign of the direction).
+struct EmitOut {
+  int64_t c;
+  int idx[3];
+  double E0, r[3], n[3], nu_cmf, nu_lab, N, tm[3], td[3];
+  int cursor;
+};
+
+__device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTables& trig, int64_t p,
+                                            EmitOut& o) {
+  const Geometry& g = a.g;
+  int64_t lo = 0, hi = g.ncell;           // last c with qoff[c] <= p
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a.qoff[mid] <= p) lo = mid; else hi = mid;
+  }
+  const int64_t c = lo;
+  o.c = c;
+  o.idx[0] = (int)(c % g.nx); o.idx[1] = (int)((c / g.nx) % g.ny); o.idx[2] = (int)(c / ((int64_t)g.nx * g.ny));
+  const double d[3] = {g.dx, g.dy, g.dz};
+  o.E0 = a.Epk[c];
+  uint64_t xu[4], xv[4];
+  draw_raw(a.seed, p, 0, xu);
+  draw_raw(a.seed, p, 1, xv);
+  double uu[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    uu[k] = u01(xu[k]);
+    o.r[k] = (-g.R + o.idx[k] * d[k]) + uu[k] * d[k];
+  }
+  isotropic(trig, u01(xu[3]), xv[0] >> 11, o.n);
+  const double v1 = u01(xv[1]);
+  if (a.emission == XT_EMIT_BAND) {
+    o.nu_cmf = a.nu_lo + v1 * (a.nu_hi - a.nu_lo);
+    int l0 = 0, l1 = a.nline;             // first sorted line with nu <= nu_cmf
+    const long long nb = bits(o.nu_cmf);
+    while (l0 < l1) {
+      const int mid = (l0 + l1) >> 1;
+      if (bits(a.nu_tab[mid]) <= nb) l1 = mid; else l0 = mid + 1;
+    }
+    o.cursor = l0;
+  } else {
+    const double* cdf = a.cdf + row_of(g, o.idx[0], o.idx[1], o.idx[2]) * a.nline;
+    const double x = v1 * a.Lc[c];
+    int l0 = 0, l1 = a.nline;             // first caller line with x < cdf
+    while (l0 < l1) {
+      const int mid = (l0 + l1) >> 1;
+      if (x < cdf[mid]) l1 = mid; else l0 = mid + 1;
+    }
+    const int s = a.sorted_of[l0 < a.nline ? l0 : a.nline - 1];
+    o.nu_cmf = a.nu_tab[s];
+    o.cursor = s + 1;
+  }
+  const double* n = o.n;
+  const double* r = o.r;
+  o.nu_lab = o.nu_cmf / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
+  o.N = a.Eph[c] / o.nu_cmf;                        // E0 / (h nu_cmf)
+  // cell walk from the position inside the cell: the nearest wall along k is
+  // d (1 - u) / n_k ahead (n_k > 0) or u d / |n_k| (n_k < 0); td carries the sign
+  double inv[3];
+  {
+    const double pxy = n[0] * n[1], pall = pxy * n[2];
+    if (fabs(pall) > 1e-280) {
+      const double q = 1.0 / pall;
+      inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) inv[k] = n[k] != 0.0 ? 1.0 / n[k] : 0.0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (n[k] != 0.0) {
+      o.tm[k] = (n[k] > 0.0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
+      o.td[k] = d[k] * inv[k];
+    } else {
+      o.tm[k] = INFINITY;
+      o.td[k] = INFINITY;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
   __shared__ FixTrigTables trig;
   stage(trig, a.trig);
   __syncthreads();
   double acc[2] = {0.0, 0.0};
-  const Geometry& g = a.g;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = a.p_begin + i;
-    int64_t lo = 0, hi = g.ncell;         // last c with qoff[c] <= p
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (a.qoff[mid] <= p) lo = mid; else hi = mid;
-    }
-    const int64_t c = lo;
-    const int idx[3] = {(int)(c % g.nx), (int)((c / g.nx) % g.ny), (int)(c / ((int64_t)g.nx * g.ny))};
-    const double d[3] = {g.dx, g.dy, g.dz};
-    const double E0 = a.Epk[c];
-    uint64_t xu[4], xv[4];
-    draw_raw(a.seed, p, 0, xu);
-    draw_raw(a.seed, p, 1, xv);
-    double r[3], n[3], uu[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      uu[k] = u01(xu[k]);
-      r[k] = (-g.R + idx[k] * d[k]) + uu[k] * d[k];
-    }
-    isotropic(trig, u01(xu[3]), xv[0] >> 11, n);
-    const U4 v{{u01(xv[0]), u01(xv[1]), u01(xv[2]), u01(xv[3])}};
-    double nu_cmf;
-    int cursor;
-    if (a.emission == XT_EMIT_BAND) {
-      nu_cmf = a.nu_lo + v.u[1] * (a.nu_hi - a.nu_lo);
-      int l0 = 0, l1 = a.nline;           // first sorted line with nu <= nu_cmf
-      const long long nb = bits(nu_cmf);
-      while (l0 < l1) {
-        const int mid = (l0 + l1) >> 1;
-        if (bits(a.nu_tab[mid]) <= nb) l1 = mid; else l0 = mid + 1;
-      }
-      cursor = l0;
-    } else {
-      const double* cdf = a.cdf + row_of(g, idx[0], idx[1], idx[2]) * a.nline;
-      const double x = v.u[1] * a.Lc[c];
-      int l0 = 0, l1 = a.nline;           // first caller line with x < cdf
-      while (l0 < l1) {
-        const int mid = (l0 + l1) >> 1;
-        if (x < cdf[mid]) l1 = mid; else l0 = mid + 1;
-      }
-      const int s = a.sorted_of[l0 < a.nline ? l0 : a.nline - 1];
-      nu_cmf = a.nu_tab[s];
-      cursor = s + 1;
-    }
-    const double nu_lab = nu_cmf / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
-    const double N = a.Eph[c] / nu_cmf;                 // E0 / (h nu_cmf)
-    // cell walk from the position inside the cell: the nearest wall along k is
-    // d (1 - u) / n_k ahead (n_k > 0) or u d / |n_k| (n_k < 0); td carries the sign
-    double inv[3];
-    {
-      const double pxy = n[0] * n[1], pall = pxy * n[2];
-      if (fabs(pall) > 1e-280) {
-        const double q = 1.0 / pall;
-        inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) inv[k] = n[k] != 0.0 ? 1.0 / n[k] : 0.0;
-      }
-    }
-    double tm[3], td[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (n[k] != 0.0) {
-        tm[k] = (n[k] > 0.0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
-        td[k] = d[k] * inv[k];
-      } else {
-        tm[k] = INFINITY;
-        td[k] = INFINITY;
-      }
-    }
+    EmitOut o;
+    emit_packet(a, trig, p, o);
     const Pool& P = a.pool;
-    P.F(F_R0X, i) = r[0]; P.F(F_R0Y, i) = r[1]; P.F(F_R0Z, i) = r[2];
-    P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
-    P.F(F_TMX, i) = tm[0]; P.F(F_TMY, i) = tm[1]; P.F(F_TMZ, i) = tm[2];
-    P.F(F_TDX, i) = td[0]; P.F(F_TDY, i) = td[1]; P.F(F_TDZ, i) = td[2];
+    P.F(F_R0X, i) = o.r[0]; P.F(F_R0Y, i) = o.r[1]; P.F(F_R0Z, i) = o.r[2];
+    P.F(F_NX, i) = o.n[0]; P.F(F_NY, i) = o.n[1]; P.F(F_NZ, i) = o.n[2];
+    P.F(F_TMX, i) = o.tm[0]; P.F(F_TMY, i) = o.tm[1]; P.F(F_TMZ, i) = o.tm[2];
+    P.F(F_TDX, i) = o.td[0]; P.F(F_TDY, i) = o.td[1]; P.F(F_TDZ, i) = o.td[2];
     // stop once N nu_line < e_cut E0 / h (the photon energy at the line below e_cut E0)
-    P.F(F_NULAB, i) = nu_lab; P.F(F_NU0, i) = nu_cmf; P.F(F_N, i) = N; P.F(F_T, i) = a.e_cut * a.Eph[c];
-    P.cell[i] = idx[0] | (idx[1] << 10) | (idx[2] << 20);
-    P.cursor[i] = cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
+    P.F(F_NULAB, i) = o.nu_lab; P.F(F_NU0, i) = o.nu_cmf; P.F(F_N, i) = o.N;
+    P.F(F_T, i) = a.e_cut * a.Eph[o.c];
+    P.cell[i] = o.idx[0] | (o.idx[1] << 10) | (o.idx[2] << 20);
+    P.cursor[i] = o.cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
     P.pid[i] = p;
-    acc[0] += N;
-    acc[1] += E0;
+    acc[0] += o.N;
+    acc[1] += o.E0;
     if (a.records) {
       double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
-      rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
+      rec[7] = (double)o.c; rec[8] = o.N; rec[9] = o.nu_cmf;
     }
   }
   const int slots[2] = {LG_EMIT_N, LG_EMIT_E};
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
 
 // ---------------------------------------------------------------- trace
 // Per-lane ledger: integer counters, FP64 sums.
-enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_NACC };
+enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_EMITN, T_EMITE, T_NACC };
 constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
@@ -325,7 +346,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   __shared__ FixTrigTables trig;
   __shared__ int rtab[3 * 1024];
   stage(fx, a.fx);
-  if (MODE == XT_MODE_SCATTER) stage(trig, a.trig);
+  if (MODE == XT_MODE_SCATTER || a.fused) stage(trig, a.trig);
   const int nt = a.g.nx + a.g.ny + a.g.nz;
   for (int k = threadIdx.x; k < nt; k += blockDim.x) rtab[k] = a.rtab[k];
   __syncthreads();
@@ -367,7 +388,39 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         base = __shfl_sync(act, base, leader);
         if (!have) {
           const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
-          if (my < (unsigned long long)a.n_list) {
+          if (my < (unsigned long long)a.n_list && MODE == XT_MODE_ATTEN && a.fused) {
+            // emit the packet here: its state goes to registers; the pool keeps
+            // what the escape tallies read (direction, lab frequency, id)
+            i = (int)my;
+            const int64_t p = a.em.p_begin + (int64_t)my;
+            EmitOut o;
+            emit_packet(a.em, trig, p, o);
+            ix = o.idx[0]; iy = o.idx[1]; iz = o.idx[2];
+            tmx = o.tm[0]; tmy = o.tm[1]; tmz = o.tm[2];
+            sx = o.td[0] < 0.0 ? -1 : 1; sy = o.td[1] < 0.0 ? -1 : 1; sz = o.td[2] < 0.0 ? -1 : 1;
+            tdx = fabs(o.td[0]); tdy = fabs(o.td[1]); tdz = fabs(o.td[2]);
+            nu0 = o.nu_cmf;
+            aslope = o.nu_lab * a.inv_ct;
+            N = o.N;
+            N_in = N;
+            Tq = a.em.e_cut * a.em.Eph[o.c];
+            cursor = o.cursor;
+            events = 0;
+            P.F(F_NX, i) = o.n[0]; P.F(F_NY, i) = o.n[1]; P.F(F_NZ, i) = o.n[2];
+            P.F(F_NULAB, i) = o.nu_lab;
+            P.pid[i] = p;
+            acc[T_EMITN] += o.N;
+            acc[T_EMITE] += o.E0;
+            if (a.records) {
+              P.inter[i] = 0;
+              double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+              rec[7] = (double)o.c; rec[8] = o.N; rec[9] = o.nu_cmf;
+            }
+            rx = RX[ix]; ry = RY[iy]; rz = RZ[iz];
+            row = rx + ry + rz;
+            seg_new = true;
+            have = true;
+          } else if (my < (unsigned long long)a.n_list) {
             i = a.list ? a.list[my] : (int)my;
             const int cs = P.cell[i];
             ix = cs & 1023; iy = (cs >> 10) & 1023; iz = cs >> 20;
@@ -559,7 +612,8 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   double cnt[4] = {(double)n_tests, (double)n_events, (double)n_guard, (double)n_inter};
   const int cslots[4] = {LG_TESTS, LG_EVENTS, LG_GUARD, LG_INTERACT};
   warp_flush(cnt, a.ledger, cslots);
-  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E};
+  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
+                             LG_EMIT_N, LG_EMIT_E};
   warp_flush(acc, a.ledger, slots);
 }
 
@@ -918,6 +972,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   ta.seg_len = c->log_seglen;
   ta.log_overflow = (unsigned long long*)(c->d_seg_n + kLogSegments);
+  // attenuation without subdomain rounds: the trace kernel emits its packets
+  ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds) ? 1 : 0;
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
@@ -930,11 +986,15 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     const int64_t n = std::min(chunk, count - off);
     ea.p_begin = p->packet_begin + off;
     ea.n = n;
-    int sl = tick(0);
-    k_emit<<<blocks_for(n, 256, 16), 256, 0, c->stream>>>(ea);
-    XT_CUDA(c, cudaGetLastError());
-    tock(sl);
-    ++kernels;
+    ta.em = ea;
+    int sl;
+    if (!ta.fused) {
+      sl = tick(0);
+      k_emit<<<blocks_for(n, 256, 16), 256, 0, c->stream>>>(ea);
+      XT_CUDA(c, cudaGetLastError());
+      tock(sl);
+      ++kernels;
+    }
 
     const int* list = nullptr;
     int64_t n_list = n;
