@@ -64,13 +64,14 @@ __device__ __forceinline__ double q63_to_double(uint64_t q, int scale) {
 
 // tau > 0 (finite).  Writes e^-tau and 1 - e^-tau.
 __device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double& ex, double& ome) {
-  if (tau >= 709.0) { ex = 0.0; ome = 1.0; return; }
+  // range tests on the bit pattern (tau > 0: integer order = numeric order)
   const uint64_t bits = (uint64_t)__double_as_longlong(tau);
+  if (bits >= (uint64_t)__double_as_longlong(709.0)) { ex = 0.0; ome = 1.0; return; }
   const int eb = (int)(bits >> 52);                        // biased exponent (tau normal, > 0)
   const uint64_t m = (bits & ((1ull << 52) - 1ull)) | (1ull << 52);
   uint64_t R;                                              // r in Q63
   int k = 0;
-  if (tau < 0.6931471805599453) {
+  if (bits < (uint64_t)__double_as_longlong(0.6931471805599453)) {
     const int sh = eb - 1012;                              // tau 2^63 = m 2^(eb-1012)
     if (sh >= 0) R = m << sh;
     else if (sh > -64) R = (m >> (-sh)) + ((m >> (-sh - 1)) & 1ull);

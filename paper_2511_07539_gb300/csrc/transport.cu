@@ -65,7 +65,8 @@ struct EmitArgs {
   const double* __restrict__ nu_tab;  // sorted
   int nline, emission;
   uint64_t seed;
-  double nu_lo, nu_hi, e_cut;
+  double nu_lo, nu_hi, nu_span, e_cut;   // nu_span = nu_hi - nu_lo
+  const double* __restrict__ wall;    // lower cell walls -R + i d per axis [nx + ny + nz], or null
   int64_t p_begin, n;
   Pool pool;
   double* __restrict__ ledger;
@@ -126,6 +127,9 @@ struct EscArgs {
 };
 
 __device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double dabs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
 
 // 32-byte line record: x = nu, y = K, z = g_l/g_u, w = (lo | up << 32) bit pattern
 struct LineRec { double x, y, z, w; };
@@ -245,15 +249,17 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
   draw_raw(a.seed, p, 0, xu);
   draw_raw(a.seed, p, 1, xv);
   double uu[3];
+  const int woff[3] = {0, g.nx, g.nx + g.ny};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     uu[k] = u01(xu[k]);
-    o.r[k] = (-g.R + o.idx[k] * d[k]) + uu[k] * d[k];
+    const double w0 = a.wall ? a.wall[woff[k] + o.idx[k]] : fma((double)o.idx[k], d[k], -g.R);
+    o.r[k] = w0 + uu[k] * d[k];
   }
   isotropic(trig, u01(xu[3]), xv[0] >> 11, o.n);
   const double v1 = u01(xv[1]);
   if (a.emission == XT_EMIT_BAND) {
-    o.nu_cmf = a.nu_lo + v1 * (a.nu_hi - a.nu_lo);
+    o.nu_cmf = a.nu_lo + v1 * a.nu_span;
     int l0 = 0, l1 = a.nline;             // first sorted line with nu <= nu_cmf
     const long long nb = bits(o.nu_cmf);
     while (l0 < l1) {
@@ -279,21 +285,22 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
   o.N = a.Eph[c] / o.nu_cmf;                        // E0 / (h nu_cmf)
   // cell walk from the position inside the cell: the nearest wall along k is
   // d (1 - u) / n_k ahead (n_k > 0) or u d / |n_k| (n_k < 0); td carries the sign
+  // (sign and zero tests on the bit patterns: the FP64 pipe is the scarce one)
   double inv[3];
   {
     const double pxy = n[0] * n[1], pall = pxy * n[2];
-    if (fabs(pall) > 1e-280) {
+    if ((bits(pall) & 0x7FFFFFFFFFFFFFFFll) > bits(1e-280)) {
       const double q = 1.0 / pall;
       inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
     } else {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) inv[k] = n[k] != 0.0 ? 1.0 / n[k] : 0.0;
+      for (int k = 0; k < 3; ++k) inv[k] = (bits(n[k]) << 1) != 0 ? 1.0 / n[k] : 0.0;
     }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    if (n[k] != 0.0) {
-      o.tm[k] = (n[k] > 0.0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
+    if ((bits(n[k]) << 1) != 0) {
+      o.tm[k] = (bits(n[k]) > 0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
       o.td[k] = d[k] * inv[k];
     } else {
       o.tm[k] = INFINITY;
@@ -397,8 +404,8 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             emit_packet(a.em, trig, p, o);
             ix = o.idx[0]; iy = o.idx[1]; iz = o.idx[2];
             tmx = o.tm[0]; tmy = o.tm[1]; tmz = o.tm[2];
-            sx = o.td[0] < 0.0 ? -1 : 1; sy = o.td[1] < 0.0 ? -1 : 1; sz = o.td[2] < 0.0 ? -1 : 1;
-            tdx = fabs(o.td[0]); tdy = fabs(o.td[1]); tdz = fabs(o.td[2]);
+            sx = bits(o.td[0]) < 0 ? -1 : 1; sy = bits(o.td[1]) < 0 ? -1 : 1; sz = bits(o.td[2]) < 0 ? -1 : 1;
+            tdx = dabs_bits(o.td[0]); tdy = dabs_bits(o.td[1]); tdz = dabs_bits(o.td[2]);
             nu0 = o.nu_cmf;
             aslope = o.nu_lab * a.inv_ct;
             N = o.N;
@@ -426,8 +433,8 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             ix = cs & 1023; iy = (cs >> 10) & 1023; iz = cs >> 20;
             tmx = P.F(F_TMX, i); tmy = P.F(F_TMY, i); tmz = P.F(F_TMZ, i);
             tdx = P.F(F_TDX, i); tdy = P.F(F_TDY, i); tdz = P.F(F_TDZ, i);
-            sx = tdx < 0.0 ? -1 : 1; sy = tdy < 0.0 ? -1 : 1; sz = tdz < 0.0 ? -1 : 1;
-            tdx = fabs(tdx); tdy = fabs(tdy); tdz = fabs(tdz);
+            sx = bits(tdx) < 0 ? -1 : 1; sy = bits(tdy) < 0 ? -1 : 1; sz = bits(tdz) < 0 ? -1 : 1;
+            tdx = dabs_bits(tdx); tdy = dabs_bits(tdy); tdz = dabs_bits(tdz);
             nu0 = P.F(F_NU0, i);
             aslope = P.F(F_NULAB, i) * a.inv_ct;
             N = P.F(F_N, i);
@@ -938,6 +945,21 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ea.seed = p->seed;
   ea.nu_lo = c->band_hi_A > 0 ? kC / (c->band_hi_A * 1e-8) : 0.0;
   ea.nu_hi = c->band_lo_A > 0 ? kC / (c->band_lo_A * 1e-8) : 0.0;
+  ea.nu_span = ea.nu_hi - ea.nu_lo;
+  {
+    // lower wall of every cell index per axis, fma(i, d, -R) as the device computes it
+    std::vector<double> wl(G.nx + G.ny + G.nz);
+    for (int x = 0; x < G.nx; ++x) wl[x] = std::fma((double)x, G.dx, -G.R);
+    for (int y = 0; y < G.ny; ++y) wl[G.nx + y] = std::fma((double)y, G.dy, -G.R);
+    for (int z = 0; z < G.nz; ++z) wl[G.nx + G.ny + z] = std::fma((double)z, G.dz, -G.R);
+    if (c->wall_n != (int64_t)wl.size()) {
+      c->wall_n = 0;
+      if ((rc = alloc(c, (void**)&c->d_wall, wl.size() * sizeof(double), "wall table"))) return rc;
+      c->wall_n = (int64_t)wl.size();
+    }
+    if ((rc = copy(c, c->d_wall, wl.data(), wl.size() * sizeof(double), "wall table"))) return rc;
+  }
+  ea.wall = c->d_wall;
   ea.e_cut = p->e_cut; ea.pool = P; ea.ledger = c->d_ledger; ea.records = d_rec;
   ea.rec_base = p->packet_begin;
   fixtrig_tables(&ea.trig);
@@ -960,7 +982,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     for (int y = 0; y < G.ny; ++y) rt[G.nx + y] = (y / G.by) * G.sx * B + (y % G.by) * G.bx;
     for (int z = 0; z < G.nz; ++z)
       rt[G.nx + G.ny + z] = (z / G.bz) * G.sy * G.sx * B + (z % G.bz) * G.by * G.bx;
-    if ((rc = alloc(c, (void**)&c->d_rtab, rt.size() * sizeof(int), "row tables"))) return rc;
+    if (c->rtab_n != (int64_t)rt.size()) {
+      c->rtab_n = 0;
+      if ((rc = alloc(c, (void**)&c->d_rtab, rt.size() * sizeof(int), "row tables"))) return rc;
+      c->rtab_n = (int64_t)rt.size();
+    }
     if ((rc = copy(c, c->d_rtab, rt.data(), rt.size() * sizeof(int), "row tables"))) return rc;
   }
   ta.rtab = c->d_rtab;
@@ -1330,6 +1356,7 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
   ea.Eph = cellE + 2 * ncell; ea.cdf = nullptr; ea.sorted_of = (const int*)(B + kNaSorted);
   ea.nu_tab = (const double*)(B + kNaNu); ea.nline = nl; ea.emission = XT_EMIT_BAND; ea.seed = a->seed;
   ea.nu_lo = kC / (a->band_hi_A * 1e-8); ea.nu_hi = kC / (a->band_lo_A * 1e-8); ea.e_cut = a->e_cut;
+  ea.nu_span = ea.nu_hi - ea.nu_lo; ea.wall = nullptr;
   ea.pool = P; ea.ledger = ledger; ea.records = nullptr; ea.rec_base = 0;
   fixtrig_tables(&ea.trig);
   TraceArgs ta{};

@@ -109,6 +109,8 @@ struct xt_ctx {
   double* d_ledger = nullptr;        // [LG_N]
   double* d_lines = nullptr;         // [sorted line] packed nu, K, gratio, (lo, up): 32 B
   int* d_rtab = nullptr;             // separable blocked-row offsets [nx + ny + nz]
+  double* d_wall = nullptr;          // lower cell walls per axis [nx + ny + nz]
+  int64_t rtab_n = 0, wall_n = 0;    // their lengths (reallocated when the grid changes)
   // touched-slot log: every estimator slot written by the last pass, so the
   // next pass clears those slots instead of the whole store
   int64_t* d_slotlog = nullptr;
