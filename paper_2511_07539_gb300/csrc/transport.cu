@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
 // Per-lane ledger: integer counters, FP64 sums.
 enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_EMITN, T_EMITE, T_NACC };
 constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
+constexpr int kRefillLanes = 24;  // empty lanes of a warp that trigger a refill with emission
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
 template <int MODE>
@@ -383,16 +384,24 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   double tmx = 0, tmy = 0, tmz = 0, tdx = 0, tdy = 0, tdz = 0, nu0 = 0, aslope = 0;
   double N = 0, N_in = 0, Tq = 0;
 
+  bool drained = false;                  // the packet list is used up (warp-uniform)
   for (;;) {
-    // ---- refill lanes whose packet ended (warp-aggregated)
+    // ---- refill lanes whose packet ended (warp-aggregated).  The loop runs
+    // warp-synchronously: with emission in the refill (FP64-heavy) the empty
+    // lanes are refilled together, once at least kRefillLanes are empty, so
+    // the emission runs with most lanes; busy lanes trace on meanwhile.
+    __syncwarp();
     {
-      const unsigned act = __activemask();
-      const unsigned m = __ballot_sync(act, !have);
+      const unsigned act = 0xffffffffu;
+      const unsigned m0 = __ballot_sync(act, !have);
+      if (m0 == act && drained) break;
+      const unsigned m = (drained || (a.fused && m0 != act && __popc(m0) < kRefillLanes)) ? 0u : m0;
       if (m) {
         const int leader = __ffs(m) - 1;
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(m));
         base = __shfl_sync(act, base, leader);
+        if (base + __popc(m) >= (unsigned long long)a.n_list) drained = true;
         if (!have) {
           const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
           if (my < (unsigned long long)a.n_list && MODE == XT_MODE_ATTEN && a.fused) {
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         }
       }
     }
-    if (!have) break;
+    if (!have) continue;
 
     // ---- search: test lines and walk cells until an interaction point is met,
     // the packet leaves the grid or its subdomain, or kMaxSteps walls are crossed
