@@ -10,7 +10,8 @@ P2  optically thin line profile of the voxelised sphere vs the hat-box
     projection integrated by quadrature.
 P3  optically thin estimator in a cell slab vs a 6-D quadrature of the
     mean-intensity integral.
-P6  photon ledger closure; comoving energy closure in scatter mode.
+P6  photon ledger closure; comoving energy closure in scatter mode; the
+    scatter-mode destruction probability of a single line.
 """
 import os
 
@@ -311,3 +312,32 @@ def test_ledgers_close():
     Ls = oracle.transport(w, mode="scatter")["ledger"]
     assert Ls["interactions"] > 1000
     assert (Ls["reemit_E_cmf"] + Ls["thermal_E"]) == pytest.approx(Ls["abs_E_cmf"], rel=1e-13)
+
+
+def test_scatter_channel_probability():
+    """Scatter mode, one line: an interaction destroys the packet with
+    probability C_ul / (C_ul + A_ul beta_S) and re-emits it in the line
+    otherwise.  In a uniform sphere every cell has the same C, A and beta, so
+    the destroyed fraction of all interactions is that probability within its
+    binomial error (C and A beta written out from their definitions)."""
+    w = synth.single_line_sphere(n=8, n_packets=60_000, f_lu=3e-3, n_scale=1.0)
+    o = oracle.transport(w, mode="scatter", per_packet=True)
+    pk = o["pkt"]
+    fate, inter = pk[:, 0], pk[:, 6]
+    n_int = float(inter.sum())
+    n_destroyed = float((fate == 2).sum())
+    c = int(np.nonzero(w.rho > 0)[0][0])
+    g_l, g_u = w.g_level[0], w.g_level[1]
+    n_l, n_u = w.pops[c, 0], w.pops[c, 1]
+    lam = w.lambda_A[0] * 1e-8
+    A = 8 * np.pi ** 2 * 4.80320471e-10 ** 2 / (9.1093837015e-28 * 2.99792458e10 * lam ** 2) * (g_l / g_u) * w.f_lu[0]
+    K = np.pi * 4.80320471e-10 ** 2 / (9.1093837015e-28 * 2.99792458e10) * w.f_lu[0] * lam * w.t
+    tau = K * (n_l - g_l / g_u * n_u)
+    beta = -np.expm1(-tau) / tau
+    ups = synth.collision_strengths(w.upsilon_seed, w.level_off)[0][0, 1]
+    C = 8.629e-6 * w.ne[c] * ups / (g_u * np.sqrt(w.Te[c]))
+    p = C / (C + A * beta)
+    assert tau > 1.0 and 0.05 < p < 0.95, (tau, p)
+    assert n_int > 2000
+    sigma = np.sqrt(p * (1 - p) / n_int)
+    assert abs(n_destroyed / n_int - p) < 4 * sigma, (n_destroyed / n_int, p, sigma)
