@@ -117,3 +117,30 @@ def test_graph_replay_and_autotune_match(xt):
             m = base > 0
             assert np.max(np.abs(out[m] / base[m] - 1)) < 1e-9
             assert all(nb in (8, 16, 32) for nb in st["panel_width"])
+
+
+def test_full_batch_sampled_vs_oracle(xt):
+    """The batched solve at its full size (64^3 cells x 10 ions = 2.6e6 systems
+    of 20-300 levels) in the launch the benchmark times (graph replay,
+    autotuned panel widths, FP32 factors refined in FP64): 60 systems drawn
+    across the level range match the FP64 oracle within 1e-6."""
+    w = synth.nlte_batch(n=64)
+    kw = dict(rates=xt.XT_RATES_JBAR, warm=xt.XT_WARM_CURRENT, jbar_W=w.jbar_W,
+              jbar_TR=w.jbar_TR, levels_used=w.levels_used)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, autotune=True,
+                      use_graph=True, **kw)
+        xt.set_populations(ctx.h, w.pops)
+        pops = np.zeros((w.ncell, w.nlev))
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, use_graph=True,
+                           pops_out=pops, **kw)
+    assert st["systems"] == w.ncell * w.n_ion and st["singular"] == 0
+    rng = np.random.default_rng(11)
+    cells = rng.choice(w.ncell, 60, replace=False)
+    ref = {}
+    for c in cells:
+        z = int(rng.integers(0, w.n_ion))
+        P, n_z, v = nlte.system(w, int(c), z)
+        ref[(int(c), z)] = (nlte.solve_se(P, n_z), v)
+    assert _check(w, pops, ref, 1e-6) < 1e-8
