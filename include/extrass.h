@@ -142,6 +142,21 @@ typedef struct {
 
 int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);
 
+/* Where the estimator store lives (Sec. 2.4.1: the photoexcitation store is
+ * split by domain because the whole of it does not fit in one node's memory).
+ * host_groups = 0 (default): on the device, ncell * nline doubles.  host_groups
+ * = G > 0: in pinned host memory, in G groups of sz/G subdomain layers along z
+ * (whole x-y layers of nz/G cells; G must divide sz); the device holds one
+ * group's slab (ncell * nline / G doubles) at a time.  run_transport then
+ * traces in rounds: every group with packets is staged (its slab from host
+ * memory, zeros on its first visit in a pass), its packets traced until they
+ * leave the group, escape or end, and the slab written back; trajectories and
+ * results are those of the device-resident store.  get_estimators and
+ * get_photoexcitation_rates stage the groups they read; solve_nlte and
+ * train_surrogate with estimator rates return XT_ESTATE for a host-held store.
+ * Frees the current store (host and device); the next run_transport allocates. */
+int set_estimator_store(xt_ctx *ctx, int32_t host_groups);
+
 /* Raw estimators S [n_cells][nline] (photons/s absorbed, divided by f_corr),
  * cells [cell_begin, +n_cells), caller line order. */
 int get_estimators(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *S);

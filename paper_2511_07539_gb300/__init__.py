@@ -171,6 +171,7 @@ def lib():
             "surrogate_predict": ([vp, vp, i64, vp], C.c_int),
             "train_surrogate": ([vp, vp, vp], C.c_int),
             "run_coupled": ([vp, vp, vp], C.c_int),
+            "set_estimator_store": ([vp, i32], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -272,6 +273,12 @@ def get_sobolev_tau(ctx, cell_begin=0, n_cells=None, tau=None, beta=None, want_b
         beta = np.zeros((n_cells, sz["nline"]))
     _check(ctx, lib().get_sobolev_tau(ctx, cell_begin, n_cells, _ptr(tau), _ptr(beta)))
     return tau, beta
+
+
+def set_estimator_store(ctx, host_groups=0):
+    """Device-resident store (0) or a pinned host store in host_groups groups of
+    subdomain z-layers, one group staged on the device at a time."""
+    _check(ctx, lib().set_estimator_store(ctx, int(host_groups)))
 
 
 def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=XT_MODE_ATTEN,
@@ -523,4 +530,4 @@ class Context:
 
 _CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations", "solve_nlte",
               "get_sobolev_tau", "run_transport", "get_estimators", "get_photoexcitation_rates",
-              "get_spectrum", "get_sizes", "run_coupled"}
+              "get_spectrum", "get_sizes", "run_coupled", "set_estimator_store"}

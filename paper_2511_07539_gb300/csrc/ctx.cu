@@ -321,6 +321,8 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_pool_f, (void**)&c->d_pool_i, (void**)&c->d_pool_pid,
                    (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_slotlog, (void**)&c->d_seg_n};
   for (void** p : ptrs) release(p);
+  if (c->h_S) cudaFreeHost(c->h_S);
+  c->h_S = nullptr;
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->ev2) cudaEventDestroy(c->ev2);
@@ -568,6 +570,34 @@ int get_sobolev_tau(xt_ctx* c, int64_t c0, int64_t nc, double* tau, double* beta
 static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int which) {
   LineTable L = line_table(c);
   double V = c->geo.dx * c->geo.dy * c->geo.dz;
+  if (c->S_groups > 0) {
+    // host-held store: a group's cells are a contiguous natural range (whole
+    // x-y layers) and its rows a contiguous slab; stage each group the range
+    // touches on the device and read it with the slab's rows offset
+    const Geometry& G = c->geo;
+    const int NG = c->S_groups;
+    const int64_t cells_g = G.ncell / NG;
+    const size_t slab_n = (size_t)cells_g * c->nline;
+    int rc;
+    for (int g = (int)(c0 / cells_g); g < NG && (int64_t)g * cells_g < c0 + nc; ++g) {
+      const int64_t a = std::max<int64_t>(c0, (int64_t)g * cells_g);
+      const int64_t b = std::min<int64_t>(c0 + nc, (int64_t)(g + 1) * cells_g);
+      if (c->S_valid.size() == (size_t)NG && c->S_valid[g])
+        XT_CUDA(c, cudaMemcpyAsync(c->d_S, c->h_S + (size_t)g * slab_n, slab_n * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+      else
+        XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, slab_n * sizeof(double), c->stream));
+      const double* Sg = c->d_S - (int64_t)g * (int64_t)slab_n;   // row r of the slab at S + r nline
+      double* o = out + (size_t)(a - c0) * c->nline;
+      const int64_t n = (b - a) * c->nline;
+      rc = deliver(c, o, (size_t)n * sizeof(double), [&](void* d) {
+        k_rates<<<grid_blocks(n, 256), 256, 0, c->stream>>>(G, L, c->d_pops, Sg, c->d_invB, c->d_orig, a, b - a, V, which, (double*)d);
+      });
+      if (rc) return rc;
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return XT_OK;
+  }
   size_t bytes = (size_t)nc * c->nline * sizeof(double);
   int64_t n = nc * c->nline;
   int rc = deliver(c, out, bytes, [&](void* d) {
@@ -575,6 +605,29 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
   });
   if (rc) return rc;
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
+int set_estimator_store(xt_ctx* c, int32_t host_groups) {
+  if (!c) return XT_EINVAL;
+  if (!c->have_grid || !c->have_atoms) return fail(c, XT_ESTATE, "set_estimator_store: init_grid and load_atomic_data first");
+  if (host_groups < 0) return fail(c, XT_EINVAL, "set_estimator_store: host_groups >= 0");
+  if (host_groups > 0 && (c->sz % host_groups != 0))
+    return fail(c, XT_EINVAL, "set_estimator_store: host_groups must divide the subdomains along z (" +
+                                  std::to_string(c->sz) + ")");
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  release((void**)&c->d_S);
+  c->S_bytes = 0;
+  if (c->h_S) cudaFreeHost(c->h_S);
+  c->h_S = nullptr;
+  c->h_S_bytes = 0;
+  c->S_valid.clear();
+  c->S_groups = host_groups;
+  c->have_S = false;
+  c->slotlog_valid = true;
+  c->slotlog_n = 0;
+  c->log_nseg = 0;
   return XT_OK;
 }
 

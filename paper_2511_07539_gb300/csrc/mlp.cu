@@ -654,6 +654,7 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   if (!c || !p) return fail(c, XT_EINVAL, "train_surrogate: null argument");
   if (!c->have_pops || !c->d_nion) return fail(c, XT_ESTATE, "train_surrogate: populations and n_ion_density needed");
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S) return fail(c, XT_ESTATE, "train_surrogate: no estimators for these populations");
+  if (p->rates == XT_RATES_ESTIMATORS && c->S_groups > 0) return fail(c, XT_ESTATE, "train_surrogate: estimator inputs from a host-held store are not supported");
   if (p->epochs < 0 || p->batch < 1 || !(p->lr > 0)) return fail(c, XT_EINVAL, "train_surrogate: epochs >= 0, batch >= 1, lr > 0");
   cudaSetDevice(c->device);
   const int nin = 3 + c->n_ion * (kJbarBins + 1), nout = c->nlev;

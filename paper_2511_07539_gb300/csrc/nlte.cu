@@ -704,6 +704,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (c->n_ion > 16) return fail(c, XT_EINVAL, "solve_nlte: at most 16 ions");
   if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR && p->precision != XT_PREC_TF32_IR)
     return fail(c, XT_EINVAL, "solve_nlte: precision");
+  if (p->rates == XT_RATES_ESTIMATORS && c->S_groups > 0)
+    return fail(c, XT_ESTATE, "solve_nlte: estimator rates from a host-held store are not supported (read them with get_photoexcitation_rates)");
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S)
     return fail(c, XT_ESTATE, "solve_nlte: estimator rates need a transport pass with the current populations");
   if (p->rates == XT_RATES_JBAR && !(p->jbar_W > 0 && p->jbar_TR > 0)) return fail(c, XT_EINVAL, "solve_nlte: jbar_W, jbar_TR > 0");

@@ -112,6 +112,8 @@ struct TraceArgs {
   unsigned long long* __restrict__ log_overflow;
   int fused;                          // attenuation without rounds: emit packets in the refill
   EmitArgs em;                        // (packet p = em.p_begin + pool slot)
+  int64_t row0;                       // first row held by S (a streamed group's slab; else 0)
+  int grp_nz;                         // rounds == 2: cells along z per streamed group
 };
 
 struct EscArgs {
@@ -453,10 +455,14 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             events = P.events[i];
             rx = RX[ix]; ry = RY[iy]; rz = RZ[iz];
             row = rx + ry + rz;
-            if (a.rounds) {
+            if (a.rounds == 2) {          // a streamed group: whole x-y layers of z cells
+              const int z0 = (iz / a.grp_nz) * a.grp_nz;
+              box_lo = z0 << 20;
+              box_hi = (g.nx - 1) | ((g.ny - 1) << 10) | ((z0 + a.grp_nz - 1) << 20);
+            } else if (a.rounds) {        // the packet's subdomain (bounds inclusive)
               const int x0 = (ix / g.bx) * g.bx, y0 = (iy / g.by) * g.by, z0 = (iz / g.bz) * g.bz;
               box_lo = x0 | (y0 << 10) | (z0 << 20);
-              box_hi = (x0 + g.bx) | ((y0 + g.by) << 10) | ((z0 + g.bz) << 20);
+              box_hi = (x0 + g.bx - 1) | ((y0 + g.by - 1) << 10) | ((z0 + g.bz - 1) << 20);
             }
             seg_new = true;
             have = true;
@@ -507,9 +513,9 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       rx = a0 ? rnew : rx; ry = a1 ? rnew : ry; rz = a2 ? rnew : rz;
       row = rx + ry + rz;
       prow = a.pops + (int64_t)row * a.nlev;
-      if (a.rounds && (ix < (box_lo & 1023) || ix >= (box_hi & 1023) ||
-                       iy < ((box_lo >> 10) & 1023) || iy >= ((box_hi >> 10) & 1023) ||
-                       iz < (box_lo >> 20) || iz >= (box_hi >> 20))) {
+      if (a.rounds && (ix < (box_lo & 1023) || ix > (box_hi & 1023) ||
+                       iy < ((box_lo >> 10) & 1023) || iy > ((box_hi >> 10) & 1023) ||
+                       iz < (box_lo >> 20) || iz > (box_hi >> 20))) {
         queued = true;
         break;
       }
@@ -525,7 +531,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       double ex, ome;
       expneg(fx, tau, ex, ome);
       if (MODE == XT_MODE_ATTEN) {
-        atomicAdd(a.S + (int64_t)row * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
+        atomicAdd(a.S + (int64_t)(row - a.row0) * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
         N = N * ex;
         if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
         ++cursor;
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
-          atomicAdd(a.S + (int64_t)row * a.nline + cursor, N);
+          atomicAdd(a.S + (int64_t)(row - a.row0) * a.nline + cursor, N);
           acc[T_ABS] += N;                    // the whole packet is absorbed
           const double Ecmf = N * kH * L.x;
           acc[T_ABSE] += Ecmf;
@@ -683,6 +689,23 @@ __global__ void k_sd_hist(Geometry g, const int* __restrict__ cell, const int* _
   }
 }
 
+// streamed groups: key = the group of the packet's cell (grp_nz cells along z per group)
+__global__ void k_grp_hist(const int* __restrict__ cell, const int* __restrict__ q, int64_t n, int grp_nz,
+                           int* __restrict__ key, unsigned* __restrict__ hist) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (cell[q ? q[j] : j] >> 20) / grp_nz;
+    key[j] = g;
+    atomicAdd(hist + g, 1u);
+  }
+}
+
+__global__ void k_iota(int* __restrict__ out, int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = (int)j;
+}
+
 __global__ void k_sd_scatter(const int* __restrict__ q, const int* __restrict__ key, int64_t n,
                              unsigned* __restrict__ fill, int* __restrict__ out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
@@ -800,9 +823,32 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (G.ncell >= (int64_t)1 << 31) return fail(c, XT_EINVAL, "run_transport: more than 2^31 cells");
   if (G.nx > 1024 || G.ny > 1024 || G.nz > 1024) return fail(c, XT_EINVAL, "run_transport: more than 1024 cells along an axis");
   int rc;
-  // estimator store
+  // estimator store: on the device, or (host groups) in pinned host memory with
+  // one group's slab on the device at a time
+  const bool host_store = c->S_groups > 0;
+  const int NG = host_store ? c->S_groups : 1;
   const size_t Sb = (size_t)G.ncell * c->nline * sizeof(double);
-  if (!c->d_S || c->S_bytes != Sb) {
+  const size_t slab_b = Sb / NG;
+  if (host_store) {
+    if (!c->d_S || c->S_bytes != slab_b) {
+      if ((rc = alloc(c, (void**)&c->d_S, slab_b, "estimator slab"))) return rc;
+      c->S_bytes = slab_b;
+    }
+    if (c->h_S_bytes != Sb) {
+      if (c->h_S) cudaFreeHost(c->h_S);
+      c->h_S = nullptr;
+      c->h_S_bytes = 0;
+      const cudaError_t e = cudaHostAlloc((void**)&c->h_S, Sb, cudaHostAllocDefault);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->h_S = nullptr;
+        return fail(c, XT_ENOMEM, "run_transport: pinned host estimator store (" + std::to_string(Sb) + " bytes)");
+      }
+      c->h_S_bytes = Sb;
+      c->S_valid.assign(NG, 0);
+    }
+    if (!p->accumulate) c->S_valid.assign(NG, 0);   // every group starts at zero
+  } else if (!c->d_S || c->S_bytes != Sb) {
     if ((rc = alloc(c, (void**)&c->d_S, Sb, "estimator store"))) return rc;
     c->S_bytes = Sb;
     XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, Sb, c->stream));
@@ -910,7 +956,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   // touched-slot log) when the log is complete, else the whole store.
   int kernels_clear = 0;
   if (!p->accumulate) {
-    if (c->slotlog_valid) {
+    if (host_store) {
+      // groups are zeroed when first staged
+    } else if (c->slotlog_valid) {
       if (c->slotlog_n > 0) {
         k_unlog<<<c->log_nseg, 256, 0, c->stream>>>(c->d_S, c->d_slotlog, c->d_seg_n, c->log_seglen);
         XT_CUDA(c, cudaGetLastError());
@@ -1008,7 +1056,10 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.seg_len = c->log_seglen;
   ta.log_overflow = (unsigned long long*)(c->d_seg_n + kLogSegments);
   // attenuation without subdomain rounds: the trace kernel emits its packets
-  ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds) ? 1 : 0;
+  ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds && !host_store) ? 1 : 0;
+  ta.row0 = 0;
+  ta.grp_nz = G.nz / NG;
+  if (host_store) ta.rounds = 2;
 
   EscArgs xa;
   xa.pool = P; xa.esc = esc; xa.spec = c->d_spec; xa.n_theta = p->n_theta; xa.n_phi = p->n_phi;
@@ -1031,6 +1082,76 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ++kernels;
     }
 
+    if (host_store) {
+      // streamed groups: the chunk's packets sorted by group; each round stages
+      // every group with packets (its slab from host memory, or zeros on its
+      // first visit of the pass), traces them until they leave the group,
+      // escape or end, and writes the slab back; packets that left a group
+      // are sorted again for the next round
+      const int64_t rows_g = G.ncell / NG;
+      const size_t slab_n = (size_t)rows_g * c->nline;
+      k_iota<<<blocks_for(n, 256, 8), 256, 0, c->stream>>>(qA, n);
+      XT_CUDA(c, cudaGetLastError());
+      ++kernels;
+      const int* list = qA;
+      int64_t n_list = n;
+      for (int round = 0; n_list > 0; ++round) {
+        if (round >= max_rounds) return fail(c, XT_ETIMEOUT, "run_transport: streamed rounds did not drain");
+        int* sorted = (list == qA) ? qB : qA;
+        int* outq = (list == qA) ? qA : qB;        // `list` is consumed by the sort
+        XT_CUDA(c, cudaMemsetAsync(hist, 0, (size_t)NG * sizeof(unsigned), c->stream));
+        k_grp_hist<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(P.cell, list, n_list, ta.grp_nz, key, hist);
+        XT_CUDA(c, cudaGetLastError());
+        std::vector<unsigned> h(NG), start(NG);
+        XT_CUDA(c, cudaMemcpyAsync(h.data(), hist, NG * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        XT_CUDA(c, cudaStreamSynchronize(c->stream));
+        unsigned run = 0;
+        for (int g = 0; g < NG; ++g) { start[g] = run; run += h[g]; }
+        XT_CUDA(c, cudaMemcpyAsync(hist + NG, start.data(), NG * sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+        k_sd_scatter<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(list, key, n_list, hist + NG, sorted);
+        XT_CUDA(c, cudaGetLastError());
+        kernels += 2;
+        XT_CUDA(c, cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), c->stream));
+        unsigned long long cnt[4] = {0, 0, 0, 0};
+        for (int g = 0; g < NG; ++g) {
+          if (h[g] == 0) continue;
+          double* hs = c->h_S + (size_t)g * slab_n;
+          if (c->S_valid[g]) XT_CUDA(c, cudaMemcpyAsync(c->d_S, hs, slab_b, cudaMemcpyHostToDevice, c->stream));
+          else XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, slab_b, c->stream));
+          XT_CUDA(c, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), c->stream));
+          ta.list = sorted + start[g];
+          ta.n_list = h[g];
+          ta.out = outq;
+          ta.row0 = (int64_t)g * rows_g;
+          const int grid = (int)std::min<int64_t>(grid_max, ((int64_t)h[g] + 255) / 256);
+          sl = tick(1);
+          if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+          else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
+          XT_CUDA(c, cudaGetLastError());
+          tock(sl);
+          ++kernels;
+          XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+          XT_CUDA(c, cudaStreamSynchronize(c->stream));
+          ++rounds;
+          if (cnt[1] > 0) {
+            xa.n_esc = (int64_t)cnt[1];
+            sl = tick(2);
+            k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
+            XT_CUDA(c, cudaGetLastError());
+            tock(sl);
+            ++kernels;
+          }
+          XT_CUDA(c, cudaMemcpyAsync(hs, c->d_S, slab_b, cudaMemcpyDeviceToHost, c->stream));
+          c->S_valid[g] = 1;
+        }
+        ta.row0 = 0;
+        n_list = (int64_t)cnt[2];
+        queued_total += n_list;
+        list = outq;
+      }
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+      continue;
+    }
     const int* list = nullptr;
     int64_t n_list = n;
     for (int round = 0; n_list > 0; ++round) {
@@ -1090,7 +1211,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_S = true;
   c->slotlog_n += (int64_t)led[LG_EVENTS] + 1;      // nonzero once anything was logged
-  if (nover > 0) {
+  if (nover > 0 && !host_store) {
     // a segment overflowed: the next pass clears the whole store; grow the log
     c->slotlog_valid = false;
     const int64_t want = std::min<int64_t>(4 * c->slotlog_cap, (int64_t)1 << 31);

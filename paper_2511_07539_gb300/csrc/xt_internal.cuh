@@ -91,8 +91,12 @@ struct xt_ctx {
   // state
   bool have_pops = false;
   double* d_pops = nullptr;          // [row][nlev]
-  double* d_S = nullptr;             // [row][sorted line]
+  double* d_S = nullptr;             // [row][sorted line] (host groups: one group's slab)
   size_t S_bytes = 0;
+  int S_groups = 0;                  // > 0: the store lives in pinned host memory in this
+  double* h_S = nullptr;             //   many groups of subdomain z-layers (rows contiguous)
+  size_t h_S_bytes = 0;
+  std::vector<char> S_valid;         // group written by the current pass (else all zero)
   bool have_S = false;
   // emission
   int64_t* d_qoff = nullptr;         // natural order [ncell+1]

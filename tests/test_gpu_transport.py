@@ -269,3 +269,33 @@ def test_consecutive_passes_clear_the_store(xt):
             if k == 0:
                 assert st["events"] > 4.4e6
             _cmp_sparse(S, o["S"], S_TOL, f"pass with seed {seed}")
+
+
+def test_host_streamed_store_matches_device_store(xt):
+    """The estimator store held in host memory in 2 and 4 groups of subdomain
+    z-layers (one group on the device at a time, packets traced group by group
+    in rounds) gives the estimators, rates, spectrum and ledger of the
+    device-resident store, on two passes in a row and after switching back."""
+    w = synth.clumpy_onion(seed=2, n=16, n_packets=200_000, n_lines=2000, level_range=(20, 50),
+                           subdomains=(2, 2, 4))
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st0 = ctx.transport(w)
+        S0 = ctx.get_estimators()
+        R0 = ctx.get_photoexcitation_rates(want=("R_lu",))[0]
+        spec0 = ctx.get_spectrum(0)
+        assert st0["events"] > 10_000
+        for groups in (2, 4, 0):
+            xt.set_estimator_store(ctx.h, groups)
+            for _ in range(2):
+                st = ctx.transport(w)
+                assert st["events"] == st0["events"] and st["tests"] == st0["tests"]
+                assert st["escaped_N"] == pytest.approx(st0["escaped_N"], rel=1e-12)
+                if groups:
+                    assert st["rounds"] >= groups
+                _cmp_sparse(ctx.get_estimators(), S0, S_TOL, f"estimators, {groups} groups")
+                _cmp_sparse(ctx.get_photoexcitation_rates(want=("R_lu",))[0], R0, S_TOL, "rates")
+                _cmp_sparse(ctx.get_spectrum(0), spec0, SPEC_TOL, "spectrum")
+            # a cell range that spans two groups
+            part = ctx.get_estimators(1000, 3000)
+            _cmp_sparse(part, S0[1000:4000], S_TOL, "estimator range")
