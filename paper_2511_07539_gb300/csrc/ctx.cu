@@ -319,7 +319,7 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_qoff, (void**)&c->d_Lc, (void**)&c->d_wline, (void**)&c->d_spec,
                    (void**)&c->d_ledger, (void**)&c->d_scratch, (void**)&c->d_lines,
                    (void**)&c->d_pool_f, (void**)&c->d_pool_i, (void**)&c->d_pool_pid,
-                   (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_slotlog, (void**)&c->d_seg_n};
+                   (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;

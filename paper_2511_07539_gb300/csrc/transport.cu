@@ -700,6 +700,19 @@ __global__ void k_grp_hist(const int* __restrict__ cell, const int* __restrict__
   }
 }
 
+// Packets that left a streamed group: those now in group `next` go to `carry`
+// (traced later in the same sweep), the others to `pend` (the next sweep).
+__global__ void k_grp_split(const int* __restrict__ cell, const int* __restrict__ q, int64_t n, int grp_nz,
+                            int next, int* __restrict__ carry, unsigned long long* __restrict__ n_carry,
+                            int* __restrict__ pend, unsigned long long* __restrict__ n_pend) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int i = q[j];
+    if ((cell[i] >> 20) / grp_nz == next) carry[atomicAdd(n_carry, 1ull)] = i;
+    else pend[atomicAdd(n_pend, 1ull)] = i;
+  }
+}
+
 __global__ void k_iota(int* __restrict__ out, int64_t n) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x)
@@ -917,6 +930,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
   if ((rc = ensure_buffers(c, chunk, nsd))) return rc;
   const int64_t cap = c->pool_cap;
+  if (host_store && c->stream_q_cap < cap) {      // out, carry in, carry out queues
+    c->stream_q_cap = 0;
+    if ((rc = alloc(c, (void**)&c->d_stream_q, (size_t)cap * 3 * sizeof(int), "group queues"))) return rc;
+    c->stream_q_cap = cap;
+  }
   int* const I = c->d_pool_i;
   Pool P;
   P.cap = cap; P.f = c->d_pool_f;
@@ -1083,24 +1101,28 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     }
 
     if (host_store) {
-      // streamed groups: the chunk's packets sorted by group; each round stages
-      // every group with packets (its slab from host memory, or zeros on its
-      // first visit of the pass), traces them until they leave the group,
-      // escape or end, and writes the slab back; packets that left a group
-      // are sorted again for the next round
+      // streamed groups, in sweeps over the groups alternately up and down in
+      // z: each group's slab is staged (from host memory, or zeros on its
+      // first visit in the pass), its pending packets traced, then the packets
+      // that entered it from the previous group of the sweep; packets leaving
+      // into the next group of the sweep follow it, the others wait for the
+      // next sweep (a straight path needs at most two sweeps).  The slab is
+      // written back after each visit.
       const int64_t rows_g = G.ncell / NG;
       const size_t slab_n = (size_t)rows_g * c->nline;
+      int* const out_tmp = c->d_stream_q;
+      int* carry_in = c->d_stream_q + cap;
+      int* carry_out = c->d_stream_q + 2 * cap;
       k_iota<<<blocks_for(n, 256, 8), 256, 0, c->stream>>>(qA, n);
       XT_CUDA(c, cudaGetLastError());
       ++kernels;
-      const int* list = qA;
-      int64_t n_list = n;
-      for (int round = 0; n_list > 0; ++round) {
-        if (round >= max_rounds) return fail(c, XT_ETIMEOUT, "run_transport: streamed rounds did not drain");
-        int* sorted = (list == qA) ? qB : qA;
-        int* outq = (list == qA) ? qA : qB;        // `list` is consumed by the sort
+      int64_t n_pend = n;
+      int dir = 1;
+      for (int sweep = 0; n_pend > 0; ++sweep, dir = -dir) {
+        if (sweep >= max_rounds) return fail(c, XT_ETIMEOUT, "run_transport: streamed sweeps did not drain");
+        // pending packets (in qA) sorted by group into qB; qA then collects the next sweep's
         XT_CUDA(c, cudaMemsetAsync(hist, 0, (size_t)NG * sizeof(unsigned), c->stream));
-        k_grp_hist<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(P.cell, list, n_list, ta.grp_nz, key, hist);
+        k_grp_hist<<<blocks_for(n_pend, 256, 8), 256, 0, c->stream>>>(P.cell, qA, n_pend, ta.grp_nz, key, hist);
         XT_CUDA(c, cudaGetLastError());
         std::vector<unsigned> h(NG), start(NG);
         XT_CUDA(c, cudaMemcpyAsync(h.data(), hist, NG * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -1108,46 +1130,69 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
         unsigned run = 0;
         for (int g = 0; g < NG; ++g) { start[g] = run; run += h[g]; }
         XT_CUDA(c, cudaMemcpyAsync(hist + NG, start.data(), NG * sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
-        k_sd_scatter<<<blocks_for(n_list, 256, 8), 256, 0, c->stream>>>(list, key, n_list, hist + NG, sorted);
+        k_sd_scatter<<<blocks_for(n_pend, 256, 8), 256, 0, c->stream>>>(qA, key, n_pend, hist + NG, qB);
         XT_CUDA(c, cudaGetLastError());
         kernels += 2;
-        XT_CUDA(c, cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), c->stream));
-        unsigned long long cnt[4] = {0, 0, 0, 0};
-        for (int g = 0; g < NG; ++g) {
-          if (h[g] == 0) continue;
+        XT_CUDA(c, cudaMemsetAsync(counters + 3, 0, 2 * sizeof(unsigned long long), c->stream));  // carry, pend
+        int64_t n_carry = 0;
+        for (int k = 0; k < NG; ++k) {
+          const int g = dir > 0 ? k : NG - 1 - k;
+          if (h[g] == 0 && n_carry == 0) continue;
           double* hs = c->h_S + (size_t)g * slab_n;
           if (c->S_valid[g]) XT_CUDA(c, cudaMemcpyAsync(c->d_S, hs, slab_b, cudaMemcpyHostToDevice, c->stream));
           else XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, slab_b, c->stream));
-          XT_CUDA(c, cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), c->stream));
-          ta.list = sorted + start[g];
-          ta.n_list = h[g];
-          ta.out = outq;
           ta.row0 = (int64_t)g * rows_g;
-          const int grid = (int)std::min<int64_t>(grid_max, ((int64_t)h[g] + 255) / 256);
-          sl = tick(1);
-          if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
-          else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
-          XT_CUDA(c, cudaGetLastError());
-          tock(sl);
-          ++kernels;
-          XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-          XT_CUDA(c, cudaStreamSynchronize(c->stream));
-          ++rounds;
-          if (cnt[1] > 0) {
-            xa.n_esc = (int64_t)cnt[1];
-            sl = tick(2);
-            k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
+          XT_CUDA(c, cudaMemsetAsync(counters + 3, 0, sizeof(unsigned long long), c->stream));  // carry out
+          const int* lists[2] = {qB + start[g], carry_in};
+          const int64_t lens[2] = {(int64_t)h[g], n_carry};
+          for (int part = 0; part < 2; ++part) {
+            if (lens[part] == 0) continue;
+            XT_CUDA(c, cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), c->stream));
+            ta.list = lists[part];
+            ta.n_list = lens[part];
+            ta.out = out_tmp;
+            const int grid = (int)std::min<int64_t>(grid_max, (lens[part] + 255) / 256);
+            sl = tick(1);
+            if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+            else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
             XT_CUDA(c, cudaGetLastError());
             tock(sl);
             ++kernels;
+            unsigned long long cnt[4];
+            XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+            XT_CUDA(c, cudaStreamSynchronize(c->stream));
+            ++rounds;
+            if (cnt[1] > 0) {
+              xa.n_esc = (int64_t)cnt[1];
+              sl = tick(2);
+              k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
+              XT_CUDA(c, cudaGetLastError());
+              tock(sl);
+              ++kernels;
+            }
+            if (cnt[2] > 0) {
+              queued_total += (int64_t)cnt[2];
+              k_grp_split<<<blocks_for((int64_t)cnt[2], 256, 8), 256, 0, c->stream>>>(
+                  P.cell, out_tmp, (int64_t)cnt[2], ta.grp_nz, g + dir, carry_out, counters + 3, qA, counters + 4);
+              XT_CUDA(c, cudaGetLastError());
+              ++kernels;
+            }
           }
           XT_CUDA(c, cudaMemcpyAsync(hs, c->d_S, slab_b, cudaMemcpyDeviceToHost, c->stream));
           c->S_valid[g] = 1;
+          unsigned long long nco = 0;
+          XT_CUDA(c, cudaMemcpyAsync(&nco, counters + 3, sizeof(nco), cudaMemcpyDeviceToHost, c->stream));
+          XT_CUDA(c, cudaStreamSynchronize(c->stream));
+          std::swap(carry_in, carry_out);
+          n_carry = (int64_t)nco;
         }
+        unsigned long long np = 0;
+        XT_CUDA(c, cudaMemcpyAsync(&np, counters + 4, sizeof(np), cudaMemcpyDeviceToHost, c->stream));
+        XT_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (n_carry > 0)      // (a straight path leaves the grid past the last group)
+          XT_CUDA(c, cudaMemcpyAsync(qA + np, carry_in, (size_t)n_carry * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+        n_pend = (int64_t)np + n_carry;
         ta.row0 = 0;
-        n_list = (int64_t)cnt[2];
-        queued_total += n_list;
-        list = outq;
       }
       XT_CUDA(c, cudaStreamSynchronize(c->stream));
       continue;

@@ -97,6 +97,8 @@ struct xt_ctx {
   double* h_S = nullptr;             //   many groups of subdomain z-layers (rows contiguous)
   size_t h_S_bytes = 0;
   std::vector<char> S_valid;         // group written by the current pass (else all zero)
+  int* d_stream_q = nullptr;         // host store: out, carry-in, carry-out packet queues
+  int64_t stream_q_cap = 0;
   bool have_S = false;
   // emission
   int64_t* d_qoff = nullptr;         // natural order [ncell+1]
