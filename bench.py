@@ -279,6 +279,30 @@ def coupled_bench(local, stream_ptr, n=32):
                          "train_ms": tr["train_ms"]}}
 
 
+def stream_bench(local, stream_ptr, groups=8, packets=100_000_000):
+    """The estimator store held in pinned host memory and streamed through the
+    device by groups of subdomain z-layers, against the device-resident store,
+    on the 64^3 onion with 1e4 lines (21 GB store; 8 groups of 2.6 GB)."""
+    import paper_2511_07539_gb300 as xt
+    import synth
+    w = synth.clumpy_onion(n_lines=10_000, n_packets=packets)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    out = {"workload": w.name, "groups": groups}
+    for name, g in (("resident", 0), ("host_streamed", groups)):
+        xt.set_estimator_store(ctx.h, g)
+        ctx.transport(w)                                   # warm-up (allocations)
+        best = None
+        for _ in range(2):
+            st = ctx.transport(w)
+            best = st if best is None or st["transport_ms"] < best["transport_ms"] else best
+        out[name] = {"value": best["events"] / (best["transport_ms"] * 1e-3), "unit": UNIT,
+                     "ms_per_pass": best["transport_ms"], "launches": best["rounds"],
+                     "store_bytes": float(w.ncell) * w.nline * 8}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +317,7 @@ def main():
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
     ap.add_argument("--coupled-n", type=int, default=32)
+    ap.add_argument("--no-stream", action="store_true", help="skip the host-streamed store measurement")
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
     ap.add_argument("--nlte-n", type=int, default=64)
     ap.add_argument("--nlte-once", action="store_true",
@@ -461,6 +486,8 @@ def main():
         line["nlte"] = nlte_bench(local, stream.cuda_stream, args.nlte_n)
     if rank == 0 and not args.no_coupled and args.workload == "onion":
         line["coupled"] = coupled_bench(local, stream.cuda_stream, args.coupled_n)
+    if rank == 0 and not args.no_stream and args.workload == "onion":
+        line["stream"] = stream_bench(local, stream.cuda_stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
