@@ -125,48 +125,62 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
       pan[r * kbp + cc] = A[(int64_t)(k0 + r) * L + k0 + cc];
     }
     block_sync();
+    // Column j: warp 0 applies the previous column's row exchange and finds the
+    // pivot row p; then every thread eliminates its rows (all r >= j but p)
+    // with row p, and the exchange of rows j and p follows in the next step
+    // (eliminating with row p in place and exchanging afterwards gives the
+    // same factor as exchanging first).  Two barriers per column.
+    int prev = -1;                                 // previous column and its pivot row
     for (int j = 0; j < kb; ++j) {
-      // argmax |pan[r][j]| over r >= j, ties to the lowest row
-      T best = 0;
-      int bi = j;
-      for (int r = j + tid; r < rows; r += blockDim.x) {
-        const T v = pan[r * kbp + j] < 0 ? -pan[r * kbp + j] : pan[r * kbp + j];
-        if (v > best) { best = v; bi = r; }
-      }
+      if (warp == 0) {
+        if (j > 0 && prev != j - 1 && prev >= 0 && lane < kb) {
+          const T t = pan[(j - 1) * kbp + lane];
+          pan[(j - 1) * kbp + lane] = pan[prev * kbp + lane];
+          pan[prev * kbp + lane] = t;
+        }
+        __syncwarp();
+        // argmax |pan[r][j]| over r >= j, ties to the lowest row
+        T best = 0;
+        int bi = j;
+        for (int r = j + lane; r < rows; r += 32) {
+          const T v = pan[r * kbp + j] < 0 ? -pan[r * kbp + j] : pan[r * kbp + j];
+          if (v > best) { best = v; bi = r; }
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) { sbest[warp] = (double)best; sidx[warp] = bi; }
-      block_sync();
-      if (tid == 0) {
-        double b = sbest[0];
-        int p = sidx[0];
-        for (int w = 1; w < nwarp; ++w)
-          if (sbest[w] > b || (sbest[w] == b && sidx[w] < p)) { b = sbest[w]; p = sidx[w]; }
-        piv[k0 + j] = k0 + p;
-        if (b == 0) { sing = 1; p = -1; }
-        spiv = p;
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          piv[k0 + j] = k0 + bi;
+          if (best == 0) sing = 1;
+          spiv = best == 0 ? -1 : bi;
+        }
       }
       block_sync();
-      const int p = spiv;
-      if (p < 0) continue;                         // uniform: zero column
-      if (p != j && tid < kb) {
-        const T t = pan[j * kbp + tid];
-        pan[j * kbp + tid] = pan[p * kbp + tid];
-        pan[p * kbp + tid] = t;
-      }
-      block_sync();
-      const T inv = T(1) / pan[j * kbp + j];
-      for (int r = j + 1 + tid; r < rows; r += blockDim.x) {
-        const T l = pan[r * kbp + j] * inv;
-        pan[r * kbp + j] = l;
-        for (int cc = j + 1; cc < kb; ++cc) pan[r * kbp + cc] -= l * pan[j * kbp + cc];
+      const int pr = spiv;
+      prev = pr < 0 ? j : pr;                      // a zero column exchanges nothing
+      if (pr >= 0) {
+        const T inv = T(1) / pan[pr * kbp + j];
+        const T* prow = pan + pr * kbp;
+        for (int r = j + tid; r < rows; r += blockDim.x) {
+          if (r == pr) continue;
+          T* row = pan + r * kbp;
+          const T l = row[j] * inv;
+          row[j] = l;
+          for (int cc = j + 1; cc < kb; ++cc) row[cc] -= l * prow[cc];
+        }
       }
       block_sync();
     }
+    // the last column's exchange
+    if (warp == 0 && prev != kb - 1 && prev >= 0 && lane < kb) {
+      const T t = pan[(kb - 1) * kbp + lane];
+      pan[(kb - 1) * kbp + lane] = pan[prev * kbp + lane];
+      pan[prev * kbp + lane] = t;
+    }
+    block_sync();
     // write the panel back; apply its row swaps to the other columns
     for (int e = tid; e < rows * kb; e += blockDim.x) {
       const int r = e / kb, cc = e - r * kb;
