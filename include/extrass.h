@@ -152,8 +152,10 @@ int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats 
  * memory, zeros on its first visit in a pass), its packets traced until they
  * leave the group, escape or end, and the slab written back; trajectories and
  * results are those of the device-resident store.  get_estimators and
- * get_photoexcitation_rates stage the groups they read; solve_nlte and
- * train_surrogate with estimator rates return XT_ESTATE for a host-held store.
+ * get_photoexcitation_rates stage the groups they read; solve_nlte with
+ * estimator rates solves group by group, each group's slab staged (no graph
+ * replay, no autotuning there); train_surrogate with estimator inputs
+ * returns XT_ESTATE for a host-held store.
  * Frees the current store (host and device); the next run_transport allocates. */
 int set_estimator_store(xt_ctx *ctx, int32_t host_groups);
 

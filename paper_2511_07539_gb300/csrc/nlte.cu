@@ -718,8 +718,6 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (c->n_ion > 16) return fail(c, XT_EINVAL, "solve_nlte: at most 16 ions");
   if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR && p->precision != XT_PREC_TF32_IR)
     return fail(c, XT_EINVAL, "solve_nlte: precision");
-  if (p->rates == XT_RATES_ESTIMATORS && c->S_groups > 0)
-    return fail(c, XT_ESTATE, "solve_nlte: estimator rates from a host-held store are not supported (read them with get_photoexcitation_rates)");
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S)
     return fail(c, XT_ESTATE, "solve_nlte: estimator rates need a transport pass with the current populations");
   if (p->rates == XT_RATES_JBAR && !(p->jbar_W > 0 && p->jbar_TR > 0)) return fail(c, XT_EINVAL, "solve_nlte: jbar_W, jbar_TR > 0");
@@ -755,13 +753,36 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   std::vector<int64_t> start(Lmax + 2, 0);
   for (int L = Lmax - 1; L >= 1; --L) start[L] = start[L + 1] + cnt[L + 1];
   std::vector<int> work(nsys);
-  {
+  // estimator rates from a host-held store: the systems go group by group
+  // (each group's cells are a contiguous natural range), longest first within
+  // a group, and each group's launch reads its staged slab
+  const bool grouped = c->S_groups > 0 && p->rates == XT_RATES_ESTIMATORS;
+  const int NG = grouped ? c->S_groups : 1;
+  std::vector<int64_t> g_begin(NG + 1, 0), g_big(NG, 0);
+  if (!grouped) {
     std::vector<int64_t> fill(start);
     for (int64_t e = 0; e < nsys; ++e) {
       const int64_t cell = e / c->n_ion;
       const int z = (int)(e % c->n_ion);
       work[fill[used[e]]++] = (int)(cell * 16 + z);
     }
+  } else {
+    const int64_t per_g = nsys / NG;                // systems of a group (cells x ions)
+    for (int g = 0; g < NG; ++g) {
+      const int64_t e0 = (int64_t)g * per_g, e1 = e0 + per_g;
+      std::vector<int64_t> cg(Lmax + 2, 0), sg(Lmax + 2, 0);
+      for (int64_t e = e0; e < e1; ++e) cg[used[e]]++;
+      for (int L = Lmax - 1; L >= 1; --L) sg[L] = sg[L + 1] + cg[L + 1];
+      for (int64_t e = e0; e < e1; ++e) {
+        const int64_t cell = e / c->n_ion;
+        const int z = (int)(e % c->n_ion);
+        work[e0 + sg[used[e]]++] = (int)(cell * 16 + z);
+      }
+      g_begin[g] = e0;
+      g_big[g] = 0;
+      for (int L = Lmax; L > kSmallL; --L) g_big[g] += cg[L];
+    }
+    g_begin[NG] = nsys;
   }
   // buffers of the solve, kept in the context between calls
   auto& B = c->se;
@@ -909,7 +930,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     launch_one(small, true, grid_s, s_);
   };
   // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
-  if (p->autotune && !B.tuned[ti]) {
+  if (p->autotune && !B.tuned[ti] && !grouped) {
     const int cand[3] = {8, 16, 32};
     for (int b = 0; b < 8; ++b) {
       // systems with L in [64 b, 64 b + 63] are contiguous in the longest-first list
@@ -943,7 +964,24 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   }
   for (int k = 0; k < 8; ++k) a.nb_bucket[k] = as.nb_bucket[k] = B.nb[ti][k];
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  if (p->use_graph) {
+  if (grouped) {
+    const int64_t cells_g = G.ncell / NG;
+    const size_t slab_n = (size_t)cells_g * c->nline;
+    for (int g = 0; g < NG; ++g) {
+      if (c->S_valid.size() == (size_t)NG && c->S_valid[g])
+        XT_CUDA(c, cudaMemcpyAsync(c->d_S, c->h_S + (size_t)g * slab_n, slab_n * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+      else
+        XT_CUDA(c, cudaMemsetAsync(c->d_S, 0, slab_n * sizeof(double), c->stream));
+      SeArgs ag = a, asg = as;
+      ag.S = asg.S = c->d_S - (int64_t)g * (int64_t)slab_n;   // row r of the group at S + r nline
+      ag.work = B.work + g_begin[g];
+      ag.n_work = g_big[g];
+      asg.work = B.work + g_begin[g] + g_big[g];
+      asg.n_work = g_begin[g + 1] - g_begin[g] - g_big[g];
+      launch_on(ag, asg, c->stream);
+    }
+  } else if (p->use_graph) {
     // one captured pair of launches per argument set, replayed on later calls
     std::vector<unsigned char> key(2 * sizeof(a) + 3 * sizeof(int));
     std::memcpy(key.data(), &a, sizeof(a));

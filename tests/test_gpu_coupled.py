@@ -97,3 +97,34 @@ def test_coupled_loop_edge_cases(xt):
     ref, _ = coupled.outer_step(w, alpha=0.5, newton_tol=1e-10)
     assert _worst(w, got, ref) < 1e-6
     assert np.all(got[w.rho == 0] == 0)
+
+
+def test_rate_solve_and_loop_from_host_streamed_store(xt):
+    """Estimator-rate solves and the coupled loop read a host-held store (two
+    groups of subdomain layers, staged one at a time) and give the results of
+    the device-resident store: the linear solve to 1e-10; the Newton loop to
+    1e-5 (two runs on the same device store already differ by up to 1e-6 on
+    this clumpy workload: the Jacobian's line terms are summed by atomics in
+    varying order, and the stiff thick-line systems carry that far)."""
+    w = synth.clumpy_onion(seed=3, n=8, n_packets=100_000, n_lines=2000, level_range=(20, 40),
+                           subdomains=(2, 2, 2))
+    ups = synth.collision_strengths(w.upsilon_seed, w.level_off)
+    out = {}
+    for groups in (0, 2):
+        with _ctx(xt) as ctx:
+            ctx.load(w)
+            xt.set_estimator_store(ctx.h, groups)
+            ctx.transport(w)
+            solved = np.zeros((w.ncell, w.nlev))
+            xt.solve_nlte(ctx.h, ups, precision=0, rates=xt.XT_RATES_ESTIMATORS,
+                          warm=xt.XT_WARM_CURRENT, pops_out=solved)
+            st = xt.run_coupled(ctx.h, ups, w.n_packets, seed=w.seed, start=xt.XT_WARM_LTE, tol=1e-4,
+                                precision=1, newton_tol=1e-10, spec_lam0_A=w.spec_band_A[0],
+                                spec_nbins=w.spec_band_A[1])
+            loop = np.zeros((w.ncell, w.nlev))
+            xt.get_populations(ctx.h, loop)
+            out[groups] = (solved, st, loop)
+    (s0, st0, l0), (s2, st2, l2) = out[0], out[2]
+    assert st0["converged"] and st2["converged"] and st0["outer"] == st2["outer"]
+    assert _worst(w, s2, s0) < 1e-10
+    assert _worst(w, l2, l0, floor=1e-20) < 1e-5
