@@ -33,10 +33,10 @@ UNIT = "interactions/s"
 BYTES_PER_EVENT = 32          # n_l, n_u reads (16 B) + estimator read-modify-write (16 B)
 # DRAM bytes (read + write) per event of the attenuation trace kernel (which
 # emits its own packets), from an ncu capture of this kernel version on the
-# 32^3 onion case (796.8 + 461.1 MB over 7,813,774 events); the bench's launch
+# 32^3 onion case (829.6 + 497.6 MB over 7,813,774 events); the bench's launch
 # is too large to capture with many passes, and its traffic is taken as
 # proportional to its events.
-TRACE_DRAM_BYTES_PER_EVENT = (796.797184e6 + 461.076736e6) / 7813774
+TRACE_DRAM_BYTES_PER_EVENT = (829.598464e6 + 497.600512e6) / 7813774
 
 
 def _measured_peaks():

@@ -330,14 +330,22 @@ typedef struct {
 int run_coupled(xt_ctx *ctx, const xt_coupled_params *p, xt_coupled_stats *stats);
 
 /* ---- numerical self-test (no paper counterpart: checks device primitives) --
- * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so two hot
- * transcendental steps are the library's own fixed-point routines on the
- * integer pipe: kind 0, the attenuation factors e^-x and 1 - e^-x of a line
- * event (x > 0); kind 1, sin(2 pi x) and cos(2 pi x) of a packet's emission
- * azimuth (0 <= x < 1, x a multiple of 2^-53).  This evaluates them for n
- * values (host or device arrays) into y0, y1 and, if r0 / r1 are not NULL,
- * CUDA's own exp(-x), -expm1(-x) or sin, cos beside them.  Runs on the current
- * device, synchronously, with temporaries of its own. */
+ * GB300 runs FP64 arithmetic at about 1/64 of its FP32 rate, so the hot
+ * transcendental and division steps are the library's own fixed-point routines
+ * on the integer pipe.  This evaluates one of them for n inputs (host or device
+ * arrays; y0, y1 and, when not NULL, r0, r1 hold n values each):
+ *   kind 0: x[i] > 0, the attenuation factors of a line event: y0 = e^-x,
+ *           y1 = 1 - e^-x; r0, r1 = CUDA's exp(-x), -expm1(-x).
+ *   kind 1: 0 <= x[i] < 1 a multiple of 2^-53, the emission azimuth:
+ *           y0 = sin(2 pi x), y1 = cos(2 pi x); r0, r1 = CUDA's sin, cos.
+ *   kind 2: x holds n pairs (a, b) of positive normal numbers, the emission's
+ *           quotients: y0 = a / b of the integer-pipe routine, r0 = CUDA's
+ *           IEEE a / b; y1, r1 are set to 0.
+ *   kind 3: x holds n pairs (u, v), multiples of 2^-53 in [0, 1), the
+ *           isotropic emission direction with mu = 2u - 1, phi = 2 pi v:
+ *           y0 = n_x, y1 = n_y, r0 = n_z; r1 is set to 0.
+ * Runs on the current device, synchronously, with temporaries of its own.
+ * XT_EINVAL for a NULL x, y0 or y1, n < 0 or an unknown kind. */
 int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, double *y1,
                       double *r0, double *r1);
 

@@ -451,10 +451,15 @@ def get_spectrum(ctx, kind=0, out=None):
 
 def xt_selftest_fixed(kind, x):
     """Device fixed-point primitives (kind 0: e^-x, 1 - e^-x; kind 1: sin, cos
-    of 2 pi x) and CUDA's exp/expm1 or sin/cos beside them."""
+    of 2 pi x) and CUDA's exp/expm1 or sin/cos beside them; kind 2: x of shape
+    (n, 2), the quotient a / b and CUDA's; kind 3: x of shape (n, 2), the
+    emission direction (n_x, n_y, n_z) for mu = 2u - 1, phi = 2 pi v."""
     x = np.ascontiguousarray(x, dtype=np.float64)
-    out = [np.zeros_like(x) for _ in range(4)]
-    rc = lib().xt_selftest_fixed(int(kind), _ptr(x), x.shape[0], *[_ptr(o) for o in out])
+    n = x.shape[0]
+    if kind >= 2 and (x.ndim != 2 or x.shape[1] != 2):
+        raise ValueError("kinds 2 and 3 take pairs, shape (n, 2)")
+    out = [np.zeros(n) for _ in range(4)]
+    rc = lib().xt_selftest_fixed(int(kind), _ptr(x), n, *[_ptr(o) for o in out])
     if rc != XT_OK:
         raise XtError(rc, "xt_selftest_fixed failed")
     return out

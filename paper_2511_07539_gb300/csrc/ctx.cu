@@ -269,10 +269,23 @@ __global__ void k_selftest_fixed(int kind, FixExpTables T, FixTrigTables R,
       expneg(T, x[i], y0[i], y1[i]);
       r0[i] = exp(-x[i]);
       r1[i] = -expm1(-x[i]);
-    } else {
+    } else if (kind == 1) {
       const uint64_t U = (uint64_t)(x[i] * 9007199254740992.0);   // exact for u = U 2^-53
       sincos_2pi(R, U, y0[i], y1[i]);
       sincos(2.0 * kPi * x[i], &r0[i], &r1[i]);
+    } else if (kind == 2) {
+      y0[i] = div_pos(x[2 * i], x[2 * i + 1]);
+      r0[i] = x[2 * i] / x[2 * i + 1];
+      y1[i] = 0.0;
+      r1[i] = 0.0;
+    } else {
+      double n[3];
+      isotropic_fix(R, (uint64_t)(x[2 * i] * 9007199254740992.0),
+                    (uint64_t)(x[2 * i + 1] * 9007199254740992.0), n);
+      y0[i] = n[0];
+      y1[i] = n[1];
+      r0[i] = n[2];
+      r1[i] = 0.0;
     }
   }
 }
@@ -316,7 +329,7 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_A, (void**)&c->d_invB, (void**)&c->d_lo, (void**)&c->d_up,
                    (void**)&c->d_orig, (void**)&c->d_down_off, (void**)&c->d_down_line,
                    (void**)&c->d_nion, (void**)&c->d_ups_down, (void**)&c->d_pops, (void**)&c->d_S,
-                   (void**)&c->d_qoff, (void**)&c->d_Lc, (void**)&c->d_wline, (void**)&c->d_spec,
+                   (void**)&c->d_qoff, (void**)&c->d_qguide, (void**)&c->d_nuguide, (void**)&c->d_Lc, (void**)&c->d_wline, (void**)&c->d_spec,
                    (void**)&c->d_ledger, (void**)&c->d_scratch, (void**)&c->d_lines,
                    (void**)&c->d_pool_f, (void**)&c->d_pool_i, (void**)&c->d_pool_pid,
                    (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n};
@@ -669,23 +682,25 @@ int get_spectrum(xt_ctx* c, int32_t kind, double* out, size_t n_cap) {
 
 int xt_selftest_fixed(int32_t kind, const double* x, int64_t n, double* y0, double* y1,
                       double* r0, double* r1) {
-  if (!x || n < 0 || !y0 || !y1 || (kind != 0 && kind != 1)) return XT_EINVAL;
+  if (!x || n < 0 || !y0 || !y1 || kind < 0 || kind > 3) return XT_EINVAL;
+  const int64_t nin = kind >= 2 ? 2 * n : n;       // kinds 2 and 3 read pairs
   FixExpTables T;
   fixexp_tables(&T);
   FixTrigTables R;
   fixtrig_tables(&R);
   const size_t b = (size_t)n * sizeof(double);
   double* d = nullptr;
-  if (cudaMalloc(&d, 5 * b + 8) != cudaSuccess) { cudaGetLastError(); return XT_ENOMEM; }
-  cudaMemcpy(d, x, b, cudaMemcpyDefault);
-  k_selftest_fixed<<<grid_blocks(n, 256), 256>>>(kind, T, R, d, n, d + n, d + 2 * n, d + 3 * n, d + 4 * n);
+  if (cudaMalloc(&d, 6 * b + 8) != cudaSuccess) { cudaGetLastError(); return XT_ENOMEM; }
+  cudaMemcpy(d, x, (size_t)nin * sizeof(double), cudaMemcpyDefault);
+  double* o = d + nin;
+  k_selftest_fixed<<<grid_blocks(n, 256), 256>>>(kind, T, R, d, n, o, o + n, o + 2 * n, o + 3 * n);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) {
-    cudaMemcpy(y0, d + n, b, cudaMemcpyDefault);
-    cudaMemcpy(y1, d + 2 * n, b, cudaMemcpyDefault);
-    if (r0) cudaMemcpy(r0, d + 3 * n, b, cudaMemcpyDefault);
-    if (r1) cudaMemcpy(r1, d + 4 * n, b, cudaMemcpyDefault);
+    cudaMemcpy(y0, o, b, cudaMemcpyDefault);
+    cudaMemcpy(y1, o + n, b, cudaMemcpyDefault);
+    if (r0) cudaMemcpy(r0, o + 2 * n, b, cudaMemcpyDefault);
+    if (r1) cudaMemcpy(r1, o + 3 * n, b, cudaMemcpyDefault);
   }
   cudaFree(d);
   return e == cudaSuccess ? XT_OK : XT_ECUDA;

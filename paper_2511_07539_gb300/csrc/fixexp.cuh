@@ -8,11 +8,12 @@
 //                                             table-driven method, ACM TOMS 15, 1989)
 //   e^-s by its Taylor series to s^9/9! (< 2^-72) in Horner form,
 //   e^-tau = 2^-k e^-j/64 e^-s, rounded once to double.
-// For tau < ln2 the complement 1 - e^-tau = 1 - e^-r is formed exactly in fixed
-// point, so it keeps full relative precision for small tau; for larger tau it
-// is 1 - e^-tau in double (no cancellation, e^-tau < 1/2).  Both results are
-// within about one ulp of the correctly rounded values; tau >= 709 gives
-// e^-tau = 0.  The tables are computed on the host (xt::fixexp_tables).
+// The complement 1 - e^-tau = 1 - 2^-k e^-r is formed in fixed point too (for
+// tau < ln2 exactly, so it keeps full relative precision for small tau; for
+// larger tau it is at least 1/2 and the dropped bits of 2^-k e^-r are below
+// 2^-63).  Both results are within about one ulp of the correctly rounded
+// values; tau >= 709 gives e^-tau = 0.  The tables are computed on the host
+// (xt::fixexp_tables).
 #pragma once
 #include <stdint.h>
 
@@ -108,8 +109,7 @@ __device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double
   for (int n = 8; n >= 0; --n) p = T.fact[n] - mul_q63(s, p);   // all partial sums stay positive
   const uint64_t E = mul_q63(T.tab[j], p);                 // e^-r in Q63, in (1/2, 1]
   ex = q63_to_double(E, -k);
-  if (k == 0) ome = q63_to_double((1ull << 63) - E, 0);
-  else ome = 1.0 - ex;
+  ome = q63_to_double((1ull << 63) - (k < 64 ? E >> k : 0ull), 0);
 }
 
 // sin(2 pi u) and cos(2 pi u) for u = U 2^-53, 0 <= U < 2^53, in fixed point.
@@ -118,7 +118,10 @@ __device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double
 // and cosine are Taylor series to delta^8 (next term < 2^-72), combined by the
 // angle-addition formulas; octant symmetries give the signs.  Results are
 // within about one ulp of sin and cos of the exact angle 2 pi u.
-__device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, double& s, double& c) {
+// sincos_2pi_q63 leaves sin and cos of the angle within its quadrant in Q63
+// and returns the quadrant (0..3); quadrant_signs maps them to the full angle.
+__device__ __forceinline__ int sincos_2pi_q63(const FixTrigTables& T, uint64_t U, uint64_t& sa,
+                                              uint64_t& ca) {
   const int oct = (int)(U >> 50);
   uint64_t g = U & ((1ull << 50) - 1ull);                  // fraction of the octant, Q50
   if (oct & 1) g = (1ull << 50) - g;                       // reflect: beta = pi/4 - theta
@@ -140,14 +143,122 @@ __device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, d
   const uint64_t sb = mul_q63(T.sin_t[j], cd) + mul_q63(T.cos_t[j], sd);   // sin beta
   const uint64_t cb = mul_q63(T.cos_t[j], cd) - mul_q63(T.sin_t[j], sd);   // cos beta
   // angle within the quadrant: alpha = beta (even octant) or pi/2 - beta (odd)
-  const uint64_t sa = (oct & 1) ? cb : sb, ca = (oct & 1) ? sb : cb;
-  const double vs = q63_to_double(sa, 0), vc = q63_to_double(ca, 0);
-  switch (oct >> 1) {
+  sa = (oct & 1) ? cb : sb;
+  ca = (oct & 1) ? sb : cb;
+  return oct >> 1;
+}
+
+// -x by flipping the sign bit (an FP64 negation would take a slot of the
+// FP64 pipe)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+__device__ __forceinline__ void quadrant_signs(int q, double vs, double vc, double& s, double& c) {
+  switch (q) {
     case 0: s = vs; c = vc; break;
-    case 1: s = vc; c = -vs; break;
-    case 2: s = -vs; c = -vc; break;
-    default: s = -vc; c = vs; break;
+    case 1: s = vc; c = neg_bits(vs); break;
+    case 2: s = neg_bits(vs); c = neg_bits(vc); break;
+    default: s = neg_bits(vc); c = vs; break;
   }
+}
+
+__device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, double& s, double& c) {
+  uint64_t sa, ca;
+  const int q = sincos_2pi_q63(T, U, sa, ca);
+  quadrant_signs(q, q63_to_double(sa, 0), q63_to_double(ca, 0), s, c);
+}
+
+// ---- quotient and square root on the integer pipe ---------------------------
+// Q63 value of 1/m for M = m 2^62, 1 <= m < 2.  The seed is the FP32 reciprocal
+// approximation of m (rcp.approx, about 23 correct bits); two Newton-Raphson
+// steps y <- y (2 - m y), each doubling the correct bits, run in 64-bit fixed
+// point, whose truncations keep the result within about 2^-61 relative.
+__device__ __forceinline__ uint64_t float_to_q63(float y) {     // 0.5 <= y <= 1
+  const uint32_t yb = __float_as_uint(y);
+  const int e = (int)(yb >> 23) - 127;                            // -1 or 0
+  return (uint64_t)((yb & 0x7FFFFFu) | 0x800000u) << (40 + e);
+}
+
+__device__ __forceinline__ uint64_t rcp_q63(uint64_t M) {
+  const float f = __uint_as_float((127u << 23) | (uint32_t)((M >> 39) & 0x7FFFFFu));
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  uint64_t Y = float_to_q63(y);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t my = (__umul64hi(M, Y) << 1) | ((M * Y) >> 63);     // m y, Q62
+    const uint64_t E = (1ull << 63) - my;                              // 2 - m y, Q62
+    Y = (__umul64hi(Y, E) << 2) | ((Y * E) >> 62);                     // Q63
+  }
+  return Y;
+}
+
+// a / b for positive normal doubles: the significands' quotient from the
+// reciprocal above and one 64 x 64-bit product, rounded once to nearest.  The
+// reciprocal's error (< 2^-60) can move the rounding only for quotients within
+// 2^-7 ulp of a midpoint, so the result is within 0.51 ulp of a / b.  A result
+// outside the normal range is left to the IEEE division.
+__device__ __forceinline__ double div_pos(double a, double b) {
+  const uint64_t ab = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+  const uint64_t frac = (1ull << 52) - 1ull;
+  const uint64_t ma = (ab & frac) | (1ull << 52), mb = (bb & frac) | (1ull << 52);
+  const uint64_t Y = rcp_q63(mb << 10);                // 2^115 / mb
+  const uint64_t q = __umul64hi(ma << 11, Y);          // (ma / mb) 2^62, in (2^61, 2^63)
+  int e = (int)(ab >> 52) - (int)(bb >> 52) + 1023;
+  uint64_t m;
+  if (q >> 62) {
+    m = (q >> 10) + ((q >> 9) & 1ull);
+  } else {
+    m = (q >> 9) + ((q >> 8) & 1ull);
+    --e;
+  }
+  if (m >> 53) { m >>= 1; ++e; }
+  if (e <= 0 || e >= 2047) return a / b;
+  return __longlong_as_double((long long)(((uint64_t)e << 52) | (m & frac)));
+}
+
+// Direction of an isotropic emission from the 53-bit integers of its two
+// uniforms, u = Umu 2^-53 and u' = Uphi 2^-53: mu = 2u - 1, phi = 2 pi u'.
+// mu is exact; sin(theta) = sqrt(1 - mu^2) = 2^-52 sqrt(X) with the exact
+// 106-bit X = Umu (2^53 - Umu); its square root comes from Newton-Raphson on
+// 1/sqrt (FP32 seed, y <- y (3 - a y^2) / 2 twice) in fixed point, and
+// n_x = sin(theta) cos(phi), n_y = sin(theta) sin(phi) are formed in Q63 and
+// rounded once.  No FP64 arithmetic.
+__device__ __forceinline__ void isotropic_fix(const FixTrigTables& T, uint64_t Umu, uint64_t Uphi,
+                                              double n[3]) {
+  const uint64_t two53 = 1ull << 53;
+  const uint64_t t2 = 2 * Umu;
+  const double mu_mag = q63_to_double(t2 >= two53 ? t2 - two53 : two53 - t2, 10);
+  n[2] = t2 >= two53 ? mu_mag : neg_bits(mu_mag);
+  uint64_t sa, ca;
+  const int q = sincos_2pi_q63(T, Uphi, sa, ca);
+  if (Umu == 0) { n[0] = 0.0; n[1] = 0.0; return; }  // mu = -1
+  const uint64_t Uc = two53 - Umu;
+  const uint64_t hi = __umul64hi(Umu, Uc), lo = Umu * Uc;              // X < 2^104
+  const int top = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  int b0 = top - 63;
+  b0 += b0 & 1;                                                          // even: X ~ xm 2^b0
+  const uint64_t xm = b0 > 0 ? (hi << (64 - b0)) | (lo >> b0) : lo << (-b0);   // [2^62, 2^64)
+  const int ea = (int)(xm >> 63);                                        // a = xm 2^-62 in [1, 4)
+  const float f = __uint_as_float(((uint32_t)(127 + ea) << 23) |
+                                  (uint32_t)((xm >> (39 + ea)) & 0x7FFFFFu));
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  uint64_t Y = float_to_q63(y);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t Y2 = mul_q63(Y, Y);
+    const uint64_t H = (__umul64hi(xm, Y2) << 1) | ((xm * Y2) >> 63);   // a y^2, Q62
+    const uint64_t G = 0xC000000000000000ull - H;                        // 3 - a y^2, Q62
+    Y = (__umul64hi(Y, G) << 1) | ((Y * G) >> 63);                       // y (3 - a y^2) / 2, Q63
+  }
+  const uint64_t S = (__umul64hi(xm, Y) << 1) | ((xm * Y) >> 63);       // sqrt(a), Q62
+  const int sc = b0 / 2 - 20;                     // sin(theta) = S 2^-63 2^sc
+  double vs, vc;
+  quadrant_signs(q, q63_to_double(mul_q63(S, sa), sc), q63_to_double(mul_q63(S, ca), sc), vs, vc);
+  n[0] = vc;
+  n[1] = vs;
 }
 
 }  // namespace xt

@@ -14,7 +14,7 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
                                               uint64_t k0, uint64_t k1, uint64_t out[4]) {
   const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
   const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
+#pragma unroll 1   // rolled: the kernels that draw are large, and instruction fetch stalls them
   for (int r = 0; r < 10; ++r) {
     if (r) { k0 += W0; k1 += W1; }
     uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;

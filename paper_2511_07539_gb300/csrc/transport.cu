@@ -54,9 +54,21 @@ struct Pool {           // structure of arrays, capacity cap
   __device__ __forceinline__ double& F(int k, int64_t i) const { return f[(int64_t)k * cap + i]; }
 };
 
+// Guide tables of the emission's two inversions (Chen & Asau's guide-table
+// method for discrete inverse transforms): the emitting cell of packet p lies
+// between the cells of packets (p >> 6) 2^6 and ((p >> 6) + 1) 2^6, and the
+// first line below a band frequency nu_lo + u span between the first lines
+// below the edges of u's bucket of width 2^-16; the binary searches then run
+// over a few entries instead of the whole tables.
+constexpr int kQGuideShift = 6;
+constexpr int kNuGuideShift = 37;                 // 2^16 buckets of the 53-bit uniform
+constexpr int kNuGuideN = (1 << (53 - kNuGuideShift)) + 1;
+
 struct EmitArgs {
   Geometry g;
   const int64_t* __restrict__ qoff;   // natural [ncell+1]
+  const int* __restrict__ qguide;     // cell of packet j 2^6 (nullptr: search all of qoff)
+  const int* __restrict__ nuguide;    // band: first line with nu <= the bucket edges (or nullptr)
   const double* __restrict__ Epk;     // natural [ncell] packet energy L_c / n_c
   const double* __restrict__ Eph;     // natural [ncell] packet energy / h
   const double* __restrict__ cdf;     // [row][caller line] (line emission)
@@ -140,15 +152,11 @@ __device__ __forceinline__ LineRec ldline(const double2* __restrict__ t, int s) 
   return LineRec{a.x, a.y, b.x, b.y};
 }
 
-// Isotropic direction: mu = 2u - 1, phi = 2 pi u' (u' = Uphi 2^-53); the sine
-// and cosine of phi come from the fixed-point routine on the integer pipe.
-__device__ __forceinline__ void isotropic(const FixTrigTables& T, double umu, uint64_t Uphi,
+// Isotropic direction: mu = 2u - 1, phi = 2 pi u', from the 53-bit integers of
+// the two uniforms, on the integer pipe (isotropic_fix).
+__device__ __forceinline__ void isotropic(const FixTrigTables& T, uint64_t Umu, uint64_t Uphi,
                                           double n[3]) {
-  const double mu = 2.0 * umu - 1.0;
-  double sp, cp;
-  sincos_2pi(T, Uphi, sp, cp);
-  const double st = sqrt(1.0 - mu * mu);
-  n[0] = st * cp; n[1] = st * sp; n[2] = mu;
+  isotropic_fix(T, Umu, Uphi, n);
 }
 
 __device__ __forceinline__ double sobolev_beta(double tau) {
@@ -238,13 +246,22 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
                                             EmitOut& o) {
   const Geometry& g = a.g;
   int64_t lo = 0, hi = g.ncell;           // last c with qoff[c] <= p
+  if (a.qguide) {                         // qoff[lo] <= p < qoff[hi]
+    const int64_t j = p >> kQGuideShift;
+    lo = a.qguide[j];
+    hi = (int64_t)a.qguide[j + 1] + 1;
+  }
   while (hi - lo > 1) {
     const int64_t mid = (lo + hi) >> 1;
     if (a.qoff[mid] <= p) lo = mid; else hi = mid;
   }
   const int64_t c = lo;
   o.c = c;
-  o.idx[0] = (int)(c % g.nx); o.idx[1] = (int)((c / g.nx) % g.ny); o.idx[2] = (int)(c / ((int64_t)g.nx * g.ny));
+  {                                       // cell indices in 32-bit arithmetic (ncell < 2^30)
+    const uint32_t c32 = (uint32_t)c, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+    const uint32_t cy = c32 / nx;
+    o.idx[0] = (int)(c32 - cy * nx); o.idx[1] = (int)(cy % ny); o.idx[2] = (int)(cy / ny);
+  }
   const double d[3] = {g.dx, g.dy, g.dz};
   o.E0 = a.Epk[c];
   uint64_t xu[4], xv[4];
@@ -258,11 +275,16 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
     const double w0 = a.wall ? a.wall[woff[k] + o.idx[k]] : fma((double)o.idx[k], d[k], -g.R);
     o.r[k] = w0 + uu[k] * d[k];
   }
-  isotropic(trig, u01(xu[3]), xv[0] >> 11, o.n);
+  isotropic(trig, xu[3] >> 11, xv[0] >> 11, o.n);
   const double v1 = u01(xv[1]);
   if (a.emission == XT_EMIT_BAND) {
-    o.nu_cmf = a.nu_lo + v1 * a.nu_span;
+    o.nu_cmf = fma(v1, a.nu_span, a.nu_lo);   // the guide's edges use the same fma
     int l0 = 0, l1 = a.nline;             // first sorted line with nu <= nu_cmf
+    if (a.nuguide) {                      // nu_cmf lies between its bucket's edges
+      const int j = (int)((xv[1] >> 11) >> kNuGuideShift);
+      l0 = a.nuguide[j + 1];
+      l1 = a.nuguide[j];
+    }
     const long long nb = bits(o.nu_cmf);
     while (l0 < l1) {
       const int mid = (l0 + l1) >> 1;
@@ -283,32 +305,43 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
   }
   const double* n = o.n;
   const double* r = o.r;
-  o.nu_lab = o.nu_cmf / (1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
-  o.N = a.Eph[c] / o.nu_cmf;                        // E0 / (h nu_cmf)
-  // cell walk from the position inside the cell: the nearest wall along k is
-  // d (1 - u) / n_k ahead (n_k > 0) or u d / |n_k| (n_k < 0); td carries the sign
-  // (sign and zero tests on the bit patterns: the FP64 pipe is the scarce one)
-  double inv[3];
-  {
-    const double pxy = n[0] * n[1], pall = pxy * n[2];
-    if ((bits(pall) & 0x7FFFFFFFFFFFFFFFll) > bits(1e-280)) {
-      const double q = 1.0 / pall;
-      inv[0] = q * (n[1] * n[2]); inv[1] = q * (n[0] * n[2]); inv[2] = q * pxy;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) inv[k] = (bits(n[k]) << 1) != 0 ? 1.0 / n[k] : 0.0;
-    }
-  }
+  // the quotients on the integer pipe (div_pos, within 0.51 ulp): GB300's FP64
+  // pipe is the scarce one, and it would spend about as much on these three
+  // divisions as on the rest of the emission
+  o.nu_lab = div_pos(o.nu_cmf, 1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
+  o.N = div_pos(a.Eph[c], o.nu_cmf);                // E0 / (h nu_cmf)
+  // cell walk from the position inside the cell: walls d / |n_k| apart, the
+  // nearest one (1 - u) d / |n_k| ahead for n_k > 0 and u d / |n_k| for n_k < 0;
+  // td carries the sign of n_k (sign and zero tests on the bit patterns)
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    if ((bits(n[k]) << 1) != 0) {
-      o.tm[k] = (bits(n[k]) > 0 ? d[k] - uu[k] * d[k] : -(uu[k] * d[k])) * inv[k];
-      o.td[k] = d[k] * inv[k];
+    const long long nb = bits(n[k]);
+    if ((nb << 1) != 0) {
+      const double t = div_pos(d[k], __longlong_as_double(nb & 0x7FFFFFFFFFFFFFFFll));
+      const uint64_t U = xu[k] >> 11;                // uu[k] = U 2^-53, 1 - uu[k] exact below
+      o.tm[k] = (nb > 0 ? q63_to_double((1ull << 53) - U, 10) : uu[k]) * t;
+      o.td[k] = nb > 0 ? t : neg_bits(t);
     } else {
       o.tm[k] = INFINITY;
       o.td[k] = INFINITY;
     }
   }
+}
+
+// nuguide[j] = first sorted line with nu <= fma(j 2^-16, span, nu_lo), the
+// lower edge of bucket j of the band emission's uniform (j = 0..2^16).
+__global__ void k_nu_guide(const double* __restrict__ nu, int nline, double nu_lo, double nu_span,
+                           int* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kNuGuideN) return;
+  const double v = (double)((uint64_t)j << kNuGuideShift) * 0x1p-53;   // exact
+  const long long eb = bits(fma(v, nu_span, nu_lo));
+  int l0 = 0, l1 = nline;
+  while (l0 < l1) {
+    const int mid = (l0 + l1) >> 1;
+    if (bits(nu[mid]) <= eb) l1 = mid; else l0 = mid + 1;
+  }
+  out[j] = l0;
 }
 
 __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
@@ -480,7 +513,11 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     bool found = false, escaped = false, queued = false;
     LineRec L;
     double n_l = 0.0, n_u = 0.0, tau = 0.0;
-    long long next_bits = cursor < a.nline ? bits(ldline(a.lines, cursor).x) : 0;
+    // the record of the next line to test is loaded one test ahead, so that its
+    // fetch overlaps the population loads of the current one
+    LineRec Ln{0.0, 0.0, 0.0, 0.0};
+    if (cursor < a.nline) Ln = ldline(a.lines, cursor);
+    long long next_bits = cursor < a.nline ? bits(Ln.x) : 0;
     for (int steps = 0;;) {
       if (seg_new) {       // nearest wall and the comoving frequency there
         double sw = tmx;
@@ -491,14 +528,16 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         seg_new = false;
       }
       while (cursor < a.nline && next_bits > end_bits) {
-        L = ldline(a.lines, cursor);
+        L = Ln;
         ++n_tests;
         n_l = prow[__double2loint(L.w)];
         n_u = prow[__double2hiint(L.w)];
+        const int cn = cursor + 1;
+        if (cn < a.nline) Ln = ldline(a.lines, cn);
         tau = L.y * (n_l - L.z * n_u);
         if (bits(tau) > taumin_bits) { found = true; break; }
-        ++cursor;
-        next_bits = cursor < a.nline ? bits(ldline(a.lines, cursor).x) : 0;
+        cursor = cn;
+        next_bits = cn < a.nline ? bits(Ln.x) : 0;
       }
       if (found) break;
       // no further line in this cell: step into the next one (branch-free in axis)
@@ -577,7 +616,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             const double s_l = a.ct * (1.0 - L.x / nu_lab) - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
 #pragma unroll
             for (int k = 0; k < 3; ++k) r[k] = r[k] + s_l * n[k];
-            isotropic(trig, w.u[2], xw[3] >> 11, n);
+            isotropic(trig, xw[2] >> 11, xw[3] >> 11, n);
             const double nu_new = ldline(a.lines, pick).x;
             N = Ecmf / (kH * nu_new);
             N_in = N;
@@ -919,6 +958,27 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     if ((rc = copy(c, c->d_Lc, hv.data(), hv.size() * sizeof(double), "Lc"))) return rc;
     if ((rc = alloc(c, (void**)&c->d_qoff, q.size() * sizeof(int64_t), "quota"))) return rc;
     if ((rc = copy(c, c->d_qoff, q.data(), q.size() * sizeof(int64_t), "quota"))) return rc;
+    // guide of the packet -> cell inversion: the cell of packet j 2^6 for
+    // j = 0..(N-1)/2^6 + 1 (ids past N map to the last cell)
+    if (p->n_packets > 0) {
+      const int64_t nj = ((p->n_packets - 1) >> kQGuideShift) + 2;
+      std::vector<int> qg(nj);
+      int64_t cc = 0;
+      for (int64_t j = 0; j < nj; ++j) {
+        const int64_t x = j << kQGuideShift;
+        while (cc + 1 < G.ncell && q[cc + 1] <= x) ++cc;
+        qg[j] = (int)cc;
+      }
+      if ((rc = alloc(c, (void**)&c->d_qguide, qg.size() * sizeof(int), "packet guide"))) return rc;
+      if ((rc = copy(c, c->d_qguide, qg.data(), qg.size() * sizeof(int), "packet guide"))) return rc;
+    }
+    if (p->emission == XT_EMIT_BAND && c->nline > 0) {
+      if ((rc = alloc(c, (void**)&c->d_nuguide, kNuGuideN * sizeof(int), "band guide"))) return rc;
+      const double nu_lo = kC / (c->band_hi_A * 1e-8), nu_hi = kC / (c->band_lo_A * 1e-8);
+      k_nu_guide<<<(kNuGuideN + 255) / 256, 256, 0, c->stream>>>(c->d_nu, c->nline, nu_lo,
+                                                                  nu_hi - nu_lo, c->d_nuguide);
+      XT_CUDA(c, cudaGetLastError());
+    }
     XT_CUDA(c, cudaStreamSynchronize(c->stream));
     c->qoff_N = p->n_packets;
     c->qoff_mode = p->emission;
@@ -1015,6 +1075,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
 
   EmitArgs ea;
   ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell;
+  ea.qguide = c->d_qguide;
+  ea.nuguide = p->emission == XT_EMIT_BAND ? c->d_nuguide : nullptr;
   ea.Eph = c->d_Lc + 2 * G.ncell; ea.cdf = c->d_wline;
   ea.sorted_of = c->d_orig; ea.nu_tab = c->d_nu; ea.nline = c->nline; ea.emission = p->emission;
   ea.seed = p->seed;
@@ -1528,6 +1590,7 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
   double* cellE = (double*)(B + kNaCellE);
   EmitArgs ea{};
   ea.g = G; ea.qoff = (const int64_t*)(B + kNaQoff); ea.Lc = cellE; ea.Epk = cellE + ncell;
+  ea.qguide = nullptr; ea.nuguide = nullptr;
   ea.Eph = cellE + 2 * ncell; ea.cdf = nullptr; ea.sorted_of = (const int*)(B + kNaSorted);
   ea.nu_tab = (const double*)(B + kNaNu); ea.nline = nl; ea.emission = XT_EMIT_BAND; ea.seed = a->seed;
   ea.nu_lo = kC / (a->band_hi_A * 1e-8); ea.nu_hi = kC / (a->band_lo_A * 1e-8); ea.e_cut = a->e_cut;

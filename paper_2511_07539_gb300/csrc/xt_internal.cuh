@@ -102,6 +102,8 @@ struct xt_ctx {
   bool have_S = false;
   // emission
   int64_t* d_qoff = nullptr;         // natural order [ncell+1]
+  int* d_qguide = nullptr;           // cell of packet j 2^6, j = 0..(N-1)/2^6 + 1
+  int* d_nuguide = nullptr;          // band emission: first sorted line below each of 2^16 + 1 edges
   int64_t qoff_N = -1;               // N the quota was built for
   int qoff_mode = -1;
   double* d_Lc = nullptr;            // natural order cell luminosity used by the quota
