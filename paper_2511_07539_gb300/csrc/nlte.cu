@@ -82,6 +82,25 @@ struct SeArgs {
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
+// w 2^k rounded to FP32 (to nearest even) with integer operations: the
+// exponent is shifted, the significand rounded from 52 to 23 bits.  Results
+// below the FP32 normal range are flushed to zero (they lie more than 2^126
+// below their row's largest entry); w must be finite and w 2^k < 2^127.
+__device__ __forceinline__ float scaled_f32(double w, int k) {
+  const uint64_t b = (uint64_t)__double_as_longlong(w);
+  const uint32_t sign = (uint32_t)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF);
+  int ef = e - 1023 + k + 127;                    // biased FP32 exponent
+  if (e == 0 || ef <= 0) return __uint_as_float(sign);
+  const uint64_t mant = b & ((1ull << 52) - 1ull);
+  uint32_t m = (uint32_t)(mant >> 29);
+  const uint64_t rem = mant & ((1ull << 29) - 1ull);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (m & 1u))) {
+    if (++m == (1u << 23)) { m = 0; ++ef; }
+  }
+  return __uint_as_float(sign | ((uint32_t)ef << 23) | m);
+}
+
 // D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
 // accumulators; per lane (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g + 8, t),
 // a2 (g, t + 4), a3 (g + 8, t + 4); b0 (t, g), b1 (t + 4, g); c0, c1 (g, 2t, 2t + 1),
@@ -113,8 +132,6 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
                           bool tc_tf32 = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   __shared__ int sing, spiv;
-  __shared__ double sbest[32];
-  __shared__ int sidx[32];
   if (tid == 0) sing = 0;
   const int kbp = nb + 1;
   for (int k0 = 0; k0 < L; k0 += nb) {
@@ -186,17 +203,20 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
       const int r = e / kb, cc = e - r * kb;
       A[(int64_t)(k0 + r) * L + k0 + cc] = pan[r * kbp + cc];
     }
-    for (int j = 0; j < kb; ++j) {
-      const int p = piv[k0 + j];
-      if (p != k0 + j)
-        for (int cc = tid; cc < L; cc += blockDim.x) {
-          if (cc >= k0 && cc < k0 + kb) continue;
+    // each thread applies the panel's exchanges in order to its own columns (the
+    // exchanges of one column depend on each other, different columns do not)
+    for (int cc = tid; cc < L; cc += blockDim.x) {
+      if (cc >= k0 && cc < k0 + kb) continue;
+      for (int j = 0; j < kb; ++j) {
+        const int p = piv[k0 + j];
+        if (p != k0 + j) {
           const T tmp = A[(int64_t)(k0 + j) * L + cc];
           A[(int64_t)(k0 + j) * L + cc] = A[(int64_t)p * L + cc];
           A[(int64_t)p * L + cc] = tmp;
         }
-      block_sync();
+      }
     }
+    block_sync();
     const int n2 = L - k0 - kb;                     // trailing columns
     if (n2 > 0) {
       // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared memory
@@ -496,13 +516,31 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           for (int u = 1 + tid; u < L; u += blockDim.x) W[(int64_t)u * L] += a.eta * dep * ups[u] / denom;
       }
       block_sync();
-      // diagonal: minus the total rate out of each level (column sums)
-      for (int i = tid; i < L; i += blockDim.x) {
-        double s = 0;
-        for (int j = 0; j < L; ++j) if (j != i) s += W[(int64_t)j * L + i];
-        sRes[i] = -s;
+      // diagonal: minus the total rate out of each level (column sums), 128
+      // columns at a time: a warp per row, 4 columns per lane, then across warps
+      {
+        double* part = (double*)sPan;              // [nwarp][128], free until the factor
+        for (int c0 = 0; c0 < L; c0 += 128) {
+          double cs[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int j = warp; j < L; j += nwarp) {
+            const double* Wr = W + (int64_t)j * L + c0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int i = c0 + lane + 32 * q;
+              if (i < L && i != j) cs[q] += Wr[lane + 32 * q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) part[warp * 128 + lane + 32 * q] = cs[q];
+          block_sync();
+          for (int i = tid; i < 128 && c0 + i < L; i += blockDim.x) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += part[w * 128 + i];
+            sRes[c0 + i] = -s;
+          }
+          block_sync();
+        }
       }
-      block_sync();
       for (int i = tid; i < L; i += blockDim.x) W[(int64_t)i * L + i] = sRes[i];
       block_sync();
       for (int j = tid; j < L; j += blockDim.x) W[j] = 1.0;   // ground-level equation -> sum n = n_z
@@ -567,15 +605,40 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
         // FP32 factor of diag(r) W diag(x0), FP64 refinement
         for (int i = tid; i < L; i += blockDim.x) sX0[i] = sX0[i] > 1e-300 ? sX0[i] : 1e-300;
         block_sync();
-        for (int i = warp; i < L; i += nwarp) {
-          const double* Wr = W + (int64_t)i * L;
-          double mx = 0;
-          for (int j = lane; j < L; j += 32) mx = fmax(mx, fabs(Wr[j] * sX0[j]));
-          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const double r = mx > 0 ? 1.0 / mx : 1.0;
-          T* Tr = WT + (int64_t)i * L;
-          for (int j = lane; j < L; j += 32) Tr[j] = (T)(Wr[j] * sX0[j] * r);
-          if (lane == 0) sR[i] = r;
+        if constexpr (sizeof(T) == 4) {
+          // powers of two as scales: column j by 2^ex_j (x0_j rounded down to
+          // one), row i by 2^er_i with er_i = -max_j (ew_ij + ex_j), so the row
+          // maxima lie in [1, 2); the scaling is then exact and, with the
+          // rounding to FP32, done on the integer pipe (scaled_f32)
+          for (int i = warp; i < L; i += nwarp) {
+            const double* Wr = W + (int64_t)i * L;
+            int mx = -1 << 20;
+            for (int j = lane; j < L; j += 32) {
+              const int ew = (int)((__double_as_longlong(Wr[j]) >> 52) & 0x7FF);
+              if (ew) mx = max(mx, ew + (int)(__double_as_longlong(sX0[j]) >> 52));
+            }
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int er = mx > -(1 << 19) ? min(max(2046 - mx, -1022), 1023) : 0;   // unbiased
+            T* Tr = WT + (int64_t)i * L;
+            for (int j = lane; j < L; j += 32)
+              Tr[j] = scaled_f32(Wr[j], (int)(__double_as_longlong(sX0[j]) >> 52) - 1023 + er);
+            if (lane == 0) sR[i] = __longlong_as_double((long long)(er + 1023) << 52);
+          }
+          block_sync();
+          // the column scale of the refinement: x0 rounded down to a power of two
+          for (int i = tid; i < L; i += blockDim.x)
+            sX0[i] = __longlong_as_double(__double_as_longlong(sX0[i]) & 0x7FF0000000000000ll);
+        } else {
+          for (int i = warp; i < L; i += nwarp) {
+            const double* Wr = W + (int64_t)i * L;
+            double mx = 0;
+            for (int j = lane; j < L; j += 32) mx = fmax(mx, fabs(Wr[j] * sX0[j]));
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const double r = mx > 0 ? 1.0 / mx : 1.0;
+            T* Tr = WT + (int64_t)i * L;
+            for (int j = lane; j < L; j += 32) Tr[j] = (T)(Wr[j] * sX0[j] * r);
+            if (lane == 0) sR[i] = r;
+          }
         }
         block_sync();
         ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12, sizeof(T) == 4 && a.precision == XT_PREC_TF32_IR);

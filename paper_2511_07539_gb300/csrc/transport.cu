@@ -648,7 +648,9 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       if (MODE == XT_MODE_ATTEN) acc[T_ABS] += N_in - N;   // photons this lane absorbed
       if (queued || (MODE == XT_MODE_SCATTER && escaped)) {
         P.F(F_TMX, i) = tmx; P.F(F_TMY, i) = tmy; P.F(F_TMZ, i) = tmz;
-        P.F(F_TDX, i) = sx * tdx; P.F(F_TDY, i) = sy * tdy; P.F(F_TDZ, i) = sz * tdz;
+        P.F(F_TDX, i) = sx < 0 ? neg_bits(tdx) : tdx;
+        P.F(F_TDY, i) = sy < 0 ? neg_bits(tdy) : tdy;
+        P.F(F_TDZ, i) = sz < 0 ? neg_bits(tdz) : tdz;
         P.F(F_NU0, i) = nu0;
         P.cursor[i] = cursor;
         P.cell[i] = ix | (iy << 10) | (iz << 20);
