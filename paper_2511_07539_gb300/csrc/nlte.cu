@@ -219,10 +219,14 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
     block_sync();
     const int n2 = L - k0 - kb;                     // trailing columns
     if (n2 > 0) {
-      // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared memory
+      // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared
+      // memory: the column's kb entries are loaded first (independent loads in
+      // flight together), then solved in place
+      for (int cc = tid; cc < n2; cc += blockDim.x)
+        for (int r = 0; r < kb; ++r) u12[r * n2 + cc] = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
       for (int cc = tid; cc < n2; cc += blockDim.x) {
         for (int r = 0; r < kb; ++r) {
-          T v = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
+          T v = u12[r * n2 + cc];
           for (int s = 0; s < r; ++s) v -= pan[r * kbp + s] * u12[s * n2 + cc];
           u12[r * n2 + cc] = v;
           A[(int64_t)(k0 + r) * L + k0 + kb + cc] = v;
