@@ -284,14 +284,19 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] += lv[a] * uv[b];
         }
+        // the tile's 16 loads first, then its stores
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b)
-            if (bi + a < m2 && bj + b < n2) {
-              T* p = A + (int64_t)(k0 + kb + bi + a) * L + k0 + kb + bj + b;
-              *p -= acc[a][b];
-            }
+            if (bi + a < m2 && bj + b < n2)
+              acc[a][b] = A[(int64_t)(k0 + kb + bi + a) * L + k0 + kb + bj + b] - acc[a][b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (bi + a < m2 && bj + b < n2)
+              A[(int64_t)(k0 + kb + bi + a) * L + k0 + kb + bj + b] = acc[a][b];
       }
       block_sync();
     }
