@@ -37,6 +37,13 @@ BYTES_PER_EVENT = 32          # n_l, n_u reads (16 B) + estimator read-modify-wr
 # is too large to capture with many passes, and its traffic is taken as
 # proportional to its events.
 TRACE_DRAM_BYTES_PER_EVENT = (829.598464e6 + 497.600512e6) / 7813774
+# FP64 thread instructions (DFMA + DMUL + DADD) per event of the same kernel and
+# capture, and the share of cycles its FP64 pipe was busy: GB300 issues FP64
+# arithmetic to 2 lanes per SM and cycle, so the event loop is bound by that
+# pipe long before HBM.
+TRACE_FP64_OPS_PER_EVENT = 3066266.381579 * (16.358191 + 19.008668 + 22.430151) / 7813774
+TRACE_FP64_PIPE_BUSY = 0.58690892
+FP64_LANES_PER_SM_CYCLE = 2
 
 
 def _measured_peaks():
@@ -455,6 +462,16 @@ def main():
     # dominant kernel: the trace loop; its device time per launch from CUDA
     # events on the launching stream inside the library
     achieved = BYTES_PER_EVENT * (ev / len(stats)) / (trace_ms * 1e-3) / 1e9
+    # the FP64 pipe beside it: thread instructions per second against the
+    # pipe's lane rate at the maximum SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = FP64_LANES_PER_SM_CYCLE * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    fp64_ach = TRACE_FP64_OPS_PER_EVENT * (ev / len(stats)) / (trace_ms * 1e-3)
+    fp64 = {"ops_per_event": TRACE_FP64_OPS_PER_EVENT, "achieved": fp64_ach, "peak": fp64_peak,
+            "unit": "FP64 thread instructions/s", "frac": fp64_ach / fp64_peak,
+            "pipe_busy_ncu": TRACE_FP64_PIPE_BUSY,
+            "source": "ops per event and pipe busy from ncu on the 32^3 onion; peak = 2 lanes "
+                      "x SMs x max SM clock"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -474,7 +491,8 @@ def main():
                      "traffic": TRACE_DRAM_BYTES_PER_EVENT * ev / len(stats),
                      "traffic_source": "ncu dram bytes per event on the 32^3 onion, scaled by events",
                      "peak_source": src, "kernel": "k_trace",
-                     "bytes_per_unit": BYTES_PER_EVENT, "unit_counted": "event"},
+                     "bytes_per_unit": BYTES_PER_EVENT, "unit_counted": "event",
+                     "fp64": fp64},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": min(e2e_ms) if e2e_ms else None},

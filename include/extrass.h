@@ -210,8 +210,8 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 #define XT_WARM_GIVEN 2
 #define XT_WARM_SURROGATE 3 /* the population surrogate's prediction (see below) */
 #define XT_SE_OK 1          /* status bits per (cell, ion) */
-#define XT_SE_FALLBACK 2    /* refinement did not converge; solved again in FP64 */
-#define XT_SE_SINGULAR 4    /* zero pivot */
+#define XT_SE_FALLBACK 2    /* FP32 factor singular or refinement not converged; solved in FP64 */
+#define XT_SE_SINGULAR 4    /* zero pivot in the FP64 factor */
 #define XT_SE_NOCONV 8      /* Newton steps ran out (populations: the last iterate) */
 typedef struct {
     int32_t precision;      /* XT_PREC_* */

@@ -83,22 +83,25 @@ struct SeArgs {
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
 // w 2^k rounded to FP32 (to nearest even) with integer operations: the
-// exponent is shifted, the significand rounded from 52 to 23 bits.  Results
-// below the FP32 normal range are flushed to zero (they lie more than 2^126
-// below their row's largest entry); w must be finite and w 2^k < 2^127.
+// exponent is shifted, the significand rounded from 52 bits to those FP32 keeps
+// (23, or fewer for results in the subnormal range, as a plain conversion
+// does); w must be finite and w 2^k < 2^127.
 __device__ __forceinline__ float scaled_f32(double w, int k) {
   const uint64_t b = (uint64_t)__double_as_longlong(w);
   const uint32_t sign = (uint32_t)(b >> 63) << 31;
   const int e = (int)((b >> 52) & 0x7FF);
-  int ef = e - 1023 + k + 127;                    // biased FP32 exponent
-  if (e == 0 || ef <= 0) return __uint_as_float(sign);
-  const uint64_t mant = b & ((1ull << 52) - 1ull);
-  uint32_t m = (uint32_t)(mant >> 29);
-  const uint64_t rem = mant & ((1ull << 29) - 1ull);
-  if (rem > (1ull << 28) || (rem == (1ull << 28) && (m & 1u))) {
-    if (++m == (1u << 23)) { m = 0; ++ef; }
-  }
-  return __uint_as_float(sign | ((uint32_t)ef << 23) | m);
+  if (e == 0) return __uint_as_float(sign);
+  const int ef = e - 1023 + k + 127;              // biased FP32 exponent
+  const uint64_t M = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  // keep M >> sh: sh = 29 for a normal result, 30 - ef below the normal range;
+  // the FP32 bits are then (ef << 23) + kept (a carry out of the significand
+  // steps the exponent, and a subnormal that rounds up to 2^-126 becomes normal)
+  const int sh = ef > 0 ? 29 : 30 - ef;
+  if (sh > 54) return __uint_as_float(sign);
+  const uint64_t kept = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  uint32_t m = (uint32_t)kept + ((rem > half || (rem == half && (kept & 1ull))) ? 1u : 0u);
+  if (ef > 0) m += ((uint32_t)(ef - 1) << 23);   // the hidden bit of kept adds the last 1
+  return __uint_as_float(sign | m);
 }
 
 // D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
@@ -650,9 +653,10 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           }
         }
         block_sync();
+        // a factor that meets an exactly zero pivot (entries of the scaled matrix
+        // below the FP32 range count as zero) goes to the FP64 solve below
         ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12, sizeof(T) == 4 && a.precision == XT_PREC_TF32_IR);
         lu_perm(sPiv, L, sPerm);
-        if (!ok) st = XT_SE_SINGULAR;
         for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = sB[i]; }
         block_sync();
         bool conv = false;
@@ -683,8 +687,8 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           }
           block_sync();
         }
-        if (ok && !conv) {
-          // not converged: the plain FP64 solve decides
+        if (!conv) {
+          // not converged, or no FP32 factor: the plain FP64 solve decides
           st |= XT_SE_FALLBACK;
           double* Wd = (double*)a.WT + (int64_t)blockIdx.x * a.wlen;   // reuse (FP64 sized)
           for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
