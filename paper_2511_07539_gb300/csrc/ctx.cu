@@ -73,8 +73,17 @@ int copy(xt_ctx* c, void* dst, const void* src, size_t n, const char* what) {
   return XT_OK;
 }
 
+// (Re)allocate *p to `bytes` of device memory.  A buffer of exactly that size
+// is kept (reloading a workload of the same shape allocates nothing); any
+// other is freed first.  Contents are undefined either way.
 int alloc(xt_ctx* c, void** p, size_t bytes, const char* what) {
-  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (*p) {
+    const auto it = c->alloc_bytes.find(*p);
+    if (bytes > 0 && it != c->alloc_bytes.end() && it->second == bytes) return XT_OK;
+    if (it != c->alloc_bytes.end()) c->alloc_bytes.erase(it);
+    cudaFree(*p);
+    *p = nullptr;
+  }
   if (bytes == 0) return XT_OK;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -83,6 +92,7 @@ int alloc(xt_ctx* c, void** p, size_t bytes, const char* what) {
     return fail(c, XT_ENOMEM, std::string("cudaMalloc failed for ") + what + " (" +
                                   std::to_string(bytes) + " bytes)");
   }
+  c->alloc_bytes[*p] = bytes;
   return XT_OK;
 }
 

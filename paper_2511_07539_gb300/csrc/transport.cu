@@ -328,6 +328,20 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
   }
 }
 
+// qguide[j] = the cell of packet j 2^6: the last c with qoff[c] <= j 2^6.
+__global__ void k_q_guide(const int64_t* __restrict__ qoff, int64_t ncell, int64_t nj,
+                          int* __restrict__ out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= nj) return;
+  const int64_t x = j << kQGuideShift;
+  int64_t lo = 0, hi = ncell;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (qoff[mid] <= x) lo = mid; else hi = mid;
+  }
+  out[j] = (int)lo;
+}
+
 // nuguide[j] = first sorted line with nu <= fma(j 2^-16, span, nu_lo), the
 // lower edge of bucket j of the band emission's uniform (j = 0..2^16).
 __global__ void k_nu_guide(const double* __restrict__ nu, int nline, double nu_lo, double nu_span,
@@ -813,8 +827,10 @@ static void packet_quota(const std::vector<double>& L, int64_t N, std::vector<in
   std::iota(order.begin(), order.end(), 0);
   const int64_t extra = std::min<int64_t>(N - used, nc);
   if (extra > 0) {
+    // the extra packets go to the `extra` largest remainders, ties to the lower
+    // cell (a total order, so selecting them needs no sort)
     auto cmp = [&](int64_t x, int64_t y) { return frac[x] > frac[y] || (frac[x] == frac[y] && x < y); };
-    std::partial_sort(order.begin(), order.begin() + extra, order.end(), cmp);
+    if (extra < nc) std::nth_element(order.begin(), order.begin() + (extra - 1), order.end(), cmp);
     for (int64_t k = 0; k < extra; ++k) n[order[k]] += 1;
   }
   qoff.assign(nc + 1, 0);
@@ -931,7 +947,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   // emission: cell luminosities, packet quota, packet energy per cell
   if (c->qoff_N != p->n_packets || c->qoff_mode != p->emission) {
     std::vector<double> Lnat;
-    if ((rc = alloc(c, (void**)&c->d_Lc, G.ncell * sizeof(double) * 3, "Lc"))) return rc;
+    if (c->Lc_n != G.ncell) {
+      c->Lc_n = 0;
+      if ((rc = alloc(c, (void**)&c->d_Lc, G.ncell * sizeof(double) * 3, "Lc"))) return rc;
+      c->Lc_n = G.ncell;
+    }
     if (p->emission == XT_EMIT_BAND) {
       Lnat = c->h_L;
     } else {
@@ -958,24 +978,27 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       hv[2 * G.ncell + k] = hv[G.ncell + k] / kH;
     }
     if ((rc = copy(c, c->d_Lc, hv.data(), hv.size() * sizeof(double), "Lc"))) return rc;
-    if ((rc = alloc(c, (void**)&c->d_qoff, q.size() * sizeof(int64_t), "quota"))) return rc;
+    if (c->qoff_n != (int64_t)q.size()) {
+      c->qoff_n = 0;
+      if ((rc = alloc(c, (void**)&c->d_qoff, q.size() * sizeof(int64_t), "quota"))) return rc;
+      c->qoff_n = (int64_t)q.size();
+    }
     if ((rc = copy(c, c->d_qoff, q.data(), q.size() * sizeof(int64_t), "quota"))) return rc;
     // guide of the packet -> cell inversion: the cell of packet j 2^6 for
     // j = 0..(N-1)/2^6 + 1 (ids past N map to the last cell)
     if (p->n_packets > 0) {
       const int64_t nj = ((p->n_packets - 1) >> kQGuideShift) + 2;
-      std::vector<int> qg(nj);
-      int64_t cc = 0;
-      for (int64_t j = 0; j < nj; ++j) {
-        const int64_t x = j << kQGuideShift;
-        while (cc + 1 < G.ncell && q[cc + 1] <= x) ++cc;
-        qg[j] = (int)cc;
+      if (c->qguide_n < nj) {
+        c->qguide_n = 0;
+        if ((rc = alloc(c, (void**)&c->d_qguide, (size_t)nj * sizeof(int), "packet guide"))) return rc;
+        c->qguide_n = nj;
       }
-      if ((rc = alloc(c, (void**)&c->d_qguide, qg.size() * sizeof(int), "packet guide"))) return rc;
-      if ((rc = copy(c, c->d_qguide, qg.data(), qg.size() * sizeof(int), "packet guide"))) return rc;
+      k_q_guide<<<(int)((nj + 255) / 256), 256, 0, c->stream>>>(c->d_qoff, G.ncell, nj, c->d_qguide);
+      XT_CUDA(c, cudaGetLastError());
     }
     if (p->emission == XT_EMIT_BAND && c->nline > 0) {
-      if ((rc = alloc(c, (void**)&c->d_nuguide, kNuGuideN * sizeof(int), "band guide"))) return rc;
+      if (!c->d_nuguide &&
+          (rc = alloc(c, (void**)&c->d_nuguide, kNuGuideN * sizeof(int), "band guide"))) return rc;
       const double nu_lo = kC / (c->band_hi_A * 1e-8), nu_hi = kC / (c->band_lo_A * 1e-8);
       k_nu_guide<<<(kNuGuideN + 255) / 256, 256, 0, c->stream>>>(c->d_nu, c->nline, nu_lo,
                                                                   nu_hi - nu_lo, c->d_nuguide);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/extrass.h"
@@ -61,6 +62,7 @@ struct xt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
+  std::unordered_map<void*, size_t> alloc_bytes;   // size of every buffer alloc() made
   // grid
   bool have_grid = false;
   xt::Geometry geo{};
@@ -102,6 +104,7 @@ struct xt_ctx {
   bool have_S = false;
   // emission
   int64_t* d_qoff = nullptr;         // natural order [ncell+1]
+  int64_t qoff_n = 0, qguide_n = 0, Lc_n = 0;   // allocated entries (cells for d_Lc)
   int* d_qguide = nullptr;           // cell of packet j 2^6, j = 0..(N-1)/2^6 + 1
   int* d_nuguide = nullptr;          // band emission: first sorted line below each of 2^16 + 1 edges
   int64_t qoff_N = -1;               // N the quota was built for
