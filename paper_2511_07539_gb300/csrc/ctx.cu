@@ -455,8 +455,13 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   std::vector<double> nu(nl);
   for (int l = 0; l < nl; ++l) nu[l] = kC / (lam[l] * 1e-8);
   std::vector<int> order(nl);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return nu[i] > nu[j]; });
+  {
+    // sort (-nu, caller index) pairs: the same order as a stable sort by nu
+    std::vector<std::pair<double, int>> key(nl);
+    for (int l = 0; l < nl; ++l) key[l] = {-nu[l], l};
+    std::sort(key.begin(), key.end());
+    for (int s = 0; s < nl; ++s) order[s] = key[s].second;
+  }
   c->h_orig_of = order;
   c->h_sorted_of.assign(nl, 0);
   for (int s = 0; s < nl; ++s) c->h_sorted_of[order[s]] = s;
