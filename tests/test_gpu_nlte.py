@@ -71,6 +71,28 @@ def test_batch_uneven_levels_vs_oracle(xt, precision, tol):
         assert worst < 1e-8
 
 
+def test_fp32_zero_pivot_falls_back_to_fp64(xt):
+    """A warm start with one level at 1e-300 of the others scales that level's
+    column of the FP32 factor below the FP32 range: the FP32 factor meets an
+    exactly zero pivot, and the system is solved in FP64 instead (status bit
+    XT_SE_FALLBACK, no singular system), to the FP64 bar."""
+    w = synth.nlte_batch(n=2, seed=3, L_range=(20, 40))
+    warm = w.pops.copy()
+    for z in range(w.n_ion):
+        warm[:, int(w.level_off[z]) + 3] = 1e-300      # level 3 of every ion
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        pops = np.zeros((w.ncell, w.nlev))
+        status = np.zeros(w.ncell * w.n_ion, dtype=np.int32)
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, rates=xt.XT_RATES_JBAR,
+                           warm=xt.XT_WARM_GIVEN, warm_in=warm, jbar_W=w.jbar_W, jbar_TR=w.jbar_TR,
+                           levels_used=w.levels_used, pops_out=pops, status_out=status)
+    assert st["singular"] == 0
+    assert st["fp64_fallbacks"] == w.ncell * w.n_ion, st
+    assert np.all(status & xt.XT_SE_FALLBACK) and not np.any(status & xt.XT_SE_SINGULAR)
+    _check(w, pops, _oracle_batch(w, range(w.ncell)), 1e-10)
+
+
 def test_lte_warm_start_and_full_levels(xt):
     w = synth.nlte_batch(n=2, seed=2, L_range=(20, 60))
     with _ctx(xt) as ctx:
