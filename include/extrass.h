@@ -232,7 +232,10 @@ typedef struct {
      * a function of the solution and takes up to newton_max steps from the warm
      * start.  Each step factors the Jacobian (M plus every line's derivative of
      * its net downward flow through beta_S) in the chosen precision, with an
-     * FP64 residual, for the correction d.  With r = max |d_i| / n_i over
+     * FP64 residual, for the correction d (refined until its last update is
+     * below max(tol, newton_tol / 100) of every level's population: the fixed
+     * point is set by the FP64 right-hand side, so the step needs no more).
+     * With r = max |d_i| / n_i over
      * levels with n_i >= 1e-30 n_z: stop when r <= newton_tol; else every level
      * moves by the factor 1 + lam d_i / n_i kept within [1/newton_maxvar,
      * newton_maxvar], lam = 1 once r <= 0.1, before that 0.95, then 0.75, 0.5,

@@ -78,6 +78,7 @@ struct SeArgs {
   double* __restrict__ iters;           // [cell * n_ion + z] refinement (or Newton) steps
   int newton_max;                       // 0: linear solve with beta_S from pops
   double newton_tol, newton_maxvar;
+  FixExpTables fx;                      // e^-tau tables (fixed point)
 };
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
@@ -102,6 +103,29 @@ __device__ __forceinline__ float scaled_f32(double w, int k) {
   uint32_t m = (uint32_t)kept + ((rem > half || (rem == half && (kept & 1ull))) ? 1u : 0u);
   if (ef > 0) m += ((uint32_t)(ef - 1) << 23);   // the hidden bit of kept adds the last 1
   return __uint_as_float(sign | m);
+}
+
+// beta_S(tau) (Eq. beta_Sobolev) and, if dbeta is not null, d beta_S / d tau,
+// without FP64 transcendentals or divisions: for tau >= 2^-10, e^-tau and
+// 1 - e^-tau in fixed point (expneg) and the quotients beta = (1 - e^-tau) / tau,
+// beta' = -(1 - e^-tau - tau e^-tau) / tau^2 on the integer pipe (div_pos);
+// below 2^-10 the Taylor series beta = sum (-tau)^k / (k+1)! and its derivative
+// to the tau^4 terms (the next terms are below 2e-18 relative).  beta = 1 and
+// beta' = 0 for tau <= 0 (no trapping).
+__device__ __forceinline__ double sobolev_beta_fix(const FixExpTables& fx, double tau, double* dbeta) {
+  const long long tb = __double_as_longlong(tau);
+  if (tb <= 0) {                                   // tau <= +0 (or negative)
+    if (dbeta) *dbeta = 0.0;
+    return 1.0;
+  }
+  if (tb < __double_as_longlong(0x1p-10)) {
+    if (dbeta) *dbeta = fma(tau, fma(tau, fma(tau, fma(tau, -1.0 / 144.0, 1.0 / 30.0), -0.125), 1.0 / 3.0), -0.5);
+    return fma(tau, fma(tau, fma(tau, fma(tau, 1.0 / 120.0, -1.0 / 24.0), 1.0 / 6.0), -0.5), 1.0);
+  }
+  double ex, ome;
+  expneg(fx, tau, ex, ome);
+  if (dbeta) *dbeta = neg_bits(div_pos(fma(-tau, ex, ome), tau * tau));
+  return div_pos(ome, tau);
 }
 
 // D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
@@ -407,7 +431,10 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   __shared__ unsigned long long item;
   __shared__ double red[32];
   __shared__ int flag;
+  __shared__ FixExpTables sfx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  for (int k = tid; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
+    reinterpret_cast<uint64_t*>(&sfx)[k] = reinterpret_cast<const uint64_t*>(&a.fx)[k];
   double* W = a.W64 + (int64_t)blockIdx.x * a.wlen;
   // each CTA owns L_max^2 doubles of WT, used as T (factor) or double (fallback)
   T* WT = (T*)((double*)a.WT + (int64_t)blockIdx.x * a.wlen);
@@ -501,14 +528,15 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           const int64_t lu = __double_as_longlong(Lr[3]);
           const int lo = (int)(lu & 0xFFFFFFFF) - off;
           const double tau = Lr[1] * (nbeta[lo] - Lr[2] * nbeta[u]);
-          const double beta = tau <= 0.0 ? 1.0 : -expm1(-tau) / tau;   // no trapping for tau <= 0
+          const double beta = sobolev_beta_fix(sfx, tau, nullptr);
           double Rlu = 0.0;
           if (a.rates == XT_RATES_JBAR) {
             Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
           } else if (a.rates == XT_RATES_ESTIMATORS) {
             // fixed per atom: the populations of the transport pass set it
             const double net = pc[off + lo] - Lr[2] * pc[off + u];
-            if (net > 0.0) Rlu = a.S[row * a.nline + s] / (net * a.V);
+            const double Sv = a.S[row * a.nline + s];
+            if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * a.V);
           }
           atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
           atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u
@@ -579,9 +607,8 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
             const int lo = (int)(lu & 0xFFFFFFFF) - off;
             const double net = sNk[lo] - Lr[2] * sNk[u];
             const double tau = Lr[1] * net;
-            double db = 0.0;
-            if (tau > 1e-8) db = (tau * exp(-tau) + expm1(-tau)) / (tau * tau);
-            else if (tau > 0.0) db = -0.5;
+            double db;
+            sobolev_beta_fix(sfx, tau, &db);
             if (db == 0.0) continue;
             const double BJ = a.rates == XT_RATES_JBAR ? a.Rj[s] : 0.0;
             const double t = db * Lr[1] * (a.A[s] * sNk[u] - BJ * net);
@@ -668,13 +695,19 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           for (int i = tid; i < L; i += blockDim.x) {
             const double d = (double)sVec[i] * sX0[i];
             sN[i] += d;
-            // relative to the solution; a Newton correction relative to 1e-8 of the level
-            dmax = fmax(dmax, fabs(d) / fmax(fabs(sN[i]), newton ? 1e-8 * sX0[i] : 1e-30 * nz));
+            // relative to the solution; a Newton correction relative to its level's
+            // population (the step needs it resolved below the Newton tolerance:
+            // the fixed point is set by the FP64 right-hand side, not by the step)
+            dmax = fmax(dmax, fabs(d) / (newton ? sX0[i] : fmax(fabs(sN[i]), 1e-30 * nz)));
           }
           for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
           if ((tid & 31) == 0) red[tid >> 5] = dmax;
           block_sync();
-          if (tid == 0) { double t = 0; for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]); flag = t < a.tol; }
+          if (tid == 0) {
+            double t = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]);
+            flag = t < (newton ? fmax(a.tol, 1e-2 * a.newton_tol) : a.tol);
+          }
           block_sync();
           if (flag && it_ir > 0) { conv = true; ++it_ir; break; }
           // residual sB - W x in FP64
@@ -976,6 +1009,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   }
   SeArgs a;
   std::memset(&a, 0, sizeof(a));
+  fixexp_tables(&a.fx);
   a.g = G; a.nlev = c->nlev; a.n_ion = c->n_ion; a.nline = c->nline;
   a.level_off = c->d_level_off; a.E = c->d_E; a.glev = c->d_g; a.nion = c->d_nion;
   a.Te = c->d_Te; a.ne = c->d_ne; a.dep = c->d_dep; a.pops = c->d_pops; a.warm = warm;
