@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   __shared__ unsigned long long item;
   __shared__ double red[32];
   __shared__ int flag;
+  __shared__ double dprev;                // the refinement's previous largest correction
   __shared__ FixExpTables sfx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   for (int k = tid; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
@@ -704,9 +705,15 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           if ((tid & 31) == 0) red[tid >> 5] = dmax;
           block_sync();
           if (tid == 0) {
+            // converged when the last correction is below the tolerance, or when
+            // the error it leaves is: refinement contracts the error by about
+            // rho = d_k / d_(k-1) per step, so after d_k is applied the error is
+            // about d_k^2 / d_(k-1) (ratio test of iterative refinement)
             double t = 0;
             for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]);
-            flag = t < (newton ? fmax(a.tol, 1e-2 * a.newton_tol) : a.tol);
+            const double tl = newton ? fmax(a.tol, 1e-2 * a.newton_tol) : a.tol;
+            flag = t < tl || (it_ir > 0 && t < 0.5 * dprev && t * t < tl * dprev);
+            dprev = t;
           }
           block_sync();
           if (flag && it_ir > 0) { conv = true; ++it_ir; break; }
