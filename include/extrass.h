@@ -187,9 +187,10 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
  *   XT_PREC_FP64     LU with partial pivoting in FP64 (the plain method).
  *   XT_PREC_FP32_IR  the system scaled by the warm start (columns) and row
  *                    maxima, LU in FP32, refined in FP64 (residual, update)
- *                    until the largest relative correction, or the error it
- *                    leaves (about d_k^2 / d_(k-1) for successive corrections
- *                    d that contract by half or more), is below tol.
+ *                    until the error every level keeps after the last
+ *                    correction is below tol (relative): |d_k|, or d_k^2 /
+ *                    |d_(k-1)| where the level's successive corrections d
+ *                    contract by half or more.
  *   XT_PREC_TF32_IR  as XT_PREC_FP32_IR with the rank-nb trailing updates of
  *                    the blocked LU on the tensor cores (TF32 operands, FP32
  *                    accumulation); more refinement steps, same FP64 result.

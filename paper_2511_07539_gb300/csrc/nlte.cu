@@ -431,7 +431,6 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   __shared__ unsigned long long item;
   __shared__ double red[32];
   __shared__ int flag;
-  __shared__ double dprev;                // the refinement's previous largest correction
   __shared__ FixExpTables sfx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   for (int k = tid; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
@@ -692,28 +691,33 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           for (int i = tid; i < L; i += blockDim.x) { const int q = sPerm[i]; sVec[i] = (T)(sRes[q] * sR[q]); }
           block_sync();
           lu_solve<T>(WT, L, sVec);
+          // the error each level keeps after this correction d_k: refinement
+          // contracts it by about rho = |d_k| / |d_(k-1)| per step, so about
+          // d_k^2 / |d_(k-1)| where the level's corrections halve or better, else
+          // |d_k| (the previous corrections sit in the panel buffer, free here);
+          // relative to the solution, or for a Newton correction to its level's
+          // population (the step needs it resolved below the Newton tolerance:
+          // the fixed point is set by the FP64 right-hand side, not by the step)
           double dmax = 0;
+          double* dprev_i = (double*)sPan;
           for (int i = tid; i < L; i += blockDim.x) {
             const double d = (double)sVec[i] * sX0[i];
             sN[i] += d;
-            // relative to the solution; a Newton correction relative to its level's
-            // population (the step needs it resolved below the Newton tolerance:
-            // the fixed point is set by the FP64 right-hand side, not by the step)
-            dmax = fmax(dmax, fabs(d) / (newton ? sX0[i] : fmax(fabs(sN[i]), 1e-30 * nz)));
+            double e = fabs(d);
+            if (it_ir > 0) {
+              const double q = fabs(dprev_i[i]);
+              if (e < 0.5 * q) e = e * (e / q);
+            }
+            dprev_i[i] = d;
+            dmax = fmax(dmax, e / (newton ? sX0[i] : fmax(fabs(sN[i]), 1e-30 * nz)));
           }
           for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
           if ((tid & 31) == 0) red[tid >> 5] = dmax;
           block_sync();
           if (tid == 0) {
-            // converged when the last correction is below the tolerance, or when
-            // the error it leaves is: refinement contracts the error by about
-            // rho = d_k / d_(k-1) per step, so after d_k is applied the error is
-            // about d_k^2 / d_(k-1) (ratio test of iterative refinement)
             double t = 0;
             for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, red[k]);
-            const double tl = newton ? fmax(a.tol, 1e-2 * a.newton_tol) : a.tol;
-            flag = t < tl || (it_ir > 0 && t < 0.5 * dprev && t * t < tl * dprev);
-            dprev = t;
+            flag = t < (newton ? fmax(a.tol, 1e-2 * a.newton_tol) : a.tol);
           }
           block_sync();
           if (flag && it_ir > 0) { conv = true; ++it_ir; break; }
