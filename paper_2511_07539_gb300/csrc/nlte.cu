@@ -7,18 +7,24 @@
 //   assemble  the FP64 rate matrix of the system in the CTA's global
 //             workspace: collisions for every level pair (Boltzmann factors
 //             per level, detailed balance), radiative lines (A beta_S,
-//             photoexcitation, stimulated emission) by atomics, the
-//             non-thermal term into the ground level, the diagonal as minus the
-//             total out-rate, the ground-level equation replaced by sum n = n_z;
-//   factor    blocked right-looking LU with partial pivoting: a warp factors
-//             each panel of nb columns in shared memory, then the CTA swaps
-//             rows, solves for the panel's U rows and updates the trailing
-//             matrix through L2 (rank-nb update from shared memory);
+//             photoexcitation, stimulated emission) by atomics, beta_S from
+//             the fixed-point exponential, the non-thermal term into the
+//             ground level, the diagonal as minus the total out-rate (column
+//             sums), the ground-level equation replaced by sum n = n_z;
+//   factor    blocked right-looking LU with partial pivoting: the CTA factors
+//             each panel of nb columns in shared memory (a warp finds each
+//             pivot), then swaps rows, solves for the panel's U rows and
+//             updates the trailing matrix through L2 (rank-nb update from
+//             shared memory);
 //   solve     blocked forward/back substitution;
-//   refine    (FP32 path) the matrix scaled by the warm start (columns) and the
-//             row maxima is factored in FP32; residuals and updates are FP64
-//             until the largest relative correction is below tol; a system
-//             that does not converge is solved again in FP64.
+//   refine    (FP32 path) the matrix scaled by powers of two near the warm
+//             start (columns) and the row maxima is factored in FP32;
+//             residuals and updates are FP64 until the error every level keeps
+//             is below tol (a ratio test on successive corrections); a system
+//             that does not converge, or whose FP32 factor meets a zero pivot,
+//             is solved again in FP64.
+// Newton mode repeats assemble..refine on the Jacobian of the rate equations
+// with beta_S taken from the iterate (Sec. 2.2).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -10,6 +10,9 @@
 //              Eq. (thin_emissivity)); lab frequency nu_cmf / (1 - n.r/ct); the
 //              cell-walk state (distance to the next wall along each axis and
 //              the distance between walls).  Written to a packet pool (SoA).
+//              The quotients and the direction's square root run on the
+//              integer pipe (fixexp.cuh), and the searches for the emitting
+//              cell and the first line start from guide tables.
 //   k_trace    persistent: every lane owns one packet; a lane whose packet ends
 //              takes the next pool entry at once (warp-aggregated counter), so
 //              warps never wait for their longest-lived packet.  One loop
