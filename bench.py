@@ -137,6 +137,35 @@ def make_workload(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+def workload_config(w, world):
+    """The `config` object of both arms' lines: the workload by name and size."""
+    store_gb = w.ncell * w.nline * 8 / 1e9          # dense estimator store, FP64
+    l2 = (f"inputs larger than L2: estimator store ({store_gb:.1f} GB) cleared every step"
+          if store_gb > 0.129 else
+          f"inputs within L2 (estimator store {store_gb * 1e3:.1f} MB): a test case, not a bench line")
+    return {"workload": w.name, "cells": w.ncell, "lines": w.nline, "levels": w.nlev,
+            "packets_per_gpu": w.n_packets, "subdomains": list(w.subdomains),
+            "mode": "attenuation", "l2": l2, "parallelism": f"replicas{world}"}
+
+
+def replica_seed(base_seed, rank):
+    """Seed of rank `rank`'s replica: every rank transports its own packets."""
+    return base_seed + 1000003 * rank
+
+
+def reduce_over_ranks(ms, ev, dist=None, device="cuda"):
+    """(largest time, summed events) over the ranks of the default process
+    group (this rank's own values without one)."""
+    import torch
+    t = torch.tensor([ms, ev], dtype=torch.float64, device=device)
+    if dist is not None:
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t = tm
+    return float(t[0]), float(t[1])
+
+
 def cpu_baseline(w, seconds=12.0):
     """The oracle, as it stands, on one host core over a bounded packet sample."""
     import oracle
@@ -183,7 +212,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "sample": "50000 packets per step"},
+            "config": workload_config(w, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{n_pk} packets, 50000-packet random contiguous ranges"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -408,7 +437,7 @@ def main():
     ctx = xt.Context(local, stream.cuda_stream)
     ctx.load(w)
     # each rank transports its own replica of the emission (independent packets)
-    seed = w.seed + 1000003 * rank
+    seed = replica_seed(w.seed, rank)
     kw = dict(seed=seed)
 
     for _ in range(args.warmup):
@@ -433,13 +462,7 @@ def main():
     trace_ms = float(np.mean([s["trace_ms"] for s in stats]))
     escape_ms = float(np.mean([s["escape_ms"] for s in stats]))
     trace_launches = float(np.mean([s["rounds"] for s in stats]))
-    t = torch.tensor([ms, ev], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tm = t.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t = tm
-    ms_max, ev_all = float(t[0]), float(t[1])
+    ms_max, ev_all = reduce_over_ranks(ms, ev, dist)
     launches = int(sum(s["kernels"] for s in stats))
     value = ev_all / (ms_max * 1e-3)
 
@@ -479,7 +502,6 @@ def main():
     d2h = spec.nbytes + 18 * 8
     e2e_val = ev_e2e / (min(e2e_ms) * 1e-3) if e2e_ms else None
 
-    store_gb = xt.get_sizes(ctx.h)["store_bytes"] / 1e9
     peaks, src = _measured_peaks()
     # dominant kernel: the trace loop; its device time per launch from CUDA
     # events on the launching stream inside the library
@@ -498,11 +520,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "cells": w.ncell, "lines": w.nline, "levels": w.nlev,
-                   "packets_per_gpu": w.n_packets, "subdomains": list(w.subdomains),
-                   "mode": "attenuation",
-                   "l2": f"inputs larger than L2: estimator store ({store_gb:.1f} GB) cleared every step",
-                   "parallelism": f"replicas{world}"},
+        "config": workload_config(w, world),
         "events_per_step": ev / len(stats),
         "tests_per_step": float(np.mean([s["tests"] for s in stats])),
         "packets_per_s": w.n_packets * world / (ms_max * 1e-3 / args.steps),
