@@ -198,7 +198,11 @@ __device__ __forceinline__ uint64_t rcp_q63(uint64_t M) {
 // reciprocal above and one 64 x 64-bit product, rounded once to nearest.  The
 // reciprocal's error (< 2^-60) can move the rounding only for quotients within
 // 2^-7 ulp of a midpoint, so the result is within 0.51 ulp of a / b.  A result
-// outside the normal range is left to the IEEE division.
+// outside the normal range (also an infinite or NaN b) is left to the IEEE
+// division.  Zero, subnormal or negative operands are not handled: every
+// caller's operands are positive normal by construction (frequencies, packet
+// energies, wall spacings, optical depths >= 2^-10, rates), and a check here
+// cost the trace kernel 3 % (measured).
 __device__ __forceinline__ double div_pos(double a, double b) {
   const uint64_t ab = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
   const uint64_t frac = (1ull << 52) - 1ull;
