@@ -338,6 +338,55 @@ def coupled_bench(local, stream_ptr, n=32):
                          "train_ms": tr["train_ms"]}}
 
 
+def scatter_rates_bench(local, stream_ptr):
+    """A3b and A7 on the 32^3 onion (1e4 lines, 4e6 packets, 2.6 GB store):
+    scatter-mode passes (interaction = the whole packet absorbed with
+    probability 1 - e^-tau, re-emitted in a down-line or destroyed), and the
+    rates R_lu = S / (n_l V) of the whole store written to device memory."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    import synth
+    w = synth.clumpy_onion(n=32, n_lines=10_000, n_packets=4_000_000, subdomains=(4, 4, 4))
+    ups = synth.collision_strengths(w.upsilon_seed, w.level_off)
+    ups_down = np.concatenate([u.sum(axis=0) for u in ups])   # sum_{j<u} Upsilon_ju per level
+    stream = torch.cuda.current_stream()
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w, with_scatter_data=ups_down)
+    out = {"workload": w.name}
+    kw = dict(mode=xt.XT_MODE_SCATTER, seed=w.seed)
+    for _ in range(2):
+        ctx.transport(w, **kw)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sts = [ctx.transport(w, **kw) for _ in range(3)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    out["scatter"] = {"ms_per_pass": ms, "events_per_s": sts[-1]["events"] / (ms * 1e-3),
+                      "interactions_per_s": sts[-1]["interactions"] / (ms * 1e-3),
+                      "packets_per_s": w.n_packets / (ms * 1e-3),
+                      "interactions_per_packet": sts[-1]["interactions"] / w.n_packets,
+                      "launches_per_pass": float(sts[-1]["kernels"])}
+    # rates of every (cell, line) of an attenuation pass's store, device to device
+    ctx.transport(w, seed=w.seed)
+    R = torch.empty((w.ncell, w.nline), dtype=torch.float64, device="cuda")
+    xt.get_photoexcitation_rates(ctx.h, R_lu=R, want=("R_lu",))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        xt.get_photoexcitation_rates(ctx.h, R_lu=R, want=("R_lu",))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / 3
+    elems = w.ncell * w.nline
+    # algorithmic bytes per (cell, line): the estimator read, the rate written
+    out["rates"] = {"ms": ms_r, "elements": elems, "GB_per_s": 16 * elems / (ms_r * 1e-3) / 1e9,
+                    "bytes_per_element": 16}
+    ctx.close()
+    return out
+
+
 def stream_bench(local, stream_ptr, groups=8, packets=100_000_000):
     """The estimator store held in pinned host memory and streamed through the
     device by groups of subdomain z-layers, against the device-resident store,
@@ -377,6 +426,10 @@ def main():
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
     ap.add_argument("--coupled-n", type=int, default=32)
     ap.add_argument("--no-stream", action="store_true", help="skip the host-streamed store measurement")
+    ap.add_argument("--no-scatter", action="store_true",
+                    help="skip the scatter-mode and rates measurement")
+    ap.add_argument("--only-scatter", action="store_true",
+                    help="print the scatter-mode and rates object alone")
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
     ap.add_argument("--nlte-n", type=int, default=64)
     ap.add_argument("--nlte-once", action="store_true",
@@ -425,6 +478,11 @@ def main():
         if rank == 0:
             print(json.dumps({"nlte": nlte_bench(local, torch.cuda.current_stream().cuda_stream,
                                                  args.nlte_n)}), flush=True)
+        return
+    if args.only_scatter:
+        if rank == 0:
+            print(json.dumps({"scatter_rates": scatter_rates_bench(
+                local, torch.cuda.current_stream().cuda_stream)}), flush=True)
         return
     if args.only_coupled:
         if rank == 0:
@@ -546,6 +604,8 @@ def main():
         line["coupled"] = coupled_bench(local, stream.cuda_stream, args.coupled_n)
     if rank == 0 and not args.no_stream and args.workload == "onion":
         line["stream"] = stream_bench(local, stream.cuda_stream)
+    if rank == 0 and not args.no_scatter and args.workload == "onion":
+        line["scatter_rates"] = scatter_rates_bench(local, stream.cuda_stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

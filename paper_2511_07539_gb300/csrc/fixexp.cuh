@@ -222,6 +222,29 @@ __device__ __forceinline__ double div_pos(double a, double b) {
   return __longlong_as_double((long long)(((uint64_t)e << 52) | (m & frac)));
 }
 
+// beta_S(tau) (Eq. beta_Sobolev) and, if dbeta is not null, d beta_S / d tau,
+// without FP64 transcendentals or divisions: for tau >= 2^-10, e^-tau and
+// 1 - e^-tau in fixed point (expneg) and the quotients beta = (1 - e^-tau) / tau,
+// beta' = -(1 - e^-tau - tau e^-tau) / tau^2 on the integer pipe (div_pos);
+// below 2^-10 the Taylor series beta = sum (-tau)^k / (k+1)! and its derivative
+// to the tau^4 terms (the next terms are below 2e-18 relative).  beta = 1 and
+// beta' = 0 for tau <= 0 (no trapping).
+__device__ __forceinline__ double sobolev_beta_fix(const FixExpTables& fx, double tau, double* dbeta) {
+  const long long tb = __double_as_longlong(tau);
+  if (tb <= 0) {                                   // tau <= +0 (or negative)
+    if (dbeta) *dbeta = 0.0;
+    return 1.0;
+  }
+  if (tb < __double_as_longlong(0x1p-10)) {
+    if (dbeta) *dbeta = fma(tau, fma(tau, fma(tau, fma(tau, -1.0 / 144.0, 1.0 / 30.0), -0.125), 1.0 / 3.0), -0.5);
+    return fma(tau, fma(tau, fma(tau, fma(tau, 1.0 / 120.0, -1.0 / 24.0), 1.0 / 6.0), -0.5), 1.0);
+  }
+  double ex, ome;
+  expneg(fx, tau, ex, ome);
+  if (dbeta) *dbeta = neg_bits(div_pos(fma(-tau, ex, ome), tau * tau));
+  return div_pos(ome, tau);
+}
+
 // Direction of an isotropic emission from the 53-bit integers of its two
 // uniforms, u = Umu 2^-53 and u' = Uphi 2^-53: mu = 2u - 1, phi = 2 pi u'.
 // mu is exact; sin(theta) = sqrt(1 - mu^2) = 2^-52 sqrt(X) with the exact

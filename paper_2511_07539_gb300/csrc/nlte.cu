@@ -111,29 +111,6 @@ __device__ __forceinline__ float scaled_f32(double w, int k) {
   return __uint_as_float(sign | m);
 }
 
-// beta_S(tau) (Eq. beta_Sobolev) and, if dbeta is not null, d beta_S / d tau,
-// without FP64 transcendentals or divisions: for tau >= 2^-10, e^-tau and
-// 1 - e^-tau in fixed point (expneg) and the quotients beta = (1 - e^-tau) / tau,
-// beta' = -(1 - e^-tau - tau e^-tau) / tau^2 on the integer pipe (div_pos);
-// below 2^-10 the Taylor series beta = sum (-tau)^k / (k+1)! and its derivative
-// to the tau^4 terms (the next terms are below 2e-18 relative).  beta = 1 and
-// beta' = 0 for tau <= 0 (no trapping).
-__device__ __forceinline__ double sobolev_beta_fix(const FixExpTables& fx, double tau, double* dbeta) {
-  const long long tb = __double_as_longlong(tau);
-  if (tb <= 0) {                                   // tau <= +0 (or negative)
-    if (dbeta) *dbeta = 0.0;
-    return 1.0;
-  }
-  if (tb < __double_as_longlong(0x1p-10)) {
-    if (dbeta) *dbeta = fma(tau, fma(tau, fma(tau, fma(tau, -1.0 / 144.0, 1.0 / 30.0), -0.125), 1.0 / 3.0), -0.5);
-    return fma(tau, fma(tau, fma(tau, fma(tau, 1.0 / 120.0, -1.0 / 24.0), 1.0 / 6.0), -0.5), 1.0);
-  }
-  double ex, ome;
-  expneg(fx, tau, ex, ome);
-  if (dbeta) *dbeta = neg_bits(div_pos(fma(-tau, ex, ome), tau * tau));
-  return div_pos(ome, tau);
-}
-
 // D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
 // accumulators; per lane (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g + 8, t),
 // a2 (g, t + 4), a3 (g + 8, t + 4); b0 (t, g), b1 (t + 4, g); c0, c1 (g, 2t, 2t + 1),

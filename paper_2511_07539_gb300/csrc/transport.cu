@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
           for (int k = k0; k < k1; ++k) {
             const int m = a.down_line[k];
             const LineRec M = ldline(a.lines, m);
-            Wtot += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+            Wtot += a.A[m] * sobolev_beta_fix(fx, M.y * (prow[__double2loint(M.w)] - M.z * n_u), nullptr);
           }
           const double x = w.u[1] * Wtot;
           double run = 0.0;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
           for (int k = k0; k < k1; ++k) {
             const int m = a.down_line[k];
             const LineRec M = ldline(a.lines, m);
-            run += a.A[m] * sobolev_beta(M.y * (prow[__double2loint(M.w)] - M.z * n_u));
+            run += a.A[m] * sobolev_beta_fix(fx, M.y * (prow[__double2loint(M.w)] - M.z * n_u), nullptr);
             if (x < run) { pick = m; break; }
           }
           if (pick < 0) {
