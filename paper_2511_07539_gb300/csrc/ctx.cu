@@ -221,29 +221,32 @@ __global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops
                         const double* __restrict__ S, const double* __restrict__ invB,
                         const int* __restrict__ sorted_of, int64_t c0, int64_t nc, double V,
                         int which, double* __restrict__ out) {
-  int64_t n = nc * L.nline;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t cl = i / L.nline;
-    int l = (int)(i - cl * L.nline);
-    int64_t c = c0 + cl;
-    int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
-    int64_t row = row_of(g, ix, iy, iz);
-    int s = sorted_of[l];
-    // the store holds net photons absorbed; gross = net / f_corr, f_corr = net_pop / n_l
-    const double Snet = S[row * L.nline + s];
-    double v = 0.0;
-    if (Snet != 0.0) {
-      const double nl = pops[row * L.nlev + L.lo[s]];
-      const double net = nl - L.gratio[s] * pops[row * L.nlev + L.up[s]];
-      if (which == 0) {
-        v = Snet * nl / net;
-      } else {
-        const double R = Snet / (net * V);           // S / (n_l V)
-        v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
+  // a block per cell at a time: the cell's row found once, its lines spread
+  // over the threads (output in caller line order, coalesced)
+  for (int64_t cl = blockIdx.x; cl < nc; cl += gridDim.x) {
+    const int64_t c = c0 + cl;
+    const int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    const int64_t row = row_of(g, ix, iy, iz);
+    const double* Sr = S + row * L.nline;
+    const double* pr = pops + row * L.nlev;
+    double* o = out + cl * L.nline;
+    for (int l = threadIdx.x; l < L.nline; l += blockDim.x) {
+      const int s = sorted_of[l];
+      // the store holds net photons absorbed; gross = net / f_corr, f_corr = net_pop / n_l
+      const double Snet = Sr[s];
+      double v = 0.0;
+      if (Snet != 0.0) {
+        const double nl = pr[L.lo[s]];
+        const double net = nl - L.gratio[s] * pr[L.up[s]];
+        if (which == 0) {
+          v = Snet * nl / net;
+        } else {
+          const double R = Snet / (net * V);         // S / (n_l V)
+          v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
+        }
       }
+      o[l] = v;
     }
-    out[i] = v;
   }
 }
 
@@ -619,7 +622,8 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
       double* o = out + (size_t)(a - c0) * c->nline;
       const int64_t n = (b - a) * c->nline;
       rc = deliver(c, o, (size_t)n * sizeof(double), [&](void* d) {
-        k_rates<<<grid_blocks(n, 256), 256, 0, c->stream>>>(G, L, c->d_pops, Sg, c->d_invB, c->d_orig, a, b - a, V, which, (double*)d);
+        k_rates<<<(int)std::max<int64_t>(1, std::min<int64_t>(b - a, 152 * 16)), 256, 0, c->stream>>>(
+            G, L, c->d_pops, Sg, c->d_invB, c->d_orig, a, b - a, V, which, (double*)d);
       });
       if (rc) return rc;
       XT_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -627,9 +631,9 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
     return XT_OK;
   }
   size_t bytes = (size_t)nc * c->nline * sizeof(double);
-  int64_t n = nc * c->nline;
   int rc = deliver(c, out, bytes, [&](void* d) {
-    k_rates<<<grid_blocks(n, 256), 256, 0, c->stream>>>(c->geo, L, c->d_pops, c->d_S, c->d_invB, c->d_orig, c0, nc, V, which, (double*)d);
+    k_rates<<<(int)std::max<int64_t>(1, std::min<int64_t>(nc, 152 * 16)), 256, 0, c->stream>>>(
+        c->geo, L, c->d_pops, c->d_S, c->d_invB, c->d_orig, c0, nc, V, which, (double*)d);
   });
   if (rc) return rc;
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
