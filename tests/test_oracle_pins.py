@@ -12,6 +12,8 @@ P3  optically thin estimator in a cell slab vs a 6-D quadrature of the
     mean-intensity integral.
 P6  photon ledger closure; comoving energy closure in scatter mode; the
     scatter-mode destruction probability of a single line.
+A7  the mean intensity of the rates readout against the Einstein relation
+    between A_ul (pinned above) and B_lu.
 """
 import os
 
@@ -73,6 +75,28 @@ def test_einstein_A_textbook_line():
     for lam, f, gl, gu, A_ref, tol in rows:
         A = L.xo_einstein_A(lam * 1e-8, gl, gu, f)
         assert A == pytest.approx(A_ref, rel=tol)
+
+
+# ---------------------------------------------------------------- A7
+def test_rates_mean_intensity_obeys_einstein_relation():
+    """Jbar = R_lu / B_lu: with the B_lu the readout implies, B = R_lu / Jbar,
+    the Einstein relation A_ul = (2 h nu^3 / c^2) (g_l / g_u) B_lu must give
+    the A_ul of the oscillator-strength form (pinned against the textbook H
+    alpha value above), so no factor of B_lu can be dropped unseen."""
+    w = synth.uniform_sphere(n=4, n_packets=2000, n_lines=12, seed=3)
+    S = np.random.default_rng(0).uniform(1.0, 2.0, (w.ncell, w.nline)) * 1e30
+    R_lu, R_ul, J = oracle.rates(w, S)
+    c = int(np.nonzero(w.rho > 0)[0][0])
+    B = R_lu[c] / J[c]
+    nu = 2.99792458e10 / (w.lambda_A * 1e-8)
+    gl, gu = w.g_level[w.lo], w.g_level[w.up]
+    A_rel = 2 * 6.62607015e-27 * nu ** 3 / 2.99792458e10 ** 2 * (gl / gu) * B
+    L = oracle.lib()
+    A_f = np.array([L.xo_einstein_A(lam * 1e-8, a, b, f)
+                    for lam, a, b, f in zip(w.lambda_A, gl, gu, w.f_lu)])
+    np.testing.assert_allclose(A_rel, A_f, rtol=1e-12)
+    np.testing.assert_allclose(R_ul[c], (gl / gu) * R_lu[c], rtol=1e-15)
+    assert np.all(R_lu[c] > 0)
 
 
 # ---------------------------------------------------------------- P7
