@@ -14,6 +14,7 @@ P6  photon ledger closure; comoving energy closure in scatter mode; the
     scatter-mode destruction probability of a single line.
 A7  the mean intensity of the rates readout against the Einstein relation
     between A_ul (pinned above) and B_lu.
+A5  spectrum normalisation (energy closure against the ledger) and isotropy.
 """
 import os
 
@@ -146,6 +147,35 @@ def test_viewer_and_lambda_bins():
         assert L.xo_lambda_bin(mid, lam0, dlog, 1000) == k
     assert L.xo_lambda_bin(lam0 * 0.999, lam0, dlog, 1000) == -1
     assert L.xo_lambda_bin(lam0 * (1 + dlog) ** 1000.5, lam0, dlog, 1000) == -1
+
+
+def test_spectrum_normalisation_and_isotropy():
+    """The binned spectrum holds every escaped erg (the ledger counts them on
+    its own); L_lambda per viewer is 4 pi / dOmega_k E / dlambda, so the
+    solid-angle average of the viewers' luminosities and the angle-summed
+    L_lambda both integrate back to it; and a spherically symmetric source
+    of isotropic emission lights every viewer in proportion to its solid angle
+    (chi-square over the 400 viewers)."""
+    w = synth.uniform_sphere(n_packets=40_000)
+    o = oracle.transport(w)
+    spec, led = o["spec"], o["ledger"]
+    E = spec.sum()
+    assert E == pytest.approx(led["esc_E"] - led["oob_E"], rel=1e-12)
+    lam0, nb = w.spec_band_A
+    L_k, L_tot, edges = oracle.spectrum_L_lambda(spec, lam0, 1e-3)
+    dlam = np.diff(edges)
+    th = np.linspace(0.0, np.pi, 21)
+    dOm = np.repeat(2 * np.pi / 20 * (np.cos(th[:-1]) - np.cos(th[1:])), 20)
+    assert (L_tot * dlam).sum() == pytest.approx(E, rel=1e-12)
+    assert ((dOm / (4 * np.pi))[:, None] * L_k * dlam[None, :]).sum() == pytest.approx(E, rel=1e-12)
+    # isotropy: energy per viewer against E dOmega_k / 4 pi, variance from the
+    # packets' spread of energies
+    Ek = spec.sum(axis=1)
+    expect = E * dOm / (4 * np.pi)
+    n_esc = 40_000 * (led["esc_N"] / led["emit_N"])       # escaped packets, about
+    mean_e = E / n_esc
+    chi2 = np.sum((Ek - expect) ** 2 / (expect * mean_e * 1.2))
+    assert chi2 / 400 < 1.6, chi2 / 400
 
 
 # ---------------------------------------------------------------- P4
