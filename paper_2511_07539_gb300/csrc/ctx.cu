@@ -10,45 +10,6 @@
 
 namespace xt {
 
-// Tables of the fixed-point exponential (fixexp.cuh).  ln2 from its series
-// sum 1/(i 2^i) in Q127 integer arithmetic; 1/n! by exact integer division;
-// e^-j/64 from the host's extended-precision expl (64 or more mantissa bits).
-void fixexp_tables(FixExpTables* t) {
-  typedef unsigned __int128 u128;
-  u128 ln2 = 0;
-  for (int i = 1; i < 127; ++i) ln2 += (((u128)1) << (127 - i)) / (u128)i;   // ln2 2^127
-  t->ln2_a = (uint64_t)(ln2 >> 74);                    // ln2 2^53
-  t->ln2_b = (uint64_t)(ln2 >> 10);                    // next 64 bits
-  const u128 one = ((u128)1) << 63;
-  u128 f = 1;
-  for (int n = 0; n < 10; ++n) {
-    if (n > 0) f *= (u128)n;
-    t->fact[n] = (uint64_t)((one + f / 2) / f);
-  }
-  for (int j = 0; j < 48; ++j) {
-    long double v = expl(-(long double)j / 64.0L) * 9223372036854775808.0L;
-    t->tab[j] = (uint64_t)(v + 0.5L);
-  }
-}
-
-// Tables of the fixed-point sine/cosine (fixexp.cuh), from the host's
-// extended-precision sinl/cosl and M_PIl; Taylor factors by integer division.
-void fixtrig_tables(FixTrigTables* t) {
-  const long double pi = 3.141592653589793238462643383279502884L;
-  const long double q63 = 9223372036854775808.0L;
-  for (int j = 0; j <= 64; ++j) {
-    t->sin_t[j] = (uint64_t)(sinl(pi * j / 256.0L) * q63 + 0.5L);
-    t->cos_t[j] = (uint64_t)(cosl(pi * j / 256.0L) * q63 + 0.5L);
-  }
-  t->pi4 = (uint64_t)(pi / 4.0L * q63 + 0.5L);
-  typedef unsigned __int128 u128;
-  const u128 one = ((u128)1) << 63;
-  for (int m = 1; m <= 8; ++m) {
-    const u128 den = (u128)m * (u128)(m + 1);
-    t->inv[m - 1] = (uint64_t)((one + den / 2) / den);
-  }
-}
-
 int fail(xt_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;

@@ -15,7 +15,19 @@
 // values; tau >= 709 gives e^-tau = 0.  The tables are computed on the host
 // (xt::fixexp_tables).
 #pragma once
+#include <math.h>
 #include <stdint.h>
+
+// XT_FIXEXP_HOST compiles these routines for the host (a CPU test checks them
+// against extended-precision references); the header it includes defines the
+// device intrinsics used below, and the FP32 approximations become the
+// correctly rounded host operations.  CUDA builds never define it.
+#ifdef XT_FIXEXP_HOST
+#include "fixexp_host.h"
+#define XT_FX static inline
+#else
+#define XT_FX __device__ __forceinline__
+#endif
 
 namespace xt {
 
@@ -33,17 +45,53 @@ struct FixTrigTables {
   uint64_t inv[8];      // 1/(m(m+1)) for m = 1..8 (Taylor factors), Q63
 };
 
-void fixtrig_tables(FixTrigTables* t);  // host
+// Tables of the fixed-point exponential (host).  ln2 from its series
+// sum 1/(i 2^i) in Q127 integer arithmetic; 1/n! by exact integer division;
+// e^-j/64 from the host's extended-precision expl (64 or more mantissa bits).
+inline void fixexp_tables(FixExpTables* t) {
+  typedef unsigned __int128 u128;
+  u128 ln2 = 0;
+  for (int i = 1; i < 127; ++i) ln2 += (((u128)1) << (127 - i)) / (u128)i;   // ln2 2^127
+  t->ln2_a = (uint64_t)(ln2 >> 74);                    // ln2 2^53
+  t->ln2_b = (uint64_t)(ln2 >> 10);                    // next 64 bits
+  const u128 one = ((u128)1) << 63;
+  u128 f = 1;
+  for (int n = 0; n < 10; ++n) {
+    if (n > 0) f *= (u128)n;
+    t->fact[n] = (uint64_t)((one + f / 2) / f);
+  }
+  for (int j = 0; j < 48; ++j) {
+    long double v = expl(-(long double)j / 64.0L) * 9223372036854775808.0L;
+    t->tab[j] = (uint64_t)(v + 0.5L);
+  }
+}
 
-void fixexp_tables(FixExpTables* t);    // host
+// Tables of the fixed-point sine/cosine (host), from the host's
+// extended-precision sinl/cosl and M_PIl; Taylor factors by integer division.
+inline void fixtrig_tables(FixTrigTables* t) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const long double q63 = 9223372036854775808.0L;
+  for (int j = 0; j <= 64; ++j) {
+    t->sin_t[j] = (uint64_t)(sinl(pi * j / 256.0L) * q63 + 0.5L);
+    t->cos_t[j] = (uint64_t)(cosl(pi * j / 256.0L) * q63 + 0.5L);
+  }
+  t->pi4 = (uint64_t)(pi / 4.0L * q63 + 0.5L);
+  typedef unsigned __int128 u128;
+  const u128 one = ((u128)1) << 63;
+  for (int m = 1; m <= 8; ++m) {
+    const u128 den = (u128)m * (u128)(m + 1);
+    t->inv[m - 1] = (uint64_t)((one + den / 2) / den);
+  }
+}
 
-__device__ __forceinline__ uint64_t mul_q63(uint64_t a, uint64_t b) {
+
+XT_FX uint64_t mul_q63(uint64_t a, uint64_t b) {
   const uint64_t hi = __umul64hi(a, b), lo = a * b;
   return (hi << 1) | (lo >> 63);
 }
 
 // q * 2^-63 * 2^scale as a double, rounded to nearest even; 0 below 2^-1022.
-__device__ __forceinline__ double q63_to_double(uint64_t q, int scale) {
+XT_FX double q63_to_double(uint64_t q, int scale) {
   if (q == 0) return 0.0;
   const int b = 63 - __clzll((long long)q);
   int e = b - 63 + scale;
@@ -64,7 +112,7 @@ __device__ __forceinline__ double q63_to_double(uint64_t q, int scale) {
 }
 
 // tau > 0 (finite).  Writes e^-tau and 1 - e^-tau.
-__device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double& ex, double& ome) {
+XT_FX void expneg(const FixExpTables& T, double tau, double& ex, double& ome) {
   // range tests on the bit pattern (tau > 0: integer order = numeric order)
   const uint64_t bits = (uint64_t)__double_as_longlong(tau);
   if (bits >= (uint64_t)__double_as_longlong(709.0)) { ex = 0.0; ome = 1.0; return; }
@@ -120,7 +168,7 @@ __device__ __forceinline__ void expneg(const FixExpTables& T, double tau, double
 // within about one ulp of sin and cos of the exact angle 2 pi u.
 // sincos_2pi_q63 leaves sin and cos of the angle within its quadrant in Q63
 // and returns the quadrant (0..3); quadrant_signs maps them to the full angle.
-__device__ __forceinline__ int sincos_2pi_q63(const FixTrigTables& T, uint64_t U, uint64_t& sa,
+XT_FX int sincos_2pi_q63(const FixTrigTables& T, uint64_t U, uint64_t& sa,
                                               uint64_t& ca) {
   const int oct = (int)(U >> 50);
   uint64_t g = U & ((1ull << 50) - 1ull);                  // fraction of the octant, Q50
@@ -150,11 +198,11 @@ __device__ __forceinline__ int sincos_2pi_q63(const FixTrigTables& T, uint64_t U
 
 // -x by flipping the sign bit (an FP64 negation would take a slot of the
 // FP64 pipe)
-__device__ __forceinline__ double neg_bits(double x) {
+XT_FX double neg_bits(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
 }
 
-__device__ __forceinline__ void quadrant_signs(int q, double vs, double vc, double& s, double& c) {
+XT_FX void quadrant_signs(int q, double vs, double vc, double& s, double& c) {
   switch (q) {
     case 0: s = vs; c = vc; break;
     case 1: s = vc; c = neg_bits(vs); break;
@@ -163,7 +211,7 @@ __device__ __forceinline__ void quadrant_signs(int q, double vs, double vc, doub
   }
 }
 
-__device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, double& s, double& c) {
+XT_FX void sincos_2pi(const FixTrigTables& T, uint64_t U, double& s, double& c) {
   uint64_t sa, ca;
   const int q = sincos_2pi_q63(T, U, sa, ca);
   quadrant_signs(q, q63_to_double(sa, 0), q63_to_double(ca, 0), s, c);
@@ -174,16 +222,20 @@ __device__ __forceinline__ void sincos_2pi(const FixTrigTables& T, uint64_t U, d
 // approximation of m (rcp.approx, about 23 correct bits); two Newton-Raphson
 // steps y <- y (2 - m y), each doubling the correct bits, run in 64-bit fixed
 // point, whose truncations keep the result within about 2^-61 relative.
-__device__ __forceinline__ uint64_t float_to_q63(float y) {     // 0.5 <= y <= 1
+XT_FX uint64_t float_to_q63(float y) {     // 0.5 <= y <= 1
   const uint32_t yb = __float_as_uint(y);
   const int e = (int)(yb >> 23) - 127;                            // -1 or 0
   return (uint64_t)((yb & 0x7FFFFFu) | 0x800000u) << (40 + e);
 }
 
-__device__ __forceinline__ uint64_t rcp_q63(uint64_t M) {
+XT_FX uint64_t rcp_q63(uint64_t M) {
   const float f = __uint_as_float((127u << 23) | (uint32_t)((M >> 39) & 0x7FFFFFu));
   float y;
+#ifdef XT_FIXEXP_HOST
+  y = 1.0f / f;
+#else
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+#endif
   uint64_t Y = float_to_q63(y);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -203,7 +255,7 @@ __device__ __forceinline__ uint64_t rcp_q63(uint64_t M) {
 // caller's operands are positive normal by construction (frequencies, packet
 // energies, wall spacings, optical depths >= 2^-10, rates), and a check here
 // cost the trace kernel 3 % (measured).
-__device__ __forceinline__ double div_pos(double a, double b) {
+XT_FX double div_pos(double a, double b) {
   const uint64_t ab = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
   const uint64_t frac = (1ull << 52) - 1ull;
   const uint64_t ma = (ab & frac) | (1ull << 52), mb = (bb & frac) | (1ull << 52);
@@ -229,7 +281,7 @@ __device__ __forceinline__ double div_pos(double a, double b) {
 // below 2^-10 the Taylor series beta = sum (-tau)^k / (k+1)! and its derivative
 // to the tau^4 terms (the next terms are below 2e-18 relative).  beta = 1 and
 // beta' = 0 for tau <= 0 (no trapping).
-__device__ __forceinline__ double sobolev_beta_fix(const FixExpTables& fx, double tau, double* dbeta) {
+XT_FX double sobolev_beta_fix(const FixExpTables& fx, double tau, double* dbeta) {
   const long long tb = __double_as_longlong(tau);
   if (tb <= 0) {                                   // tau <= +0 (or negative)
     if (dbeta) *dbeta = 0.0;
@@ -252,7 +304,7 @@ __device__ __forceinline__ double sobolev_beta_fix(const FixExpTables& fx, doubl
 // 1/sqrt (FP32 seed, y <- y (3 - a y^2) / 2 twice) in fixed point, and
 // n_x = sin(theta) cos(phi), n_y = sin(theta) sin(phi) are formed in Q63 and
 // rounded once.  No FP64 arithmetic.
-__device__ __forceinline__ void isotropic_fix(const FixTrigTables& T, uint64_t Umu, uint64_t Uphi,
+XT_FX void isotropic_fix(const FixTrigTables& T, uint64_t Umu, uint64_t Uphi,
                                               double n[3]) {
   const uint64_t two53 = 1ull << 53;
   const uint64_t t2 = 2 * Umu;
@@ -271,7 +323,11 @@ __device__ __forceinline__ void isotropic_fix(const FixTrigTables& T, uint64_t U
   const float f = __uint_as_float(((uint32_t)(127 + ea) << 23) |
                                   (uint32_t)((xm >> (39 + ea)) & 0x7FFFFFu));
   float y;
+#ifdef XT_FIXEXP_HOST
+  y = 1.0f / sqrtf(f);
+#else
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+#endif
   uint64_t Y = float_to_q63(y);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {

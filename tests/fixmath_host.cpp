@@ -1,0 +1,42 @@
+// The library's fixed-point routines (fixexp.cuh) compiled for the host, with
+// C entry points for a CPU test.  Test infrastructure only.
+#define XT_FIXEXP_HOST
+#include "fixexp.cuh"
+
+using namespace xt;
+
+extern "C" {
+
+void h_div_pos(const double* a, const double* b, double* q, long n) {
+  for (long i = 0; i < n; ++i) q[i] = div_pos(a[i], b[i]);
+}
+
+void h_expneg(const double* tau, double* ex, double* ome, long n) {
+  FixExpTables T;
+  fixexp_tables(&T);
+  for (long i = 0; i < n; ++i) expneg(T, tau[i], ex[i], ome[i]);
+}
+
+void h_sincos(const uint64_t* U, double* s, double* c, long n) {
+  FixTrigTables T;
+  fixtrig_tables(&T);
+  for (long i = 0; i < n; ++i) sincos_2pi(T, U[i], s[i], c[i]);
+}
+
+void h_isotropic(const uint64_t* Umu, const uint64_t* Uphi, double* nx, double* ny, double* nz, long n) {
+  FixTrigTables T;
+  fixtrig_tables(&T);
+  for (long i = 0; i < n; ++i) {
+    double v[3];
+    isotropic_fix(T, Umu[i], Uphi[i], v);
+    nx[i] = v[0]; ny[i] = v[1]; nz[i] = v[2];
+  }
+}
+
+void h_beta(const double* tau, double* beta, double* dbeta, long n) {
+  FixExpTables T;
+  fixexp_tables(&T);
+  for (long i = 0; i < n; ++i) beta[i] = sobolev_beta_fix(T, tau[i], &dbeta[i]);
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+"""The library's integer-pipe routines (fixexp.cuh: the quotient, the
+emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
+beta and its derivative) compiled for the host from the same source and
+checked against mpmath on the CPU, so that they are pinned without a GPU.
+On the device the FP32 seeds of the two Newton-Raphson iterations come from
+rcp/rsqrt.approx instead of the correctly rounded host operations; the bounds
+below hold for either seed.  (The same routines run on the GB300 in
+test_gpu_math.py.)"""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2511_07539_gb300", "csrc")
+EPS = 2.220446049250313e-16
+
+
+@pytest.fixture(scope="module")
+def fx(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    so = str(tmp_path_factory.mktemp("fixmath") / "fixmath_host.so")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-ffp-contract=off", "-I", HERE,
+                    "-I", CSRC, os.path.join(HERE, "fixmath_host.cpp"), "-o", so], check=True)
+    return C.CDLL(so)
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _call(lib, name, ins, nout):
+    n = ins[0].shape[0]
+    outs = [np.zeros(n) for _ in range(nout)]
+    getattr(lib, name)(*[_p(a) for a in ins], *[_p(o) for o in outs], C.c_long(n))
+    return outs
+
+
+def test_quotient(fx):
+    rng = np.random.default_rng(4)
+    a = 10 ** rng.uniform(-300, 300, 50000)
+    b = 10 ** rng.uniform(-300, 300, 50000)
+    keep = np.abs(np.log10(a) - np.log10(b)) < 300         # quotient in the normal range
+    a, b = a[keep], b[keep]
+    (q,) = _call(fx, "h_div_pos", [a, b], 1)
+    ulp = np.abs(q - a / b) / np.spacing(a / b)
+    assert ulp.max() <= 1.0 and np.mean(ulp == 0) > 0.98
+    mp.mp.dps = 40
+    for i in np.concatenate([np.nonzero(ulp > 0)[0][:100], np.arange(0, a.size, 211)]):
+        exact = mp.mpf(float(a[i])) / mp.mpf(float(b[i]))
+        assert abs(q[i] - exact) <= 0.51 * np.spacing(q[i]), (a[i], b[i])
+
+
+def test_exponential(fx):
+    rng = np.random.default_rng(5)
+    ln2 = np.log(2.0)
+    tau = np.concatenate([10 ** rng.uniform(-4, np.log10(700), 20000), ln2 * np.arange(1, 300),
+                          ln2 * np.arange(1, 300) * (1 + 2 * EPS), [0.6931471805599453, 1e-4]])
+    ex, ome = _call(fx, "h_expneg", [tau], 2)
+    mp.mp.dps = 40
+    for i in range(0, tau.size, 13):
+        te = mp.e ** (-mp.mpf(float(tau[i])))
+        assert abs(ex[i] - te) <= 0.6 * EPS * te, tau[i]
+        assert abs(ome[i] - (1 - te)) <= 8 * EPS * (1 - te), tau[i]
+
+
+def test_azimuth_and_direction(fx):
+    rng = np.random.default_rng(6)
+    U = np.concatenate([rng.integers(0, 2 ** 53, 20000, dtype=np.int64),
+                        np.array([0, 1, 2 ** 50, 2 ** 52, 2 ** 53 - 1], dtype=np.int64)]).astype(np.uint64)
+    V = rng.integers(0, 2 ** 53, U.size, dtype=np.int64).astype(np.uint64)
+    s, c = _call(fx, "h_sincos", [V], 2)
+    nx, ny, nz = _call(fx, "h_isotropic", [U, V], 3)
+    mu = (2 * U.astype(np.int64) - 2 ** 53).astype(np.float64) * 2.0 ** -53
+    np.testing.assert_array_equal(nz, mu)
+    np.testing.assert_allclose(nx * nx + ny * ny + nz * nz, 1.0, rtol=0, atol=4 * EPS)
+    mp.mp.dps = 50
+    for i in np.concatenate([np.arange(0, U.size, 17), np.arange(U.size - 5, U.size)]):
+        phi = 2 * mp.pi * mp.mpf(int(V[i])) / mp.mpf(2) ** 53
+        for got, ref in ((s[i], mp.sin(phi)), (c[i], mp.cos(phi))):
+            assert abs(got - ref) <= 0.5 * EPS * abs(ref) + 4e-18, (V[i], got)
+        m = 2 * mp.mpf(int(U[i])) / mp.mpf(2) ** 53 - 1
+        st = mp.sqrt(1 - m * m)
+        for got, ref in ((nx[i], st * mp.cos(phi)), (ny[i], st * mp.sin(phi))):
+            assert abs(got - ref) <= 0.6 * EPS * abs(ref) + 5e-18 * st, (U[i], V[i], got)
+
+
+def test_sobolev_beta_and_derivative(fx):
+    rng = np.random.default_rng(7)
+    tau = np.concatenate([10 ** rng.uniform(-20, 4, 5000), [0.0, -1.0, 2.0 ** -10,
+                          np.nextafter(2.0 ** -10, 0), 1e-300, 709.0, 800.0, 1e6]])
+    beta, dbeta = _call(fx, "h_beta", [tau], 2)
+    assert beta[-8] == 1.0 and dbeta[-8] == 0.0 and beta[-7] == 1.0 and dbeta[-7] == 0.0
+    mp.mp.dps = 50
+    for i in range(tau.size):
+        t = mp.mpf(float(tau[i]))
+        if t <= 0:
+            continue
+        b = -mp.expm1(-t) / t
+        if t < mp.mpf("1e-3"):      # the closed form cancels: its Taylor series
+            db = mp.fsum(k * (-t) ** (k - 1) * (-1) / mp.factorial(k + 1) for k in range(1, 40))
+        else:
+            db = (t * mp.exp(-t) + mp.expm1(-t)) / (t * t)
+        assert abs(beta[i] - b) <= 3 * EPS * b, (tau[i], beta[i])
+        # the derivative's numerator cancels to about tau^2 / 2 for small tau:
+        # a relative error up to ~2 / tau ulp just above the series range
+        bound = 4 * EPS if tau[i] < 2.0 ** -10 else 4 * EPS * max(1.0, 2.0 / float(tau[i]))
+        assert abs(dbeta[i] - db) <= bound * abs(db), (tau[i], dbeta[i], float(db))
