@@ -89,28 +89,6 @@ struct SeArgs {
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
-// w 2^k rounded to FP32 (to nearest even) with integer operations: the
-// exponent is shifted, the significand rounded from 52 bits to those FP32 keeps
-// (23, or fewer for results in the subnormal range, as a plain conversion
-// does); w must be finite and w 2^k < 2^127.
-__device__ __forceinline__ float scaled_f32(double w, int k) {
-  const uint64_t b = (uint64_t)__double_as_longlong(w);
-  const uint32_t sign = (uint32_t)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0) return __uint_as_float(sign);
-  const int ef = e - 1023 + k + 127;              // biased FP32 exponent
-  const uint64_t M = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
-  // keep M >> sh: sh = 29 for a normal result, 30 - ef below the normal range;
-  // the FP32 bits are then (ef << 23) + kept (a carry out of the significand
-  // steps the exponent, and a subnormal that rounds up to 2^-126 becomes normal)
-  const int sh = ef > 0 ? 29 : 30 - ef;
-  if (sh > 54) return __uint_as_float(sign);
-  const uint64_t kept = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-  uint32_t m = (uint32_t)kept + ((rem > half || (rem == half && (kept & 1ull))) ? 1u : 0u);
-  if (ef > 0) m += ((uint32_t)(ef - 1) << 23);   // the hidden bit of kept adds the last 1
-  return __uint_as_float(sign | m);
-}
-
 // D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
 // accumulators; per lane (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g + 8, t),
 // a2 (g, t + 4), a3 (g + 8, t + 4); b0 (t, g), b1 (t + 4, g); c0, c1 (g, 2t, 2t + 1),

@@ -39,4 +39,8 @@ void h_beta(const double* tau, double* beta, double* dbeta, long n) {
   for (long i = 0; i < n; ++i) beta[i] = sobolev_beta_fix(T, tau[i], &dbeta[i]);
 }
 
+void h_scaled_f32(const double* w, const int* k, float* out, long n) {
+  for (long i = 0; i < n; ++i) out[i] = scaled_f32(w[i], k[i]);
+}
+
 }  // extern "C"

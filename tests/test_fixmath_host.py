@@ -1,6 +1,7 @@
 """The library's integer-pipe routines (fixexp.cuh: the quotient, the
 emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
-beta and its derivative) compiled for the host from the same source and
+beta and its derivative, the scaled rounding to FP32 of the rate solve)
+compiled for the host from the same source and
 checked against mpmath on the CPU, so that they are pinned without a GPU.
 On the device the FP32 seeds of the two Newton-Raphson iterations come from
 rcp/rsqrt.approx instead of the correctly rounded host operations; the bounds
@@ -112,3 +113,24 @@ def test_sobolev_beta_and_derivative(fx):
         # a relative error up to ~2 / tau ulp just above the series range
         bound = 4 * EPS if tau[i] < 2.0 ** -10 else 4 * EPS * max(1.0, 2.0 / float(tau[i]))
         assert abs(dbeta[i] - db) <= bound * abs(db), (tau[i], dbeta[i], float(db))
+
+
+def test_scaled_rounding_to_fp32(fx):
+    """w 2^k rounded to FP32 with integer operations equals the correctly
+    rounded conversion (to nearest even, subnormals kept) bit for bit."""
+    rng = np.random.default_rng(8)
+    n = 200000
+    w = rng.choice([-1.0, 1.0], n) * 10 ** rng.uniform(-300, 300, n)
+    ew = np.frexp(w)[1] - 1
+    k = rng.integers(-200, 80, n) - ew                       # results from 2^-200 to 2^80
+    k = k.astype(np.int32)
+    # ties and the subnormal boundary: 24- and 25-bit significands near 2^-126 and 2^-149
+    m = rng.integers(2 ** 24, 2 ** 25, 2000).astype(np.float64)
+    w2 = np.concatenate([m, -m]) * 2.0 ** -24
+    k2 = rng.integers(-160, -120, w2.size).astype(np.int32)
+    w, k = np.concatenate([w, w2]), np.concatenate([k, k2])
+    out = np.zeros(w.size, dtype=np.float32)
+    fx.h_scaled_f32(_p(w), _p(k), _p(out), C.c_long(w.size))
+    with np.errstate(over="ignore", under="ignore"):
+        ref = np.ldexp(w, k).astype(np.float32)
+    np.testing.assert_array_equal(out.view(np.uint32), ref.view(np.uint32))
