@@ -6,11 +6,20 @@
 #pragma once
 #include <stdint.h>
 
+// XT_FIXEXP_HOST compiles the generator for the host (a CPU test checks it
+// against an independent implementation); CUDA builds never define it.
+#ifdef XT_FIXEXP_HOST
+#include "fixexp_host.h"
+#define XT_PX static inline
+#else
+#define XT_PX __device__ __forceinline__
+#endif
+
 namespace xt {
 
 struct U4 { double u[4]; };
 
-__device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+XT_PX void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
                                               uint64_t k0, uint64_t k1, uint64_t out[4]) {
   const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
   const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
@@ -26,7 +35,7 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
 }
 
 // (x >> 11) 2^-53 assembled from its bits with integer operations only (exact).
-__device__ __forceinline__ double u01(uint64_t x) {
+XT_PX double u01(uint64_t x) {
   const uint64_t m = x >> 11;
   if (m == 0) return 0.0;
   const int b = 63 - __clzll((long long)m);          // top bit, 0..52
@@ -35,11 +44,11 @@ __device__ __forceinline__ double u01(uint64_t x) {
 }
 
 // Raw words of draw e of a packet (the uniforms are their top 53 bits).
-__device__ __forceinline__ void draw_raw(uint64_t seed, int64_t packet, uint64_t e, uint64_t x[4]) {
+XT_PX void draw_raw(uint64_t seed, int64_t packet, uint64_t e, uint64_t x[4]) {
   philox4x64_10((uint64_t)packet, e, 0, 0, seed, 0, x);
 }
 
-__device__ __forceinline__ U4 draw(uint64_t seed, int64_t packet, uint64_t e) {
+XT_PX U4 draw(uint64_t seed, int64_t packet, uint64_t e) {
   uint64_t x[4];
   philox4x64_10((uint64_t)packet, e, 0, 0, seed, 0, x);
   U4 r;

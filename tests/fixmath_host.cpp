@@ -2,6 +2,7 @@
 // C entry points for a CPU test.  Test infrastructure only.
 #define XT_FIXEXP_HOST
 #include "fixexp.cuh"
+#include "philox.cuh"
 
 using namespace xt;
 
@@ -41,6 +42,16 @@ void h_beta(const double* tau, double* beta, double* dbeta, long n) {
 
 void h_scaled_f32(const double* w, const int* k, float* out, long n) {
   for (long i = 0; i < n; ++i) out[i] = scaled_f32(w[i], k[i]);
+}
+
+void h_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out, long n) {
+  for (long i = 0; i < n; ++i)
+    philox4x64_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], key[2 * i], key[2 * i + 1],
+                  out + 4 * i);
+}
+
+void h_u01(const uint64_t* x, double* out, long n) {
+  for (long i = 0; i < n; ++i) out[i] = u01(x[i]);
 }
 
 }  // extern "C"

@@ -1,7 +1,8 @@
 """The library's integer-pipe routines (fixexp.cuh: the quotient, the
 emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
-beta and its derivative, the scaled rounding to FP32 of the rate solve)
-compiled for the host from the same source and
+beta and its derivative, the scaled rounding to FP32 of the rate solve; and
+the Philox generator of philox.cuh) compiled for the host from the same
+source and
 checked against mpmath on the CPU, so that they are pinned without a GPU.
 On the device the FP32 seeds of the two Newton-Raphson iterations come from
 rcp/rsqrt.approx instead of the correctly rounded host operations; the bounds
@@ -134,3 +135,24 @@ def test_scaled_rounding_to_fp32(fx):
     with np.errstate(over="ignore", under="ignore"):
         ref = np.ldexp(w, k).astype(np.float32)
     np.testing.assert_array_equal(out.view(np.uint32), ref.view(np.uint32))
+
+
+def test_philox_vs_numpy(fx):
+    """The CUDA side's Philox4x64-10 against numpy's independent Philox (which
+    increments its counter before use), and u = (x >> 11) 2^-53 exactly."""
+    rng = np.random.default_rng(9)
+    n = 300
+    ctr = rng.integers(0, 2 ** 63, (n, 4), dtype=np.int64).astype(np.uint64)
+    ctr[:, 0] |= np.uint64(1)                    # nonzero 256-bit counter
+    key = rng.integers(0, 2 ** 63, (n, 2), dtype=np.int64).astype(np.uint64)
+    out = np.zeros((n, 4), dtype=np.uint64)
+    fx.h_philox(_p(ctr), _p(key), _p(out), C.c_long(n))
+    for i in range(n):
+        c = [int(x) for x in ctr[i]]
+        c256 = c[0] + (c[1] << 64) + (c[2] << 128) + (c[3] << 192)
+        bg = np.random.Philox(counter=c256 - 1, key=int(key[i, 0]) + (int(key[i, 1]) << 64))
+        assert np.array_equal(out[i], bg.random_raw(4).astype(np.uint64)), i
+    x = np.concatenate([out.ravel(), np.array([0, 2 ** 11 - 1, 2 ** 11, 2 ** 64 - 1], dtype=np.uint64)])
+    u = np.zeros(x.size)
+    fx.h_u01(_p(x), _p(u), C.c_long(x.size))
+    np.testing.assert_array_equal(u, (x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
