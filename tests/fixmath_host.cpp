@@ -1,8 +1,10 @@
-// The library's fixed-point routines (fixexp.cuh) compiled for the host, with
-// C entry points for a CPU test.  Test infrastructure only.
+// The library's fixed-point routines (fixexp.cuh), its Philox generator and
+// its packet quota compiled for the host, with C entry points for a CPU test.
+// Test infrastructure only.
 #define XT_FIXEXP_HOST
 #include "fixexp.cuh"
 #include "philox.cuh"
+#include "quota.h"
 
 using namespace xt;
 
@@ -52,6 +54,13 @@ void h_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out, long n) {
 
 void h_u01(const uint64_t* x, double* out, long n) {
   for (long i = 0; i < n; ++i) out[i] = u01(x[i]);
+}
+
+void h_quota(const double* L, long nc, long N, int64_t* qoff) {
+  std::vector<double> Lv(L, L + nc);
+  std::vector<int64_t> q;
+  packet_quota(Lv, (int64_t)N, q);
+  for (long i = 0; i <= nc; ++i) qoff[i] = q[i];
 }
 
 }  // extern "C"

@@ -1,8 +1,8 @@
 """The library's integer-pipe routines (fixexp.cuh: the quotient, the
 emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
 beta and its derivative, the scaled rounding to FP32 of the rate solve; and
-the Philox generator of philox.cuh) compiled for the host from the same
-source and
+the Philox generator of philox.cuh; the packet quota of quota.h) compiled
+for the host from the same source and
 checked against mpmath on the CPU, so that they are pinned without a GPU.
 On the device the FP32 seeds of the two Newton-Raphson iterations come from
 rcp/rsqrt.approx instead of the correctly rounded host operations; the bounds
@@ -156,3 +156,22 @@ def test_philox_vs_numpy(fx):
     u = np.zeros(x.size)
     fx.h_u01(_p(x), _p(u), C.c_long(x.size))
     np.testing.assert_array_equal(u, (x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
+
+
+def test_packet_quota_matches_the_oracle(fx):
+    """The library's largest-remainder quota (a selection of the largest
+    remainders, ties to the lower cell) equals the oracle's (pinned by brute
+    force) exactly, ties and empty cells included."""
+    import oracle
+    rng = np.random.default_rng(10)
+    for N in [1, 7, 1000, 123457, 100_000_000]:
+        for kind in range(3):
+            L = rng.random(5000) * (rng.random(5000) > 0.3)
+            if kind == 1:
+                L = np.round(L * 4) / 4                  # many equal remainders
+            if kind == 2:
+                L[:] = 0.0
+                L[rng.integers(0, 5000, 7)] = 1.0
+            q = np.zeros(L.size + 1, dtype=np.int64)
+            fx.h_quota(_p(L), C.c_long(L.size), C.c_long(N), _p(q))
+            np.testing.assert_array_equal(q, oracle.packet_quota(L, N))
