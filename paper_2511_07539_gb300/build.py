@@ -42,7 +42,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(
+    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(
         os.path.join(HERE, "..", "include", "*.h"))
     nvcc = _nvcc()
     objs = []
