@@ -1076,7 +1076,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   EmitArgs ea;
   ea.g = G; ea.qoff = c->d_qoff; ea.Lc = c->d_Lc; ea.Epk = c->d_Lc + G.ncell;
   ea.qguide = c->d_qguide;
-  ea.nuguide = p->emission == XT_EMIT_BAND ? c->d_nuguide : nullptr;
+  // (built with the quota for band emission over a non-empty line list)
+  ea.nuguide = (p->emission == XT_EMIT_BAND && c->nline > 0) ? c->d_nuguide : nullptr;
   ea.Eph = c->d_Lc + 2 * G.ncell; ea.cdf = c->d_wline;
   ea.sorted_of = c->d_orig; ea.nu_tab = c->d_nu; ea.nline = c->nline; ea.emission = p->emission;
   ea.seed = p->seed;
