@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "packet-line interactions/s"
 UNIT = "interactions/s"
 BYTES_PER_EVENT = 32          # n_l, n_u reads (16 B) + estimator read-modify-write (16 B)
+# per packet of the fused pass: the cell's packet energies read (16 B), and the
+# direction, lab frequency and id written for the escape tallies (40 B)
+BYTES_PER_PACKET = 56
 # DRAM bytes (read + write) per event of the attenuation trace kernel (which
 # emits its own packets), from an ncu capture of this kernel version on the
 # 32^3 onion case (829.3 + 497.9 MB over 7,813,774 events); the bench's launch
@@ -134,7 +137,49 @@ def make_workload(args):
                                   subdomains=(4, 4, 4))
     if args.workload == "sphere":
         return synth.uniform_sphere(n_packets=min(args.packets, 100_000))
+    if args.workload == "onion-thin":      # the event loop's regime: ~35 events per packet
+        return thin_onion(min(args.packets, THIN_PACKETS))
     raise SystemExit(f"unknown workload {args.workload}")
+
+
+THIN_POP_SCALE = 1e-7       # every population of the 64^3 onion scaled down
+THIN_PACKETS = 20_000_000
+
+
+def thin_onion(n_packets=THIN_PACKETS):
+    """The 64^3 x 1e5-line onion with every level population scaled by 1e-7:
+    the lines are 1e7 times thinner, so a packet meets ~300 resonances and
+    ~35 interaction points (tau_S > 1e-4) before it leaves or drops below the
+    energy cut, instead of ~3 and ~2 at the paper-scale densities."""
+    import synth
+    w = synth.clumpy_onion(n_packets=n_packets)
+    w.pops = w.pops * THIN_POP_SCALE
+    w.name = w.name + f"_pops_x{THIN_POP_SCALE:g}"
+    return w
+
+
+def thin_bench(local, stream_ptr, passes=3):
+    """The attenuation pass on the thin-line onion (the event loop dominates):
+    events/s and the trace kernel's algorithmic HBM rate at 32 B per event."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    w = thin_onion()
+    peaks, _ = _measured_peaks()
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    ctx.transport(w)
+    sts = [ctx.transport(w) for _ in range(passes)]
+    torch.cuda.synchronize()
+    ctx.close()
+    ev = float(np.mean([s["events"] for s in sts]))
+    tr = float(np.mean([s["trace_ms"] for s in sts]))
+    dev = float(np.mean([s["transport_ms"] for s in sts]))
+    ach = BYTES_PER_EVENT * ev / (tr * 1e-3) / 1e9
+    return {"workload": w.name, "packets": w.n_packets, "events_per_pass": ev,
+            "tests_per_pass": float(np.mean([s["tests"] for s in sts])),
+            "events_per_packet": ev / w.n_packets, "pass_device_ms": dev, "trace_ms": tr,
+            "value": ev / (dev * 1e-3), "unit": UNIT,
+            "trace_GB_per_s": ach, "frac_hbm": ach / peaks["hbm_gbs"]}
 
 
 def workload_config(w, world):
@@ -420,7 +465,9 @@ def main():
     ap.add_argument("--packets", type=int, default=100_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="onion", choices=["onion", "onion-small", "sphere"])
+    ap.add_argument("--workload", default="onion",
+                    choices=["onion", "onion-small", "onion-thin", "sphere"])
+    ap.add_argument("--no-thin", action="store_true", help="skip the thin-line measurement")
     ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
@@ -569,6 +616,11 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak = FP64_LANES_PER_SM_CYCLE * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6
     fp64_ach = TRACE_FP64_OPS_PER_EVENT * (ev / len(stats)) / (trace_ms * 1e-3)
+    # a second view: the per-packet bytes of the fused pass beside the events'
+    wp_b = BYTES_PER_EVENT * (ev / len(stats)) + BYTES_PER_PACKET * w.n_packets
+    with_packets = {"bytes_per_event": BYTES_PER_EVENT, "bytes_per_packet": BYTES_PER_PACKET,
+                    "achieved": wp_b / (trace_ms * 1e-3) / 1e9,
+                    "frac": wp_b / (trace_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     fp64 = {"ops_per_event": TRACE_FP64_OPS_PER_EVENT, "achieved": fp64_ach, "peak": fp64_peak,
             "unit": "FP64 thread instructions/s", "frac": fp64_ach / fp64_peak,
             "pipe_busy_ncu": TRACE_FP64_PIPE_BUSY,
@@ -590,7 +642,7 @@ def main():
                      "traffic_source": "ncu dram bytes per event on the 32^3 onion, scaled by events",
                      "peak_source": src, "kernel": "k_trace",
                      "bytes_per_unit": BYTES_PER_EVENT, "unit_counted": "event",
-                     "fp64": fp64},
+                     "fp64": fp64, "with_packets": with_packets},
         "clocks": clk.summary(),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": min(e2e_ms) if e2e_ms else None},
@@ -598,6 +650,8 @@ def main():
         "gpu_launches": launches,
     }
     ctx.close()
+    if rank == 0 and not args.no_thin and args.workload == "onion":
+        line["thin_lines"] = thin_bench(local, stream.cuda_stream)
     if rank == 0 and not args.no_nlte and args.workload == "onion":
         line["nlte"] = nlte_bench(local, stream.cuda_stream, args.nlte_n)
     if rank == 0 and not args.no_coupled and args.workload == "onion":

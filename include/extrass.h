@@ -356,9 +356,9 @@ int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, doub
                       double *r0, double *r1);
 
 /* ---- transport without device allocation (no paper counterpart) -----------
- * For callers that cannot call cudaMalloc: code running while a CUDA stream is
- * being captured into a graph, programs whose device memory is handed out once
- * at start-up by another framework's allocator, or embedders held to a fixed
+ * For callers that cannot call cudaMalloc: programs whose device memory is
+ * handed out once at start-up by another framework's allocator (a second
+ * allocator would fragment or overrun its pool), or embedders held to a fixed
  * device-memory budget.  run_transport_noalloc does one attenuation-mode pass
  * (band emission, the whole grid one domain) like run_transport, but it makes
  * no device allocation: its working memory is a file-scope device array of
@@ -382,7 +382,10 @@ int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, doub
  *     photoexcitation estimators, photons/s absorbed divided by f_corr, as
  *     get_estimators returns them; spec [n_theta*n_phi][spec_nbins] the escaped
  *     lab-frame energy per bin, as get_spectrum kind 0; `out` the ledger (the
- *     timing fields are 0).  Synchronous on `cuda_stream`. */
+ *     timing fields are 0).
+ *   - The call is synchronous: it waits on `cuda_stream` after staging the
+ *     inputs, after every chunk and at the end, and reads counters back to the
+ *     host between chunks. */
 #define XT_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define XT_NOALLOC_MAX_CELLS 65536
 #define XT_NOALLOC_MAX_LINES 16384

@@ -196,6 +196,31 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _check_device_f64(name, a, n):
+    """`a` must be a contiguous float64 CUDA tensor of exactly n elements."""
+    import torch
+    if not isinstance(a, torch.Tensor) or a.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float64")
+    if a.numel() != n:
+        raise ValueError(f"{name} has {a.numel()} elements, {n} required")
+
+
+def _check_records(rec, n):
+    """Packet records: [n][XT_PKT_FIELDS] contiguous float64 (host or device)."""
+    if rec is None:
+        return
+    if hasattr(rec, "data_ptr"):
+        import torch
+        ok = rec.dtype == torch.float64 and rec.is_contiguous() and rec.numel() == n * XT_PKT_FIELDS
+    else:
+        ok = (isinstance(rec, np.ndarray) and rec.dtype == np.float64 and rec.flags.c_contiguous
+              and rec.size == n * XT_PKT_FIELDS)
+    if not ok:
+        raise ValueError(f"packet_records must be contiguous float64 with {n} x {XT_PKT_FIELDS} elements")
+
+
 def _f64(a):
     if a is None or hasattr(a, "data_ptr"):
         return a
@@ -285,6 +310,9 @@ def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=
                   emission=XT_EMIT_BAND, tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
                   spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1, accumulate=False,
                   max_events=1_000_000, subdomain_rounds=False, packet_records=None, check=True):
+    if packet_records is not None:
+        _check_records(packet_records, int(n_packets) - int(packet_begin) if packet_count < 0
+                       else int(packet_count))
     p = TransportParams(int(n_packets), int(packet_begin), int(packet_count), int(seed), int(mode),
                         int(emission), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
                         int(spec_nbins), int(bool(accumulate)), int(max_events), int(bool(subdomain_rounds)),
@@ -470,8 +498,20 @@ def run_transport_noalloc(nx, ny, nz, v_max, t, L_cell, band_A, g_level, lo, up,
                           n_phi=20, spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1,
                           max_events=1_000_000, stream=None):
     """One attenuation-mode pass that makes no device allocation (see
-    include/extrass.h).  pops, S and spec must be CUDA tensors."""
+    include/extrass.h).  pops, S and spec must be contiguous float64 CUDA
+    tensors of ncell*nlev, ncell*nline and n_theta*n_phi*spec_nbins elements;
+    the library cannot check the sizes of caller buffers, so they are checked
+    here (ValueError)."""
     keep = [_f64(L_cell), _f64(g_level), _i32(lo), _i32(up), _f64(lambda_A), _f64(f_lu)]
+    ncell, nlev, nline = int(nx) * int(ny) * int(nz), len(keep[1]), len(keep[2])
+    if len(keep[0]) != ncell:
+        raise ValueError(f"L_cell has {len(keep[0])} entries, the grid {ncell} cells")
+    for name, a in (("up", keep[3]), ("lambda_A", keep[4]), ("f_lu", keep[5])):
+        if len(a) != nline:
+            raise ValueError(f"{name} has {len(a)} entries, lo has {nline}")
+    for name, a, n in (("pops", pops, ncell * nlev), ("S", S, ncell * nline),
+                       ("spec", spec, int(n_theta) * int(n_phi) * int(spec_nbins))):
+        _check_device_f64(name, a, n)
     a = NoallocTransport(nx, ny, nz, v_max, t, _ptr(keep[0]), band_A[0], band_A[1],
                          int(len(keep[1])), int(len(keep[2])), _ptr(keep[1]), _ptr(keep[2]),
                          _ptr(keep[3]), _ptr(keep[4]), _ptr(keep[5]), _ptr(pops), int(n_packets),

@@ -1360,10 +1360,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
 // ============================================================================
 // Transport without device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph, drivers whose device memory is carved up once
-// at start-up by another framework's allocator, or embedders that must keep a
-// fixed device-memory budget.  run_transport_noalloc gives them one
+// Some callers cannot call cudaMalloc: programs whose device memory is carved
+// up once at start-up by another framework's allocator, or embedders that must
+// keep a fixed device-memory budget.  run_transport_noalloc gives them one
 // attenuation-mode transport pass that allocates nothing: its working memory
 // (line table, packet quota, packet pool, escape list, counters, ledger) lives
 // in the file-scope array below, of fixed size, which every GPU that loads the
@@ -1451,7 +1450,8 @@ __global__ void k_na_finish(double* __restrict__ S, const double* __restrict__ p
 static double h_na_L[kNaMaxCells], h_na_cellE[3 * kNaMaxCells];
 static int64_t h_na_q[kNaMaxCells + 1];
 static double h_na_frac[kNaMaxCells];
-static int h_na_ord[kNaMaxCells > kNaMaxLines ? kNaMaxCells : kNaMaxLines];
+static int64_t h_na_qord[kNaMaxCells];
+static int h_na_ord[kNaMaxLines];
 static double h_na_lam[kNaMaxLines], h_na_f[kNaMaxLines], h_na_nu[kNaMaxLines];
 static int h_na_lo[kNaMaxLines], h_na_up[kNaMaxLines], h_na_sorted[kNaMaxLines];
 static double h_na_g[1 << 16];
@@ -1531,32 +1531,14 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
     const int64_t lu = (int64_t)(uint32_t)h_na_lo[l] | ((int64_t)h_na_up[l] << 32);
     std::memcpy(&h_na_lines[4 * s + 3], &lu, sizeof(lu));
   }
-  // ---- packet quota by largest remainder, packet energies
-  double tot = 0.0;
-  for (int64_t k = 0; k < ncell; ++k) tot += h_na_L[k];
-  int64_t used = 0;
+  // ---- packet quota by largest remainder (the routine run_transport uses, on
+  // the fixed staging buffers), packet energies
+  packet_quota(h_na_L, ncell, a->n_packets, h_na_q, h_na_frac, h_na_qord);
   for (int64_t k = 0; k < ncell; ++k) {
-    const double q = tot > 0.0 ? ((double)a->n_packets * h_na_L[k]) / tot : 0.0;
-    const double fl = std::floor(q);
-    h_na_q[k + 1] = (int64_t)fl;
-    h_na_frac[k] = q - fl;
-    used += (int64_t)fl;
-    h_na_ord[k] = (int)k;
-  }
-  const int64_t extra = std::min<int64_t>(a->n_packets - used, ncell);
-  if (extra > 0) {
-    std::partial_sort(h_na_ord, h_na_ord + extra, h_na_ord + ncell, [](int x, int y) {
-      return h_na_frac[x] > h_na_frac[y] || (h_na_frac[x] == h_na_frac[y] && x < y);
-    });
-    for (int64_t k = 0; k < extra; ++k) h_na_q[h_na_ord[k] + 1] += 1;
-  }
-  h_na_q[0] = 0;
-  for (int64_t k = 0; k < ncell; ++k) {
-    const int64_t nq = h_na_q[k + 1];
+    const int64_t nq = h_na_q[k + 1] - h_na_q[k];
     h_na_cellE[k] = h_na_L[k];
     h_na_cellE[ncell + k] = nq > 0 ? h_na_L[k] / (double)nq : 0.0;
     h_na_cellE[2 * ncell + k] = h_na_cellE[ncell + k] / kH;
-    h_na_q[k + 1] += h_na_q[k];
   }
   for (int x = 0; x < a->nx; ++x) h_na_rtab[x] = x;
   for (int y = 0; y < a->ny; ++y) h_na_rtab[a->nx + y] = y * a->nx;

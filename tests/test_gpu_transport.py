@@ -163,6 +163,25 @@ def test_edge_cases(xt):
         assert e.value.code == xt.XT_EINVAL
 
 
+@pytest.mark.parametrize("views", [(20, 20), (9, 14)])
+def test_spectrum_normalisations_vs_oracle(xt, views):
+    """get_spectrum kinds 1 and 2 (isotropic-equivalent L_lambda per viewer,
+    4 pi / dOmega_k E / dlambda, and the angle-summed L_lambda) against the
+    oracle's normalisation of its own binned energy, element by element."""
+    nt, nph = views
+    w = synth.uniform_sphere(n_packets=60_000, seed=31)
+    w.pops = w.pops * 1e-3
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        ctx.transport(w, n_theta=nt, n_phi=nph)
+        L_k, L_tot = ctx.get_spectrum(1), ctx.get_spectrum(2)
+        o = oracle.transport(w, n_theta=nt, n_phi=nph)
+        Lk_o, Lt_o, _ = oracle.spectrum_L_lambda(o["spec"], w.spec_band_A[0], 1e-3, nt, nph)
+        assert L_k.shape == Lk_o.shape and L_tot.shape == Lt_o.shape
+        _cmp_sparse(L_k, Lk_o, SPEC_TOL, "L_lambda per viewer")
+        _cmp_sparse(L_tot, Lt_o, SPEC_TOL, "angle-summed L_lambda")
+
+
 def test_event_guard_reports_timeout(xt):
     w = synth.uniform_sphere(n=8, n_packets=2000, seed=9)
     w.pops = w.pops * 1e-5
@@ -207,16 +226,18 @@ def onion():
     return synth.clumpy_onion()
 
 
-def test_clumpy_onion_full_grid_packet_subset(xt, onion):
+@pytest.mark.parametrize("rounds", [True, False])
+def test_clumpy_onion_full_grid_packet_subset(xt, onion, rounds):
     """Paper-scale grid and line list (64^3 x 1e5 lines, 8^3 subdomains), a
     contiguous packet subset: every estimator slot the oracle touches, and
-    nothing else in those cells."""
+    nothing else in those cells.  rounds=False is the benchmark's path (the
+    trace kernel emits its own packets, the whole grid one domain)."""
     w = onion
     with _ctx(xt) as ctx:
         ctx.load(w)
-        p0, m = 61_234_567, 60_000
-        st, rec = _records(xt, ctx, w, packet_begin=p0, packet_count=m, subdomain_rounds=True)
-        assert st["rounds"] > 1
+        p0, m = (61_234_567, 60_000) if rounds else (17_000_001, 60_000)
+        st, rec = _records(xt, ctx, w, packet_begin=p0, packet_count=m, subdomain_rounds=rounds)
+        assert (st["rounds"] > 1) == rounds
         o = oracle.transport(w, p_begin=p0, p_end=p0 + m, per_packet=True)
         _cmp_records(rec, o["pkt"])
         slots, vals = o["S_slots"], o["S_values"]

@@ -9,7 +9,8 @@ P5  event histories vs a brute-force restatement (bisection on the comoving
 P2  optically thin line profile of the voxelised sphere vs the hat-box
     projection integrated by quadrature.
 P3  optically thin estimator in a cell slab vs a 6-D quadrature of the
-    mean-intensity integral.
+    mean-intensity integral; the rates readout's mean intensity in a thin
+    uniform sphere vs the closed-form J(r) of a uniformly emitting sphere.
 P6  photon ledger closure; comoving energy closure in scatter mode; the
     scatter-mode destruction probability of a single line.
 A7  the mean intensity of the rates readout against the Einstein relation
@@ -98,6 +99,63 @@ def test_rates_mean_intensity_obeys_einstein_relation():
     np.testing.assert_allclose(A_rel, A_f, rtol=1e-12)
     np.testing.assert_allclose(R_ul[c], (gl / gu) * R_lu[c], rtol=1e-15)
     assert np.all(R_lu[c] > 0)
+
+
+def _thin_sphere(n=32, n_packets=1_000_000, n_lines=1000, v_max=5e7, q=0.97, seed=41):
+    """Uniform sphere of optically thin lines (tau_S 5e-4..2e-3 in every active
+    cell) with populations n_i ~ g_i q^i, so that f_corr = 1 - q^(u-l) spans
+    0.03..0.8: a readout that divided by n_l instead of n_l - (g_l/g_u) n_u,
+    or dropped the stimulated-emission correction, would be off by 1/f_corr.
+    v_max = 500 km/s keeps the first-order Doppler terms (v/c) below 0.2 %."""
+    w = synth.uniform_sphere(n=n, n_packets=n_packets, n_lines=n_lines, n_levels=50, seed=seed)
+    w.v_max = v_max
+    nz = w.n_ion_density[:, 0]
+    x = w.g_level * q ** np.arange(w.nlev)
+    w.pops = nz[:, None] * (x / x.sum())[None, :]
+    c = int(np.nonzero(nz > 0)[0][0])
+    net = w.pops[c, w.lo] - w.g_level[w.lo] / w.g_level[w.up] * w.pops[c, w.up]
+    tau_t = 10 ** np.random.default_rng(seed).uniform(np.log10(5e-4), np.log10(2e-3), w.nline)
+    w.f_lu = tau_t / (oracle.PI_E2_MC * w.lambda_A * 1e-8 * w.t * net)
+    return w
+
+
+def test_rates_thin_sphere_mean_intensity_closed_form():
+    """P3 for the rates readout: in an optically thin uniform sphere with flat
+    j_nu, Jbar = R_lu / B_lu with R_lu = S / (n_l V) must equal the
+    mean intensity of a uniformly emitting sphere,
+    J(r) = (j R / 2) [1 + (R^2 - r^2) / (2 r R) ln((R + r) / (R - r))],
+    j = L_cell / (4 pi V dnu_band), to Monte Carlo error, in every radial
+    shell and for every part of the line list.  This fixes the cell volume,
+    the division by n_l and f_corr, and B_lu of the readout (the Einstein
+    relation pin above fixes only the ratio of R_lu and Jbar)."""
+    w = _thin_sphere()
+    act = w.rho > 0
+    tau, _ = oracle.tau_beta(w, int(np.nonzero(act)[0][0]), 1)
+    assert 1e-4 < tau.min() and tau.max() < 3e-3            # thin, but interaction points
+    o = oracle.transport(w)
+    _, _, J = oracle.rates(w, o["S"])
+    R = w.v_max * w.t
+    xc = synth.cell_centres(w.nx, w.v_max) * w.t
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2).reshape(-1)
+    c = 2.99792458e10
+    dnu = c / (w.band_A[0] * 1e-8) - c / (w.band_A[1] * 1e-8)
+    V = (2 * R / w.nx) ** 3
+    j = w.L_cell[act][0] / V / (4 * np.pi * dnu)
+    rr = np.clip(r, 1e-9 * R, (1 - 1e-9) * R)       # (cells outside the sphere are not compared)
+    J_exact = j * R / 2 * (1 + (R * R - rr * rr) / (2 * rr * R) * np.log((R + rr) / (R - rr)))
+    Jc = J.mean(axis=1)
+    for a, b in [(0, 0.3), (0.3, 0.45), (0.45, 0.6), (0.6, 0.75), (0.75, 0.9)]:
+        m = act & (r / R >= a) & (r / R < b)
+        ratio = Jc[m].sum() / J_exact[m].sum()
+        assert ratio == pytest.approx(1.0, abs=0.03), (a, b, ratio)
+    # flat in frequency: every tenth of the line list (sorted by wavelength)
+    # sees the same field in the inner sphere
+    inner = act & (r < 0.75 * R)
+    order = np.argsort(w.lambda_A)
+    for part in np.array_split(order, 10):
+        ratio = J[np.ix_(inner, part)].mean(axis=1).sum() / J_exact[inner].sum()
+        assert ratio == pytest.approx(1.0, abs=0.05), ratio
 
 
 # ---------------------------------------------------------------- P7
