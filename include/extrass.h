@@ -99,6 +99,11 @@ int get_sobolev_tau(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *ta
 #define XT_EMIT_BAND 0      /* flat-in-nu band emission with L_cell */
 #define XT_EMIT_LINES 1     /* line emissivity A_ul dE beta N_u, Eq. (thin_emissivity) */
 #define XT_PKT_FIELDS 11    /* per-packet record, see xt_transport_params.packet_records */
+/* Estimator increments (Sec. 2.3.2) are pre-reduced per warp: lanes adding to
+ * the same (cell, line) slot are summed and one FP64 atomic adds the sum.  This
+ * flag turns that off (one atomic per increment); results differ only in the
+ * order of the additions. */
+#define XT_FLAG_NO_WARP_REDUCE 1
 
 typedef struct {
     int64_t n_packets;      /* N of the whole emission (sets the per-cell quota) */
@@ -119,7 +124,7 @@ typedef struct {
                              * subdomain of init_grid is a domain of its own; a packet
                              * that crosses into another subdomain is queued and
                              * carried on in the next round (Sec. 2.4.1 bundles) */
-    int32_t flags;          /* reserved, 0 */
+    int32_t flags;          /* XT_FLAG_* bits, 0 by default */
     /* Optional [packet_count][XT_PKT_FIELDS] doubles: fate (0 escaped,
      * 1 dropped below e_cut, 2 collisionally destroyed, 3 guard), events,
      * N_final, escaped lab energy, viewer, lambda bin, interactions, emitting

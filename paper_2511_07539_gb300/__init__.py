@@ -22,6 +22,7 @@ XT_OK, XT_EINVAL, XT_ENOMEM, XT_ECUDA, XT_ETIMEOUT, XT_ENOTCONV, XT_ESTATE = 0, 
 XT_MODE_ATTEN, XT_MODE_SCATTER = 0, 1
 XT_EMIT_BAND, XT_EMIT_LINES = 0, 1
 XT_PKT_FIELDS = 11
+XT_FLAG_NO_WARP_REDUCE = 1
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
               "N0", "nu_cmf0", "nu_lab"]
 
@@ -309,14 +310,15 @@ def set_estimator_store(ctx, host_groups=0):
 def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=XT_MODE_ATTEN,
                   emission=XT_EMIT_BAND, tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
                   spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1, accumulate=False,
-                  max_events=1_000_000, subdomain_rounds=False, packet_records=None, check=True):
+                  max_events=1_000_000, subdomain_rounds=False, packet_records=None, check=True,
+                  flags=0):
     if packet_records is not None:
         _check_records(packet_records, int(n_packets) - int(packet_begin) if packet_count < 0
                        else int(packet_count))
     p = TransportParams(int(n_packets), int(packet_begin), int(packet_count), int(seed), int(mode),
                         int(emission), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
                         int(spec_nbins), int(bool(accumulate)), int(max_events), int(bool(subdomain_rounds)),
-                        0, _ptr(packet_records))
+                        int(flags), _ptr(packet_records))
     st = TransportStats()
     rc = lib().run_transport(ctx, C.byref(p), C.byref(st))
     if check:

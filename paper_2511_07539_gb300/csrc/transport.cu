@@ -130,6 +130,7 @@ struct TraceArgs {
   EmitArgs em;                        // (packet p = em.p_begin + pool slot)
   int64_t row0;                       // first row held by S (a streamed group's slab; else 0)
   int grp_nz;                         // rounds == 2: cells along z per streamed group
+  int warp_reduce;                    // pre-reduce estimator increments by slot per warp
 };
 
 struct EscArgs {
@@ -219,6 +220,38 @@ __device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsign
   if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
   base = __shfl_sync(act, base, leader);
   if (want) buf[base + __popc(m & ((1u << lane) - 1u))] = idx;
+}
+
+// Estimator increment with a warp-level pre-reduction by slot: the lanes of the
+// current active set that add to the same slot are found with one match, every
+// lane of such a group sums its peers' values (in lane order, one shuffle per
+// further member of the largest group), and only the lowest lane of each group
+// issues the FP64 atomic and logs the slot.  Returns whether this lane did.
+__device__ __forceinline__ bool warp_add_slot(double* __restrict__ S, int64_t slot, double v,
+                                              bool reduce) {
+  if (!reduce) {
+    atomicAdd(S + slot, v);
+    return true;
+  }
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __match_any_sync(act, (unsigned long long)slot);
+  const unsigned gmax = __reduce_max_sync(act, (unsigned)__popc(m));
+  double sum = v;
+  if (gmax > 1) {
+    unsigned others = m & ~(1u << lane);
+    for (unsigned k = 1; k < gmax; ++k) {
+      const int src = others ? __ffs(others) - 1 : lane;
+      const double x = __shfl_sync(act, v, src);
+      if (others) {
+        sum += x;
+        others &= others - 1;
+      }
+    }
+  }
+  if (lane != __ffs(m) - 1) return false;
+  atomicAdd(S + slot, sum);
+  return true;
 }
 
 // Clear the slots listed in each block's log segment.
@@ -580,15 +613,18 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     }
     int fate = -1;                        // -1 alive
     if (found) {
-      const unsigned long long k = atomicAdd(&blk_log, 1ull);
-      if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
       // ---- line event (lanes that found one run this together)
       ++events;
       ++n_events;
       double ex, ome;
       expneg(fx, tau, ex, ome);
       if (MODE == XT_MODE_ATTEN) {
-        atomicAdd(a.S + (int64_t)(row - a.row0) * a.nline + cursor, N * ome);   // net photons; / f_corr at readout
+        // net photons (divided by f_corr at readout), pre-reduced over the lanes
+        // of the warp that hit the same slot; the adding lane logs the slot
+        if (warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N * ome, a.warp_reduce)) {
+          const unsigned long long k = atomicAdd(&blk_log, 1ull);
+          if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
+        }
         N = N * ex;
         if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
         ++cursor;
@@ -599,10 +635,14 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         uint64_t xw[4];
         draw_raw(a.seed, p, 2 + (uint64_t)nd, xw);
         const U4 w{{u01(xw[0]), u01(xw[1]), u01(xw[2]), u01(xw[3])}};
+        {   // every event's slot is logged (interaction or not), as before the draw
+          const unsigned long long k = atomicAdd(&blk_log, 1ull);
+          if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
+        }
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
-          atomicAdd(a.S + (int64_t)(row - a.row0) * a.nline + cursor, N);
+          warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N, a.warp_reduce);
           acc[T_ABS] += N;                    // the whole packet is absorbed
           const double Ecmf = N * kH * L.x;
           acc[T_ABSE] += Ecmf;
@@ -1140,6 +1180,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds && !host_store) ? 1 : 0;
   ta.row0 = 0;
   ta.grp_nz = G.nz / NG;
+  ta.warp_reduce = (p->flags & XT_FLAG_NO_WARP_REDUCE) ? 0 : 1;
   if (host_store) ta.rounds = 2;
 
   EscArgs xa;
@@ -1591,6 +1632,7 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
   ta.rtab = (const int*)(B + kNaRtab);
   ta.slotlog = (int64_t*)(B + kNaLog); ta.seg_n = (int64_t*)(B + kNaSegN); ta.seg_len = 0;
   ta.log_overflow = (unsigned long long*)(B + kNaSegN + 8ull * kNaSegs);
+  ta.warp_reduce = 1;
   EscArgs xa{};
   xa.pool = P; xa.esc = esc; xa.spec = a->spec; xa.n_theta = a->n_theta; xa.n_phi = a->n_phi;
   xa.nbins = a->spec_nbins; xa.lam0 = a->spec_lam0_A; xa.log1p_dlog = std::log1p(a->spec_dlog);

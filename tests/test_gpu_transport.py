@@ -182,6 +182,24 @@ def test_spectrum_normalisations_vs_oracle(xt, views):
         _cmp_sparse(L_tot, Lt_o, SPEC_TOL, "angle-summed L_lambda")
 
 
+@pytest.mark.parametrize("flags", [0, 1])
+def test_warp_prereduction_of_estimators(xt, flags):
+    """Few lines and thin: the lanes of a warp often add to the same (cell,
+    line) slot at once.  With the warp pre-reduction (flags 0) and without it
+    (XT_FLAG_NO_WARP_REDUCE), the estimators equal the oracle's."""
+    w = synth.uniform_sphere(n=6, n_packets=200_000, n_lines=12, n_levels=8, seed=35)
+    w.lambda_A = np.linspace(5000.0, 5080.0, 12)     # every packet meets most lines
+    w.band_A = (4990.0, 5100.0)
+    w.spec_band_A = synth._spectrum_grid(w.band_A[0], w.band_A[1], w.v_max)
+    w.pops = w.pops * 1e-3
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st = ctx.transport(w, flags=flags)
+        o = oracle.transport(w)
+        assert st["events"] == o["ledger"]["events"] > 200_000      # over ~1500 slots
+        _cmp_sparse(ctx.get_estimators(), o["S"], S_TOL, f"estimators, flags {flags}")
+
+
 def test_event_guard_reports_timeout(xt):
     w = synth.uniform_sphere(n=8, n_packets=2000, seed=9)
     w.pops = w.pops * 1e-5
