@@ -78,7 +78,18 @@ typedef struct {
     const double *f_lu;         /* [nline] absorption oscillator strength */
     const double *n_ion_density;/* [ncell*n_ion] cm^-3 (may be NULL) */
     const double *ups_down;     /* [nlev] sum_{j<u} Upsilon_ju; scatter mode only (may be NULL) */
+    /* Photoionization (Sec. 2.3.1), all three NULL for none.  The lowest
+     * pi_nlev[z] levels of ion z photoionize, with the hydrogenic cross
+     * section of Eq. (sigma_OTSPI): sigma = 7.9e-18 cm^2 (lambda / lambda_ion)^3
+     * (1 - E_u / chi_ion)^-1/2 / (charge + 1)^2 below the threshold wavelength
+     * lambda_ion = h c / (chi_ion - E_u).  Photoionizing level k counts ion by
+     * ion, lowest level first (k = sum_{z' < z} pi_nlev[z'] + i for level i of
+     * ion z); at most XT_PI_MAX of them; every threshold chi_ion - E_u > 0. */
+    const double *chi_ion;      /* [n_ion] erg, ionization energy from the ion's ground level */
+    const int32_t *charge;      /* [n_ion] charge of the ion (0 neutral, 1 singly ionized, ...) */
+    const int32_t *pi_nlev;     /* [n_ion] photoionizing levels of the ion (0..its level count) */
 } xt_atom_desc;
+#define XT_PI_MAX 256
 int load_atomic_data(xt_ctx *ctx, const xt_atom_desc *a);
 
 /* Level populations [ncell][nlev] in cm^-3 (natural cell order). */
@@ -143,6 +154,8 @@ typedef struct {
     double queued;          /* packets handed between subdomains */
     double emit_ms, trace_ms, escape_ms;   /* summed device time per kernel kind */
     double kernels;         /* kernels launched by this call */
+    double photoionized_N;  /* photons absorbed by photoionization (Sec. 2.3.1) */
+    double photoionized_E;  /* their energy at absorption (comoving), erg/s */
 } xt_transport_stats;
 
 int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);
@@ -174,6 +187,17 @@ int get_estimators(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *S);
  * [n_cells][nline]; any may be NULL; slots with n_l = 0 give 0. */
 int get_photoexcitation_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells,
                               double *R_lu, double *R_ul, double *Jbar);
+
+/* ---- photoionization rates (Sec. 2.3.1) ---------------------------------
+ * After an attenuation-mode run_transport with photoionization data loaded:
+ * Gamma [n_cells][n_pi] (s^-1), Gamma_PI,k = N_abs,k / (n_k V), the photons
+ * absorbed by photoionizing level k in the cell over the atoms in that level
+ * (0 where n_k = 0), levels in the order of xt_atom_desc; heating [n_cells]
+ * (erg/s), the absorbed photons' energy above their thresholds.  Either may be
+ * NULL.  The same rules for host/device pointers as everywhere; XT_ESTATE
+ * without a transport pass with photoionization. */
+int get_photoionization_rates(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *Gamma,
+                              double *heating);
 
 /* ---- A5: spectrum (Secs. 2, 2.3) ----------------------------------------
  * kind 0: escaped lab-frame energy per (viewer, bin) [n_theta*n_phi][nbins], erg/s
@@ -422,6 +446,7 @@ typedef struct {
     int64_t ncell, nlev, nline, n_ion;
     int64_t spec_views, spec_bins;
     int64_t store_bytes;    /* device bytes of the estimator store */
+    int64_t n_pi;           /* photoionizing levels */
 } xt_sizes;
 int get_sizes(xt_ctx *ctx, xt_sizes *out);
 

@@ -14,7 +14,8 @@ Parts:
                App. A.1).
   this file    ctypes binding; A7 rates from estimators (Sec. 2.3.2: a
                photoexcitation rate per line and cell, photodeexcitation from
-               detailed balance); spectrum normalisation (Sec. 2.3).
+               detailed balance); photoionization rates (Sec. 2.3.1);
+               spectrum normalisation (Sec. 2.3).
   nlte.py      statistical-equilibrium rate matrices and their FP64 solve.
   mlp.py       FP64 MLP forward/backward/Adam for the surrogate.
 """
@@ -35,7 +36,8 @@ H_PLANCK = 6.62607015e-27
 PI_E2_MC = np.pi * 4.80320471e-10 ** 2 / (9.1093837015e-28 * 2.99792458e10)
 
 LEDGER = ["emit_N", "esc_N", "abs_N", "drop_N", "emit_E", "esc_E", "oob_E", "events",
-          "tests", "guard", "thermal_E", "interactions", "abs_E_cmf", "reemit_E_cmf"]
+          "tests", "guard", "thermal_E", "interactions", "abs_E_cmf", "reemit_E_cmf",
+          "pi_N", "pi_E"]
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
               "N0", "nu_cmf0", "nu_lab"]
 
@@ -60,7 +62,9 @@ class _Problem(C.Structure):
                 ("g", C.c_void_p), ("E_level", C.c_void_p), ("pops", C.c_void_p),
                 ("lo", C.c_void_p), ("up", C.c_void_p),
                 ("lambda_A", C.c_void_p), ("f_lu", C.c_void_p),
-                ("ne", C.c_void_p), ("Te", C.c_void_p), ("ups_down", C.c_void_p)]
+                ("ne", C.c_void_p), ("Te", C.c_void_p), ("ups_down", C.c_void_p),
+                ("n_pi", C.c_int32), ("pi_level", C.c_void_p), ("pi_Eion", C.c_void_p),
+                ("pi_charge", C.c_void_p)]
 
 
 class _Params(C.Structure):
@@ -94,7 +98,9 @@ def lib():
         _lib.xo_nu_cmf.argtypes = [d, C.c_void_p, C.c_void_p, d, d]
         _lib.xo_transport.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
-                                      C.c_void_p]
+                                      C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.xo_sigma_pi.restype = d
+        _lib.xo_sigma_pi.argtypes = [d, d, d, C.c_int32]
         _lib.xo_emission.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.xo_tau_beta.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
         _lib.xo_packet_quota.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
@@ -123,10 +129,18 @@ class _Keep:
                          lam=_c64(w.lambda_A), f=_c64(w.f_lu), ne=_c64(w.ne), Te=_c64(w.Te),
                          ups=_c64(ups_down if ups_down is not None else np.zeros(w.nlev)))
         a = self.arrs
+        self.n_pi = 0
+        if getattr(w, "pi_nlev", None) is not None:
+            import synth
+            lev, eion, ch = synth.pi_levels(w)
+            a.update(pi_lev=_ci32(lev), pi_eion=_c64(eion), pi_ch=_ci32(ch))
+            self.n_pi = int(lev.shape[0])
         self.pb = _Problem(w.nx, w.ny, w.nz, w.v_max, w.t, _ptr(a["L"]), w.band_A[0],
                            w.band_A[1], w.nlev, w.nline, _ptr(a["g"]), _ptr(a["E"]),
                            _ptr(a["pops"]), _ptr(a["lo"]), _ptr(a["up"]), _ptr(a["lam"]),
-                           _ptr(a["f"]), _ptr(a["ne"]), _ptr(a["Te"]), _ptr(a["ups"]))
+                           _ptr(a["f"]), _ptr(a["ne"]), _ptr(a["Te"]), _ptr(a["ups"]),
+                           self.n_pi, _ptr(a.get("pi_lev")), _ptr(a.get("pi_eion")),
+                           _ptr(a.get("pi_ch")))
 
 
 def upsilon_down_sums(w) -> np.ndarray:
@@ -148,10 +162,17 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     cell order, the workload's line order), spec [n_theta*n_phi, n_bins]
     (escaped lab-frame energy, erg/s), the photon/energy ledger and, if asked,
     per-packet records.  With ``sparse`` (default: when the dense store would
-    exceed 2 GB) S is returned as summed (cell, line, value) records instead."""
+    exceed 2 GB) S is returned as summed (cell, line, value) records instead.
+    A workload with photoionization data (attenuation mode) also gives S_pi
+    [ncell, n_pi] (photons/s absorbed per photoionizing level) and heat
+    [ncell] (erg/s of photon energy above the thresholds)."""
     N = w.n_packets if n_packets is None else n_packets
     p_end = N if p_end is None else p_end
     keep = _Keep(w, upsilon_down_sums(w) if mode == "scatter" else None)
+    if keep.n_pi and mode != "atten":
+        raise ValueError("photoionization is part of the attenuation mode only")
+    S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
+    heat = np.zeros(w.ncell) if keep.n_pi else None
     lam0, nbins = w.spec_band_A
     pr = _Params(N, p_begin, p_end, w.seed if seed is None else seed,
                  0 if mode == "atten" else 1, 0 if emission == "band" else 1,
@@ -160,7 +181,7 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
         sparse = w.ncell * w.nline * 8 > 2e9
     S = None if sparse else np.zeros((w.ncell, w.nline))
     spec = np.zeros((n_theta * n_phi, nbins))
-    ledger = np.zeros(16)
+    ledger = np.zeros(20)
     pkt = np.zeros((p_end - p_begin, len(PKT_FIELDS))) if per_packet else None
     rec = None
     nrec = np.zeros(1, dtype=np.int64)
@@ -168,10 +189,13 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
         cap = rec_cap if rec_cap is not None else max(1024, 64 * (p_end - p_begin))
         rec = np.zeros(cap, dtype=[("cell", np.int64), ("line", np.int64), ("value", np.float64)])
     rc = lib().xo_transport(C.byref(keep.pb), C.byref(pr), _ptr(S), _ptr(spec), _ptr(ledger),
-                            _ptr(pkt), _ptr(rec), 0 if rec is None else rec.shape[0], _ptr(nrec))
+                            _ptr(pkt), _ptr(rec), 0 if rec is None else rec.shape[0], _ptr(nrec),
+                            _ptr(S_pi), _ptr(heat))
     if rc != 0:
         raise RuntimeError(f"oracle record buffer too small ({nrec[0]} records)")
     out = dict(S=S, spec=spec, ledger=dict(zip(LEDGER, ledger[:len(LEDGER)].tolist())))
+    if keep.n_pi:
+        out["S_pi"], out["heat"] = S_pi, heat
     if sparse:
         r = rec[: nrec[0]]
         key = r["cell"] * w.nline + r["line"]
@@ -244,6 +268,22 @@ def rates(w, S):
     B_lu = 4.0 * np.pi * PI_E2_MC * w.f_lu / (H_PLANCK * nu)
     Jbar = R_lu / B_lu[None, :]
     return R_lu, R_ul, Jbar
+
+
+def pi_rates(w, S_pi):
+    """Photoionization rates Gamma_PI,i = N_abs,i / (n_i V) [s^-1] of every
+    photoionizing level and cell (Sec. 2.3.1: photons absorbed by the level
+    over the number of atoms in it); levels with n_i = 0 give 0."""
+    import synth
+    lev, _, _ = synth.pi_levels(w)
+    N_i = w.pops[:, lev] * cell_volume(w)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(N_i > 0, S_pi / N_i, 0.0)
+
+
+def sigma_pi(lambda_cm, E_u, E_ion, charge):
+    """Eq. (sigma_OTSPI), the oracle's hydrogenic cross section [cm^2]."""
+    return lib().xo_sigma_pi(float(lambda_cm), float(E_u), float(E_ion), int(charge))
 
 
 def spectrum_L_lambda(spec, lam0, dlog, n_theta=20, n_phi=20):

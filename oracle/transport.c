@@ -21,6 +21,12 @@
  *   - Viewing directions: 20 x 20 equal-angle (theta, phi) bins (Sec. 2);
  *     output on a 0.1 % logarithmic wavelength grid (Sec. 2.3).
  *   - Line emissivity A_ul dE_ul beta N_u, Eq. (thin_emissivity), App. A.1.
+ *   - Photoionization on every path segment (Sec. 2.3.1): tau_PI,i =
+ *     sigma_PI,i d n_i for every level whose threshold lies below the photon
+ *     energy, sigma_PI from the hydrogenic form of Eq. (sigma_OTSPI); the
+ *     segment absorbs N (1 - e^-tau), tau = sum_i tau_PI,i, shared among the
+ *     levels in proportion to tau_PI,i; the excess photon energy over each
+ *     threshold is heating; Gamma_PI,i = N_abs,i / (n_i V).
  * Readings where the paper is silent are documented with each function.
  *
  * Build: gcc -O2 -ffp-contract=off -shared -fPIC (no FMA contraction, so the
@@ -115,6 +121,11 @@ typedef struct {
     const double *lambda_A, *f_lu; /* [nline] */
     const double *ne, *Te;     /* [ncell] */
     const double *ups_down;    /* [nlev] sum over j<u of Upsilon_ju (SCATTER only) */
+    /* photoionizing levels (Sec. 2.3.1); n_pi = 0: none */
+    int32_t n_pi;
+    const int32_t *pi_level;   /* [n_pi] global level index */
+    const double *pi_Eion;     /* [n_pi] erg, ionization energy of the level's ion (from its ground) */
+    const int32_t *pi_charge;  /* [n_pi] charge of the level's ion */
 } xo_problem;
 
 typedef struct {
@@ -130,7 +141,8 @@ typedef struct {
 } xo_params;
 
 enum { L_EMIT_N, L_ESC_N, L_ABS_N, L_DROP_N, L_EMIT_E, L_ESC_E, L_OOB_E, L_EVENTS,
-       L_TESTS, L_GUARD, L_THERMAL_E, L_INTERACT, L_ABS_E_CMF, L_REEMIT_E_CMF, L_NLEDGER };
+       L_TESTS, L_GUARD, L_THERMAL_E, L_INTERACT, L_ABS_E_CMF, L_REEMIT_E_CMF,
+       L_PI_N, L_PI_E, L_NLEDGER };
 
 typedef struct {
     const xo_problem *pb;
@@ -145,6 +157,7 @@ typedef struct {
     int64_t *qoff;       /* [ncell+1] packet quota prefix */
     double *wline;       /* [ncell*nline] line emission weights (emission_mode 1) */
     int32_t *down_off, *down_line;   /* CSR over upper levels of radiative down-lines */
+    double *pi_tau;      /* [n_pi] work space of one photoionization segment */
 } prep_t;
 
 static const double *g_sort_nu;
@@ -242,12 +255,82 @@ static int prep(prep_t *P, const xo_problem *pb, const xo_params *pr) {
     }
     P->qoff = malloc(sizeof(int64_t) * (size_t)(P->ncell + 1));
     xo_packet_quota(P->Lc, P->ncell, pr->n_packets, P->qoff);
+    P->pi_tau = calloc((size_t)(pb->n_pi > 0 ? pb->n_pi : 1), sizeof(double));
     return 0;
 }
 
 static void unprep(prep_t *P) {
     free(P->order); free(P->pos); free(P->nu); free(P->A); free(P->Lc); free(P->qoff);
-    free(P->wline); free(P->down_off); free(P->down_line);
+    free(P->wline); free(P->down_off); free(P->down_line); free(P->pi_tau);
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Eq. (sigma_OTSPI): hydrogenic photoionization cross section [cm^2] of a
+ * level of energy E_u in an ion of ionization energy E_ion and charge C, for a
+ * photon of wavelength lambda below the threshold wavelength
+ * lambda_ion = h c / (E_ion - E_u); Gaunt factor 1. */
+double xo_sigma_pi(double lambda_cm, double E_u, double E_ion, int32_t C) {
+    double lam_ion = XO_H * XO_C / (E_ion - E_u);
+    double x = lambda_cm / lam_ion;
+    return 7.9e-18 * x * x * x * pow(1.0 - E_u / E_ion, -0.5) / ((C + 1.0) * (C + 1.0));
+}
+
+/* Photoionization along the path r + s n, s in [s0, s1], of a packet of N
+ * photons with lab frequency nu_lab (Sec. 2.3.1).  Readings: the photon
+ * wavelength of the segment is the comoving one at its start, s0 (the
+ * paper evaluates sigma_PI "for each distance d that a ray travels"); a level
+ * takes part if the photon energy there exceeds its threshold E_ion - E_u, and
+ * its path length stops where the comoving frequency, falling along the
+ * segment, reaches the threshold ("d is modified").  N_abs = N (1 - e^-tau),
+ * level i gets N_abs tau_i / tau; the excess h nu - (E_ion - E_u) of each
+ * absorbed photon is heating.  Returns 1 when the packet's photon energy at the
+ * segment end has fallen below e_cut of its start (the rest is dropped). */
+static int pi_segment(const prep_t *P, int64_t cell, const double *pc, double nu_lab,
+                      const double n[3], const double r[3], double s0, double s1, double *N,
+                      double E0, double *S_pi, double *heat, double *ledger) {
+    const xo_problem *pb = P->pb;
+    double d = s1 - s0;
+    if (d < 0.0) d = 0.0;
+    double q[3] = {r[0] + s0 * n[0], r[1] + s0 * n[1], r[2] + s0 * n[2]};
+    double nu_a = nu_lab * (1.0 - dot3(n, q) / P->ct);
+    double lam_a = XO_C / nu_a;
+    double tot = 0.0;
+    for (int32_t k = 0; k < pb->n_pi; k++) {
+        double Eu = pb->E_level[pb->pi_level[k]];
+        double chi = pb->pi_Eion[k] - Eu;
+        P->pi_tau[k] = 0.0;
+        if (XO_H * nu_a > chi) {
+            double dk = d;
+            double s_th = (nu_a - chi / XO_H) * P->ct / nu_lab;   /* where nu_cmf = chi / h */
+            if (s_th < dk) dk = s_th;
+            double sig = xo_sigma_pi(lam_a, Eu, pb->pi_Eion[k], pb->pi_charge[k]);
+            P->pi_tau[k] = sig * dk * pc[pb->pi_level[k]];
+            tot += P->pi_tau[k];
+        }
+    }
+    if (tot > 0.0) {
+        double ex, ome;
+        if (tot > XO_LN2) { ex = exp(-tot); ome = 1.0 - ex; }
+        else { ome = -expm1(-tot); ex = 1.0 - ome; }
+        double Nabs = *N * ome;
+        for (int32_t k = 0; k < pb->n_pi; k++) {
+            if (P->pi_tau[k] <= 0.0) continue;
+            double share = Nabs * P->pi_tau[k] / tot;
+            double chi = pb->pi_Eion[k] - pb->E_level[pb->pi_level[k]];
+            if (S_pi) S_pi[cell * pb->n_pi + k] += share;
+            if (heat) heat[cell] += share * (XO_H * nu_a - chi);
+        }
+        ledger[L_PI_N] += Nabs;
+        ledger[L_PI_E] += Nabs * XO_H * nu_a;
+        *N = *N * ex;
+    }
+    double nu_b = nu_a - nu_lab * d / P->ct;          /* comoving frequency at the segment end */
+    if (*N * XO_H * nu_b < P->pr->e_cut * E0) {
+        ledger[L_DROP_N] += *N;
+        return 1;
+    }
+    return 0;
 }
 
 static int64_t cell_of_packet(const prep_t *P, int64_t p) {
@@ -277,7 +360,6 @@ static void isotropic(double umu, double uphi, double n[3]) {
     n[0] = st * cos(phi); n[1] = st * sin(phi); n[2] = mu;
 }
 
-static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 /* Viewing-direction bin: theta in [0,pi] and phi in [0,2pi) cut into equal angles. */
 int32_t xo_viewer_bin(const double n[3], int32_t n_theta, int32_t n_phi) {
@@ -320,7 +402,7 @@ static void add_estimator(double *S, int64_t cell, int32_t nline, int32_t l, dou
 #define XO_PKT_FIELDS 11
 
 static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec,
-                             double *ledger, double *pkt) {
+                             double *ledger, double *pkt, double *S_pi, double *heat) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     int64_t c = cell_of_packet(P, p);
@@ -382,6 +464,7 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
         for (int a = 0; a < 3; a++) r_end[a] = r[a] + s_wall * n[a];
         double nu_end = nu_lab * (1.0 - dot3(n, r_end) / ct);
         int restart = 0;
+        double s_pi = 0.0;          /* start of the photoionization segment, from r */
         while (cursor < pb->nline && P->nu[cursor] > nu_end) {
             int32_t l = P->order[cursor];
             ledger[L_TESTS] += 1.0;
@@ -390,10 +473,20 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
             double lam = pb->lambda_A[l] * 1e-8;
             double tau = xo_tau_sobolev(P->A[l], g_l, g_u, lam, n_l, n_u, pb->t);
             if (tau > pr->tau_min) {
+                double nu_l = P->nu[cursor];
+                if (pr->mode == 0 && pb->n_pi > 0) {
+                    /* the ray moves to the resonance point, photoionizing on the way
+                     * (Sec. 2.3.2); the line sees what photoionization left */
+                    double s_l = ct * (1.0 - nu_l / nu_lab) - dot3(n, r);
+                    if (pi_segment(P, cell, pc, nu_lab, n, r, s_pi, s_l, &N, E0, S_pi, heat, ledger)) {
+                        fate = 1;
+                        goto done;
+                    }
+                    if (s_l > s_pi) s_pi = s_l;
+                }
                 events++;
                 ledger[L_EVENTS] += 1.0;
                 double f_corr = 1.0 - g_l * n_u / (g_u * n_l);
-                double nu_l = P->nu[cursor];
                 /* 1 - e^-tau and e^-tau, each without cancellation */
                 double ex, ome;
                 if (tau > XO_LN2) { ex = exp(-tau); ome = 1.0 - ex; }
@@ -466,6 +559,11 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
             cursor++;
         }
         if (restart) continue;
+        if (pr->mode == 0 && pb->n_pi > 0 &&
+            pi_segment(P, cell, pc, nu_lab, n, r, s_pi, s_wall, &N, E0, S_pi, heat, ledger)) {
+            fate = 1;
+            goto done;
+        }
         /* advance to the wall and step into the next cell */
         for (int a = 0; a < 3; a++) r[a] = r_end[a];
         idx[axis] += (n[axis] > 0.0) ? 1 : -1;
@@ -493,15 +591,19 @@ done:
 /* Transport packets [p_begin, p_end) of an N-packet emission.  S (natural cell
  * order x caller line order; may be NULL), spec and ledger are accumulated
  * into; pkt (optional) receives XO_PKT_FIELDS doubles per packet; rec
- * (optional) receives one (cell, line, value) record per estimator increment.
+ * (optional) receives one (cell, line, value) record per estimator increment;
+ * S_pi [ncell][n_pi] and heat [ncell] (optional) the photons absorbed per
+ * photoionizing level and the photoionization heating (erg/s) per cell.
  * Returns 0, or -1 if more than rec_cap records were produced. */
 int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *spec,
-                 double *ledger, double *pkt, xo_rec *rec, int64_t rec_cap, int64_t *rec_n) {
+                 double *ledger, double *pkt, xo_rec *rec, int64_t rec_cap, int64_t *rec_n,
+                 double *S_pi, double *heat) {
     prep_t P;
     g_rec = rec; g_rec_cap = rec_cap; g_rec_n = 0;
     prep(&P, pb, pr);
     for (int64_t p = pr->p_begin; p < pr->p_end; p++)
-        transport_packet(&P, p, S, spec, ledger, pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL);
+        transport_packet(&P, p, S, spec, ledger, pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL,
+                         S_pi, heat);
     unprep(&P);
     if (rec_n) *rec_n = g_rec_n;
     g_rec = NULL;

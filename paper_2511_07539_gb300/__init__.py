@@ -46,7 +46,8 @@ class AtomDesc(C.Structure):
     _fields_ = [("n_ion", C.c_int32), ("nline", C.c_int32),
                 ("level_off", C.c_void_p), ("E_level", C.c_void_p), ("g_level", C.c_void_p),
                 ("lo", C.c_void_p), ("up", C.c_void_p), ("lambda_A", C.c_void_p),
-                ("f_lu", C.c_void_p), ("n_ion_density", C.c_void_p), ("ups_down", C.c_void_p)]
+                ("f_lu", C.c_void_p), ("n_ion_density", C.c_void_p), ("ups_down", C.c_void_p),
+                ("chi_ion", C.c_void_p), ("charge", C.c_void_p), ("pi_nlev", C.c_void_p)]
 
 
 class TransportParams(C.Structure):
@@ -64,7 +65,7 @@ class TransportParams(C.Structure):
 STATS_FIELDS = ["emitted_N", "escaped_N", "absorbed_N", "dropped_N", "emitted_E", "escaped_E",
                 "out_of_band_E", "events", "tests", "guard", "thermal_E", "interactions",
                 "abs_E_cmf", "reemit_E_cmf", "transport_ms", "zero_ms", "rounds", "queued",
-                "emit_ms", "trace_ms", "escape_ms", "kernels"]
+                "emit_ms", "trace_ms", "escape_ms", "kernels", "photoionized_N", "photoionized_E"]
 
 
 class TransportStats(C.Structure):
@@ -134,7 +135,7 @@ class NlteStats(C.Structure):
 
 class Sizes(C.Structure):
     _fields_ = [(f, C.c_int64) for f in
-                ["ncell", "nlev", "nline", "n_ion", "spec_views", "spec_bins", "store_bytes"]]
+                ["ncell", "nlev", "nline", "n_ion", "spec_views", "spec_bins", "store_bytes", "n_pi"]]
 
 
 _lib = None
@@ -161,6 +162,7 @@ def lib():
             "run_transport": ([vp, vp, vp], C.c_int),
             "get_estimators": ([vp, i64, i64, vp], C.c_int),
             "get_photoexcitation_rates": ([vp, i64, i64, vp, vp, vp], C.c_int),
+            "get_photoionization_rates": ([vp, i64, i64, vp, vp], C.c_int),
             "get_spectrum": ([vp, i32, vp, C.c_size_t], C.c_int),
             "get_sizes": ([vp, vp], C.c_int),
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
@@ -263,11 +265,13 @@ def init_grid(ctx, nx, ny, nz, v_max, t, Te, ne, L_cell=None, band_A=(0.0, 0.0),
 
 
 def load_atomic_data(ctx, level_off, E_level, g_level, lo, up, lambda_A, f_lu,
-                     n_ion_density=None, ups_down=None):
+                     n_ion_density=None, ups_down=None, chi_ion=None, charge=None, pi_nlev=None):
     lo_, up_, off_ = _i32(lo), _i32(up), _i32(level_off)
-    fl = [_f64(x) for x in (E_level, g_level, lambda_A, f_lu, n_ion_density, ups_down)]
+    fl = [_f64(x) for x in (E_level, g_level, lambda_A, f_lu, n_ion_density, ups_down, chi_ion)]
+    ch_, np_ = (_i32(charge) if charge is not None else None), (_i32(pi_nlev) if pi_nlev is not None else None)
     d = AtomDesc(len(off_) - 1, len(lo_), _ptr(off_), _ptr(fl[0]), _ptr(fl[1]), _ptr(lo_),
-                 _ptr(up_), _ptr(fl[2]), _ptr(fl[3]), _ptr(fl[4]), _ptr(fl[5]))
+                 _ptr(up_), _ptr(fl[2]), _ptr(fl[3]), _ptr(fl[4]), _ptr(fl[5]), _ptr(fl[6]),
+                 _ptr(ch_), _ptr(np_))
     _check(ctx, lib().load_atomic_data(ctx, C.byref(d)))
 
 
@@ -349,6 +353,20 @@ def get_photoexcitation_rates(ctx, cell_begin=0, n_cells=None, R_lu=None, R_ul=N
     _check(ctx, lib().get_photoexcitation_rates(ctx, cell_begin, n_cells, _ptr(R_lu), _ptr(R_ul),
                                                 _ptr(Jbar)))
     return R_lu, R_ul, Jbar
+
+
+def get_photoionization_rates(ctx, cell_begin=0, n_cells=None, Gamma=None, heating=None,
+                              want=("Gamma", "heating")):
+    """Photoionization rates [n_cells, n_pi] (s^-1) and heating [n_cells] (erg/s)
+    of the last attenuation pass (Sec. 2.3.1)."""
+    sz = get_sizes(ctx)
+    n_cells = sz["ncell"] - cell_begin if n_cells is None else n_cells
+    if Gamma is None and "Gamma" in want:
+        Gamma = np.zeros((n_cells, sz["n_pi"]))
+    if heating is None and "heating" in want:
+        heating = np.zeros(n_cells)
+    _check(ctx, lib().get_photoionization_rates(ctx, cell_begin, n_cells, _ptr(Gamma), _ptr(heating)))
+    return Gamma, heating
 
 
 def solve_nlte(ctx, upsilon, precision=XT_PREC_FP32_IR, rates=XT_RATES_ESTIMATORS,
@@ -558,7 +576,9 @@ class Context:
         init_grid(self.h, w.nx, w.ny, w.nz, w.v_max, w.t, w.Te, w.ne, w.L_cell, w.band_A,
                   rho=w.rho, deposition=w.deposition, subdomains=sd)
         load_atomic_data(self.h, w.level_off, w.E_level, w.g_level, w.lo, w.up, w.lambda_A,
-                         w.f_lu, n_ion_density=w.n_ion_density, ups_down=with_scatter_data)
+                         w.f_lu, n_ion_density=w.n_ion_density, ups_down=with_scatter_data,
+                         chi_ion=getattr(w, "chi_ion", None), charge=getattr(w, "charge", None),
+                         pi_nlev=getattr(w, "pi_nlev", None))
         set_populations(self.h, w.pops if pops is None else pops)
 
     def transport(self, w, **kw):
@@ -577,4 +597,5 @@ class Context:
 
 _CTX_FUNCS = {"init_grid", "load_atomic_data", "set_populations", "get_populations", "solve_nlte",
               "get_sobolev_tau", "run_transport", "get_estimators", "get_photoexcitation_rates",
-              "get_spectrum", "get_sizes", "run_coupled", "set_estimator_store"}
+              "get_spectrum", "get_sizes", "run_coupled", "set_estimator_store",
+              "get_photoionization_rates"}

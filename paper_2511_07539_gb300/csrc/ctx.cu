@@ -306,7 +306,10 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_qoff, (void**)&c->d_qguide, (void**)&c->d_nuguide, (void**)&c->d_Lc, (void**)&c->d_wline, (void**)&c->d_spec,
                    (void**)&c->d_ledger, (void**)&c->d_scratch, (void**)&c->d_lines,
                    (void**)&c->d_pool_f, (void**)&c->d_pool_i, (void**)&c->d_pool_pid,
-                   (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n};
+                   (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n,
+                   (void**)&c->d_pi_nuth, (void**)&c->d_pi_sig, (void**)&c->d_pi_chi, (void**)&c->d_pi_lev,
+                   (void**)&c->d_pi_sorted_of, (void**)&c->d_kappa, (void**)&c->d_piG, (void**)&c->d_piD,
+                   (void**)&c->d_piH};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;
@@ -370,6 +373,69 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
   c->have_grid = true;
   c->have_atoms = c->have_pops = c->have_S = false;
   c->qoff_N = -1;
+  return XT_OK;
+}
+
+// Photoionizing levels of load_atomic_data (Sec. 2.3.1, Eq. sigma_OTSPI):
+// thresholds, the cross section's constant factor sig (sigma = sig lambda^3),
+// sorted by threshold frequency, descending (ties in the caller's order).
+static int load_photoionization(xt_ctx* c, const xt_atom_desc* a, const std::vector<int>& off,
+                                const std::vector<double>& E) {
+  c->npi = 0;
+  c->have_pi = false;
+  c->h_pi_sorted_of.clear();
+  const int given = (a->chi_ion != nullptr) + (a->charge != nullptr) + (a->pi_nlev != nullptr);
+  if (given == 0) return XT_OK;
+  if (given != 3) return fail(c, XT_EINVAL, "load_atomic_data: chi_ion, charge and pi_nlev go together");
+  int rc;
+  const int nz = a->n_ion;
+  std::vector<double> chi(nz);
+  std::vector<int> ch(nz), np(nz);
+  if ((rc = copy(c, chi.data(), a->chi_ion, nz * sizeof(double), "chi_ion"))) return rc;
+  if ((rc = copy(c, ch.data(), a->charge, nz * sizeof(int), "charge"))) return rc;
+  if ((rc = copy(c, np.data(), a->pi_nlev, nz * sizeof(int), "pi_nlev"))) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> nuth, sig, thr;
+  std::vector<int> lev;
+  for (int z = 0; z < nz; ++z) {
+    if (np[z] < 0 || np[z] > off[z + 1] - off[z])
+      return fail(c, XT_EINVAL, "load_atomic_data: pi_nlev[" + std::to_string(z) + "] outside 0..levels of the ion");
+    if (ch[z] < 0) return fail(c, XT_EINVAL, "load_atomic_data: charge[" + std::to_string(z) + "] < 0");
+    for (int i = 0; i < np[z]; ++i) {
+      const int l = off[z] + i;
+      const double x = chi[z] - E[l];                       // threshold energy
+      if (!(x > 0) || !std::isfinite(chi[z]))
+        return fail(c, XT_EINVAL, "load_atomic_data: photoionization threshold chi_ion - E_u <= 0 (ion " +
+                                      std::to_string(z) + ", level " + std::to_string(i) + ")");
+      const double inv_lam_ion = x / (kH * kC);             // 1 / lambda_ion [cm^-1]
+      const double q = (double)(ch[z] + 1);
+      sig.push_back(7.9e-18 * inv_lam_ion * inv_lam_ion * inv_lam_ion / std::sqrt(1.0 - E[l] / chi[z]) / (q * q));
+      nuth.push_back(x / kH);
+      thr.push_back(x);
+      lev.push_back(l);
+    }
+  }
+  const int n = (int)lev.size();
+  if (n > XT_PI_MAX)
+    return fail(c, XT_EINVAL, "load_atomic_data: " + std::to_string(n) + " photoionizing levels exceed XT_PI_MAX");
+  std::vector<int> ord(n);
+  for (int k = 0; k < n; ++k) ord[k] = k;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return nuth[x] > nuth[y]; });
+  std::vector<double> s_nu(n), s_sig(n), s_chi(n);
+  std::vector<int> s_lev(n);
+  c->h_pi_sorted_of.assign(n, 0);
+  for (int s = 0; s < n; ++s) {
+    const int k = ord[s];
+    s_nu[s] = nuth[k]; s_sig[s] = sig[k]; s_chi[s] = thr[k]; s_lev[s] = lev[k];
+    c->h_pi_sorted_of[k] = s;
+  }
+  c->npi = n;
+  if (n == 0) return XT_OK;
+  if ((rc = to_device(c, s_nu, &c->d_pi_nuth, "pi thresholds"))) return rc;
+  if ((rc = to_device(c, s_sig, &c->d_pi_sig, "pi cross sections"))) return rc;
+  if ((rc = to_device(c, s_chi, &c->d_pi_chi, "pi threshold energies"))) return rc;
+  if ((rc = to_device(c, s_lev, &c->d_pi_lev, "pi levels"))) return rc;
+  if ((rc = to_device(c, c->h_pi_sorted_of, &c->d_pi_sorted_of, "pi order"))) return rc;
   return XT_OK;
 }
 
@@ -478,6 +544,7 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   if ((rc = to_device(c, ups, &c->d_ups_down, "ups_down"))) return rc;
   if (a->n_ion_density && (rc = upload_rows(c, a->n_ion_density, &c->d_nion, a->n_ion, "n_ion_density")))
     return rc;
+  if ((rc = load_photoionization(c, a, off, E))) return rc;
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_atoms = true;
   c->have_pops = c->have_S = false;
@@ -645,6 +712,88 @@ int get_photoexcitation_rates(xt_ctx* c, int64_t c0, int64_t nc, double* R_lu, d
   return XT_OK;
 }
 
+// Photoionization rates Gamma_k = N_abs,k / (n_k V) and heating per cell
+// (Sec. 2.3.1) from the pass's per-cell accumulators: a segment that
+// photoionized over length d added X d (X = N beta(tau) lambda^3, beta =
+// (1 - e^-tau) / tau) to G[row][b], b its first level with the whole length,
+// and X d_k to D[row][k] for a level k whose threshold it crossed after d_k;
+// level k (sorted) then absorbed N_abs,k = sig_k n_k (sum_{b <= k} G[b] + D[k]).
+// Heating = h sum (N_abs nu) - sum_k N_abs,k chi_k.  A thread per cell.
+__global__ void k_pi_rates(Geometry g, int npi, const double* __restrict__ pops, int nlev,
+                           const double* __restrict__ G, const double* __restrict__ D,
+                           const double* __restrict__ H, const double* __restrict__ sig,
+                           const double* __restrict__ chi, const int* __restrict__ lev,
+                           int64_t c0, int64_t nc, double V, double* __restrict__ Gamma,
+                           double* __restrict__ heat) {
+  for (int64_t cl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cl < nc;
+       cl += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + cl;
+    const int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    const int64_t row = row_of(g, ix, iy, iz);
+    const double* Gr = G + row * (npi + 1);
+    const double* Dr = D + row * npi;
+    const double* pr = pops + row * nlev;
+    double run = 0.0, absorbed = 0.0;
+    for (int s = 0; s < npi; ++s) {
+      run += Gr[s];
+      const double n = pr[lev[s]];
+      const double Nabs = sig[s] * n * (run + Dr[s]);
+      absorbed += Nabs * chi[s];
+      if (Gamma) Gamma[cl * npi + s] = n > 0.0 ? Nabs / (n * V) : 0.0;
+    }
+    if (heat) heat[cl] = kH * H[row] - absorbed;
+  }
+}
+
+// Sorted level order to the caller's, row by row (in place through a copy).
+__global__ void k_pi_reorder(const double* __restrict__ in, const int* __restrict__ sorted_of, int npi,
+                             int64_t nc, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc * npi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cl = i / npi;
+    const int k = (int)(i - cl * npi);
+    out[i] = in[cl * npi + sorted_of[k]];
+  }
+}
+
+int get_photoionization_rates(xt_ctx* c, int64_t c0, int64_t nc, double* Gamma, double* heating) {
+  if (!c) return XT_EINVAL;
+  if (!c->have_pi || !c->have_S)
+    return fail(c, XT_ESTATE, "get_photoionization_rates: no attenuation pass with photoionization data");
+  int rc = check_range(c, c0, nc, "get_photoionization_rates");
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  const Geometry& G = c->geo;
+  const double V = G.dx * G.dy * G.dz;
+  const int npi = c->npi;
+  const int blocks = grid_blocks(std::max<int64_t>(nc, 1), 128);
+  // Gamma: sorted order into the first half of the scratch, then reordered
+  const size_t gb = (size_t)nc * npi * sizeof(double), hb = (size_t)nc * sizeof(double);
+  if (Gamma) {
+    if ((rc = ensure_scratch(c, 2 * gb + hb))) return rc;
+    double* tmp = (double*)c->d_scratch;
+    k_pi_rates<<<blocks, 128, 0, c->stream>>>(G, npi, c->d_pops, c->nlev, c->d_piG, c->d_piD, c->d_piH,
+                                             c->d_pi_sig, c->d_pi_chi, c->d_pi_lev, c0, nc, V, tmp,
+                                             nullptr);
+    XT_CUDA(c, cudaGetLastError());
+    double* dst = is_device_ptr(Gamma) ? Gamma : tmp + (size_t)nc * npi;
+    k_pi_reorder<<<grid_blocks(std::max<int64_t>(nc * npi, 1), 256), 256, 0, c->stream>>>(
+        tmp, c->d_pi_sorted_of, npi, nc, dst);
+    XT_CUDA(c, cudaGetLastError());
+    if (dst != Gamma && (rc = copy(c, Gamma, dst, gb, "photoionization rates"))) return rc;
+  }
+  if (heating) {
+    rc = deliver(c, heating, hb, [&](void* d) {
+      k_pi_rates<<<blocks, 128, 0, c->stream>>>(G, npi, c->d_pops, c->nlev, c->d_piG, c->d_piD, c->d_piH,
+                                               c->d_pi_sig, c->d_pi_chi, c->d_pi_lev, c0, nc, V, nullptr,
+                                               (double*)d);
+    });
+    if (rc) return rc;
+  }
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  return XT_OK;
+}
+
 int get_spectrum(xt_ctx* c, int32_t kind, double* out, size_t n_cap) {
   if (!c || !out) return fail(c, XT_EINVAL, "get_spectrum: null argument");
   if (!c->d_spec) return fail(c, XT_ESTATE, "get_spectrum: run_transport first");
@@ -691,6 +840,7 @@ int get_sizes(xt_ctx* c, xt_sizes* o) {
   o->ncell = c->geo.ncell; o->nlev = c->nlev; o->nline = c->nline; o->n_ion = c->n_ion;
   o->spec_views = c->spec_views; o->spec_bins = c->spec_bins;
   o->store_bytes = (int64_t)c->S_bytes;
+  o->n_pi = c->npi;
   return XT_OK;
 }
 

@@ -44,7 +44,7 @@
 namespace xt {
 
 enum PoolField { F_R0X, F_R0Y, F_R0Z, F_NX, F_NY, F_NZ, F_TMX, F_TMY, F_TMZ, F_TDX, F_TDY, F_TDZ,
-                 F_NULAB, F_NU0, F_N, F_T, NF };
+                 F_NULAB, F_NU0, F_N, F_T, F_SPI, NF };   // F_SPI: start of the photoionization segment
 
 struct Pool {           // structure of arrays, capacity cap
   int64_t cap;
@@ -131,6 +131,16 @@ struct TraceArgs {
   int64_t row0;                       // first row held by S (a streamed group's slab; else 0)
   int grp_nz;                         // rounds == 2: cells along z per streamed group
   int warp_reduce;                    // pre-reduce estimator increments by slot per warp
+  // photoionization (the PI instance): levels sorted by threshold frequency,
+  // descending; per-cell suffix sums and accumulators (see pi_segment)
+  int npi;
+  const double* __restrict__ pi_nuth;  // [npi] Hz
+  const double* __restrict__ pi_sig;   // [npi] sigma = sig lambda^3
+  const int* __restrict__ pi_lev;      // [npi]
+  const double* __restrict__ kappa;    // [row][npi+1]
+  double* __restrict__ piG;            // [row][npi+1]
+  double* __restrict__ piD;            // [row][npi]
+  double* __restrict__ piH;            // [row]
 };
 
 struct EscArgs {
@@ -413,6 +423,7 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
     // stop once N nu_line < e_cut E0 / h (the photon energy at the line below e_cut E0)
     P.F(F_NULAB, i) = o.nu_lab; P.F(F_NU0, i) = o.nu_cmf; P.F(F_N, i) = o.N;
     P.F(F_T, i) = a.e_cut * a.Eph[o.c];
+    P.F(F_SPI, i) = 0.0;
     P.cell[i] = o.idx[0] | (o.idx[1] << 10) | (o.idx[2] << 20);
     P.cursor[i] = o.cursor; P.events[i] = 0; P.ndraw[i] = 0; P.inter[i] = 0;
     P.pid[i] = p;
@@ -427,22 +438,88 @@ __global__ void __launch_bounds__(256) k_emit(const EmitArgs a) {
   warp_flush(acc, a.ledger, slots);
 }
 
+// ---------------------------------------------------------------- photoionization
+// Photoionization on one path segment (Sec. 2.3.1), s0..s1 along the ray (s
+// from the emission point, comoving frequency nu0 - aslope s).  Every level
+// whose threshold lies below the photon energy at the segment start takes
+// part over the whole length d = s1 - s0, or up to where the falling comoving
+// frequency reaches its threshold; sigma_k = sig_k lambda^3 with the
+// wavelength at the segment start (Eq. sigma_OTSPI).  So
+//   tau = lambda^3 (d kappa[b] + sum_{crossed k} sig_k n_k d_k),
+// kappa[b] the cell's suffix sum of sig n over the levels that keep the whole
+// length (sorted positions >= b).  The packet loses N (1 - e^-tau); level k's
+// share N_abs tau_k / tau is X sig_k n_k d_k with X = N beta(tau) lambda^3,
+// beta = (1 - e^-tau) / tau, so the cell keeps X d at G[b] and X d_k at D[k]
+// for the crossed levels (one atomic for the common part), and N_abs nu for
+// the heating.  pcur is the first level still active at s0 and moves past the
+// crossed ones.  Returns whether the photon energy at s1 fell below the cut.
+__device__ __forceinline__ bool pi_segment(const TraceArgs& a, const FixExpTables& fx,
+                                           const double* s_nuth, const double* s_sig, const int* s_lev,
+                                           int row, const double* prow, double s0, double s1,
+                                           double nu0, double aslope, double inv_as, int& pcur,
+                                           double& N, double& N_pi, double& E_pi, double Tq) {
+  double d = s1 - s0;
+  if (bits(d) <= 0) d = 0.0;                        // (rounding can put s1 just before s0)
+  const double nu_a = fma(-aslope, s0, nu0);
+  const double nu_b = fma(-aslope, bits(d) > 0 ? s1 : s0, nu0);
+  int kb = pcur;
+  double tc = 0.0;
+  while (kb < a.npi && s_nuth[kb] >= nu_b) {        // thresholds crossed inside the segment
+    tc = fma(s_sig[kb] * prow[s_lev[kb]], (nu_a - s_nuth[kb]) * inv_as, tc);
+    ++kb;
+  }
+  const int64_t rb = (int64_t)row * (a.npi + 1);
+  const double lam = div_pos(kC, nu_a);
+  const double l3 = lam * lam * lam;
+  const double tau = l3 * fma(a.kappa[rb + kb], d, tc);
+  if (bits(tau) > 0) {
+    double ex, ome, beta;
+    if (bits(tau) < bits(0x1p-10)) {                // series: keeps 1 - e^-tau exact for tiny tau
+      beta = sobolev_beta_fix(fx, tau, nullptr);
+      ome = tau * beta;
+      ex = 1.0 - ome;
+    } else {
+      expneg(fx, tau, ex, ome);
+      beta = div_pos(ome, tau);
+    }
+    const double X = N * beta * l3;
+    if (kb < a.npi && bits(d) > 0) warp_add_slot(a.piG, rb + kb, X * d, a.warp_reduce);
+    for (int k = pcur; k < kb; ++k)
+      atomicAdd(a.piD + (int64_t)row * a.npi + k, X * ((nu_a - s_nuth[k]) * inv_as));
+    const double Nabs = N * ome;
+    N_pi += Nabs;
+    E_pi += Nabs * nu_a;
+    warp_add_slot(a.piH, row, Nabs * nu_a, a.warp_reduce);
+    N = N * ex;
+  }
+  pcur = kb;
+  return bits(N * nu_b) < bits(Tq);
+}
+
 // ---------------------------------------------------------------- trace
 // Per-lane ledger: integer counters, FP64 sums.
-enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_EMITN, T_EMITE, T_NACC };
+enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_EMITN, T_EMITE, T_NACC, T_PIN = T_NACC, T_PIE };
 constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
 constexpr int kRefillLanes = 24;  // empty lanes of a warp that trigger a refill with emission
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
-template <int MODE>
-__global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(const TraceArgs a) {
+template <int MODE, bool PI = false>
+__global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
   __shared__ int rtab[3 * 1024];
+  constexpr int kPiS = PI ? XT_PI_MAX : 1;          // photoionization tables (PI instance)
+  __shared__ double s_nuth[kPiS], s_sig[kPiS];
+  __shared__ int s_lev[kPiS];
   stage(fx, a.fx);
   if (MODE == XT_MODE_SCATTER || a.fused) stage(trig, a.trig);
   const int nt = a.g.nx + a.g.ny + a.g.nz;
   for (int k = threadIdx.x; k < nt; k += blockDim.x) rtab[k] = a.rtab[k];
+  if constexpr (PI) {
+    for (int k = threadIdx.x; k < a.npi; k += blockDim.x) {
+      s_nuth[k] = a.pi_nuth[k]; s_sig[k] = a.pi_sig[k]; s_lev[k] = a.pi_lev[k];
+    }
+  }
   __syncthreads();
   const int* RX = rtab;
   const int* RY = rtab + a.g.nx;
@@ -455,9 +532,10 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   const Pool& P = a.pool;
   const int lane = threadIdx.x & 31;
   const long long taumin_bits = __double_as_longlong(a.tau_min);
-  double acc[T_NACC];
+  constexpr int kAcc = PI ? T_PIE + 1 : T_NACC;
+  double acc[kAcc];
 #pragma unroll
-  for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kAcc; ++k) acc[k] = 0.0;
   unsigned n_tests = 0, n_events = 0, n_guard = 0, n_inter = 0;
 
   bool have = false, seg_new = true;
@@ -469,6 +547,10 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   long long end_bits = 0;
   double tmx = 0, tmy = 0, tmz = 0, tdx = 0, tdy = 0, tdz = 0, nu0 = 0, aslope = 0;
   double N = 0, N_in = 0, Tq = 0;
+  // photoionization state (PI instance): segment start, 1 / aslope, the
+  // packet's photoionized photons, first level still active, the wall ahead
+  double s_pi = 0, inv_as = 0, N_pi = 0, s_wall = 0;
+  int pcur = 0;
 
   bool drained = false;                  // the packet list is used up (warp-uniform)
   for (;;) {
@@ -508,6 +590,13 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             Tq = a.em.e_cut * a.em.Eph[o.c];
             cursor = o.cursor;
             events = 0;
+            if constexpr (PI) {
+              s_pi = 0.0;
+              N_pi = 0.0;
+              inv_as = div_pos(a.ct, o.nu_lab);
+              pcur = 0;
+              while (pcur < a.npi && s_nuth[pcur] >= nu0) ++pcur;
+            }
             P.F(F_NX, i) = o.n[0]; P.F(F_NY, i) = o.n[1]; P.F(F_NZ, i) = o.n[2];
             P.F(F_NULAB, i) = o.nu_lab;
             P.pid[i] = p;
@@ -537,6 +626,14 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
             Tq = P.F(F_T, i);
             cursor = P.cursor[i];
             events = P.events[i];
+            if constexpr (PI) {
+              s_pi = P.F(F_SPI, i);
+              N_pi = 0.0;
+              inv_as = div_pos(a.ct, P.F(F_NULAB, i));
+              const double nu_s = fma(-aslope, s_pi, nu0);
+              pcur = 0;
+              while (pcur < a.npi && s_nuth[pcur] >= nu_s) ++pcur;
+            }
             rx = RX[ix]; ry = RY[iy]; rz = RZ[iz];
             row = rx + ry + rz;
             if (a.rounds == 2) {          // a streamed group: whole x-y layers of z cells
@@ -561,7 +658,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     // (so that no lane keeps its warp waiting long); the event code below then
     // runs for all lanes that found one together.
     const double* prow = a.pops + (int64_t)row * a.nlev;
-    bool found = false, escaped = false, queued = false;
+    bool found = false, escaped = false, queued = false, pi_drop = false;
     LineRec L;
     double n_l = 0.0, n_u = 0.0, tau = 0.0;
     // the record of the next line to test is loaded one test ahead, so that its
@@ -576,6 +673,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         if (bits(tmy) < bits(sw)) { sw = tmy; axis = 1; }   // ties to the lowest axis
         if (bits(tmz) < bits(sw)) { sw = tmz; axis = 2; }
         end_bits = bits(nu0 - aslope * sw);
+        if constexpr (PI) s_wall = sw;
         seg_new = false;
       }
       while (cursor < a.nline && next_bits > end_bits) {
@@ -591,6 +689,14 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         next_bits = cn < a.nline ? bits(Ln.x) : 0;
       }
       if (found) break;
+      if constexpr (PI) {      // photoionization up to the wall (Sec. 2.3.1)
+        if (pi_segment(a, fx, s_nuth, s_sig, s_lev, row, prow, s_pi, s_wall, nu0, aslope, inv_as, pcur,
+                       N, N_pi, acc[T_PIE], Tq)) {
+          pi_drop = true;
+          break;
+        }
+        if (bits(s_wall) > bits(s_pi)) s_pi = s_wall;
+      }
       // no further line in this cell: step into the next one (branch-free in axis)
       const bool a0 = axis == 0, a1 = axis == 1, a2 = axis == 2;
       const int coord = (a0 ? ix : a1 ? iy : iz) + (a0 ? sx : a1 ? sy : sz);
@@ -612,6 +718,18 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
       if (++steps >= kMaxSteps) break;
     }
     int fate = -1;                        // -1 alive
+    if constexpr (PI) {
+      if (found) {             // the ray moves to the resonance point, photoionizing on the way
+        const double s_l = (nu0 - L.x) * inv_as;
+        if (pi_segment(a, fx, s_nuth, s_sig, s_lev, row, prow, s_pi, s_l, nu0, aslope, inv_as, pcur,
+                       N, N_pi, acc[T_PIE], Tq)) {
+          pi_drop = true;
+          found = false;
+        }
+        if (bits(s_l) > bits(s_pi)) s_pi = s_l;
+      }
+      if (pi_drop) { acc[T_DROP] += N; fate = 1; }
+    }
     if (found) {
       // ---- line event (lanes that found one run this together)
       ++events;
@@ -703,7 +821,14 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
     if (escaped || queued || fate >= 0) {
       P.F(F_N, i) = N;
       P.events[i] = events;
-      if (MODE == XT_MODE_ATTEN) acc[T_ABS] += N_in - N;   // photons this lane absorbed
+      if (MODE == XT_MODE_ATTEN) {
+        if constexpr (PI) {
+          acc[T_ABS] += (N_in - N) - N_pi;               // photons the lines absorbed
+          acc[T_PIN] += N_pi;
+        } else {
+          acc[T_ABS] += N_in - N;                        // photons this lane absorbed
+        }
+      }
       if (queued || (MODE == XT_MODE_SCATTER && escaped)) {
         P.F(F_TMX, i) = tmx; P.F(F_TMY, i) = tmy; P.F(F_TMZ, i) = tmz;
         P.F(F_TDX, i) = sx < 0 ? neg_bits(tdx) : tdx;
@@ -712,6 +837,7 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
         P.F(F_NU0, i) = nu0;
         P.cursor[i] = cursor;
         P.cell[i] = ix | (iy << 10) | (iz << 20);
+        if constexpr (PI) P.F(F_SPI, i) = s_pi;
       }
       if (fate >= 0 && a.records) {
         double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
@@ -733,8 +859,11 @@ __global__ void __launch_bounds__(256, MODE == XT_MODE_ATTEN ? 4 : 2) k_trace(co
   double cnt[4] = {(double)n_tests, (double)n_events, (double)n_guard, (double)n_inter};
   const int cslots[4] = {LG_TESTS, LG_EVENTS, LG_GUARD, LG_INTERACT};
   warp_flush(cnt, a.ledger, cslots);
-  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
-                             LG_EMIT_N, LG_EMIT_E};
+  const int all_slots[T_PIE + 1] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
+                                    LG_EMIT_N, LG_EMIT_E, LG_PI_N, LG_PI_E};
+  int slots[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) slots[k] = all_slots[k];
   warp_flush(acc, a.ledger, slots);
 }
 
@@ -852,6 +981,24 @@ __global__ void k_line_emission(Geometry g, const double2* __restrict__ lines,
 }
 
 
+// Photoionization: per cell the suffix sums kappa[b] = sum_{k >= b} sig_k n_k
+// over the levels sorted by threshold frequency (descending), kappa[npi] = 0.
+__global__ void k_pi_kappa(int64_t nrows, int npi, int nlev, const double* __restrict__ pops,
+                           const double* __restrict__ sig, const int* __restrict__ lev,
+                           double* __restrict__ kappa) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double* pr = pops + r * nlev;
+    double* kr = kappa + r * (npi + 1);
+    double run = 0.0;
+    kr[npi] = 0.0;
+    for (int k = npi - 1; k >= 0; --k) {
+      run += sig[k] * pr[lev[k]];
+      kr[k] = run;
+    }
+  }
+}
+
 static int sm_count() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -905,6 +1052,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (p->max_events < 1) return fail(c, XT_EINVAL, "run_transport: max_events must be >= 1");
   if (!(p->tau_min > 0) || !(p->e_cut >= 0)) return fail(c, XT_EINVAL, "run_transport: tau_min > 0 and e_cut >= 0 required");
   if (c->nline < 1) return fail(c, XT_ESTATE, "run_transport: no lines loaded");
+  const bool pi = c->npi > 0;
+  if (pi && p->mode != XT_MODE_ATTEN)
+    return fail(c, XT_EINVAL, "run_transport: photoionization is part of the attenuation mode only");
   if (G.ncell >= (int64_t)1 << 31) return fail(c, XT_EINVAL, "run_transport: more than 2^31 cells");
   if (G.nx > 1024 || G.ny > 1024 || G.nz > 1024) return fail(c, XT_EINVAL, "run_transport: more than 1024 cells along an axis");
   int rc;
@@ -1060,8 +1210,36 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     }
   }
 
+  // photoionization: per-cell arrays, the cell's suffix sums from the populations
+  if (pi) {
+    const int64_t rows = G.ncell;
+    if (c->pi_rows != rows || c->pi_npi != c->npi) {
+      c->pi_rows = 0;
+      if ((rc = alloc(c, (void**)&c->d_kappa, (size_t)rows * (c->npi + 1) * sizeof(double), "pi kappa"))) return rc;
+      if ((rc = alloc(c, (void**)&c->d_piG, (size_t)rows * (c->npi + 1) * sizeof(double), "pi G"))) return rc;
+      if ((rc = alloc(c, (void**)&c->d_piD, (size_t)rows * c->npi * sizeof(double), "pi D"))) return rc;
+      if ((rc = alloc(c, (void**)&c->d_piH, (size_t)rows * sizeof(double), "pi H"))) return rc;
+      XT_CUDA(c, cudaMemsetAsync(c->d_piG, 0, (size_t)rows * (c->npi + 1) * sizeof(double), c->stream));
+      XT_CUDA(c, cudaMemsetAsync(c->d_piD, 0, (size_t)rows * c->npi * sizeof(double), c->stream));
+      XT_CUDA(c, cudaMemsetAsync(c->d_piH, 0, (size_t)rows * sizeof(double), c->stream));
+      c->pi_rows = rows;
+      c->pi_npi = c->npi;
+    }
+    k_pi_kappa<<<blocks_for(rows, 128, 8), 128, 0, c->stream>>>(rows, c->npi, c->nlev, c->d_pops, c->d_pi_sig,
+                                                                c->d_pi_lev, c->d_kappa);
+    XT_CUDA(c, cudaGetLastError());
+    if (!p->accumulate) {
+      XT_CUDA(c, cudaMemsetAsync(c->d_piG, 0, (size_t)rows * (c->npi + 1) * sizeof(double), c->stream));
+      XT_CUDA(c, cudaMemsetAsync(c->d_piD, 0, (size_t)rows * c->npi * sizeof(double), c->stream));
+      XT_CUDA(c, cudaMemsetAsync(c->d_piH, 0, (size_t)rows * sizeof(double), c->stream));
+    }
+  }
+  c->have_pi = pi;
+
   int occ = 0;
-  if (p->mode == XT_MODE_ATTEN)
+  if (p->mode == XT_MODE_ATTEN && pi)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true>, 256, 0);
+  else if (p->mode == XT_MODE_ATTEN)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_SCATTER>, 256, 0);
@@ -1181,6 +1359,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.row0 = 0;
   ta.grp_nz = G.nz / NG;
   ta.warp_reduce = (p->flags & XT_FLAG_NO_WARP_REDUCE) ? 0 : 1;
+  ta.npi = pi ? c->npi : 0;
+  ta.pi_nuth = c->d_pi_nuth; ta.pi_sig = c->d_pi_sig; ta.pi_lev = c->d_pi_lev;
+  ta.kappa = c->d_kappa; ta.piG = c->d_piG; ta.piD = c->d_piD; ta.piH = c->d_piH;
   if (host_store) ta.rounds = 2;
 
   EscArgs xa;
@@ -1257,7 +1438,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
             ta.out = out_tmp;
             const int grid = (int)std::min<int64_t>(grid_max, (lens[part] + 255) / 256);
             sl = tick(1);
-            if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+            if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+            else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
             else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
             XT_CUDA(c, cudaGetLastError());
             tock(sl);
@@ -1311,7 +1493,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+      if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
       XT_CUDA(c, cudaGetLastError());
       tock(sl);
@@ -1373,7 +1556,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   if (out) {
     double* o = &out->emitted_N;
-    for (int k = 0; k < LG_N; ++k) o[k] = led[k];
+    for (int k = 0; k < LG_STATS; ++k) o[k] = led[k];
+    out->photoionized_N = led[LG_PI_N];
+    out->photoionized_E = kH * led[LG_PI_E];
     float ms_all = 0, ms_clear = 0;
     cudaEventElapsedTime(&ms_all, c->ev0, c->ev2);
     cudaEventElapsedTime(&ms_clear, c->ev0, c->ev1);
@@ -1676,7 +1861,7 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
   if (out) {
     std::memset(out, 0, sizeof(*out));
     double* o = &out->emitted_N;
-    for (int k = 0; k < LG_N; ++k) o[k] = led[k];
+    for (int k = 0; k < LG_STATS; ++k) o[k] = led[k];
     out->rounds = 1;
     out->kernels = kernels;
   }

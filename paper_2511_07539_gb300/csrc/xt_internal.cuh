@@ -18,9 +18,13 @@ constexpr double kMe = 9.1093837015e-28;
 constexpr double kPi = 3.14159265358979323846;
 
 // Per-packet ledger slots (device accumulators), same order as xt_transport_stats.
+// The first LG_STATS slots map one to one onto the leading fields of
+// xt_transport_stats; the photoionization slots onto its last two (LG_PI_E
+// holds photons x Hz, times h on the host).
 enum Ledger {
   LG_EMIT_N, LG_ESC_N, LG_ABS_N, LG_DROP_N, LG_EMIT_E, LG_ESC_E, LG_OOB_E, LG_EVENTS,
-  LG_TESTS, LG_GUARD, LG_THERMAL_E, LG_INTERACT, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_N
+  LG_TESTS, LG_GUARD, LG_THERMAL_E, LG_INTERACT, LG_ABS_E_CMF, LG_REEMIT_E_CMF,
+  LG_STATS, LG_PI_N = LG_STATS, LG_PI_E, LG_N
 };
 
 // Read-only view of everything the transport kernel needs (passed by value).
@@ -90,6 +94,22 @@ struct xt_ctx {
   int *d_down_off = nullptr, *d_down_line = nullptr;
   double* d_nion = nullptr;          // [row][n_ion]
   double* d_ups_down = nullptr;      // [nlev]
+  // photoionizing levels, sorted by threshold frequency (descending; ties in
+  // the caller's order k)
+  int npi = 0;
+  std::vector<int> h_pi_sorted_of;   // caller k -> sorted position
+  double* d_pi_nuth = nullptr;       // [npi] threshold frequency (Hz)
+  double* d_pi_sig = nullptr;        // [npi] sigma = sig lambda^3 (lambda in cm)
+  double* d_pi_chi = nullptr;        // [npi] threshold energy (erg)
+  int* d_pi_lev = nullptr;           // [npi] global level
+  int* d_pi_sorted_of = nullptr;     // [npi] caller k -> sorted position
+  double* d_kappa = nullptr;         // [row][npi+1] suffix sums of sig n_level per cell
+  double* d_piG = nullptr;           // [row][npi+1] segment weights by first full-length level
+  double* d_piD = nullptr;           // [row][npi]   weights of levels whose threshold a segment crossed
+  double* d_piH = nullptr;           // [row] absorbed photons x frequency
+  int64_t pi_rows = 0;               // rows the per-cell photoionization arrays hold
+  int pi_npi = 0;                    //   for this many levels
+  bool have_pi = false;              // the last pass photoionized
   // state
   bool have_pops = false;
   double* d_pops = nullptr;          // [row][nlev]

@@ -80,6 +80,12 @@ class Workload:
     levels_used: np.ndarray = None  # [ncell, n_ion] levels kept per (cell, ion); None = all
     jbar_W: float = 0.0           # mean intensity model W B_nu(T_R) for the rate solves
     jbar_TR: float = 0.0
+    # photoionization data (None: no photoionizing levels): per ion the
+    # ionization energy from its ground level [erg], its charge, and how many of
+    # its lowest levels photoionize
+    chi_ion: np.ndarray = None
+    charge: np.ndarray = None
+    pi_nlev: np.ndarray = None
 
     @property
     def ncell(self) -> int:
@@ -348,6 +354,40 @@ def nlte_batch(n: int = 64, seed: int = 0, n_ion: int = 10, L_max: int = 300,
         levels_used=levels_used, jbar_W=5.6e-5, jbar_TR=8000.0)
     w_.upsilon = collision_strengths(seed, level_off)
     return w_
+
+
+def with_photoionization(w: Workload, chi_eV=None, charge=None, pi_nlev=9, seed=None) -> Workload:
+    """Adds photoionization data to a workload (in place; returns it).
+
+    Recipe (the paper's atomic data are not available): per ion an ionization
+    energy chi_eV (default: uniform in 10.5-14 eV from ``seed``), a charge
+    (default: ion index mod 3, i.e. neutral, singly and doubly ionized stages),
+    and the lowest ``pi_nlev`` levels photoionizing (the ground level and the
+    next eight by default, as the paper's on-the-spot treatment takes)."""
+    rng = np.random.default_rng([w.seed if seed is None else seed, 4231])
+    if chi_eV is None:
+        chi_eV = rng.uniform(10.5, 14.0, w.n_ion)
+    chi = np.broadcast_to(np.asarray(chi_eV, dtype=np.float64), (w.n_ion,)) * EV
+    if charge is None:
+        charge = np.arange(w.n_ion) % 3
+    L = np.diff(w.level_off)
+    w.chi_ion = np.ascontiguousarray(chi)
+    w.charge = np.ascontiguousarray(np.broadcast_to(np.asarray(charge), (w.n_ion,)), dtype=np.int32)
+    w.pi_nlev = np.minimum(np.broadcast_to(np.asarray(pi_nlev), (w.n_ion,)), L).astype(np.int32)
+    return w
+
+
+def pi_levels(w: Workload):
+    """The photoionizing levels in their order (ion by ion, lowest first):
+    global level index, ionization energy and charge of the level's ion."""
+    lev, eion, ch = [], [], []
+    for z in range(w.n_ion):
+        for i in range(int(w.pi_nlev[z])):
+            lev.append(int(w.level_off[z]) + i)
+            eion.append(float(w.chi_ion[z]))
+            ch.append(int(w.charge[z]))
+    return (np.array(lev, dtype=np.int32), np.array(eion, dtype=np.float64),
+            np.array(ch, dtype=np.int32))
 
 
 def workload(name: str, **kw) -> Workload:
