@@ -141,7 +141,26 @@ typedef struct {
      * N_final, escaped lab energy, viewer, lambda bin, interactions, emitting
      * cell, N0, comoving emission frequency, final lab frequency. */
     double *packet_records;
+    /* XT_SAMPLER_MC: n_packets Monte Carlo packets by the cells' integer quota.
+     * XT_SAMPLER_RAYS (Sec. 2.3): from the middle of every emitting cell, for
+     * every bin of the output grid (spec_lam0_A, spec_dlog, spec_nbins) that
+     * holds emission, one ray towards every viewer, along the centre direction
+     * of the viewer's (theta, phi) bin, carrying the cell's emission in the bin
+     * times dOmega_k / 4 pi, at the bin's reddest feature (band emission: the
+     * red edge of the bin's overlap with the band; line emission: the reddest
+     * line in the bin, the ray starting past it).  No random numbers; ray r =
+     * (emitting-cell rank, bin rank, viewer) row-major over cells with
+     * emission in natural order, emitting bins in wavelength order and
+     * viewers; n_packets is ignored and packet_begin / packet_count address
+     * rays (xt_transport_stats.rays gives their number; packet_count = 0 only
+     * counts them).  A ray whose cell has no emission in its bin is empty:
+     * record fate 4, not traced.  Attenuation mode, without subdomain rounds,
+     * with the estimator store on the device; every line must lie on the
+     * output grid for line emission (XT_EINVAL otherwise). */
+    int32_t sampler;
 } xt_transport_params;
+#define XT_SAMPLER_MC 0
+#define XT_SAMPLER_RAYS 1
 
 /* Ledger and timing of the last run_transport (photons/s and erg/s). */
 typedef struct {
@@ -156,6 +175,7 @@ typedef struct {
     double kernels;         /* kernels launched by this call */
     double photoionized_N;  /* photons absorbed by photoionization (Sec. 2.3.1) */
     double photoionized_E;  /* their energy at absorption (comoving), erg/s */
+    double rays;            /* XT_SAMPLER_RAYS: rays of the whole enumeration */
 } xt_transport_stats;
 
 int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);

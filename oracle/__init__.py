@@ -73,7 +73,7 @@ class _Params(C.Structure):
                 ("tau_min", C.c_double), ("e_cut", C.c_double),
                 ("n_theta", C.c_int32), ("n_phi", C.c_int32),
                 ("spec_lam0_A", C.c_double), ("spec_dlog", C.c_double),
-                ("spec_nbins", C.c_int32), ("max_events", C.c_int64)]
+                ("spec_nbins", C.c_int32), ("max_events", C.c_int64), ("sampler", C.c_int32)]
 
 
 _lib = None
@@ -102,6 +102,8 @@ def lib():
         _lib.xo_sigma_pi.restype = d
         _lib.xo_sigma_pi.argtypes = [d, d, d, C.c_int32]
         _lib.xo_emission.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.xo_ray_count.restype = C.c_int64
+        _lib.xo_ray_count.argtypes = [C.c_void_p, C.c_void_p]
         _lib.xo_tau_beta.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
         _lib.xo_packet_quota.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
         _lib.xo_philox4x64_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -152,10 +154,29 @@ def upsilon_down_sums(w) -> np.ndarray:
     return out
 
 
+def _params(w, N, p_begin, p_end, seed, mode, emission, tau_min, e_cut, n_theta, n_phi, spec_dlog,
+            max_events, sampler):
+    lam0, nbins = w.spec_band_A
+    return _Params(N, p_begin, p_end, w.seed if seed is None else seed,
+                   0 if mode == "atten" else 1, 0 if emission == "band" else 1,
+                   tau_min, e_cut, n_theta, n_phi, lam0, spec_dlog, nbins, max_events,
+                   1 if sampler == "rays" else 0)
+
+
+def ray_count(w, emission="band", n_theta=20, n_phi=20, spec_dlog=1e-3):
+    """Rays of the RAYS sampler: emitting cells x emitting wavelength bins x viewers."""
+    keep = _Keep(w)
+    pr = _params(w, 0, 0, 0, 0, "atten", emission, 1e-4, 1e-6, n_theta, n_phi, spec_dlog, 1, "rays")
+    n = lib().xo_ray_count(C.byref(keep.pb), C.byref(pr))
+    if n < 0:
+        raise ValueError("an emitting line lies outside the output wavelength grid")
+    return int(n)
+
+
 def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
               emission="band", tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
               spec_dlog=1e-3, max_events=1_000_000, per_packet=False, sparse=None,
-              rec_cap=None):
+              rec_cap=None, sampler="mc"):
     """Run packets [p_begin, p_end) of the workload's emission through the grid.
 
     Returns S [ncell, nline] (photons/s absorbed, divided by f_corr; natural
@@ -166,7 +187,10 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     A workload with photoionization data (attenuation mode) also gives S_pi
     [ncell, n_pi] (photons/s absorbed per photoionizing level) and heat
     [ncell] (erg/s of photon energy above the thresholds)."""
-    N = w.n_packets if n_packets is None else n_packets
+    if sampler == "rays":
+        N = ray_count(w, emission, n_theta, n_phi, spec_dlog)
+    else:
+        N = w.n_packets if n_packets is None else n_packets
     p_end = N if p_end is None else p_end
     keep = _Keep(w, upsilon_down_sums(w) if mode == "scatter" else None)
     if keep.n_pi and mode != "atten":
@@ -174,9 +198,8 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
     heat = np.zeros(w.ncell) if keep.n_pi else None
     lam0, nbins = w.spec_band_A
-    pr = _Params(N, p_begin, p_end, w.seed if seed is None else seed,
-                 0 if mode == "atten" else 1, 0 if emission == "band" else 1,
-                 tau_min, e_cut, n_theta, n_phi, lam0, spec_dlog, nbins, max_events)
+    pr = _params(w, N, p_begin, p_end, seed, mode, emission, tau_min, e_cut, n_theta, n_phi,
+                 spec_dlog, max_events, sampler)
     if sparse is None:
         sparse = w.ncell * w.nline * 8 > 2e9
     S = None if sparse else np.zeros((w.ncell, w.nline))
@@ -191,9 +214,11 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     rc = lib().xo_transport(C.byref(keep.pb), C.byref(pr), _ptr(S), _ptr(spec), _ptr(ledger),
                             _ptr(pkt), _ptr(rec), 0 if rec is None else rec.shape[0], _ptr(nrec),
                             _ptr(S_pi), _ptr(heat))
+    if rc == -2:
+        raise ValueError("an emitting line lies outside the output wavelength grid")
     if rc != 0:
         raise RuntimeError(f"oracle record buffer too small ({nrec[0]} records)")
-    out = dict(S=S, spec=spec, ledger=dict(zip(LEDGER, ledger[:len(LEDGER)].tolist())))
+    out = dict(S=S, spec=spec, ledger=dict(zip(LEDGER, ledger[:len(LEDGER)].tolist())), n=N)
     if keep.n_pi:
         out["S_pi"], out["heat"] = S_pi, heat
     if sparse:
@@ -214,7 +239,7 @@ def emission(w, n_packets=None, emission="band"):
     keep = _Keep(w)
     N = w.n_packets if n_packets is None else n_packets
     pr = _Params(N, 0, 0, 0, 0, 0 if emission == "band" else 1, 1e-4, 1e-6, 20, 20, 1.0, 1e-3,
-                 1, 1)
+                 1, 1, 0)
     Lc = np.zeros(w.ncell)
     qoff = np.zeros(w.ncell + 1, dtype=np.int64)
     lib().xo_emission(C.byref(keep.pb), C.byref(pr), _ptr(Lc), _ptr(qoff))

@@ -138,6 +138,7 @@ typedef struct {
     double spec_lam0_A, spec_dlog;
     int32_t spec_nbins;
     int64_t max_events;
+    int32_t sampler;           /* 0 Monte Carlo packets, 1 rays per (cell, bin, viewer) */
 } xo_params;
 
 enum { L_EMIT_N, L_ESC_N, L_ABS_N, L_DROP_N, L_EMIT_E, L_ESC_E, L_OOB_E, L_EVENTS,
@@ -158,6 +159,16 @@ typedef struct {
     double *wline;       /* [ncell*nline] line emission weights (emission_mode 1) */
     int32_t *down_off, *down_line;   /* CSR over upper levels of radiative down-lines */
     double *pi_tau;      /* [n_pi] work space of one photoionization segment */
+    /* RAYS sampler: emitting cells, emitting bins, viewing directions */
+    int64_t n_rcell;
+    int64_t *rcell;      /* natural indices of the cells with L_c > 0 */
+    int32_t n_rbin;
+    double *rbin_nu;     /* comoving start frequency of each emitting bin */
+    int32_t *rbin_cursor;/* first line its rays test */
+    double *rbin_frac;   /* band emission: the bin's share of the band */
+    int32_t *rbin_off, *rbin_line;   /* line emission: lines of each bin (CSR, ascending index) */
+    double *view_n;      /* [n_theta n_phi][3] direction of each viewer's centre */
+    double *view_w;      /* [n_theta n_phi] dOmega_k / 4 pi */
 } prep_t;
 
 static const double *g_sort_nu;
@@ -262,6 +273,98 @@ static int prep(prep_t *P, const xo_problem *pb, const xo_params *pr) {
 static void unprep(prep_t *P) {
     free(P->order); free(P->pos); free(P->nu); free(P->A); free(P->Lc); free(P->qoff);
     free(P->wline); free(P->down_off); free(P->down_line); free(P->pi_tau);
+    free(P->rcell); free(P->rbin_nu); free(P->rbin_cursor); free(P->rbin_frac);
+    free(P->rbin_off); free(P->rbin_line); free(P->view_n); free(P->view_w);
+}
+
+static int32_t cursor_at(const prep_t *P, double nu);
+int64_t xo_lambda_bin(double lam_A, double lam0, double dlog, int32_t nbins);
+
+/* The RAYS sampler (Sec. 2.3): from the middle of every emitting cell, for
+ * every wavelength bin j of the output grid that holds emission, one ray
+ * towards every viewer k, with N = E_bin,ij (dOmega_k / 4 pi) / (h nu_j).
+ * Readings: the paper prints the solid-angle factor as a division by
+ * dOmega_k; the rays of a cell and bin must carry its emission isotropically
+ * (the stated purpose of the factor), so each carries the share
+ * dOmega_k / 4 pi.  A ray leaves along the centre direction of its viewer's
+ * (theta, phi) bin.  nu_j is the reddest feature of the bin: for band emission
+ * the red edge of the bin's overlap with the band (the ray tests the lines at
+ * or below it), for line emission the reddest line in the bin (the ray starts
+ * past it, as a line-emitted packet does).  Bins are the output grid's
+ * lam0 (1 + dlog)^j.  Returns -1 if an emitting line lies outside the grid. */
+static int rays_prep(prep_t *P) {
+    const xo_problem *pb = P->pb;
+    const xo_params *pr = P->pr;
+    int32_t nb = pr->spec_nbins;
+    P->rcell = malloc(sizeof(int64_t) * (size_t)(P->ncell > 0 ? P->ncell : 1));
+    P->n_rcell = 0;
+    for (int64_t c = 0; c < P->ncell; c++)
+        if (P->Lc[c] > 0.0) P->rcell[P->n_rcell++] = c;
+    P->rbin_nu = malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+    P->rbin_cursor = malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+    P->rbin_frac = calloc((size_t)(nb > 0 ? nb : 1), sizeof(double));
+    P->n_rbin = 0;
+    if (pr->emission_mode == 0) {
+        double nu_lo = XO_C / (pb->band_hi_A * 1e-8), nu_hi = XO_C / (pb->band_lo_A * 1e-8);
+        for (int32_t j = 0; j < nb; j++) {
+            double l0 = pr->spec_lam0_A * pow(1.0 + pr->spec_dlog, (double)j);
+            double l1 = pr->spec_lam0_A * pow(1.0 + pr->spec_dlog, (double)(j + 1));
+            double a = l0 > pb->band_lo_A ? l0 : pb->band_lo_A;
+            double b = l1 < pb->band_hi_A ? l1 : pb->band_hi_A;
+            if (!(b > a)) continue;
+            double nu_red = XO_C / (b * 1e-8), nu_blue = XO_C / (a * 1e-8);
+            int32_t k = P->n_rbin++;
+            P->rbin_nu[k] = nu_red;
+            P->rbin_cursor[k] = cursor_at(P, nu_red);
+            P->rbin_frac[k] = (nu_blue - nu_red) / (nu_hi - nu_lo);
+        }
+    } else {
+        int32_t nl = pb->nline;
+        int32_t *bin_of = malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+        int32_t *cnt = calloc((size_t)nb + 1, sizeof(int32_t));
+        for (int32_t l = 0; l < nl; l++) {
+            int64_t j = xo_lambda_bin(pb->lambda_A[l], pr->spec_lam0_A, pr->spec_dlog, nb);
+            if (j < 0) { free(bin_of); free(cnt); return -1; }
+            bin_of[l] = (int32_t)j;
+            cnt[j + 1]++;
+        }
+        int32_t *jmap = malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+        for (int32_t j = 0; j < nb; j++) jmap[j] = cnt[j + 1] > 0 ? P->n_rbin++ : -1;
+        P->rbin_off = calloc((size_t)P->n_rbin + 1, sizeof(int32_t));
+        P->rbin_line = malloc(sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1));
+        for (int32_t l = 0; l < nl; l++) P->rbin_off[jmap[bin_of[l]] + 1]++;
+        for (int32_t k = 0; k < P->n_rbin; k++) P->rbin_off[k + 1] += P->rbin_off[k];
+        int32_t *fill = calloc((size_t)P->n_rbin + 1, sizeof(int32_t));
+        for (int32_t l = 0; l < nl; l++) {
+            int32_t k = jmap[bin_of[l]];
+            P->rbin_line[P->rbin_off[k] + fill[k]++] = l;
+        }
+        for (int32_t k = 0; k < P->n_rbin; k++) {
+            /* reddest line of the bin; equal frequencies: start past the last of them */
+            int32_t best = -1;
+            for (int32_t q = P->rbin_off[k]; q < P->rbin_off[k + 1]; q++) {
+                int32_t s = P->pos[P->rbin_line[q]];
+                if (best < 0 || s > best) best = s;
+            }
+            P->rbin_nu[k] = P->nu[best];
+            P->rbin_cursor[k] = best + 1;
+        }
+        free(bin_of); free(cnt); free(jmap); free(fill);
+    }
+    int32_t nv = pr->n_theta * pr->n_phi;
+    P->view_n = malloc(sizeof(double) * 3 * (size_t)nv);
+    P->view_w = malloc(sizeof(double) * (size_t)nv);
+    for (int32_t it = 0; it < pr->n_theta; it++)
+        for (int32_t ip = 0; ip < pr->n_phi; ip++) {
+            int32_t k = it * pr->n_phi + ip;
+            double th = XO_PI * (it + 0.5) / pr->n_theta, ph = 2.0 * XO_PI * (ip + 0.5) / pr->n_phi;
+            double th0 = XO_PI * it / pr->n_theta, th1 = XO_PI * (it + 1) / pr->n_theta;
+            P->view_n[3 * k] = sin(th) * cos(ph);
+            P->view_n[3 * k + 1] = sin(th) * sin(ph);
+            P->view_n[3 * k + 2] = cos(th);
+            P->view_w[k] = (2.0 * XO_PI / pr->n_phi) * (cos(th0) - cos(th1)) / (4.0 * XO_PI);
+        }
+    return 0;
 }
 
 static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -401,6 +504,10 @@ static void add_estimator(double *S, int64_t cell, int32_t nline, int32_t l, dou
  * final nu_lab */
 #define XO_PKT_FIELDS 11
 
+static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], double r[3], double n[3],
+                      double nu_cmf, int32_t cursor, double E0, double *S, double *spec,
+                      double *ledger, double *pkt, double *S_pi, double *heat);
+
 static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec,
                              double *ledger, double *pkt, double *S_pi, double *heat) {
     const xo_problem *pb = P->pb;
@@ -413,7 +520,7 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
     draw4(pr->seed, p, 0, u);
     draw4(pr->seed, p, 1, v);
     double d[3] = {P->dx, P->dy, P->dz};
-    int32_t idx[3] = {ix, iy, iz}, nn[3] = {pb->nx, pb->ny, pb->nz};
+    int32_t idx[3] = {ix, iy, iz};
     double r[3];
     for (int a = 0; a < 3; a++) r[a] = (-P->R + idx[a] * d[a]) + u[a] * d[a];
     double n[3];
@@ -435,6 +542,56 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
         nu_cmf = XO_C / (pb->lambda_A[pick] * 1e-8);
         cursor = P->pos[pick] + 1;           /* start past the emitting line */
     }
+    propagate(P, p, c, idx, r, n, nu_cmf, cursor, E0, S, spec, ledger, pkt, S_pi, heat);
+}
+
+/* Ray r of the RAYS sampler: r = (cell rank, bin rank, viewer) in row-major
+ * order over the emitting cells, the emitting bins and the viewers.  A ray
+ * whose cell has no emission in its bin is empty: fate 4, nothing traced. */
+static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, double *ledger,
+                          double *pkt, double *S_pi, double *heat) {
+    const xo_problem *pb = P->pb;
+    const xo_params *pr = P->pr;
+    int64_t nv = (int64_t)pr->n_theta * pr->n_phi;
+    int64_t ci = r / ((int64_t)P->n_rbin * nv), rem = r - ci * (int64_t)P->n_rbin * nv;
+    int32_t jb = (int32_t)(rem / nv), k = (int32_t)(rem - (int64_t)jb * nv);
+    int64_t c = P->rcell[ci];
+    double E_bin;
+    if (pr->emission_mode == 0) {
+        E_bin = P->Lc[c] * P->rbin_frac[jb];
+    } else {
+        E_bin = 0.0;
+        for (int32_t q = P->rbin_off[jb]; q < P->rbin_off[jb + 1]; q++)
+            E_bin += P->wline[c * pb->nline + P->rbin_line[q]];
+    }
+    double E0 = E_bin * P->view_w[k];
+    if (!(E0 > 0.0)) {
+        if (pkt) {
+            memset(pkt, 0, sizeof(double) * XO_PKT_FIELDS);
+            pkt[0] = 4; pkt[4] = -1; pkt[5] = -1; pkt[7] = (double)c;
+        }
+        return;
+    }
+    int32_t idx[3] = {(int32_t)(c % pb->nx), (int32_t)((c / pb->nx) % pb->ny), (int32_t)(c / ((int64_t)pb->nx * pb->ny))};
+    double d[3] = {P->dx, P->dy, P->dz};
+    double rr[3], n[3];
+    for (int a = 0; a < 3; a++) {
+        rr[a] = (-P->R + idx[a] * d[a]) + 0.5 * d[a];     /* the middle of the cell */
+        n[a] = P->view_n[3 * k + a];
+    }
+    propagate(P, r, c, idx, rr, n, P->rbin_nu[jb], P->rbin_cursor[jb], E0, S, spec, ledger, pkt, S_pi, heat);
+}
+
+/* The event loop of one packet or ray from its emission (Secs. 2.3, 2.3.2):
+ * cell idx (natural index c), position r, direction n, comoving frequency
+ * nu_cmf, first line to test `cursor`, energy E0 (erg/s). */
+static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], double r[3], double n[3],
+                      double nu_cmf, int32_t cursor, double E0, double *S, double *spec,
+                      double *ledger, double *pkt, double *S_pi, double *heat) {
+    const xo_problem *pb = P->pb;
+    const xo_params *pr = P->pr;
+    double d[3] = {P->dx, P->dy, P->dz};
+    int32_t nn[3] = {pb->nx, pb->ny, pb->nz};
     double ct = P->ct;
     double nu_lab = nu_cmf / (1.0 - dot3(n, r) / ct);
     double N = E0 / (XO_H * nu_cmf);
@@ -601,13 +758,27 @@ int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *s
     prep_t P;
     g_rec = rec; g_rec_cap = rec_cap; g_rec_n = 0;
     prep(&P, pb, pr);
-    for (int64_t p = pr->p_begin; p < pr->p_end; p++)
-        transport_packet(&P, p, S, spec, ledger, pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL,
-                         S_pi, heat);
+    if (pr->sampler == 1 && rays_prep(&P) != 0) { unprep(&P); g_rec = NULL; return -2; }
+    for (int64_t p = pr->p_begin; p < pr->p_end; p++) {
+        double *pk = pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL;
+        if (pr->sampler == 1) transport_ray(&P, p, S, spec, ledger, pk, S_pi, heat);
+        else transport_packet(&P, p, S, spec, ledger, pk, S_pi, heat);
+    }
     unprep(&P);
     if (rec_n) *rec_n = g_rec_n;
     g_rec = NULL;
     return (rec && g_rec_n > rec_cap) ? -1 : 0;
+}
+
+/* Number of rays of the RAYS sampler (emitting cells x emitting bins x
+ * viewers), or -1 if an emitting line lies outside the output grid. */
+int64_t xo_ray_count(const xo_problem *pb, const xo_params *pr) {
+    prep_t P;
+    prep(&P, pb, pr);
+    int64_t n = -1;
+    if (rays_prep(&P) == 0) n = P.n_rcell * (int64_t)P.n_rbin * pr->n_theta * pr->n_phi;
+    unprep(&P);
+    return n;
 }
 
 /* Per-cell luminosity and packet quota as the transport sees them. */

@@ -23,6 +23,7 @@ XT_MODE_ATTEN, XT_MODE_SCATTER = 0, 1
 XT_EMIT_BAND, XT_EMIT_LINES = 0, 1
 XT_PKT_FIELDS = 11
 XT_FLAG_NO_WARP_REDUCE = 1
+XT_SAMPLER_MC, XT_SAMPLER_RAYS = 0, 1
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
               "N0", "nu_cmf0", "nu_lab"]
 
@@ -59,13 +60,14 @@ class TransportParams(C.Structure):
                 ("spec_lam0_A", C.c_double), ("spec_dlog", C.c_double),
                 ("spec_nbins", C.c_int32), ("accumulate", C.c_int32),
                 ("max_events", C.c_int64), ("subdomain_rounds", C.c_int32), ("flags", C.c_int32),
-                ("packet_records", C.c_void_p)]
+                ("packet_records", C.c_void_p), ("sampler", C.c_int32)]
 
 
 STATS_FIELDS = ["emitted_N", "escaped_N", "absorbed_N", "dropped_N", "emitted_E", "escaped_E",
                 "out_of_band_E", "events", "tests", "guard", "thermal_E", "interactions",
                 "abs_E_cmf", "reemit_E_cmf", "transport_ms", "zero_ms", "rounds", "queued",
-                "emit_ms", "trace_ms", "escape_ms", "kernels", "photoionized_N", "photoionized_E"]
+                "emit_ms", "trace_ms", "escape_ms", "kernels", "photoionized_N", "photoionized_E",
+                "rays"]
 
 
 class TransportStats(C.Structure):
@@ -315,14 +317,21 @@ def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=
                   emission=XT_EMIT_BAND, tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
                   spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1, accumulate=False,
                   max_events=1_000_000, subdomain_rounds=False, packet_records=None, check=True,
-                  flags=0):
+                  flags=0, sampler=XT_SAMPLER_MC):
+    def params(count, rec):
+        return TransportParams(int(n_packets), int(packet_begin), int(count), int(seed), int(mode),
+                               int(emission), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
+                               int(spec_nbins), int(bool(accumulate)), int(max_events),
+                               int(bool(subdomain_rounds)), int(flags), _ptr(rec), int(sampler))
     if packet_records is not None:
-        _check_records(packet_records, int(n_packets) - int(packet_begin) if packet_count < 0
+        total = int(n_packets)
+        if sampler == XT_SAMPLER_RAYS and packet_count < 0:      # the number of rays first
+            st0 = TransportStats()
+            _check(ctx, lib().run_transport(ctx, C.byref(params(0, None)), C.byref(st0)))
+            total = int(st0.rays)
+        _check_records(packet_records, total - int(packet_begin) if packet_count < 0
                        else int(packet_count))
-    p = TransportParams(int(n_packets), int(packet_begin), int(packet_count), int(seed), int(mode),
-                        int(emission), tau_min, e_cut, n_theta, n_phi, spec_lam0_A, spec_dlog,
-                        int(spec_nbins), int(bool(accumulate)), int(max_events), int(bool(subdomain_rounds)),
-                        int(flags), _ptr(packet_records))
+    p = params(packet_count, packet_records)
     st = TransportStats()
     rc = lib().run_transport(ctx, C.byref(p), C.byref(st))
     if check:
@@ -427,7 +436,7 @@ def run_coupled(ctx, upsilon, n_packets, seed=0, start=XT_WARM_LTE, start_in=Non
     si = _f64(start_in) if start_in is not None else None
     tp = TransportParams(int(n_packets), 0, -1, int(seed), XT_MODE_ATTEN, int(emission), tau_min, e_cut,
                          20, 20, spec_lam0_A, spec_dlog, int(spec_nbins), 0, int(max_events),
-                         int(bool(subdomain_rounds)), 0, None)
+                         int(bool(subdomain_rounds)), 0, None, XT_SAMPLER_MC)
     np_ = NlteParams(int(precision), XT_RATES_ESTIMATORS, XT_WARM_CURRENT, int(max_iter), float(ir_tol),
                      float(jbar_W), float(jbar_TR), float(eta_nt), _ptr(lu), None, _ptr(ups),
                      int(bool(use_graph)), 0, int(newton_max), float(newton_tol), float(newton_maxvar))

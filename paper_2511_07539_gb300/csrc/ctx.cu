@@ -309,7 +309,7 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n,
                    (void**)&c->d_pi_nuth, (void**)&c->d_pi_sig, (void**)&c->d_pi_chi, (void**)&c->d_pi_lev,
                    (void**)&c->d_pi_sorted_of, (void**)&c->d_kappa, (void**)&c->d_piG, (void**)&c->d_piD,
-                   (void**)&c->d_piH};
+                   (void**)&c->d_piH, (void**)&c->d_rays};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;
@@ -517,6 +517,8 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   std::vector<int> fill(nlev, 0);
   for (int l = 0; l < nl; ++l) dline[doff[up[l]] + fill[up[l]]++] = c->h_sorted_of[l];
   c->n_ion = a->n_ion; c->nlev = nlev; c->nline = nl;
+  c->h_nu_sorted = s_nu;
+  c->h_lam_caller = lam;
   c->h_level_off = off; c->h_g = g; c->h_E = E;
   if ((rc = to_device(c, off, &c->d_level_off, "level_off"))) return rc;
   if ((rc = to_device(c, g, &c->d_g, "g"))) return rc;

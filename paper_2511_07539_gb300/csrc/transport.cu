@@ -68,6 +68,18 @@ constexpr int kQGuideShift = 6;
 constexpr int kNuGuideShift = 37;                 // 2^16 buckets of the 53-bit uniform
 constexpr int kNuGuideN = (1 << (53 - kNuGuideShift)) + 1;
 
+// The RAYS sampler's tables (Sec. 2.3): ray r = (emitting-cell rank, emitting
+// bin rank, viewer) in row-major order.
+struct RayTables {
+  int64_t nbin, nview;
+  const int* __restrict__ rcell;       // natural index of each emitting cell
+  const double* __restrict__ bin_nu;   // [nbin] comoving start frequency (the bin's reddest feature)
+  const int* __restrict__ bin_cursor;  // [nbin] first line its rays test
+  const double* __restrict__ bin_frac; // band: [nbin] the bin's share of the band
+  const double* __restrict__ Ebin;     // lines: [row][nbin] the cell's emission in the bin
+  const double* __restrict__ view;     // [nview][4] direction of the viewer's centre, dOmega / 4 pi
+};
+
 struct EmitArgs {
   Geometry g;
   const int64_t* __restrict__ qoff;   // natural [ncell+1]
@@ -89,6 +101,8 @@ struct EmitArgs {
   double* __restrict__ records;       // record of packet p at (p - rec_base)
   int64_t rec_base;
   FixTrigTables trig;
+  int rays;                           // the RAYS sampler instead of Monte Carlo packets
+  RayTables ray;
 };
 
 struct TraceArgs {
@@ -288,6 +302,56 @@ struct EmitOut {
   double E0, r[3], n[3], nu_cmf, nu_lab, N, tm[3], td[3];
   int cursor;
 };
+
+// Ray r of the RAYS sampler (Sec. 2.3): from the middle of its cell along its
+// viewer's centre direction, at its bin's start frequency, with the bin's
+// emission times dOmega_k / 4 pi.  E0 = 0 marks an empty ray (the cell has no
+// emission in the bin), which is not traced.  The walls are half a cell away.
+__device__ __forceinline__ void emit_ray(const EmitArgs& a, int64_t rid, EmitOut& o) {
+  const Geometry& g = a.g;
+  const RayTables& T = a.ray;
+  const int64_t per_cell = T.nbin * T.nview;
+  const int64_t ci = rid / per_cell;
+  const int64_t rem = rid - ci * per_cell;
+  const int64_t jb = rem / T.nview;
+  const int k = (int)(rem - jb * T.nview);
+  const int64_t c = T.rcell[ci];
+  o.c = c;
+  {
+    const uint32_t c32 = (uint32_t)c, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+    const uint32_t cy = c32 / nx;
+    o.idx[0] = (int)(c32 - cy * nx); o.idx[1] = (int)(cy % ny); o.idx[2] = (int)(cy / ny);
+  }
+  const double2 v01 = __ldg(reinterpret_cast<const double2*>(T.view) + 2 * k);
+  const double2 v23 = __ldg(reinterpret_cast<const double2*>(T.view) + 2 * k + 1);
+  const double E_bin = T.Ebin ? T.Ebin[row_of(g, o.idx[0], o.idx[1], o.idx[2]) * T.nbin + jb]
+                              : a.Lc[c] * T.bin_frac[jb];
+  o.E0 = E_bin * v23.y;
+  if (!(o.E0 > 0.0)) return;
+  const double d[3] = {g.dx, g.dy, g.dz};
+  o.n[0] = v01.x; o.n[1] = v01.y; o.n[2] = v23.x;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)   // (-R + i d) + d / 2, rounded step by step
+    o.r[q] = __dadd_rn(__dadd_rn(-g.R, __dmul_rn((double)o.idx[q], d[q])), 0.5 * d[q]);
+  o.nu_cmf = T.bin_nu[jb];
+  o.cursor = T.bin_cursor[jb];
+  const double* n = o.n;
+  const double* r = o.r;
+  o.nu_lab = div_pos(o.nu_cmf, 1.0 - (n[0] * r[0] + n[1] * r[1] + n[2] * r[2]) * g.inv_ct);
+  o.N = div_pos(o.E0, kH * o.nu_cmf);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const long long nb = __double_as_longlong(n[q]);
+    if ((nb << 1) != 0) {
+      const double t = div_pos(d[q], __longlong_as_double(nb & 0x7FFFFFFFFFFFFFFFll));
+      o.tm[q] = 0.5 * t;
+      o.td[q] = nb > 0 ? t : neg_bits(t);
+    } else {
+      o.tm[q] = INFINITY;
+      o.td[q] = INFINITY;
+    }
+  }
+}
 
 __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTables& trig, int64_t p,
                                             EmitOut& o) {
@@ -503,7 +567,7 @@ constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yi
 constexpr int kRefillLanes = 24;  // empty lanes of a warp that trigger a refill with emission
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
-template <int MODE, bool PI = false>
+template <int MODE, bool PI = false, bool RAYS = false>
 __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
@@ -578,7 +642,16 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
             i = (int)my;
             const int64_t p = a.em.p_begin + (int64_t)my;
             EmitOut o;
-            emit_packet(a.em, trig, p, o);
+            if constexpr (RAYS) emit_ray(a.em, p, o);
+            else emit_packet(a.em, trig, p, o);
+            if (RAYS && !(o.E0 > 0.0)) {           // an empty ray: recorded, not traced
+              if (a.records) {
+                double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+                rec[0] = 4.0; rec[1] = 0.0; rec[2] = 0.0; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+                rec[6] = 0.0; rec[7] = (double)o.c; rec[8] = 0.0; rec[9] = 0.0; rec[10] = 0.0;
+              }
+              continue;
+            }
             ix = o.idx[0]; iy = o.idx[1]; iz = o.idx[2];
             tmx = o.tm[0]; tmy = o.tm[1]; tmz = o.tm[2];
             sx = bits(o.td[0]) < 0 ? -1 : 1; sy = bits(o.td[1]) < 0 ? -1 : 1; sz = bits(o.td[2]) < 0 ? -1 : 1;
@@ -587,7 +660,8 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
             aslope = o.nu_lab * a.inv_ct;
             N = o.N;
             N_in = N;
-            Tq = a.em.e_cut * a.em.Eph[o.c];
+            if constexpr (RAYS) Tq = (a.em.e_cut * o.E0) * (1.0 / kH);
+            else Tq = a.em.e_cut * a.em.Eph[o.c];
             cursor = o.cursor;
             events = 0;
             if constexpr (PI) {
@@ -999,6 +1073,35 @@ __global__ void k_pi_kappa(int64_t nrows, int npi, int nlev, const double* __res
   }
 }
 
+// The RAYS sampler with line emission: per cell the emission of every line,
+// A_ul h nu beta_S N_u (Eq. thin_emissivity), summed into the cell's
+// wavelength bins (caller line order, so each bin's sum runs in ascending
+// line index) and in total (Lc, natural order).
+__global__ void k_ray_line_bins(Geometry g, const double2* __restrict__ lines, const double* __restrict__ A,
+                                int nline, int nlev, const double* __restrict__ pops,
+                                const int* __restrict__ sorted_of, const int* __restrict__ bin_of_line,
+                                int64_t nbin, double V, double* __restrict__ Ebin, double* __restrict__ Lc) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
+    const int64_t row = row_of(g, ix, iy, iz);
+    const double* pc = pops + row * nlev;
+    double* er = Ebin + row * nbin;
+    for (int64_t j = 0; j < nbin; ++j) er[j] = 0.0;
+    double run = 0.0;
+    for (int l = 0; l < nline; ++l) {
+      const int s = sorted_of[l];
+      const LineRec L = ldline(lines, s);
+      const double nu_ = pc[__double2hiint(L.w)];
+      const double tau = L.y * (pc[__double2loint(L.w)] - L.z * nu_);
+      const double w = A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * V;
+      run += w;
+      er[bin_of_line[l]] += w;
+    }
+    Lc[c] = run;
+  }
+}
+
 static int sm_count() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -1035,15 +1138,159 @@ static int ensure_buffers(xt_ctx* c, int64_t cap, int nsd) {
   return XT_OK;
 }
 
+// Tables of the RAYS sampler (Sec. 2.3) for this pass: emitting cells, the
+// emitting bins of the output grid with their start frequency and first line,
+// the band share of each bin or the cells' emission per bin (line emission),
+// the viewers' centre directions and solid-angle shares.  Returns the number
+// of rays in *n_rays.
+static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, const double*& Lc_nat,
+                      int64_t* n_rays) {
+  const Geometry& G = c->geo;
+  const int nb = p->spec_nbins;
+  const double lam0 = p->spec_lam0_A, dlog = p->spec_dlog;
+  const int nl = c->nline;
+  std::vector<double> bnu, bfrac;
+  std::vector<int> bcur, bin_of_line;
+  const std::vector<double>& snu = c->h_nu_sorted;
+  auto cursor_at = [&](double nu) {      // first sorted line with nu <= the given one
+    int lo = 0, hi = nl;
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (snu[mid] <= nu) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  };
+  if (p->emission == XT_EMIT_BAND) {
+    const double nu_lo = kC / (c->band_hi_A * 1e-8), nu_hi = kC / (c->band_lo_A * 1e-8);
+    for (int j = 0; j < nb; ++j) {
+      const double l0 = lam0 * std::pow(1.0 + dlog, (double)j);
+      const double l1 = lam0 * std::pow(1.0 + dlog, (double)(j + 1));
+      const double a = l0 > c->band_lo_A ? l0 : c->band_lo_A;
+      const double b = l1 < c->band_hi_A ? l1 : c->band_hi_A;
+      if (!(b > a)) continue;
+      const double nu_red = kC / (b * 1e-8), nu_blue = kC / (a * 1e-8);
+      bnu.push_back(nu_red);
+      bcur.push_back(cursor_at(nu_red));
+      bfrac.push_back((nu_blue - nu_red) / (nu_hi - nu_lo));
+    }
+  } else {
+    std::vector<int> jmap(nb, -1), best(nb, -1), bin_j(nl);
+    for (int l = 0; l < nl; ++l) {
+      const double la = c->h_lam_caller[l];
+      int64_t j = -1;
+      if (la >= lam0) {
+        const double k = std::floor(std::log(la / lam0) / std::log1p(dlog));
+        if (k < (double)nb) j = (int64_t)k;
+      }
+      if (j < 0) return fail(c, XT_EINVAL, "run_transport: line " + std::to_string(l) +
+                                               " lies outside the output grid (RAYS sampler, line emission)");
+      bin_j[l] = (int)j;
+      const int s = c->h_sorted_of[l];
+      if (best[j] < 0 || s > best[j]) best[j] = s;
+    }
+    int nbin = 0;
+    for (int j = 0; j < nb; ++j)
+      if (best[j] >= 0) {
+        jmap[j] = nbin++;
+        bnu.push_back(snu[best[j]]);
+        bcur.push_back(best[j] + 1);
+      }
+    bin_of_line.resize(nl);
+    for (int l = 0; l < nl; ++l) bin_of_line[l] = jmap[bin_j[l]];
+  }
+  const int64_t nbin = (int64_t)bnu.size();
+  const int nview = p->n_theta * p->n_phi;
+  std::vector<double> view(4 * (size_t)nview);
+  for (int it = 0; it < p->n_theta; ++it)
+    for (int ip = 0; ip < p->n_phi; ++ip) {
+      const int k = it * p->n_phi + ip;
+      const double th = kPi * (it + 0.5) / p->n_theta, ph = 2.0 * kPi * (ip + 0.5) / p->n_phi;
+      const double th0 = kPi * it / p->n_theta, th1 = kPi * (it + 1) / p->n_theta;
+      view[4 * k] = std::sin(th) * std::cos(ph);
+      view[4 * k + 1] = std::sin(th) * std::sin(ph);
+      view[4 * k + 2] = std::cos(th);
+      view[4 * k + 3] = (2.0 * kPi / p->n_phi) * (std::cos(th0) - std::cos(th1)) / (4.0 * kPi);
+    }
+  // one device allocation, carved: view | bin_nu | bin_frac | Lc | Ebin | bin_cursor | bin_of_line | rcell
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const bool lines = p->emission == XT_EMIT_LINES;
+  const size_t o_view = 0, o_nu = al(o_view + 32 * (size_t)nview), o_frac = al(o_nu + 8 * nbin);
+  const size_t o_Lc = al(o_frac + 8 * nbin), o_E = al(o_Lc + 8 * (size_t)G.ncell);
+  const size_t o_cur = al(o_E + (lines ? 8 * (size_t)G.ncell * nbin : 0));
+  const size_t o_bol = al(o_cur + 4 * nbin), o_rc = al(o_bol + 4 * (size_t)nl);
+  const size_t total = al(o_rc + 4 * (size_t)G.ncell);
+  int rc;
+  if (c->rays_bytes < total) {
+    c->rays_bytes = 0;
+    if ((rc = alloc(c, &c->d_rays, total, "ray tables"))) return rc;
+    c->rays_bytes = total;
+  }
+  char* B = (char*)c->d_rays;
+  if ((rc = copy(c, B + o_view, view.data(), view.size() * 8, "ray tables"))) return rc;
+  if (nbin > 0) {
+    if ((rc = copy(c, B + o_nu, bnu.data(), 8 * nbin, "ray tables"))) return rc;
+    if ((rc = copy(c, B + o_cur, bcur.data(), 4 * nbin, "ray tables"))) return rc;
+    if (!lines && (rc = copy(c, B + o_frac, bfrac.data(), 8 * nbin, "ray tables"))) return rc;
+  }
+  std::vector<double> Lnat;
+  if (lines) {
+    if ((rc = copy(c, B + o_bol, bin_of_line.data(), 4 * (size_t)nl, "ray tables"))) return rc;
+    k_ray_line_bins<<<blocks_for(G.ncell, 128, 16), 128, 0, c->stream>>>(
+        G, (const double2*)c->d_lines, c->d_A, nl, c->nlev, c->d_pops, c->d_orig, (const int*)(B + o_bol),
+        nbin, G.dx * G.dy * G.dz, (double*)(B + o_E), (double*)(B + o_Lc));
+    XT_CUDA(c, cudaGetLastError());
+    Lnat.resize(G.ncell);
+    XT_CUDA(c, cudaMemcpyAsync(Lnat.data(), B + o_Lc, G.ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else {
+    Lnat = c->h_L;
+    if ((rc = copy(c, B + o_Lc, Lnat.data(), G.ncell * sizeof(double), "ray tables"))) return rc;
+  }
+  std::vector<int> rcell;
+  for (int64_t k = 0; k < G.ncell; ++k)
+    if (Lnat[k] > 0.0) rcell.push_back((int)k);
+  if (!rcell.empty() && (rc = copy(c, B + o_rc, rcell.data(), 4 * rcell.size(), "ray tables"))) return rc;
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
+  T.nbin = nbin;
+  T.nview = nview;
+  T.rcell = (const int*)(B + o_rc);
+  T.bin_nu = (const double*)(B + o_nu);
+  T.bin_cursor = (const int*)(B + o_cur);
+  T.bin_frac = (const double*)(B + o_frac);
+  T.Ebin = lines ? (const double*)(B + o_E) : nullptr;
+  T.view = (const double*)(B + o_view);
+  Lc_nat = (const double*)(B + o_Lc);
+  *n_rays = (int64_t)rcell.size() * nbin * nview;
+  return XT_OK;
+}
+
 extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transport_stats* out) {
   if (!c || !p) return fail(c, XT_EINVAL, "run_transport: null argument");
   if (!c->have_pops) return fail(c, XT_ESTATE, "run_transport: set_populations first");
   cudaSetDevice(c->device);
   const Geometry& G = c->geo;
+  const bool rays = p->sampler == XT_SAMPLER_RAYS;
+  if (p->sampler != XT_SAMPLER_MC && !rays) return fail(c, XT_EINVAL, "run_transport: sampler");
+  if (rays && (p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0))
+    return fail(c, XT_EINVAL, "run_transport: the RAYS sampler runs in attenuation mode without subdomain "
+                              "rounds, with the estimator store on the device");
   if (p->n_packets < 0) return fail(c, XT_EINVAL, "run_transport: n_packets < 0");
-  const int64_t count = p->packet_count < 0 ? p->n_packets - p->packet_begin : p->packet_count;
-  if (p->packet_begin < 0 || count < 0 || p->packet_begin + count > p->n_packets)
-    return fail(c, XT_EINVAL, "run_transport: packet range outside [0, n_packets)");
+  if (p->n_theta < 1 || p->n_phi < 1 || p->spec_nbins < 1 || !(p->spec_lam0_A > 0) || !(p->spec_dlog > 0))
+    return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
+  if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
+  RayTables rtab_rays{};
+  const double* ray_Lc = nullptr;
+  int64_t n_total = p->n_packets;
+  if (rays) {
+    if (c->nline < 1) return fail(c, XT_ESTATE, "run_transport: no lines loaded");
+    if (p->emission == XT_EMIT_BAND && !c->d_L) return fail(c, XT_ESTATE, "run_transport: band emission needs L_cell in init_grid");
+    int rcr = build_rays(c, p, rtab_rays, ray_Lc, &n_total);
+    if (rcr) return rcr;
+  }
+  const int64_t count = p->packet_count < 0 ? n_total - p->packet_begin : p->packet_count;
+  if (p->packet_begin < 0 || count < 0 || p->packet_begin + count > n_total)
+    return fail(c, XT_EINVAL, rays ? "run_transport: ray range outside [0, rays)"
+                                   : "run_transport: packet range outside [0, n_packets)");
   if (p->mode != XT_MODE_ATTEN && p->mode != XT_MODE_SCATTER) return fail(c, XT_EINVAL, "run_transport: mode");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
   if (p->emission == XT_EMIT_BAND && !c->d_L) return fail(c, XT_ESTATE, "run_transport: band emission needs L_cell in init_grid");
@@ -1110,7 +1357,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     XT_CUDA(c, cudaMemsetAsync(c->d_spec, 0, spec_b, c->stream));
   }
   // emission: cell luminosities, packet quota, packet energy per cell
-  if (c->qoff_N != p->n_packets || c->qoff_mode != p->emission) {
+  if (!rays && (c->qoff_N != p->n_packets || c->qoff_mode != p->emission)) {
     std::vector<double> Lnat;
     if (c->Lc_n != G.ncell) {
       c->Lc_n = 0;
@@ -1237,7 +1484,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   c->have_pi = pi;
 
   int occ = 0;
-  if (p->mode == XT_MODE_ATTEN && pi)
+  if (rays && pi)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true, true>, 256, 0);
+  else if (rays)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, false, true>, 256, 0);
+  else if (p->mode == XT_MODE_ATTEN && pi)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true>, 256, 0);
   else if (p->mode == XT_MODE_ATTEN)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN>, 256, 0);
@@ -1316,6 +1567,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     if ((rc = copy(c, c->d_wall, wl.data(), wl.size() * sizeof(double), "wall table"))) return rc;
   }
   ea.wall = c->d_wall;
+  ea.rays = rays ? 1 : 0;
+  ea.ray = rtab_rays;
+  if (rays) ea.Lc = ray_Lc;
   ea.e_cut = p->e_cut; ea.pool = P; ea.ledger = c->d_ledger; ea.records = d_rec;
   ea.rec_base = p->packet_begin;
   fixtrig_tables(&ea.trig);
@@ -1493,7 +1747,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+      if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (rays) k_trace<XT_MODE_ATTEN, false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
       XT_CUDA(c, cudaGetLastError());
@@ -1559,6 +1815,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     for (int k = 0; k < LG_STATS; ++k) o[k] = led[k];
     out->photoionized_N = led[LG_PI_N];
     out->photoionized_E = kH * led[LG_PI_E];
+    out->rays = rays ? (double)n_total : 0.0;
     float ms_all = 0, ms_clear = 0;
     cudaEventElapsedTime(&ms_all, c->ev0, c->ev2);
     cudaEventElapsedTime(&ms_clear, c->ev0, c->ev1);

@@ -85,6 +85,8 @@ struct xt_ctx {
   std::vector<double> h_g, h_E;
   std::vector<int> h_sorted_of;      // caller line -> sorted position
   std::vector<int> h_orig_of;        // sorted position -> caller line
+  std::vector<double> h_nu_sorted;   // line frequencies, sorted (descending)
+  std::vector<double> h_lam_caller;  // line wavelengths (A), caller order
   int* d_level_off = nullptr;
   double* d_g = nullptr;
   double* d_E = nullptr;
@@ -110,6 +112,8 @@ struct xt_ctx {
   int64_t pi_rows = 0;               // rows the per-cell photoionization arrays hold
   int pi_npi = 0;                    //   for this many levels
   bool have_pi = false;              // the last pass photoionized
+  void* d_rays = nullptr;            // the RAYS sampler's tables (one allocation, carved)
+  size_t rays_bytes = 0;
   // state
   bool have_pops = false;
   double* d_pops = nullptr;          // [row][nlev]
