@@ -74,9 +74,10 @@ def solve_all(w, R_lu, eta=0.5, newton=False, newton_tol=1e-6):
 
 
 def outer_step(w, n_packets=None, seed=None, alpha=1.0, eta=0.5, tau_min=1e-4, emission="band",
-               newton=True, newton_tol=1e-6):
+               newton=True, newton_tol=1e-6, sampler="mc", n_theta=20, n_phi=20, spec_dlog=1e-3):
     """One outer step from w.pops; returns (relaxed populations, solved s_k)."""
-    o = transport(w, n_packets=n_packets, seed=seed, emission=emission, tau_min=tau_min)
+    o = transport(w, n_packets=n_packets, seed=seed, emission=emission, tau_min=tau_min,
+                  sampler=sampler, n_theta=n_theta, n_phi=n_phi, spec_dlog=spec_dlog)
     R_lu = rates(w, o["S"])[0]
     s = solve_all(w, R_lu, eta=eta, newton=newton, newton_tol=newton_tol)
     return relax(w.pops, s, alpha), s
@@ -84,14 +85,17 @@ def outer_step(w, n_packets=None, seed=None, alpha=1.0, eta=0.5, tau_min=1e-4, e
 
 def coupled_loop(w, n_packets=None, seed=None, alpha=1.0, tol=1e-3, floor=1e-20,
                  max_outer=60, eta=0.5, tau_min=1e-4, emission="band", newton=True,
-                 newton_tol=1e-6):
+                 newton_tol=1e-6, sampler="mc", n_theta=20, n_phi=20, spec_dlog=1e-3):
     """Runs outer steps from w.pops until the change is <= tol.  Returns
-    (populations, steps, history of changes); steps = -1 if max_outer ran out."""
+    (populations, steps, history of changes); steps = -1 if max_outer ran out.
+    emission="lines" with sampler="rays" is the paper's loop: the lines emit
+    from the current populations (Eq. thin_emissivity), traced as the paper's
+    rays (Sec. 2.3), so that a step is a smooth map of the populations."""
     w = copy.copy(w)
     hist = []
     for k in range(max_outer):
         n_new, _ = outer_step(w, n_packets, seed, alpha, eta, tau_min, emission, newton,
-                              newton_tol)
+                              newton_tol, sampler, n_theta, n_phi, spec_dlog)
         ch = max_change(w.pops, n_new, w, floor)
         hist.append(ch)
         w.pops = n_new

@@ -427,16 +427,19 @@ def run_coupled(ctx, upsilon, n_packets, seed=0, start=XT_WARM_LTE, start_in=Non
                 newton_tol=1e-6, newton_maxvar=10.0, max_iter=8, ir_tol=1e-10, jbar_W=0.0,
                 jbar_TR=0.0, eta_nt=0.5, levels_used=None, use_graph=False, emission=XT_EMIT_BAND,
                 tau_min=1e-4, e_cut=1e-6, spec_lam0_A=1000.0, spec_dlog=1e-3, spec_nbins=1,
-                max_events=1_000_000, subdomain_rounds=False, check=True):
-    """A10: the coupled loop (see include/extrass.h, run_coupled)."""
+                max_events=1_000_000, subdomain_rounds=False, check=True, sampler=XT_SAMPLER_MC,
+                n_theta=20, n_phi=20):
+    """A10: the coupled loop (see include/extrass.h, run_coupled).  The paper's
+    loop: emission=XT_EMIT_LINES (the lines emit from the current populations)
+    with sampler=XT_SAMPLER_RAYS."""
     if isinstance(upsilon, (list, tuple)):
         upsilon = np.concatenate([np.ascontiguousarray(u, dtype=np.float64).ravel() for u in upsilon])
     ups = _f64(upsilon)
     lu = _i32(levels_used) if levels_used is not None else None
     si = _f64(start_in) if start_in is not None else None
     tp = TransportParams(int(n_packets), 0, -1, int(seed), XT_MODE_ATTEN, int(emission), tau_min, e_cut,
-                         20, 20, spec_lam0_A, spec_dlog, int(spec_nbins), 0, int(max_events),
-                         int(bool(subdomain_rounds)), 0, None, XT_SAMPLER_MC)
+                         int(n_theta), int(n_phi), spec_lam0_A, spec_dlog, int(spec_nbins), 0,
+                         int(max_events), int(bool(subdomain_rounds)), 0, None, int(sampler))
     np_ = NlteParams(int(precision), XT_RATES_ESTIMATORS, XT_WARM_CURRENT, int(max_iter), float(ir_tol),
                      float(jbar_W), float(jbar_TR), float(eta_nt), _ptr(lu), None, _ptr(ups),
                      int(bool(use_graph)), 0, int(newton_max), float(newton_tol), float(newton_maxvar))

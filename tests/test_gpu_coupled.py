@@ -128,3 +128,32 @@ def test_rate_solve_and_loop_from_host_streamed_store(xt):
     assert st0["converged"] and st2["converged"] and st0["outer"] == st2["outer"]
     assert _worst(w, s2, s0) < 1e-10
     assert _worst(w, l2, l0, floor=1e-20) < 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coupled_loop_line_emission_rays_vs_oracle(xt, precision):
+    """The paper's loop (Secs. 2, 2.3): the lines emit from the current
+    populations (Eq. thin_emissivity) and are traced as rays (one per emitting
+    cell, wavelength bin and viewer), so a step is a deterministic, smooth map
+    of the populations.  On a 6^3 sphere at 1 % of the plain-method density
+    (where this iteration, a Lambda iteration, converges; at full density its
+    thick lines keep it from converging): the same number of outer steps to a
+    change of 1e-3 and the same populations as the oracle's loop."""
+    w = synth.uniform_sphere(seed=4, n=6, n_packets=1)
+    w.upsilon = synth.collision_strengths(4, w.level_off)
+    w.n_ion_density = w.n_ion_density * 1e-2
+    w.pops = w.pops * 1e-2
+    kw = dict(n_theta=5, n_phi=6, spec_dlog=0.002)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st = xt.run_coupled(ctx.h, w.upsilon, 1, seed=w.seed, start=xt.XT_WARM_CURRENT, tol=1e-3,
+                            precision=precision, newton_tol=1e-10, emission=xt.XT_EMIT_LINES,
+                            sampler=xt.XT_SAMPLER_RAYS, spec_lam0_A=w.spec_band_A[0],
+                            spec_nbins=w.spec_band_A[1], max_outer=60, **kw)
+        got = np.zeros((w.ncell, w.nlev))
+        xt.get_populations(ctx.h, got)
+    ref, steps, hist = coupled.coupled_loop(w, tol=1e-3, newton_tol=1e-10, emission="lines",
+                                            sampler="rays", max_outer=60, **kw)
+    assert steps > 10 and st["converged"] and steps == st["outer"], (st, hist)
+    assert st["not_converged"] == 0
+    assert _worst(w, got, ref) < 1e-6

@@ -64,7 +64,7 @@ def _check(xt, ctx, w, emission="band", nt=9, nph=10, dlog=0.02, pi=False, **kw)
         _cmp(G, oracle.pi_rates(w, o["S_pi"]), TOL, "photoionization rates")
     L = o["ledger"]
     assert st["events"] == L["events"] and st["tests"] == L["tests"]
-    assert st["emitted_E"] == pytest.approx(L["emit_E"], rel=1e-12)
+    assert st["emitted_E"] == pytest.approx(L["emit_E"], rel=1e-9)     # sums over ~1e6 rays
     return st, o
 
 
