@@ -176,14 +176,17 @@ def ray_count(w, emission="band", n_theta=20, n_phi=20, spec_dlog=1e-3):
 def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
               emission="band", tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20,
               spec_dlog=1e-3, max_events=1_000_000, per_packet=False, sparse=None,
-              rec_cap=None, sampler="mc"):
+              rec_cap=None, sampler="mc", estimators=True):
     """Run packets [p_begin, p_end) of the workload's emission through the grid.
 
     Returns S [ncell, nline] (photons/s absorbed, divided by f_corr; natural
     cell order, the workload's line order), spec [n_theta*n_phi, n_bins]
     (escaped lab-frame energy, erg/s), the photon/energy ledger and, if asked,
     per-packet records.  With ``sparse`` (default: when the dense store would
-    exceed 2 GB) S is returned as summed (cell, line, value) records instead.
+    exceed 2 GB) S is returned as summed (cell, line, value) records instead;
+    estimators=False keeps no estimators (S is None; the same arithmetic
+    runs, and no shared state of the C code is touched, so calls on disjoint
+    packet ranges may run in parallel threads).
     A workload with photoionization data (attenuation mode) also gives S_pi
     [ncell, n_pi] (photons/s absorbed per photoionizing level) and heat
     [ncell] (erg/s of photon energy above the thresholds)."""
@@ -200,9 +203,11 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     lam0, nbins = w.spec_band_A
     pr = _params(w, N, p_begin, p_end, seed, mode, emission, tau_min, e_cut, n_theta, n_phi,
                  spec_dlog, max_events, sampler)
-    if sparse is None:
+    if not estimators:
+        sparse = False
+    elif sparse is None:
         sparse = w.ncell * w.nline * 8 > 2e9
-    S = None if sparse else np.zeros((w.ncell, w.nline))
+    S = None if (sparse or not estimators) else np.zeros((w.ncell, w.nline))
     spec = np.zeros((n_theta * n_phi, nbins))
     ledger = np.zeros(20)
     pkt = np.zeros((p_end - p_begin, len(PKT_FIELDS))) if per_packet else None

@@ -309,7 +309,7 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n,
                    (void**)&c->d_pi_nuth, (void**)&c->d_pi_sig, (void**)&c->d_pi_chi, (void**)&c->d_pi_lev,
                    (void**)&c->d_pi_sorted_of, (void**)&c->d_kappa, (void**)&c->d_piG, (void**)&c->d_piD,
-                   (void**)&c->d_piH, (void**)&c->d_rays};
+                   (void**)&c->d_piH, (void**)&c->d_rays, (void**)&c->d_low_off, (void**)&c->d_low_line};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;
@@ -516,6 +516,12 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   for (int u = 0; u < nlev; ++u) doff[u + 1] += doff[u];
   std::vector<int> fill(nlev, 0);
   for (int l = 0; l < nl; ++l) dline[doff[up[l]] + fill[up[l]]++] = c->h_sorted_of[l];
+  // radiative lines per lower level, ascending caller index
+  std::vector<int> loff(nlev + 1, 0), lline(nl);
+  for (int l = 0; l < nl; ++l) loff[lo[l] + 1]++;
+  for (int i = 0; i < nlev; ++i) loff[i + 1] += loff[i];
+  std::vector<int> lfill(nlev, 0);
+  for (int l = 0; l < nl; ++l) lline[loff[lo[l]] + lfill[lo[l]]++] = c->h_sorted_of[l];
   c->n_ion = a->n_ion; c->nlev = nlev; c->nline = nl;
   c->h_nu_sorted = s_nu;
   c->h_lam_caller = lam;
@@ -543,6 +549,8 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   if ((rc = to_device(c, c->h_sorted_of, &c->d_orig, "sorted_of"))) return rc;
   if ((rc = to_device(c, doff, &c->d_down_off, "down_off"))) return rc;
   if ((rc = to_device(c, dline, &c->d_down_line, "down_line"))) return rc;
+  if ((rc = to_device(c, loff, &c->d_low_off, "low_off"))) return rc;
+  if ((rc = to_device(c, lline, &c->d_low_line, "low_line"))) return rc;
   if ((rc = to_device(c, ups, &c->d_ups_down, "ups_down"))) return rc;
   if (a->n_ion_density && (rc = upload_rows(c, a->n_ion_density, &c->d_nion, a->n_ion, "n_ion_density")))
     return rc;

@@ -64,6 +64,8 @@ struct SeArgs {
   const double* __restrict__ A;         // sorted
   const int* __restrict__ down_off;     // [nlev + 1] lines by upper level
   const int* __restrict__ down_line;
+  const int* __restrict__ low_off;      // [nlev + 1] lines by lower level
+  const int* __restrict__ low_line;
   const double* __restrict__ S;         // estimators (net photons) [row][sorted line]
   const double* __restrict__ Rj;        // photoexcitation per sorted line (Jbar model)
   int rates;
@@ -86,6 +88,21 @@ struct SeArgs {
   double newton_tol, newton_maxvar;
   FixExpTables fx;                      // e^-tau tables (fixed point)
 };
+
+// Newton: the derivative of a line's net downward flow F = A beta n_u -
+// beta B J_ext (n_l - g_l/g_u n_u) through beta_S, t = beta'(tau) K (A n_u -
+// B J_ext net); F enters row l with +, row u with - (so dF/dn_l = t and dF/dn_u
+// = -g_l/g_u t).  Lr is the line's packed record (nu, K, g_l/g_u, lo | up).
+__device__ __forceinline__ double line_jac_t(const SeArgs& a, const FixExpTables& fx, const double* Lr,
+                                             int s, double n_lo, double n_up) {
+  const double net = n_lo - Lr[2] * n_up;
+  const double tau = Lr[1] * net;
+  double db;
+  sobolev_beta_fix(fx, tau, &db);
+  if (db == 0.0) return 0.0;
+  const double BJ = a.rates == XT_RATES_JBAR ? a.Rj[s] : 0.0;
+  return db * Lr[1] * (a.A[s] * n_up - BJ * net);
+}
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
@@ -480,10 +497,13 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
         }
       }
       block_sync();
-      // radiative lines of the kept levels (lines by upper level u < L)
-      for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
+      // radiative lines of the kept levels (lines by upper level u < L): a
+      // thread per upper level, its lines in a fixed order, so that every
+      // entry is summed in the same order on every run (a line u -> lo writes
+      // only column u and row u, which no other upper level's lines touch)
+      for (int u = 1 + tid; u < L; u += blockDim.x) {
         const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
-        for (int k = k0 + (tid & 7); k < k1; k += 8) {
+        for (int k = k0; k < k1; ++k) {
           const int s = a.down_line[k];
           const double* Lr = a.lines + 4 * (int64_t)s;
           const int64_t lu = __double_as_longlong(Lr[3]);
@@ -499,8 +519,8 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
             const double Sv = a.S[row * a.nline + s];
             if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * a.V);
           }
-          atomicAdd(W + (int64_t)lo * L + u, a.A[s] * beta + Lr[2] * Rlu);   // u -> lo
-          atomicAdd(W + (int64_t)u * L + lo, Rlu);                            // lo -> u
+          W[(int64_t)lo * L + u] += a.A[s] * beta + Lr[2] * Rlu;   // u -> lo
+          W[(int64_t)u * L + lo] += Rlu;                            // lo -> u
         }
       }
       // non-thermal excitation from the ground level
@@ -559,27 +579,36 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           if (lane == 0) sB[i] = (i == 0 ? nz : 0.0) - s;
         }
         block_sync();
-        for (int u = 1 + tid / 8; u < L; u += blockDim.x / 8) {
+        // a thread per upper level writes its lines' entries of column u and
+        // row u (no other thread's); then a thread per lower level adds the
+        // t of the lines below it to its diagonal, both in fixed line order
+        for (int u = 1 + tid; u < L; u += blockDim.x) {
           const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
-          for (int k = k0 + (tid & 7); k < k1; k += 8) {
+          double du = 0.0;
+          for (int k = k0; k < k1; ++k) {
             const int s = a.down_line[k];
             const double* Lr = a.lines + 4 * (int64_t)s;
-            const int64_t lu = __double_as_longlong(Lr[3]);
-            const int lo = (int)(lu & 0xFFFFFFFF) - off;
-            const double net = sNk[lo] - Lr[2] * sNk[u];
-            const double tau = Lr[1] * net;
-            double db;
-            sobolev_beta_fix(sfx, tau, &db);
-            if (db == 0.0) continue;
-            const double BJ = a.rates == XT_RATES_JBAR ? a.Rj[s] : 0.0;
-            const double t = db * Lr[1] * (a.A[s] * sNk[u] - BJ * net);
-            if (lo != 0) {
-              atomicAdd(W + (int64_t)lo * L + lo, t);
-              atomicAdd(W + (int64_t)lo * L + u, -Lr[2] * t);
-            }
-            atomicAdd(W + (int64_t)u * L + lo, -t);
-            atomicAdd(W + (int64_t)u * L + u, Lr[2] * t);
+            const int lo = (int)(__double_as_longlong(Lr[3]) & 0xFFFFFFFF) - off;
+            const double t = line_jac_t(a, sfx, Lr, s, sNk[lo], sNk[u]);
+            if (t == 0.0) continue;
+            if (lo != 0) W[(int64_t)lo * L + u] += -Lr[2] * t;
+            W[(int64_t)u * L + lo] += -t;
+            du += Lr[2] * t;
           }
+          W[(int64_t)u * L + u] += du;
+        }
+        block_sync();
+        for (int lo = 1 + tid; lo < L; lo += blockDim.x) {
+          const int q0 = a.low_off[off + lo], q1 = a.low_off[off + lo + 1];
+          double dl = 0.0;
+          for (int q = q0; q < q1; ++q) {
+            const int s = a.low_line[q];
+            const double* Lr = a.lines + 4 * (int64_t)s;
+            const int u = (int)(__double_as_longlong(Lr[3]) >> 32) - off;
+            if (u >= L) continue;                       // upper level not kept
+            dl += line_jac_t(a, sfx, Lr, s, sNk[lo], sNk[u]);
+          }
+          W[(int64_t)lo * L + lo] += dl;
         }
         // the column scale of the FP32 factor: the iterate (levels below
         // 1e-30 n_z need no relative accuracy)
@@ -987,6 +1016,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.Te = c->d_Te; a.ne = c->d_ne; a.dep = c->d_dep; a.pops = c->d_pops; a.warm = warm;
   a.pops_out = B.pops_new; a.status = B.status; a.lines = c->d_lines; a.A = c->d_A;
   a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = B.Rj;
+  a.low_off = c->d_low_off; a.low_line = c->d_low_line;
   a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = B.ups; a.ups_off = B.upsoff;
   a.levels_used = B.used; a.work = B.work; a.n_work = n_big; a.counter = B.cnt;
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
