@@ -182,6 +182,42 @@ def thin_bench(local, stream_ptr, passes=3):
             "trace_GB_per_s": ach, "frac_hbm": ach / peaks["hbm_gbs"]}
 
 
+def collision_sphere(n_packets=20_000_000):
+    """A 16^3 sphere whose 12 lines lie within 5000-5080 A and whose band is
+    4990-5100 A: every packet meets most lines, so the lanes of a warp often
+    add to the same (cell, line) estimator slot at once."""
+    import synth
+    w = synth.uniform_sphere(n=16, n_packets=n_packets, n_lines=12, n_levels=8, seed=35)
+    w.lambda_A = np.linspace(5000.0, 5080.0, 12)
+    w.band_A = (4990.0, 5100.0)
+    w.spec_band_A = synth._spectrum_grid(w.band_A[0], w.band_A[1], w.v_max)
+    w.pops = w.pops * 1e-3
+    w.name = "collision_sphere_16^3_12lines"
+    return w
+
+
+def prereduce_bench(local, stream_ptr, w_main):
+    """The trace kernel with the warp pre-reduction of estimator increments
+    (default) and without it (XT_FLAG_NO_WARP_REDUCE), on the paper-scale
+    onion, its thin-line variant and a workload whose lanes often share a slot."""
+    import paper_2511_07539_gb300 as xt
+    out = {}
+    for name, w in (("onion", w_main), ("thin_lines", thin_onion()), ("collisions", collision_sphere())):
+        ctx = xt.Context(local, stream_ptr)
+        ctx.load(w)
+        res = {}
+        for flags in (0, xt.XT_FLAG_NO_WARP_REDUCE, 0, xt.XT_FLAG_NO_WARP_REDUCE):
+            ctx.transport(w, flags=flags)
+            ms = min(ctx.transport(w, flags=flags)["trace_ms"] for _ in range(2))
+            key = "reduce" if flags == 0 else "no_reduce"
+            res[key] = min(ms, res.get(key, ms))
+        st = ctx.transport(w)
+        ctx.close()
+        out[name] = {"trace_ms_reduce": res["reduce"], "trace_ms_no_reduce": res["no_reduce"],
+                     "events": st["events"], "ratio": res["no_reduce"] / res["reduce"]}
+    return out
+
+
 def workload_config(w, world):
     """The `config` object of both arms' lines: the workload by name and size."""
     store_gb = w.ncell * w.nline * 8 / 1e9          # dense estimator store, FP64
@@ -484,6 +520,8 @@ def main():
     ap.add_argument("--workload", default="onion",
                     choices=["onion", "onion-small", "onion-thin", "sphere"])
     ap.add_argument("--no-thin", action="store_true", help="skip the thin-line measurement")
+    ap.add_argument("--prereduce", action="store_true",
+                    help="also time the trace kernel with and without the warp pre-reduction")
     ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
@@ -668,6 +706,8 @@ def main():
     ctx.close()
     if rank == 0 and not args.no_thin and args.workload == "onion":
         line["thin_lines"] = thin_bench(local, stream.cuda_stream)
+    if rank == 0 and args.prereduce and args.workload == "onion":
+        line["prereduce"] = prereduce_bench(local, stream.cuda_stream, w)
     if rank == 0 and not args.no_nlte and args.workload == "onion":
         line["nlte"] = nlte_bench(local, stream.cuda_stream, args.nlte_n)
     if rank == 0 and not args.no_coupled and args.workload == "onion":
