@@ -198,18 +198,18 @@ def collision_sphere(n_packets=20_000_000):
 
 def prereduce_bench(local, stream_ptr, w_main):
     """The trace kernel with the warp pre-reduction of estimator increments
-    (default) and without it (XT_FLAG_NO_WARP_REDUCE), on the paper-scale
-    onion, its thin-line variant and a workload whose lanes often share a slot."""
+    (XT_FLAG_WARP_REDUCE) and without it (default), on the paper-scale onion,
+    its thin-line variant and a workload whose lanes often share a slot."""
     import paper_2511_07539_gb300 as xt
     out = {}
     for name, w in (("onion", w_main), ("thin_lines", thin_onion()), ("collisions", collision_sphere())):
         ctx = xt.Context(local, stream_ptr)
         ctx.load(w)
         res = {}
-        for flags in (0, xt.XT_FLAG_NO_WARP_REDUCE, 0, xt.XT_FLAG_NO_WARP_REDUCE):
+        for flags in (xt.XT_FLAG_WARP_REDUCE, 0, xt.XT_FLAG_WARP_REDUCE, 0):
             ctx.transport(w, flags=flags)
             ms = min(ctx.transport(w, flags=flags)["trace_ms"] for _ in range(2))
-            key = "reduce" if flags == 0 else "no_reduce"
+            key = "reduce" if flags else "no_reduce"
             res[key] = min(ms, res.get(key, ms))
         st = ctx.transport(w)
         ctx.close()

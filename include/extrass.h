@@ -110,11 +110,12 @@ int get_sobolev_tau(xt_ctx *ctx, int64_t cell_begin, int64_t n_cells, double *ta
 #define XT_EMIT_BAND 0      /* flat-in-nu band emission with L_cell */
 #define XT_EMIT_LINES 1     /* line emissivity A_ul dE beta N_u, Eq. (thin_emissivity) */
 #define XT_PKT_FIELDS 11    /* per-packet record, see xt_transport_params.packet_records */
-/* Estimator increments (Sec. 2.3.2) are pre-reduced per warp: lanes adding to
- * the same (cell, line) slot are summed and one FP64 atomic adds the sum.  This
- * flag turns that off (one atomic per increment); results differ only in the
- * order of the additions. */
-#define XT_FLAG_NO_WARP_REDUCE 1
+/* Pre-reduce the estimator increments (Sec. 2.3.2) per warp: lanes adding to
+ * the same (cell, line) slot are summed and one FP64 atomic adds the sum
+ * (attenuation mode with Monte Carlo packets, without photoionization; other
+ * passes ignore the flag).  Off by default: one atomic per increment measured
+ * faster on GB300.  Results differ only in the order of the additions. */
+#define XT_FLAG_WARP_REDUCE 1
 
 typedef struct {
     int64_t n_packets;      /* N of the whole emission (sets the per-cell quota) */
@@ -461,6 +462,34 @@ typedef struct {
 } xt_noalloc_transport;
 int run_transport_noalloc(const xt_noalloc_transport *a, void *cuda_stream,
                           xt_transport_stats *out, char *errbuf, size_t errlen);
+
+/* ---- spatial decomposition across processes (Sec. 2.4.1) ------------------
+ * One process per GPU owns a domain, the cells with z in [z_lo, z_hi) (whole
+ * x-y layers), and holds the estimators, photoionization rates and spectrum
+ * tallies that arise in it; packets that cross into another domain are handed
+ * to that domain's process as bundles of packet states (the paper's managers
+ * exchange bundles of rays between nodes, App. B).  One call: with emit != 0
+ * the packets of [packet_begin, packet_begin + packet_count) of the
+ * n_packets-packet emission whose emitting cell lies in the domain start
+ * here; the n_in packets of bundle_in (from other domains) resume; every
+ * packet is traced until it escapes, ends, or enters a cell outside the
+ * domain, and those are written to bundle_out (XT_BUNDLE_FIELDS doubles each;
+ * entry[XT_BUNDLE_CELL] holds the cell it entered, ix + 1024 iy + 1048576 iz,
+ * which tells the caller the receiving domain).  *n_out is their number; if
+ * it exceeds out_cap nothing is written past out_cap and XT_EINVAL is
+ * returned (call again with a larger buffer after the same inputs: the pass
+ * is deterministic).  accumulate works as in run_transport (0 on a domain's
+ * first call of a pass, 1 on the calls that resume its bundles).  Attenuation
+ * mode with Monte Carlo packets, the estimator store on the device, no
+ * packet records.  Results summed over the domains equal run_transport's on
+ * the whole grid (up to the order of additions); a packet's trajectory does
+ * not depend on the decomposition.  bundle_in and bundle_out may be host or
+ * device memory. */
+#define XT_BUNDLE_FIELDS 24
+#define XT_BUNDLE_CELL 17
+int run_transport_domain(xt_ctx *ctx, const xt_transport_params *p, int32_t z_lo, int32_t z_hi,
+                         int32_t emit, const double *bundle_in, int64_t n_in, double *bundle_out,
+                         int64_t out_cap, int64_t *n_out, xt_transport_stats *out);
 
 typedef struct {
     int64_t ncell, nlev, nline, n_ion;

@@ -102,6 +102,9 @@ def lib():
         _lib.xo_sigma_pi.restype = d
         _lib.xo_sigma_pi.argtypes = [d, d, d, C.c_int32]
         _lib.xo_emission.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.xo_transport_domain.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                             C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.xo_ray_count.restype = C.c_int64
         _lib.xo_ray_count.argtypes = [C.c_void_p, C.c_void_p]
         _lib.xo_tau_beta.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
@@ -237,6 +240,48 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     if per_packet:
         out["pkt"] = pkt
     return out
+
+
+STATE_FIELDS = 21          # doubles per packet state handed between domains
+STATE_Z = 4                # the z index of the cell the packet entered
+
+
+def transport_domain(w, z_lo, z_hi, emit, bundle_in=None, n_theta=20, n_phi=20, spec_dlog=1e-3,
+                     tau_min=1e-4, e_cut=1e-6, seed=None, max_events=1_000_000):
+    """One domain of a spatial decomposition (Sec. 2.4.1): the cells with z in
+    [z_lo, z_hi).  With emit, the workload's packets emitted in the domain
+    start; the packets of bundle_in (states from other domains, [n,
+    STATE_FIELDS]) resume.  Returns S [ncell, nline] (only the domain's cells
+    written), spec, ledger, S_pi and heat (with photoionization data), and the
+    states of the packets that entered another domain's cells."""
+    keep = _Keep(w)
+    lam0, nbins = w.spec_band_A
+    pr = _params(w, w.n_packets, 0, w.n_packets, seed, "atten", "band", tau_min, e_cut, n_theta,
+                 n_phi, spec_dlog, max_events, "mc")
+    S = np.zeros((w.ncell, w.nline))
+    spec = np.zeros((n_theta * n_phi, nbins))
+    ledger = np.zeros(20)
+    S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
+    heat = np.zeros(w.ncell) if keep.n_pi else None
+    bin_ = np.zeros((0, STATE_FIELDS)) if bundle_in is None else np.ascontiguousarray(bundle_in, dtype=np.float64)
+    cap = max(1024, 4 * bin_.shape[0], w.n_packets // 2)
+    while True:
+        out = np.zeros((cap, STATE_FIELDS))
+        n_out = np.zeros(1, dtype=np.int64)
+        S[:] = 0.0; spec[:] = 0.0; ledger[:] = 0.0
+        if S_pi is not None:
+            S_pi[:] = 0.0; heat[:] = 0.0
+        rc = lib().xo_transport_domain(C.byref(keep.pb), C.byref(pr), int(z_lo), int(z_hi), int(bool(emit)),
+                                       _ptr(bin_), bin_.shape[0], _ptr(out), cap, _ptr(n_out), _ptr(S),
+                                       _ptr(spec), _ptr(ledger), _ptr(S_pi), _ptr(heat))
+        if rc == 0:
+            break
+        cap = int(n_out[0])
+    res = dict(S=S, spec=spec, ledger=dict(zip(LEDGER, ledger[:len(LEDGER)].tolist())),
+               bundle=out[: int(n_out[0])])
+    if keep.n_pi:
+        res["S_pi"], res["heat"] = S_pi, heat
+    return res
 
 
 def emission(w, n_packets=None, emission="band"):

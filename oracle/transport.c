@@ -504,12 +504,33 @@ static void add_estimator(double *S, int64_t cell, int32_t nline, int32_t l, dou
  * final nu_lab */
 #define XO_PKT_FIELDS 11
 
+/* A packet in flight: everything the event loop carries from one cell to the
+ * next (resumable, for the spatial decomposition across processes). */
+typedef struct {
+    int64_t p, c;                       /* packet id, emitting cell */
+    int32_t idx[3];                     /* current cell */
+    double r[3], n[3];                  /* position (on the entry wall), direction */
+    double nu_lab, N, E0, N0, nu_cmf0;
+    int32_t cursor;
+    int64_t events, interactions, ndraw;
+} xo_state;
+#define XO_STATE_FIELDS 21
+
+/* Where packets that leave a domain go (NULL: the whole grid is the domain). */
+typedef struct {
+    int32_t z_lo, z_hi;                 /* the domain: cells with z in [z_lo, z_hi) */
+    double *out;                        /* XO_STATE_FIELDS doubles per leaving packet */
+    int64_t cap, n;
+} xo_domain;
+
+static void trace(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger,
+                  double *pkt, double *S_pi, double *heat, xo_domain *dom);
 static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], double r[3], double n[3],
                       double nu_cmf, int32_t cursor, double E0, double *S, double *spec,
-                      double *ledger, double *pkt, double *S_pi, double *heat);
+                      double *ledger, double *pkt, double *S_pi, double *heat, xo_domain *dom);
 
 static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec,
-                             double *ledger, double *pkt, double *S_pi, double *heat) {
+                             double *ledger, double *pkt, double *S_pi, double *heat, xo_domain *dom) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     int64_t c = cell_of_packet(P, p);
@@ -542,7 +563,7 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
         nu_cmf = XO_C / (pb->lambda_A[pick] * 1e-8);
         cursor = P->pos[pick] + 1;           /* start past the emitting line */
     }
-    propagate(P, p, c, idx, r, n, nu_cmf, cursor, E0, S, spec, ledger, pkt, S_pi, heat);
+    propagate(P, p, c, idx, r, n, nu_cmf, cursor, E0, S, spec, ledger, pkt, S_pi, heat, dom);
 }
 
 /* Ray r of the RAYS sampler: r = (cell rank, bin rank, viewer) in row-major
@@ -579,7 +600,8 @@ static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, d
         rr[a] = (-P->R + idx[a] * d[a]) + 0.5 * d[a];     /* the middle of the cell */
         n[a] = P->view_n[3 * k + a];
     }
-    propagate(P, r, c, idx, rr, n, P->rbin_nu[jb], P->rbin_cursor[jb], E0, S, spec, ledger, pkt, S_pi, heat);
+    propagate(P, r, c, idx, rr, n, P->rbin_nu[jb], P->rbin_cursor[jb], E0, S, spec, ledger, pkt, S_pi, heat,
+              NULL);
 }
 
 /* The event loop of one packet or ray from its emission (Secs. 2.3, 2.3.2):
@@ -587,18 +609,54 @@ static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, d
  * nu_cmf, first line to test `cursor`, energy E0 (erg/s). */
 static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], double r[3], double n[3],
                       double nu_cmf, int32_t cursor, double E0, double *S, double *spec,
-                      double *ledger, double *pkt, double *S_pi, double *heat) {
+                      double *ledger, double *pkt, double *S_pi, double *heat, xo_domain *dom) {
+    xo_state st;
+    st.p = p; st.c = c;
+    for (int a = 0; a < 3; a++) { st.idx[a] = idx[a]; st.r[a] = r[a]; st.n[a] = n[a]; }
+    st.nu_lab = nu_cmf / (1.0 - dot3(n, r) / P->ct);
+    st.N = E0 / (XO_H * nu_cmf);
+    st.E0 = E0; st.N0 = st.N; st.nu_cmf0 = nu_cmf;
+    st.cursor = cursor;
+    st.events = st.interactions = st.ndraw = 0;
+    ledger[L_EMIT_N] += st.N;
+    ledger[L_EMIT_E] += E0;
+    trace(P, &st, S, spec, ledger, pkt, S_pi, heat, dom);
+}
+
+/* The packet's state as XO_STATE_FIELDS doubles (integers exactly). */
+static void state_pack(const xo_state *st, double *o) {
+    o[0] = (double)st->p; o[1] = (double)st->c;
+    for (int a = 0; a < 3; a++) { o[2 + a] = st->idx[a]; o[5 + a] = st->r[a]; o[8 + a] = st->n[a]; }
+    o[11] = st->nu_lab; o[12] = st->N; o[13] = st->E0; o[14] = st->N0; o[15] = st->nu_cmf0;
+    o[16] = st->cursor; o[17] = (double)st->events; o[18] = (double)st->interactions;
+    o[19] = (double)st->ndraw; o[20] = 0.0;
+}
+
+static void state_unpack(const double *o, xo_state *st) {
+    st->p = (int64_t)o[0]; st->c = (int64_t)o[1];
+    for (int a = 0; a < 3; a++) { st->idx[a] = (int32_t)o[2 + a]; st->r[a] = o[5 + a]; st->n[a] = o[8 + a]; }
+    st->nu_lab = o[11]; st->N = o[12]; st->E0 = o[13]; st->N0 = o[14]; st->nu_cmf0 = o[15];
+    st->cursor = (int32_t)o[16]; st->events = (int64_t)o[17]; st->interactions = (int64_t)o[18];
+    st->ndraw = (int64_t)o[19];
+}
+
+/* The event loop from the state st until the packet ends (its record, if
+ * asked, written to pkt) or, with a domain, enters a cell outside it (its
+ * state then appended to dom->out). */
+static void trace(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger,
+                  double *pkt, double *S_pi, double *heat, xo_domain *dom) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     double d[3] = {P->dx, P->dy, P->dz};
     int32_t nn[3] = {pb->nx, pb->ny, pb->nz};
     double ct = P->ct;
-    double nu_lab = nu_cmf / (1.0 - dot3(n, r) / ct);
-    double N = E0 / (XO_H * nu_cmf);
-    const double N0 = N, nu_cmf0 = nu_cmf;
-    ledger[L_EMIT_N] += N;
-    ledger[L_EMIT_E] += E0;
-    int64_t events = 0, interactions = 0, ndraw = 0;
+    int64_t p = st->p, c = st->c;
+    int32_t *idx = st->idx;
+    double *r = st->r, *n = st->n;
+    double nu_lab = st->nu_lab, N = st->N, E0 = st->E0;
+    const double N0 = st->N0, nu_cmf0 = st->nu_cmf0;
+    int32_t cursor = st->cursor;
+    int64_t events = st->events, interactions = st->interactions, ndraw = st->ndraw;
     int fate = 0;    /* 0 escaped, 1 dropped below the energy cut, 2 thermalised, 3 event guard */
     double esc_E = 0.0;
     int32_t vbin = -1;
@@ -736,6 +794,14 @@ static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], dou
             fate = 0;
             goto done;
         }
+        if (dom && (idx[2] < dom->z_lo || idx[2] >= dom->z_hi)) {
+            /* the packet leaves the domain: hand its state on (Sec. 2.4.1) */
+            st->nu_lab = nu_lab; st->N = N; st->cursor = cursor;
+            st->events = events; st->interactions = interactions; st->ndraw = ndraw;
+            if (dom->n < dom->cap) state_pack(st, dom->out + dom->n * XO_STATE_FIELDS);
+            dom->n++;
+            return;
+        }
     }
 done:
     if (pkt) {
@@ -762,12 +828,47 @@ int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *s
     for (int64_t p = pr->p_begin; p < pr->p_end; p++) {
         double *pk = pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL;
         if (pr->sampler == 1) transport_ray(&P, p, S, spec, ledger, pk, S_pi, heat);
-        else transport_packet(&P, p, S, spec, ledger, pk, S_pi, heat);
+        else transport_packet(&P, p, S, spec, ledger, pk, S_pi, heat, NULL);
     }
     unprep(&P);
     if (rec_n) *rec_n = g_rec_n;
     g_rec = NULL;
     return (rec && g_rec_n > rec_cap) ? -1 : 0;
+}
+
+/* Spatial decomposition across processes (Sec. 2.4.1): one domain of the
+ * grid, the cells with z in [z_lo, z_hi).  With emit != 0 the packets of
+ * [p_begin, p_end) that are emitted in the domain are traced; then the packets
+ * of bundle_in (n_in states of XO_STATE_FIELDS doubles, handed on by other
+ * domains) resume.  Every packet is traced until it ends or enters a cell of
+ * another domain; the states of those are written to bundle_out (at most
+ * out_cap, their number in *n_out).  Estimators, spectrum and ledger
+ * accumulate as in xo_transport (emission is counted where the packet is
+ * emitted).  Attenuation mode, Monte Carlo packets.  Returns 0, or -1 if
+ * bundle_out was too small (its first out_cap states are written). */
+int xo_transport_domain(const xo_problem *pb, const xo_params *pr, int32_t z_lo, int32_t z_hi,
+                        int32_t emit, const double *bundle_in, int64_t n_in, double *bundle_out,
+                        int64_t out_cap, int64_t *n_out, double *S, double *spec, double *ledger,
+                        double *S_pi, double *heat) {
+    prep_t P;
+    g_rec = NULL;
+    prep(&P, pb, pr);
+    xo_domain dom = {z_lo, z_hi, bundle_out, out_cap, 0};
+    int64_t nxy = (int64_t)pb->nx * pb->ny;
+    if (emit)
+        for (int64_t p = pr->p_begin; p < pr->p_end; p++) {
+            int64_t c = cell_of_packet(&P, p);
+            int32_t z = (int32_t)(c / nxy);
+            if (z >= z_lo && z < z_hi) transport_packet(&P, p, S, spec, ledger, NULL, S_pi, heat, &dom);
+        }
+    for (int64_t k = 0; k < n_in; k++) {
+        xo_state st;
+        state_unpack(bundle_in + k * XO_STATE_FIELDS, &st);
+        trace(&P, &st, S, spec, ledger, NULL, S_pi, heat, &dom);
+    }
+    unprep(&P);
+    *n_out = dom.n;
+    return dom.n > out_cap ? -1 : 0;
 }
 
 /* Number of rays of the RAYS sampler (emitting cells x emitting bins x

@@ -22,7 +22,7 @@ XT_OK, XT_EINVAL, XT_ENOMEM, XT_ECUDA, XT_ETIMEOUT, XT_ENOTCONV, XT_ESTATE = 0, 
 XT_MODE_ATTEN, XT_MODE_SCATTER = 0, 1
 XT_EMIT_BAND, XT_EMIT_LINES = 0, 1
 XT_PKT_FIELDS = 11
-XT_FLAG_NO_WARP_REDUCE = 1
+XT_FLAG_WARP_REDUCE = 1
 XT_SAMPLER_MC, XT_SAMPLER_RAYS = 0, 1
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
               "N0", "nu_cmf0", "nu_lab"]
@@ -169,6 +169,7 @@ def lib():
             "get_sizes": ([vp, vp], C.c_int),
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
             "run_transport_noalloc": ([vp, vp, vp, C.c_char_p, C.c_size_t], C.c_int),
+            "run_transport_domain": ([vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, vp], C.c_int),
             "solve_nlte": ([vp, vp, vp, vp, vp], C.c_int),
             "surrogate_init": ([vp, vp, i32, C.c_uint64], C.c_int),
             "surrogate_weights": ([vp, i32, vp, C.c_size_t], C.c_int),
@@ -337,6 +338,34 @@ def run_transport(ctx, n_packets, seed=0, packet_begin=0, packet_count=-1, mode=
     if check:
         _check(ctx, rc)
     return st.as_dict() if check else (rc, st.as_dict())
+
+
+XT_BUNDLE_FIELDS, XT_BUNDLE_CELL = 24, 17
+
+
+def run_transport_domain(ctx, z_lo, z_hi, emit, bundle_in=None, bundle_out=None, n_packets=0, seed=0,
+                         tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20, spec_lam0_A=1000.0,
+                         spec_dlog=1e-3, spec_nbins=1, accumulate=False, max_events=1_000_000,
+                         flags=0):
+    """One call of a process's domain (see include/extrass.h): returns
+    (stats, n_out); the leaving packets' states are in bundle_out[:n_out]
+    (a [cap, XT_BUNDLE_FIELDS] float64 array or tensor, host or device)."""
+    n_in = 0 if bundle_in is None else int(bundle_in.shape[0])
+    cap = 0 if bundle_out is None else int(bundle_out.shape[0])
+    for name, b in (("bundle_in", bundle_in), ("bundle_out", bundle_out)):
+        if b is not None and (b.ndim != 2 or b.shape[1] != XT_BUNDLE_FIELDS):
+            raise ValueError(f"{name} must have shape [n, {XT_BUNDLE_FIELDS}]")
+    p = TransportParams(int(n_packets), 0, -1, int(seed), XT_MODE_ATTEN, XT_EMIT_BAND, tau_min, e_cut,
+                        int(n_theta), int(n_phi), spec_lam0_A, spec_dlog, int(spec_nbins),
+                        int(bool(accumulate)), int(max_events), 0, int(flags), None, XT_SAMPLER_MC)
+    st = TransportStats()
+    n_out = C.c_int64()
+    rc = lib().run_transport_domain(ctx, C.byref(p), int(z_lo), int(z_hi), int(bool(emit)),
+                                    _ptr(bundle_in) if n_in else None, n_in,
+                                    _ptr(bundle_out) if cap else None, cap, C.byref(n_out), C.byref(st))
+    if rc != XT_OK and not (rc == XT_EINVAL and n_out.value > cap):
+        _check(ctx, rc)
+    return st.as_dict(), int(n_out.value)
 
 
 def get_estimators(ctx, cell_begin=0, n_cells=None, out=None):

@@ -144,7 +144,7 @@ struct TraceArgs {
   EmitArgs em;                        // (packet p = em.p_begin + pool slot)
   int64_t row0;                       // first row held by S (a streamed group's slab; else 0)
   int grp_nz;                         // rounds == 2: cells along z per streamed group
-  int warp_reduce;                    // pre-reduce estimator increments by slot per warp
+  int dom_zlo, dom_zhi;               // rounds == 3: the domain's z layers
   // photoionization (the PI instance): levels sorted by threshold frequency,
   // descending; per-cell suffix sums and accumulators (see pi_segment)
   int npi;
@@ -251,6 +251,10 @@ __device__ __forceinline__ void warp_append(bool want, int idx, int* buf, unsign
 // lane of such a group sums its peers' values (in lane order, one shuffle per
 // further member of the largest group), and only the lowest lane of each group
 // issues the FP64 atomic and logs the slot.  Returns whether this lane did.
+// (Opt-in, XT_FLAG_WARP_REDUCE: measured on GB300 it made the trace kernel 1
+// to 3 % slower on every workload tried, the collision-heavy one included;
+// the hardware's own handling of same-address atomics leaves it nothing to
+// gain, and its code costs instruction-cache room.)
 __device__ __forceinline__ bool warp_add_slot(double* __restrict__ S, int64_t slot, double v,
                                               bool reduce) {
   if (!reduce) {
@@ -547,13 +551,13 @@ __device__ __forceinline__ bool pi_segment(const TraceArgs& a, const FixExpTable
       beta = div_pos(ome, tau);
     }
     const double X = N * beta * l3;
-    if (kb < a.npi && bits(d) > 0) warp_add_slot(a.piG, rb + kb, X * d, a.warp_reduce);
+    if (kb < a.npi && bits(d) > 0) atomicAdd(a.piG + rb + kb, X * d);
     for (int k = pcur; k < kb; ++k)
       atomicAdd(a.piD + (int64_t)row * a.npi + k, X * ((nu_a - s_nuth[k]) * inv_as));
     const double Nabs = N * ome;
     N_pi += Nabs;
     E_pi += Nabs * nu_a;
-    warp_add_slot(a.piH, row, Nabs * nu_a, a.warp_reduce);
+    atomicAdd(a.piH + row, Nabs * nu_a);
     N = N * ex;
   }
   pcur = kb;
@@ -567,7 +571,7 @@ constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yi
 constexpr int kRefillLanes = 24;  // empty lanes of a warp that trigger a refill with emission
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
-template <int MODE, bool PI = false, bool RAYS = false>
+template <int MODE, bool PI = false, bool RAYS = false, bool WR = false>
 __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k_trace(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
@@ -710,7 +714,10 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
             }
             rx = RX[ix]; ry = RY[iy]; rz = RZ[iz];
             row = rx + ry + rz;
-            if (a.rounds == 2) {          // a streamed group: whole x-y layers of z cells
+            if (a.rounds == 3) {          // a process's domain: whole x-y layers
+              box_lo = a.dom_zlo << 20;
+              box_hi = (g.nx - 1) | ((g.ny - 1) << 10) | ((a.dom_zhi - 1) << 20);
+            } else if (a.rounds == 2) {   // a streamed group: whole x-y layers of z cells
               const int z0 = (iz / a.grp_nz) * a.grp_nz;
               box_lo = z0 << 20;
               box_hi = (g.nx - 1) | ((g.ny - 1) << 10) | ((z0 + a.grp_nz - 1) << 20);
@@ -813,7 +820,7 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
       if (MODE == XT_MODE_ATTEN) {
         // net photons (divided by f_corr at readout), pre-reduced over the lanes
         // of the warp that hit the same slot; the adding lane logs the slot
-        if (warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N * ome, a.warp_reduce)) {
+        if (warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N * ome, WR)) {
           const unsigned long long k = atomicAdd(&blk_log, 1ull);
           if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
         }
@@ -834,7 +841,7 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
-          warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N, a.warp_reduce);
+          warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N, WR);
           acc[T_ABS] += N;                    // the whole packet is absorbed
           const double Ecmf = N * kH * L.x;
           acc[T_ABSE] += Ecmf;
@@ -1021,6 +1028,35 @@ __global__ void k_iota(int* __restrict__ out, int64_t n) {
     out[j] = (int)j;
 }
 
+// Bundles of packets handed between domains: pool entry <-> XT_BUNDLE_FIELDS
+// doubles (the NF state fields, then cell, cursor, events, draws,
+// interactions and id; integers exactly).
+static_assert(NF + 6 <= XT_BUNDLE_FIELDS && NF == XT_BUNDLE_CELL, "bundle layout");
+__global__ void k_bundle_in(Pool P, const double* __restrict__ in, int64_t n, int64_t base) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double* e = in + j * XT_BUNDLE_FIELDS;
+    const int64_t i = base + j;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) P.F(k, i) = e[k];
+    P.cell[i] = (int)e[NF]; P.cursor[i] = (int)e[NF + 1]; P.events[i] = (int)e[NF + 2];
+    P.ndraw[i] = (int)e[NF + 3]; P.inter[i] = (int)e[NF + 4]; P.pid[i] = (int64_t)e[NF + 5];
+  }
+}
+
+__global__ void k_bundle_out(Pool P, const int* __restrict__ q, int64_t n, double* __restrict__ out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double* e = out + j * XT_BUNDLE_FIELDS;
+    const int i = q[j];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) e[k] = P.F(k, i);
+    e[NF] = (double)P.cell[i]; e[NF + 1] = (double)P.cursor[i]; e[NF + 2] = (double)P.events[i];
+    e[NF + 3] = (double)P.ndraw[i]; e[NF + 4] = (double)P.inter[i]; e[NF + 5] = (double)P.pid[i];
+    for (int k = NF + 6; k < XT_BUNDLE_FIELDS; ++k) e[k] = 0.0;
+  }
+}
+
 __global__ void k_sd_scatter(const int* __restrict__ q, const int* __restrict__ key, int64_t n,
                              unsigned* __restrict__ fill, int* __restrict__ out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
@@ -1117,6 +1153,22 @@ static int blocks_for(int64_t n, int threads, int per_sm) {
 }  // namespace xt
 
 using namespace xt;
+
+// Run `fill(dev_out)` writing `bytes` and deliver them to `user` (host or
+// device memory).
+template <class F>
+static int deliver(xt_ctx* c, void* user, size_t bytes, F fill) {
+  if (is_device_ptr(user)) {
+    fill(user);
+    XT_CUDA(c, cudaGetLastError());
+    return XT_OK;
+  }
+  int rc = ensure_scratch(c, bytes);
+  if (rc) return rc;
+  fill(c->d_scratch);
+  XT_CUDA(c, cudaGetLastError());
+  return copy(c, user, c->d_scratch, bytes, "device-to-host copy");
+}
 
 // Packet pool (NF doubles, 9 ints, one id per slot), counters and the
 // subdomain histogram, grown on demand and kept in the context.
@@ -1287,10 +1339,15 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     int rcr = build_rays(c, p, rtab_rays, ray_Lc, &n_total);
     if (rcr) return rcr;
   }
-  const int64_t count = p->packet_count < 0 ? n_total - p->packet_begin : p->packet_count;
-  if (p->packet_begin < 0 || count < 0 || p->packet_begin + count > n_total)
+  const int64_t count_all = p->packet_count < 0 ? n_total - p->packet_begin : p->packet_count;
+  if (p->packet_begin < 0 || count_all < 0 || p->packet_begin + count_all > n_total)
     return fail(c, XT_EINVAL, rays ? "run_transport: ray range outside [0, rays)"
                                    : "run_transport: packet range outside [0, n_packets)");
+  const bool dom = c->dom.active;
+  if (dom && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || p->packet_records))
+    return fail(c, XT_EINVAL, "run_transport_domain: attenuation mode with Monte Carlo packets, the store "
+                              "on the device, no subdomain rounds and no packet records");
+  int64_t count = count_all;
   if (p->mode != XT_MODE_ATTEN && p->mode != XT_MODE_SCATTER) return fail(c, XT_EINVAL, "run_transport: mode");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
   if (p->emission == XT_EMIT_BAND && !c->d_L) return fail(c, XT_ESTATE, "run_transport: band emission needs L_cell in init_grid");
@@ -1396,6 +1453,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       c->qoff_n = (int64_t)q.size();
     }
     if ((rc = copy(c, c->d_qoff, q.data(), q.size() * sizeof(int64_t), "quota"))) return rc;
+    c->h_qoff = q;
     // guide of the packet -> cell inversion: the cell of packet j 2^6 for
     // j = 0..(N-1)/2^6 + 1 (ids past N map to the last cell)
     if (p->n_packets > 0) {
@@ -1422,6 +1480,19 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   // packet pool and queues
   const int nsd = c->sx * c->sy * c->sz;
+  // a process's domain: its own packets are those of its cells (whole z
+  // layers, a contiguous id range of the quota), then the bundle it receives
+  int64_t dom_e0 = 0, dom_emit = 0;
+  if (dom) {
+    const int64_t nxy = (int64_t)G.nx * G.ny;
+    const int64_t q0 = c->h_qoff[(size_t)(c->dom.z_lo * nxy)], q1 = c->h_qoff[(size_t)(c->dom.z_hi * nxy)];
+    dom_e0 = std::max<int64_t>(q0, p->packet_begin);
+    const int64_t e1 = std::min<int64_t>(q1, p->packet_begin + count_all);
+    dom_emit = c->dom.emit && e1 > dom_e0 ? e1 - dom_e0 : 0;
+    count = dom_emit + c->dom.n_in;
+    if (count > ((int64_t)1 << 27))
+      return fail(c, XT_EINVAL, "run_transport_domain: more than 2^27 packets in one call");
+  }
   // one chunk of up to 2^27 packets (23 GB of pool): the whole emission of a
   // paper-scale pass runs while the estimator store is being cleared
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
@@ -1609,10 +1680,10 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.seg_len = c->log_seglen;
   ta.log_overflow = (unsigned long long*)(c->d_seg_n + kLogSegments);
   // attenuation without subdomain rounds: the trace kernel emits its packets
-  ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds && !host_store) ? 1 : 0;
+  ta.fused = (p->mode == XT_MODE_ATTEN && !p->subdomain_rounds && !host_store && !dom) ? 1 : 0;
   ta.row0 = 0;
   ta.grp_nz = G.nz / NG;
-  ta.warp_reduce = (p->flags & XT_FLAG_NO_WARP_REDUCE) ? 0 : 1;
+  const bool wr = (p->flags & XT_FLAG_WARP_REDUCE) != 0 && p->mode == XT_MODE_ATTEN && !pi && !rays;
   ta.npi = pi ? c->npi : 0;
   ta.pi_nuth = c->d_pi_nuth; ta.pi_sig = c->d_pi_sig; ta.pi_lev = c->d_pi_lev;
   ta.kappa = c->d_kappa; ta.piG = c->d_piG; ta.piD = c->d_piD; ta.piH = c->d_piH;
@@ -1625,7 +1696,75 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
 
   const int max_rounds = 1 << 20;
   int64_t rounds = 0, queued_total = 0;
-  for (int64_t off = 0; off < count; off += chunk) {
+  if (dom) {
+    // one launch: the domain's own packets and the received bundle, traced
+    // until they end or leave the domain; those are written out as a bundle
+    int sl;
+    if (dom_emit > 0) {
+      ea.p_begin = dom_e0;
+      ea.n = dom_emit;
+      sl = tick(0);
+      k_emit<<<blocks_for(dom_emit, 256, 16), 256, 0, c->stream>>>(ea);
+      XT_CUDA(c, cudaGetLastError());
+      tock(sl);
+      ++kernels;
+    }
+    const int64_t n_in = c->dom.n_in;
+    const size_t in_b = (size_t)n_in * XT_BUNDLE_FIELDS * sizeof(double);
+    if (n_in > 0) {
+      const double* src = c->dom.in;
+      if (!is_device_ptr(src)) {
+        if ((rc = ensure_scratch(c, in_b))) return rc;
+        if ((rc = copy(c, c->d_scratch, src, in_b, "bundle in"))) return rc;
+        src = (const double*)c->d_scratch;
+      }
+      k_bundle_in<<<blocks_for(n_in, 256, 8), 256, 0, c->stream>>>(P, src, n_in, dom_emit);
+      XT_CUDA(c, cudaGetLastError());
+      ++kernels;
+    }
+    c->dom.n_out = 0;
+    if (count > 0) {
+      XT_CUDA(c, cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), c->stream));
+      ta.rounds = 3;
+      ta.dom_zlo = c->dom.z_lo;
+      ta.dom_zhi = c->dom.z_hi;
+      ta.list = nullptr;
+      ta.n_list = count;
+      ta.out = qA;
+      const int grid = (int)std::min<int64_t>(grid_max, (count + 255) / 256);
+      sl = tick(1);
+      if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
+      XT_CUDA(c, cudaGetLastError());
+      tock(sl);
+      ++kernels;
+      unsigned long long cnt[4];
+      XT_CUDA(c, cudaMemcpyAsync(cnt, counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+      ++rounds;
+      if (cnt[1] > 0) {
+        xa.n_esc = (int64_t)cnt[1];
+        sl = tick(2);
+        k_escape<<<blocks_for(xa.n_esc, 256, 8), 256, 0, c->stream>>>(xa);
+        XT_CUDA(c, cudaGetLastError());
+        tock(sl);
+        ++kernels;
+      }
+      const int64_t nq = (int64_t)cnt[2];
+      c->dom.n_out = nq;
+      queued_total = nq;
+      const int64_t nw = std::min<int64_t>(nq, c->dom.out_cap);
+      if (nw > 0 && c->dom.out) {
+        rc = deliver(c, c->dom.out, (size_t)nw * XT_BUNDLE_FIELDS * sizeof(double), [&](void* d) {
+          k_bundle_out<<<blocks_for(nw, 256, 8), 256, 0, c->stream>>>(P, qA, nw, (double*)d);
+        });
+        if (rc) return rc;
+        ++kernels;
+      }
+    }
+  }
+  for (int64_t off = 0; !dom && off < count; off += chunk) {
     const int64_t n = std::min(chunk, count - off);
     ea.p_begin = p->packet_begin + off;
     ea.n = n;
@@ -1693,6 +1832,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
             const int grid = (int)std::min<int64_t>(grid_max, (lens[part] + 255) / 256);
             sl = tick(1);
             if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+            else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
             else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
             else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
             XT_CUDA(c, cudaGetLastError());
@@ -1750,6 +1890,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays) k_trace<XT_MODE_ATTEN, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_SCATTER><<<grid, 256, 0, c->stream>>>(ta);
       XT_CUDA(c, cudaGetLastError());
@@ -1839,6 +1980,29 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   return XT_OK;
 }
 
+
+extern "C" int run_transport_domain(xt_ctx* c, const xt_transport_params* p, int32_t z_lo, int32_t z_hi,
+                                    int32_t emit, const double* bundle_in, int64_t n_in, double* bundle_out,
+                                    int64_t out_cap, int64_t* n_out, xt_transport_stats* out) {
+  if (!c || !p || !n_out) return fail(c, XT_EINVAL, "run_transport_domain: null argument");
+  if (!c->have_grid) return fail(c, XT_ESTATE, "run_transport_domain: init_grid first");
+  if (z_lo < 0 || z_hi > c->geo.nz || z_lo >= z_hi)
+    return fail(c, XT_EINVAL, "run_transport_domain: need 0 <= z_lo < z_hi <= nz");
+  if (n_in < 0 || (n_in > 0 && !bundle_in) || out_cap < 0 || (out_cap > 0 && !bundle_out))
+    return fail(c, XT_EINVAL, "run_transport_domain: bundle arguments");
+  c->dom.active = true;
+  c->dom.z_lo = z_lo; c->dom.z_hi = z_hi; c->dom.emit = emit ? 1 : 0;
+  c->dom.in = bundle_in; c->dom.n_in = n_in; c->dom.out = bundle_out; c->dom.out_cap = out_cap;
+  c->dom.n_out = 0;
+  const int rc = run_transport(c, p, out);
+  c->dom.active = false;
+  *n_out = c->dom.n_out;
+  if (rc) return rc;
+  if (c->dom.n_out > out_cap)
+    return fail(c, XT_EINVAL, "run_transport_domain: " + std::to_string(c->dom.n_out) +
+                                  " packets leave the domain, bundle_out holds " + std::to_string(out_cap));
+  return XT_OK;
+}
 
 // ============================================================================
 // Transport without device allocation.
@@ -2074,7 +2238,6 @@ extern "C" int run_transport_noalloc(const xt_noalloc_transport* a, void* cuda_s
   ta.rtab = (const int*)(B + kNaRtab);
   ta.slotlog = (int64_t*)(B + kNaLog); ta.seg_n = (int64_t*)(B + kNaSegN); ta.seg_len = 0;
   ta.log_overflow = (unsigned long long*)(B + kNaSegN + 8ull * kNaSegs);
-  ta.warp_reduce = 1;
   EscArgs xa{};
   xa.pool = P; xa.esc = esc; xa.spec = a->spec; xa.n_theta = a->n_theta; xa.n_phi = a->n_phi;
   xa.nbins = a->spec_nbins; xa.lam0 = a->spec_lam0_A; xa.log1p_dlog = std::log1p(a->spec_dlog);

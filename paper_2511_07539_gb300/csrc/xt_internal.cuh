@@ -113,6 +113,14 @@ struct xt_ctx {
   int64_t pi_rows = 0;               // rows the per-cell photoionization arrays hold
   int pi_npi = 0;                    //   for this many levels
   bool have_pi = false;              // the last pass photoionized
+  // spatial decomposition: the domain of the current run_transport_domain call
+  struct Domain {
+    bool active = false;
+    int z_lo = 0, z_hi = 0, emit = 0;
+    const double* in = nullptr; int64_t n_in = 0;
+    double* out = nullptr; int64_t out_cap = 0, n_out = 0;
+  } dom;
+  std::vector<int64_t> h_qoff;       // the packet quota (natural order prefix) on the host
   void* d_rays = nullptr;            // the RAYS sampler's tables (one allocation, carved)
   size_t rays_bytes = 0;
   // state

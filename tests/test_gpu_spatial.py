@@ -1,0 +1,81 @@
+"""Spatial decomposition (Sec. 2.4.1) on the GPU through the C ABI: the
+domains of run_transport_domain, each on a context of its own, driven in one
+process by the bundle-exchange driver (run_local: the domains step in
+lockstep; bundles of packet states go from context to context on the
+device).  The sums over the domains equal one run_transport of the whole
+grid: estimators and photoionization rates 1e-10, spectrum 1e-9, events and
+tests exact."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xt():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a GPU"
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_07539_gb300 as xt
+    return xt
+
+
+def _cmp(got, want, tol, what):
+    mg, mw = got != 0, want != 0
+    assert np.array_equal(mg, mw), f"{what}: support differs ({mg.sum()} vs {mw.sum()})"
+    if mw.any():
+        err = np.max(np.abs(got[mw] / want[mw] - 1))
+        assert err < tol, f"{what}: max rel err {err}"
+
+
+@pytest.mark.parametrize("world,pi", [(2, False), (4, True)])
+def test_domains_sum_to_the_whole_grid(xt, world, pi):
+    import torch
+    from paper_2511_07539_gb300 import spatial
+    w = synth.clumpy_onion(seed=2, n=16, n_packets=400_000, n_lines=2000, level_range=(20, 50),
+                           subdomains=(2, 2, 4))
+    if pi:
+        synth.with_photoionization(w)
+    w.pops = w.pops * 1e-3
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = dict(n_packets=w.n_packets, seed=w.seed, spec_lam0_A=w.spec_band_A[0],
+              spec_nbins=w.spec_band_A[1])
+    ref = xt.Context(0, stream)
+    ref.load(w)
+    st = ref.transport(w)
+    S_ref, spec_ref = ref.get_estimators(), ref.get_spectrum(0)
+    G_ref = ref.get_photoionization_rates()[0] if pi else None
+    ref.close()
+    ctxs, trs = [], []
+    for r in range(world):
+        c = xt.Context(0, stream)
+        c.load(w)
+        ctxs.append(c)
+        trs.append(spatial.LibDomainTracer(c, *spatial.slab(r, w.nz, world), **kw))
+    rounds = spatial.run_local(trs, w.nz)
+    assert 1 <= rounds <= world - 1
+    S = np.zeros_like(S_ref)
+    spec = np.zeros_like(spec_ref)
+    G = np.zeros_like(G_ref) if pi else None
+    ev = tests = 0.0
+    nxy = w.nx * w.ny
+    for r, (c, t) in enumerate(zip(ctxs, trs)):
+        z0, z1 = spatial.slab(r, w.nz, world)
+        S[z0 * nxy:z1 * nxy] = c.get_estimators(z0 * nxy, (z1 - z0) * nxy)
+        spec += c.get_spectrum(0)
+        if pi:
+            G[z0 * nxy:z1 * nxy] = c.get_photoionization_rates(z0 * nxy, (z1 - z0) * nxy)[0]
+        # a domain's store holds nothing outside its cells
+        if z0 > 0:
+            assert not c.get_estimators(0, z0 * nxy).any()
+        ev += sum(s["events"] for s in t.stats)
+        tests += sum(s["tests"] for s in t.stats)
+        c.close()
+    assert ev == st["events"] and tests == st["tests"]
+    _cmp(S, S_ref, 1e-10, "estimators")
+    _cmp(spec, spec_ref, 1e-9, "spectrum")
+    if pi:
+        _cmp(G, G_ref, 1e-10, "photoionization rates")

@@ -185,8 +185,8 @@ def test_spectrum_normalisations_vs_oracle(xt, views):
 @pytest.mark.parametrize("flags", [0, 1])
 def test_warp_prereduction_of_estimators(xt, flags):
     """Few lines and thin: the lanes of a warp often add to the same (cell,
-    line) slot at once.  With the warp pre-reduction (flags 0) and without it
-    (XT_FLAG_NO_WARP_REDUCE), the estimators equal the oracle's."""
+    line) slot at once.  With the warp pre-reduction (XT_FLAG_WARP_REDUCE) and
+    without it (flags 0), the estimators equal the oracle's."""
     w = synth.uniform_sphere(n=6, n_packets=200_000, n_lines=12, n_levels=8, seed=35)
     w.lambda_A = np.linspace(5000.0, 5080.0, 12)     # every packet meets most lines
     w.band_A = (4990.0, 5100.0)
