@@ -182,6 +182,31 @@ def thin_bench(local, stream_ptr, passes=3):
             "trace_GB_per_s": ach, "frac_hbm": ach / peaks["hbm_gbs"]}
 
 
+def rays_bench(local, stream_ptr):
+    """The RAYS sampler (Sec. 2.3) on the 32^3 onion with the paper-scale line
+    list (1e5 lines): rays from every cell centre for every 1 % bin of the
+    band and 10 x 10 viewers, with each group's line window staged in shared
+    memory (default) and with the line list read from global memory."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    import synth
+    w = synth.clumpy_onion(n=32, n_packets=1, subdomains=(4, 4, 4))
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    kw = dict(sampler=xt.XT_SAMPLER_RAYS, n_theta=10, n_phi=10, spec_dlog=1e-2)
+    out = {"workload": w.name + "_rays_10x10_viewers_1pc_bins"}
+    for name, flags in (("staged", 0), ("unstaged", xt.XT_FLAG_RAYS_UNSTAGED)):
+        ctx.transport(w, flags=flags, **kw)
+        st = min((ctx.transport(w, flags=flags, **kw) for _ in range(2)), key=lambda x: x["trace_ms"])
+        out[name] = {"trace_ms": st["trace_ms"], "rays": st["rays"], "events": st["events"],
+                     "tests": st["tests"], "rays_per_s": st["rays"] / (st["trace_ms"] * 1e-3),
+                     "events_per_s": st["events"] / (st["trace_ms"] * 1e-3)}
+    ctx.close()
+    torch.cuda.synchronize()
+    out["speedup_staged"] = out["unstaged"]["trace_ms"] / out["staged"]["trace_ms"]
+    return out
+
+
 def collision_sphere(n_packets=20_000_000):
     """A 16^3 sphere whose 12 lines lie within 5000-5080 A and whose band is
     4990-5100 A: every packet meets most lines, so the lanes of a warp often
@@ -520,6 +545,7 @@ def main():
     ap.add_argument("--workload", default="onion",
                     choices=["onion", "onion-small", "onion-thin", "sphere"])
     ap.add_argument("--no-thin", action="store_true", help="skip the thin-line measurement")
+    ap.add_argument("--no-rays", action="store_true", help="skip the RAYS-sampler measurement")
     ap.add_argument("--prereduce", action="store_true",
                     help="also time the trace kernel with and without the warp pre-reduction")
     ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
@@ -706,6 +732,8 @@ def main():
     ctx.close()
     if rank == 0 and not args.no_thin and args.workload == "onion":
         line["thin_lines"] = thin_bench(local, stream.cuda_stream)
+    if rank == 0 and not args.no_rays and args.workload == "onion":
+        line["rays"] = rays_bench(local, stream.cuda_stream)
     if rank == 0 and args.prereduce and args.workload == "onion":
         line["prereduce"] = prereduce_bench(local, stream.cuda_stream, w)
     if rank == 0 and not args.no_nlte and args.workload == "onion":

@@ -78,6 +78,7 @@ struct RayTables {
   const double* __restrict__ bin_frac; // band: [nbin] the bin's share of the band
   const double* __restrict__ Ebin;     // lines: [row][nbin] the cell's emission in the bin
   const double* __restrict__ view;     // [nview][4] direction of the viewer's centre, dOmega / 4 pi
+  const int* __restrict__ win_len;     // [nbin] lines a ray of the bin can reach (staged window)
 };
 
 struct EmitArgs {
@@ -948,6 +949,186 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
   warp_flush(acc, a.ledger, slots);
 }
 
+// ---------------------------------------------------------------- staged rays
+// The RAYS sampler with the line list staged in shared memory.  The rays of
+// one (cell, bin) group start in the same cell at the same comoving frequency
+// nu_j and only ever test lines below it, down to where the largest Doppler
+// drift across the grid can take them; that frequency window of the sorted
+// line records is copied into shared memory by the bulk-copy engine
+// (cp.async.bulk, completion on an mbarrier) once per group, and every ray of
+// the group reads its line records from there (beyond the window, from global
+// memory).  A CTA takes one group at a time; a thread traces a ray to its end.
+// Attenuation mode, no photoionization; the event logic is k_trace's.
+constexpr int kStageLines = 2048;              // window capacity: 64 KB of 32-byte records
+constexpr long long kStageSpin = 1ll << 26;    // bound of the wait for a window
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__global__ void __launch_bounds__(256, 2) k_trace_rays_staged(const TraceArgs a, const int* __restrict__ win_len,
+                                                             int64_t p_end, unsigned long long* __restrict__ err) {
+  extern __shared__ __align__(128) double2 s_lines[];      // kStageLines x 2 double2
+  __shared__ FixExpTables fx;
+  __shared__ int rtab[3 * 1024];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned long long blk_log;
+  __shared__ int s_abort;
+  stage(fx, a.fx);
+  const int nt = a.g.nx + a.g.ny + a.g.nz;
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) rtab[k] = a.rtab[k];
+  if (threadIdx.x == 0) {
+    blk_log = (unsigned long long)a.seg_n[blockIdx.x];
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+  }
+  __syncthreads();
+  const int* RX = rtab;
+  const int* RY = rtab + a.g.nx;
+  const int* RZ = rtab + a.g.nx + a.g.ny;
+  int64_t* const my_log = a.slotlog + (int64_t)blockIdx.x * a.seg_len;
+  const Geometry& g = a.g;
+  const Pool& P = a.pool;
+  const RayTables& T = a.em.ray;
+  const long long taumin_bits = __double_as_longlong(a.tau_min);
+  double acc[T_NACC];
+#pragma unroll
+  for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+  unsigned n_tests = 0, n_events = 0, n_guard = 0;
+  const int64_t rays_per_group = T.nview;
+  const int64_t p_begin = a.em.p_begin;
+  const int64_t g_first = p_begin / rays_per_group, g_last = (p_end + rays_per_group - 1) / rays_per_group;
+  uint32_t phase = 0;
+  for (int64_t gi = g_first + blockIdx.x; gi < g_last; gi += gridDim.x) {
+    const int64_t jb = gi % T.nbin;
+    const int base = T.bin_cursor[jb];
+    const int wl = min(win_len[jb], kStageLines);
+    __syncthreads();                                   // the previous window is no longer read
+    if (threadIdx.x == 0 && wl > 0) {
+      const uint32_t bytes = (uint32_t)wl * 32u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   ::"r"(smem_addr(&bar)), "r"(bytes) : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   ::"r"(smem_addr(s_lines)), "l"(a.lines + 2 * (int64_t)base), "r"(bytes), "r"(smem_addr(&bar))
+                   : "memory");
+    }
+    if (wl > 0) {
+      // every thread waits for the window (bounded: a copy that never lands
+      // sets the error flag and ends the kernel)
+      uint32_t done = 0;
+      for (long long it = 0; it < kStageSpin && !done; ++it)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_addr(&bar)), "r"(phase) : "memory");
+      if (!done) atomicExch(&s_abort, 1);
+      phase ^= 1u;
+    }
+    __syncthreads();
+    if (s_abort) {
+      if (threadIdx.x == 0) atomicAdd(err, 1ull);
+      break;
+    }
+    for (int64_t k = threadIdx.x; k < rays_per_group; k += blockDim.x) {
+      const int64_t rid = gi * rays_per_group + k;
+      if (rid < p_begin || rid >= p_end) continue;
+      const int i = (int)(rid - p_begin);
+      EmitOut o;
+      emit_ray(a.em, rid, o);
+      if (!(o.E0 > 0.0)) {
+        if (a.records) {
+          double* rec = a.records + (rid - a.rec_base) * XT_PKT_FIELDS;
+          rec[0] = 4.0; rec[1] = 0.0; rec[2] = 0.0; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+          rec[6] = 0.0; rec[7] = (double)o.c; rec[8] = 0.0; rec[9] = 0.0; rec[10] = 0.0;
+        }
+        continue;
+      }
+      int ix = o.idx[0], iy = o.idx[1], iz = o.idx[2];
+      double tmx = o.tm[0], tmy = o.tm[1], tmz = o.tm[2];
+      const int sx = bits(o.td[0]) < 0 ? -1 : 1, sy = bits(o.td[1]) < 0 ? -1 : 1, sz = bits(o.td[2]) < 0 ? -1 : 1;
+      const double tdx = dabs_bits(o.td[0]), tdy = dabs_bits(o.td[1]), tdz = dabs_bits(o.td[2]);
+      const double nu0 = o.nu_cmf, aslope = o.nu_lab * a.inv_ct;
+      double N = o.N;
+      const double N_in = N, Tq = (a.em.e_cut * o.E0) * (1.0 / kH);
+      int cursor = o.cursor, events = 0;
+      P.F(F_NX, i) = o.n[0]; P.F(F_NY, i) = o.n[1]; P.F(F_NZ, i) = o.n[2];
+      P.F(F_NULAB, i) = o.nu_lab;
+      P.pid[i] = rid;
+      acc[T_EMITN] += o.N;
+      acc[T_EMITE] += o.E0;
+      if (a.records) {
+        double* rec = a.records + (rid - a.rec_base) * XT_PKT_FIELDS;
+        rec[7] = (double)o.c; rec[8] = o.N; rec[9] = o.nu_cmf;
+      }
+      int row = RX[ix] + RY[iy] + RZ[iz];
+      int fate = -1;
+      bool escaped = false;
+      for (;;) {
+        double sw = tmx;
+        int axis = 0;
+        if (bits(tmy) < bits(sw)) { sw = tmy; axis = 1; }
+        if (bits(tmz) < bits(sw)) { sw = tmz; axis = 2; }
+        const long long end_bits = bits(nu0 - aslope * sw);
+        const double* prow = a.pops + (int64_t)row * a.nlev;
+        for (;;) {
+          if (cursor >= a.nline) break;
+          const int wi = cursor - base;
+          const LineRec L = (wi >= 0 && wi < wl)
+                                ? LineRec{s_lines[2 * wi].x, s_lines[2 * wi].y, s_lines[2 * wi + 1].x, s_lines[2 * wi + 1].y}
+                                : ldline(a.lines, cursor);
+          if (bits(L.x) <= end_bits) break;
+          ++n_tests;
+          const double n_l = prow[__double2loint(L.w)], n_u = prow[__double2hiint(L.w)];
+          const double tau = L.y * (n_l - L.z * n_u);
+          if (bits(tau) > taumin_bits) {
+            ++events;
+            ++n_events;
+            double ex, ome;
+            expneg(fx, tau, ex, ome);
+            atomicAdd(a.S + (int64_t)row * a.nline + cursor, N * ome);
+            const unsigned long long kk = atomicAdd(&blk_log, 1ull);
+            if (kk < (unsigned long long)a.seg_len) my_log[kk] = (int64_t)row * a.nline + cursor;
+            N = N * ex;
+            if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; break; }
+            if (events >= a.max_events) { ++n_guard; fate = 3; break; }
+          }
+          ++cursor;
+        }
+        if (fate >= 0) break;
+        const bool a0 = axis == 0, a1 = axis == 1;
+        const int coord = (a0 ? ix : a1 ? iy : iz) + (a0 ? sx : a1 ? sy : sz);
+        const double tnew = (a0 ? tmx : a1 ? tmy : tmz) + (a0 ? tdx : a1 ? tdy : tdz);
+        if (a0) { ix = coord; tmx = tnew; } else if (a1) { iy = coord; tmy = tnew; } else { iz = coord; tmz = tnew; }
+        if (coord < 0 || coord >= (a0 ? g.nx : a1 ? g.ny : g.nz)) { escaped = true; break; }
+        row = RX[ix] + RY[iy] + RZ[iz];
+      }
+      P.F(F_N, i) = N;
+      P.events[i] = events;
+      acc[T_ABS] += N_in - N;
+      if (fate >= 0 && a.records) {
+        double* rec = a.records + (rid - a.rec_base) * XT_PKT_FIELDS;
+        rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+        rec[6] = 0.0; rec[10] = o.nu_lab;
+      }
+      if (escaped) {
+        P.inter[i] = 0;
+        a.esc[atomicAdd(a.n_esc, 1ull)] = i;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long nb = blk_log;
+    if (nb > (unsigned long long)a.seg_len) atomicAdd(a.log_overflow, 1ull);
+    a.seg_n[blockIdx.x] = (int64_t)(nb < (unsigned long long)a.seg_len ? nb : a.seg_len);
+  }
+  double cnt[3] = {(double)n_tests, (double)n_events, (double)n_guard};
+  const int cslots[3] = {LG_TESTS, LG_EVENTS, LG_GUARD};
+  warp_flush(cnt, a.ledger, cslots);
+  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
+                             LG_EMIT_N, LG_EMIT_E};
+  warp_flush(acc, a.ledger, slots);
+}
+
 // ---------------------------------------------------------------- escape
 __global__ void __launch_bounds__(256) k_escape(const EscArgs a) {
   double acc[3] = {0.0, 0.0, 0.0};
@@ -1251,6 +1432,23 @@ static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, con
     for (int l = 0; l < nl; ++l) bin_of_line[l] = jmap[bin_j[l]];
   }
   const int64_t nbin = (int64_t)bnu.size();
+  // the lines a ray of a bin can reach: its comoving frequency falls by at most
+  // nu_lab s_max / ct with s_max <= 2 sqrt(3) R (the cube's diagonal) and
+  // nu_lab <= nu_j / (1 - sqrt(3) R / ct); a little margin on top
+  std::vector<int> wlen(nbin);
+  {
+    const double b = c->v_max / kC, r3 = std::sqrt(3.0);
+    const double drop = 2.0 * r3 * b / (1.0 - r3 * b) * 1.01 + 1e-9;
+    for (int64_t j = 0; j < nbin; ++j) {
+      const double nu_min = bnu[j] * (1.0 - drop);
+      int lo = bcur[j], hi = nl;                     // first line below nu_min
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (snu[mid] < nu_min) hi = mid; else lo = mid + 1;
+      }
+      wlen[j] = lo - bcur[j];
+    }
+  }
   const int nview = p->n_theta * p->n_phi;
   std::vector<double> view(4 * (size_t)nview);
   for (int it = 0; it < p->n_theta; ++it)
@@ -1270,7 +1468,8 @@ static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, con
   const size_t o_Lc = al(o_frac + 8 * nbin), o_E = al(o_Lc + 8 * (size_t)G.ncell);
   const size_t o_cur = al(o_E + (lines ? 8 * (size_t)G.ncell * nbin : 0));
   const size_t o_bol = al(o_cur + 4 * nbin), o_rc = al(o_bol + 4 * (size_t)nl);
-  const size_t total = al(o_rc + 4 * (size_t)G.ncell);
+  const size_t o_wl = al(o_rc + 4 * (size_t)G.ncell);
+  const size_t total = al(o_wl + 4 * (size_t)nbin);
   int rc;
   if (c->rays_bytes < total) {
     c->rays_bytes = 0;
@@ -1282,6 +1481,7 @@ static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, con
   if (nbin > 0) {
     if ((rc = copy(c, B + o_nu, bnu.data(), 8 * nbin, "ray tables"))) return rc;
     if ((rc = copy(c, B + o_cur, bcur.data(), 4 * nbin, "ray tables"))) return rc;
+    if ((rc = copy(c, B + o_wl, wlen.data(), 4 * nbin, "ray tables"))) return rc;
     if (!lines && (rc = copy(c, B + o_frac, bfrac.data(), 8 * nbin, "ray tables"))) return rc;
   }
   std::vector<double> Lnat;
@@ -1311,6 +1511,7 @@ static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, con
   T.bin_frac = (const double*)(B + o_frac);
   T.Ebin = lines ? (const double*)(B + o_E) : nullptr;
   T.view = (const double*)(B + o_view);
+  T.win_len = (const int*)(B + o_wl);
   Lc_nat = (const double*)(B + o_Lc);
   *n_rays = (int64_t)rcell.size() * nbin * nview;
   return XT_OK;
@@ -1684,6 +1885,18 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   ta.row0 = 0;
   ta.grp_nz = G.nz / NG;
   const bool wr = (p->flags & XT_FLAG_WARP_REDUCE) != 0 && p->mode == XT_MODE_ATTEN && !pi && !rays;
+  const bool staged = rays && !pi && (p->flags & XT_FLAG_RAYS_UNSTAGED) == 0;
+  if (staged) {
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+      XT_CUDA(c, cudaFuncSetAttribute(k_trace_rays_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kStageLines * 32));
+      attr_set[dev] = true;
+    }
+    XT_CUDA(c, cudaMemsetAsync(counters + 5, 0, sizeof(unsigned long long), c->stream));
+  }
   ta.npi = pi ? c->npi : 0;
   ta.pi_nuth = c->d_pi_nuth; ta.pi_sig = c->d_pi_sig; ta.pi_lev = c->d_pi_lev;
   ta.kappa = c->d_kappa; ta.piG = c->d_piG; ta.piD = c->d_piD; ta.piH = c->d_piH;
@@ -1888,7 +2101,12 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
       if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
-      else if (rays) k_trace<XT_MODE_ATTEN, false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (rays && staged) {
+        const int64_t groups = (ea.p_begin + n + ea.ray.nview - 1) / ea.ray.nview - ea.p_begin / ea.ray.nview;
+        const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)grid_max, (int64_t)sm_count() * 2, groups}));
+        k_trace_rays_staged<<<sgrid, 256, kStageLines * 32, c->stream>>>(ta, ea.ray.win_len, ea.p_begin + n,
+                                                                           counters + 5);
+      } else if (rays) k_trace<XT_MODE_ATTEN, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (p->mode == XT_MODE_ATTEN) k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
@@ -1974,6 +2192,12 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     out->trace_ms = kind_ms[1];
     out->escape_ms = kind_ms[2];
     out->kernels = kernels;
+  }
+  if (staged) {
+    unsigned long long stage_err = 0;
+    XT_CUDA(c, cudaMemcpyAsync(&stage_err, counters + 5, sizeof(stage_err), cudaMemcpyDeviceToHost, c->stream));
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (stage_err) return fail(c, XT_ETIMEOUT, "run_transport: a staged line window did not arrive in time");
   }
   if (led[LG_GUARD] > 0)
     return fail(c, XT_ETIMEOUT, "run_transport: " + std::to_string((long long)led[LG_GUARD]) + " packets hit max_events");

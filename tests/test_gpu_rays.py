@@ -68,14 +68,29 @@ def _check(xt, ctx, w, emission="band", nt=9, nph=10, dlog=0.02, pi=False, **kw)
     return st, o
 
 
-@pytest.mark.parametrize("views", [(9, 10), (6, 18)])
-def test_rays_band_emission(xt, views):
+@pytest.mark.parametrize("views,flags", [((9, 10), 0), ((6, 18), 0), ((9, 10), 2)])
+def test_rays_band_emission(xt, views, flags):
+    """flags 0: the line window of every (cell, bin) group staged in shared
+    memory; 2 (XT_FLAG_RAYS_UNSTAGED): line records from global memory."""
     w = synth.uniform_sphere(n=8, n_packets=1, seed=81)
     w.pops = w.pops * 1e-3
     with _ctx(xt) as ctx:
         ctx.load(w)
-        st, o = _check(xt, ctx, w, nt=views[0], nph=views[1])
+        st, o = _check(xt, ctx, w, nt=views[0], nph=views[1], flags=flags)
         assert o["ledger"]["events"] > 10_000
+
+
+def test_rays_staged_window_at_paper_line_density(xt):
+    """1e4 lines over 1000 A - 3 um on a 16^3 onion: each bin's window holds
+    hundreds of line records; staged and unstaged passes give the oracle's
+    estimators and spectrum."""
+    w = synth.clumpy_onion(seed=5, n=16, n_packets=1, n_lines=10_000, level_range=(20, 40),
+                           subdomains=(2, 2, 2))
+    w.pops = w.pops * 1e-6
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        for flags in (0, 2):
+            _check(xt, ctx, w, nt=3, nph=6, dlog=0.05, flags=flags)
 
 
 def test_rays_line_emission_with_photoionization(xt):
