@@ -201,7 +201,13 @@ int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats 
  * estimator rates solves group by group, each group's slab staged (no graph
  * replay, no autotuning there); train_surrogate with estimator inputs
  * returns XT_ESTATE for a host-held store.
+ * host_groups = XT_STORE_COMPACT_ROWS (-1): on the device, with rows only for
+ * the cells that have populations (a cell without matter has no optical depth
+ * and gets no estimator; 1.1e6 of the 2.1e6 cells of a 128^3 cube around a
+ * sphere): the store shrinks by the empty cells' share; readouts give zeros
+ * for the others.  The row map follows the populations of each pass.
  * Frees the current store (host and device); the next run_transport allocates. */
+#define XT_STORE_COMPACT_ROWS (-1)
 int set_estimator_store(xt_ctx *ctx, int32_t host_groups);
 
 /* Raw estimators S [n_cells][nline] (photons/s absorbed, divided by f_corr),

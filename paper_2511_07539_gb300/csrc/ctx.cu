@@ -181,20 +181,21 @@ __global__ void k_tau_beta(Geometry g, LineTable L, const double* __restrict__ p
 __global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops,
                         const double* __restrict__ S, const double* __restrict__ invB,
                         const int* __restrict__ sorted_of, int64_t c0, int64_t nc, double V,
-                        int which, double* __restrict__ out) {
+                        int which, double* __restrict__ out, const int* __restrict__ crow) {
   // a block per cell at a time: the cell's row found once, its lines spread
   // over the threads (output in caller line order, coalesced)
   for (int64_t cl = blockIdx.x; cl < nc; cl += gridDim.x) {
     const int64_t c = c0 + cl;
     const int ix = (int)(c % g.nx), iy = (int)((c / g.nx) % g.ny), iz = (int)(c / ((int64_t)g.nx * g.ny));
     const int64_t row = row_of(g, ix, iy, iz);
-    const double* Sr = S + row * L.nline;
+    const int64_t sr = crow ? (int64_t)crow[row] : row;    // the cell's row in the store (-1: none)
+    const double* Sr = S + (sr < 0 ? 0 : sr) * L.nline;
     const double* pr = pops + row * L.nlev;
     double* o = out + cl * L.nline;
     for (int l = threadIdx.x; l < L.nline; l += blockDim.x) {
       const int s = sorted_of[l];
       // the store holds net photons absorbed; gross = net / f_corr, f_corr = net_pop / n_l
-      const double Snet = Sr[s];
+      const double Snet = sr < 0 ? 0.0 : Sr[s];
       double v = 0.0;
       if (Snet != 0.0) {
         const double nl = pr[L.lo[s]];
@@ -309,7 +310,8 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_counters, (void**)&c->d_hist, (void**)&c->d_rtab, (void**)&c->d_wall, (void**)&c->d_stream_q, (void**)&c->d_slotlog, (void**)&c->d_seg_n,
                    (void**)&c->d_pi_nuth, (void**)&c->d_pi_sig, (void**)&c->d_pi_chi, (void**)&c->d_pi_lev,
                    (void**)&c->d_pi_sorted_of, (void**)&c->d_kappa, (void**)&c->d_piG, (void**)&c->d_piD,
-                   (void**)&c->d_piH, (void**)&c->d_rays, (void**)&c->d_low_off, (void**)&c->d_low_line};
+                   (void**)&c->d_piH, (void**)&c->d_rays, (void**)&c->d_low_off, (void**)&c->d_low_line,
+                   (void**)&c->d_crow};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;
@@ -661,7 +663,7 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
       const int64_t n = (b - a) * c->nline;
       rc = deliver(c, o, (size_t)n * sizeof(double), [&](void* d) {
         k_rates<<<(int)std::max<int64_t>(1, std::min<int64_t>(b - a, 152 * 16)), 256, 0, c->stream>>>(
-            G, L, c->d_pops, Sg, c->d_invB, c->d_orig, a, b - a, V, which, (double*)d);
+            G, L, c->d_pops, Sg, c->d_invB, c->d_orig, a, b - a, V, which, (double*)d, nullptr);
       });
       if (rc) return rc;
       XT_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -671,7 +673,8 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
   size_t bytes = (size_t)nc * c->nline * sizeof(double);
   int rc = deliver(c, out, bytes, [&](void* d) {
     k_rates<<<(int)std::max<int64_t>(1, std::min<int64_t>(nc, 152 * 16)), 256, 0, c->stream>>>(
-        c->geo, L, c->d_pops, c->d_S, c->d_invB, c->d_orig, c0, nc, V, which, (double*)d);
+        c->geo, L, c->d_pops, c->d_S, c->d_invB, c->d_orig, c0, nc, V, which, (double*)d,
+        c->S_compact ? c->d_crow : nullptr);
   });
   if (rc) return rc;
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -681,7 +684,8 @@ static int rates_common(xt_ctx* c, int64_t c0, int64_t nc, double* out, int whic
 int set_estimator_store(xt_ctx* c, int32_t host_groups) {
   if (!c) return XT_EINVAL;
   if (!c->have_grid || !c->have_atoms) return fail(c, XT_ESTATE, "set_estimator_store: init_grid and load_atomic_data first");
-  if (host_groups < 0) return fail(c, XT_EINVAL, "set_estimator_store: host_groups >= 0");
+  if (host_groups < XT_STORE_COMPACT_ROWS)
+    return fail(c, XT_EINVAL, "set_estimator_store: host_groups >= 0 or XT_STORE_COMPACT_ROWS");
   if (host_groups > 0 && (c->sz % host_groups != 0))
     return fail(c, XT_EINVAL, "set_estimator_store: host_groups must divide the subdomains along z (" +
                                   std::to_string(c->sz) + ")");
@@ -693,7 +697,10 @@ int set_estimator_store(xt_ctx* c, int32_t host_groups) {
   c->h_S = nullptr;
   c->h_S_bytes = 0;
   c->S_valid.clear();
-  c->S_groups = host_groups;
+  c->S_compact = host_groups == XT_STORE_COMPACT_ROWS;
+  c->S_groups = host_groups > 0 ? host_groups : 0;
+  c->h_crow.clear();
+  c->n_crow = 0;
   c->have_S = false;
   c->slotlog_valid = true;
   c->slotlog_n = 0;

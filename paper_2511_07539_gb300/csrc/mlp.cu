@@ -452,6 +452,7 @@ struct FeatArgs {
   float* __restrict__ T;                 // [ncell][nlev]
   float* __restrict__ M;                 // [ncell][nlev]
   double V;
+  const int* __restrict__ crow;          // compact store: the cell's row in S, -1 none
 };
 
 // One block per cell: x = ((log10 ne - 7), (log10 Te - 3.7)/0.3, (log10 D + 14),
@@ -473,7 +474,8 @@ __global__ void k_features(const FeatArgs a) {
     if (a.Jline) {
       J = a.Jline[s];
     } else {
-      const double Snet = a.S[row * a.nline + s];
+      const int64_t sr = a.crow ? (int64_t)a.crow[row] : (int64_t)row;
+      const double Snet = sr < 0 ? 0.0 : a.S[sr * a.nline + s];
       const double* L = a.lines + 4 * (int64_t)s;
       const int64_t lu = __double_as_longlong(L[3]);
       const double net = a.pops[row * a.nlev + (int)(lu & 0xFFFFFFFF)] - L[2] * a.pops[row * a.nlev + (int)(lu >> 32)];
@@ -603,6 +605,7 @@ static int build_features(xt_ctx* c, int rates, double jbar_W, double jbar_TR, c
   a.g = G; a.n_ion = c->n_ion; a.nlev = c->nlev; a.nline = c->nline; a.nbin = kJbarBins;
   a.level_off = c->d_level_off; a.ne = c->d_ne; a.Te = c->d_Te; a.dep = c->d_dep; a.nion = c->d_nion;
   a.pops = c->d_pops; a.levels_used = levels_used_dev; a.lines = c->d_lines; a.S = c->d_S;
+  a.crow = c->S_compact ? c->d_crow : nullptr;
   a.Jline = rates == XT_RATES_ESTIMATORS ? nullptr : d_J; a.invB = c->d_invB;
   a.line_ion = d_ion; a.line_bin = d_bin; a.X = X; a.T = T; a.M = M;
   a.V = G.dx * G.dy * G.dz;

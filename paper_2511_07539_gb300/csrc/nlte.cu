@@ -67,6 +67,7 @@ struct SeArgs {
   const int* __restrict__ low_off;      // [nlev + 1] lines by lower level
   const int* __restrict__ low_line;
   const double* __restrict__ S;         // estimators (net photons) [row][sorted line]
+  const int* __restrict__ crow;         // compact store: the cell's row in S, -1 none (nullptr: dense)
   const double* __restrict__ Rj;        // photoexcitation per sorted line (Jbar model)
   int rates;
   double V;
@@ -516,7 +517,8 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           } else if (a.rates == XT_RATES_ESTIMATORS) {
             // fixed per atom: the populations of the transport pass set it
             const double net = pc[off + lo] - Lr[2] * pc[off + u];
-            const double Sv = a.S[row * a.nline + s];
+            const int64_t sr = a.crow ? (int64_t)a.crow[row] : (int64_t)row;
+            const double Sv = sr < 0 ? 0.0 : a.S[sr * a.nline + s];
             if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * a.V);
           }
           W[(int64_t)lo * L + u] += a.A[s] * beta + Lr[2] * Rlu;   // u -> lo
@@ -1016,6 +1018,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.Te = c->d_Te; a.ne = c->d_ne; a.dep = c->d_dep; a.pops = c->d_pops; a.warm = warm;
   a.pops_out = B.pops_new; a.status = B.status; a.lines = c->d_lines; a.A = c->d_A;
   a.down_off = c->d_down_off; a.down_line = c->d_down_line; a.S = c->d_S; a.Rj = B.Rj;
+  a.crow = c->S_compact ? c->d_crow : nullptr;
   a.low_off = c->d_low_off; a.low_line = c->d_low_line;
   a.rates = p->rates; a.V = G.dx * G.dy * G.dz; a.ups = B.ups; a.ups_off = B.upsoff;
   a.levels_used = B.used; a.work = B.work; a.n_work = n_big; a.counter = B.cnt;

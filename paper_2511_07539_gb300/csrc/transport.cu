@@ -146,6 +146,7 @@ struct TraceArgs {
   int64_t row0;                       // first row held by S (a streamed group's slab; else 0)
   int grp_nz;                         // rounds == 2: cells along z per streamed group
   int dom_zlo, dom_zhi;               // rounds == 3: the domain's z layers
+  const int* __restrict__ crow;       // compact store: the cell's row in S, -1 none (nullptr: dense)
   // photoionization (the PI instance): levels sorted by threshold frequency,
   // descending; per-cell suffix sums and accumulators (see pi_segment)
   int npi;
@@ -821,9 +822,10 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
       if (MODE == XT_MODE_ATTEN) {
         // net photons (divided by f_corr at readout), pre-reduced over the lanes
         // of the warp that hit the same slot; the adding lane logs the slot
-        if (warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N * ome, WR)) {
+        const int64_t slot = (a.crow ? (int64_t)a.crow[row] : (int64_t)(row - a.row0)) * a.nline + cursor;
+        if (warp_add_slot(a.S, slot, N * ome, WR)) {
           const unsigned long long k = atomicAdd(&blk_log, 1ull);
-          if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
+          if (k < (unsigned long long)a.seg_len) my_log[k] = slot;
         }
         N = N * ex;
         if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
@@ -835,14 +837,15 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
         uint64_t xw[4];
         draw_raw(a.seed, p, 2 + (uint64_t)nd, xw);
         const U4 w{{u01(xw[0]), u01(xw[1]), u01(xw[2]), u01(xw[3])}};
+        const int64_t slot = (a.crow ? (int64_t)a.crow[row] : (int64_t)(row - a.row0)) * a.nline + cursor;
         {   // every event's slot is logged (interaction or not), as before the draw
           const unsigned long long k = atomicAdd(&blk_log, 1ull);
-          if (k < (unsigned long long)a.seg_len) my_log[k] = (int64_t)row * a.nline + cursor;
+          if (k < (unsigned long long)a.seg_len) my_log[k] = slot;
         }
         if (w.u[0] < ome) {
           P.inter[i] += 1;
           ++n_inter;
-          warp_add_slot(a.S, (int64_t)(row - a.row0) * a.nline + cursor, N, WR);
+          warp_add_slot(a.S, slot, N, WR);
           acc[T_ABS] += N;                    // the whole packet is absorbed
           const double Ecmf = N * kH * L.x;
           acc[T_ABSE] += Ecmf;
@@ -1084,9 +1087,10 @@ __global__ void __launch_bounds__(256, 2) k_trace_rays_staged(const TraceArgs a,
             ++n_events;
             double ex, ome;
             expneg(fx, tau, ex, ome);
-            atomicAdd(a.S + (int64_t)row * a.nline + cursor, N * ome);
+            const int64_t slot = (a.crow ? (int64_t)a.crow[row] : (int64_t)row) * a.nline + cursor;
+            atomicAdd(a.S + slot, N * ome);
             const unsigned long long kk = atomicAdd(&blk_log, 1ull);
-            if (kk < (unsigned long long)a.seg_len) my_log[kk] = (int64_t)row * a.nline + cursor;
+            if (kk < (unsigned long long)a.seg_len) my_log[kk] = slot;
             N = N * ex;
             if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; break; }
             if (events >= a.max_events) { ++n_guard; fate = 3; break; }
@@ -1271,6 +1275,19 @@ __global__ void k_line_emission(Geometry g, const double2* __restrict__ lines,
   }
 }
 
+
+// Compact store: 1 for the rows whose populations are not all zero.
+__global__ void k_row_flags(int64_t nrows, int nlev, const double* __restrict__ pops, int* __restrict__ flag) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const double* pr = pops + r * nlev;
+    bool any = false;
+    for (int l = lane; l < nlev; l += 32) any |= pr[l] != 0.0;
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) flag[r] = any ? 1 : 0;
+  }
+}
 
 // Photoionization: per cell the suffix sums kappa[b] = sum_{k >= b} sig_k n_k
 // over the levels sorted by threshold frequency (descending), kappa[npi] = 0.
@@ -1567,7 +1584,36 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   // one group's slab on the device at a time
   const bool host_store = c->S_groups > 0;
   const int NG = host_store ? c->S_groups : 1;
-  const size_t Sb = (size_t)G.ncell * c->nline * sizeof(double);
+  if (c->S_compact) {
+    // rows only for the cells with populations: the map from this pass's
+    // populations; a new map starts from a zeroed store
+    std::vector<int> flag(G.ncell);
+    {
+      int* d_flag = nullptr;
+      if ((rc = ensure_scratch(c, G.ncell * sizeof(int)))) return rc;
+      d_flag = (int*)c->d_scratch;
+      k_row_flags<<<blocks_for(G.ncell * 32, 256, 16), 256, 0, c->stream>>>(G.ncell, c->nlev, c->d_pops, d_flag);
+      XT_CUDA(c, cudaGetLastError());
+      XT_CUDA(c, cudaMemcpyAsync(flag.data(), d_flag, G.ncell * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    std::vector<int> crow(G.ncell);
+    int64_t nr = 0;
+    for (int64_t r = 0; r < G.ncell; ++r) crow[r] = flag[r] ? (int)nr++ : -1;
+    if (crow != c->h_crow) {
+      if (p->accumulate && !c->h_crow.empty())
+        return fail(c, XT_ESTATE, "run_transport: the cells with populations changed within an accumulating sequence");
+      if (!c->d_crow || (int64_t)c->h_crow.size() != G.ncell) {
+        if ((rc = alloc(c, (void**)&c->d_crow, G.ncell * sizeof(int), "store row map"))) return rc;
+      }
+      if ((rc = copy(c, c->d_crow, crow.data(), G.ncell * sizeof(int), "store row map"))) return rc;
+      c->h_crow = crow;
+      c->n_crow = nr;
+      release((void**)&c->d_S);      // reallocated (and zeroed) below for the new map
+      c->S_bytes = 0;
+    }
+  }
+  const size_t Sb = (size_t)(c->S_compact ? c->n_crow : G.ncell) * c->nline * sizeof(double);
   const size_t slab_b = Sb / NG;
   if (host_store) {
     if (!c->d_S || c->S_bytes != slab_b) {
@@ -1898,6 +1944,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     XT_CUDA(c, cudaMemsetAsync(counters + 5, 0, sizeof(unsigned long long), c->stream));
   }
   ta.npi = pi ? c->npi : 0;
+  ta.crow = c->S_compact ? c->d_crow : nullptr;
   ta.pi_nuth = c->d_pi_nuth; ta.pi_sig = c->d_pi_sig; ta.pi_lev = c->d_pi_lev;
   ta.kappa = c->d_kappa; ta.piG = c->d_piG; ta.piD = c->d_piD; ta.piH = c->d_piH;
   if (host_store) ta.rounds = 2;

@@ -128,6 +128,10 @@ struct xt_ctx {
   double* d_pops = nullptr;          // [row][nlev]
   double* d_S = nullptr;             // [row][sorted line] (host groups: one group's slab)
   size_t S_bytes = 0;
+  bool S_compact = false;            // the store holds rows only for cells with populations:
+  int* d_crow = nullptr;             //   [row] its row in the store, or -1
+  int64_t n_crow = 0;
+  std::vector<int> h_crow;
   int S_groups = 0;                  // > 0: the store lives in pinned host memory in this
   double* h_S = nullptr;             //   many groups of subdomain z-layers (rows contiguous)
   size_t h_S_bytes = 0;

@@ -338,3 +338,41 @@ def test_host_streamed_store_matches_device_store(xt):
             # a cell range that spans two groups
             part = ctx.get_estimators(1000, 3000)
             _cmp_sparse(part, S0[1000:4000], S_TOL, "estimator range")
+
+
+def test_compact_rows_store_matches_dense(xt):
+    """XT_STORE_COMPACT_ROWS holds estimator rows only for cells with
+    populations (here the 2176 cells of the sphere, of 4096): estimators,
+    rates and an estimator-rate solve equal the dense store's, on passes in
+    a row and after the cells with populations change."""
+    w = synth.uniform_sphere(n_packets=60_000, seed=41)
+    w.pops = w.pops * 1e-3
+    ups = synth.collision_strengths(w.upsilon_seed, w.level_off)
+    res = {}
+    for mode in (0, xt.XT_STORE_COMPACT_ROWS):
+        with _ctx(xt) as ctx:
+            ctx.load(w)
+            xt.set_estimator_store(ctx.h, mode)
+            out = []
+            for seed in (41, 42):
+                st = ctx.transport(w, seed=seed)
+                out.append((st["events"], ctx.get_estimators(), ctx.get_photoexcitation_rates()[2]))
+            sz = xt.get_sizes(ctx.h)["store_bytes"]
+            p = np.zeros((w.ncell, w.nlev))
+            xt.solve_nlte(ctx.h, ups, precision=0, rates=xt.XT_RATES_ESTIMATORS, warm=xt.XT_WARM_CURRENT,
+                          pops_out=p)
+            # fewer cells with populations: a new row map
+            pops2 = w.pops.copy()
+            pops2[: w.ncell // 2] = 0.0
+            ctx.set_populations(pops2)
+            st2 = ctx.transport(w, seed=43)
+            res[mode] = (out, sz, p, st2["events"], ctx.get_estimators())
+    (o0, sz0, p0, e0, S0), (o1, sz1, p1, e1, S1) = res[0], res[xt.XT_STORE_COMPACT_ROWS]
+    assert sz1 == 2176 * w.nline * 8 and sz0 == w.ncell * w.nline * 8
+    for a, b in zip(o0, o1):
+        assert a[0] == b[0]
+        _cmp_sparse(b[1], a[1], S_TOL, "compact estimators")
+        _cmp_sparse(b[2], a[2], S_TOL, "compact Jbar")
+    np.testing.assert_allclose(p1, p0, rtol=1e-10)
+    assert e0 == e1
+    _cmp_sparse(S1, S0, S_TOL, "compact estimators after a new row map")
