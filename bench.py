@@ -207,6 +207,39 @@ def rays_bench(local, stream_ptr):
     return out
 
 
+def cfg5_bench(local, stream_ptr, packets=1_000_000_000):
+    """The full-loop scale (128^3 cells, 10 ions, 2e4 lines, 1e9 packets, 4^3
+    subdomains) on one GPU: the dense FP64 store (336 GB) does not fit the
+    device, the store with rows for the cells with matter only (1.1e6 of 2.1e6)
+    does.  Times one transport pass and the estimator-rate solve of every
+    (cell, ion) that follows it (one outer step of the coupled loop)."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    import synth
+    t0 = time.perf_counter()
+    w = synth.clumpy_onion(n=128, n_lines=20_000, n_packets=packets, subdomains=(4, 4, 4))
+    ups = synth.collision_strengths(w.upsilon_seed, w.level_off)
+    gen_s = time.perf_counter() - t0
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    xt.set_estimator_store(ctx.h, xt.XT_STORE_COMPACT_ROWS)
+    st0 = ctx.transport(w)                    # allocations, row map
+    torch.cuda.synchronize()
+    st = ctx.transport(w)
+    sz = xt.get_sizes(ctx.h)
+    sol = xt.solve_nlte(ctx.h, ups, precision=xt.XT_PREC_FP32_IR, rates=xt.XT_RATES_ESTIMATORS,
+                        warm=xt.XT_WARM_CURRENT)
+    free, total = torch.cuda.mem_get_info()
+    ctx.close()
+    return {"workload": w.name, "cells": w.ncell, "cells_with_matter": int((w.rho > 0).sum()),
+            "lines": w.nline, "packets": packets, "generate_s": gen_s,
+            "store_GB": sz["store_bytes"] / 1e9, "dense_store_GB": w.ncell * w.nline * 8 / 1e9,
+            "transport_ms": st["transport_ms"], "events": st["events"],
+            "events_per_s": st["events"] / (st["transport_ms"] * 1e-3),
+            "first_pass_ms": st0["transport_ms"], "solve_ms": sol["solve_ms"], "systems": sol["systems"],
+            "fp64_fallbacks": sol["fp64_fallbacks"], "device_GB_free_after": free / 1e9}
+
+
 def collision_sphere(n_packets=20_000_000):
     """A 16^3 sphere whose 12 lines lie within 5000-5080 A and whose band is
     4990-5100 A: every packet meets most lines, so the lanes of a warp often
@@ -558,6 +591,8 @@ def main():
     ap.add_argument("--only-scatter", action="store_true",
                     help="print the scatter-mode and rates object alone")
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
+    ap.add_argument("--only-cfg5", action="store_true",
+                    help="print the 128^3 full-loop-scale object alone (a pass and a solve)")
     ap.add_argument("--nlte-n", type=int, default=64)
     ap.add_argument("--nlte-once", action="store_true",
                     help="with --only-nlte: one plain mixed-precision launch (profiling case)")
@@ -605,6 +640,11 @@ def main():
         if rank == 0:
             print(json.dumps({"nlte": nlte_bench(local, torch.cuda.current_stream().cuda_stream,
                                                  args.nlte_n)}), flush=True)
+        return
+    if args.only_cfg5:
+        if rank == 0:
+            print(json.dumps({"cfg5": cfg5_bench(local, torch.cuda.current_stream().cuda_stream)}),
+                  flush=True)
         return
     if args.only_scatter:
         if rank == 0:

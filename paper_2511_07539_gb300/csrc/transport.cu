@@ -962,21 +962,22 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
 // the group reads its line records from there (beyond the window, from global
 // memory).  A CTA takes one group at a time; a thread traces a ray to its end.
 // Attenuation mode, no photoionization; the event logic is k_trace's.
-constexpr int kStageLines = 2048;              // window capacity: 64 KB of 32-byte records
+constexpr int kStageLines = 1536;              // window capacity: 48 KB of 32-byte records
+constexpr int kStageRays = 512;                // rays per batch (consecutive bins of one cell)
 constexpr long long kStageSpin = 1ll << 26;    // bound of the wait for a window
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__global__ void __launch_bounds__(256, 2) k_trace_rays_staged(const TraceArgs a, const int* __restrict__ win_len,
+__global__ void __launch_bounds__(256, 3) k_trace_rays_staged(const TraceArgs a, const int* __restrict__ win_len,
                                                              int64_t p_end, unsigned long long* __restrict__ err) {
   extern __shared__ __align__(128) double2 s_lines[];      // kStageLines x 2 double2
   __shared__ FixExpTables fx;
   __shared__ int rtab[3 * 1024];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long blk_log;
-  __shared__ int s_abort;
+  __shared__ int s_abort, s_next;
   stage(fx, a.fx);
   const int nt = a.g.nx + a.g.ny + a.g.nz;
   for (int k = threadIdx.x; k < nt; k += blockDim.x) rtab[k] = a.rtab[k];
@@ -998,15 +999,26 @@ __global__ void __launch_bounds__(256, 2) k_trace_rays_staged(const TraceArgs a,
 #pragma unroll
   for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
   unsigned n_tests = 0, n_events = 0, n_guard = 0;
+  // a batch: up to kStageRays rays of consecutive bins of one cell, whose
+  // windows overlap (the bins' start frequencies fall with the bin index)
   const int64_t rays_per_group = T.nview;
+  const int64_t gpb = max((int64_t)1, (int64_t)kStageRays / rays_per_group);   // groups per batch
+  const int64_t bpc = (T.nbin + gpb - 1) / gpb;                                 // batches per cell
   const int64_t p_begin = a.em.p_begin;
-  const int64_t g_first = p_begin / rays_per_group, g_last = (p_end + rays_per_group - 1) / rays_per_group;
+  const int64_t c_first = p_begin / (rays_per_group * T.nbin);
+  const int64_t c_last = (p_end + rays_per_group * T.nbin - 1) / (rays_per_group * T.nbin);
   uint32_t phase = 0;
-  for (int64_t gi = g_first + blockIdx.x; gi < g_last; gi += gridDim.x) {
-    const int64_t jb = gi % T.nbin;
-    const int base = T.bin_cursor[jb];
-    const int wl = min(win_len[jb], kStageLines);
+  for (int64_t bt = c_first * bpc + blockIdx.x; bt < c_last * bpc; bt += gridDim.x) {
+    const int64_t ci = bt / bpc, j0 = (bt - ci * bpc) * gpb, j1 = min(j0 + gpb, T.nbin);
+    const int64_t r0 = max(p_begin, (ci * T.nbin + j0) * rays_per_group);
+    const int64_t r1 = min(p_end, (ci * T.nbin + j1) * rays_per_group);
+    if (r1 <= r0) continue;                          // (uniform over the CTA)
+    const int base = T.bin_cursor[j0];
+    int hi = base;
+    for (int64_t j = j0; j < j1; ++j) hi = max(hi, T.bin_cursor[j] + win_len[j]);
+    const int wl = min(hi - base, kStageLines);
     __syncthreads();                                   // the previous window is no longer read
+    if (threadIdx.x == 0) s_next = 0;
     if (threadIdx.x == 0 && wl > 0) {
       const uint32_t bytes = (uint32_t)wl * 32u;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1031,9 +1043,11 @@ __global__ void __launch_bounds__(256, 2) k_trace_rays_staged(const TraceArgs a,
       if (threadIdx.x == 0) atomicAdd(err, 1ull);
       break;
     }
-    for (int64_t k = threadIdx.x; k < rays_per_group; k += blockDim.x) {
-      const int64_t rid = gi * rays_per_group + k;
-      if (rid < p_begin || rid >= p_end) continue;
+    const int nr = (int)(r1 - r0);
+    for (;;) {
+      const int k = atomicAdd(&s_next, 1);           // the next ray of the batch
+      if (k >= nr) break;
+      const int64_t rid = r0 + k;
       const int i = (int)(rid - p_begin);
       EmitOut o;
       emit_ray(a.em, rid, o);
@@ -2149,8 +2163,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       sl = tick(1);
       if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && staged) {
-        const int64_t groups = (ea.p_begin + n + ea.ray.nview - 1) / ea.ray.nview - ea.p_begin / ea.ray.nview;
-        const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)grid_max, (int64_t)sm_count() * 2, groups}));
+        const int64_t gpb = std::max<int64_t>(1, kStageRays / ea.ray.nview);
+        const int64_t per_cell = ea.ray.nview * ea.ray.nbin;
+        const int64_t batches = ((ea.p_begin + n + per_cell - 1) / per_cell - ea.p_begin / per_cell) *
+                                ((ea.ray.nbin + gpb - 1) / gpb);
+        const int sgrid = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)grid_max, (int64_t)sm_count() * 3, batches}));
         k_trace_rays_staged<<<sgrid, 256, kStageLines * 32, c->stream>>>(ta, ea.ray.win_len, ea.p_begin + n,
                                                                            counters + 5);
       } else if (rays) k_trace<XT_MODE_ATTEN, false, true><<<grid, 256, 0, c->stream>>>(ta);
