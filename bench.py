@@ -192,18 +192,21 @@ def rays_bench(local, stream_ptr):
     import synth
     w = synth.clumpy_onion(n=32, n_packets=1, subdomains=(4, 4, 4))
     ctx = xt.Context(local, stream_ptr)
-    ctx.load(w)
     kw = dict(sampler=xt.XT_SAMPLER_RAYS, n_theta=10, n_phi=10, spec_dlog=1e-2)
     out = {"workload": w.name + "_rays_10x10_viewers_1pc_bins"}
-    for name, flags in (("staged", 0), ("unstaged", xt.XT_FLAG_RAYS_UNSTAGED)):
-        ctx.transport(w, flags=flags, **kw)
-        st = min((ctx.transport(w, flags=flags, **kw) for _ in range(2)), key=lambda x: x["trace_ms"])
-        out[name] = {"trace_ms": st["trace_ms"], "rays": st["rays"], "events": st["events"],
-                     "tests": st["tests"], "rays_per_s": st["rays"] / (st["trace_ms"] * 1e-3),
-                     "events_per_s": st["events"] / (st["trace_ms"] * 1e-3)}
+    for dens, scale in (("paper_density", 1.0), ("thin_lines", THIN_POP_SCALE)):
+        ctx.load(w, pops=w.pops * scale)
+        res = {}
+        for name, flags in (("staged", 0), ("unstaged", xt.XT_FLAG_RAYS_UNSTAGED)):
+            ctx.transport(w, flags=flags, **kw)
+            st = min((ctx.transport(w, flags=flags, **kw) for _ in range(2)), key=lambda x: x["trace_ms"])
+            res[name] = {"trace_ms": st["trace_ms"], "rays": st["rays"], "events": st["events"],
+                         "tests": st["tests"], "rays_per_s": st["rays"] / (st["trace_ms"] * 1e-3),
+                         "events_per_s": st["events"] / (st["trace_ms"] * 1e-3)}
+        res["speedup_staged"] = res["unstaged"]["trace_ms"] / res["staged"]["trace_ms"]
+        out[dens] = res
     ctx.close()
     torch.cuda.synchronize()
-    out["speedup_staged"] = out["unstaged"]["trace_ms"] / out["staged"]["trace_ms"]
     return out
 
 
