@@ -185,8 +185,10 @@ def thin_bench(local, stream_ptr, passes=3):
 def rays_bench(local, stream_ptr):
     """The RAYS sampler (Sec. 2.3) on the 32^3 onion with the paper-scale line
     list (1e5 lines): rays from every cell centre for every 1 % bin of the
-    band and 10 x 10 viewers, with each group's line window staged in shared
-    memory (default) and with the line list read from global memory."""
+    band and 10 x 10 viewers, with each batch's line window staged in shared
+    memory (XT_FLAG_RAYS_STAGED) and with the line list read through L2
+    (default), at the paper-scale line density and with 1e7 times thinner
+    lines."""
     import torch
     import paper_2511_07539_gb300 as xt
     import synth
@@ -197,7 +199,7 @@ def rays_bench(local, stream_ptr):
     for dens, scale in (("paper_density", 1.0), ("thin_lines", THIN_POP_SCALE)):
         ctx.load(w, pops=w.pops * scale)
         res = {}
-        for name, flags in (("staged", 0), ("unstaged", xt.XT_FLAG_RAYS_UNSTAGED)):
+        for name, flags in (("staged", xt.XT_FLAG_RAYS_STAGED), ("unstaged", 0)):
             ctx.transport(w, flags=flags, **kw)
             st = min((ctx.transport(w, flags=flags, **kw) for _ in range(2)), key=lambda x: x["trace_ms"])
             res[name] = {"trace_ms": st["trace_ms"], "rays": st["rays"], "events": st["events"],

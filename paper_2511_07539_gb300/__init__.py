@@ -23,7 +23,7 @@ XT_MODE_ATTEN, XT_MODE_SCATTER = 0, 1
 XT_EMIT_BAND, XT_EMIT_LINES = 0, 1
 XT_PKT_FIELDS = 11
 XT_FLAG_WARP_REDUCE = 1
-XT_FLAG_RAYS_UNSTAGED = 2
+XT_FLAG_RAYS_STAGED = 2
 XT_STORE_COMPACT_ROWS = -1
 XT_SAMPLER_MC, XT_SAMPLER_RAYS = 0, 1
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",

@@ -70,8 +70,8 @@ def _check(xt, ctx, w, emission="band", nt=9, nph=10, dlog=0.02, pi=False, **kw)
 
 @pytest.mark.parametrize("views,flags", [((9, 10), 0), ((6, 18), 0), ((9, 10), 2)])
 def test_rays_band_emission(xt, views, flags):
-    """flags 0: the line window of every (cell, bin) group staged in shared
-    memory; 2 (XT_FLAG_RAYS_UNSTAGED): line records from global memory."""
+    """flags 0: line records through L2; 2 (XT_FLAG_RAYS_STAGED): the line
+    window of every batch of rays staged in shared memory."""
     w = synth.uniform_sphere(n=8, n_packets=1, seed=81)
     w.pops = w.pops * 1e-3
     with _ctx(xt) as ctx:
