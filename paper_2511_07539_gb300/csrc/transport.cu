@@ -284,12 +284,23 @@ __device__ __forceinline__ bool warp_add_slot(double* __restrict__ S, int64_t sl
   return true;
 }
 
-// Clear the slots listed in each block's log segment.
+// Clear the slots listed in each block's log segment.  Eight slot indices are
+// loaded before their stores, so that a thread keeps eight loads in flight
+// instead of waiting on each (the kernel is bound by that latency).
 __global__ void k_unlog(double* __restrict__ S, const int64_t* __restrict__ log,
                         const int64_t* __restrict__ seg_n, int64_t seg_len) {
   const int64_t n = seg_n[blockIdx.x];
   const int64_t* l = log + (int64_t)blockIdx.x * seg_len;
-  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) S[l[k]] = 0.0;
+  const int64_t B = blockDim.x;
+  int64_t k = threadIdx.x;
+  for (; k + 7 * B < n; k += 8 * B) {
+    int64_t a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = __ldcs(l + k + q * B);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) S[a[q]] = 0.0;
+  }
+  for (; k < n; k += B) S[l[k]] = 0.0;
 }
 
 // ---------------------------------------------------------------- emission
