@@ -36,16 +36,17 @@ BYTES_PER_EVENT = 32          # n_l, n_u reads (16 B) + estimator read-modify-wr
 BYTES_PER_PACKET = 56
 # DRAM bytes (read + write) per event of the attenuation trace kernel (which
 # emits its own packets), from an ncu capture of this kernel version on the
-# 32^3 onion case (829.3 + 497.9 MB over 7,813,774 events); the bench's launch
-# is too large to capture with many passes, and its traffic is taken as
-# proportional to its events.
-TRACE_DRAM_BYTES_PER_EVENT = (829.295872e6 + 497.947648e6) / 7813774
+# 32^3 onion case (829.96 + 496.58 MB over 7,813,774 events;
+# profiles/k_trace_onion32_full.md); the bench's launch is too large to
+# capture with many passes, and its traffic is taken as proportional to its
+# events.
+TRACE_DRAM_BYTES_PER_EVENT = (829.959680e6 + 496.577536e6) / 7813774
 # FP64 thread instructions (DFMA + DMUL + DADD) per event of the same kernel and
 # capture, and the share of cycles its FP64 pipe was busy: GB300 issues FP64
 # arithmetic to 2 lanes per SM and cycle, so the event loop is bound by that
 # pipe long before HBM.
-TRACE_FP64_OPS_PER_EVENT = 3072667.881579 * (16.324111 + 18.969066 + 22.383421) / 7813774
-TRACE_FP64_PIPE_BUSY = 0.58935402
+TRACE_FP64_OPS_PER_EVENT = 3075609.776316 * (16.308496 + 18.950921 + 22.362010) / 7813774
+TRACE_FP64_PIPE_BUSY = 0.58324374
 FP64_LANES_PER_SM_CYCLE = 2
 
 
