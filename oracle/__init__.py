@@ -63,6 +63,8 @@ class _Problem(C.Structure):
                 ("lo", C.c_void_p), ("up", C.c_void_p),
                 ("lambda_A", C.c_void_p), ("f_lu", C.c_void_p),
                 ("ne", C.c_void_p), ("Te", C.c_void_p), ("ups_down", C.c_void_p),
+                ("geometry", C.c_int32), ("r_edges", C.c_void_p), ("th_edges", C.c_void_p),
+                ("ph_edges", C.c_void_p),
                 ("n_pi", C.c_int32), ("pi_level", C.c_void_p), ("pi_Eion", C.c_void_p),
                 ("pi_charge", C.c_void_p)]
 
@@ -105,6 +107,7 @@ def lib():
         _lib.xo_transport_domain.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                              C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.xo_cell_volumes.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.xo_ray_count.restype = C.c_int64
         _lib.xo_ray_count.argtypes = [C.c_void_p, C.c_void_p]
         _lib.xo_tau_beta.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
@@ -134,6 +137,9 @@ class _Keep:
                          lam=_c64(w.lambda_A), f=_c64(w.f_lu), ne=_c64(w.ne), Te=_c64(w.Te),
                          ups=_c64(ups_down if ups_down is not None else np.zeros(w.nlev)))
         a = self.arrs
+        self.sph = getattr(w, "geometry", "cartesian") == "spherical"
+        if self.sph:
+            a.update(re=_c64(w.r_edges), te=_c64(w.theta_edges), pe=_c64(w.phi_edges))
         self.n_pi = 0
         if getattr(w, "pi_nlev", None) is not None:
             import synth
@@ -144,6 +150,7 @@ class _Keep:
                            w.band_A[1], w.nlev, w.nline, _ptr(a["g"]), _ptr(a["E"]),
                            _ptr(a["pops"]), _ptr(a["lo"]), _ptr(a["up"]), _ptr(a["lam"]),
                            _ptr(a["f"]), _ptr(a["ne"]), _ptr(a["Te"]), _ptr(a["ups"]),
+                           1 if self.sph else 0, _ptr(a.get("re")), _ptr(a.get("te")), _ptr(a.get("pe")),
                            self.n_pi, _ptr(a.get("pi_lev")), _ptr(a.get("pi_eion")),
                            _ptr(a.get("pi_ch")))
 
@@ -201,6 +208,8 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     keep = _Keep(w, upsilon_down_sums(w) if mode == "scatter" else None)
     if keep.n_pi and mode != "atten":
         raise ValueError("photoionization is part of the attenuation mode only")
+    if keep.sph and (mode != "atten" or keep.n_pi or sampler != "mc"):
+        raise ValueError("the spherical grid: attenuation mode, Monte Carlo packets, no photoionization")
     S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
     heat = np.zeros(w.ncell) if keep.n_pi else None
     lam0, nbins = w.spec_band_A
@@ -322,6 +331,14 @@ def philox4x64_10(ctr, key):
 
 
 def cell_volume(w):
+    """Cell volume: one number for the Cartesian cube, per cell [ncell] for the
+    spherical grid ((r1^3 - r0^3)/3 (cos theta0 - cos theta1)(phi1 - phi0))."""
+    if getattr(w, "geometry", "cartesian") == "spherical":
+        keep = _Keep(w)
+        pr = _params(w, 0, 0, 0, 0, "atten", "band", 1e-4, 1e-6, 20, 20, 1e-3, 1, "mc")
+        v = np.zeros(w.ncell)
+        lib().xo_cell_volumes(C.byref(keep.pb), C.byref(pr), _ptr(v))
+        return v
     return (2.0 * w.v_max * w.t / w.nx) * (2.0 * w.v_max * w.t / w.ny) * (2.0 * w.v_max * w.t / w.nz)
 
 
@@ -334,6 +351,7 @@ def rates(w, S):
     intensity Jbar = R_lu / B_lu with B_lu = 4 pi (pi e^2 / m_e c) f_lu / (h nu).
     Slots with n_l = 0 give 0."""
     V = cell_volume(w)
+    V = V[:, None] if np.ndim(V) else V
     n_l = w.pops[:, w.lo]
     with np.errstate(divide="ignore", invalid="ignore"):
         R_lu = np.where(n_l > 0, S / (n_l * V), 0.0)

@@ -121,6 +121,11 @@ typedef struct {
     const double *lambda_A, *f_lu; /* [nline] */
     const double *ne, *Te;     /* [ncell] */
     const double *ups_down;    /* [nlev] sum over j<u of Upsilon_ju (SCATTER only) */
+    /* spherical grid: nx, ny, nz cells in r, theta, phi between the edges
+     * (velocities in cm/s, angles in radians; first theta 0, last pi; first
+     * phi 0, last 2 pi); geometry 0: the Cartesian cube */
+    int32_t geometry;
+    const double *r_edges, *th_edges, *ph_edges;
     /* photoionizing levels (Sec. 2.3.1); n_pi = 0: none */
     int32_t n_pi;
     const int32_t *pi_level;   /* [n_pi] global level index */
@@ -159,6 +164,11 @@ typedef struct {
     double *wline;       /* [ncell*nline] line emission weights (emission_mode 1) */
     int32_t *down_off, *down_line;   /* CSR over upper levels of radiative down-lines */
     double *pi_tau;      /* [n_pi] work space of one photoionization segment */
+    /* spherical grid: shell radii (cm), cos theta of the polar edges (flag of an
+     * equatorial edge, crossed as the plane z = 0), cos and sin of the
+     * azimuthal edges (edge nz is edge 0), cell volumes */
+    double *sR, *cth, *cph, *sph, *vol;
+    int32_t *eq;
     /* RAYS sampler: emitting cells, emitting bins, viewing directions */
     int64_t n_rcell;
     int64_t *rcell;      /* natural indices of the cells with L_c > 0 */
@@ -247,9 +257,16 @@ static int prep(prep_t *P, const xo_problem *pb, const xo_params *pr) {
         for (int64_t c = 0; c < P->ncell; c++) P->Lc[c] = pb->L_cell[c];
     } else {
         /* Eq. (thin_emissivity): A_ul dE_ul beta_S N_u, N_u = n_u V_cell */
-        double V = P->dx * P->dy * P->dz;
         P->wline = calloc((size_t)(P->ncell * nl), sizeof(double));
         for (int64_t c = 0; c < P->ncell; c++) {
+            double V = P->dx * P->dy * P->dz;
+            if (pb->geometry == 1) {    /* (prep's spherical tables come later: the volume here) */
+                int32_t ir = (int32_t)(c % pb->nx), it = (int32_t)((c / pb->nx) % pb->ny);
+                int32_t ip = (int32_t)(c / ((int64_t)pb->nx * pb->ny));
+                double r0 = pb->r_edges[ir] * pb->t, r1 = pb->r_edges[ir + 1] * pb->t;
+                V = (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 * (cos(pb->th_edges[it]) - cos(pb->th_edges[it + 1]))
+                    * (pb->ph_edges[ip + 1] - pb->ph_edges[ip]);
+            }
             const double *n = pb->pops + c * pb->nlev;
             double sum = 0.0;
             for (int32_t l = 0; l < nl; l++) {
@@ -267,6 +284,30 @@ static int prep(prep_t *P, const xo_problem *pb, const xo_params *pr) {
     P->qoff = malloc(sizeof(int64_t) * (size_t)(P->ncell + 1));
     xo_packet_quota(P->Lc, P->ncell, pr->n_packets, P->qoff);
     P->pi_tau = calloc((size_t)(pb->n_pi > 0 ? pb->n_pi : 1), sizeof(double));
+    if (pb->geometry == 1) {
+        P->sR = malloc(sizeof(double) * (size_t)(pb->nx + 1));
+        P->cth = malloc(sizeof(double) * (size_t)(pb->ny + 1));
+        P->eq = calloc((size_t)(pb->ny + 1), sizeof(int32_t));
+        P->cph = malloc(sizeof(double) * (size_t)(pb->nz + 1));
+        P->sph = malloc(sizeof(double) * (size_t)(pb->nz + 1));
+        P->vol = malloc(sizeof(double) * (size_t)P->ncell);
+        for (int32_t i = 0; i <= pb->nx; i++) P->sR[i] = pb->r_edges[i] * pb->t;
+        for (int32_t j = 0; j <= pb->ny; j++) {
+            P->cth[j] = cos(pb->th_edges[j]);
+            P->eq[j] = fabs(P->cth[j]) < 1e-12;
+        }
+        for (int32_t k = 0; k <= pb->nz; k++) {
+            double ph = pb->ph_edges[k == pb->nz ? 0 : k];
+            P->cph[k] = cos(ph);
+            P->sph[k] = sin(ph);
+        }
+        for (int64_t c = 0; c < P->ncell; c++) {
+            int32_t ir = (int32_t)(c % pb->nx), it = (int32_t)((c / pb->nx) % pb->ny);
+            int32_t ip = (int32_t)(c / ((int64_t)pb->nx * pb->ny));
+            P->vol[c] = (P->sR[ir + 1] * P->sR[ir + 1] * P->sR[ir + 1] - P->sR[ir] * P->sR[ir] * P->sR[ir]) / 3.0
+                        * (P->cth[it] - P->cth[it + 1]) * (pb->ph_edges[ip + 1] - pb->ph_edges[ip]);
+        }
+    }
     return 0;
 }
 
@@ -275,6 +316,7 @@ static void unprep(prep_t *P) {
     free(P->wline); free(P->down_off); free(P->down_line); free(P->pi_tau);
     free(P->rcell); free(P->rbin_nu); free(P->rbin_cursor); free(P->rbin_frac);
     free(P->rbin_off); free(P->rbin_line); free(P->view_n); free(P->view_w);
+    free(P->sR); free(P->cth); free(P->eq); free(P->cph); free(P->sph); free(P->vol);
 }
 
 static int32_t cursor_at(const prep_t *P, double nu);
@@ -513,6 +555,7 @@ typedef struct {
     double nu_lab, N, E0, N0, nu_cmf0;
     int32_t cursor;
     int64_t events, interactions, ndraw;
+    double s;                           /* spherical grid: path from the emission point r */
 } xo_state;
 #define XO_STATE_FIELDS 21
 
@@ -543,7 +586,17 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
     double d[3] = {P->dx, P->dy, P->dz};
     int32_t idx[3] = {ix, iy, iz};
     double r[3];
-    for (int a = 0; a < 3; a++) r[a] = (-P->R + idx[a] * d[a]) + u[a] * d[a];
+    if (pb->geometry == 1) {
+        /* uniform in the spherical cell: r^3, cos theta and phi uniform */
+        double R0 = P->sR[ix], R1 = P->sR[ix + 1];
+        double rr = cbrt(R0 * R0 * R0 + u[0] * (R1 * R1 * R1 - R0 * R0 * R0));
+        double ct = P->cth[iy] - u[1] * (P->cth[iy] - P->cth[iy + 1]);
+        double ph = pb->ph_edges[iz] + u[2] * (pb->ph_edges[iz + 1] - pb->ph_edges[iz]);
+        double q = 1.0 - ct * ct, st = q > 0.0 ? sqrt(q) : 0.0;
+        r[0] = rr * st * cos(ph); r[1] = rr * st * sin(ph); r[2] = rr * ct;
+    } else {
+        for (int a = 0; a < 3; a++) r[a] = (-P->R + idx[a] * d[a]) + u[a] * d[a];
+    }
     double n[3];
     isotropic(u[3], v[0], n);
     double nu_cmf, nu_lo = XO_C / (pb->band_hi_A * 1e-8), nu_hi = XO_C / (pb->band_lo_A * 1e-8);
@@ -618,6 +671,7 @@ static void propagate(const prep_t *P, int64_t p, int64_t c, int32_t idx[3], dou
     st.E0 = E0; st.N0 = st.N; st.nu_cmf0 = nu_cmf;
     st.cursor = cursor;
     st.events = st.interactions = st.ndraw = 0;
+    st.s = 0.0;
     ledger[L_EMIT_N] += st.N;
     ledger[L_EMIT_E] += E0;
     trace(P, &st, S, spec, ledger, pkt, S_pi, heat, dom);
@@ -629,7 +683,7 @@ static void state_pack(const xo_state *st, double *o) {
     for (int a = 0; a < 3; a++) { o[2 + a] = st->idx[a]; o[5 + a] = st->r[a]; o[8 + a] = st->n[a]; }
     o[11] = st->nu_lab; o[12] = st->N; o[13] = st->E0; o[14] = st->N0; o[15] = st->nu_cmf0;
     o[16] = st->cursor; o[17] = (double)st->events; o[18] = (double)st->interactions;
-    o[19] = (double)st->ndraw; o[20] = 0.0;
+    o[19] = (double)st->ndraw; o[20] = st->s;
 }
 
 static void state_unpack(const double *o, xo_state *st) {
@@ -638,6 +692,172 @@ static void state_unpack(const double *o, xo_state *st) {
     st->nu_lab = o[11]; st->N = o[12]; st->E0 = o[13]; st->N0 = o[14]; st->nu_cmf0 = o[15];
     st->cursor = (int32_t)o[16]; st->events = (int64_t)o[17]; st->interactions = (int64_t)o[18];
     st->ndraw = (int64_t)o[19];
+    st->s = o[20];
+}
+
+/* Spherical grid: the path s > s_cur from the emission point p0 along n at
+ * which the ray leaves cell idx, and through which face (*kind: 0 outer
+ * sphere, 1 inner sphere, 2 lower theta cone, 3 upper theta cone, 4 lower phi
+ * half-plane, 5 upper phi half-plane).  Every face's crossing is computed
+ * from p0 and n alone, so the face just crossed gives exactly s_cur again and
+ * is excluded by s > s_cur.  A cone |z| = cos(theta) |p| counts on its own
+ * nappe only (z of the sign of cos theta); an equatorial edge is the plane
+ * z = 0; a half-plane counts on its own side of the axis. */
+static double cone_cross(const double p0[3], const double n[3], double c, int eq, double b, double pp,
+                         double s_cur) {
+    if (eq) {
+        if (n[2] == 0.0) return INFINITY;
+        double s = -p0[2] / n[2];
+        return s > s_cur ? s : INFINITY;
+    }
+    double c2 = c * c;
+    double A = n[2] * n[2] - c2, B = p0[2] * n[2] - c2 * b, C = p0[2] * p0[2] - c2 * pp;
+    double r[2];
+    int nr = 0;
+    if (A == 0.0) {
+        if (B == 0.0) return INFINITY;
+        r[nr++] = -C / (2.0 * B);
+    } else {
+        double disc = B * B - A * C;
+        if (disc < 0.0) return INFINITY;
+        double sq = sqrt(disc);
+        double s1 = (-B - sq) / A, s2 = (-B + sq) / A;
+        r[nr++] = s1 < s2 ? s1 : s2;
+        r[nr++] = s1 < s2 ? s2 : s1;
+    }
+    for (int k = 0; k < nr; k++)
+        if (r[k] > s_cur && (p0[2] + r[k] * n[2]) * c > 0.0) return r[k];
+    return INFINITY;
+}
+
+static double sph_exit(const prep_t *P, const double p0[3], const double n[3], const int32_t idx[3],
+                       double s_cur, int *kind) {
+    const xo_problem *pb = P->pb;
+    double b = dot3(p0, n), pp = dot3(p0, p0);
+    double best = INFINITY;
+    *kind = -1;
+    double R1 = P->sR[idx[0] + 1];
+    double disc = b * b - (pp - R1 * R1);
+    if (disc > 0.0) {
+        double s = -b + sqrt(disc);
+        if (s > s_cur && s < best) { best = s; *kind = 0; }
+    }
+    if (idx[0] > 0) {
+        double R0 = P->sR[idx[0]];
+        double d0 = b * b - (pp - R0 * R0);
+        if (d0 > 0.0) {
+            double s = -b - sqrt(d0);
+            if (s > s_cur && s < best) { best = s; *kind = 1; }
+        }
+    }
+    for (int e = 0; e < 2; e++) {
+        int32_t j = idx[1] + e;
+        if (j == 0 || j == pb->ny) continue;            /* the polar axis */
+        double s = cone_cross(p0, n, P->cth[j], P->eq[j], b, pp, s_cur);
+        if (s < best) { best = s; *kind = 2 + e; }
+    }
+    if (pb->nz > 1)
+        for (int e = 0; e < 2; e++) {
+            int32_t k = idx[2] + e;
+            double cs = P->cph[k], sn = P->sph[k];
+            double den = n[1] * cs - n[0] * sn;           /* n . (-sin, cos, 0) */
+            if (den == 0.0) continue;
+            double s = -(p0[1] * cs - p0[0] * sn) / den;
+            if (!(s > s_cur) || !(s < best)) continue;
+            double qx = p0[0] + s * n[0], qy = p0[1] + s * n[1];
+            if (qx * cs + qy * sn > 0.0) { best = s; *kind = 4 + e; }
+        }
+    return best;
+}
+
+/* The event loop on the spherical grid (attenuation mode): as in trace, with
+ * the walk through (r, theta, phi) cells; the packet's position is p0 + s n. */
+static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger, double *pkt) {
+    const xo_problem *pb = P->pb;
+    const xo_params *pr = P->pr;
+    double ct = P->ct;
+    int64_t c = st->c;
+    int32_t *idx = st->idx;
+    const double *p0 = st->r, *n = st->n;
+    double nu_lab = st->nu_lab, N = st->N, E0 = st->E0, s = st->s;
+    int32_t cursor = st->cursor;
+    int64_t events = st->events;
+    int fate = 0;
+    double esc_E = 0.0;
+    int32_t vbin = -1;
+    int64_t lbin = -1;
+    for (;;) {
+        int64_t cell = ((int64_t)idx[2] * pb->ny + idx[1]) * pb->nx + idx[0];
+        const double *pc = pb->pops + cell * pb->nlev;
+        int kind;
+        double s_exit = sph_exit(P, p0, n, idx, s, &kind);
+        double r_end[3];
+        for (int a = 0; a < 3; a++) r_end[a] = p0[a] + s_exit * n[a];
+        double nu_end = nu_lab * (1.0 - dot3(n, r_end) / ct);
+        while (cursor < pb->nline && P->nu[cursor] > nu_end) {
+            int32_t l = P->order[cursor];
+            ledger[L_TESTS] += 1.0;
+            double n_l = pc[pb->lo[l]], n_u = pc[pb->up[l]];
+            double g_l = pb->g[pb->lo[l]], g_u = pb->g[pb->up[l]];
+            double lam = pb->lambda_A[l] * 1e-8;
+            double tau = xo_tau_sobolev(P->A[l], g_l, g_u, lam, n_l, n_u, pb->t);
+            if (tau > pr->tau_min) {
+                double nu_l = P->nu[cursor];
+                events++;
+                ledger[L_EVENTS] += 1.0;
+                double f_corr = 1.0 - g_l * n_u / (g_u * n_l);
+                double ex, ome;
+                if (tau > XO_LN2) { ex = exp(-tau); ome = 1.0 - ex; }
+                else { ome = -expm1(-tau); ex = 1.0 - ome; }
+                double dN = N * ome;
+                add_estimator(S, cell, pb->nline, l, dN / f_corr);
+                N = N * ex;
+                ledger[L_ABS_N] += dN;
+                if (N * XO_H * nu_l < pr->e_cut * E0) {
+                    ledger[L_DROP_N] += N;
+                    fate = 1;
+                    goto done;
+                }
+                if (events >= pr->max_events) { fate = 3; ledger[L_GUARD] += 1.0; goto done; }
+            }
+            cursor++;
+        }
+        s = s_exit;
+        if (kind == 0) {
+            if (++idx[0] == pb->nx) {                     /* leaves the outer sphere */
+                double E = N * XO_H * nu_lab;
+                esc_E = E;
+                ledger[L_ESC_N] += N;
+                ledger[L_ESC_E] += E;
+                vbin = xo_viewer_bin(n, pr->n_theta, pr->n_phi);
+                lbin = xo_lambda_bin(XO_C / nu_lab * 1e8, pr->spec_lam0_A, pr->spec_dlog, pr->spec_nbins);
+                if (lbin >= 0) spec[(int64_t)vbin * pr->spec_nbins + lbin] += E;
+                else ledger[L_OOB_E] += E;
+                fate = 0;
+                goto done;
+            }
+        } else if (kind == 1) {
+            idx[0]--;
+        } else if (kind == 2) {
+            idx[1]--;
+        } else if (kind == 3) {
+            idx[1]++;
+        } else if (kind == 4) {
+            idx[2] = idx[2] == 0 ? pb->nz - 1 : idx[2] - 1;
+        } else if (kind == 5) {
+            idx[2] = idx[2] == pb->nz - 1 ? 0 : idx[2] + 1;
+        } else {
+            fate = 3;                                      /* no face ahead (cannot happen inside) */
+            ledger[L_GUARD] += 1.0;
+            goto done;
+        }
+    }
+done:
+    if (pkt) {
+        pkt[0] = fate; pkt[1] = (double)events; pkt[2] = N; pkt[3] = esc_E;
+        pkt[4] = vbin; pkt[5] = (double)lbin; pkt[6] = 0.0; pkt[7] = (double)c;
+        pkt[8] = st->N0; pkt[9] = st->nu_cmf0; pkt[10] = nu_lab;
+    }
 }
 
 /* The event loop from the state st until the packet ends (its record, if
@@ -645,6 +865,10 @@ static void state_unpack(const double *o, xo_state *st) {
  * state then appended to dom->out). */
 static void trace(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger,
                   double *pkt, double *S_pi, double *heat, xo_domain *dom) {
+    if (P->pb->geometry == 1) {
+        trace_sph(P, st, S, spec, ledger, pkt);
+        return;
+    }
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     double d[3] = {P->dx, P->dy, P->dz};
@@ -880,6 +1104,16 @@ int64_t xo_ray_count(const xo_problem *pb, const xo_params *pr) {
     if (rays_prep(&P) == 0) n = P.n_rcell * (int64_t)P.n_rbin * pr->n_theta * pr->n_phi;
     unprep(&P);
     return n;
+}
+
+/* Cell volumes (cm^3) of the spherical grid, natural order. */
+int xo_cell_volumes(const xo_problem *pb, const xo_params *pr, double *vol) {
+    prep_t P;
+    prep(&P, pb, pr);
+    if (pb->geometry == 1) memcpy(vol, P.vol, sizeof(double) * (size_t)P.ncell);
+    else for (int64_t c = 0; c < P.ncell; c++) vol[c] = P.dx * P.dy * P.dz;
+    unprep(&P);
+    return 0;
 }
 
 /* Per-cell luminosity and packet quota as the transport sees them. */

@@ -80,6 +80,12 @@ class Workload:
     levels_used: np.ndarray = None  # [ncell, n_ion] levels kept per (cell, ion); None = all
     jbar_W: float = 0.0           # mean intensity model W B_nu(T_R) for the rate solves
     jbar_TR: float = 0.0
+    # spherical grid (geometry "spherical"): cell edges in velocity (cm/s) and
+    # angle; nx, ny, nz are then the radial, polar and azimuthal cell counts
+    geometry: str = "cartesian"
+    r_edges: np.ndarray = None
+    theta_edges: np.ndarray = None
+    phi_edges: np.ndarray = None
     # photoionization data (None: no photoionizing levels): per ion the
     # ionization energy from its ground level [erg], its charge, and how many of
     # its lowest levels photoionize
@@ -281,6 +287,54 @@ def clumpy_onion(seed: int = 0, n_packets: int = 100_000_000, n: int = 64,
         seed=seed, subdomains=tuple(subdomains),
         spec_band_A=_spectrum_grid(band[0], band[1], v_max),
         meta={"active_cells": int(active.sum()), "levels_per_ion": Ls.tolist()})
+
+
+def spherical_sphere(seed: int = 0, n_packets: int = 100_000, nr: int = 12, nth: int = 8,
+                     nph: int = 12, n_lines: int = 100, n_levels: int = 20,
+                     f_range=(1e-4, 1.0), subdomains=(1, 1, 4), clumps: bool = False) -> Workload:
+    """The plain-method sphere on the paper's kind of grid: nr x nth x nph
+    cells in (r, theta, phi) (Sec. 2: radial shells of equal velocity width,
+    equal polar and azimuthal angles; the paper's validation model has 38 x 15
+    x 30), every cell inside v_max; subdomains are phi slices (Sec. 2.4.1).
+    Uniform density 1e-15 g/cm^3 (with clumps: the lognormal factor of the
+    onion model drawn per cell), Te 5000 K, ne 1e7; the atoms and lines of
+    uniform_sphere; band emission 2900-10000 A with L_cell proportional to the
+    cell's volume (times its density with clumps)."""
+    v_max, t = 5.0e8, 200.0 * DAY
+    ncell = nr * nth * nph
+    rng = np.random.default_rng(seed)
+    E, g, lo, up, lam, f = _synthetic_ion(rng, n_levels, n_lines, (3000.0, 10000.0), f_range,
+                                          unique_pairs=True)
+    r_edges = np.linspace(0.0, v_max, nr + 1)
+    th_edges = np.linspace(0.0, np.pi, nth + 1)
+    ph_edges = np.linspace(0.0, 2.0 * np.pi, nph + 1)
+    # natural order c = (iph * nth + ith) * nr + ir
+    ir = np.tile(np.arange(nr), nth * nph)
+    ith = np.tile(np.repeat(np.arange(nth), nr), nph)
+    iph = np.repeat(np.arange(nph), nr * nth)
+    vol = ((r_edges[ir + 1] ** 3 - r_edges[ir] ** 3) / 3.0 * (np.cos(th_edges[ith]) - np.cos(th_edges[ith + 1]))
+           * (ph_edges[iph + 1] - ph_edges[iph]))
+    fac = np.exp(0.5 * rng.standard_normal(ncell) - 0.125) if clumps else np.ones(ncell)
+    rho = 1e-15 * fac
+    Te = np.full(ncell, 5000.0)
+    ne = 1e7 * fac
+    A = np.array([56.0])
+    n_ion_density = (rho / (A[0] * M_U))[:, None].copy()
+    level_off = np.array([0, n_levels], dtype=np.int32)
+    pops = lte_populations(n_ion_density, level_off, E, g, Te)
+    L_cell = 1e40 * vol * fac / (vol * fac).sum()
+    deposition = L_cell / (vol * t ** 3)
+    band = (2900.0, 10000.0)
+    return Workload(
+        name=f"spherical_sphere_{nr}x{nth}x{nph}_{n_lines}lines_{n_packets}pk", nx=nr, ny=nth, nz=nph,
+        v_max=v_max, t=t, rho=rho, Te=Te, ne=ne, deposition=deposition, L_cell=L_cell,
+        band_A=band, n_ion=1, level_off=level_off, E_level=E, g_level=g,
+        ion_mass_u=A, n_ion_density=n_ion_density,
+        lo=lo.astype(np.int32), up=up.astype(np.int32), lambda_A=lam, f_lu=f,
+        pops=pops, upsilon_seed=seed, n_packets=n_packets, seed=seed,
+        subdomains=tuple(subdomains), spec_band_A=_spectrum_grid(band[0], band[1], v_max),
+        meta={"active_cells": ncell}, geometry="spherical", r_edges=r_edges,
+        theta_edges=th_edges, phi_edges=ph_edges)
 
 
 def single_line_sphere(n: int = 16, n_packets: int = 100_000, seed: int = 3,

@@ -1,0 +1,108 @@
+"""Pins of the oracle on the spherical (r, theta, phi) grid (Sec. 2: the
+paper's models are spherical grids of shells, polar and azimuthal sectors;
+Sec. 2.4.1: phi slices as subdomains), against things other than itself (no
+GPU).
+
+- The cells tile the sphere: their volumes sum to 4/3 pi R^3.
+- Optically thin line emission from a uniform sphere: every packet's lab
+  wavelength follows the first-order Doppler shift of its emission point and
+  direction, and their distribution is the parabolic profile of a uniformly
+  emitting sphere, (3/4)(1 - x^2) in x = (lambda - lambda_l) c / (lambda_l
+  v_max) (chi-square).
+- Optically thin lines: the rates readout's mean intensity per radial shell
+  equals the closed form J(r) of a uniformly emitting sphere (here the grid is
+  the sphere, no voxelised edge), also where the absorbers' density changes
+  from cell to cell (an event booked in the wrong cell would carry the wrong
+  cell's population and break the per-cell mean intensity).
+- The photon ledger closes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+C = 2.99792458e10
+
+
+def test_cells_tile_the_sphere():
+    w = synth.spherical_sphere(nr=7, nth=5, nph=9)
+    V = oracle.cell_volume(w)
+    R = w.v_max * w.t
+    assert V.sum() == pytest.approx(4.0 / 3.0 * np.pi * R ** 3, rel=1e-13)
+    assert np.all(V > 0)
+
+
+def test_thin_line_parabolic_profile():
+    w = synth.spherical_sphere(n_packets=200_000, nr=10, nth=6, nph=8, n_lines=1, n_levels=2, seed=3)
+    w.lambda_A = np.array([5000.0])
+    w.f_lu = np.array([1e-3])
+    w.pops = w.pops * 1e-30                               # no line can absorb
+    w.pops[:, 1] = w.pops[:, 0]                           # upper level populated: it emits
+    w.spec_band_A = synth._spectrum_grid(4800.0, 5200.0, w.v_max)
+    o = oracle.transport(w, emission="lines", per_packet=True)
+    pk = o["pkt"]
+    assert o["ledger"]["events"] == 0 and np.all(pk[:, 0] == 0)
+    lam = C / pk[:, 10] * 1e8
+    x = (lam - 5000.0) / 5000.0 / (w.v_max / C)
+    # first order in v/c: lambda_lab = lambda_l (1 - n.r / ct), |n.r| / ct <= v_max / c
+    assert np.all(np.abs(x) <= 1.0 + 1e-9)
+    edges = np.linspace(-1, 1, 41)
+    cnt, _ = np.histogram(x, edges)
+    F = lambda t: 0.75 * (t - t ** 3 / 3.0) + 0.5
+    expct = len(x) * np.diff(F(edges))
+    chi2 = np.sum((cnt - expct) ** 2 / expct) / len(cnt)
+    assert 0.5 < chi2 < 1.6, chi2
+    # a wrong volume weighting of the emission (e.g. uniform in r) or Doppler
+    # sign moves the moments
+    assert np.mean(x ** 2) == pytest.approx(0.2, abs=0.004)        # <x^2> of (3/4)(1 - x^2)
+    assert abs(np.mean(x)) < 0.004
+
+
+@pytest.mark.parametrize("clumps", [False, True])
+def test_thin_sphere_mean_intensity(clumps):
+    w = synth.spherical_sphere(n_packets=600_000, nr=16, nth=8, nph=12, n_lines=1000, n_levels=50,
+                               seed=41, clumps=clumps)
+    w.v_max = 5e7
+    w.r_edges = w.r_edges * 0.1                           # the grid follows v_max
+    V = oracle.cell_volume(w)
+    w.L_cell = 1e40 * V / V.sum()                         # uniform emissivity
+    nz = w.n_ion_density[:, 0]
+    q = 0.97
+    x = w.g_level * q ** np.arange(w.nlev)
+    w.pops = nz[:, None] * (x / x.sum())[None, :]
+    net = w.pops[0, w.lo] - w.g_level[w.lo] / w.g_level[w.up] * w.pops[0, w.up]
+    tau_t = 10 ** np.random.default_rng(41).uniform(np.log10(5e-4), np.log10(2e-3), w.nline)
+    w.f_lu = tau_t / (oracle.PI_E2_MC * w.lambda_A * 1e-8 * w.t * net)
+    w.f_lu = w.f_lu * (1e-15 / w.rho.max())               # densest cell keeps tau < 2e-3 (clumps)
+    # no Sobolev optical depth cut: in the thinnest cells of the clumpy model
+    # the lines fall below the default 1e-4
+    o = oracle.transport(w, tau_min=1e-12)
+    _, _, J = oracle.rates(w, o["S"])
+    R = w.v_max * w.t
+    rc = 0.5 * (w.r_edges[:-1] + w.r_edges[1:]) * w.t
+    ir = np.tile(np.arange(w.nx), w.ny * w.nz)
+    r = rc[ir]
+    dnu = C / (w.band_A[0] * 1e-8) - C / (w.band_A[1] * 1e-8)
+    j = 1e40 / V.sum() / (4 * np.pi * dnu)
+    J_exact = j * R / 2 * (1 + (R * R - r * r) / (2 * r * R) * np.log((R + r) / (R - r)))
+    Jc = J.mean(axis=1)
+    for a, b in [(0, 0.3), (0.3, 0.5), (0.5, 0.7), (0.7, 0.9)]:
+        m = (r / R >= a) & (r / R < b)
+        ratio = Jc[m].sum() / J_exact[m].sum()
+        assert ratio == pytest.approx(1.0, abs=0.03), (a, b, ratio)
+    if clumps:
+        # the mean intensity does not follow the absorbers' density
+        m = r / R < 0.8
+        rel = Jc[m] / J_exact[m]
+        cc = np.corrcoef(np.log(w.rho[m]), rel)[0, 1]
+        assert abs(cc) < 0.2, cc
+
+
+def test_ledger_closes():
+    w = synth.spherical_sphere(n_packets=40_000, seed=9, clumps=True)
+    w.pops = w.pops * 1e-3
+    o = oracle.transport(w)
+    L = o["ledger"]
+    assert L["events"] > 10_000 and L["guard"] == 0
+    assert L["esc_N"] + L["abs_N"] + L["drop_N"] == pytest.approx(L["emit_N"], rel=1e-13)
