@@ -52,6 +52,8 @@ void xt_destroy(xt_ctx *ctx);
 const char *xt_last_error(const xt_ctx *ctx);
 
 /* ---- grid (Sec. 2: snapshot, homologous v = r/t) ------------------------ */
+#define XT_GEOM_CARTESIAN 0   /* the cube [-v_max t, v_max t]^3 of nx x ny x nz equal cells */
+#define XT_GEOM_SPHERICAL 1   /* shells x polar sectors x azimuthal sectors (Sec. 2) */
 typedef struct {
     int32_t nx, ny, nz;     /* cells per axis; the cube spans [-v_max t, v_max t]^3 */
     int32_t sx, sy, sz;     /* subdomains per axis (Sec. 2.4.1); must divide nx, ny, nz */
@@ -63,6 +65,21 @@ typedef struct {
     const double *L_cell;   /* [ncell] erg/s emitted in the flat-nu band (may be NULL) */
     const double *deposition; /* [ncell] erg/s/cm^3 non-thermal input (may be NULL) */
     double band_lo_A, band_hi_A;  /* emission band of L_cell, flat in frequency */
+    /* Spherical grid (geometry = XT_GEOM_SPHERICAL; the paper's models are
+     * spherical grids of radial shells, polar and azimuthal sectors, Sec. 2,
+     * with subdomains that are azimuthal slices, Sec. 2.4.1): nx, ny, nz count
+     * the cells in r, theta and phi, cell c = (iphi * ny + itheta) * nx + ir,
+     * and sx, sy, sz block that index space as for the cube (phi slices:
+     * sx = sy = 1).  r_edges [nx+1] velocities in cm/s, strictly increasing
+     * from 0 to v_max (the shell radii are r_edges t); theta_edges [ny+1]
+     * radians, strictly increasing from 0 to pi; phi_edges [nz+1] radians,
+     * strictly increasing from 0 to 2 pi.  Host or device memory, read during
+     * the call.  With XT_GEOM_CARTESIAN the three are ignored (may be NULL).
+     * Every cell volume the readouts use (rates, the rate solve, line
+     * emission) is then the spherical cell's, (r1^3 - r0^3) / 3 (cos theta0 -
+     * cos theta1) (phi1 - phi0). */
+    int32_t geometry;
+    const double *r_edges, *theta_edges, *phi_edges;
 } xt_grid_desc;
 int init_grid(xt_ctx *ctx, const xt_grid_desc *g);
 
@@ -187,6 +204,15 @@ typedef struct {
     double rays;            /* XT_SAMPLER_RAYS: rays of the whole enumeration */
 } xt_transport_stats;
 
+/* On a spherical grid (XT_GEOM_SPHERICAL) run_transport takes attenuation
+ * mode with Monte Carlo packets, without subdomain rounds and without
+ * photoionization data, with the estimator store on the device (dense or
+ * compact rows); other passes, and run_transport_domain, return XT_EINVAL.
+ * Packets start uniformly in their cell's volume (r^3, cos theta and phi
+ * uniform) and walk from cell to cell through the shells' spheres, the polar
+ * edges' cones (the plane z = 0 for theta = pi/2) and the azimuthal edges'
+ * half-planes; every crossing is taken from the packet's emission point and
+ * direction, so that a face met twice gives the same path length both times. */
 int run_transport(xt_ctx *ctx, const xt_transport_params *p, xt_transport_stats *out);
 
 /* Where the estimator store lives (Sec. 2.4.1: the photoexcitation store is

@@ -26,6 +26,7 @@ XT_FLAG_WARP_REDUCE = 1
 XT_FLAG_RAYS_STAGED = 2
 XT_STORE_COMPACT_ROWS = -1
 XT_SAMPLER_MC, XT_SAMPLER_RAYS = 0, 1
+XT_GEOM_CARTESIAN, XT_GEOM_SPHERICAL = 0, 1
 PKT_FIELDS = ["fate", "events", "N_final", "esc_E", "viewer", "lbin", "interactions", "cell",
               "N0", "nu_cmf0", "nu_lab"]
 
@@ -42,7 +43,9 @@ class GridDesc(C.Structure):
                 ("v_max", C.c_double), ("t", C.c_double),
                 ("rho", C.c_void_p), ("Te", C.c_void_p), ("ne", C.c_void_p),
                 ("L_cell", C.c_void_p), ("deposition", C.c_void_p),
-                ("band_lo_A", C.c_double), ("band_hi_A", C.c_double)]
+                ("band_lo_A", C.c_double), ("band_hi_A", C.c_double),
+                ("geometry", C.c_int32), ("r_edges", C.c_void_p), ("theta_edges", C.c_void_p),
+                ("phi_edges", C.c_void_p)]
 
 
 class AtomDesc(C.Structure):
@@ -263,9 +266,19 @@ def xt_last_error(ctx):
 
 
 def init_grid(ctx, nx, ny, nz, v_max, t, Te, ne, L_cell=None, band_A=(0.0, 0.0), rho=None,
-              deposition=None, subdomains=(1, 1, 1)):
+              deposition=None, subdomains=(1, 1, 1), spherical_edges=None):
+    """spherical_edges = (r_edges [nx+1] cm/s, theta_edges [ny+1], phi_edges
+    [nz+1] radians) selects the spherical grid; None the cube."""
     keep = [_f64(x) for x in (rho, Te, ne, L_cell, deposition)]
-    d = GridDesc(nx, ny, nz, *subdomains, v_max, t, *[_ptr(x) for x in keep], *band_A)
+    geom, edges = XT_GEOM_CARTESIAN, [None, None, None]
+    if spherical_edges is not None:
+        geom = XT_GEOM_SPHERICAL
+        edges = [_f64(e) for e in spherical_edges]
+        for e, n_, what in zip(edges, (nx, ny, nz), ("r_edges", "theta_edges", "phi_edges")):
+            if e.size != n_ + 1:
+                raise ValueError(f"init_grid: {what} needs {n_ + 1} entries, got {e.size}")
+    d = GridDesc(nx, ny, nz, *subdomains, v_max, t, *[_ptr(x) for x in keep], *band_A, geom,
+                 *[_ptr(e) for e in edges])
     _check(ctx, lib().init_grid(ctx, C.byref(d)))
 
 
@@ -616,8 +629,11 @@ class Context:
         """init_grid + load_atomic_data + set_populations from a workload object
         (attributes as produced by the input generator)."""
         sd = tuple(subdomains) if subdomains is not None else tuple(w.subdomains)
+        edges = None
+        if getattr(w, "geometry", "cartesian") == "spherical":
+            edges = (w.r_edges, w.theta_edges, w.phi_edges)
         init_grid(self.h, w.nx, w.ny, w.nz, w.v_max, w.t, w.Te, w.ne, w.L_cell, w.band_A,
-                  rho=w.rho, deposition=w.deposition, subdomains=sd)
+                  rho=w.rho, deposition=w.deposition, subdomains=sd, spherical_edges=edges)
         load_atomic_data(self.h, w.level_off, w.E_level, w.g_level, w.lo, w.up, w.lambda_A,
                          w.f_lu, n_ion_density=w.n_ion_density, ups_down=with_scatter_data,
                          chi_ion=getattr(w, "chi_ion", None), charge=getattr(w, "charge", None),

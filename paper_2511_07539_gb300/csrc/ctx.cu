@@ -192,6 +192,7 @@ __global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops
     const double* Sr = S + (sr < 0 ? 0 : sr) * L.nline;
     const double* pr = pops + row * L.nlev;
     double* o = out + cl * L.nline;
+    const double Vc = g.vol ? g.vol[row] : V;
     for (int l = threadIdx.x; l < L.nline; l += blockDim.x) {
       const int s = sorted_of[l];
       // the store holds net photons absorbed; gross = net / f_corr, f_corr = net_pop / n_l
@@ -203,7 +204,7 @@ __global__ void k_rates(Geometry g, LineTable L, const double* __restrict__ pops
         if (which == 0) {
           v = Snet * nl / net;
         } else {
-          const double R = Snet / (net * V);         // S / (n_l V)
+          const double R = Snet / (net * Vc);        // S / (n_l V)
           v = which == 1 ? R : which == 2 ? L.gratio[s] * R : R * invB[s];
         }
       }
@@ -311,7 +312,7 @@ void xt_destroy(xt_ctx* c) {
                    (void**)&c->d_pi_nuth, (void**)&c->d_pi_sig, (void**)&c->d_pi_chi, (void**)&c->d_pi_lev,
                    (void**)&c->d_pi_sorted_of, (void**)&c->d_kappa, (void**)&c->d_piG, (void**)&c->d_piD,
                    (void**)&c->d_piH, (void**)&c->d_rays, (void**)&c->d_low_off, (void**)&c->d_low_line,
-                   (void**)&c->d_crow};
+                   (void**)&c->d_crow, (void**)&c->d_vol, (void**)&c->d_sph};
   for (void** p : ptrs) release(p);
   if (c->h_S) cudaFreeHost(c->h_S);
   c->h_S = nullptr;
@@ -346,6 +347,33 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
   if (!g->Te || !g->ne) return fail(c, XT_EINVAL, "init_grid: Te and ne are required");
   if (g->L_cell && !(g->band_hi_A > g->band_lo_A && g->band_lo_A > 0))
     return fail(c, XT_EINVAL, "init_grid: band_lo_A < band_hi_A required with L_cell");
+  if (g->geometry != XT_GEOM_CARTESIAN && g->geometry != XT_GEOM_SPHERICAL)
+    return fail(c, XT_EINVAL, "init_grid: geometry must be XT_GEOM_CARTESIAN or XT_GEOM_SPHERICAL");
+  const bool sph = g->geometry == XT_GEOM_SPHERICAL;
+  // spherical grid: edges checked before anything of the context changes
+  std::vector<double> re, te, pe, tab, vol_nat;
+  if (sph) {
+    if (!g->r_edges || !g->theta_edges || !g->phi_edges)
+      return fail(c, XT_EINVAL, "init_grid: a spherical grid needs r_edges, theta_edges and phi_edges");
+    re.resize(g->nx + 1); te.resize(g->ny + 1); pe.resize(g->nz + 1);
+    int rc0;
+    if ((rc0 = copy(c, re.data(), g->r_edges, re.size() * sizeof(double), "r_edges"))) return rc0;
+    if ((rc0 = copy(c, te.data(), g->theta_edges, te.size() * sizeof(double), "theta_edges"))) return rc0;
+    if ((rc0 = copy(c, pe.data(), g->phi_edges, pe.size() * sizeof(double), "phi_edges"))) return rc0;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    auto increasing = [](const std::vector<double>& e, double last) {
+      if (e[0] != 0.0) return false;
+      for (size_t i = 1; i < e.size(); ++i)
+        if (!(e[i] > e[i - 1]) || !std::isfinite(e[i])) return false;
+      return std::fabs(e.back() - last) <= 1e-12 * last;
+    };
+    if (!increasing(re, g->v_max))
+      return fail(c, XT_EINVAL, "init_grid: r_edges must increase strictly from 0 to v_max");
+    if (!increasing(te, kPi))
+      return fail(c, XT_EINVAL, "init_grid: theta_edges must increase strictly from 0 to pi");
+    if (!increasing(pe, 2.0 * kPi))
+      return fail(c, XT_EINVAL, "init_grid: phi_edges must increase strictly from 0 to 2 pi");
+  }
   Geometry& G = c->geo;
   G.nx = g->nx; G.ny = g->ny; G.nz = g->nz;
   G.bx = g->nx / g->sx; G.by = g->ny / g->sy; G.bz = g->nz / g->sz;
@@ -359,6 +387,49 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
   c->v_max = g->v_max; c->t = g->t;
   c->band_lo_A = g->band_lo_A; c->band_hi_A = g->band_hi_A;
   int rc;
+  G.vol = nullptr;
+  G.sph = nullptr;
+  c->geometry = g->geometry;
+  if (!sph) {
+    release((void**)&c->d_vol);
+    release((void**)&c->d_sph);
+    c->h_sph.clear();
+  } else {
+    // the walk's tables (shell radii, cos theta with equatorial edges exactly
+    // 0, cos and sin phi with edge nz taken as edge 0, phi) and the volumes
+    // (r1^3 - r0^3) / 3 (cos theta0 - cos theta1) (phi1 - phi0), natural order
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    tab.assign((size_t)(nx + 1) + (ny + 1) + 3 * (size_t)(nz + 1), 0.0);
+    double* sR = tab.data();
+    double* cth = sR + nx + 1;
+    double* cph = cth + ny + 1;
+    double* sphi = cph + nz + 1;
+    double* phe = sphi + nz + 1;
+    std::vector<double> ct_raw(ny + 1);
+    for (int i = 0; i <= nx; ++i) sR[i] = re[i] * g->t;
+    for (int j = 0; j <= ny; ++j) {
+      ct_raw[j] = std::cos(te[j]);
+      cth[j] = std::fabs(ct_raw[j]) < 1e-12 ? 0.0 : ct_raw[j];
+    }
+    for (int k = 0; k <= nz; ++k) {
+      const double ph = pe[k == nz ? 0 : k];
+      cph[k] = std::cos(ph);
+      sphi[k] = std::sin(ph);
+      phe[k] = pe[k];
+    }
+    vol_nat.resize(G.ncell);
+    for (int64_t cc = 0; cc < G.ncell; ++cc) {
+      const int ir = (int)(cc % nx), it = (int)((cc / nx) % ny), ip = (int)(cc / ((int64_t)nx * ny));
+      vol_nat[cc] = (sR[ir + 1] * sR[ir + 1] * sR[ir + 1] - sR[ir] * sR[ir] * sR[ir]) / 3.0 *
+                    (ct_raw[it] - ct_raw[it + 1]) * (pe[ip + 1] - pe[ip]);
+    }
+    if ((rc = alloc(c, (void**)&c->d_sph, tab.size() * sizeof(double), "spherical tables"))) return rc;
+    if ((rc = copy(c, c->d_sph, tab.data(), tab.size() * sizeof(double), "spherical tables"))) return rc;
+    if ((rc = upload_rows(c, vol_nat.data(), &c->d_vol, 1, "cell volumes"))) return rc;
+    c->h_sph = tab;
+    G.vol = c->d_vol;
+    G.sph = c->d_sph;
+  }
   if ((rc = upload_rows(c, g->Te, &c->d_Te, 1, "Te"))) return rc;
   if ((rc = upload_rows(c, g->ne, &c->d_ne, 1, "ne"))) return rc;
   if (g->rho && (rc = upload_rows(c, g->rho, &c->d_rho, 1, "rho"))) return rc;

@@ -479,7 +479,8 @@ __global__ void k_features(const FeatArgs a) {
       const double* L = a.lines + 4 * (int64_t)s;
       const int64_t lu = __double_as_longlong(L[3]);
       const double net = a.pops[row * a.nlev + (int)(lu & 0xFFFFFFFF)] - L[2] * a.pops[row * a.nlev + (int)(lu >> 32)];
-      J = (Snet != 0.0 && net > 0.0) ? Snet / (net * a.V) * a.invB[s] : 0.0;
+      const double Vc = a.g.vol ? a.g.vol[row] : a.V;
+      J = (Snet != 0.0 && net > 0.0) ? Snet / (net * Vc) * a.invB[s] : 0.0;
     }
     if (J > 0.0) {
       const int k = a.line_ion[s] * a.nbin + a.line_bin[s];

@@ -70,7 +70,7 @@ struct SeArgs {
   const int* __restrict__ crow;         // compact store: the cell's row in S, -1 none (nullptr: dense)
   const double* __restrict__ Rj;        // photoexcitation per sorted line (Jbar model)
   int rates;
-  double V;
+  double V;                             // cell volume of the cube (a spherical grid's: g.vol[row])
   const double* __restrict__ ups;       // per ion [L_z][L_z]
   const int64_t* __restrict__ ups_off;
   const int* __restrict__ levels_used;  // [cell * n_ion + z] or nullptr
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
             const double net = pc[off + lo] - Lr[2] * pc[off + u];
             const int64_t sr = a.crow ? (int64_t)a.crow[row] : (int64_t)row;
             const double Sv = sr < 0 ? 0.0 : a.S[sr * a.nline + s];
-            if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * a.V);
+            if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * (a.g.vol ? a.g.vol[row] : a.V));
           }
           W[(int64_t)lo * L + u] += a.A[s] * beta + Lr[2] * Rlu;   // u -> lo
           W[(int64_t)u * L + lo] += Rlu;                            // lo -> u

@@ -370,10 +370,9 @@ __device__ __forceinline__ void emit_ray(const EmitArgs& a, int64_t rid, EmitOut
   }
 }
 
-__device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTables& trig, int64_t p,
-                                            EmitOut& o) {
-  const Geometry& g = a.g;
-  int64_t lo = 0, hi = g.ncell;           // last c with qoff[c] <= p
+// The emitting cell of packet p: the last c with qoff[c] <= p.
+__device__ __forceinline__ int64_t quota_cell(const EmitArgs& a, int64_t p) {
+  int64_t lo = 0, hi = a.g.ncell;
   if (a.qguide) {                         // qoff[lo] <= p < qoff[hi]
     const int64_t j = p >> kQGuideShift;
     lo = a.qguide[j];
@@ -383,7 +382,48 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
     const int64_t mid = (lo + hi) >> 1;
     if (a.qoff[mid] <= p) lo = mid; else hi = mid;
   }
-  const int64_t c = lo;
+  return lo;
+}
+
+// Comoving frequency and first line to test of a packet of cell c (natural
+// index, cell indices idx) from its uniform draw xv1: flat in nu over the
+// band, or a line picked by its share of the cell's line emission (the packet
+// then starts past that line).
+__device__ __forceinline__ void emit_frequency(const EmitArgs& a, uint64_t xv1, int64_t c, const int idx[3],
+                                               double& nu_cmf, int& cursor) {
+  const double v1 = u01(xv1);
+  if (a.emission == XT_EMIT_BAND) {
+    nu_cmf = fma(v1, a.nu_span, a.nu_lo);   // the guide's edges use the same fma
+    int l0 = 0, l1 = a.nline;             // first sorted line with nu <= nu_cmf
+    if (a.nuguide) {                      // nu_cmf lies between its bucket's edges
+      const int j = (int)((xv1 >> 11) >> kNuGuideShift);
+      l0 = a.nuguide[j + 1];
+      l1 = a.nuguide[j];
+    }
+    const long long nb = bits(nu_cmf);
+    while (l0 < l1) {
+      const int mid = (l0 + l1) >> 1;
+      if (bits(a.nu_tab[mid]) <= nb) l1 = mid; else l0 = mid + 1;
+    }
+    cursor = l0;
+  } else {
+    const double* cdf = a.cdf + row_of(a.g, idx[0], idx[1], idx[2]) * a.nline;
+    const double x = v1 * a.Lc[c];
+    int l0 = 0, l1 = a.nline;             // first caller line with x < cdf
+    while (l0 < l1) {
+      const int mid = (l0 + l1) >> 1;
+      if (x < cdf[mid]) l1 = mid; else l0 = mid + 1;
+    }
+    const int s = a.sorted_of[l0 < a.nline ? l0 : a.nline - 1];
+    nu_cmf = a.nu_tab[s];
+    cursor = s + 1;
+  }
+}
+
+__device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTables& trig, int64_t p,
+                                            EmitOut& o) {
+  const Geometry& g = a.g;
+  const int64_t c = quota_cell(a, p);
   o.c = c;
   {                                       // cell indices in 32-bit arithmetic (ncell < 2^30)
     const uint32_t c32 = (uint32_t)c, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
@@ -404,33 +444,7 @@ __device__ __forceinline__ void emit_packet(const EmitArgs& a, const FixTrigTabl
     o.r[k] = w0 + uu[k] * d[k];
   }
   isotropic(trig, xu[3] >> 11, xv[0] >> 11, o.n);
-  const double v1 = u01(xv[1]);
-  if (a.emission == XT_EMIT_BAND) {
-    o.nu_cmf = fma(v1, a.nu_span, a.nu_lo);   // the guide's edges use the same fma
-    int l0 = 0, l1 = a.nline;             // first sorted line with nu <= nu_cmf
-    if (a.nuguide) {                      // nu_cmf lies between its bucket's edges
-      const int j = (int)((xv[1] >> 11) >> kNuGuideShift);
-      l0 = a.nuguide[j + 1];
-      l1 = a.nuguide[j];
-    }
-    const long long nb = bits(o.nu_cmf);
-    while (l0 < l1) {
-      const int mid = (l0 + l1) >> 1;
-      if (bits(a.nu_tab[mid]) <= nb) l1 = mid; else l0 = mid + 1;
-    }
-    o.cursor = l0;
-  } else {
-    const double* cdf = a.cdf + row_of(g, o.idx[0], o.idx[1], o.idx[2]) * a.nline;
-    const double x = v1 * a.Lc[c];
-    int l0 = 0, l1 = a.nline;             // first caller line with x < cdf
-    while (l0 < l1) {
-      const int mid = (l0 + l1) >> 1;
-      if (x < cdf[mid]) l1 = mid; else l0 = mid + 1;
-    }
-    const int s = a.sorted_of[l0 < a.nline ? l0 : a.nline - 1];
-    o.nu_cmf = a.nu_tab[s];
-    o.cursor = s + 1;
-  }
+  emit_frequency(a, xv[1], c, o.idx, o.nu_cmf, o.cursor);
   const double* n = o.n;
   const double* r = o.r;
   // the quotients on the integer pipe (div_pos, within 0.51 ulp): GB300's FP64
@@ -1161,6 +1175,269 @@ __global__ void __launch_bounds__(256, 3) k_trace_rays_staged(const TraceArgs a,
   warp_flush(acc, a.ledger, slots);
 }
 
+// ---------------------------------------------------------------- spherical grid
+// The attenuation pass on a spherical grid (Sec. 2: radial shells, polar and
+// azimuthal sectors).  A thread owns one packet at a time: it emits it (cell
+// from the quota, a point uniform in the cell's volume, isotropic direction,
+// comoving frequency as on the cube) and walks it from face to face until it
+// escapes or ends, then takes the next one.  The walk's coordinate is the path
+// s from the emission point p0 along n; every face's crossing is solved from
+// p0 and n alone (b = p0.n, pp = p0.p0 per packet), so the face just crossed
+// gives exactly the current s again and is excluded by s > s_cur: no nudging
+// and no accumulated error.  Within a cell the lines between the comoving
+// frequency now and at the exit face are tested as in k_trace; escaped
+// packets go to k_escape through the pool.
+struct SphTables {
+  const double *sR, *cth, *cph, *sph, *phe;   // see Geometry::sph
+  int nx, ny, nz;
+};
+
+// First crossing s > s_cur of the cone |z| = c |p| on its own nappe (z of the
+// sign of c), or of the plane z = 0 for c = 0 (an equatorial edge); INFINITY
+// if there is none.  The quadratic (n_z^2 - c^2) s^2 + 2 (p0_z n_z - c^2 b) s
+// + (p0_z^2 - c^2 pp) = 0.
+__device__ __noinline__ double sph_cone(const double p0[3], const double n[3], double c, double b,
+                                        double pp, double s_cur) {
+  if (c == 0.0) {
+    if (n[2] == 0.0) return INFINITY;
+    const double s = -p0[2] / n[2];
+    return s > s_cur ? s : INFINITY;
+  }
+  const double c2 = c * c;
+  const double A = n[2] * n[2] - c2, B = p0[2] * n[2] - c2 * b, C = p0[2] * p0[2] - c2 * pp;
+  double r0, r1 = INFINITY;
+  if (A == 0.0) {
+    if (B == 0.0) return INFINITY;
+    r0 = -C / (2.0 * B);
+  } else {
+    const double disc = B * B - A * C;
+    if (disc < 0.0) return INFINITY;
+    const double sq = sqrt(disc);
+    const double s1 = (-B - sq) / A, s2 = (-B + sq) / A;
+    r0 = fmin(s1, s2);
+    r1 = fmax(s1, s2);
+  }
+  if (r0 > s_cur && (p0[2] + r0 * n[2]) * c > 0.0) return r0;
+  if (r1 > s_cur && r1 < INFINITY && (p0[2] + r1 * n[2]) * c > 0.0) return r1;
+  return INFINITY;
+}
+
+// Path at which the packet leaves cell (ir, it, ip), and through which face
+// (kind 0 outer sphere, 1 inner sphere, 2 lower polar edge, 3 upper polar
+// edge, 4 lower azimuthal edge, 5 upper azimuthal edge; -1 none).  The polar
+// axis (edges 0 and ny) is no face; an azimuthal edge is the half-plane on its
+// own side of the axis; with one azimuthal sector there are none.
+__device__ __forceinline__ double sph_exit(const SphTables& T, const double p0[3], const double n[3], double b,
+                                           double pp, int ir, int it, int ip, double s_cur, int& kind) {
+  double best = INFINITY;
+  kind = -1;
+  const double R1 = T.sR[ir + 1];
+  const double d1 = b * b - (pp - R1 * R1);
+  if (d1 > 0.0) {
+    const double s = -b + sqrt(d1);
+    if (s > s_cur) { best = s; kind = 0; }
+  }
+  if (ir > 0) {
+    const double R0 = T.sR[ir];
+    const double d0 = b * b - (pp - R0 * R0);
+    if (d0 > 0.0) {
+      const double s = -b - sqrt(d0);
+      if (s > s_cur && s < best) { best = s; kind = 1; }
+    }
+  }
+#pragma unroll 1
+  for (int e = 0; e < 2; ++e) {
+    const int j = it + e;
+    if (j == 0 || j == T.ny) continue;
+    const double s = sph_cone(p0, n, T.cth[j], b, pp, s_cur);
+    if (s < best) { best = s; kind = 2 + e; }
+  }
+  if (T.nz > 1) {
+#pragma unroll 1
+    for (int e = 0; e < 2; ++e) {
+      const int k = ip + e;
+      const double cs = T.cph[k], sn = T.sph[k];
+      const double den = n[1] * cs - n[0] * sn;          // n . (-sin phi, cos phi, 0)
+      if (den == 0.0) continue;
+      const double s = -(p0[1] * cs - p0[0] * sn) / den;
+      if (!(s > s_cur) || !(s < best)) continue;
+      const double qx = p0[0] + s * n[0], qy = p0[1] + s * n[1];
+      if (qx * cs + qy * sn > 0.0) { best = s; kind = 4 + e; }
+    }
+  }
+  return best;
+}
+
+// Warp-aggregated counter increment by the lanes that reach it together:
+// returns this lane's value.
+__device__ __forceinline__ unsigned long long take_next(unsigned long long* ctr) {
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(act) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(act));
+  base = __shfl_sync(act, base, leader);
+  return base + __popc(act & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
+  __shared__ FixExpTables fx;
+  __shared__ FixTrigTables trig;
+  __shared__ unsigned long long blk_log;
+  stage(fx, a.fx);
+  stage(trig, a.trig);
+  if (threadIdx.x == 0) blk_log = (unsigned long long)a.seg_n[blockIdx.x];
+  __syncthreads();
+  int64_t* const my_log = a.slotlog + (int64_t)blockIdx.x * a.seg_len;
+  const Geometry& g = a.g;
+  const EmitArgs& em = a.em;
+  const Pool& P = a.pool;
+  SphTables T;
+  T.nx = g.nx; T.ny = g.ny; T.nz = g.nz;
+  T.sR = g.sph; T.cth = T.sR + g.nx + 1; T.cph = T.cth + g.ny + 1; T.sph = T.cph + g.nz + 1;
+  T.phe = T.sph + g.nz + 1;
+  const int* RX = a.rtab;
+  const int* RY = a.rtab + g.nx;
+  const int* RZ = a.rtab + g.nx + g.ny;
+  const long long taumin_bits = bits(a.tau_min);
+  // a straight path meets each sphere and cone at most twice, each half-plane once
+  const int max_faces = 2 * (g.nx + g.ny) + g.nz + 8;
+  double acc[T_NACC];
+#pragma unroll
+  for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+  unsigned n_tests = 0, n_events = 0, n_guard = 0;
+  for (;;) {
+    const unsigned long long my = take_next(a.counter);
+    if (my >= (unsigned long long)a.n_list) break;
+    const int i = (int)my;
+    const int64_t p = em.p_begin + (int64_t)my;
+    // ---- emission
+    const int64_t c = quota_cell(em, p);
+    int idx[3];
+    {
+      const uint32_t c32 = (uint32_t)c, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+      const uint32_t cy = c32 / nx;
+      idx[0] = (int)(c32 - cy * nx); idx[1] = (int)(cy % ny); idx[2] = (int)(cy / ny);
+    }
+    uint64_t xu[4], xv[4];
+    draw_raw(em.seed, p, 0, xu);
+    draw_raw(em.seed, p, 1, xv);
+    double p0[3], n[3];
+    {   // uniform in the cell's volume: r^3, cos theta and phi uniform
+      const double R0 = T.sR[idx[0]], R1 = T.sR[idx[0] + 1];
+      const double R03 = R0 * R0 * R0, R13 = R1 * R1 * R1;
+      const double rr = cbrt(R03 + u01(xu[0]) * (R13 - R03));
+      const double c0 = T.cth[idx[1]], c1 = T.cth[idx[1] + 1];
+      const double ct = c0 - u01(xu[1]) * (c0 - c1);
+      const double ph0 = T.phe[idx[2]], ph1 = T.phe[idx[2] + 1];
+      const double ph = ph0 + u01(xu[2]) * (ph1 - ph0);
+      double sp, cp;
+      sincos(ph, &sp, &cp);
+      const double q = 1.0 - ct * ct;
+      const double st = q > 0.0 ? sqrt(q) : 0.0;
+      p0[0] = rr * st * cp; p0[1] = rr * st * sp; p0[2] = rr * ct;
+    }
+    isotropic(trig, xu[3] >> 11, xv[0] >> 11, n);
+    double nu_cmf;
+    int cursor;
+    emit_frequency(em, xv[1], c, idx, nu_cmf, cursor);
+    const double b = n[0] * p0[0] + n[1] * p0[1] + n[2] * p0[2];
+    const double pp = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
+    const double nu_lab = div_pos(nu_cmf, 1.0 - b * a.inv_ct);
+    const double aslope = nu_lab * a.inv_ct;           // d nu_cmf / ds
+    double N = div_pos(em.Eph[c], nu_cmf);             // E0 / (h nu_cmf)
+    const double N_in = N;
+    const double Tq = em.e_cut * em.Eph[c];
+    P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
+    P.F(F_NULAB, i) = nu_lab;
+    P.pid[i] = p;
+    acc[T_EMITN] += N;
+    acc[T_EMITE] += em.Epk[c];
+    if (a.records) {
+      P.inter[i] = 0;
+      double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+      rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
+    }
+    // ---- walk
+    int ix = idx[0], iy = idx[1], iz = idx[2];
+    int row = RX[ix] + RY[iy] + RZ[iz];
+    int events = 0, fate = -1;
+    bool escaped = false;
+    double s = 0.0;
+    for (int faces = 0;; ++faces) {
+      int kind;
+      const double s_exit = sph_exit(T, p0, n, b, pp, ix, iy, iz, s, kind);
+      if (kind < 0 || faces >= max_faces) { ++n_guard; fate = 3; break; }
+      const long long end_bits = bits(nu_cmf - aslope * s_exit);
+      const double* prow = a.pops + (int64_t)row * a.nlev;
+      while (cursor < a.nline) {
+        const LineRec L = ldline(a.lines, cursor);
+        if (bits(L.x) <= end_bits) break;
+        ++n_tests;
+        const double n_l = prow[__double2loint(L.w)], n_u = prow[__double2hiint(L.w)];
+        const double tau = L.y * (n_l - L.z * n_u);
+        if (bits(tau) > taumin_bits) {
+          ++events;
+          ++n_events;
+          double ex, ome;
+          expneg(fx, tau, ex, ome);
+          const int64_t slot = (a.crow ? (int64_t)a.crow[row] : (int64_t)row) * a.nline + cursor;
+          atomicAdd(a.S + slot, N * ome);
+          const unsigned long long k = atomicAdd(&blk_log, 1ull);
+          if (k < (unsigned long long)a.seg_len) my_log[k] = slot;
+          N = N * ex;
+          if (bits(N * L.x) < bits(Tq)) { acc[T_DROP] += N; fate = 1; }
+          else if (events >= a.max_events) { ++n_guard; fate = 3; }
+        }
+        ++cursor;
+        if (fate >= 0) break;
+      }
+      if (fate >= 0) break;
+      s = s_exit;
+      if (kind == 0) {
+        if (++ix == g.nx) { escaped = true; break; }
+      } else if (kind == 1) {
+        --ix;
+      } else if (kind == 2) {
+        --iy;
+      } else if (kind == 3) {
+        ++iy;
+      } else if (kind == 4) {
+        iz = iz == 0 ? g.nz - 1 : iz - 1;
+      } else {
+        iz = iz == g.nz - 1 ? 0 : iz + 1;
+      }
+      row = RX[ix] + RY[iy] + RZ[iz];
+    }
+    // ---- the packet leaves the thread
+    P.F(F_N, i) = N;
+    P.events[i] = events;
+    acc[T_ABS] += N_in - N;
+    if (fate >= 0 && a.records) {
+      double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+      rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+      rec[6] = 0.0; rec[10] = nu_lab;
+    }
+    if (escaped) {
+      const unsigned long long k = take_next(a.n_esc);
+      a.esc[k] = i;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long nb = blk_log;
+    if (nb > (unsigned long long)a.seg_len) atomicAdd(a.log_overflow, 1ull);
+    a.seg_n[blockIdx.x] = (int64_t)(nb < (unsigned long long)a.seg_len ? nb : a.seg_len);
+  }
+  __syncwarp();
+  double cnt[3] = {(double)n_tests, (double)n_events, (double)n_guard};
+  const int cslots[3] = {LG_TESTS, LG_EVENTS, LG_GUARD};
+  warp_flush(cnt, a.ledger, cslots);
+  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
+                             LG_EMIT_N, LG_EMIT_E};
+  warp_flush(acc, a.ledger, slots);
+}
+
 // ---------------------------------------------------------------- escape
 __global__ void __launch_bounds__(256) k_escape(const EscArgs a) {
   double acc[3] = {0.0, 0.0, 0.0};
@@ -1290,13 +1567,14 @@ __global__ void k_line_emission(Geometry g, const double2* __restrict__ lines,
     const int64_t row = row_of(g, ix, iy, iz);
     const double* pc = pops + row * nlev;
     double* cr = cdf + row * nline;
+    const double Vc = g.vol ? g.vol[row] : V;
     double run = 0.0;
     for (int l = 0; l < nline; ++l) {
       const int s = sorted_of[l];
       const LineRec L = ldline(lines, s);
       const double nu_ = pc[__double2hiint(L.w)];
       const double tau = L.y * (pc[__double2loint(L.w)] - L.z * nu_);
-      run += A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * V;
+      run += A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * Vc;
       cr[l] = run;
     }
     Lc[c] = run;
@@ -1576,6 +1854,12 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   if (p->n_theta < 1 || p->n_phi < 1 || p->spec_nbins < 1 || !(p->spec_lam0_A > 0) || !(p->spec_dlog > 0))
     return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
+  const bool sph = c->geometry == XT_GEOM_SPHERICAL;
+  if (sph && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->dom.active ||
+              c->npi > 0))
+    return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode with Monte Carlo packets, "
+                              "without subdomain rounds, packet states between domains or photoionization data, "
+                              "with the estimator store on the device");
   RayTables rtab_rays{};
   const double* ray_Lc = nullptr;
   int64_t n_total = p->n_packets;
@@ -1830,7 +2114,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   c->have_pi = pi;
 
   int occ = 0;
-  if (rays && pi)
+  if (sph)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_sph, 256, 0);
+  else if (rays && pi)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true, true>, 256, 0);
   else if (rays)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, false, true>, 256, 0);
@@ -2175,7 +2461,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph) k_trace_sph<<<grid, 256, 0, c->stream>>>(ta);
+      else if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && staged) {
         const int64_t gpb = std::max<int64_t>(1, kStageRays / ea.ray.nview);
         const int64_t per_cell = ea.ray.nview * ea.ray.nbin;
@@ -2278,7 +2565,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     if (stage_err) return fail(c, XT_ETIMEOUT, "run_transport: a staged line window did not arrive in time");
   }
   if (led[LG_GUARD] > 0)
-    return fail(c, XT_ETIMEOUT, "run_transport: " + std::to_string((long long)led[LG_GUARD]) + " packets hit max_events");
+    return fail(c, XT_ETIMEOUT, "run_transport: " + std::to_string((long long)led[LG_GUARD]) +
+                                    (sph ? " packets hit max_events or the walk's face limit" : " packets hit max_events"));
   return XT_OK;
 }
 

@@ -34,6 +34,12 @@ struct Geometry {
   int sx, sy;            // subdomains per axis (x, y)
   int64_t ncell;
   double R, dx, dy, dz, ct, inv_ct;
+  // spherical grid (both nullptr for the cube): cell volumes [row], and the
+  // walk's tables [shell radii (nx+1) | cos theta (ny+1), exactly 0 for an
+  // equatorial edge | cos phi (nz+1) | sin phi (nz+1) | phi (nz+1)], edge nz
+  // of the azimuthal tables being edge 0 again for cos and sin
+  const double* vol = nullptr;
+  const double* sph = nullptr;
 };
 
 struct LineTable {        // lines in descending-frequency ("sorted") order
@@ -78,6 +84,10 @@ struct xt_ctx {
   double* d_rho = nullptr;
   double* d_dep = nullptr;
   double* d_L = nullptr;             // row order
+  int geometry = XT_GEOM_CARTESIAN;
+  double* d_vol = nullptr;           // spherical grid: cell volumes, row order
+  double* d_sph = nullptr;           //   and the walk's tables (Geometry::sph)
+  std::vector<double> h_sph;
   // atoms
   bool have_atoms = false;
   int n_ion = 0, nlev = 0, nline = 0;
