@@ -213,6 +213,46 @@ def rays_bench(local, stream_ptr):
     return out
 
 
+SPH_POP_SCALE = 1e-6
+
+
+def paper_sphere(n_packets=20_000_000):
+    """The paper's spherical grid (38 x 15 x 30 zones in r, theta, phi; Sec.
+    2) in 30 azimuthal slices, lognormal clumps, one ion of 200 levels with 1e4
+    lines, level populations scaled by 1e-6 (about 35 interaction points per
+    packet, 40 % of the packets escape)."""
+    import synth
+    w = synth.spherical_sphere(n_packets=n_packets, seed=23, nr=38, nth=15, nph=30, n_lines=10_000,
+                               n_levels=200, subdomains=(1, 1, 30), clumps=True)
+    w.pops = w.pops * SPH_POP_SCALE
+    w.name = w.name + f"_pops_x{SPH_POP_SCALE:g}"
+    return w
+
+
+def sph_bench(local, stream_ptr, passes=3, n_packets=20_000_000):
+    """The attenuation pass on the paper's spherical grid: events/s and the
+    trace kernel's algorithmic HBM rate at 32 B per event."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    w = paper_sphere(n_packets)
+    peaks, _ = _measured_peaks()
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    ctx.transport(w)
+    sts = [ctx.transport(w) for _ in range(passes)]
+    torch.cuda.synchronize()
+    ctx.close()
+    ev = float(np.mean([s["events"] for s in sts]))
+    tr = float(np.mean([s["trace_ms"] for s in sts]))
+    dev = float(np.mean([s["transport_ms"] for s in sts]))
+    ach = BYTES_PER_EVENT * ev / (tr * 1e-3) / 1e9
+    return {"workload": w.name, "packets": w.n_packets, "cells": w.ncell, "events_per_pass": ev,
+            "tests_per_pass": float(np.mean([s["tests"] for s in sts])),
+            "events_per_packet": ev / w.n_packets, "pass_device_ms": dev, "trace_ms": tr,
+            "value": ev / (dev * 1e-3), "unit": UNIT, "packets_per_s": w.n_packets / (dev * 1e-3),
+            "trace_GB_per_s": ach, "frac_hbm": ach / peaks["hbm_gbs"], "kernel": "k_trace_sph"}
+
+
 def cfg5_bench(local, stream_ptr, packets=1_000_000_000):
     """The full-loop scale (128^3 cells, 10 ions, 2e4 lines, 1e9 packets, 4^3
     subdomains) on one GPU: the dense FP64 store (336 GB) does not fit the
@@ -585,6 +625,9 @@ def main():
                     choices=["onion", "onion-small", "onion-thin", "sphere"])
     ap.add_argument("--no-thin", action="store_true", help="skip the thin-line measurement")
     ap.add_argument("--no-rays", action="store_true", help="skip the RAYS-sampler measurement")
+    ap.add_argument("--no-sph", action="store_true", help="skip the spherical-grid measurement")
+    ap.add_argument("--only-sph", action="store_true", help="print the spherical-grid object alone")
+    ap.add_argument("--sph-packets", type=int, default=20_000_000)
     ap.add_argument("--prereduce", action="store_true",
                     help="also time the trace kernel with and without the warp pre-reduction")
     ap.add_argument("--no-nlte", action="store_true", help="skip the rate-solve measurement")
@@ -651,6 +694,11 @@ def main():
         if rank == 0:
             print(json.dumps({"cfg5": cfg5_bench(local, torch.cuda.current_stream().cuda_stream)}),
                   flush=True)
+        return
+    if args.only_sph:
+        if rank == 0:
+            print(json.dumps({"spherical": sph_bench(local, torch.cuda.current_stream().cuda_stream,
+                                                     n_packets=args.sph_packets)}), flush=True)
         return
     if args.only_scatter:
         if rank == 0:
@@ -780,6 +828,8 @@ def main():
         line["thin_lines"] = thin_bench(local, stream.cuda_stream)
     if rank == 0 and not args.no_rays and args.workload == "onion":
         line["rays"] = rays_bench(local, stream.cuda_stream)
+    if rank == 0 and not args.no_sph and args.workload == "onion":
+        line["spherical"] = sph_bench(local, stream.cuda_stream, n_packets=args.sph_packets)
     if rank == 0 and args.prereduce and args.workload == "onion":
         line["prereduce"] = prereduce_bench(local, stream.cuda_stream, w)
     if rank == 0 and not args.no_nlte and args.workload == "onion":

@@ -1177,107 +1177,125 @@ __global__ void __launch_bounds__(256, 3) k_trace_rays_staged(const TraceArgs a,
 
 // ---------------------------------------------------------------- spherical grid
 // The attenuation pass on a spherical grid (Sec. 2: radial shells, polar and
-// azimuthal sectors).  A thread owns one packet at a time: it emits it (cell
-// from the quota, a point uniform in the cell's volume, isotropic direction,
-// comoving frequency as on the cube) and walks it from face to face until it
-// escapes or ends, then takes the next one.  The walk's coordinate is the path
-// s from the emission point p0 along n; every face's crossing is solved from
-// p0 and n alone (b = p0.n, pp = p0.p0 per packet), so the face just crossed
-// gives exactly the current s again and is excluded by s > s_cur: no nudging
-// and no accumulated error.  Within a cell the lines between the comoving
-// frequency now and at the exit face are tested as in k_trace; escaped
-// packets go to k_escape through the pool.
-struct SphTables {
-  const double *sR, *cth, *cph, *sph, *phe;   // see Geometry::sph
-  int nx, ny, nz;
-};
+// azimuthal sectors).  The walk's coordinate is the path s from the emission
+// point p0 along n; every face crossing is a root of a quadratic (a sphere or
+// a polar cone) or a linear equation (the equatorial plane, an azimuthal
+// half-plane) in s whose coefficients come from p0 and n alone (b = p0.n,
+// pp = p0.p0 per packet), solved by one routine, so that a face solved again
+// gives exactly the path at which it was crossed and is excluded by s > s_cur:
+// no nudging and no accumulated error.  The three families of faces (shells,
+// polar edges, azimuthal edges) keep their next crossing; crossing a face
+// changes only its own family's faces, so only that family is solved again.
+// Within a family one face is solved first: along a straight line phi is
+// monotonic (the side is the sign of (p0 x n)_z), d cos(theta) / ds changes sign
+// at most once (its numerator nz pp - z0 b + s (nz b - z0) is linear in s),
+// and a shell's inner sphere can only be met while r decreases (s < -b); the
+// other face of the family is solved only when the first has no crossing.
+// The persistent warp loop follows k_trace: a lane walks its packet one face
+// per iteration, testing the lines between the comoving frequency now and at
+// that face (as in k_trace), and empty lanes are refilled together with fresh
+// packets (emission: cell from the quota, a point uniform in the cell's volume,
+// isotropic direction, comoving frequency as on the cube).  Escaped packets go
+// to k_escape through the pool.
+constexpr int kSphRefill = 16;   // empty lanes of a warp that trigger a refill
 
-// First crossing s > s_cur of the cone |z| = c |p| on its own nappe (z of the
-// sign of c), or of the plane z = 0 for c = 0 (an equatorial edge); INFINITY
-// if there is none.  The quadratic (n_z^2 - c^2) s^2 + 2 (p0_z n_z - c^2 b) s
-// + (p0_z^2 - c^2 pp) = 0.
-__device__ __noinline__ double sph_cone(const double p0[3], const double n[3], double c, double b,
-                                        double pp, double s_cur) {
-  if (c == 0.0) {
-    if (n[2] == 0.0) return INFINITY;
-    const double s = -p0[2] / n[2];
-    return s > s_cur ? s : INFINITY;
-  }
-  const double c2 = c * c;
-  const double A = n[2] * n[2] - c2, B = p0[2] * n[2] - c2 * b, C = p0[2] * p0[2] - c2 * pp;
-  double r0, r1 = INFINITY;
-  if (A == 0.0) {
-    if (B == 0.0) return INFINITY;
-    r0 = -C / (2.0 * B);
+enum { SF_INNER, SF_OUTER, SF_CONE, SF_PLANE, SF_HALF };
+
+// Next crossing s > s_cur (s_cur >= 0) of face family fam (0 shells, 1 polar
+// edges, 2 azimuthal edges) from cell (ir, it, ip), and the face (kind 0 outer
+// sphere, 1 inner sphere, 2 lower polar edge, 3 upper polar edge, 4 lower
+// azimuthal edge, 5 upper azimuthal edge; -1 and INFINITY for none).  Every
+// face is A s^2 + 2 B s + C = 0 (a sphere A = 1, B = b, C = pp - R^2; a cone;
+// A = 0 for a plane), solved with one square root and one reciprocal for all
+// of them, so that the lanes of a warp on different families stay together;
+// comparisons are on the bit patterns (integer pipe: the FP64 pipe, 2 lanes
+// per SM and cycle, is the scarce one).  For a sphere the reciprocal is 1 and
+// the roots are -b -/+ sqrt(disc) exactly.  Not inlined: every crossing of the
+// kernel is solved by this one code.
+__device__ __noinline__ double sph_next(const double* __restrict__ tab, int tnx, int tny, int tnz, int fam,
+                                        double p0x, double p0y, double p0z, double nx_, double ny_,
+                                        double nz_, double b, double pp, int ir, int it, int ip,
+                                        double s_cur, int* kind_out) {
+  const double* sR = tab;
+  const double* cth = sR + tnx + 1;
+  const double* cph = cth + tny + 1;
+  const double* sph = cph + tnz + 1;
+  const long long scb = bits(s_cur);
+  const long long infb = bits(INFINITY);
+  int k;
+  if (fam == 0) {
+    k = (ir > 0 && bits(-b) > scb) ? 1 : 0;                          // r decreasing: s < -b
+  } else if (fam == 1) {
+    const double g = nz_ * pp - p0z * b + s_cur * (nz_ * b - p0z);   // sign of d cos(theta) / ds
+    k = bits(g) > 0 ? 2 : 3;
+    const int j = it + k - 2;
+    if (j == 0 || j == tny) k = 5 - k;                                // the polar axis is no face
+    const int j2 = it + k - 2;
+    if (j2 == 0 || j2 == tny) k = -1;
   } else {
+    k = tnz < 2 ? -1 : (bits(p0x * ny_ - p0y * nx_) > 0 ? 5 : 4);
+  }
+  for (int att = 0; att < 2 && k >= 0; ++att) {
+    double A, B, C, u = 0.0, v = 0.0;
+    int side;
+    if (k <= 1) {
+      const double R = sR[ir + 1 - k];
+      A = 1.0; B = b; C = pp - R * R;
+      side = k == 1 ? SF_INNER : SF_OUTER;
+    } else if (k <= 3) {
+      const double c = cth[it + k - 2];
+      if ((bits(c) << 1) == 0) {                                      // the plane z = 0
+        A = 0.0; B = 0.5 * nz_; C = p0z;
+        side = SF_PLANE;
+      } else {
+        const double c2 = c * c;
+        A = nz_ * nz_ - c2; B = p0z * nz_ - c2 * b; C = p0z * p0z - c2 * pp;
+        side = SF_CONE;
+        u = c;
+      }
+    } else {
+      const int e = ip + k - 4;
+      u = cph[e]; v = sph[e];
+      A = 0.0; B = 0.5 * (ny_ * u - nx_ * v); C = p0y * u - p0x * v;
+      side = SF_HALF;
+    }
+    const bool lin = (bits(A) << 1) == 0;
     const double disc = B * B - A * C;
-    if (disc < 0.0) return INFINITY;
-    const double sq = sqrt(disc);
-    const double s1 = (-B - sq) / A, s2 = (-B + sq) / A;
-    r0 = fmin(s1, s2);
-    r1 = fmax(s1, s2);
+    const long long db = bits(disc);
+    const double sq = db > 0 ? sqrt(disc) : 0.0;
+    const double inv = 1.0 / (lin ? B + B : A);
+    double r0 = INFINITY, r1 = INFINITY;
+    if (lin) {
+      if ((bits(B) << 1) != 0) r0 = -C * inv;
+    } else if (db > 0 || ((db << 1) == 0 && side == SF_CONE)) {
+      const double sa = (-B - sq) * inv, sb = (-B + sq) * inv;
+      const bool apos = bits(A) > 0;                                  // then sa <= sb
+      r0 = apos ? sa : sb;
+      r1 = apos ? sb : sa;
+      if (side == SF_INNER) r1 = INFINITY;                            // the nearer crossing only
+      else if (side == SF_OUTER) { r0 = r1; r1 = INFINITY; }          // the farther only
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double r = q == 0 ? r0 : r1;
+      const long long rb = bits(r);
+      if (rb <= scb || rb >= infb) continue;                          // r > s_cur, finite
+      bool on = true;
+      if (side == SF_CONE) on = bits((p0z + r * nz_) * u) > 0;        // its own nappe
+      else if (side == SF_HALF) on = bits((p0x + r * nx_) * u + (p0y + r * ny_) * v) > 0;  // its own side
+      if (on) { *kind_out = k; return r; }
+    }
+    if (att == 0) {                                                   // the family's other face
+      if (fam == 0) k = k == 1 ? 0 : -1;
+      else if (fam == 1) {
+        k = 5 - k;
+        const int j = it + k - 2;
+        if (j == 0 || j == tny) k = -1;
+      } else k = 9 - k;
+    }
   }
-  if (r0 > s_cur && (p0[2] + r0 * n[2]) * c > 0.0) return r0;
-  if (r1 > s_cur && r1 < INFINITY && (p0[2] + r1 * n[2]) * c > 0.0) return r1;
+  *kind_out = -1;
   return INFINITY;
-}
-
-// Path at which the packet leaves cell (ir, it, ip), and through which face
-// (kind 0 outer sphere, 1 inner sphere, 2 lower polar edge, 3 upper polar
-// edge, 4 lower azimuthal edge, 5 upper azimuthal edge; -1 none).  The polar
-// axis (edges 0 and ny) is no face; an azimuthal edge is the half-plane on its
-// own side of the axis; with one azimuthal sector there are none.
-__device__ __forceinline__ double sph_exit(const SphTables& T, const double p0[3], const double n[3], double b,
-                                           double pp, int ir, int it, int ip, double s_cur, int& kind) {
-  double best = INFINITY;
-  kind = -1;
-  const double R1 = T.sR[ir + 1];
-  const double d1 = b * b - (pp - R1 * R1);
-  if (d1 > 0.0) {
-    const double s = -b + sqrt(d1);
-    if (s > s_cur) { best = s; kind = 0; }
-  }
-  if (ir > 0) {
-    const double R0 = T.sR[ir];
-    const double d0 = b * b - (pp - R0 * R0);
-    if (d0 > 0.0) {
-      const double s = -b - sqrt(d0);
-      if (s > s_cur && s < best) { best = s; kind = 1; }
-    }
-  }
-#pragma unroll 1
-  for (int e = 0; e < 2; ++e) {
-    const int j = it + e;
-    if (j == 0 || j == T.ny) continue;
-    const double s = sph_cone(p0, n, T.cth[j], b, pp, s_cur);
-    if (s < best) { best = s; kind = 2 + e; }
-  }
-  if (T.nz > 1) {
-#pragma unroll 1
-    for (int e = 0; e < 2; ++e) {
-      const int k = ip + e;
-      const double cs = T.cph[k], sn = T.sph[k];
-      const double den = n[1] * cs - n[0] * sn;          // n . (-sin phi, cos phi, 0)
-      if (den == 0.0) continue;
-      const double s = -(p0[1] * cs - p0[0] * sn) / den;
-      if (!(s > s_cur) || !(s < best)) continue;
-      const double qx = p0[0] + s * n[0], qy = p0[1] + s * n[1];
-      if (qx * cs + qy * sn > 0.0) { best = s; kind = 4 + e; }
-    }
-  }
-  return best;
-}
-
-// Warp-aggregated counter increment by the lanes that reach it together:
-// returns this lane's value.
-__device__ __forceinline__ unsigned long long take_next(unsigned long long* ctr) {
-  const unsigned act = __activemask();
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(act) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(act));
-  base = __shfl_sync(act, base, leader);
-  return base + __popc(act & ((1u << lane) - 1u));
 }
 
 __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
@@ -1292,82 +1310,118 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   const Geometry& g = a.g;
   const EmitArgs& em = a.em;
   const Pool& P = a.pool;
-  SphTables T;
-  T.nx = g.nx; T.ny = g.ny; T.nz = g.nz;
-  T.sR = g.sph; T.cth = T.sR + g.nx + 1; T.cph = T.cth + g.ny + 1; T.sph = T.cph + g.nz + 1;
-  T.phe = T.sph + g.nz + 1;
+  const double* const sR = g.sph;
+  const double* const cth = sR + g.nx + 1;
+  const double* const phe = cth + g.ny + 1 + 2 * (g.nz + 1);
   const int* RX = a.rtab;
   const int* RY = a.rtab + g.nx;
   const int* RZ = a.rtab + g.nx + g.ny;
   const long long taumin_bits = bits(a.tau_min);
+  const int lane = threadIdx.x & 31;
   // a straight path meets each sphere and cone at most twice, each half-plane once
   const int max_faces = 2 * (g.nx + g.ny) + g.nz + 8;
   double acc[T_NACC];
 #pragma unroll
   for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
   unsigned n_tests = 0, n_events = 0, n_guard = 0;
+
+  bool have = false, drained = false;
+  int i = 0, ix = 0, iy = 0, iz = 0, row = 0, cursor = 0, events = 0, faces = 0;
+  int k_r = -1, k_t = -1, k_p = -1;
+  double p0x = 0, p0y = 0, p0z = 0, nxv = 0, nyv = 0, nzv = 0, b = 0, pp = 0, s = 0;
+  double s_r = 0, s_t = 0, s_p = 0, nu_cmf = 0, aslope = 0, N = 0, N_in = 0, Tq = 0;
   for (;;) {
-    const unsigned long long my = take_next(a.counter);
-    if (my >= (unsigned long long)a.n_list) break;
-    const int i = (int)my;
-    const int64_t p = em.p_begin + (int64_t)my;
-    // ---- emission
-    const int64_t c = quota_cell(em, p);
-    int idx[3];
+    __syncwarp();
     {
-      const uint32_t c32 = (uint32_t)c, nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
-      const uint32_t cy = c32 / nx;
-      idx[0] = (int)(c32 - cy * nx); idx[1] = (int)(cy % ny); idx[2] = (int)(cy / ny);
+      const unsigned full = 0xffffffffu;
+      const unsigned m0 = __ballot_sync(full, !have);
+      if (m0 == full && drained) break;
+      const unsigned m = (drained || (m0 != full && __popc(m0) < kSphRefill)) ? 0u : m0;
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(full, base, leader);
+        if (base + __popc(m) >= (unsigned long long)a.n_list) drained = true;
+        const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
+        if (!have && my < (unsigned long long)a.n_list) {
+          // ---- emission
+          i = (int)my;
+          const int64_t p = em.p_begin + (int64_t)my;
+          const int64_t c = quota_cell(em, p);
+          int idx[3];
+          {
+            const uint32_t c32 = (uint32_t)c, gx = (uint32_t)g.nx, gy = (uint32_t)g.ny;
+            const uint32_t cy = c32 / gx;
+            idx[0] = (int)(c32 - cy * gx); idx[1] = (int)(cy % gy); idx[2] = (int)(cy / gy);
+          }
+          uint64_t xu[4], xv[4];
+          draw_raw(em.seed, p, 0, xu);
+          draw_raw(em.seed, p, 1, xv);
+          {   // uniform in the cell's volume: r^3, cos theta and phi uniform
+            const double R0 = sR[idx[0]], R1 = sR[idx[0] + 1];
+            const double R03 = R0 * R0 * R0, R13 = R1 * R1 * R1;
+            const double rr = cbrt(R03 + u01(xu[0]) * (R13 - R03));
+            const double c0 = cth[idx[1]], c1 = cth[idx[1] + 1];
+            const double ct = c0 - u01(xu[1]) * (c0 - c1);
+            const double ph0 = phe[idx[2]], ph1 = phe[idx[2] + 1];
+            const double ph = ph0 + u01(xu[2]) * (ph1 - ph0);
+            double sp, cp;
+            sincos(ph, &sp, &cp);
+            const double q = 1.0 - ct * ct;
+            const double st = bits(q) > 0 ? sqrt(q) : 0.0;
+            p0x = rr * st * cp; p0y = rr * st * sp; p0z = rr * ct;
+          }
+          double n[3];
+          isotropic(trig, xu[3] >> 11, xv[0] >> 11, n);
+          nxv = n[0]; nyv = n[1]; nzv = n[2];
+          emit_frequency(em, xv[1], c, idx, nu_cmf, cursor);
+          b = nxv * p0x + nyv * p0y + nzv * p0z;
+          pp = p0x * p0x + p0y * p0y + p0z * p0z;
+          const double nu_lab = div_pos(nu_cmf, 1.0 - b * a.inv_ct);
+          aslope = nu_lab * a.inv_ct;                      // d nu_cmf / ds
+          N = div_pos(em.Eph[c], nu_cmf);                  // E0 / (h nu_cmf)
+          N_in = N;
+          Tq = em.e_cut * em.Eph[c];
+          P.F(F_NX, i) = nxv; P.F(F_NY, i) = nyv; P.F(F_NZ, i) = nzv;
+          P.F(F_NULAB, i) = nu_lab;
+          P.pid[i] = p;
+          acc[T_EMITN] += N;
+          acc[T_EMITE] += em.Epk[c];
+          if (a.records) {
+            P.inter[i] = 0;
+            double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+            rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
+          }
+          ix = idx[0]; iy = idx[1]; iz = idx[2];
+          row = RX[ix] + RY[iy] + RZ[iz];
+          s = 0.0;
+          events = 0;
+          faces = 0;
+          s_r = sph_next(g.sph, g.nx, g.ny, g.nz, 0, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                           &k_r);
+          s_t = sph_next(g.sph, g.nx, g.ny, g.nz, 1, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                           &k_t);
+          s_p = sph_next(g.sph, g.nx, g.ny, g.nz, 2, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                           &k_p);
+          have = true;
+        }
+      }
     }
-    uint64_t xu[4], xv[4];
-    draw_raw(em.seed, p, 0, xu);
-    draw_raw(em.seed, p, 1, xv);
-    double p0[3], n[3];
-    {   // uniform in the cell's volume: r^3, cos theta and phi uniform
-      const double R0 = T.sR[idx[0]], R1 = T.sR[idx[0] + 1];
-      const double R03 = R0 * R0 * R0, R13 = R1 * R1 * R1;
-      const double rr = cbrt(R03 + u01(xu[0]) * (R13 - R03));
-      const double c0 = T.cth[idx[1]], c1 = T.cth[idx[1] + 1];
-      const double ct = c0 - u01(xu[1]) * (c0 - c1);
-      const double ph0 = T.phe[idx[2]], ph1 = T.phe[idx[2] + 1];
-      const double ph = ph0 + u01(xu[2]) * (ph1 - ph0);
-      double sp, cp;
-      sincos(ph, &sp, &cp);
-      const double q = 1.0 - ct * ct;
-      const double st = q > 0.0 ? sqrt(q) : 0.0;
-      p0[0] = rr * st * cp; p0[1] = rr * st * sp; p0[2] = rr * ct;
-    }
-    isotropic(trig, xu[3] >> 11, xv[0] >> 11, n);
-    double nu_cmf;
-    int cursor;
-    emit_frequency(em, xv[1], c, idx, nu_cmf, cursor);
-    const double b = n[0] * p0[0] + n[1] * p0[1] + n[2] * p0[2];
-    const double pp = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
-    const double nu_lab = div_pos(nu_cmf, 1.0 - b * a.inv_ct);
-    const double aslope = nu_lab * a.inv_ct;           // d nu_cmf / ds
-    double N = div_pos(em.Eph[c], nu_cmf);             // E0 / (h nu_cmf)
-    const double N_in = N;
-    const double Tq = em.e_cut * em.Eph[c];
-    P.F(F_NX, i) = n[0]; P.F(F_NY, i) = n[1]; P.F(F_NZ, i) = n[2];
-    P.F(F_NULAB, i) = nu_lab;
-    P.pid[i] = p;
-    acc[T_EMITN] += N;
-    acc[T_EMITE] += em.Epk[c];
-    if (a.records) {
-      P.inter[i] = 0;
-      double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
-      rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
-    }
-    // ---- walk
-    int ix = idx[0], iy = idx[1], iz = idx[2];
-    int row = RX[ix] + RY[iy] + RZ[iz];
-    int events = 0, fate = -1;
+    const unsigned busy = __ballot_sync(0xffffffffu, have);
+    if (!have) continue;
+
+    // ---- one face: the lines up to it, then across it
+    double s_exit = s_r;                                // (all >= 0: compared as bit patterns)
+    int kind = k_r;
+    if (bits(s_t) < bits(s_exit)) { s_exit = s_t; kind = k_t; }   // ties to the lower kind
+    if (bits(s_p) < bits(s_exit)) { s_exit = s_p; kind = k_p; }
+    int fate = -1, fam = 0;
     bool escaped = false;
-    double s = 0.0;
-    for (int faces = 0;; ++faces) {
-      int kind;
-      const double s_exit = sph_exit(T, p0, n, b, pp, ix, iy, iz, s, kind);
-      if (kind < 0 || faces >= max_faces) { ++n_guard; fate = 3; break; }
+    if (kind < 0 || ++faces > max_faces) {
+      ++n_guard;
+      fate = 3;
+    } else {
       const long long end_bits = bits(nu_cmf - aslope * s_exit);
       const double* prow = a.pops + (int64_t)row * a.nlev;
       while (cursor < a.nline) {
@@ -1392,44 +1446,59 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
         ++cursor;
         if (fate >= 0) break;
       }
-      if (fate >= 0) break;
-      s = s_exit;
-      if (kind == 0) {
-        if (++ix == g.nx) { escaped = true; break; }
-      } else if (kind == 1) {
-        --ix;
-      } else if (kind == 2) {
-        --iy;
-      } else if (kind == 3) {
-        ++iy;
-      } else if (kind == 4) {
-        iz = iz == 0 ? g.nz - 1 : iz - 1;
-      } else {
-        iz = iz == g.nz - 1 ? 0 : iz + 1;
+      if (fate < 0) {
+        s = s_exit;
+        if (kind <= 1) {
+          fam = 0;
+          if (kind == 0) escaped = ++ix == g.nx;
+          else --ix;
+        } else if (kind <= 3) {
+          fam = 1;
+          iy += kind == 2 ? -1 : 1;
+        } else {
+          fam = 2;
+          iz = kind == 4 ? (iz == 0 ? g.nz - 1 : iz - 1) : (iz == g.nz - 1 ? 0 : iz + 1);
+        }
+        if (!escaped) row = RX[ix] + RY[iy] + RZ[iz];
       }
-      row = RX[ix] + RY[iy] + RZ[iz];
     }
-    // ---- the packet leaves the thread
-    P.F(F_N, i) = N;
-    P.events[i] = events;
-    acc[T_ABS] += N_in - N;
-    if (fate >= 0 && a.records) {
-      double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
-      rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
-      rec[6] = 0.0; rec[10] = nu_lab;
+    // ---- the crossed family's next face, solved by every busy lane of the
+    // warp together after the divergent line tests (a lane without a face to
+    // solve passes cell (0, 0, 0) and drops the result): measured 1.5x faster
+    // than solving inside the lanes' own branches
+    __syncwarp(busy);
+    {
+      const bool solve = fate < 0 && !escaped;
+      int kn;
+      const double sn = sph_next(g.sph, g.nx, g.ny, g.nz, fam, p0x, p0y, p0z, nxv, nyv, nzv, b, pp,
+                                 solve ? ix : 0, solve ? iy : 0, solve ? iz : 0, s, &kn);
+      if (solve) {
+        if (fam == 0) { s_r = sn; k_r = kn; }
+        else if (fam == 1) { s_t = sn; k_t = kn; }
+        else { s_p = sn; k_p = kn; }
+      }
     }
-    if (escaped) {
-      const unsigned long long k = take_next(a.n_esc);
-      a.esc[k] = i;
+    // ---- the packet leaves the lane
+    if (escaped || fate >= 0) {
+      P.F(F_N, i) = N;
+      P.events[i] = events;
+      acc[T_ABS] += N_in - N;
+      if (fate >= 0 && a.records) {
+        double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
+        rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+        rec[6] = 0.0; rec[10] = P.F(F_NULAB, i);
+      }
+      have = false;
     }
+    warp_append(escaped, i, a.esc, a.n_esc);
   }
+  __syncwarp();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned long long nb = blk_log;
     if (nb > (unsigned long long)a.seg_len) atomicAdd(a.log_overflow, 1ull);
     a.seg_n[blockIdx.x] = (int64_t)(nb < (unsigned long long)a.seg_len ? nb : a.seg_len);
   }
-  __syncwarp();
   double cnt[3] = {(double)n_tests, (double)n_events, (double)n_guard};
   const int cslots[3] = {LG_TESTS, LG_EVENTS, LG_GUARD};
   warp_flush(cnt, a.ledger, cslots);
