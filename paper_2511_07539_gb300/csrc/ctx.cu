@@ -587,14 +587,18 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   std::vector<int> doff(nlev + 1, 0), dline(nl);
   for (int l = 0; l < nl; ++l) doff[up[l] + 1]++;
   for (int u = 0; u < nlev; ++u) doff[u + 1] += doff[u];
-  std::vector<int> fill(nlev, 0);
-  for (int l = 0; l < nl; ++l) dline[doff[up[l]] + fill[up[l]]++] = c->h_sorted_of[l];
-  // radiative lines per lower level, ascending caller index
+  std::vector<int> fill(nlev, 0), dpos(nl);
+  for (int l = 0; l < nl; ++l) {
+    dpos[l] = doff[up[l]] + fill[up[l]]++;
+    dline[dpos[l]] = c->h_sorted_of[l];
+  }
+  // radiative lines per lower level, ascending caller index, as their
+  // positions in the down-line lists
   std::vector<int> loff(nlev + 1, 0), lline(nl);
   for (int l = 0; l < nl; ++l) loff[lo[l] + 1]++;
   for (int i = 0; i < nlev; ++i) loff[i + 1] += loff[i];
   std::vector<int> lfill(nlev, 0);
-  for (int l = 0; l < nl; ++l) lline[loff[lo[l]] + lfill[lo[l]]++] = c->h_sorted_of[l];
+  for (int l = 0; l < nl; ++l) lline[loff[lo[l]] + lfill[lo[l]]++] = dpos[l];
   c->n_ion = a->n_ion; c->nlev = nlev; c->nline = nl;
   c->h_nu_sorted = s_nu;
   c->h_lam_caller = lam;

@@ -64,8 +64,8 @@ struct SeArgs {
   const double* __restrict__ A;         // sorted
   const int* __restrict__ down_off;     // [nlev + 1] lines by upper level
   const int* __restrict__ down_line;
-  const int* __restrict__ low_off;      // [nlev + 1] lines by lower level
-  const int* __restrict__ low_line;
+  const int* __restrict__ low_off;      // [nlev + 1] lines by lower level,
+  const int* __restrict__ low_line;     //   as positions k in down_line
   const double* __restrict__ S;         // estimators (net photons) [row][sorted line]
   const int* __restrict__ crow;         // compact store: the cell's row in S, -1 none (nullptr: dense)
   const double* __restrict__ Rj;        // photoexcitation per sorted line (Jbar model)
@@ -498,31 +498,49 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
         }
       }
       block_sync();
-      // radiative lines of the kept levels (lines by upper level u < L): a
-      // thread per upper level, its lines in a fixed order, so that every
+      // radiative lines of the kept levels (the lines of upper levels 1..L-1,
+      // positions kA..kB-1 of down_line): each line's two rate terms, a thread
+      // per line, into the panel buffer (free until the factor); then a thread
+      // per upper level adds its lines' terms in a fixed order, so that every
       // entry is summed in the same order on every run (a line u -> lo writes
-      // only column u and row u, which no other upper level's lines touch)
+      // only column u and row u, which no other upper level's lines touch).
+      // Without room in the buffer the thread per upper level computes them.
+      const int kA = a.down_off[off + 1], kB = a.down_off[off + L], nk = kB - kA;
+      double* const lbuf = (double*)sPan;
+      const bool lbuffered = 2 * (size_t)nk * sizeof(double) <= se_pan_bytes(MAXL);
+      auto line_terms = [&](int k, double& down, double& up_rate) {
+        const int s = a.down_line[k];
+        const double* Lr = a.lines + 4 * (int64_t)s;
+        const int64_t lu = __double_as_longlong(Lr[3]);
+        const int lo = (int)(lu & 0xFFFFFFFF) - off, u = (int)(lu >> 32) - off;
+        const double tau = Lr[1] * (nbeta[lo] - Lr[2] * nbeta[u]);
+        const double beta = sobolev_beta_fix(sfx, tau, nullptr);
+        double Rlu = 0.0;
+        if (a.rates == XT_RATES_JBAR) {
+          Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
+        } else if (a.rates == XT_RATES_ESTIMATORS) {
+          // fixed per atom: the populations of the transport pass set it
+          const double net = pc[off + lo] - Lr[2] * pc[off + u];
+          const int64_t sr = a.crow ? (int64_t)a.crow[row] : (int64_t)row;
+          const double Sv = sr < 0 ? 0.0 : a.S[sr * a.nline + s];
+          if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * (a.g.vol ? a.g.vol[row] : a.V));
+        }
+        down = a.A[s] * beta + Lr[2] * Rlu;                           // u -> lo
+        up_rate = Rlu;                                                // lo -> u
+      };
+      if (lbuffered) {
+        for (int k = kA + tid; k < kB; k += blockDim.x) line_terms(k, lbuf[k - kA], lbuf[nk + k - kA]);
+        block_sync();
+      }
       for (int u = 1 + tid; u < L; u += blockDim.x) {
         const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
         for (int k = k0; k < k1; ++k) {
-          const int s = a.down_line[k];
-          const double* Lr = a.lines + 4 * (int64_t)s;
-          const int64_t lu = __double_as_longlong(Lr[3]);
-          const int lo = (int)(lu & 0xFFFFFFFF) - off;
-          const double tau = Lr[1] * (nbeta[lo] - Lr[2] * nbeta[u]);
-          const double beta = sobolev_beta_fix(sfx, tau, nullptr);
-          double Rlu = 0.0;
-          if (a.rates == XT_RATES_JBAR) {
-            Rlu = a.Rj[s] * beta;   // external field, Sobolev-absorbed part
-          } else if (a.rates == XT_RATES_ESTIMATORS) {
-            // fixed per atom: the populations of the transport pass set it
-            const double net = pc[off + lo] - Lr[2] * pc[off + u];
-            const int64_t sr = a.crow ? (int64_t)a.crow[row] : (int64_t)row;
-            const double Sv = sr < 0 ? 0.0 : a.S[sr * a.nline + s];
-            if (net > 0.0 && Sv > 0.0) Rlu = div_pos(Sv, net * (a.g.vol ? a.g.vol[row] : a.V));
-          }
-          W[(int64_t)lo * L + u] += a.A[s] * beta + Lr[2] * Rlu;   // u -> lo
-          W[(int64_t)u * L + lo] += Rlu;                            // lo -> u
+          const int lo = (int)(__double_as_longlong(a.lines[4 * (int64_t)a.down_line[k] + 3]) & 0xFFFFFFFF) - off;
+          double down, up_rate;
+          if (lbuffered) { down = lbuf[k - kA]; up_rate = lbuf[nk + k - kA]; }
+          else line_terms(k, down, up_rate);
+          W[(int64_t)lo * L + u] += down;
+          W[(int64_t)u * L + lo] += up_rate;
         }
       }
       // non-thermal excitation from the ground level
@@ -581,18 +599,30 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           if (lane == 0) sB[i] = (i == 0 ? nz : 0.0) - s;
         }
         block_sync();
-        // a thread per upper level writes its lines' entries of column u and
-        // row u (no other thread's); then a thread per lower level adds the
-        // t of the lines below it to its diagonal, both in fixed line order
+        // each line's t, a thread per line, into the panel buffer (without
+        // room there it is computed where it is used); then a thread per upper
+        // level writes its lines' entries of column u and row u (no other
+        // thread's), and a thread per lower level adds the t of the lines
+        // below it to its diagonal, both in fixed line order
+        const bool tbuffered = (size_t)nk * sizeof(double) <= se_pan_bytes(MAXL);
+        auto line_t = [&](int k) {
+          const int s = a.down_line[k];
+          const double* Lr = a.lines + 4 * (int64_t)s;
+          const int64_t lu = __double_as_longlong(Lr[3]);
+          return line_jac_t(a, sfx, Lr, s, sNk[(int)(lu & 0xFFFFFFFF) - off], sNk[(int)(lu >> 32) - off]);
+        };
+        if (tbuffered) {
+          for (int k = kA + tid; k < kB; k += blockDim.x) lbuf[k - kA] = line_t(k);
+          block_sync();
+        }
         for (int u = 1 + tid; u < L; u += blockDim.x) {
           const int k0 = a.down_off[off + u], k1 = a.down_off[off + u + 1];
           double du = 0.0;
           for (int k = k0; k < k1; ++k) {
-            const int s = a.down_line[k];
-            const double* Lr = a.lines + 4 * (int64_t)s;
-            const int lo = (int)(__double_as_longlong(Lr[3]) & 0xFFFFFFFF) - off;
-            const double t = line_jac_t(a, sfx, Lr, s, sNk[lo], sNk[u]);
+            const double t = tbuffered ? lbuf[k - kA] : line_t(k);
             if (t == 0.0) continue;
+            const double* Lr = a.lines + 4 * (int64_t)a.down_line[k];
+            const int lo = (int)(__double_as_longlong(Lr[3]) & 0xFFFFFFFF) - off;
             if (lo != 0) W[(int64_t)lo * L + u] += -Lr[2] * t;
             W[(int64_t)u * L + lo] += -t;
             du += Lr[2] * t;
@@ -604,11 +634,9 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           const int q0 = a.low_off[off + lo], q1 = a.low_off[off + lo + 1];
           double dl = 0.0;
           for (int q = q0; q < q1; ++q) {
-            const int s = a.low_line[q];
-            const double* Lr = a.lines + 4 * (int64_t)s;
-            const int u = (int)(__double_as_longlong(Lr[3]) >> 32) - off;
-            if (u >= L) continue;                       // upper level not kept
-            dl += line_jac_t(a, sfx, Lr, s, sNk[lo], sNk[u]);
+            const int k = a.low_line[q];
+            if (k >= kB) continue;                      // upper level not kept
+            dl += tbuffered ? lbuf[k - kA] : line_t(k);
           }
           W[(int64_t)lo * L + lo] += dl;
         }

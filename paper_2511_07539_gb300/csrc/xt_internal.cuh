@@ -104,7 +104,7 @@ struct xt_ctx {
   double* d_invB = nullptr;          // 1 / B_lu (sorted)
   int *d_lo = nullptr, *d_up = nullptr, *d_orig = nullptr;
   int *d_down_off = nullptr, *d_down_line = nullptr;
-  int *d_low_off = nullptr, *d_low_line = nullptr;   // lines by lower level (sorted indices)
+  int *d_low_off = nullptr, *d_low_line = nullptr;   // lines by lower level (positions in d_down_line)
   double* d_nion = nullptr;          // [row][n_ion]
   double* d_ups_down = nullptr;      // [nlev]
   // photoionizing levels, sorted by threshold frequency (descending; ties in
