@@ -445,6 +445,16 @@ int run_coupled(xt_ctx *ctx, const xt_coupled_params *p, xt_coupled_stats *stats
 int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, double *y1,
                       double *r0, double *r1);
 
+/* Check of the tensor-core path that the batched LU's trailing updates take
+ * (tcgen05 MMA, kind::tf32, operands in shared memory, accumulator in TMEM):
+ * D [128][N] = A B^T for A [128][32] and B [N][32] (host arrays, row-major,
+ * FP32), with A and B rounded to TF32 (nearest, ties away from zero) and the
+ * products summed in FP32 by the tensor core.  N a multiple of 16 in
+ * [16, 256].  Runs one CTA on `device`, synchronously, with temporaries of its
+ * own.  XT_EINVAL for a bad N or a NULL array; XT_ETIMEOUT if the MMA's
+ * completion was not seen within its bounded wait. */
+int xt_selftest_tc(int device, int N, const float *A, const float *B, float *D);
+
 /* ---- transport without device allocation (no paper counterpart) -----------
  * For callers that cannot call cudaMalloc: programs whose device memory is
  * handed out once at start-up by another framework's allocator (a second

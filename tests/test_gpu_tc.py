@@ -1,0 +1,56 @@
+"""The tensor-core path of the batched LU (tcgen05 MMA, kind::tf32, operands
+in shared memory, accumulator in TMEM) against numpy (needs a GPU): D = A B^T
+with A and B rounded to TF32 (nearest, ties away from zero) equals the
+float64 product of the rounded operands to FP32 accumulation error."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xt():
+    import torch
+    assert torch.cuda.is_available(), "GPU test run without a GPU"
+    import __graft_entry__ as g
+    g.build()
+    import paper_2511_07539_gb300 as xt
+    return xt
+
+
+def tf32(x):
+    """Round float32 to TF32 (10 mantissa bits), nearest, ties away from zero."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32)
+
+
+@pytest.mark.parametrize("N", [16, 48, 128, 256])
+def test_tf32_gemm_vs_numpy(xt, N):
+    rng = np.random.default_rng(N)
+    A = rng.standard_normal((128, 32)).astype(np.float32)
+    B = rng.standard_normal((N, 32)).astype(np.float32)
+    A[5] = 0.0                       # a zero row and an exactly representable column
+    B[:, 3] = 0.25
+    D = xt.xt_selftest_tc(A, B)
+    ref = tf32(A).astype(np.float64) @ tf32(B).astype(np.float64).T
+    scale = np.abs(tf32(A)).astype(np.float64) @ np.abs(tf32(B)).astype(np.float64).T
+    assert np.all(np.isfinite(D))
+    err = np.abs(D - ref) / np.maximum(scale, 1e-30)
+    assert err.max() < 2e-6, err.max()
+    # the rounding to TF32 is what the tensor core sees: the unrounded product differs more
+    assert np.abs(A.astype(np.float64) @ B.astype(np.float64).T - ref).max() > 1e-4
+
+
+def test_tf32_gemm_rows_and_columns_are_not_mixed(xt):
+    """Unit vectors pick single entries: a transposed or shifted operand layout
+    would move them."""
+    A = np.zeros((128, 32), np.float32)
+    B = np.zeros((64, 32), np.float32)
+    for r in range(128):
+        A[r, r % 32] = r + 1
+    for n in range(64):
+        B[n, (3 * n) % 32] = 1.0 / (n + 1)
+    D = xt.xt_selftest_tc(A, B)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    np.testing.assert_allclose(D, ref, rtol=2e-3, atol=0)
