@@ -286,6 +286,68 @@ def cfg5_bench(local, stream_ptr, packets=1_000_000_000):
             "fp64_fallbacks": sol["fp64_fallbacks"], "device_GB_free_after": free / 1e9}
 
 
+def cfg5_loop_bench(local, stream_ptr, packets=1_000_000_000):
+    """A10 at the full-loop scale: the coupled loop to a relative population
+    change <= 1e-3 on 128^3 cells (1.1e6 with matter; 10 ions of 20-60 levels,
+    2e4 lines, 1e9 packets per pass, 4^3 subdomains, the estimator store with
+    rows for the cells with matter only), the plain loop (FP64 factors from
+    Boltzmann populations) against the fast one (FP32 factors with FP64
+    refinement from the surrogate's prediction).  The surrogate is trained
+    beforehand, outside the timing, on the converged populations of a 32^3
+    realization with the same atoms.  Both loops timed by the host clock around
+    the whole run_coupled call."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    import synth
+    kw = dict(seed=1, n_lines=20_000, level_range=(20, 60), subdomains=(4, 4, 4))
+    A = synth.clumpy_onion(n=32, n_packets=2_000_000, **kw)
+    B = synth.clumpy_onion(n=128, n_packets=packets, field_seed=2, **kw)
+    for k in ("level_off", "E_level", "g_level", "lo", "up", "lambda_A", "f_lu"):
+        assert np.array_equal(getattr(A, k), getattr(B, k)), k      # the same atoms
+    ups = synth.collision_strengths(A.upsilon_seed, A.level_off)
+    common = dict(tol=1e-3, jbar_W=5.6e-5, jbar_TR=8000.0, spec_lam0_A=B.spec_band_A[0],
+                  spec_nbins=B.spec_band_A[1], seed=B.seed)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(A)
+    t0 = time.perf_counter()
+    stA = xt.run_coupled(ctx.h, ups, A.n_packets, start=xt.XT_WARM_LTE, precision=xt.XT_PREC_FP32_IR,
+                         **common)
+    tr = xt.train_surrogate(ctx.h, epochs=60, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
+                            jbar_W=5.6e-5, jbar_TR=8000.0)
+    prep_s = time.perf_counter() - t0
+    res, pops = {}, {}
+    for name, start, prec in (("plain_fp64", xt.XT_WARM_LTE, xt.XT_PREC_FP64),
+                              ("surrogate_mixed", xt.XT_WARM_SURROGATE, xt.XT_PREC_FP32_IR)):
+        ctx.load(B)
+        xt.set_estimator_store(ctx.h, xt.XT_STORE_COMPACT_ROWS)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = xt.run_coupled(ctx.h, ups, B.n_packets, start=start, precision=prec, max_outer=30, **common)
+        torch.cuda.synchronize()
+        host_s = time.perf_counter() - t1
+        p = np.zeros((B.ncell, B.nlev))
+        xt.get_populations(ctx.h, p)
+        pops[name] = p
+        res[name] = {k: st[k] for k in ("outer", "converged", "wall_ms", "start_ms", "transport_ms",
+                                        "solve_ms", "newton_steps", "max_newton_steps", "not_converged",
+                                        "change")}
+        res[name]["host_s"] = host_s
+    sz = xt.get_sizes(ctx.h)
+    free, _ = torch.cuda.mem_get_info()
+    ctx.close()
+    nz = np.repeat(B.n_ion_density, np.diff(B.level_off), axis=1)
+    ref = pops["plain_fp64"]
+    sig = (ref >= 1e-20 * nz) & (nz > 0)
+    dev = float(np.max(np.abs(pops["surrogate_mixed"][sig] / ref[sig] - 1)))
+    return {"workload": B.name + " (clump field 2; surrogate trained on a 32^3 realization)",
+            "cells": B.ncell, "cells_with_matter": int((B.rho > 0).sum()), "systems": B.ncell * B.n_ion,
+            "store_GB": sz["store_bytes"] / 1e9, "device_GB_free_after": free / 1e9, "tol": 1e-3, **res,
+            "max_rel_dev_vs_plain": dev,
+            "speedup_surrogate_mixed_vs_plain": res["plain_fp64"]["wall_ms"] / res["surrogate_mixed"]["wall_ms"],
+            "training": {"outer_32": stA["outer"], "last_loss": tr["last_loss"], "steps": tr["steps"],
+                         "train_ms": tr["train_ms"], "prep_s": prep_s}}
+
+
 def collision_sphere(n_packets=20_000_000):
     """A 16^3 sphere whose 12 lines lie within 5000-5080 A and whose band is
     4990-5100 A: every packet meets most lines, so the lanes of a warp often
@@ -642,6 +704,8 @@ def main():
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
     ap.add_argument("--only-cfg5", action="store_true",
                     help="print the 128^3 full-loop-scale object alone (a pass and a solve)")
+    ap.add_argument("--only-cfg5-loop", action="store_true",
+                    help="print the 128^3 coupled-loop object alone (plain vs surrogate + mixed)")
     ap.add_argument("--nlte-n", type=int, default=64)
     ap.add_argument("--nlte-once", action="store_true",
                     help="with --only-nlte: one plain mixed-precision launch (profiling case)")
@@ -693,6 +757,11 @@ def main():
     if args.only_cfg5:
         if rank == 0:
             print(json.dumps({"cfg5": cfg5_bench(local, torch.cuda.current_stream().cuda_stream)}),
+                  flush=True)
+        return
+    if args.only_cfg5_loop:
+        if rank == 0:
+            print(json.dumps({"cfg5_loop": cfg5_loop_bench(local, torch.cuda.current_stream().cuda_stream)}),
                   flush=True)
         return
     if args.only_sph:

@@ -90,9 +90,8 @@ extern "C" int run_coupled(xt_ctx* c, const xt_coupled_params* p, xt_coupled_sta
   if (p->start == XT_WARM_GIVEN) {
     if ((rc = set_populations(c, p->start_in))) return finish(rc);
   } else if (p->start == XT_WARM_LTE || p->start == XT_WARM_SURROGATE) {
-    if (!c->d_pops) {
-      if ((rc = alloc(c, (void**)&c->d_pops, pops_n * sizeof(double), "pops"))) return finish(rc);
-    }
+    // sized for the current grid and atoms (alloc keeps a buffer of that size)
+    if ((rc = alloc(c, (void**)&c->d_pops, pops_n * sizeof(double), "pops"))) return finish(rc);
     if (p->start == XT_WARM_LTE) rc = lte_fill(c, d_used, c->d_pops);
     else rc = surrogate_warm(c, XT_RATES_JBAR, p->nlte->jbar_W, p->nlte->jbar_TR, d_used, c->d_pops);
     if (rc) return finish(rc);

@@ -644,19 +644,9 @@ int set_populations(xt_ctx* c, const double* pops) {
   if (!c->have_atoms) return fail(c, XT_ESTATE, "set_populations: load_atomic_data first");
   cudaSetDevice(c->device);
   int rc;
-  if (c->d_pops) {   // reuse the allocation
-    size_t bytes = (size_t)c->geo.ncell * c->nlev * sizeof(double);
-    const double* src = pops;
-    if (!is_device_ptr(pops)) {
-      if ((rc = ensure_scratch(c, bytes))) return rc;
-      if ((rc = copy(c, c->d_scratch, pops, bytes, "pops"))) return rc;
-      src = (const double*)c->d_scratch;
-    }
-    k_nat_to_row<<<grid_blocks(c->geo.ncell * c->nlev, 256), 256, 0, c->stream>>>(c->geo, src, c->d_pops, c->nlev);
-    XT_CUDA(c, cudaGetLastError());
-  } else if ((rc = upload_rows(c, pops, &c->d_pops, c->nlev, "pops"))) {
-    return rc;
-  }
+  // sized for the current grid and atoms (alloc keeps a buffer of that size;
+  // a context reloaded with another grid gets a new one)
+  if ((rc = upload_rows(c, pops, &c->d_pops, c->nlev, "pops"))) return rc;
   c->have_pops = true;
   c->have_S = false;     // estimators refer to the populations of their transport pass
   if (c->qoff_mode == XT_EMIT_LINES) c->qoff_N = -1;

@@ -178,3 +178,32 @@ def test_coupled_loop_line_emission_rays_vs_oracle(xt, precision):
     assert steps > 10 and st["converged"] and steps == st["outer"], (st, hist)
     assert st["not_converged"] == 0
     assert _worst(w, got, ref) < 1e-6
+
+
+def test_context_reloaded_with_a_larger_grid(xt):
+    """A context loaded with a 6^3 grid and then with a 10^3 grid gives what a
+    fresh context gives on the 10^3 grid: the populations, the start
+    populations of the loop and every buffer follow the new grid."""
+    small = synth.uniform_sphere(seed=4, n=6, n_packets=20_000)
+    big = synth.uniform_sphere(seed=4, n=10, n_packets=30_000)
+    ups_s = synth.collision_strengths(4, small.level_off)
+    ups_b = synth.collision_strengths(4, big.level_off)
+    kw = dict(start=xt.XT_WARM_LTE, tol=1e-12, max_outer=2, precision=0, newton_tol=1e-10)
+
+    def run(ctx, w, ups):
+        ctx.load(w)
+        back = np.zeros((w.ncell, w.nlev))
+        xt.get_populations(ctx.h, back)
+        assert np.array_equal(back, w.pops)
+        xt.run_coupled(ctx.h, ups, w.n_packets, seed=w.seed, spec_lam0_A=w.spec_band_A[0],
+                       spec_nbins=w.spec_band_A[1], **kw)
+        p = np.zeros((w.ncell, w.nlev))
+        xt.get_populations(ctx.h, p)
+        return p
+
+    with _ctx(xt) as ctx:
+        run(ctx, small, ups_s)
+        got = run(ctx, big, ups_b)
+    with _ctx(xt) as ctx:
+        ref = run(ctx, big, ups_b)
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=0)
