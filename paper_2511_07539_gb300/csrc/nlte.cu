@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "fixexp.cuh"
+#include "tc.cuh"
 #include "xt_internal.cuh"
 
 namespace xt {
@@ -85,6 +86,8 @@ struct SeArgs {
   int max_iter;
   int nb_bucket[8];                     // panel width per 64-level bucket
   double* __restrict__ iters;           // [cell * n_ion + z] refinement (or Newton) steps
+  int tmem_cols;                        // > 0: TF32 factors' trailing updates on the tensor cores
+  unsigned long long* __restrict__ tc_err;   //   (TMEM columns per CTA; CTAs that gave up)
   int newton_max;                       // 0: linear solve with beta_S from pops
   double newton_tol, newton_maxvar;
   FixExpTables fx;                      // e^-tau tables (fixed point)
@@ -107,24 +110,24 @@ __device__ __forceinline__ double line_jac_t(const SeArgs& a, const FixExpTables
 
 __device__ __forceinline__ void block_sync() { __syncthreads(); }
 
-// D = A B + D for one 16 x 8 x 8 tile, TF32 inputs (rounded to nearest), FP32
-// accumulators; per lane (g = lane / 4, t = lane % 4): a0 (g, t), a1 (g + 8, t),
-// a2 (g, t + 4), a3 (g + 8, t + 4); b0 (t, g), b1 (t + 4, g); c0, c1 (g, 2t, 2t + 1),
-// c2, c3 (g + 8, 2t, 2t + 1).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void mma_tf32_16x8x8(float (&c)[4], float a0, float a1, float a2, float a3,
-                                                float b0, float b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(to_tf32(a0)), "r"(to_tf32(a1)), "r"(to_tf32(a2)), "r"(to_tf32(a3)), "r"(to_tf32(b0)),
-        "r"(to_tf32(b1)));
-}
+// Tensor-core state of a CTA (shared memory): the TMEM accumulator (ncols
+// columns), the mbarrier that MMA completions arrive on and its phase; ok = 0
+// once a bounded wait ran out (the CTA then keeps to the CUDA cores).
+struct TcState {
+  uint64_t bar;
+  uint32_t taddr, phase;
+  int ncols, ok;
+  unsigned long long* err;     // global count of CTAs that gave up on the tensor cores
+};
+constexpr long long kTcSpin = 1ll << 24;   // polls of an MMA completion before giving up
+// Byte offset of the TcState in the U12 buffer (kSeNbMax x kSeMaxL floats): an
+// FP32 panel step uses kb x n2 <= kSeNbMax x (kSeMaxL - kSeNbMax) of it
+// (panels of 32 columns; 16-column panels use half the rows), and the operand B
+// of the tensor cores <= (kSeMaxL - kSeNbMax) rows of 128 bytes, the same.
+constexpr size_t kTcStateOff = (size_t)kSeNbMax * (kSeMaxL - kSeNbMax) * 4;
+static_assert(kTcStateOff + sizeof(TcState) <= (size_t)kSeNbMax * kSeMaxL * 4, "TcState in the U12 buffer");
+static_assert(kTcStateOff % 8 == 0, "TcState alignment");
+static_assert((size_t)8 * (kSeMaxL - 8) * 8 <= kTcStateOff, "FP64 fallback panels below the TcState");
 
 // ---- blocked LU with partial pivoting of the L x L row-major matrix A (global)
 // Panels of nb columns are staged in shared memory with row stride nb + 1 (no
@@ -133,10 +136,105 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float (&c)[4], float a0, float a
 // multipliers and the rank-1 update of the panel, one thread per row.  Then
 // the CTA applies the swaps to the other columns, solves for the panel's U
 // rows and updates the trailing matrix through L2 (rank-nb update).
+// A22 -= L21 U12 of one panel step on the tensor cores (see lu_factor); false
+// if an MMA completion was not seen within its bounded wait (the CTA then
+// stops using the tensor cores and the factor is treated as singular, which
+// sends the system to the FP64 solve).
+__device__ __noinline__ bool lu_trailing_tc(float* __restrict__ A, int L, int k0, int kb, int kbp, int m2, int n2, int Npad,
+                               float* pan, float* u12, TcState* tc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned char* const Bs = reinterpret_cast<unsigned char*>(u12);
+  unsigned char* const As = reinterpret_cast<unsigned char*>(pan + kb * kbp);   // L21's first row
+  // operand B: U12 rounded to TF32, zero outside kb x n2
+  for (int e = tid; e < Npad * 32; e += blockDim.x) {
+    const int n = e >> 5, k = e & 31;
+    uint32_t* q = reinterpret_cast<uint32_t*>(Bs + tc::tile_off(n, k, Npad));
+    *q = (n < n2 && k < kb) ? tc::to_tf32(__uint_as_float(*q)) : 0u;
+  }
+  const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
+  const int nmax = tc->ncols < 256 ? tc->ncols : 256;
+  const uint32_t taddr = tc->taddr;
+  uint32_t ph = tc->phase;
+  bool ok = true;
+  for (int t0 = 0; t0 < m2 && ok; t0 += 128) {
+    // operand A: rows t0..t0+127 of L21, through registers (the region they
+    // are written to holds the first rows themselves)
+    float av[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, r = e >> 5, k = e & 31;
+      av[q] = (t0 + r < m2 && k < kb) ? pan[(kb + t0 + r) * kbp + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q, r = e >> 5, k = e & 31;
+      *reinterpret_cast<uint32_t*>(As + tc::tile_off(r, k, 128)) = tc::to_tf32(av[q]);
+    }
+    tc::fence_smem_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    for (int n0 = 0; n0 < Npad; n0 += nmax) {
+      const int Nc = min(nmax, Npad - n0);
+      if (tid == 0) {
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(k * 4096), 2048, 128);
+          const uint64_t bd = tc::smem_desc(b0 + (uint32_t)((2 * k * (Npad >> 3) + (n0 >> 3)) * 128),
+                                            (uint32_t)(Npad >> 3) * 128, 128);
+          tc::mma_tf32(taddr, ad, bd, tc::idesc_tf32(128, Nc), k > 0);
+        }
+        tc::commit(&tc->bar);
+      }
+      const bool got = tc::bar_wait(&tc->bar, ph, kTcSpin);
+      ph ^= 1u;
+      if (!__syncthreads_and(got)) { ok = false; break; }
+      tc::fence_after();
+      // D rows 32 (warp % 4) + lane of the tile, half (warp / 4) of the columns
+      const int q4 = warp & 3, half = Nc >> 1, c0 = (warp >> 2) * half;
+      const int r = t0 + 32 * q4 + lane;
+      for (int c = 0; c < half; c += 16) {
+        float v[16];
+        tc::ld16(taddr + ((uint32_t)(32 * q4) << 16) + (uint32_t)(c0 + c), v);
+        if (r < m2) {
+          float* Ar = A + (int64_t)(k0 + kb + r) * L + k0 + kb + n0 + c0 + c;
+          const int nv = n2 - (n0 + c0 + c);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (q < nv) Ar[q] -= v[q];
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+    }
+  }
+  if (tid == 0) {
+    tc->phase = ph;
+    if (!ok) {
+      tc->ok = 0;
+      atomicAdd(tc->err, 1ull);
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
+// With tc (FP32 factors, 256 threads, panels of 32 columns), trailing updates
+// of at least kTcMinRows rows run on the tensor cores (tcgen05, kind::tf32):
+// U12 is solved straight into the canonical operand layout of tc.cuh in the
+// u12 buffer (40 KB: 320 rows x 32 K), rounded to TF32 and zero-padded; each
+// tile of 128 rows of L21 is read from the panel into registers and written in
+// that layout at the start of L21's own rows in the panel buffer (128 rows of
+// 33 floats hold its 16 KB, so no row still to be read is overwritten); the
+// MMAs accumulate L21 U12 in TMEM, and the CTA subtracts it from A22 through
+// tcgen05 loads (a warp per 32 rows and half the columns).
+constexpr int kTcMinRows = 32;
+
 template <typename T>
 __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T* u12,
-                          bool tc_tf32 = false) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+                          TcState* tc = nullptr) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ int sing, spiv;
   if (tid == 0) sing = 0;
   const int kbp = nb + 1;
@@ -225,55 +323,51 @@ __device__ bool lu_factor(T* __restrict__ A, int L, int nb, int* piv, T* pan, T*
     block_sync();
     const int n2 = L - k0 - kb;                     // trailing columns
     if (n2 > 0) {
+      bool use_tc = false;
+      int Npad = 0;
+      if constexpr (sizeof(T) == 4) {
+        use_tc = tc != nullptr && tc->ok && n2 >= kTcMinRows && kb == 32 && blockDim.x == 256 &&
+                 ((tc::smem_u32(pan + kb * kbp) | tc::smem_u32(u12)) & 15) == 0;   // operand alignment
+        Npad = (n2 + 31) & ~31;
+      }
       // U12 = L11^-1 A12 (unit lower), one column per thread, kept in shared
       // memory: the column's kb entries are loaded first (independent loads in
-      // flight together), then solved in place
-      for (int cc = tid; cc < n2; cc += blockDim.x)
-        for (int r = 0; r < kb; ++r) u12[r * n2 + cc] = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
-      for (int cc = tid; cc < n2; cc += blockDim.x) {
-        for (int r = 0; r < kb; ++r) {
-          T v = u12[r * n2 + cc];
-          for (int s = 0; s < r; ++s) v -= pan[r * kbp + s] * u12[s * n2 + cc];
-          u12[r * n2 + cc] = v;
-          A[(int64_t)(k0 + r) * L + k0 + kb + cc] = v;
+      // flight together), then solved in place; row-major [kb][n2], or for the
+      // tensor cores as operand B (row cc, K r)
+      if (use_tc) {
+        unsigned char* const ub = reinterpret_cast<unsigned char*>(u12);
+        for (int cc = tid; cc < n2; cc += blockDim.x) {
+          for (int r = 0; r < kb; ++r)
+            *reinterpret_cast<T*>(ub + tc::tile_off(cc, r, Npad)) = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
+          for (int r = 0; r < kb; ++r) {
+            T v = *reinterpret_cast<T*>(ub + tc::tile_off(cc, r, Npad));
+            for (int s = 0; s < r; ++s) v -= pan[r * kbp + s] * *reinterpret_cast<T*>(ub + tc::tile_off(cc, s, Npad));
+            *reinterpret_cast<T*>(ub + tc::tile_off(cc, r, Npad)) = v;
+            A[(int64_t)(k0 + r) * L + k0 + kb + cc] = v;
+          }
+        }
+      } else {
+        for (int cc = tid; cc < n2; cc += blockDim.x)
+          for (int r = 0; r < kb; ++r) u12[r * n2 + cc] = A[(int64_t)(k0 + r) * L + k0 + kb + cc];
+        for (int cc = tid; cc < n2; cc += blockDim.x) {
+          for (int r = 0; r < kb; ++r) {
+            T v = u12[r * n2 + cc];
+            for (int s = 0; s < r; ++s) v -= pan[r * kbp + s] * u12[s * n2 + cc];
+            u12[r * n2 + cc] = v;
+            A[(int64_t)(k0 + r) * L + k0 + kb + cc] = v;
+          }
         }
       }
       block_sync();
       const int m2 = L - k0 - kb;                   // trailing rows
-      if (tc_tf32) {
-        // A22 -= L21 U12 on the tensor cores: TF32 operands, FP32 accumulation,
-        // one 16 x 8 output tile per warp and step (mma.sync m16n8k8)
-        const int g = lane >> 2, t4 = lane & 3;
-        const int mt = (m2 + 15) >> 4, ntl = (n2 + 7) >> 3;
-        for (int t = warp; t < mt * ntl; t += nwarp) {
-          const int bi = (t / ntl) << 4, bj = (t % ntl) << 3;
-          float c[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int k = 0; k < kb; k += 8) {
-            const int ka = k + t4, kc = k + t4 + 4;
-            const int ra = bi + g, rb = bi + g + 8;
-            const float a0 = (ra < m2 && ka < kb) ? (float)pan[(kb + ra) * kbp + ka] : 0.f;
-            const float a1 = (rb < m2 && ka < kb) ? (float)pan[(kb + rb) * kbp + ka] : 0.f;
-            const float a2 = (ra < m2 && kc < kb) ? (float)pan[(kb + ra) * kbp + kc] : 0.f;
-            const float a3 = (rb < m2 && kc < kb) ? (float)pan[(kb + rb) * kbp + kc] : 0.f;
-            const int cb = bj + g;
-            const float b0 = (cb < n2 && ka < kb) ? (float)u12[ka * n2 + cb] : 0.f;
-            const float b1 = (cb < n2 && kc < kb) ? (float)u12[kc * n2 + cb] : 0.f;
-            mma_tf32_16x8x8(c, a0, a1, a2, a3, b0, b1);
-          }
-          const int r0 = bi + g, cc0 = bj + 2 * t4;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = r0 + ((q >> 1) << 3), cc = cc0 + (q & 1);
-            if (r < m2 && cc < n2) A[(int64_t)(k0 + kb + r) * L + k0 + kb + cc] -= (T)c[q];
-          }
-        }
-        block_sync();
-        continue;
+      if constexpr (sizeof(T) == 4) {
+        if (use_tc && !lu_trailing_tc(A, L, k0, kb, kbp, m2, n2, Npad, pan, u12, tc)) sing = 1;
       }
+      if (use_tc) continue;
       // A22 -= L21 U12: 4 x 4 register tiles
-      const int tr = (m2 + 3) / 4, tc = (n2 + 3) / 4;
-      for (int t = tid; t < tr * tc; t += blockDim.x) {
-        const int bi = (t / tc) * 4, bj = (t % tc) * 4;
+      const int tr = (m2 + 3) / 4, tcl = (n2 + 3) / 4;
+      for (int t = tid; t < tr * tcl; t += blockDim.x) {
+        const int bi = (t / tcl) * 4, bj = (t % tcl) * 4;
         T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -389,7 +483,11 @@ __device__ void lu_solve(const T* __restrict__ A, int L, T* x) {
 // MAXL: largest level count the CTA takes (the large kernel 320 with 256
 // threads, the small one 64 with 64 threads: short block-wide steps cost few
 // warps, and several CTAs share an SM).
-template <typename T, int MAXL, int THREADS>
+// TC: the tensor-core instance (TF32 factors of the large systems).  A kernel
+// that holds tcgen05 instructions ran one CTA per SM where the same kernel
+// without them ran two (measured: the CUDA occupancy query reports 1 at any
+// shared-memory size), so the FP32 and FP64 instances carry none.
+template <typename T, int MAXL, int THREADS, bool TC = false>
 __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   extern __shared__ double sm[];
   double* sE = sm;                       // per-level vectors (MAXL each)
@@ -412,6 +510,29 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
   __shared__ int flag;
   __shared__ FixExpTables sfx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  // the tensor-core leg (TF32 factors of the large systems): TMEM for the
+  // accumulator, allocated for the whole persistent launch (the host sizes it
+  // so that the CTAs resident on an SM never ask for more than its 512
+  // columns); the CTA's state sits in the tail of the U12 buffer, which no
+  // FP32 panel reaches (a static variable would cost the SM its second CTA)
+  TcState* tcp = nullptr;
+  if constexpr (TC && sizeof(T) == 4 && MAXL > kSmallL && THREADS == 256) {
+    if (a.tmem_cols > 0) {
+      TcState* const ts = reinterpret_cast<TcState*>(reinterpret_cast<unsigned char*>(sU12) + kTcStateOff);
+      if (warp == 0) tc::tmem_alloc(&ts->taddr, (uint32_t)a.tmem_cols);
+      if (tid == 0) {
+        tc::bar_init(&ts->bar, 1);
+        ts->phase = 0;
+        ts->ncols = a.tmem_cols;
+        ts->ok = 1;
+        ts->err = a.tc_err;
+      }
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      tcp = ts;
+    }
+  }
   for (int k = tid; k < (int)(sizeof(FixExpTables) / 8); k += blockDim.x)
     reinterpret_cast<uint64_t*>(&sfx)[k] = reinterpret_cast<const uint64_t*>(&a.fx)[k];
   double* W = a.W64 + (int64_t)blockIdx.x * a.wlen;
@@ -702,7 +823,7 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
         block_sync();
         // a factor that meets an exactly zero pivot (entries of the scaled matrix
         // below the FP32 range count as zero) goes to the FP64 solve below
-        ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12, sizeof(T) == 4 && a.precision == XT_PREC_TF32_IR);
+        ok = lu_factor<T>(WT, L, nb, sPiv, sPan, sU12, tcp);
         lu_perm(sPiv, L, sPerm);
         for (int i = tid; i < L; i += blockDim.x) { sN[i] = 0.0; sRes[i] = sB[i]; }
         block_sync();
@@ -757,7 +878,9 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
           double* Wd = (double*)a.WT + (int64_t)blockIdx.x * a.wlen;   // reuse (FP64 sized)
           for (int e = tid; e < L * L; e += blockDim.x) Wd[e] = W[e];
           block_sync();
-          ok = lu_factor<double>(Wd, L, 16, sPiv, (double*)sPan, (double*)sU12);
+          // (8-column panels where the tensor-core state sits in the U12 tail:
+          // 8 x 312 doubles stay clear of it)
+          ok = lu_factor<double>(Wd, L, tcp ? 8 : 16, sPiv, (double*)sPan, (double*)sU12);
           lu_perm(sPiv, L, sPerm);
           for (int i = tid; i < L; i += blockDim.x) sN[i] = sB[sPerm[i]];
           block_sync();
@@ -806,6 +929,13 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
       if (a.iters) a.iters[cell * a.n_ion + z] = iters;
     }
     block_sync();
+  }
+  if constexpr (TC) {
+    if (tcp) {                           // every thread left the loop together
+      tc::fence_before();
+      __syncthreads();
+      if (warp == 0) tc::tmem_free(tcp->taddr, (uint32_t)a.tmem_cols);
+    }
   }
 }
 
@@ -945,6 +1075,11 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<double, kSeMaxL, kSeThreads>, kSeThreads, smem);
     cudaFuncSetAttribute(k_se<double, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<double, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
+  } else if (ti == 2) {
+    cudaFuncSetAttribute(k_se<float, kSeMaxL, kSeThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float, kSeMaxL, kSeThreads, true>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<float, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<float, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
   } else {
     cudaFuncSetAttribute(k_se<float, kSeMaxL, kSeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float, kSeMaxL, kSeThreads>, kSeThreads, smem);
@@ -1053,7 +1188,18 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
   a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_maxvar = p->newton_maxvar;
+  // TF32 factors: the large systems' trailing updates on the tensor cores, with
+  // TMEM columns such that the CTAs resident on an SM fit its 512 (a CTA's
+  // allocation would otherwise wait for one that never frees it)
+  if (p->precision == XT_PREC_TF32_IR) {
+    const int cols = 512 / std::max(per_sm, 1);
+    int pw = 32;
+    while (pw * 2 <= cols && pw < 256) pw *= 2;
+    a.tmem_cols = cols >= 32 ? pw : 0;
+    a.tc_err = B.cnt + 7;
+  }
   SeArgs as = a;                         // the small systems: own work range, counter, workspace
+  as.tmem_cols = 0;
   as.work = B.work + n_big; as.n_work = n_small; as.counter = B.cnt + 1;
   as.W64 = B.W64 + (size_t)grid * wlen; as.WT = B.WT + (size_t)grid * wlen; as.wlen = wlen_s;
   // one kernel (small = the 64-level one) on a work range
@@ -1064,16 +1210,18 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
       else k_se<float, kSmallL, kSmallThreads><<<g_, kSmallThreads, smem_s, s_>>>(args);
     } else {
       if (pi == 0) k_se<double, kSeMaxL, kSeThreads><<<g_, kSeThreads, smem, s_>>>(args);
+      else if (ti == 2) k_se<float, kSeMaxL, kSeThreads, true><<<g_, kSeThreads, smem, s_>>>(args);
       else k_se<float, kSeMaxL, kSeThreads><<<g_, kSeThreads, smem, s_>>>(args);
     }
   };
   auto launch_on = [&](const SeArgs& big, const SeArgs& small, cudaStream_t s_) {
-    cudaMemsetAsync(B.cnt, 0, 8 * sizeof(unsigned long long), s_);
+    cudaMemsetAsync(B.cnt, 0, 2 * sizeof(unsigned long long), s_);   // the two work counters
     launch_one(big, false, grid, s_);
     launch_one(small, true, grid_s, s_);
   };
   // ---- autotuner: panel width per 64-level bucket, timed on a sample of each
-  if (p->autotune && !B.tuned[ti] && !grouped) {
+  // (the tensor-core leg keeps panels of 32 columns, the width its operand tiles take)
+  if (p->autotune && !B.tuned[ti] && !grouped && ti != 2) {
     const int cand[3] = {8, 16, 32};
     for (int b = 0; b < 8; ++b) {
       // systems with L in [64 b, 64 b + 63] are contiguous in the longest-first list
@@ -1106,6 +1254,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     B.tuned[ti] = true;
   }
   for (int k = 0; k < 8; ++k) a.nb_bucket[k] = as.nb_bucket[k] = B.nb[ti][k];
+  XT_CUDA(c, cudaMemsetAsync(B.cnt + 7, 0, sizeof(unsigned long long), c->stream));   // tensor-core give-ups
   XT_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   if (grouped) {
     const int64_t cells_g = G.ncell / NG;
@@ -1201,6 +1350,13 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     stats->lu_flops = flops_lu;
     for (int k = 0; k < 8; ++k) stats->panel_width[k] = a.nb_bucket[k];
     stats->not_converged = (double)nnc;
+  }
+  if (p->precision == XT_PREC_TF32_IR) {
+    unsigned long long gave_up = 0;
+    XT_CUDA(c, cudaMemcpy(&gave_up, B.cnt + 7, sizeof(gave_up), cudaMemcpyDeviceToHost));
+    if (gave_up > 0)
+      return fail(c, XT_ETIMEOUT, "solve_nlte: " + std::to_string(gave_up) +
+                                      " CTAs did not see a tensor-core MMA complete within the bounded wait");
   }
   if (nsing > 0) return fail(c, XT_ENOTCONV, "solve_nlte: " + std::to_string(nsing) + " singular systems");
   return XT_OK;

@@ -54,3 +54,29 @@ def test_tf32_gemm_rows_and_columns_are_not_mixed(xt):
     D = xt.xt_selftest_tc(A, B)
     ref = A.astype(np.float64) @ B.astype(np.float64).T
     np.testing.assert_allclose(D, ref, rtol=2e-3, atol=0)
+
+
+def test_tensor_core_trailing_updates_in_the_rate_solve(xt):
+    """The TF32 leg of the batched solve (trailing updates of the LU on the
+    tensor cores) on systems of 250-300 levels (several 128-row tiles and two
+    column chunks per update): no system falls back to FP64, the refinement
+    converges in a few steps, and the populations agree with the FP32 leg's."""
+    import synth
+    import torch
+    w = synth.nlte_batch(n=3, seed=2, L_range=(250, 300))
+    out = {}
+    for prec in (xt.XT_PREC_FP32_IR, xt.XT_PREC_TF32_IR):
+        with xt.Context(0, torch.cuda.current_stream().cuda_stream) as ctx:
+            ctx.load(w)
+            pops = np.zeros((w.ncell, w.nlev))
+            st = xt.solve_nlte(ctx.h, w.upsilon, precision=prec, rates=xt.XT_RATES_JBAR,
+                               warm=xt.XT_WARM_CURRENT, jbar_W=w.jbar_W, jbar_TR=w.jbar_TR,
+                               levels_used=w.levels_used, pops_out=pops)
+        out[prec] = (pops, st)
+    (p32, s32), (ptc, stc) = out[xt.XT_PREC_FP32_IR], out[xt.XT_PREC_TF32_IR]
+    assert stc["fp64_fallbacks"] == 0 and stc["singular"] == 0, stc
+    assert stc["mean_iter"] <= 4.0 and stc["max_iter_used"] <= 8, stc
+    assert list(stc["panel_width"])[4:] == [32, 32, 32, 32]
+    nz = np.repeat(w.n_ion_density, np.diff(w.level_off), axis=1)
+    sig = (p32 >= 1e-30 * nz) & (nz > 0)
+    assert np.max(np.abs(ptc[sig] / p32[sig] - 1)) < 1e-8
