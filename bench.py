@@ -707,6 +707,8 @@ def main():
     ap.add_argument("--only-cfg5-loop", action="store_true",
                     help="print the 128^3 coupled-loop object alone (plain vs surrogate + mixed)")
     ap.add_argument("--nlte-n", type=int, default=64)
+    ap.add_argument("--nlte-precision", default="fp32", choices=["fp32", "tf32", "fp64"],
+                    help="with --only-nlte --nlte-once: the factor precision of that launch")
     ap.add_argument("--nlte-once", action="store_true",
                     help="with --only-nlte: one plain mixed-precision launch (profiling case)")
     ap.add_argument("--rounds-steps", type=int, default=1,
@@ -744,7 +746,8 @@ def main():
         w = synth.nlte_batch(n=args.nlte_n)
         ctx = xt.Context(local, torch.cuda.current_stream().cuda_stream)
         ctx.load(w)
-        st = xt.solve_nlte(ctx.h, w.upsilon, precision=xt.XT_PREC_FP32_IR, rates=xt.XT_RATES_JBAR,
+        prec = {"fp32": xt.XT_PREC_FP32_IR, "tf32": xt.XT_PREC_TF32_IR, "fp64": xt.XT_PREC_FP64}[args.nlte_precision]
+        st = xt.solve_nlte(ctx.h, w.upsilon, precision=prec, rates=xt.XT_RATES_JBAR,
                            jbar_W=w.jbar_W, jbar_TR=w.jbar_TR, levels_used=w.levels_used)
         ctx.close()
         print(json.dumps({"nlte_once": st}), flush=True)
