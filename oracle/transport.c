@@ -772,7 +772,8 @@ static double sph_exit(const prep_t *P, const double p0[3], const double n[3], c
 
 /* The event loop on the spherical grid (attenuation mode): as in trace, with
  * the walk through (r, theta, phi) cells; the packet's position is p0 + s n. */
-static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger, double *pkt) {
+static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger, double *pkt,
+                      xo_domain *dom) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     double ct = P->ct;
@@ -851,6 +852,14 @@ static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, do
             ledger[L_GUARD] += 1.0;
             goto done;
         }
+        if (dom && (idx[2] < dom->z_lo || idx[2] >= dom->z_hi)) {
+            /* the packet enters another domain's phi slices: hand its state on
+             * (Sec. 2.4.1), the path s from its emission point included */
+            st->nu_lab = nu_lab; st->N = N; st->cursor = cursor; st->events = events; st->s = s;
+            if (dom->n < dom->cap) state_pack(st, dom->out + dom->n * XO_STATE_FIELDS);
+            dom->n++;
+            return;
+        }
     }
 done:
     if (pkt) {
@@ -866,7 +875,7 @@ done:
 static void trace(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger,
                   double *pkt, double *S_pi, double *heat, xo_domain *dom) {
     if (P->pb->geometry == 1) {
-        trace_sph(P, st, S, spec, ledger, pkt);
+        trace_sph(P, st, S, spec, ledger, pkt, dom);
         return;
     }
     const xo_problem *pb = P->pb;

@@ -106,3 +106,60 @@ def test_ledger_closes():
     L = o["ledger"]
     assert L["events"] > 10_000 and L["guard"] == 0
     assert L["esc_N"] + L["abs_N"] + L["drop_N"] == pytest.approx(L["emit_N"], rel=1e-13)
+
+
+class _Domain:
+    """One phi-slab domain traced by the oracle; sums what its calls tally."""
+
+    def __init__(self, w, z_lo, z_hi):
+        self.w, self.z_lo, self.z_hi = w, z_lo, z_hi
+        self.S = self.spec = None
+        self.ledger = {}
+
+    def step(self, emit, bundle_in):
+        import torch
+        b = None if bundle_in is None else bundle_in.numpy()
+        o = oracle.transport_domain(self.w, self.z_lo, self.z_hi, emit, b)
+        self.S = o["S"] if self.S is None else self.S + o["S"]
+        self.spec = o["spec"] if self.spec is None else self.spec + o["spec"]
+        for k, v in o["ledger"].items():
+            self.ledger[k] = self.ledger.get(k, 0.0) + v
+        return torch.from_numpy(o["bundle"])
+
+    def z_of(self, bundle):
+        import torch
+        return bundle[:, oracle.STATE_Z].to(torch.int64)
+
+
+@pytest.mark.parametrize("world", [1, 3, 4])
+def test_phi_slab_domains_sum_to_the_whole(world):
+    """The paper's decomposition of the spherical grid (Sec. 2.4.1): each domain
+    holds whole phi slices; a packet entering another domain's slices is handed
+    on with its state (the path from its emission point included) and resumes
+    there.  The domains' sums equal the single-domain pass; phi wraps around,
+    and a straight ray crosses each slab boundary at most once."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2511_07539_gb300 import spatial
+    w = synth.spherical_sphere(n_packets=20_000, seed=5, clumps=True)      # 12 phi slices
+    w.pops = w.pops * 1e-3
+    doms = [_Domain(w, *spatial.slab(r, w.nz, world)) for r in range(world)]
+    rounds = spatial.run_local(doms, w.nz)
+    assert (rounds == 0) == (world == 1) and rounds <= world - 1
+    S, spec = sum(d.S for d in doms), sum(d.spec for d in doms)
+    ref = oracle.transport(w)
+    m = ref["S"] != 0
+    assert np.array_equal(S != 0, m)
+    assert np.max(np.abs(S[m] / ref["S"][m] - 1)) < 1e-12
+    ms = ref["spec"] != 0
+    assert np.array_equal(spec != 0, ms)
+    assert np.max(np.abs(spec[ms] / ref["spec"][ms] - 1)) < 1e-12
+    tot = {}
+    for d in doms:
+        for k, v in d.ledger.items():
+            tot[k] = tot.get(k, 0.0) + v
+    L = ref["ledger"]
+    assert tot["events"] == L["events"] and tot["tests"] == L["tests"]
+    for k in ("emit_N", "esc_N", "abs_N", "drop_N", "esc_E"):
+        assert tot[k] == pytest.approx(L[k], rel=1e-12)
