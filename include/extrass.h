@@ -207,7 +207,8 @@ typedef struct {
 /* On a spherical grid (XT_GEOM_SPHERICAL) run_transport takes attenuation
  * mode with Monte Carlo packets, without subdomain rounds and without
  * photoionization data, with the estimator store on the device (dense or
- * compact rows); other passes, and run_transport_domain, return XT_EINVAL.
+ * compact rows; run_transport_domain with phi-slice domains); other passes
+ * return XT_EINVAL.
  * Packets start uniformly in their cell's volume (r^3, cos theta and phi
  * uniform) and walk from cell to cell through the shells' spheres, the polar
  * edges' cones (the plane z = 0 for theta = pi/2) and the azimuthal edges'
@@ -534,7 +535,13 @@ int run_transport_noalloc(const xt_noalloc_transport *a, void *cuda_stream,
  * packet records.  Results summed over the domains equal run_transport's on
  * the whole grid (up to the order of additions); a packet's trajectory does
  * not depend on the decomposition.  bundle_in and bundle_out may be host or
- * device memory. */
+ * device memory.  An entry of bundle_in whose cell lies outside the grid, or
+ * whose line cursor (entry[XT_BUNDLE_CELL + 1]) lies outside [0, nline], makes
+ * the call return XT_EINVAL before anything is traced.  On a spherical grid
+ * the domains are slices of whole azimuthal sectors (z is the phi index; the
+ * paper's decomposition of its spherical grid, Sec. 2.4.1), phi wrapping
+ * around, and a handed-on state carries the packet's path from its emission
+ * point. */
 #define XT_BUNDLE_FIELDS 24
 #define XT_BUNDLE_CELL 17
 int run_transport_domain(xt_ctx *ctx, const xt_transport_params *p, int32_t z_lo, int32_t z_hi,

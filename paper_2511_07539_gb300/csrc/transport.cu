@@ -1298,6 +1298,14 @@ __device__ __noinline__ double sph_next(const double* __restrict__ tab, int tnx,
   return INFINITY;
 }
 
+// DOM: one domain of a spatial decomposition across processes (Sec. 2.4.1,
+// rounds == 3): work items below em.n are the domain's own packets, emitted
+// here; the rest resume from the pool (states received from other domains).
+// A packet that enters a cell outside the domain's phi slices [dom_zlo,
+// dom_zhi) leaves: its state (emission point, direction, lab and comoving
+// frequency, photons, energy cut, path s, cursor, events, cell) goes to the
+// pool and its slot to the out list.
+template <bool DOM>
 __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
@@ -1344,7 +1352,30 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
         base = __shfl_sync(full, base, leader);
         if (base + __popc(m) >= (unsigned long long)a.n_list) drained = true;
         const unsigned long long my = base + __popc(m & ((1u << lane) - 1u));
-        if (!have && my < (unsigned long long)a.n_list) {
+        if (DOM && !have && my < (unsigned long long)a.n_list && my >= (unsigned long long)em.n) {
+          // ---- a packet handed on by another domain resumes
+          i = (int)my;
+          const int cs = P.cell[i];
+          ix = cs & 1023; iy = (cs >> 10) & 1023; iz = cs >> 20;
+          p0x = P.F(F_R0X, i); p0y = P.F(F_R0Y, i); p0z = P.F(F_R0Z, i);
+          nxv = P.F(F_NX, i); nyv = P.F(F_NY, i); nzv = P.F(F_NZ, i);
+          nu_cmf = P.F(F_NU0, i);
+          aslope = P.F(F_NULAB, i) * a.inv_ct;
+          N = P.F(F_N, i);
+          N_in = N;
+          Tq = P.F(F_T, i);
+          s = P.F(F_TMX, i);
+          cursor = P.cursor[i];
+          events = P.events[i];
+          faces = 0;
+          b = nxv * p0x + nyv * p0y + nzv * p0z;
+          pp = p0x * p0x + p0y * p0y + p0z * p0z;
+          row = RX[ix] + RY[iy] + RZ[iz];
+          s_r = sph_next(g.sph, g.nx, g.ny, g.nz, 0, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, s, &k_r);
+          s_t = sph_next(g.sph, g.nx, g.ny, g.nz, 1, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, s, &k_t);
+          s_p = sph_next(g.sph, g.nx, g.ny, g.nz, 2, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, s, &k_p);
+          have = true;
+        } else if (!have && my < (unsigned long long)a.n_list) {
           // ---- emission
           i = (int)my;
           const int64_t p = em.p_begin + (int64_t)my;
@@ -1417,7 +1448,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
     if (bits(s_t) < bits(s_exit)) { s_exit = s_t; kind = k_t; }   // ties to the lower kind
     if (bits(s_p) < bits(s_exit)) { s_exit = s_p; kind = k_p; }
     int fate = -1, fam = 0;
-    bool escaped = false;
+    bool escaped = false, queued = false;
     if (kind < 0 || ++faces > max_faces) {
       ++n_guard;
       fate = 3;
@@ -1460,6 +1491,16 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
           iz = kind == 4 ? (iz == 0 ? g.nz - 1 : iz - 1) : (iz == g.nz - 1 ? 0 : iz + 1);
         }
         if (!escaped) row = RX[ix] + RY[iy] + RZ[iz];
+        if (DOM && !escaped && (iz < a.dom_zlo || iz >= a.dom_zhi)) {
+          // ---- the packet enters another domain's slices: its state goes on
+          queued = true;
+          P.F(F_R0X, i) = p0x; P.F(F_R0Y, i) = p0y; P.F(F_R0Z, i) = p0z;
+          P.F(F_NU0, i) = nu_cmf;
+          P.F(F_T, i) = Tq;
+          P.F(F_TMX, i) = s;
+          P.cursor[i] = cursor;
+          P.cell[i] = ix | (iy << 10) | (iz << 20);
+        }
       }
     }
     // ---- the crossed family's next face, solved by every busy lane of the
@@ -1468,7 +1509,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
     // than solving inside the lanes' own branches
     __syncwarp(busy);
     {
-      const bool solve = fate < 0 && !escaped;
+      const bool solve = fate < 0 && !escaped && !queued;
       int kn;
       const double sn = sph_next(g.sph, g.nx, g.ny, g.nz, fam, p0x, p0y, p0z, nxv, nyv, nzv, b, pp,
                                  solve ? ix : 0, solve ? iy : 0, solve ? iz : 0, s, &kn);
@@ -1479,7 +1520,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
       }
     }
     // ---- the packet leaves the lane
-    if (escaped || fate >= 0) {
+    if (escaped || queued || fate >= 0) {
       P.F(F_N, i) = N;
       P.events[i] = events;
       acc[T_ABS] += N_in - N;
@@ -1491,6 +1532,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
       have = false;
     }
     warp_append(escaped, i, a.esc, a.n_esc);
+    if (DOM) warp_append(queued, i, a.out, a.n_out);
   }
   __syncwarp();
   __syncthreads();
@@ -1591,14 +1633,23 @@ __global__ void k_iota(int* __restrict__ out, int64_t n) {
 // doubles (the NF state fields, then cell, cursor, events, draws,
 // interactions and id; integers exactly).
 static_assert(NF + 6 <= XT_BUNDLE_FIELDS && NF == XT_BUNDLE_CELL, "bundle layout");
-__global__ void k_bundle_in(Pool P, const double* __restrict__ in, int64_t n, int64_t base) {
+// Received packet states into the pool; entries whose cell lies outside the
+// grid or whose line cursor lies outside [0, nline] are counted in *bad (the
+// caller refuses the bundle before any trace kernel reads the pool).
+__global__ void k_bundle_in(Pool P, const double* __restrict__ in, int64_t n, int64_t base, Geometry g,
+                            int nline, unsigned long long* __restrict__ bad) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
     const double* e = in + j * XT_BUNDLE_FIELDS;
     const int64_t i = base + j;
 #pragma unroll
     for (int k = 0; k < NF; ++k) P.F(k, i) = e[k];
-    P.cell[i] = (int)e[NF]; P.cursor[i] = (int)e[NF + 1]; P.events[i] = (int)e[NF + 2];
+    const double cd = e[NF], ud = e[NF + 1];
+    const bool ok = cd >= 0.0 && cd < 1073741824.0 && ud >= 0.0 && ud <= (double)nline;
+    const int cs = ok ? (int)cd : 0;
+    const int cx = cs & 1023, cy = (cs >> 10) & 1023, cz = cs >> 20;
+    if (!ok || cx >= g.nx || cy >= g.ny || cz >= g.nz) atomicAdd(bad, 1ull);
+    P.cell[i] = cs; P.cursor[i] = ok ? (int)ud : 0; P.events[i] = (int)e[NF + 2];
     P.ndraw[i] = (int)e[NF + 3]; P.inter[i] = (int)e[NF + 4]; P.pid[i] = (int64_t)e[NF + 5];
   }
 }
@@ -1924,11 +1975,10 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
   const bool sph = c->geometry == XT_GEOM_SPHERICAL;
-  if (sph && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->dom.active ||
-              c->npi > 0))
+  if (sph && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->npi > 0))
     return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode with Monte Carlo packets, "
-                              "without subdomain rounds, packet states between domains or photoionization data, "
-                              "with the estimator store on the device");
+                              "without subdomain rounds or photoionization data, with the estimator store on "
+                              "the device");
   RayTables rtab_rays{};
   const double* ray_Lc = nullptr;
   int64_t n_total = p->n_packets;
@@ -2184,7 +2234,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
 
   int occ = 0;
   if (sph)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_sph, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_sph<false>, 256, 0);
   else if (rays && pi)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true, true>, 256, 0);
   else if (rays)
@@ -2343,9 +2393,10 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     // one launch: the domain's own packets and the received bundle, traced
     // until they end or leave the domain; those are written out as a bundle
     int sl;
-    if (dom_emit > 0) {
-      ea.p_begin = dom_e0;
-      ea.n = dom_emit;
+    ea.p_begin = dom_e0;
+    ea.n = dom_emit;
+    ta.em = ea;                        // (the spherical walk emits the domain's packets itself)
+    if (dom_emit > 0 && !sph) {
       sl = tick(0);
       k_emit<<<blocks_for(dom_emit, 256, 16), 256, 0, c->stream>>>(ea);
       XT_CUDA(c, cudaGetLastError());
@@ -2361,9 +2412,18 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
         if ((rc = copy(c, c->d_scratch, src, in_b, "bundle in"))) return rc;
         src = (const double*)c->d_scratch;
       }
-      k_bundle_in<<<blocks_for(n_in, 256, 8), 256, 0, c->stream>>>(P, src, n_in, dom_emit);
+      XT_CUDA(c, cudaMemsetAsync(counters + 6, 0, sizeof(unsigned long long), c->stream));
+      k_bundle_in<<<blocks_for(n_in, 256, 8), 256, 0, c->stream>>>(P, src, n_in, dom_emit, G, c->nline,
+                                                                    counters + 6);
       XT_CUDA(c, cudaGetLastError());
       ++kernels;
+      unsigned long long bad = 0;
+      XT_CUDA(c, cudaMemcpyAsync(&bad, counters + 6, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+      XT_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (bad > 0)
+        return fail(c, XT_EINVAL, "run_transport_domain: " + std::to_string(bad) +
+                                      " bundle_in entries with a cell outside the grid or a line cursor "
+                                      "outside [0, nline]");
     }
     c->dom.n_out = 0;
     if (count > 0) {
@@ -2376,7 +2436,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = qA;
       const int grid = (int)std::min<int64_t>(grid_max, (count + 255) / 256);
       sl = tick(1);
-      if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph) k_trace_sph<true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
       XT_CUDA(c, cudaGetLastError());
@@ -2530,7 +2591,7 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (sph) k_trace_sph<<<grid, 256, 0, c->stream>>>(ta);
+      if (sph) k_trace_sph<false><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && staged) {
         const int64_t gpb = std::max<int64_t>(1, kStageRays / ea.ray.nview);

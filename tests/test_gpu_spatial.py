@@ -79,3 +79,64 @@ def test_domains_sum_to_the_whole_grid(xt, world, pi):
     _cmp(spec, spec_ref, 1e-9, "spectrum")
     if pi:
         _cmp(G, G_ref, 1e-10, "photoionization rates")
+
+
+@pytest.mark.parametrize("world", [3, 4])
+def test_phi_slab_domains_on_the_spherical_grid(xt, world):
+    """The paper's decomposition of its spherical grid (Sec. 2.4.1): domains of
+    whole phi slices (the azimuthal index is the grid's third), packets handed
+    on with their path from the emission point; phi wraps around.  The sums
+    over the domains equal one run_transport of the whole grid."""
+    import torch
+    from paper_2511_07539_gb300 import spatial
+    w = synth.spherical_sphere(n_packets=200_000, seed=5, clumps=True)      # 12 phi slices
+    w.pops = w.pops * 1e-3
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = dict(n_packets=w.n_packets, seed=w.seed, spec_lam0_A=w.spec_band_A[0],
+              spec_nbins=w.spec_band_A[1])
+    ref = xt.Context(0, stream)
+    ref.load(w)
+    st = ref.transport(w)
+    S_ref, spec_ref = ref.get_estimators(), ref.get_spectrum(0)
+    ref.close()
+    ctxs, trs = [], []
+    for r in range(world):
+        c = xt.Context(0, stream)
+        c.load(w)
+        ctxs.append(c)
+        trs.append(spatial.LibDomainTracer(c, *spatial.slab(r, w.nz, world), **kw))
+    rounds = spatial.run_local(trs, w.nz)
+    assert 1 <= rounds <= world - 1
+    S = np.zeros_like(S_ref)
+    spec = np.zeros_like(spec_ref)
+    ev = tests = 0.0
+    nxy = w.nx * w.ny
+    for r, (c, t) in enumerate(zip(ctxs, trs)):
+        z0, z1 = spatial.slab(r, w.nz, world)
+        S[z0 * nxy:z1 * nxy] = c.get_estimators(z0 * nxy, (z1 - z0) * nxy)
+        spec += c.get_spectrum(0)
+        ev += t.stats[-1]["events"]
+        tests += t.stats[-1]["tests"]
+        c.close()
+    assert ev == st["events"] and tests == st["tests"]
+    _cmp(S, S_ref, 1e-10, "estimators")
+    _cmp(spec, spec_ref, 1e-9, "spectrum")
+
+
+def test_malformed_bundle_is_refused(xt):
+    """A received state whose cell lies outside the grid, or whose line cursor
+    lies outside the line list, is refused (XT_EINVAL) before it is traced."""
+    import torch
+    w = synth.spherical_sphere(n_packets=2_000, seed=5)
+    with xt.Context(0, torch.cuda.current_stream().cuda_stream) as ctx:
+        ctx.load(w)
+        for cell, cursor in [(float(1 << 30), 0.0), (float(w.nx | (w.ny << 10)), 0.0),
+                             (0.0, float(w.nline + 1)), (-1.0, 0.0)]:
+            b = np.zeros((1, xt.XT_BUNDLE_FIELDS))
+            b[0, xt.XT_BUNDLE_CELL] = cell
+            b[0, xt.XT_BUNDLE_CELL + 1] = cursor
+            with pytest.raises(xt.XtError) as e:
+                xt.run_transport_domain(ctx.h, 0, w.nz, False, bundle_in=b, n_packets=w.n_packets,
+                                        seed=w.seed, spec_lam0_A=w.spec_band_A[0],
+                                        spec_nbins=w.spec_band_A[1])
+            assert e.value.code == xt.XT_EINVAL
