@@ -1076,8 +1076,13 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     cudaFuncSetAttribute(k_se<double, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<double, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
   } else if (ti == 2) {
+    // the occupancy query reports one CTA per SM for the instance that holds
+    // tcgen05 code, but the SM runs two (measured: 1.55x faster launched at
+    // two per SM); the launch takes the residency of the same kernel without
+    // that code (same shared memory, more registers)
     cudaFuncSetAttribute(k_se<float, kSeMaxL, kSeThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float, kSeMaxL, kSeThreads, true>, kSeThreads, smem);
+    cudaFuncSetAttribute(k_se<float, kSeMaxL, kSeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_se<float, kSeMaxL, kSeThreads>, kSeThreads, smem);
     cudaFuncSetAttribute(k_se<float, kSmallL, kSmallThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_se<float, kSmallL, kSmallThreads>, kSmallThreads, smem_s);
   } else {
@@ -1192,7 +1197,14 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   // TMEM columns such that the CTAs resident on an SM fit its 512 (a CTA's
   // allocation would otherwise wait for one that never frees it)
   if (p->precision == XT_PREC_TF32_IR) {
-    const int cols = 512 / std::max(per_sm, 1);
+    // residency bound by shared memory (1 KB per CTA reserved by the system),
+    // whatever the launch assumed: TMEM columns x resident CTAs <= 512
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device);
+    cudaFuncAttributes fa_tc;
+    cudaFuncGetAttributes(&fa_tc, k_se<float, kSeMaxL, kSeThreads, true>);
+    const int res_smem = std::max(1, (int)((size_t)smem_sm / (smem + fa_tc.sharedSizeBytes + 1024)));
+    const int cols = 512 / std::max(std::max(per_sm, res_smem), 1);
     int pw = 32;
     while (pw * 2 <= cols && pw < 256) pw *= 2;
     a.tmem_cols = cols >= 32 ? pw : 0;
