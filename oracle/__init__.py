@@ -208,8 +208,8 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     keep = _Keep(w, upsilon_down_sums(w) if mode == "scatter" else None)
     if keep.n_pi and mode != "atten":
         raise ValueError("photoionization is part of the attenuation mode only")
-    if keep.sph and (mode != "atten" or keep.n_pi or sampler != "mc"):
-        raise ValueError("the spherical grid: attenuation mode, Monte Carlo packets, no photoionization")
+    if keep.sph and (mode != "atten" or keep.n_pi):
+        raise ValueError("the spherical grid: attenuation mode, no photoionization")
     S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
     heat = np.zeros(w.ncell) if keep.n_pi else None
     lam0, nbins = w.spec_band_A

@@ -653,6 +653,13 @@ static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, d
         rr[a] = (-P->R + idx[a] * d[a]) + 0.5 * d[a];     /* the middle of the cell */
         n[a] = P->view_n[3 * k + a];
     }
+    if (pb->geometry == 1) {
+        /* spherical cell: the middle of its radius, polar and azimuthal ranges */
+        double rm = 0.5 * (P->sR[idx[0]] + P->sR[idx[0] + 1]);
+        double th = 0.5 * (pb->th_edges[idx[1]] + pb->th_edges[idx[1] + 1]);
+        double ph = 0.5 * (pb->ph_edges[idx[2]] + pb->ph_edges[idx[2] + 1]);
+        rr[0] = rm * sin(th) * cos(ph); rr[1] = rm * sin(th) * sin(ph); rr[2] = rm * cos(th);
+    }
     propagate(P, r, c, idx, rr, n, P->rbin_nu[jb], P->rbin_cursor[jb], E0, S, spec, ledger, pkt, S_pi, heat,
               NULL);
 }

@@ -163,3 +163,70 @@ def test_phi_slab_domains_sum_to_the_whole(world):
     assert tot["events"] == L["events"] and tot["tests"] == L["tests"]
     for k in ("emit_N", "esc_N", "abs_N", "drop_N", "esc_E"):
         assert tot[k] == pytest.approx(L[k], rel=1e-12)
+
+
+def _thin_single_line(w, lam_A=6000.0):
+    w.lambda_A = np.array([lam_A])
+    w.f_lu = np.array([1e-3])
+    w.lo = np.array([0], np.int32)
+    w.up = np.array([1], np.int32)
+    w.pops = w.pops * 1e-30
+    w.pops[:, 1] = w.pops[:, 0]
+    return w
+
+
+def test_thin_rays_on_the_spherical_grid():
+    """The RAYS sampler on the spherical grid (Sec. 2.3), optically thin: every
+    ray escapes into its own viewer, and the comoving energy per viewer is the
+    emission times dOmega_k / 4 pi."""
+    nt, nph = 6, 8
+    w = synth.spherical_sphere(n_packets=1, seed=3, nr=6, nth=4, nph=6)
+    w.pops = w.pops * 1e-30
+    o = oracle.transport(w, sampler="rays", n_theta=nt, n_phi=nph, spec_dlog=0.01, per_packet=True)
+    L = o["ledger"]
+    assert L["events"] == 0
+    assert L["emit_E"] == pytest.approx(w.L_cell.sum(), rel=1e-9)
+    pk = o["pkt"]
+    Ecmf = pk[:, 8] * 6.62607015e-27 * pk[:, 9]
+    k = np.arange(o["n"]) % (nt * nph)
+    per_view = np.bincount(k, weights=Ecmf, minlength=nt * nph)
+    th = np.linspace(0.0, np.pi, nt + 1)
+    dOm = np.repeat(2 * np.pi / nph * (np.cos(th[:-1]) - np.cos(th[1:])), nph)
+    np.testing.assert_allclose(per_view, w.L_cell.sum() * dOm / (4 * np.pi), rtol=1e-10)
+    assert np.array_equal(pk[:, 4], k.astype(float))
+
+
+def test_single_line_rays_start_at_the_cell_middle():
+    """One thin emission line, rays on the spherical grid: every ray's lab
+    wavelength follows from the middle of its cell's r, theta and phi ranges and
+    its viewer's direction by the first-order Doppler formula; the spectrum
+    binned from that restatement equals the oracle's."""
+    w = _thin_single_line(synth.spherical_sphere(n_packets=1, seed=7, nr=5, nth=4, nph=6, n_lines=1,
+                                                 n_levels=2))
+    nt, nph, dlog = 5, 8, 2e-4
+    lam0 = 6000.0 * (1 - 0.03)
+    nb = int(np.log(1.06 / 0.97) / np.log1p(dlog)) + 1
+    w.spec_band_A = (lam0, nb)
+    o = oracle.transport(w, sampler="rays", emission="lines", n_theta=nt, n_phi=nph, spec_dlog=dlog)
+    nu_l = C / (6000.0 * 1e-8)
+    spec = np.zeros((nt * nph, nb))
+    Lc, _ = oracle.emission(w, n_packets=1, emission="lines")
+    th = np.linspace(0.0, np.pi, nt + 1)
+    w_k = np.repeat(2 * np.pi / nph * (np.cos(th[:-1]) - np.cos(th[1:])), nph) / (4 * np.pi)
+    for c in np.nonzero(Lc > 0)[0]:
+        ir, it_, ip_ = c % w.nx, (c // w.nx) % w.ny, c // (w.nx * w.ny)
+        rm = 0.5 * (w.r_edges[ir] + w.r_edges[ir + 1]) * w.t
+        tm = 0.5 * (w.theta_edges[it_] + w.theta_edges[it_ + 1])
+        pm = 0.5 * (w.phi_edges[ip_] + w.phi_edges[ip_ + 1])
+        r = rm * np.array([np.sin(tm) * np.cos(pm), np.sin(tm) * np.sin(pm), np.cos(tm)])
+        for it in range(nt):
+            for ip in range(nph):
+                k = it * nph + ip
+                tc, pc = np.pi * (it + 0.5) / nt, 2 * np.pi * (ip + 0.5) / nph
+                n = np.array([np.sin(tc) * np.cos(pc), np.sin(tc) * np.sin(pc), np.cos(tc)])
+                nu_lab = nu_l / (1 - n @ r / (C * w.t))
+                b = int(np.floor(np.log(C / nu_lab * 1e8 / lam0) / np.log1p(dlog)))
+                spec[k, b] += Lc[c] * w_k[k] * nu_lab / nu_l
+    m = spec > 0
+    assert np.array_equal(m, o["spec"] > 0)
+    np.testing.assert_allclose(o["spec"][m], spec[m], rtol=1e-12)
