@@ -399,12 +399,14 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
     // 0, cos and sin phi with edge nz taken as edge 0, phi) and the volumes
     // (r1^3 - r0^3) / 3 (cos theta0 - cos theta1) (phi1 - phi0), natural order
     const int nx = g->nx, ny = g->ny, nz = g->nz;
-    tab.assign((size_t)(nx + 1) + (ny + 1) + 3 * (size_t)(nz + 1), 0.0);
+    tab.assign((size_t)(nx + 1) + 2 * (size_t)(ny + 1) + 3 * (size_t)(nz + 1), 0.0);
     double* sR = tab.data();
     double* cth = sR + nx + 1;
     double* cph = cth + ny + 1;
     double* sphi = cph + nz + 1;
     double* phe = sphi + nz + 1;
+    double* the = phe + nz + 1;
+    for (int j = 0; j <= ny; ++j) the[j] = te[j];
     std::vector<double> ct_raw(ny + 1);
     for (int i = 0; i <= nx; ++i) sR[i] = re[i] * g->t;
     for (int j = 0; j <= ny; ++j) {

@@ -1305,7 +1305,8 @@ __device__ __noinline__ double sph_next(const double* __restrict__ tab, int tnx,
 // dom_zhi) leaves: its state (emission point, direction, lab and comoving
 // frequency, photons, energy cut, path s, cursor, events, cell) goes to the
 // pool and its slot to the out list.
-template <bool DOM>
+// RAYS: the rays of the RAYS sampler instead of Monte Carlo packets.
+template <bool DOM, bool RAYS = false>
 __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
@@ -1321,6 +1322,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   const double* const sR = g.sph;
   const double* const cth = sR + g.nx + 1;
   const double* const phe = cth + g.ny + 1 + 2 * (g.nz + 1);
+  const double* const the = phe + g.nz + 1;
   const int* RX = a.rtab;
   const int* RY = a.rtab + g.nx;
   const int* RZ = a.rtab + g.nx + g.ny;
@@ -1379,8 +1381,50 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
           // ---- emission
           i = (int)my;
           const int64_t p = em.p_begin + (int64_t)my;
-          const int64_t c = quota_cell(em, p);
+          int64_t c;
           int idx[3];
+          double E0;
+          bool live = true;
+          if constexpr (RAYS) {
+            // ray p (Sec. 2.3): (emitting-cell rank, bin rank, viewer), from the
+            // middle of the cell's r, theta and phi ranges along the viewer's
+            // centre direction, carrying the bin's emission times dOmega / 4 pi
+            const RayTables& T = em.ray;
+            const int64_t per_cell = T.nbin * T.nview;
+            const int64_t ci = p / per_cell, rem = p - ci * per_cell, jb = rem / T.nview;
+            const int kv = (int)(rem - jb * T.nview);
+            c = T.rcell[ci];
+            {
+              const uint32_t c32 = (uint32_t)c, gx = (uint32_t)g.nx, gy = (uint32_t)g.ny;
+              const uint32_t cy = c32 / gx;
+              idx[0] = (int)(c32 - cy * gx); idx[1] = (int)(cy % gy); idx[2] = (int)(cy / gy);
+            }
+            const double2 v01 = __ldg(reinterpret_cast<const double2*>(T.view) + 2 * kv);
+            const double2 v23 = __ldg(reinterpret_cast<const double2*>(T.view) + 2 * kv + 1);
+            const double E_bin = T.Ebin ? T.Ebin[row_of(g, idx[0], idx[1], idx[2]) * T.nbin + jb]
+                                        : em.Lc[c] * T.bin_frac[jb];
+            E0 = E_bin * v23.y;
+            if (!(E0 > 0.0)) {                 // an empty ray: recorded, not traced
+              if (a.records) {
+                double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+                rec[0] = 4.0; rec[1] = 0.0; rec[2] = 0.0; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
+                rec[6] = 0.0; rec[7] = (double)c; rec[8] = 0.0; rec[9] = 0.0; rec[10] = 0.0;
+              }
+              live = false;                    // (the lane stays empty; no early continue: every
+            }                                  //  lane reaches the warp-wide ballot below)
+            nxv = v01.x; nyv = v01.y; nzv = v23.x;
+            const double rm = 0.5 * (sR[idx[0]] + sR[idx[0] + 1]);
+            const double tm = 0.5 * (the[idx[1]] + the[idx[1] + 1]);
+            const double pm = 0.5 * (phe[idx[2]] + phe[idx[2] + 1]);
+            double st, ct, sp, cp;
+            sincos(tm, &st, &ct);
+            sincos(pm, &sp, &cp);
+            p0x = rm * st * cp; p0y = rm * st * sp; p0z = rm * ct;
+            nu_cmf = T.bin_nu[jb];
+            cursor = T.bin_cursor[jb];
+          } else {
+          c = quota_cell(em, p);
+          E0 = em.Epk[c];
           {
             const uint32_t c32 = (uint32_t)c, gx = (uint32_t)g.nx, gy = (uint32_t)g.ny;
             const uint32_t cy = c32 / gx;
@@ -1407,35 +1451,43 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
           isotropic(trig, xu[3] >> 11, xv[0] >> 11, n);
           nxv = n[0]; nyv = n[1]; nzv = n[2];
           emit_frequency(em, xv[1], c, idx, nu_cmf, cursor);
-          b = nxv * p0x + nyv * p0y + nzv * p0z;
-          pp = p0x * p0x + p0y * p0y + p0z * p0z;
-          const double nu_lab = div_pos(nu_cmf, 1.0 - b * a.inv_ct);
-          aslope = nu_lab * a.inv_ct;                      // d nu_cmf / ds
-          N = div_pos(em.Eph[c], nu_cmf);                  // E0 / (h nu_cmf)
-          N_in = N;
-          Tq = em.e_cut * em.Eph[c];
-          P.F(F_NX, i) = nxv; P.F(F_NY, i) = nyv; P.F(F_NZ, i) = nzv;
-          P.F(F_NULAB, i) = nu_lab;
-          P.pid[i] = p;
-          acc[T_EMITN] += N;
-          acc[T_EMITE] += em.Epk[c];
-          if (a.records) {
-            P.inter[i] = 0;
-            double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
-            rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
           }
-          ix = idx[0]; iy = idx[1]; iz = idx[2];
-          row = RX[ix] + RY[iy] + RZ[iz];
-          s = 0.0;
-          events = 0;
-          faces = 0;
-          s_r = sph_next(g.sph, g.nx, g.ny, g.nz, 0, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
-                           &k_r);
-          s_t = sph_next(g.sph, g.nx, g.ny, g.nz, 1, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
-                           &k_t);
-          s_p = sph_next(g.sph, g.nx, g.ny, g.nz, 2, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
-                           &k_p);
-          have = true;
+          if (live) {
+            b = nxv * p0x + nyv * p0y + nzv * p0z;
+            pp = p0x * p0x + p0y * p0y + p0z * p0z;
+            const double nu_lab = div_pos(nu_cmf, 1.0 - b * a.inv_ct);
+            aslope = nu_lab * a.inv_ct;                      // d nu_cmf / ds
+            if constexpr (RAYS) {
+              N = div_pos(E0, kH * nu_cmf);
+              Tq = (em.e_cut * E0) * (1.0 / kH);
+            } else {
+              N = div_pos(em.Eph[c], nu_cmf);                // E0 / (h nu_cmf)
+              Tq = em.e_cut * em.Eph[c];
+            }
+            N_in = N;
+            P.F(F_NX, i) = nxv; P.F(F_NY, i) = nyv; P.F(F_NZ, i) = nzv;
+            P.F(F_NULAB, i) = nu_lab;
+            P.pid[i] = p;
+            acc[T_EMITN] += N;
+            acc[T_EMITE] += E0;
+            if (a.records) {
+              P.inter[i] = 0;
+              double* rec = a.records + (p - a.rec_base) * XT_PKT_FIELDS;
+              rec[7] = (double)c; rec[8] = N; rec[9] = nu_cmf;
+            }
+            ix = idx[0]; iy = idx[1]; iz = idx[2];
+            row = RX[ix] + RY[iy] + RZ[iz];
+            s = 0.0;
+            events = 0;
+            faces = 0;
+            s_r = sph_next(g.sph, g.nx, g.ny, g.nz, 0, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                             &k_r);
+            s_t = sph_next(g.sph, g.nx, g.ny, g.nz, 1, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                             &k_t);
+            s_p = sph_next(g.sph, g.nx, g.ny, g.nz, 2, p0x, p0y, p0z, nxv, nyv, nzv, b, pp, ix, iy, iz, 0.0,
+                             &k_p);
+            have = true;
+          }
         }
       }
     }
@@ -1754,7 +1806,7 @@ __global__ void k_ray_line_bins(Geometry g, const double2* __restrict__ lines, c
       const LineRec L = ldline(lines, s);
       const double nu_ = pc[__double2hiint(L.w)];
       const double tau = L.y * (pc[__double2loint(L.w)] - L.z * nu_);
-      const double w = A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * V;
+      const double w = A[s] * (kH * L.x) * sobolev_beta(tau) * nu_ * (g.vol ? g.vol[row] : V);
       run += w;
       er[bin_of_line[l]] += w;
     }
@@ -1975,10 +2027,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
   const bool sph = c->geometry == XT_GEOM_SPHERICAL;
-  if (sph && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->npi > 0))
-    return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode with Monte Carlo packets, "
-                              "without subdomain rounds or photoionization data, with the estimator store on "
-                              "the device");
+  if (sph && (p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->npi > 0))
+    return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode, without subdomain "
+                              "rounds or photoionization data, with the estimator store on the device");
   RayTables rtab_rays{};
   const double* ray_Lc = nullptr;
   int64_t n_total = p->n_packets;
@@ -2591,7 +2642,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (sph) k_trace_sph<false><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph && rays) k_trace_sph<false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph) k_trace_sph<false><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && staged) {
         const int64_t gpb = std::max<int64_t>(1, kStageRays / ea.ray.nview);

@@ -153,8 +153,7 @@ def test_rejected_passes(xt):
     w = synth.spherical_sphere(n_packets=1000, seed=1)
     with _ctx(xt) as ctx:
         ctx.load(w)
-        for kw in [dict(mode=xt.XT_MODE_SCATTER), dict(sampler=xt.XT_SAMPLER_RAYS),
-                   dict(subdomain_rounds=True)]:
+        for kw in [dict(mode=xt.XT_MODE_SCATTER), dict(subdomain_rounds=True)]:
             rc, _ = ctx.transport(w, check=False, **kw)
             assert rc == xt.XT_EINVAL, kw
         xt.set_estimator_store(ctx.h, 1)
@@ -221,3 +220,41 @@ def test_coupled_loop_vs_oracle(xt, precision):
     m = (ref >= 1e-30 * nz) & (nz > 0)
     worst = float(np.max(np.abs(got[m] / ref[m] - 1)))
     assert worst < 1e-6
+
+
+@pytest.mark.parametrize("emission", ["band", "lines"])
+def test_rays_on_the_spherical_grid(xt, emission):
+    """The RAYS sampler on the spherical grid (Sec. 2.3, the paper's pass): rays
+    from the middle of every emitting cell's r, theta and phi ranges, one per
+    emitting bin and viewer; histories, estimators and spectrum against the
+    oracle.  The 7 x 7 viewers share no direction with the cells' middles (a
+    viewer centre at a cell's middle azimuth sends that cell's ray through the
+    polar axis, where the next sector is a rounding matter on both sides; the
+    paper's 20 x 20 viewers on its 38 x 15 x 30 grid share none either)."""
+    w = synth.spherical_sphere(n_packets=1, seed=9, nr=6, nth=4, nph=6, subdomains=(1, 1, 3))
+    kw = dict(sampler=xt.XT_SAMPLER_RAYS, n_theta=7, n_phi=7, spec_dlog=0.01)
+    em = xt.XT_EMIT_BAND if emission == "band" else xt.XT_EMIT_LINES
+    if emission == "lines":
+        w.spec_band_A = synth._spectrum_grid(2800.0, 10500.0, w.v_max, dlog=0.01)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st0 = ctx.transport(w, packet_count=0, emission=em, **kw)
+        nr = int(st0["rays"])
+        rec = np.zeros((nr, xt.XT_PKT_FIELDS))
+        st = ctx.transport(w, packet_records=rec, emission=em, **kw)
+        S = ctx.get_estimators()
+        spec = ctx.get_spectrum(0)
+    o = oracle.transport(w, sampler="rays", emission=emission, n_theta=7, n_phi=7, spec_dlog=0.01,
+                         per_packet=True)
+    assert o["n"] == nr and st["events"] > 1000
+    pk = o["pkt"]
+    assert np.array_equal(rec[:, 0], pk[:, 0]) and np.array_equal(rec[:, 1], pk[:, 1])
+    assert np.array_equal(rec[:, 7], pk[:, 7])
+    live = pk[:, 0] != 4
+    np.testing.assert_allclose(rec[live, 8], pk[live, 8], rtol=1e-12)
+    np.testing.assert_allclose(rec[live, 10], pk[live, 10], rtol=1e-13)
+    _cmp_sparse(S, o["S"], S_TOL, "estimators")
+    _cmp_sparse(spec, o["spec"], SPEC_TOL, "spectrum")
+    L = o["ledger"]
+    assert st["events"] == L["events"] and st["tests"] == L["tests"]
+    assert st["emitted_E"] == pytest.approx(L["emit_E"], rel=1e-9)
