@@ -208,8 +208,8 @@ def transport(w, p_begin=0, p_end=None, n_packets=None, seed=None, mode="atten",
     keep = _Keep(w, upsilon_down_sums(w) if mode == "scatter" else None)
     if keep.n_pi and mode != "atten":
         raise ValueError("photoionization is part of the attenuation mode only")
-    if keep.sph and (mode != "atten" or keep.n_pi):
-        raise ValueError("the spherical grid: attenuation mode, no photoionization")
+    if keep.sph and mode != "atten":
+        raise ValueError("the spherical grid: attenuation mode")
     S_pi = np.zeros((w.ncell, keep.n_pi)) if keep.n_pi else None
     heat = np.zeros(w.ncell) if keep.n_pi else None
     lam0, nbins = w.spec_band_A
@@ -369,7 +369,8 @@ def pi_rates(w, S_pi):
     over the number of atoms in it); levels with n_i = 0 give 0."""
     import synth
     lev, _, _ = synth.pi_levels(w)
-    N_i = w.pops[:, lev] * cell_volume(w)
+    V = cell_volume(w)
+    N_i = w.pops[:, lev] * (V[:, None] if np.ndim(V) else V)
     with np.errstate(divide="ignore", invalid="ignore"):
         return np.where(N_i > 0, S_pi / N_i, 0.0)
 

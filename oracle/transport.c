@@ -779,8 +779,12 @@ static double sph_exit(const prep_t *P, const double p0[3], const double n[3], c
 
 /* The event loop on the spherical grid (attenuation mode): as in trace, with
  * the walk through (r, theta, phi) cells; the packet's position is p0 + s n. */
+static int pi_segment(const prep_t *P, int64_t cell, const double *pc, double nu_lab,
+                      const double n[3], const double r[3], double s0, double s1, double *N,
+                      double E0, double *S_pi, double *heat, double *ledger);
+
 static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger, double *pkt,
-                      xo_domain *dom) {
+                      double *S_pi, double *heat, xo_domain *dom) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     double ct = P->ct;
@@ -802,6 +806,7 @@ static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, do
         double r_end[3];
         for (int a = 0; a < 3; a++) r_end[a] = p0[a] + s_exit * n[a];
         double nu_end = nu_lab * (1.0 - dot3(n, r_end) / ct);
+        double s_pi = s;            /* start of the photoionization segment (path from p0) */
         while (cursor < pb->nline && P->nu[cursor] > nu_end) {
             int32_t l = P->order[cursor];
             ledger[L_TESTS] += 1.0;
@@ -811,6 +816,16 @@ static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, do
             double tau = xo_tau_sobolev(P->A[l], g_l, g_u, lam, n_l, n_u, pb->t);
             if (tau > pr->tau_min) {
                 double nu_l = P->nu[cursor];
+                if (pb->n_pi > 0) {
+                    /* the ray moves to the resonance point, photoionizing on the way
+                     * (Secs. 2.3.1, 2.3.2); the line sees what photoionization left */
+                    double s_l = ct * (1.0 - nu_l / nu_lab) - dot3(n, p0);
+                    if (pi_segment(P, cell, pc, nu_lab, n, p0, s_pi, s_l, &N, E0, S_pi, heat, ledger)) {
+                        fate = 1;
+                        goto done;
+                    }
+                    if (s_l > s_pi) s_pi = s_l;
+                }
                 events++;
                 ledger[L_EVENTS] += 1.0;
                 double f_corr = 1.0 - g_l * n_u / (g_u * n_l);
@@ -829,6 +844,11 @@ static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, do
                 if (events >= pr->max_events) { fate = 3; ledger[L_GUARD] += 1.0; goto done; }
             }
             cursor++;
+        }
+        if (pb->n_pi > 0 &&
+            pi_segment(P, cell, pc, nu_lab, n, p0, s_pi, s_exit, &N, E0, S_pi, heat, ledger)) {
+            fate = 1;
+            goto done;
         }
         s = s_exit;
         if (kind == 0) {
@@ -882,7 +902,7 @@ done:
 static void trace(const prep_t *P, xo_state *st, double *S, double *spec, double *ledger,
                   double *pkt, double *S_pi, double *heat, xo_domain *dom) {
     if (P->pb->geometry == 1) {
-        trace_sph(P, st, S, spec, ledger, pkt, dom);
+        trace_sph(P, st, S, spec, ledger, pkt, S_pi, heat, dom);
         return;
     }
     const xo_problem *pb = P->pb;

@@ -230,3 +230,57 @@ def test_single_line_rays_start_at_the_cell_middle():
     m = spec > 0
     assert np.array_equal(m, o["spec"] > 0)
     np.testing.assert_allclose(o["spec"][m], spec[m], rtol=1e-12)
+
+
+H = 6.62607015e-27
+
+
+def test_thin_sphere_photoionization_rates_on_the_spherical_grid():
+    """Photoionization on every segment of the spherical walk (Sec. 2.3.1),
+    optically thin: the rate of each photoionizing level per radial shell is the
+    closed form of a uniformly emitting sphere, Gamma(r) = 4 pi J(r) sig c^3 /
+    (3 h) (nu_th^-3 - nu_hi^-3) for the hydrogenic sigma = sig lambda^3 of
+    Eq. sigma_OTSPI and a flat J_nu (the grid is the sphere itself)."""
+    w = synth.spherical_sphere(n_packets=600_000, nr=16, nth=6, nph=8, n_lines=5, n_levels=20, seed=61,
+                               subdomains=(1, 1, 4))
+    w.v_max = 5e7
+    w.r_edges = w.r_edges * 0.1
+    w.f_lu = np.full(w.nline, 1e-30)                      # no line interacts
+    synth.with_photoionization(w, chi_eV=6.0, charge=1, pi_nlev=8)
+    w.pops = np.ones((w.ncell, 1)) * np.linspace(1.0, 2.0, w.nlev)[None, :]
+    V = oracle.cell_volume(w)
+    w.L_cell = 1e40 * V / V.sum()
+    o = oracle.transport(w)
+    G = oracle.pi_rates(w, o["S_pi"])
+    lev, eion, ch = synth.pi_levels(w)
+    R = w.v_max * w.t
+    rc = 0.5 * (w.r_edges[:-1] + w.r_edges[1:]) * w.t
+    r = rc[np.tile(np.arange(w.nx), w.ny * w.nz)]
+    nu_lo, nu_hi = C / (w.band_A[1] * 1e-8), C / (w.band_A[0] * 1e-8)
+    j = 1e40 / V.sum() / (4 * np.pi * (nu_hi - nu_lo))
+    J = j * R / 2 * (1 + (R * R - r * r) / (2 * r * R) * np.log((R + r) / (R - r)))
+    tested = 0
+    for k in range(lev.shape[0]):
+        nu_th = (eion[k] - w.E_level[lev[k]]) / H
+        if nu_th >= nu_hi * (1 - 2 * w.v_max / C):
+            assert np.all(G[:, k] == 0), k
+            continue
+        sig = oracle.sigma_pi(1.0, w.E_level[lev[k]], eion[k], int(ch[k]))
+        want = 4 * np.pi * J * sig * C ** 3 / (3 * H) * (max(nu_th, nu_lo) ** -3 - nu_hi ** -3)
+        for a, b in [(0, 0.4), (0.4, 0.6), (0.6, 0.8)]:
+            m = (r / R >= a) & (r / R < b)
+            ratio = G[m, k].sum() / want[m].sum()
+            assert ratio == pytest.approx(1.0, abs=0.03), (k, a, b, ratio)
+        tested += 1
+    assert tested >= 3
+
+
+def test_ledger_closes_with_photoionization_on_the_spherical_grid():
+    w = synth.spherical_sphere(n_packets=30_000, seed=71, clumps=True)
+    synth.with_photoionization(w, chi_eV=6.0, charge=0, pi_nlev=9)
+    w.pops = w.pops * 1e-3
+    o = oracle.transport(w)
+    L = o["ledger"]
+    assert L["pi_N"] > 0.05 * L["emit_N"] and L["abs_N"] > 0.05 * L["emit_N"] and L["events"] > 10_000
+    assert L["esc_N"] + L["abs_N"] + L["pi_N"] + L["drop_N"] == pytest.approx(L["emit_N"], rel=1e-13)
+    assert o["S_pi"].sum() == pytest.approx(L["pi_N"], rel=1e-12)
