@@ -206,10 +206,10 @@ typedef struct {
 
 /* On a spherical grid (XT_GEOM_SPHERICAL) run_transport takes attenuation
  * mode with Monte Carlo packets or rays (XT_SAMPLER_RAYS: each ray starts at
- * the middle of its cell's r, theta and phi ranges), without subdomain rounds
- * and without photoionization data, with the estimator store on the device
- * (dense or compact rows; run_transport_domain with phi-slice domains); other
- * passes return XT_EINVAL.
+ * the middle of its cell's r, theta and phi ranges), with photoionization
+ * on every segment, without subdomain rounds, with the estimator store on the
+ * device (dense or compact rows; run_transport_domain with phi-slice
+ * domains); other passes return XT_EINVAL.
  * Packets start uniformly in their cell's volume (r^3, cos theta and phi
  * uniform) and walk from cell to cell through the shells' spheres, the polar
  * edges' cones (the plane z = 0 for theta = pi/2) and the azimuthal edges'

@@ -823,7 +823,7 @@ __global__ void k_pi_rates(Geometry g, int npi, const double* __restrict__ pops,
       const double n = pr[lev[s]];
       const double Nabs = sig[s] * n * (run + Dr[s]);
       absorbed += Nabs * chi[s];
-      if (Gamma) Gamma[cl * npi + s] = n > 0.0 ? Nabs / (n * V) : 0.0;
+      if (Gamma) Gamma[cl * npi + s] = n > 0.0 ? Nabs / (n * (g.vol ? g.vol[row] : V)) : 0.0;
     }
     if (heat) heat[cl] = kH * H[row] - absorbed;
   }

@@ -1306,13 +1306,24 @@ __device__ __noinline__ double sph_next(const double* __restrict__ tab, int tnx,
 // frequency, photons, energy cut, path s, cursor, events, cell) goes to the
 // pool and its slot to the out list.
 // RAYS: the rays of the RAYS sampler instead of Monte Carlo packets.
-template <bool DOM, bool RAYS = false>
+// PI: photoionization on every segment (Sec. 2.3.1, pi_segment as in k_trace:
+// up to each line's resonance point before the line acts, then up to the
+// exit face), the path coordinate being the walk's own.
+template <bool DOM, bool RAYS = false, bool PI = false>
 __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   __shared__ FixExpTables fx;
   __shared__ FixTrigTables trig;
   __shared__ unsigned long long blk_log;
+  constexpr int kPiS = PI ? XT_PI_MAX : 1;          // photoionization tables (PI instance)
+  __shared__ double s_nuth[kPiS], s_sig[kPiS];
+  __shared__ int s_lev[kPiS];
   stage(fx, a.fx);
   stage(trig, a.trig);
+  if constexpr (PI) {
+    for (int k = threadIdx.x; k < a.npi; k += blockDim.x) {
+      s_nuth[k] = a.pi_nuth[k]; s_sig[k] = a.pi_sig[k]; s_lev[k] = a.pi_lev[k];
+    }
+  }
   if (threadIdx.x == 0) blk_log = (unsigned long long)a.seg_n[blockIdx.x];
   __syncthreads();
   int64_t* const my_log = a.slotlog + (int64_t)blockIdx.x * a.seg_len;
@@ -1330,9 +1341,10 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   // a straight path meets each sphere and cone at most twice, each half-plane once
   const int max_faces = 2 * (g.nx + g.ny) + g.nz + 8;
-  double acc[T_NACC];
+  constexpr int kAcc = PI ? T_PIE + 1 : T_NACC;
+  double acc[kAcc];
 #pragma unroll
-  for (int k = 0; k < T_NACC; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kAcc; ++k) acc[k] = 0.0;
   unsigned n_tests = 0, n_events = 0, n_guard = 0;
 
   bool have = false, drained = false;
@@ -1340,6 +1352,10 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   int k_r = -1, k_t = -1, k_p = -1;
   double p0x = 0, p0y = 0, p0z = 0, nxv = 0, nyv = 0, nzv = 0, b = 0, pp = 0, s = 0;
   double s_r = 0, s_t = 0, s_p = 0, nu_cmf = 0, aslope = 0, N = 0, N_in = 0, Tq = 0;
+  // photoionization: segment start, 1 / aslope, the packet's photoionized
+  // photons, first level still active
+  double s_pi = 0, inv_as = 0, N_pi = 0;
+  int pcur = 0;
   for (;;) {
     __syncwarp();
     {
@@ -1370,6 +1386,14 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
           cursor = P.cursor[i];
           events = P.events[i];
           faces = 0;
+          if constexpr (PI) {
+            s_pi = P.F(F_SPI, i);
+            N_pi = 0.0;
+            inv_as = div_pos(a.ct, P.F(F_NULAB, i));
+            const double nu_s = fma(-aslope, s_pi, nu_cmf);
+            pcur = 0;
+            while (pcur < a.npi && s_nuth[pcur] >= nu_s) ++pcur;
+          }
           b = nxv * p0x + nyv * p0y + nzv * p0z;
           pp = p0x * p0x + p0y * p0y + p0z * p0z;
           row = RX[ix] + RY[iy] + RZ[iz];
@@ -1465,6 +1489,13 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
               Tq = em.e_cut * em.Eph[c];
             }
             N_in = N;
+            if constexpr (PI) {
+              s_pi = 0.0;
+              N_pi = 0.0;
+              inv_as = div_pos(a.ct, nu_lab);
+              pcur = 0;
+              while (pcur < a.npi && s_nuth[pcur] >= nu_cmf) ++pcur;
+            }
             P.F(F_NX, i) = nxv; P.F(F_NY, i) = nyv; P.F(F_NZ, i) = nzv;
             P.F(F_NULAB, i) = nu_lab;
             P.pid[i] = p;
@@ -1514,6 +1545,16 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
         const double n_l = prow[__double2loint(L.w)], n_u = prow[__double2hiint(L.w)];
         const double tau = L.y * (n_l - L.z * n_u);
         if (bits(tau) > taumin_bits) {
+          if constexpr (PI) {    // to the resonance point, photoionizing on the way
+            const double s_l = (nu_cmf - L.x) * inv_as;
+            if (pi_segment(a, fx, s_nuth, s_sig, s_lev, row, prow, s_pi, s_l, nu_cmf, aslope, inv_as, pcur, N,
+                           N_pi, acc[T_PIE], Tq)) {
+              acc[T_DROP] += N;
+              fate = 1;
+              break;
+            }
+            if (bits(s_l) > bits(s_pi)) s_pi = s_l;
+          }
           ++events;
           ++n_events;
           double ex, ome;
@@ -1528,6 +1569,17 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
         }
         ++cursor;
         if (fate >= 0) break;
+      }
+      if constexpr (PI) {      // photoionization up to the exit face
+        if (fate < 0) {
+          if (pi_segment(a, fx, s_nuth, s_sig, s_lev, row, prow, s_pi, s_exit, nu_cmf, aslope, inv_as, pcur,
+                         N, N_pi, acc[T_PIE], Tq)) {
+            acc[T_DROP] += N;
+            fate = 1;
+          } else if (bits(s_exit) > bits(s_pi)) {
+            s_pi = s_exit;
+          }
+        }
       }
       if (fate < 0) {
         s = s_exit;
@@ -1550,6 +1602,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
           P.F(F_NU0, i) = nu_cmf;
           P.F(F_T, i) = Tq;
           P.F(F_TMX, i) = s;
+          if constexpr (PI) P.F(F_SPI, i) = s_pi;
           P.cursor[i] = cursor;
           P.cell[i] = ix | (iy << 10) | (iz << 20);
         }
@@ -1575,7 +1628,12 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
     if (escaped || queued || fate >= 0) {
       P.F(F_N, i) = N;
       P.events[i] = events;
-      acc[T_ABS] += N_in - N;
+      if constexpr (PI) {
+        acc[T_ABS] += (N_in - N) - N_pi;               // photons the lines absorbed
+        acc[T_PIN] += N_pi;
+      } else {
+        acc[T_ABS] += N_in - N;
+      }
       if (fate >= 0 && a.records) {
         double* rec = a.records + (P.pid[i] - a.rec_base) * XT_PKT_FIELDS;
         rec[0] = fate; rec[1] = events; rec[2] = N; rec[3] = 0.0; rec[4] = -1.0; rec[5] = -1.0;
@@ -1596,8 +1654,11 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
   double cnt[3] = {(double)n_tests, (double)n_events, (double)n_guard};
   const int cslots[3] = {LG_TESTS, LG_EVENTS, LG_GUARD};
   warp_flush(cnt, a.ledger, cslots);
-  const int slots[T_NACC] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
-                             LG_EMIT_N, LG_EMIT_E};
+  const int all_slots[T_PIE + 1] = {LG_ABS_N, LG_DROP_N, LG_ABS_E_CMF, LG_REEMIT_E_CMF, LG_THERMAL_E,
+                                    LG_EMIT_N, LG_EMIT_E, LG_PI_N, LG_PI_E};
+  int slots[kAcc];
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) slots[k] = all_slots[k];
   warp_flush(acc, a.ledger, slots);
 }
 
@@ -2027,9 +2088,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return fail(c, XT_EINVAL, "run_transport: spectrum grid (n_theta, n_phi, spec_nbins, spec_lam0_A, spec_dlog)");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
   const bool sph = c->geometry == XT_GEOM_SPHERICAL;
-  if (sph && (p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || c->npi > 0))
+  if (sph && (p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0))
     return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode, without subdomain "
-                              "rounds or photoionization data, with the estimator store on the device");
+                              "rounds, with the estimator store on the device");
   RayTables rtab_rays{};
   const double* ray_Lc = nullptr;
   int64_t n_total = p->n_packets;
@@ -2284,7 +2345,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   c->have_pi = pi;
 
   int occ = 0;
-  if (sph)
+  if (sph && pi)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_sph<false, false, true>, 256, 0);
+  else if (sph)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_sph<false>, 256, 0);
   else if (rays && pi)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<XT_MODE_ATTEN, true, true>, 256, 0);
@@ -2487,7 +2550,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = qA;
       const int grid = (int)std::min<int64_t>(grid_max, (count + 255) / 256);
       sl = tick(1);
-      if (sph) k_trace_sph<true><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph && pi) k_trace_sph<true, false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph) k_trace_sph<true><<<grid, 256, 0, c->stream>>>(ta);
       else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else k_trace<XT_MODE_ATTEN><<<grid, 256, 0, c->stream>>>(ta);
@@ -2642,7 +2706,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = (list == qA) ? qB : qA;
       const int grid = (int)std::min<int64_t>(grid_max, (n_list + 255) / 256);
       sl = tick(1);
-      if (sph && rays) k_trace_sph<false, true><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph && rays && pi) k_trace_sph<false, true, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph && rays) k_trace_sph<false, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph && pi) k_trace_sph<false, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (sph) k_trace_sph<false><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && pi) k_trace<XT_MODE_ATTEN, true, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (rays && staged) {

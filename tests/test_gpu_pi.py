@@ -139,3 +139,37 @@ def test_scatter_mode_with_photoionization_is_refused(xt):
         with pytest.raises(xt.XtError) as e:
             ctx.transport(w, mode=xt.XT_MODE_SCATTER)
         assert e.value.code == xt.XT_EINVAL and "attenuation" in str(e.value)
+
+
+def test_spherical_grid_with_photoionization(xt):
+    """Photoionization on every segment of the spherical walk (the paper's
+    grid): histories, rates, heating, estimators, spectrum and ledger against
+    the oracle."""
+    w = synth.spherical_sphere(n_packets=60_000, seed=71, clumps=True)
+    synth.with_photoionization(w, chi_eV=6.0, charge=0, pi_nlev=9)
+    w.pops = w.pops * 1e-3
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st, o = _check_pass(xt, ctx, w)
+        assert o["ledger"]["pi_N"] > 0.05 * o["ledger"]["emit_N"]
+
+
+def test_spherical_rays_with_photoionization(xt):
+    """The RAYS sampler with photoionization on the spherical grid (7 x 7
+    viewers: no viewer centre at a cell's middle direction)."""
+    w = synth.spherical_sphere(n_packets=1, seed=72, nr=6, nth=4, nph=6, subdomains=(1, 1, 3))
+    synth.with_photoionization(w, chi_eV=6.0, charge=0, pi_nlev=9)
+    w.pops = w.pops * 1e-3
+    kw = dict(n_theta=7, n_phi=7, spec_dlog=0.01)
+    with _ctx(xt) as ctx:
+        ctx.load(w)
+        st = ctx.transport(w, sampler=xt.XT_SAMPLER_RAYS, **kw)
+        G, heat = ctx.get_photoionization_rates()
+        S = ctx.get_estimators()
+    o = oracle.transport(w, sampler="rays", **kw)
+    _cmp(S, o["S"], TOL, "line estimators")
+    _cmp_rates(G, oracle.pi_rates(w, o["S_pi"]), "photoionization rates")
+    np.testing.assert_allclose(heat, o["heat"], rtol=TOL, atol=1e-12 * np.abs(o["heat"]).max())
+    L = o["ledger"]
+    assert st["events"] == L["events"] and L["pi_N"] > 0.05 * L["emit_N"]
+    assert abs(st["photoionized_N"] - L["pi_N"]) <= 1e-9 * st["emitted_N"]

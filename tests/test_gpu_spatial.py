@@ -81,8 +81,8 @@ def test_domains_sum_to_the_whole_grid(xt, world, pi):
         _cmp(G, G_ref, 1e-10, "photoionization rates")
 
 
-@pytest.mark.parametrize("world", [3, 4])
-def test_phi_slab_domains_on_the_spherical_grid(xt, world):
+@pytest.mark.parametrize("world,pi", [(3, False), (4, True)])
+def test_phi_slab_domains_on_the_spherical_grid(xt, world, pi):
     """The paper's decomposition of its spherical grid (Sec. 2.4.1): domains of
     whole phi slices (the azimuthal index is the grid's third), packets handed
     on with their path from the emission point; phi wraps around.  The sums
@@ -90,6 +90,8 @@ def test_phi_slab_domains_on_the_spherical_grid(xt, world):
     import torch
     from paper_2511_07539_gb300 import spatial
     w = synth.spherical_sphere(n_packets=200_000, seed=5, clumps=True)      # 12 phi slices
+    if pi:
+        synth.with_photoionization(w)
     w.pops = w.pops * 1e-3
     stream = torch.cuda.current_stream().cuda_stream
     kw = dict(n_packets=w.n_packets, seed=w.seed, spec_lam0_A=w.spec_band_A[0],
@@ -98,6 +100,7 @@ def test_phi_slab_domains_on_the_spherical_grid(xt, world):
     ref.load(w)
     st = ref.transport(w)
     S_ref, spec_ref = ref.get_estimators(), ref.get_spectrum(0)
+    G_ref = ref.get_photoionization_rates()[0] if pi else None
     ref.close()
     ctxs, trs = [], []
     for r in range(world):
@@ -109,18 +112,23 @@ def test_phi_slab_domains_on_the_spherical_grid(xt, world):
     assert 1 <= rounds <= world - 1
     S = np.zeros_like(S_ref)
     spec = np.zeros_like(spec_ref)
+    G = np.zeros_like(G_ref) if pi else None
     ev = tests = 0.0
     nxy = w.nx * w.ny
     for r, (c, t) in enumerate(zip(ctxs, trs)):
         z0, z1 = spatial.slab(r, w.nz, world)
         S[z0 * nxy:z1 * nxy] = c.get_estimators(z0 * nxy, (z1 - z0) * nxy)
         spec += c.get_spectrum(0)
+        if pi:
+            G[z0 * nxy:z1 * nxy] = c.get_photoionization_rates(z0 * nxy, (z1 - z0) * nxy)[0]
         ev += t.stats[-1]["events"]
         tests += t.stats[-1]["tests"]
         c.close()
     assert ev == st["events"] and tests == st["tests"]
     _cmp(S, S_ref, 1e-10, "estimators")
     _cmp(spec, spec_ref, 1e-9, "spectrum")
+    if pi:
+        _cmp(G, G_ref, 1e-10, "photoionization rates")
 
 
 def test_malformed_bundle_is_refused(xt):

@@ -168,11 +168,6 @@ def test_rejected_passes(xt):
             with pytest.raises((xt.XtError, ValueError)):
                 xt.init_grid(ctx.h, w.nx, w.ny, w.nz, w.v_max, w.t, w.Te, w.ne, w.L_cell, w.band_A,
                              spherical_edges=e)
-    wp = synth.with_photoionization(synth.spherical_sphere(n_packets=1000, seed=1))
-    with _ctx(xt) as ctx:
-        ctx.load(wp)
-        rc, _ = ctx.transport(wp, check=False)
-        assert rc == xt.XT_EINVAL
 
 
 def test_paper_grid_sampled(xt):
