@@ -253,6 +253,34 @@ def sph_bench(local, stream_ptr, passes=3, n_packets=20_000_000):
             "trace_GB_per_s": ach, "frac_hbm": ach / peaks["hbm_gbs"], "kernel": "k_trace_sph"}
 
 
+def paper_rays_bench(local, stream_ptr, steps=1):
+    """The paper's radiative-transfer pass at its own scale (Sec. 2.3, the ray
+    count of its validation pass): the RAYS sampler on the 38 x 15 x 30
+    spherical grid of paper_sphere(), band emission over 400-15000 A on the 0.1 %
+    output grid from 400 A (3626 emitting bins) and 20 x 20 viewers: 17,100 x
+    3626 x 400 = 2.48e10 rays per pass.  One warm-up pass, then `steps` timed."""
+    import torch
+    import paper_2511_07539_gb300 as xt
+    w = paper_sphere(1)
+    w.band_A = (400.0, 15000.0)
+    nb = int(np.ceil(np.log(15000.0 * (1.0 + 1.5 * w.v_max / 2.99792458e10) / 400.0) / np.log1p(1e-3)))
+    kw = dict(sampler=xt.XT_SAMPLER_RAYS, n_theta=20, n_phi=20, spec_lam0_A=400.0, spec_dlog=1e-3,
+              spec_nbins=nb, seed=w.seed)
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    xt.run_transport(ctx.h, 1, **kw)
+    sts = [xt.run_transport(ctx.h, 1, **kw) for _ in range(steps)]
+    torch.cuda.synchronize()
+    ctx.close()
+    st = min(sts, key=lambda x: x["transport_ms"])
+    return {"workload": w.name.replace("_1pk", "_rays") + "_band_400-15000A_0.1pc_bins_20x20_viewers",
+            "rays": st["rays"], "events": st["events"], "tests": st["tests"],
+            "pass_device_ms": st["transport_ms"], "trace_ms": st["trace_ms"],
+            "rays_per_s": st["rays"] / (st["transport_ms"] * 1e-3),
+            "events_per_s": st["events"] / (st["transport_ms"] * 1e-3),
+            "trace_launches": st["rounds"], "escaped_E_over_emitted": st["escaped_E"] / st["emitted_E"]}
+
+
 def cfg5_bench(local, stream_ptr, packets=1_000_000_000):
     """The full-loop scale (128^3 cells, 10 ions, 2e4 lines, 1e9 packets, 4^3
     subdomains) on one GPU: the dense FP64 store (336 GB) does not fit the
@@ -707,6 +735,8 @@ def main():
     ap.add_argument("--only-nlte", action="store_true", help="print the rate-solve object alone")
     ap.add_argument("--only-cfg5", action="store_true",
                     help="print the 128^3 full-loop-scale object alone (a pass and a solve)")
+    ap.add_argument("--only-paper-rays", action="store_true",
+                    help="print the paper's full RAYS pass on its spherical grid alone (2.48e10 rays)")
     ap.add_argument("--only-cfg5-loop", action="store_true",
                     help="print the 128^3 coupled-loop object alone (plain vs surrogate + mixed)")
     ap.add_argument("--nlte-n", type=int, default=64)
@@ -763,6 +793,11 @@ def main():
     if args.only_cfg5:
         if rank == 0:
             print(json.dumps({"cfg5": cfg5_bench(local, torch.cuda.current_stream().cuda_stream)}),
+                  flush=True)
+        return
+    if args.only_paper_rays:
+        if rank == 0:
+            print(json.dumps({"paper_rays": paper_rays_bench(local, torch.cuda.current_stream().cuda_stream)}),
                   flush=True)
         return
     if args.only_cfg5_loop:
