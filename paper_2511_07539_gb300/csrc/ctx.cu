@@ -399,13 +399,14 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
     // 0, cos and sin phi with edge nz taken as edge 0, phi) and the volumes
     // (r1^3 - r0^3) / 3 (cos theta0 - cos theta1) (phi1 - phi0), natural order
     const int nx = g->nx, ny = g->ny, nz = g->nz;
-    tab.assign((size_t)(nx + 1) + 2 * (size_t)(ny + 1) + 3 * (size_t)(nz + 1), 0.0);
+    tab.assign((size_t)(nx + 1) + 2 * (size_t)(ny + 1) + 3 * (size_t)(nz + 1) + 3 * (size_t)G.ncell, 0.0);
     double* sR = tab.data();
     double* cth = sR + nx + 1;
     double* cph = cth + ny + 1;
     double* sphi = cph + nz + 1;
     double* phe = sphi + nz + 1;
     double* the = phe + nz + 1;
+    double* mid = the + ny + 1;
     for (int j = 0; j <= ny; ++j) the[j] = te[j];
     std::vector<double> ct_raw(ny + 1);
     for (int i = 0; i <= nx; ++i) sR[i] = re[i] * g->t;
@@ -424,6 +425,12 @@ int init_grid(xt_ctx* c, const xt_grid_desc* g) {
       const int ir = (int)(cc % nx), it = (int)((cc / nx) % ny), ip = (int)(cc / ((int64_t)nx * ny));
       vol_nat[cc] = (sR[ir + 1] * sR[ir + 1] * sR[ir + 1] - sR[ir] * sR[ir] * sR[ir]) / 3.0 *
                     (ct_raw[it] - ct_raw[it + 1]) * (pe[ip + 1] - pe[ip]);
+      // the middle of the cell's r, theta and phi ranges (where its rays start)
+      const double rm = 0.5 * (sR[ir] + sR[ir + 1]);
+      const double tm = 0.5 * (te[it] + te[it + 1]), pm = 0.5 * (pe[ip] + pe[ip + 1]);
+      mid[3 * cc] = rm * std::sin(tm) * std::cos(pm);
+      mid[3 * cc + 1] = rm * std::sin(tm) * std::sin(pm);
+      mid[3 * cc + 2] = rm * std::cos(tm);
     }
     if ((rc = alloc(c, (void**)&c->d_sph, tab.size() * sizeof(double), "spherical tables"))) return rc;
     if ((rc = copy(c, c->d_sph, tab.data(), tab.size() * sizeof(double), "spherical tables"))) return rc;

@@ -1437,13 +1437,8 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
               live = false;                    // (the lane stays empty; no early continue: every
             }                                  //  lane reaches the warp-wide ballot below)
             nxv = v01.x; nyv = v01.y; nzv = v23.x;
-            const double rm = 0.5 * (sR[idx[0]] + sR[idx[0] + 1]);
-            const double tm = 0.5 * (the[idx[1]] + the[idx[1] + 1]);
-            const double pm = 0.5 * (phe[idx[2]] + phe[idx[2] + 1]);
-            double st, ct, sp, cp;
-            sincos(tm, &st, &ct);
-            sincos(pm, &sp, &cp);
-            p0x = rm * st * cp; p0y = rm * st * sp; p0z = rm * ct;
+            const double* const mid = the + g.ny + 1 + 3 * c;   // the cell's middle, tabulated
+            p0x = mid[0]; p0y = mid[1]; p0z = mid[2];
             nu_cmf = T.bin_nu[jb];
             cursor = T.bin_cursor[jb];
           } else {

@@ -37,7 +37,9 @@ struct Geometry {
   // spherical grid (both nullptr for the cube): cell volumes [row], and the
   // walk's tables [shell radii (nx+1) | cos theta (ny+1), exactly 0 for an
   // equatorial edge | cos phi (nz+1) | sin phi (nz+1) | phi (nz+1) | theta
-  // (ny+1)], edge nz of the azimuthal tables being edge 0 again for cos and sin
+  // (ny+1) | the middle of every cell's r, theta and phi ranges as x, y, z
+  // (3 ncell, natural order)], edge nz of the azimuthal tables being edge 0
+  // again for cos and sin
   const double* vol = nullptr;
   const double* sph = nullptr;
 };
