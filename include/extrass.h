@@ -286,6 +286,10 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
  *   XT_PREC_TF32_IR  as XT_PREC_FP32_IR with the rank-nb trailing updates of
  *                    the blocked LU on the tensor cores (TF32 operands, FP32
  *                    accumulation); more refinement steps, same FP64 result.
+ *   XT_PREC_BF16_IR  as XT_PREC_TF32_IR with BF16 operands (8-bit
+ *                    significands): the factors are coarser, so refinement
+ *                    takes more steps, and a system whose refinement does not
+ *                    reach tol within max_iter steps is solved in FP64.
  * Rates: XT_RATES_ESTIMATORS uses the last transport pass (R_lu = S/(n_l V));
  * XT_RATES_JBAR illuminates every line with the external field
  * J_nu = jbar_W B_nu(jbar_TR), of which a Sobolev region absorbs the part
@@ -297,6 +301,7 @@ int get_spectrum(xt_ctx *ctx, int32_t kind, double *out, size_t n_cap);
 #define XT_PREC_FP64 0
 #define XT_PREC_FP32_IR 1
 #define XT_PREC_TF32_IR 2   /* as FP32_IR, the trailing updates of the LU on the tensor cores (TF32) */
+#define XT_PREC_BF16_IR 3   /* the same with BF16 operands */
 #define XT_RATES_NONE 0
 #define XT_RATES_ESTIMATORS 1
 #define XT_RATES_JBAR 2
@@ -456,6 +461,11 @@ int xt_selftest_fixed(int32_t kind, const double *x, int64_t n, double *y0, doub
  * own.  XT_EINVAL for a bad N or a NULL array; XT_ETIMEOUT if the MMA's
  * completion was not seen within its bounded wait. */
 int xt_selftest_tc(int device, int N, const float *A, const float *B, float *D);
+
+/* The same check for the BF16 leg (kind::f16 with BF16 operands): A and B
+ * rounded to BF16 (nearest, ties to even), products summed in FP32.  Same
+ * arguments, layout and errors as xt_selftest_tc. */
+int xt_selftest_tc_bf16(int device, int N, const float *A, const float *B, float *D);
 
 /* ---- transport without device allocation (no paper counterpart) -----------
  * For callers that cannot call cudaMalloc: programs whose device memory is

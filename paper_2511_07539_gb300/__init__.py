@@ -95,7 +95,7 @@ class NoallocTransport(C.Structure):
                 ("S", C.c_void_p), ("spec", C.c_void_p)]
 
 
-XT_PREC_FP64, XT_PREC_FP32_IR, XT_PREC_TF32_IR = 0, 1, 2
+XT_PREC_FP64, XT_PREC_FP32_IR, XT_PREC_TF32_IR, XT_PREC_BF16_IR = 0, 1, 2, 3
 XT_RATES_NONE, XT_RATES_ESTIMATORS, XT_RATES_JBAR = 0, 1, 2
 XT_WARM_CURRENT, XT_WARM_LTE, XT_WARM_GIVEN = 0, 1, 2
 XT_SE_OK, XT_SE_FALLBACK, XT_SE_SINGULAR, XT_SE_NOCONV = 1, 2, 4, 8
@@ -174,6 +174,7 @@ def lib():
             "get_sizes": ([vp, vp], C.c_int),
             "xt_selftest_fixed": ([i32, vp, i64, vp, vp, vp, vp], C.c_int),
             "xt_selftest_tc": ([C.c_int, C.c_int, vp, vp, vp], C.c_int),
+            "xt_selftest_tc_bf16": ([C.c_int, C.c_int, vp, vp, vp], C.c_int),
             "run_transport_noalloc": ([vp, vp, vp, C.c_char_p, C.c_size_t], C.c_int),
             "run_transport_domain": ([vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, vp], C.c_int),
             "solve_nlte": ([vp, vp, vp, vp, vp], C.c_int),
@@ -571,18 +572,25 @@ def xt_selftest_fixed(kind, x):
 
 
 
-def xt_selftest_tc(A, B, device=0):
-    """D = A B^T on the tensor cores (TF32 inputs, FP32 accumulation): A [128][32],
-    B [N][32] float32, N a multiple of 16 in [16, 256]; returns D [128][N]."""
+def xt_selftest_tc(A, B, device=0, bf16=False):
+    """D = A B^T on the tensor cores (TF32 inputs, or BF16 with bf16=True; FP32
+    accumulation): A [128][32], B [N][32] float32, N a multiple of 16 in
+    [16, 256]; returns D [128][N]."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     if A.shape != (128, 32) or B.ndim != 2 or B.shape[1] != 32:
         raise ValueError("xt_selftest_tc: A must be [128][32] and B [N][32]")
     D = np.zeros((128, B.shape[0]), dtype=np.float32)
-    rc = lib().xt_selftest_tc(int(device), int(B.shape[0]), _ptr(A), _ptr(B), _ptr(D))
+    fn = lib().xt_selftest_tc_bf16 if bf16 else lib().xt_selftest_tc
+    rc = fn(int(device), int(B.shape[0]), _ptr(A), _ptr(B), _ptr(D))
     if rc != XT_OK:
         raise XtError(rc, "xt_selftest_tc failed")
     return D
+
+
+def xt_selftest_tc_bf16(A, B, device=0):
+    """xt_selftest_tc with the operands rounded to BF16 (kind::f16)."""
+    return xt_selftest_tc(A, B, device, bf16=True)
 
 def run_transport_noalloc(nx, ny, nz, v_max, t, L_cell, band_A, g_level, lo, up, lambda_A, f_lu,
                           pops, S, spec, n_packets, seed=0, tau_min=1e-4, e_cut=1e-6, n_theta=20,

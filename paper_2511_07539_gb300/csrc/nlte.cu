@@ -86,8 +86,9 @@ struct SeArgs {
   int max_iter;
   int nb_bucket[8];                     // panel width per 64-level bucket
   double* __restrict__ iters;           // [cell * n_ion + z] refinement (or Newton) steps
-  int tmem_cols;                        // > 0: TF32 factors' trailing updates on the tensor cores
+  int tmem_cols;                        // > 0: FP32 factors' trailing updates on the tensor cores
   unsigned long long* __restrict__ tc_err;   //   (TMEM columns per CTA; CTAs that gave up)
+  int tc_bf16;                          //   with BF16 operands, else TF32
   int newton_max;                       // 0: linear solve with beta_S from pops
   double newton_tol, newton_maxvar;
   FixExpTables fx;                      // e^-tau tables (fixed point)
@@ -117,6 +118,7 @@ struct TcState {
   uint64_t bar;
   uint32_t taddr, phase;
   int ncols, ok;
+  int bf16;                    // operands in BF16 (kind::f16), else TF32
   unsigned long long* err;     // global count of CTAs that gave up on the tensor cores
 };
 constexpr long long kTcSpin = 1ll << 24;   // polls of an MMA completion before giving up
@@ -145,11 +147,40 @@ __device__ __noinline__ bool lu_trailing_tc(float* __restrict__ A, int L, int k0
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* const Bs = reinterpret_cast<unsigned char*>(u12);
   unsigned char* const As = reinterpret_cast<unsigned char*>(pan + kb * kbp);   // L21's first row
-  // operand B: U12 rounded to TF32, zero outside kb x n2
-  for (int e = tid; e < Npad * 32; e += blockDim.x) {
-    const int n = e >> 5, k = e & 31;
-    uint32_t* q = reinterpret_cast<uint32_t*>(Bs + tc::tile_off(n, k, Npad));
-    *q = (n < n2 && k < kb) ? tc::to_tf32(__uint_as_float(*q)) : 0u;
+  const bool bf = tc->bf16 != 0;
+  if (bf) {
+    // operand B: U12 rounded to BF16, zero outside kb x n2, in the 16-bit
+    // layout; each thread converts 16-byte groups of 8 K elements (two of the
+    // 32-bit chunks) through registers, since the new tile overwrites the old
+    constexpr int kGroups = (kSeMaxL * 4 + 255) / 256;   // Npad <= kSeMaxL rows of 4 groups
+    uint4 gv[kGroups];
+#pragma unroll
+    for (int q = 0; q < kGroups; ++q) {
+      const int gi = tid + 256 * q, n = gi >> 2, k8 = (gi & 3) << 3;
+      uint4 o = make_uint4(0u, 0u, 0u, 0u);
+      if (gi < Npad * 4 && n < n2) {
+        const float4 lo = *reinterpret_cast<const float4*>(Bs + tc::tile_off(n, k8, Npad));
+        const float4 hi = *reinterpret_cast<const float4*>(Bs + tc::tile_off(n, k8 + 4, Npad));
+        o.x = tc::pack_bf16(k8 < kb ? lo.x : 0.f, k8 + 1 < kb ? lo.y : 0.f);
+        o.y = tc::pack_bf16(k8 + 2 < kb ? lo.z : 0.f, k8 + 3 < kb ? lo.w : 0.f);
+        o.z = tc::pack_bf16(k8 + 4 < kb ? hi.x : 0.f, k8 + 5 < kb ? hi.y : 0.f);
+        o.w = tc::pack_bf16(k8 + 6 < kb ? hi.z : 0.f, k8 + 7 < kb ? hi.w : 0.f);
+      }
+      gv[q] = o;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGroups; ++q) {
+      const int gi = tid + 256 * q;
+      if (gi < Npad * 4) *reinterpret_cast<uint4*>(Bs + tc::tile_off16(gi >> 2, (gi & 3) << 3, Npad)) = gv[q];
+    }
+  } else {
+    // operand B: U12 rounded to TF32, zero outside kb x n2
+    for (int e = tid; e < Npad * 32; e += blockDim.x) {
+      const int n = e >> 5, k = e & 31;
+      uint32_t* q = reinterpret_cast<uint32_t*>(Bs + tc::tile_off(n, k, Npad));
+      *q = (n < n2 && k < kb) ? tc::to_tf32(__uint_as_float(*q)) : 0u;
+    }
   }
   const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs);
   const int nmax = tc->ncols < 256 ? tc->ncols : 256;
@@ -166,10 +197,18 @@ __device__ __noinline__ bool lu_trailing_tc(float* __restrict__ A, int L, int k0
       av[q] = (t0 + r < m2 && k < kb) ? pan[(kb + t0 + r) * kbp + k] : 0.f;
     }
     __syncthreads();
+    if (bf) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = tid + 256 * q, r = e >> 5, k = e & 31;
-      *reinterpret_cast<uint32_t*>(As + tc::tile_off(r, k, 128)) = tc::to_tf32(av[q]);
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + 256 * q, r = e >> 5, k = e & 31;
+        *reinterpret_cast<uint16_t*>(As + tc::tile_off16(r, k, 128)) = tc::to_bf16(av[q]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int e = tid + 256 * q, r = e >> 5, k = e & 31;
+        *reinterpret_cast<uint32_t*>(As + tc::tile_off(r, k, 128)) = tc::to_tf32(av[q]);
+      }
     }
     tc::fence_smem_async();
     tc::fence_before();
@@ -178,11 +217,13 @@ __device__ __noinline__ bool lu_trailing_tc(float* __restrict__ A, int L, int k0
     for (int n0 = 0; n0 < Npad; n0 += nmax) {
       const int Nc = min(nmax, Npad - n0);
       if (tid == 0) {
-        for (int k = 0; k < 4; ++k) {
+        // one MMA per 32 bytes of K (two 16-byte chunks): 4 in TF32, 2 in BF16
+        for (int k = 0; k < (bf ? 2 : 4); ++k) {
           const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(k * 4096), 2048, 128);
           const uint64_t bd = tc::smem_desc(b0 + (uint32_t)((2 * k * (Npad >> 3) + (n0 >> 3)) * 128),
                                             (uint32_t)(Npad >> 3) * 128, 128);
-          tc::mma_tf32(taddr, ad, bd, tc::idesc_tf32(128, Nc), k > 0);
+          if (bf) tc::mma_bf16(taddr, ad, bd, tc::idesc_bf16(128, Nc), k > 0);
+          else tc::mma_tf32(taddr, ad, bd, tc::idesc_tf32(128, Nc), k > 0);
         }
         tc::commit(&tc->bar);
       }
@@ -221,14 +262,16 @@ __device__ __noinline__ bool lu_trailing_tc(float* __restrict__ A, int L, int k0
 }
 
 // With tc (FP32 factors, 256 threads, panels of 32 columns), trailing updates
-// of at least kTcMinRows rows run on the tensor cores (tcgen05, kind::tf32):
-// U12 is solved straight into the canonical operand layout of tc.cuh in the
-// u12 buffer (40 KB: 320 rows x 32 K), rounded to TF32 and zero-padded; each
-// tile of 128 rows of L21 is read from the panel into registers and written in
-// that layout at the start of L21's own rows in the panel buffer (128 rows of
-// 33 floats hold its 16 KB, so no row still to be read is overwritten); the
-// MMAs accumulate L21 U12 in TMEM, and the CTA subtracts it from A22 through
-// tcgen05 loads (a warp per 32 rows and half the columns).
+// of at least kTcMinRows rows run on the tensor cores (tcgen05, kind::tf32,
+// or kind::f16 with BF16 operands): U12 is solved straight into the canonical
+// 32-bit operand layout of tc.cuh in the u12 buffer (40 KB: 320 rows x 32 K),
+// then rounded to TF32 in place, or to BF16 into the 16-bit layout at the
+// buffer's start, and zero-padded; each tile of 128 rows of L21 is read from
+// the panel into registers and written in the operand layout at the start of
+// L21's own rows in the panel buffer (128 rows of 33 floats hold its 16 KB, or
+// 8 KB in BF16, so no row still to be read is overwritten); the MMAs
+// accumulate L21 U12 in TMEM (FP32), and the CTA subtracts it from A22
+// through tcgen05 loads (a warp per 32 rows and half the columns).
 constexpr int kTcMinRows = 32;
 
 template <typename T>
@@ -525,6 +568,7 @@ __global__ void __launch_bounds__(THREADS) k_se(const SeArgs a) {
         ts->phase = 0;
         ts->ncols = a.tmem_cols;
         ts->ok = 1;
+        ts->bf16 = a.tc_bf16;
         ts->err = a.tc_err;
       }
       tc::fence_before();
@@ -986,7 +1030,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   if (!c->have_pops || !c->have_atoms) return fail(c, XT_ESTATE, "solve_nlte: load_atomic_data and set_populations first");
   if (!c->d_nion) return fail(c, XT_ESTATE, "solve_nlte: n_ion_density was not given to load_atomic_data");
   if (c->n_ion > 16) return fail(c, XT_EINVAL, "solve_nlte: at most 16 ions");
-  if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR && p->precision != XT_PREC_TF32_IR)
+  if (p->precision != XT_PREC_FP64 && p->precision != XT_PREC_FP32_IR && p->precision != XT_PREC_TF32_IR &&
+      p->precision != XT_PREC_BF16_IR)
     return fail(c, XT_EINVAL, "solve_nlte: precision");
   if (p->rates == XT_RATES_ESTIMATORS && !c->have_S)
     return fail(c, XT_ESTATE, "solve_nlte: estimator rates need a transport pass with the current populations");
@@ -1063,7 +1108,8 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   }
   const size_t ups_n = (size_t)ups_off[c->n_ion];
   const int pi = p->precision == XT_PREC_FP64 ? 0 : 1;           // kernel type: double / float
-  const int ti = p->precision == XT_PREC_TF32_IR ? 2 : pi;        // tuning slot
+  const bool tcore = p->precision == XT_PREC_TF32_IR || p->precision == XT_PREC_BF16_IR;
+  const int ti = tcore ? 2 : pi;                                   // tuning slot
   const size_t tsz = pi == 0 ? sizeof(double) : sizeof(float);
   // systems with more than kSmallL levels go to the large kernel, the rest
   // (the tail of the longest-first list) to the small one
@@ -1193,10 +1239,10 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
   a.W64 = B.W64; a.WT = B.WT; a.wlen = wlen; a.precision = p->precision; a.tol = p->tol;
   a.eta = p->eta_nt; a.max_iter = p->max_iter; a.iters = B.iters;
   a.newton_max = p->newton_max; a.newton_tol = p->newton_tol; a.newton_maxvar = p->newton_maxvar;
-  // TF32 factors: the large systems' trailing updates on the tensor cores, with
+  // TF32 or BF16 factors: the large systems' trailing updates on the tensor cores, with
   // TMEM columns such that the CTAs resident on an SM fit its 512 (a CTA's
   // allocation would otherwise wait for one that never frees it)
-  if (p->precision == XT_PREC_TF32_IR) {
+  if (tcore) {
     // residency bound by shared memory (1 KB per CTA reserved by the system),
     // whatever the launch assumed: TMEM columns x resident CTAs <= 512
     int smem_sm = 0;
@@ -1209,6 +1255,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     while (pw * 2 <= cols && pw < 256) pw *= 2;
     a.tmem_cols = cols >= 32 ? pw : 0;
     a.tc_err = B.cnt + 7;
+    a.tc_bf16 = p->precision == XT_PREC_BF16_IR;
   }
   SeArgs as = a;                         // the small systems: own work range, counter, workspace
   as.tmem_cols = 0;
@@ -1363,7 +1410,7 @@ extern "C" int solve_nlte(xt_ctx* c, const xt_nlte_params* p, double* pops_out, 
     for (int k = 0; k < 8; ++k) stats->panel_width[k] = a.nb_bucket[k];
     stats->not_converged = (double)nnc;
   }
-  if (p->precision == XT_PREC_TF32_IR) {
+  if (tcore) {
     unsigned long long gave_up = 0;
     XT_CUDA(c, cudaMemcpy(&gave_up, B.cnt + 7, sizeof(gave_up), cudaMemcpyDeviceToHost));
     if (gave_up > 0)

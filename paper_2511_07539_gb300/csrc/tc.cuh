@@ -1,6 +1,7 @@
 // Blackwell tensor-core helpers (tcgen05, sm_103a): TMEM allocation, the
 // shared-memory operand layout, one-thread MMA issue, commit to an mbarrier,
-// bounded waits and TMEM loads.  Used by the batched LU's trailing updates.
+// bounded waits and TMEM loads, for TF32 (kind::tf32) and BF16 (kind::f16)
+// operands.  Used by the batched LU's trailing updates.
 //
 // Operand layout (both A and B K-major, no swizzle): a tile of R rows (M or N)
 // by 32 K elements of 32 bits is stored as core matrices of 8 rows x 16 bytes
@@ -25,6 +26,12 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int rows) {
   return (uint32_t)((((k >> 2) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
 }
 
+// The same for 16-bit elements (BF16): core matrices of 8 rows x 8 elements,
+// K chunk j holding k = 8j..8j+7; a tile of R rows x 32 K is 4 chunks.
+__device__ __forceinline__ uint32_t tile_off16(int row, int k, int rows) {
+  return (uint32_t)((((k >> 3) * (rows >> 3) + (row >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
 // Shared-memory matrix descriptor: start address, leading and stride byte
 // offsets (all >> 4), descriptor version 1, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -36,6 +43,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // M rows and N columns.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, D F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // TMEM allocation of ncols columns (power of two >= 32) by one whole warp; the
@@ -67,6 +79,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+
+// The same with BF16 operands (kind::f16: K = 16 per MMA, 32 bytes of a row).
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
       : "memory");
 }
@@ -121,6 +143,17 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
+}
+
+// Round to BF16 (nearest, ties to even), as a 16-bit pattern.
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+  uint16_t r;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+  return r;
+}
+// Two BF16 in one word, a at the lower address.
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  return (uint32_t)to_bf16(a) | ((uint32_t)to_bf16(b) << 16);
 }
 
 }  // namespace tc
