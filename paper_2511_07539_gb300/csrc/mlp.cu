@@ -123,10 +123,20 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g) {
       }
 }
 
-// masked MSE: dY = 2 mask (Y - T) / sum(mask) (as bf16 and fp32); loss sum
+// Step state on the device, st[0] = t (the step within the current block of
+// training steps: which batch, mask sum and loss slot to use), st[1] = the
+// Adam steps taken so far (batches with a non-empty mask).  Kernels read it,
+// so one captured step serves every step of the loop.
+
+// masked MSE: dY = 2 mask (Y - T) / sum(mask) (as bf16 and fp32), the mask sum
+// msumv[t]; the loss sum to lossv[t]; an empty mask gives dY = 0 and counts no
+// Adam step
 __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
-                       const float* __restrict__ mask, int64_t n, double inv_msum,
-                       float* __restrict__ dY, __nv_bfloat16* __restrict__ dYb, double* loss) {
+                       const float* __restrict__ mask, int64_t n, const double* __restrict__ msumv,
+                       int64_t* st, float* __restrict__ dY, __nv_bfloat16* __restrict__ dYb, double* lossv) {
+  const int64_t t = st[0];
+  const double ms = msumv[t];
+  const double inv_msum = ms > 0 ? 1.0 / ms : 0.0;
   double s = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -137,7 +147,8 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
     dYb[i] = __float2bfloat16(d);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv_msum);
+  if ((threadIdx.x & 31) == 0) atomicAdd(lossv + t, s * inv_msum);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && ms > 0) st[1] += 1;
 }
 
 // dZ = dH * GELU'(Z) (fp32 and bf16)
@@ -160,9 +171,15 @@ __global__ void k_colsum(const float* __restrict__ G, int rows, int cols, float*
   out[c] = s;
 }
 
+// Adam on the FP32 master weights (bias corrections from the step count
+// st[1]), with the BF16 copy; nothing when step t's mask was empty
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ gW, float* __restrict__ m,
                        float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
-                       float c1, float c2, __nv_bfloat16* __restrict__ wb) {
+                       const double* __restrict__ msumv, const int64_t* __restrict__ st,
+                       __nv_bfloat16* __restrict__ wb) {
+  if (!(msumv[st[0]] > 0)) return;
+  const float ts = (float)st[1];
+  const float c1 = 1.f - powf(b1, ts), c2 = 1.f - powf(b2, ts);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = gW[i];
@@ -174,6 +191,8 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ gW, floa
     wb[i] = __float2bfloat16(wi);
   }
 }
+
+__global__ void k_next_step(int64_t* st) { st[0] += 1; }
 
 __global__ void k_to_bf16(const float* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -208,14 +227,15 @@ struct xt_mlp {
   float* v = nullptr;
   float* g = nullptr;                 // gradients
   __nv_bfloat16* wb = nullptr;        // BF16 copy
-  int64_t step = 0;
   int64_t cap = 0;                    // batch capacity of the activations
   std::vector<float*> Z;              // [B][size_k] pre-activations (k = 1..L)
   std::vector<__nv_bfloat16*> H;      // [B][size_k] bf16 activations (H[0] = input)
   float* dA = nullptr; float* dB = nullptr;      // fp32 gradient buffers [B][max]
   __nv_bfloat16* dAb = nullptr; __nv_bfloat16* dBb = nullptr;
   float* T = nullptr; float* M = nullptr; float* X = nullptr;
-  double* loss = nullptr;
+  double* loss = nullptr;             // one step's loss (surrogate_train_step)
+  double* msum1 = nullptr;            //   and its mask sum
+  int64_t* st = nullptr;              // step state: t, Adam steps taken
 };
 
 int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float* grads_out,
@@ -225,7 +245,7 @@ static void mlp_free(xt_mlp* n) {
   if (!n) return;
   void** ps[] = {(void**)&n->w, (void**)&n->m, (void**)&n->v, (void**)&n->g, (void**)&n->wb,
                  (void**)&n->dA, (void**)&n->dB, (void**)&n->dAb, (void**)&n->dBb, (void**)&n->T,
-                 (void**)&n->M, (void**)&n->X, (void**)&n->loss};
+                 (void**)&n->M, (void**)&n->X, (void**)&n->loss, (void**)&n->msum1, (void**)&n->st};
   for (void** p : ps) release(p);
   for (auto& p : n->Z) release((void**)&p);
   for (auto& p : n->H) release((void**)&p);
@@ -260,6 +280,7 @@ static int mlp_ensure_batch(xt_ctx* c, xt_mlp* n, int64_t B) {
   if ((rc = alloc(c, (void**)&n->M, (size_t)B * n->sizes[L] * 4, "mlp mask"))) return rc;
   if ((rc = alloc(c, (void**)&n->X, (size_t)B * n->sizes[0] * 4, "mlp input"))) return rc;
   if (!n->loss && (rc = alloc(c, (void**)&n->loss, 8, "mlp loss"))) return rc;
+  if (!n->msum1 && (rc = alloc(c, (void**)&n->msum1, 8, "mlp mask sum"))) return rc;
   n->cap = B;
   return XT_OK;
 }
@@ -304,6 +325,8 @@ int surrogate_init(xt_ctx* c, const int32_t* sizes, int32_t n_sizes, uint64_t se
   if ((rc = alloc(c, (void**)&n->v, o * 4, "mlp adam"))) return rc;
   if ((rc = alloc(c, (void**)&n->g, o * 4, "mlp grads"))) return rc;
   if ((rc = alloc(c, (void**)&n->wb, o * 2, "mlp weights"))) return rc;
+  if ((rc = alloc(c, (void**)&n->st, 2 * sizeof(int64_t), "mlp step state"))) return rc;
+  XT_CUDA(c, cudaMemsetAsync(n->st, 0, 2 * sizeof(int64_t), c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->w, 0, o * 4, c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->m, 0, o * 4, c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->v, 0, o * 4, c->stream));
@@ -314,7 +337,6 @@ int surrogate_init(xt_ctx* c, const int32_t* sizes, int32_t n_sizes, uint64_t se
   k_to_bf16<<<gb(o), 256, 0, c->stream>>>(n->w, o, n->wb);
   XT_CUDA(c, cudaGetLastError());
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
-  n->step = 0;
   return XT_OK;
 }
 
@@ -379,19 +401,21 @@ int surrogate_predict(xt_ctx* c, const float* X, int64_t B, float* Y) {
 
 }  // extern "C"
 
-// Forward, loss, backward and (optionally) Adam on the batch already in
-// n->X / n->T / n->M.
-int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float* grads_out,
-                double* loss_out) {
-  xt_mlp* n = c->mlp;
+// Forward, loss, backward and (optionally) Adam of one step, on the batch in
+// n->H[0] (bf16 input) / n->T / n->M, enqueued on stream s with no host
+// synchronisation (the step, its mask sum msumv[t] and loss slot lossv[t] are
+// read on the device from n->st, so the sequence can be captured once).
+static void mlp_enqueue_step(xt_mlp* n, int64_t B, cudaStream_t s, const double* msumv, double* lossv,
+                             double lr, bool update) {
   const int L = (int)n->sizes.size() - 1;
   const int nout = n->sizes[L];
-  cudaStream_t s = c->stream;
-  k_to_bf16<<<gb(B * n->sizes[0]), 256, 0, s>>>(n->X, B * n->sizes[0], n->H[0]);
-  mlp_forward(c, n, B);
-  XT_CUDA(c, cudaMemsetAsync(n->loss, 0, 8, s));
+  for (int k = 1; k <= L; ++k) {
+    const int fi = n->sizes[k - 1], fo = n->sizes[k];
+    gemm(s, n->H[k - 1], fi, 1, n->wb + n->woff[k - 1], fo, 1, n->Z[k], fo, n->w + n->boff[k - 1],
+         k < L ? n->H[k] : nullptr, fo, (int)B, fo, fi);
+  }
   // dY
-  k_loss<<<gb(B * nout), 256, 0, s>>>(n->Z[L], n->T, n->M, B * nout, 1.0 / msum, n->dA, n->dAb, n->loss);
+  k_loss<<<gb(B * nout), 256, 0, s>>>(n->Z[L], n->T, n->M, B * nout, msumv, n->st, n->dA, n->dAb, lossv);
   float* dZ = n->dA;
   __nv_bfloat16* dZb = n->dAb;
   float* dH = n->dB;
@@ -412,14 +436,23 @@ int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float*
       dH = (dZ == n->dA) ? n->dB : n->dA;
     }
   }
+  if (update)
+    k_adam<<<gb(n->nparam), 256, 0, s>>>(n->w, n->g, n->m, n->v, n->nparam, (float)lr, 0.9f, 0.999f, 1e-8f,
+                                         msumv, n->st, n->wb);
+}
+
+// One step on the batch already in n->X / n->T / n->M with mask sum msum
+// (surrogate_train_step), step state t = 0.
+int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float* grads_out,
+                double* loss_out) {
+  xt_mlp* n = c->mlp;
+  cudaStream_t s = c->stream;
+  k_to_bf16<<<gb(B * n->sizes[0]), 256, 0, s>>>(n->X, B * n->sizes[0], n->H[0]);
+  XT_CUDA(c, cudaMemsetAsync(n->loss, 0, 8, s));
+  XT_CUDA(c, cudaMemsetAsync(n->st, 0, sizeof(int64_t), s));
+  XT_CUDA(c, cudaMemcpyAsync(n->msum1, &msum, 8, cudaMemcpyHostToDevice, s));
+  mlp_enqueue_step(n, B, s, n->msum1, n->loss, lr, update != 0);
   XT_CUDA(c, cudaGetLastError());
-  if (update) {
-    n->step += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
-    k_adam<<<gb(n->nparam), 256, 0, s>>>(n->w, n->g, n->m, n->v, n->nparam, (float)lr, b1, b2, 1e-8f, c1, c2, n->wb);
-    XT_CUDA(c, cudaGetLastError());
-  }
   int rc;
   if (grads_out && (rc = copy(c, grads_out, n->g, n->nparam * 4, "grads"))) return rc;
   double l = 0;
@@ -513,23 +546,30 @@ __global__ void k_features(const FeatArgs a) {
   }
 }
 
-// gather rows idx[b] of X, T, M into the batch buffers
+// gather rows idx[t B + b] of X (as the bf16 input layer), T and M into the
+// batch buffers (step t = st[0]); the mask sum to msumv[t]
 __global__ void k_gather(const float* __restrict__ X, const float* __restrict__ T, const float* __restrict__ M,
-                         const int* __restrict__ idx, int64_t B, int nin, int nout, float* __restrict__ bx,
-                         float* __restrict__ bt, float* __restrict__ bm, double* msum) {
+                         const int* __restrict__ idx, const int64_t* __restrict__ st, int64_t B, int nin,
+                         int nout, __nv_bfloat16* __restrict__ hx, float* __restrict__ bt,
+                         float* __restrict__ bm, double* msumv) {
+  const int64_t t = st[0];
+  idx += t * B;
+  const int w = nin > nout ? nin : nout;
   double s = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * nout;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * w;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / nout, j = e - b * nout;
+    const int64_t b = e / w, j = e - b * w;
     const int64_t r = idx[b];
-    bt[e] = T[r * nout + j];
-    const float mv = M[r * nout + j];
-    bm[e] = mv;
-    s += mv;
-    if (j < nin) bx[b * nin + j] = X[r * nin + j];
+    if (j < nout) {
+      bt[b * nout + j] = T[r * nout + j];
+      const float mv = M[r * nout + j];
+      bm[b * nout + j] = mv;
+      s += mv;
+    }
+    if (j < nin) hx[b * nin + j] = __float2bfloat16(X[r * nin + j]);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(msum, s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(msumv + t, s);
 }
 
 // warm populations from predictions: n_i = n_z 10^(10 y_i) over the kept
@@ -678,13 +718,16 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   }
   float *X = nullptr, *T = nullptr, *M = nullptr;
   int* d_idx = nullptr;
-  double* d_msum = nullptr;
-  auto cleanup = [&]() { void* ps[] = {d_used, X, T, M, d_idx, d_msum}; for (void* q : ps) if (q) cudaFree(q); };
+  double *d_msum = nullptr, *d_loss = nullptr;
+  cudaGraphExec_t gex = nullptr;
+  auto cleanup = [&]() {
+    void* ps[] = {d_used, X, T, M, d_idx, d_msum, d_loss};
+    for (void* q : ps) if (q) cudaFree(q);
+    if (gex) cudaGraphExecDestroy(gex);
+  };
   if ((rc = alloc(c, (void**)&X, (size_t)N * nin * 4, "features")) ||
       (rc = alloc(c, (void**)&T, (size_t)N * nout * 4, "targets")) ||
-      (rc = alloc(c, (void**)&M, (size_t)N * nout * 4, "mask")) ||
-      (rc = alloc(c, (void**)&d_idx, (size_t)N * sizeof(int), "batch index")) ||
-      (rc = alloc(c, (void**)&d_msum, 8, "mask sum"))) { cleanup(); return rc; }
+      (rc = alloc(c, (void**)&M, (size_t)N * nout * 4, "mask"))) { cleanup(); return rc; }
   if ((rc = build_features(c, p->rates, p->jbar_W, p->jbar_TR, d_used, X, T, M))) { cleanup(); return rc; }
   // cells with matter only
   std::vector<double> nion(N * c->n_ion);
@@ -705,25 +748,63 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   if (cells.empty()) { cleanup(); return fail(c, XT_EINVAL, "train_surrogate: no cell with matter"); }
   const int64_t B = std::min<int64_t>(p->batch, (int64_t)cells.size());
   if ((rc = mlp_ensure_batch(c, n, B))) { cleanup(); return rc; }
+  // The steps run in blocks of whole epochs: the host shuffles the cells of
+  // each epoch of a block (a step takes the next B of them; an epoch's tail
+  // short of B is left out), uploads the block's batch indices, and replays
+  // one captured step per batch with no host synchronisation; the block's
+  // mask sums and losses come back at its end.
+  const int64_t per_epoch = (int64_t)cells.size() / B;
+  const int64_t block_epochs = std::max<int64_t>(
+      1, std::min<int64_t>(p->epochs, ((int64_t)64 << 20) / std::max<int64_t>(per_epoch * B * 4, 1)));
+  const int64_t block_steps = block_epochs * per_epoch;
+  if ((rc = alloc(c, (void**)&d_idx, (size_t)block_steps * B * sizeof(int), "batch index")) ||
+      (rc = alloc(c, (void**)&d_msum, (size_t)block_steps * 8, "mask sums")) ||
+      (rc = alloc(c, (void**)&d_loss, (size_t)block_steps * 8, "losses"))) { cleanup(); return rc; }
+  {
+    // one step captured on the context's side stream: gather, forward,
+    // backward, Adam, and the step counter
+    cudaGraph_t graph = nullptr;
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    XT_CUDA(c, cudaStreamBeginCapture(c->side, cudaStreamCaptureModeThreadLocal));
+    k_gather<<<gb(B * std::max(nin, nout)), 256, 0, c->side>>>(X, T, M, d_idx, n->st, B, nin, nout, n->H[0],
+                                                               n->T, n->M, d_msum);
+    mlp_enqueue_step(n, B, c->side, d_msum, d_loss, p->lr, true);
+    k_next_step<<<1, 1, 0, c->side>>>(n->st);
+    const cudaError_t e1 = cudaStreamEndCapture(c->side, &graph);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaGraphInstantiate(&gex, graph, 0) : e1;
+    if (graph) cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+      gex = nullptr;
+      cleanup();
+      return fail(c, XT_ECUDA, std::string("train_surrogate: step graph: ") + cudaGetErrorString(e2));
+    }
+  }
   uint64_t rng = p->seed * 0x9E3779B97F4A7C15ull + 1;
   auto next = [&]() { rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17; return rng; };
   double first = -1, last = 0;
   int64_t steps = 0;
+  std::vector<int> hidx((size_t)block_steps * B);
+  std::vector<double> hms(block_steps), hl(block_steps);
   cudaEventRecord(c->ev0, c->stream);
-  for (int ep = 0; ep < p->epochs; ++ep) {
-    for (int64_t k = (int64_t)cells.size() - 1; k > 0; --k) std::swap(cells[k], cells[next() % (k + 1)]);
-    if ((rc = copy(c, d_idx, cells.data(), cells.size() * sizeof(int), "batch index"))) { cleanup(); return rc; }
-    for (int64_t o = 0; o + B <= (int64_t)cells.size(); o += B) {
-      cudaMemsetAsync(d_msum, 0, 8, c->stream);
-      k_gather<<<gb(B * nout), 256, 0, c->stream>>>(X, T, M, d_idx + o, B, nin, nout, n->X, n->T, n->M, d_msum);
-      double msum = 0;
-      XT_CUDA(c, cudaMemcpyAsync(&msum, d_msum, 8, cudaMemcpyDeviceToHost, c->stream));
-      XT_CUDA(c, cudaStreamSynchronize(c->stream));
-      if (!(msum > 0)) continue;
-      double loss = 0;
-      if ((rc = xt_mlp_step(c, B, msum, p->lr, 1, nullptr, &loss))) { cleanup(); return rc; }
-      if (first < 0) first = loss;
-      last = loss;
+  for (int64_t ep0 = 0; ep0 < p->epochs; ep0 += block_epochs) {
+    const int64_t ne = std::min<int64_t>(block_epochs, p->epochs - ep0), ns = ne * per_epoch;
+    for (int64_t e = 0; e < ne; ++e) {
+      for (int64_t k = (int64_t)cells.size() - 1; k > 0; --k) std::swap(cells[k], cells[next() % (k + 1)]);
+      std::copy(cells.begin(), cells.begin() + per_epoch * B, hidx.begin() + e * per_epoch * B);
+    }
+    if (ns == 0) continue;
+    if ((rc = copy(c, d_idx, hidx.data(), (size_t)ns * B * sizeof(int), "batch index"))) { cleanup(); return rc; }
+    XT_CUDA(c, cudaMemsetAsync(d_msum, 0, (size_t)ns * 8, c->stream));
+    XT_CUDA(c, cudaMemsetAsync(d_loss, 0, (size_t)ns * 8, c->stream));
+    XT_CUDA(c, cudaMemsetAsync(n->st, 0, sizeof(int64_t), c->stream));
+    for (int64_t t = 0; t < ns; ++t) XT_CUDA(c, cudaGraphLaunch(gex, c->stream));
+    if ((rc = copy(c, hms.data(), d_msum, (size_t)ns * 8, "mask sums")) ||
+        (rc = copy(c, hl.data(), d_loss, (size_t)ns * 8, "losses"))) { cleanup(); return rc; }
+    XT_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int64_t t = 0; t < ns; ++t) {
+      if (!(hms[t] > 0)) continue;             // an empty mask: no step
+      if (first < 0) first = hl[t];
+      last = hl[t];
       ++steps;
     }
   }
