@@ -4,9 +4,11 @@
 // and per ion log10 n_z / 10 (it sets the optical depths); output: log10(n_i / n_z) / 10 of every level (clipped at -30 in
 // log10, masked beyond the kept levels).  Hidden layers GELU (tanh form,
 // Hendrycks & Gimpel 2016), linear output; masked mean squared error; Adam
-// (Kingma & Ba 2015) on FP32 master weights.  Every matrix product runs in
-// BF16 on the tensor cores with FP32 accumulation (warp-level mma.sync
-// m16n8k16); bias, activation, loss and optimizer kernels are FP32.
+// (Kingma & Ba 2015) on FP32 master weights.  Training runs in the fused
+// kernel of mlp_train.cu (tcgen05 MMAs, every step in one launch); this file
+// holds the network's setup, the training loop's batches and the prediction
+// forward pass, whose products (batches of up to every cell) run in BF16
+// with FP32 accumulation (warp-level mma.sync m16n8k16).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -14,6 +16,7 @@
 
 #include <cuda_bf16.h>
 
+#include "mlp.cuh"
 #include "philox.cuh"
 #include "xt_internal.cuh"
 
@@ -37,13 +40,6 @@ struct GemmArgs {
 __device__ __forceinline__ float gelu_f(float z) {
   const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
   return 0.5f * z * (1.0f + tanhf(u));
-}
-
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-  const float th = tanhf(u);
-  const float du = 0.7978845608028654f * (1.0f + 3.0f * 0.044715f * z * z);
-  return 0.5f * (1.0f + th) + 0.5f * z * (1.0f - th * th) * du;
 }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -123,77 +119,6 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const GemmArgs g) {
       }
 }
 
-// Step state on the device, st[0] = t (the step within the current block of
-// training steps: which batch, mask sum and loss slot to use), st[1] = the
-// Adam steps taken so far (batches with a non-empty mask).  Kernels read it,
-// so one captured step serves every step of the loop.
-
-// masked MSE: dY = 2 mask (Y - T) / sum(mask) (as bf16 and fp32), the mask sum
-// msumv[t]; the loss sum to lossv[t]; an empty mask gives dY = 0 and counts no
-// Adam step
-__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
-                       const float* __restrict__ mask, int64_t n, const double* __restrict__ msumv,
-                       int64_t* st, float* __restrict__ dY, __nv_bfloat16* __restrict__ dYb, double* lossv) {
-  const int64_t t = st[0];
-  const double ms = msumv[t];
-  const double inv_msum = ms > 0 ? 1.0 / ms : 0.0;
-  double s = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float r = mask[i] * (Y[i] - T[i]);
-    s += (double)r * (double)(Y[i] - T[i]);
-    const float d = (float)(2.0 * inv_msum) * r;
-    dY[i] = d;
-    dYb[i] = __float2bfloat16(d);
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(lossv + t, s * inv_msum);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && ms > 0) st[1] += 1;
-}
-
-// dZ = dH * GELU'(Z) (fp32 and bf16)
-__global__ void k_gelu_back(const float* __restrict__ dH, const float* __restrict__ Z, int64_t n,
-                            float* __restrict__ dZ, __nv_bfloat16* __restrict__ dZb) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float d = dH[i] * gelu_grad_f(Z[i]);
-    dZ[i] = d;
-    dZb[i] = __float2bfloat16(d);
-  }
-}
-
-// column sums of G [rows][cols] (bias gradients)
-__global__ void k_colsum(const float* __restrict__ G, int rows, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  float s = 0.f;
-  for (int r = 0; r < rows; ++r) s += G[(int64_t)r * cols + c];
-  out[c] = s;
-}
-
-// Adam on the FP32 master weights (bias corrections from the step count
-// st[1]), with the BF16 copy; nothing when step t's mask was empty
-__global__ void k_adam(float* __restrict__ w, const float* __restrict__ gW, float* __restrict__ m,
-                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
-                       const double* __restrict__ msumv, const int64_t* __restrict__ st,
-                       __nv_bfloat16* __restrict__ wb) {
-  if (!(msumv[st[0]] > 0)) return;
-  const float ts = (float)st[1];
-  const float c1 = 1.f - powf(b1, ts), c2 = 1.f - powf(b2, ts);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = gW[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    wb[i] = __float2bfloat16(wi);
-  }
-}
-
-__global__ void k_next_step(int64_t* st) { st[0] += 1; }
-
 __global__ void k_to_bf16(const float* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -217,38 +142,20 @@ static int gb(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 
 
 using namespace xt;
 
-// ---- network state in the context ------------------------------------------
-struct xt_mlp {
-  std::vector<int> sizes;             // n_in, h, ..., n_out
-  int64_t nparam = 0;
-  std::vector<int64_t> woff, boff;    // offsets of W_k and b_k in the flat vector
-  float* w = nullptr;                 // FP32 master
-  float* m = nullptr;
-  float* v = nullptr;
-  float* g = nullptr;                 // gradients
-  __nv_bfloat16* wb = nullptr;        // BF16 copy
-  int64_t cap = 0;                    // batch capacity of the activations
-  std::vector<float*> Z;              // [B][size_k] pre-activations (k = 1..L)
-  std::vector<__nv_bfloat16*> H;      // [B][size_k] bf16 activations (H[0] = input)
-  float* dA = nullptr; float* dB = nullptr;      // fp32 gradient buffers [B][max]
-  __nv_bfloat16* dAb = nullptr; __nv_bfloat16* dBb = nullptr;
-  float* T = nullptr; float* M = nullptr; float* X = nullptr;
-  double* loss = nullptr;             // one step's loss (surrogate_train_step)
-  double* msum1 = nullptr;            //   and its mask sum
-  int64_t* st = nullptr;              // step state: t, Adam steps taken
-};
-
 int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float* grads_out,
                 double* loss_out);
 
 static void mlp_free(xt_mlp* n) {
   if (!n) return;
-  void** ps[] = {(void**)&n->w, (void**)&n->m, (void**)&n->v, (void**)&n->g, (void**)&n->wb,
-                 (void**)&n->dA, (void**)&n->dB, (void**)&n->dAb, (void**)&n->dBb, (void**)&n->T,
-                 (void**)&n->M, (void**)&n->X, (void**)&n->loss, (void**)&n->msum1, (void**)&n->st};
+  void** ps[] = {(void**)&n->w,     (void**)&n->m,     (void**)&n->v,     (void**)&n->g,
+                 (void**)&n->wb,    (void**)&n->wp,    (void**)&n->wt,    (void**)&n->X,
+                 (void**)&n->dz[0], (void**)&n->dz[1], (void**)&n->T,     (void**)&n->M,
+                 (void**)&n->loss,  (void**)&n->msum1, (void**)&n->st,    (void**)&n->bar};
   for (void** p : ps) release(p);
   for (auto& p : n->Z) release((void**)&p);
   for (auto& p : n->H) release((void**)&p);
+  for (auto& p : n->hp) release((void**)&p);
+  for (auto& p : n->zp) release((void**)&p);
 }
 
 namespace xt {
@@ -258,6 +165,7 @@ void mlp_destroy(xt_mlp* n) {
 }
 }  // namespace xt
 
+// Prediction buffers for batches of up to B rows.
 static int mlp_ensure_batch(xt_ctx* c, xt_mlp* n, int64_t B) {
   if (B <= n->cap) return XT_OK;
   int rc;
@@ -266,21 +174,11 @@ static int mlp_ensure_batch(xt_ctx* c, xt_mlp* n, int64_t B) {
   for (auto& q : n->H) release((void**)&q);
   n->Z.assign(L + 1, nullptr);
   n->H.assign(L + 1, nullptr);
-  int mx = 0;
-  for (int s : n->sizes) mx = std::max(mx, s);
   for (int k = 0; k <= L; ++k) {
     if (k > 0 && (rc = alloc(c, (void**)&n->Z[k], (size_t)B * n->sizes[k] * 4, "mlp activations"))) return rc;
     if ((rc = alloc(c, (void**)&n->H[k], (size_t)B * n->sizes[k] * 2, "mlp activations"))) return rc;
   }
-  if ((rc = alloc(c, (void**)&n->dA, (size_t)B * mx * 4, "mlp gradients"))) return rc;
-  if ((rc = alloc(c, (void**)&n->dB, (size_t)B * mx * 4, "mlp gradients"))) return rc;
-  if ((rc = alloc(c, (void**)&n->dAb, (size_t)B * mx * 2, "mlp gradients"))) return rc;
-  if ((rc = alloc(c, (void**)&n->dBb, (size_t)B * mx * 2, "mlp gradients"))) return rc;
-  if ((rc = alloc(c, (void**)&n->T, (size_t)B * n->sizes[L] * 4, "mlp targets"))) return rc;
-  if ((rc = alloc(c, (void**)&n->M, (size_t)B * n->sizes[L] * 4, "mlp mask"))) return rc;
   if ((rc = alloc(c, (void**)&n->X, (size_t)B * n->sizes[0] * 4, "mlp input"))) return rc;
-  if (!n->loss && (rc = alloc(c, (void**)&n->loss, 8, "mlp loss"))) return rc;
-  if (!n->msum1 && (rc = alloc(c, (void**)&n->msum1, 8, "mlp mask sum"))) return rc;
   n->cap = B;
   return XT_OK;
 }
@@ -320,13 +218,14 @@ int surrogate_init(xt_ctx* c, const int32_t* sizes, int32_t n_sizes, uint64_t se
   }
   n->nparam = o;
   int rc;
+  if ((rc = mlp_layout_copies(c, n))) return rc;
   if ((rc = alloc(c, (void**)&n->w, o * 4, "mlp weights"))) return rc;
   if ((rc = alloc(c, (void**)&n->m, o * 4, "mlp adam"))) return rc;
   if ((rc = alloc(c, (void**)&n->v, o * 4, "mlp adam"))) return rc;
   if ((rc = alloc(c, (void**)&n->g, o * 4, "mlp grads"))) return rc;
   if ((rc = alloc(c, (void**)&n->wb, o * 2, "mlp weights"))) return rc;
-  if ((rc = alloc(c, (void**)&n->st, 2 * sizeof(int64_t), "mlp step state"))) return rc;
-  XT_CUDA(c, cudaMemsetAsync(n->st, 0, 2 * sizeof(int64_t), c->stream));
+  if ((rc = alloc(c, (void**)&n->st, sizeof(int64_t), "mlp step count"))) return rc;
+  XT_CUDA(c, cudaMemsetAsync(n->st, 0, sizeof(int64_t), c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->w, 0, o * 4, c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->m, 0, o * 4, c->stream));
   XT_CUDA(c, cudaMemsetAsync(n->v, 0, o * 4, c->stream));
@@ -334,7 +233,7 @@ int surrogate_init(xt_ctx* c, const int32_t* sizes, int32_t n_sizes, uint64_t se
     const int64_t cnt = (int64_t)n->sizes[k] * n->sizes[k + 1];
     k_init_w<<<gb(cnt), 256, 0, c->stream>>>(n->w + n->woff[k], cnt, (float)std::sqrt(2.0 / n->sizes[k]), seed, (uint64_t)k);
   }
-  k_to_bf16<<<gb(o), 256, 0, c->stream>>>(n->w, o, n->wb);
+  mlp_sync_copies(c, n);
   XT_CUDA(c, cudaGetLastError());
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   return XT_OK;
@@ -348,7 +247,7 @@ int surrogate_weights(xt_ctx* c, int32_t set, float* flat, size_t n_cap) {
   int rc;
   if (set) {
     if ((rc = copy(c, n->w, flat, n->nparam * 4, "weights"))) return rc;
-    k_to_bf16<<<gb(n->nparam), 256, 0, c->stream>>>(n->w, n->nparam, n->wb);
+    mlp_sync_copies(c, n);
     XT_CUDA(c, cudaGetLastError());
   } else if ((rc = copy(c, flat, n->w, n->nparam * 4, "weights"))) {
     return rc;
@@ -367,7 +266,7 @@ int surrogate_train_step(xt_ctx* c, const float* X, const float* T, const float*
   cudaSetDevice(c->device);
   xt_mlp* n = c->mlp;
   int rc;
-  if ((rc = mlp_ensure_batch(c, n, B))) return rc;
+  if ((rc = mlp_ensure_batch(c, n, B)) || (rc = mlp_train_buffers(c, n, B))) return rc;
   const int L = (int)n->sizes.size() - 1;
   const int nin = n->sizes[0], nout = n->sizes[L];
   if ((rc = copy(c, n->X, X, B * nin * 4, "X"))) return rc;
@@ -401,63 +300,21 @@ int surrogate_predict(xt_ctx* c, const float* X, int64_t B, float* Y) {
 
 }  // extern "C"
 
-// Forward, loss, backward and (optionally) Adam of one step, on the batch in
-// n->H[0] (bf16 input) / n->T / n->M, enqueued on stream s with no host
-// synchronisation (the step, its mask sum msumv[t] and loss slot lossv[t] are
-// read on the device from n->st, so the sequence can be captured once).
-static void mlp_enqueue_step(xt_mlp* n, int64_t B, cudaStream_t s, const double* msumv, double* lossv,
-                             double lr, bool update) {
-  const int L = (int)n->sizes.size() - 1;
-  const int nout = n->sizes[L];
-  for (int k = 1; k <= L; ++k) {
-    const int fi = n->sizes[k - 1], fo = n->sizes[k];
-    gemm(s, n->H[k - 1], fi, 1, n->wb + n->woff[k - 1], fo, 1, n->Z[k], fo, n->w + n->boff[k - 1],
-         k < L ? n->H[k] : nullptr, fo, (int)B, fo, fi);
-  }
-  // dY
-  k_loss<<<gb(B * nout), 256, 0, s>>>(n->Z[L], n->T, n->M, B * nout, msumv, n->st, n->dA, n->dAb, lossv);
-  float* dZ = n->dA;
-  __nv_bfloat16* dZb = n->dAb;
-  float* dH = n->dB;
-  for (int k = L; k >= 1; --k) {
-    const int fi = n->sizes[k - 1], fo = n->sizes[k];
-    // dW_k = H_{k-1}^T dZ : A(m = i, kk = b) = H[b][i]; B(kk = b, n = o) = dZ[b][o]
-    gemm(s, n->H[k - 1], 1, fi, dZb, fo, 1, n->g + n->woff[k - 1], fo, nullptr, nullptr, 0, fi, fo, (int)B);
-    k_colsum<<<(fo + 127) / 128, 128, 0, s>>>(dZ, (int)B, fo, n->g + n->boff[k - 1]);
-    if (k > 1) {
-      // dH_{k-1} = dZ W_k^T : A = dZ [B][fo]; B(kk = o, n = i) = W[i][o]
-      gemm(s, dZb, fo, 1, n->wb + n->woff[k - 1], 1, fo, dH, fi, nullptr, nullptr, 0, (int)B, fi, fo);
-      float* dZn = (dZ == n->dA) ? n->dB : n->dA;
-      __nv_bfloat16* dZnb = (dZb == n->dAb) ? n->dBb : n->dAb;
-      // dZ_{k-1} = dH * GELU'(Z_{k-1}); dH and dZn may share storage (elementwise)
-      k_gelu_back<<<gb(B * fi), 256, 0, s>>>(dH, n->Z[k - 1], B * fi, dZn, dZnb);
-      dZ = dZn;
-      dZb = dZnb;
-      dH = (dZ == n->dA) ? n->dB : n->dA;
-    }
-  }
-  if (update)
-    k_adam<<<gb(n->nparam), 256, 0, s>>>(n->w, n->g, n->m, n->v, n->nparam, (float)lr, 0.9f, 0.999f, 1e-8f,
-                                         msumv, n->st, n->wb);
-}
-
-// One step on the batch already in n->X / n->T / n->M with mask sum msum
-// (surrogate_train_step), step state t = 0.
+// One step of the fused training kernel on the batch already in n->X / n->T
+// / n->M (surrogate_train_step).
 int xt_mlp_step(xt_ctx* c, int64_t B, double msum, double lr, int update, float* grads_out,
                 double* loss_out) {
+  (void)msum;   // the kernel sums the mask itself
   xt_mlp* n = c->mlp;
-  cudaStream_t s = c->stream;
-  k_to_bf16<<<gb(B * n->sizes[0]), 256, 0, s>>>(n->X, B * n->sizes[0], n->H[0]);
-  XT_CUDA(c, cudaMemsetAsync(n->loss, 0, 8, s));
-  XT_CUDA(c, cudaMemsetAsync(n->st, 0, sizeof(int64_t), s));
-  XT_CUDA(c, cudaMemcpyAsync(n->msum1, &msum, 8, cudaMemcpyHostToDevice, s));
-  mlp_enqueue_step(n, B, s, n->msum1, n->loss, lr, update != 0);
-  XT_CUDA(c, cudaGetLastError());
+  XT_CUDA(c, cudaMemsetAsync(n->loss, 0, 8, c->stream));
+  XT_CUDA(c, cudaMemsetAsync(n->msum1, 0, 8, c->stream));
   int rc;
+  if ((rc = mlp_train_run(c, n, B, TrainSrc{n->X, n->T, n->M, nullptr}, 1, n->msum1, n->loss, lr, update != 0)))
+    return rc;
   if (grads_out && (rc = copy(c, grads_out, n->g, n->nparam * 4, "grads"))) return rc;
   double l = 0;
-  XT_CUDA(c, cudaMemcpyAsync(&l, n->loss, 8, cudaMemcpyDeviceToHost, s));
-  XT_CUDA(c, cudaStreamSynchronize(s));
+  XT_CUDA(c, cudaMemcpyAsync(&l, n->loss, 8, cudaMemcpyDeviceToHost, c->stream));
+  XT_CUDA(c, cudaStreamSynchronize(c->stream));
   if (loss_out) *loss_out = l;
   return XT_OK;
 }
@@ -544,32 +401,6 @@ __global__ void k_features(const FeatArgs a) {
       }
     }
   }
-}
-
-// gather rows idx[t B + b] of X (as the bf16 input layer), T and M into the
-// batch buffers (step t = st[0]); the mask sum to msumv[t]
-__global__ void k_gather(const float* __restrict__ X, const float* __restrict__ T, const float* __restrict__ M,
-                         const int* __restrict__ idx, const int64_t* __restrict__ st, int64_t B, int nin,
-                         int nout, __nv_bfloat16* __restrict__ hx, float* __restrict__ bt,
-                         float* __restrict__ bm, double* msumv) {
-  const int64_t t = st[0];
-  idx += t * B;
-  const int w = nin > nout ? nin : nout;
-  double s = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < B * w;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = e / w, j = e - b * w;
-    const int64_t r = idx[b];
-    if (j < nout) {
-      bt[b * nout + j] = T[r * nout + j];
-      const float mv = M[r * nout + j];
-      bm[b * nout + j] = mv;
-      s += mv;
-    }
-    if (j < nin) hx[b * nin + j] = __float2bfloat16(X[r * nin + j]);
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(msumv + t, s);
 }
 
 // warm populations from predictions: n_i = n_z 10^(10 y_i) over the kept
@@ -719,11 +550,9 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   float *X = nullptr, *T = nullptr, *M = nullptr;
   int* d_idx = nullptr;
   double *d_msum = nullptr, *d_loss = nullptr;
-  cudaGraphExec_t gex = nullptr;
   auto cleanup = [&]() {
     void* ps[] = {d_used, X, T, M, d_idx, d_msum, d_loss};
     for (void* q : ps) if (q) cudaFree(q);
-    if (gex) cudaGraphExecDestroy(gex);
   };
   if ((rc = alloc(c, (void**)&X, (size_t)N * nin * 4, "features")) ||
       (rc = alloc(c, (void**)&T, (size_t)N * nout * 4, "targets")) ||
@@ -747,12 +576,11 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   }
   if (cells.empty()) { cleanup(); return fail(c, XT_EINVAL, "train_surrogate: no cell with matter"); }
   const int64_t B = std::min<int64_t>(p->batch, (int64_t)cells.size());
-  if ((rc = mlp_ensure_batch(c, n, B))) { cleanup(); return rc; }
   // The steps run in blocks of whole epochs: the host shuffles the cells of
   // each epoch of a block (a step takes the next B of them; an epoch's tail
-  // short of B is left out), uploads the block's batch indices, and replays
-  // one captured step per batch with no host synchronisation; the block's
-  // mask sums and losses come back at its end.
+  // short of B is left out), uploads the block's batch indices, and one launch
+  // of the fused kernel runs all of the block's steps; the block's mask sums
+  // and losses come back at its end.
   const int64_t per_epoch = (int64_t)cells.size() / B;
   const int64_t block_epochs = std::max<int64_t>(
       1, std::min<int64_t>(p->epochs, ((int64_t)64 << 20) / std::max<int64_t>(per_epoch * B * 4, 1)));
@@ -760,25 +588,6 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
   if ((rc = alloc(c, (void**)&d_idx, (size_t)block_steps * B * sizeof(int), "batch index")) ||
       (rc = alloc(c, (void**)&d_msum, (size_t)block_steps * 8, "mask sums")) ||
       (rc = alloc(c, (void**)&d_loss, (size_t)block_steps * 8, "losses"))) { cleanup(); return rc; }
-  {
-    // one step captured on the context's side stream: gather, forward,
-    // backward, Adam, and the step counter
-    cudaGraph_t graph = nullptr;
-    XT_CUDA(c, cudaStreamSynchronize(c->stream));
-    XT_CUDA(c, cudaStreamBeginCapture(c->side, cudaStreamCaptureModeThreadLocal));
-    k_gather<<<gb(B * std::max(nin, nout)), 256, 0, c->side>>>(X, T, M, d_idx, n->st, B, nin, nout, n->H[0],
-                                                               n->T, n->M, d_msum);
-    mlp_enqueue_step(n, B, c->side, d_msum, d_loss, p->lr, true);
-    k_next_step<<<1, 1, 0, c->side>>>(n->st);
-    const cudaError_t e1 = cudaStreamEndCapture(c->side, &graph);
-    const cudaError_t e2 = e1 == cudaSuccess ? cudaGraphInstantiate(&gex, graph, 0) : e1;
-    if (graph) cudaGraphDestroy(graph);
-    if (e2 != cudaSuccess) {
-      gex = nullptr;
-      cleanup();
-      return fail(c, XT_ECUDA, std::string("train_surrogate: step graph: ") + cudaGetErrorString(e2));
-    }
-  }
   uint64_t rng = p->seed * 0x9E3779B97F4A7C15ull + 1;
   auto next = [&]() { rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17; return rng; };
   double first = -1, last = 0;
@@ -796,8 +605,10 @@ extern "C" int train_surrogate(xt_ctx* c, const xt_train_params* p, xt_train_sta
     if ((rc = copy(c, d_idx, hidx.data(), (size_t)ns * B * sizeof(int), "batch index"))) { cleanup(); return rc; }
     XT_CUDA(c, cudaMemsetAsync(d_msum, 0, (size_t)ns * 8, c->stream));
     XT_CUDA(c, cudaMemsetAsync(d_loss, 0, (size_t)ns * 8, c->stream));
-    XT_CUDA(c, cudaMemsetAsync(n->st, 0, sizeof(int64_t), c->stream));
-    for (int64_t t = 0; t < ns; ++t) XT_CUDA(c, cudaGraphLaunch(gex, c->stream));
+    if ((rc = mlp_train_run(c, n, B, TrainSrc{X, T, M, d_idx}, ns, d_msum, d_loss, p->lr, true))) {
+      cleanup();
+      return rc;
+    }
     if ((rc = copy(c, hms.data(), d_msum, (size_t)ns * 8, "mask sums")) ||
         (rc = copy(c, hl.data(), d_loss, (size_t)ns * 8, "losses"))) { cleanup(); return rc; }
     XT_CUDA(c, cudaStreamSynchronize(c->stream));
