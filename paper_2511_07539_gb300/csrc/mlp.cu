@@ -150,12 +150,14 @@ static void mlp_free(xt_mlp* n) {
   void** ps[] = {(void**)&n->w,     (void**)&n->m,     (void**)&n->v,     (void**)&n->g,
                  (void**)&n->wb,    (void**)&n->wp,    (void**)&n->wt,    (void**)&n->X,
                  (void**)&n->dz[0], (void**)&n->dz[1], (void**)&n->T,     (void**)&n->M,
+                 (void**)&n->dzT[0], (void**)&n->dzT[1],
                  (void**)&n->loss,  (void**)&n->msum1, (void**)&n->st,    (void**)&n->bar};
   for (void** p : ps) release(p);
   for (auto& p : n->Z) release((void**)&p);
   for (auto& p : n->H) release((void**)&p);
   for (auto& p : n->hp) release((void**)&p);
   for (auto& p : n->zp) release((void**)&p);
+  for (auto& p : n->hT) release((void**)&p);
 }
 
 namespace xt {

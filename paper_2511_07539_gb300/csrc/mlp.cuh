@@ -33,6 +33,10 @@ struct xt_mlp {
   std::vector<__nv_bfloat16*> hp;     // [B][P(s_k)] activations, k = 0..L-1
   std::vector<float*> zp;             // [B][s_k] pre-activations, k = 1..L-1 (index k)
   __nv_bfloat16* dz[2] = {nullptr, nullptr};   // [B][P(max s)] output gradients, alternating
+  // the same transposed, rows of P(B): hT_k [s_k + 1][P(B)] (the last row all
+  // ones over the batch, for the bias gradients), dzT [max s][P(B)]
+  std::vector<__nv_bfloat16*> hT;
+  __nv_bfloat16* dzT[2] = {nullptr, nullptr};
   float* T = nullptr;                 // [B][s_L] targets and mask of the batch
   float* M = nullptr;
   double* loss = nullptr;             // one step's loss and mask sum (surrogate_train_step)

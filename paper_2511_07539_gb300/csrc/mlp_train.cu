@@ -8,9 +8,11 @@
 //   backward dW_k = H_(k-1)^T dZ_k         rows = inputs i, K = batch; an extra
 //            row of ones in H^T gives the bias gradient sum_b dZ_k in row s_(k-1)
 //            dH_(k-1) = dZ_k W_k^T          rows = batch, K = s_k
-// The CTA stages both operands through registers into the canonical K-major
-// layout of tc.cuh (transposing where the product wants it), in chunks of 256
-// K; the epilogues read the accumulator with tcgen05.ld.  Hidden activations
+// The epilogues write every activation and output gradient twice, by rows
+// ([b][i]) and transposed ([i][b]), so that each product's operands are rows
+// with K contiguous; the CTA stages them through registers into the canonical
+// K-major layout of tc.cuh, in chunks of 256 K, and reads the accumulator with
+// tcgen05.ld.  Hidden activations
 // GELU (tanh form), loss and Adam as in the per-kernel reference of mlp.cu.
 #include <cuda_runtime.h>
 
@@ -37,6 +39,7 @@ struct TrainArgs {
   const float* X; const float* Tsrc; const float* Msrc; const int* idx;
   float* Tb; float* Mb;                          // the batch's targets and mask
   __nv_bfloat16* hp[kTrMaxL]; float* zp[kTrMaxL]; __nv_bfloat16* dz[2];
+  __nv_bfloat16* hT[kTrMaxL]; __nv_bfloat16* dzT[2]; int bT;   // transposed copies, rows of bT = P(B)
   __nv_bfloat16* wp; __nv_bfloat16* wt; int64_t wpo[kTrMaxL], wto[kTrMaxL];
   float* w; float* m; float* v; float* g; __nv_bfloat16* wb;
   int64_t woff[kTrMaxL], boff[kTrMaxL];
@@ -90,67 +93,30 @@ __device__ bool grid_barrier(unsigned* bar) {
 
 // Operand rows r < R (128 or 32) of a K chunk, element (r, k) =
 // src[(r0 + r) ld + kc + k], zero for r0 + r >= nrows; k < kn (a multiple of
-// 16 with kc + kn <= ld, ld a multiple of 16), in 16-byte pieces.
+// 16 with kc + kn <= ld, ld a multiple of 16), in 16-byte pieces.  A warp
+// takes 8 rows x 4 pieces (lane % 8 the row, lane / 8 the piece): each row's
+// pieces are 64 contiguous bytes of the source, and every 8 lanes store 128
+// contiguous bytes of the tile (no bank conflicts).
 template <int R>
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int ld,
                                            int r0, int nrows, int kc, int kn) {
+  constexpr int kGroups = R / 8;
   constexpr int kMax = R * (kTrKC / 8) / kTrThreads;
-  const int per_row = kn >> 3, pieces = R * per_row;
+  const int per_row = kn >> 3;
   uint4 val[kMax];
 #pragma unroll
   for (int q = 0; q < kMax; ++q) {
-    const int e = threadIdx.x + kTrThreads * q;
+    const int sl = threadIdx.x + kTrThreads * q, lane = sl & 31, w = sl >> 5;
+    const int r = (w % kGroups) * 8 + (lane & 7), c8 = (w / kGroups) * 4 + (lane >> 3);
     val[q] = make_uint4(0u, 0u, 0u, 0u);
-    if (e < pieces) {
-      const int r = e / per_row, k8 = (e - r * per_row) << 3;
-      if (r0 + r < nrows) val[q] = *reinterpret_cast<const uint4*>(src + (int64_t)(r0 + r) * ld + kc + k8);
-    }
+    if (c8 < per_row && r0 + r < nrows)
+      val[q] = *reinterpret_cast<const uint4*>(src + (int64_t)(r0 + r) * ld + kc + 8 * c8);
   }
 #pragma unroll
   for (int q = 0; q < kMax; ++q) {
-    const int e = threadIdx.x + kTrThreads * q;
-    if (e < pieces) {
-      const int r = e / per_row, k8 = (e - r * per_row) << 3;
-      *reinterpret_cast<uint4*>(dst + tc::tile_off16(r, k8, R)) = val[q];
-    }
-  }
-}
-
-// The transposed operand: element (r, k) = src[(kc + k) ld + r0 + r] for
-// kc + k < kvalid and r0 + r < nvalid, 1 in row r0 + r == ones (a row of ones
-// over the valid k), else zero; read in 16-byte pieces along r, written as
-// single elements.
-template <int R>
-__device__ __forceinline__ void stage_cols(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int ld,
-                                           int r0, int nvalid, int ones, int kc, int kn, int kvalid) {
-  constexpr int kMax = R / 8 * kTrKC / kTrThreads;
-  constexpr int rp = R / 8;
-  const int pieces = kn * rp;
-  uint4 val[kMax];
-#pragma unroll
-  for (int q = 0; q < kMax; ++q) {
-    const int e = threadIdx.x + kTrThreads * q;
-    val[q] = make_uint4(0u, 0u, 0u, 0u);
-    if (e < pieces) {
-      const int k = e / rp, c = r0 + ((e - k * rp) << 3);
-      if (kc + k < kvalid && c + 8 <= ld) val[q] = *reinterpret_cast<const uint4*>(src + (int64_t)(kc + k) * ld + c);
-    }
-  }
-  const uint16_t one = 0x3F80u;   // 1.0 in BF16
-#pragma unroll
-  for (int q = 0; q < kMax; ++q) {
-    const int e = threadIdx.x + kTrThreads * q;
-    if (e < pieces) {
-      const int k = e / rp, r8 = (e - k * rp) << 3;
-      const uint32_t wv[4] = {val[q].x, val[q].y, val[q].z, val[q].w};
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int mrow = r0 + r8 + j;
-        uint16_t x = (uint16_t)(wv[j >> 1] >> ((j & 1) * 16));
-        if (mrow >= nvalid) x = (mrow == ones && kc + k < kvalid) ? one : (uint16_t)0;
-        *reinterpret_cast<uint16_t*>(dst + tc::tile_off16(r8 + j, k, R)) = x;
-      }
-    }
+    const int sl = threadIdx.x + kTrThreads * q, lane = sl & 31, w = sl >> 5;
+    const int r = (w % kGroups) * 8 + (lane & 7), c8 = (w / kGroups) * 4 + (lane >> 3);
+    if (c8 < per_row) *reinterpret_cast<uint4*>(dst + tc::tile_off16(r, 8 * c8, R)) = val[q];
   }
 }
 
@@ -226,8 +192,14 @@ __device__ void phase_gather(const TrainArgs& a, int64_t t) {
   for (int64_t e = tid; e < (int64_t)B * pin; e += nth) {
     const int b = (int)(e / pin), j = (int)(e - (int64_t)b * pin);
     const int64_t r = idx ? idx[b] : b;
-    a.hp[0][e] = __float2bfloat16(j < nin ? a.X[r * nin + j] : 0.f);
+    const __nv_bfloat16 x = __float2bfloat16(j < nin ? a.X[r * nin + j] : 0.f);
+    a.hp[0][e] = x;
+    if (j < nin) a.hT[0][(int64_t)j * a.bT + b] = x;
   }
+  // the row of ones after each layer's inputs (bias gradients), once per launch
+  if (t == 0)
+    for (int k = 0; k < a.L; ++k)
+      for (int64_t b = tid; b < B; b += nth) a.hT[k][(int64_t)a.s[k] * a.bT + b] = __float2bfloat16(1.f);
   double ms = 0;
   for (int64_t e = tid; e < (int64_t)B * nout; e += nth) {
     float mv;
@@ -306,7 +278,9 @@ __device__ bool phase_forward(const TrainArgs& a, int k, int64_t t, TcCta& tc_, 
           if (o < so) {
             const float z = v[q] + bias[o];
             a.zp[k][(int64_t)b * so + o] = z;
-            a.hp[k][(int64_t)b * po + o] = __float2bfloat16(tr_gelu(z));
+            const __nv_bfloat16 h = __float2bfloat16(tr_gelu(z));
+            a.hp[k][(int64_t)b * po + o] = h;
+            a.hT[k][(int64_t)o * a.bT + b] = h;
           } else if (o < po) {
             a.hp[k][(int64_t)b * po + o] = __float2bfloat16(0.f);
           }
@@ -317,7 +291,9 @@ __device__ bool phase_forward(const TrainArgs& a, int k, int64_t t, TcCta& tc_, 
             const float d = y - a.Tb[(int64_t)b * so + o];
             const float r = a.Mb[(int64_t)b * so + o] * d;
             loss += (double)r * (double)d;
-            dY[o] = __float2bfloat16((float)(2.0 * inv) * r);
+            const __nv_bfloat16 gy = __float2bfloat16((float)(2.0 * inv) * r);
+            dY[o] = gy;
+            a.dzT[k & 1][(int64_t)o * a.bT + b] = gy;
           } else if (o < po) {
             dY[o] = __float2bfloat16(0.f);
           }
@@ -330,16 +306,17 @@ __device__ bool phase_forward(const TrainArgs& a, int k, int64_t t, TcCta& tc_, 
 }
 
 // Backward through layer k (L..1): the weight and bias gradients (tiles of
-// 128 inputs, the row of ones last, x 32 outputs; K = the batch) and, for
+// 128 inputs, the row of ones last, x 32 outputs; K = the batch, from the
+// transposed copies) and, for
 // k > 1, dZ_(k-1) = (dZ_k W_k^T) GELU'(Z_(k-1)) (tiles of 128 batch rows x 32
 // inputs; K = s_k), in one set of tiles.
 __device__ bool phase_backward(const TrainArgs& a, int k, TcCta& tc_, unsigned char* sa, unsigned char* sb) {
   const int B = a.B, si = a.s[k - 1], so = a.s[k], pi = a.ps[k - 1], po = a.ps[k];
-  const int bpad = pad16(B);
   const int nt1 = (so + kTrN - 1) / kTrN, t1 = ((si + 1 + 127) / 128) * nt1;
   const int nt2 = (si + kTrN - 1) / kTrN, t2 = k > 1 ? ((B + 127) / 128) * nt2 : 0;
   const __nv_bfloat16* dZ = a.dz[k & 1];
-  const __nv_bfloat16* H = a.hp[k - 1];
+  const __nv_bfloat16* dZT = a.dzT[k & 1];
+  const __nv_bfloat16* HT = a.hT[k - 1];
   const __nv_bfloat16* Wp = a.wp + a.wpo[k - 1];
   float* gW = a.g + a.woff[k - 1];
   float* gb = a.g + a.boff[k - 1];
@@ -347,8 +324,8 @@ __device__ bool phase_backward(const TrainArgs& a, int k, TcCta& tc_, unsigned c
     if (tile < t1) {
       const int m0 = (tile / nt1) * 128, n0 = (tile % nt1) * kTrN;
       const bool ok = mma_tile(
-          tc_, sa, sb, bpad, [&](int kc, int kn) { stage_cols<128>(sa, H, pi, m0, si, si, kc, kn, B); },
-          [&](int kc, int kn) { stage_cols<kTrN>(sb, dZ, a.dzld, n0, so, -1, kc, kn, B); });
+          tc_, sa, sb, a.bT, [&](int kc, int kn) { stage_rows<128>(sa, HT, a.bT, m0, si + 1, kc, kn); },
+          [&](int kc, int kn) { stage_rows<kTrN>(sb, dZT, a.bT, n0, so, kc, kn); });
       if (!ok) return false;
       epilogue(tc_, [&](int row, int c0, const float* v) {
         const int i = m0 + row;
@@ -369,6 +346,7 @@ __device__ bool phase_backward(const TrainArgs& a, int k, TcCta& tc_, unsigned c
           [&](int kc, int kn) { stage_rows<kTrN>(sb, Wp, po, n0, si, kc, kn); });
       if (!ok) return false;
       __nv_bfloat16* dZn = a.dz[(k - 1) & 1];
+      __nv_bfloat16* dZnT = a.dzT[(k - 1) & 1];
       const float* Z = a.zp[k - 1];
       epilogue(tc_, [&](int row, int c0, const float* v) {
         const int b = m0 + row;
@@ -376,9 +354,11 @@ __device__ bool phase_backward(const TrainArgs& a, int k, TcCta& tc_, unsigned c
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int i = n0 + c0 + q;
-          if (i < si)
-            dZn[(int64_t)b * a.dzld + i] = __float2bfloat16(v[q] * tr_gelu_grad(Z[(int64_t)b * si + i]));
-          else if (i < pi)
+          if (i < si) {
+            const __nv_bfloat16 d = __float2bfloat16(v[q] * tr_gelu_grad(Z[(int64_t)b * si + i]));
+            dZn[(int64_t)b * a.dzld + i] = d;
+            dZnT[(int64_t)i * a.bT + b] = d;
+          } else if (i < pi)
             dZn[(int64_t)b * a.dzld + i] = __float2bfloat16(0.f);
         }
       });
@@ -487,10 +467,14 @@ int mlp_train_buffers(xt_ctx* c, xt_mlp* n, int64_t B) {
   const int L = (int)n->sizes.size() - 1;
   for (auto& q : n->hp) release((void**)&q);
   for (auto& q : n->zp) release((void**)&q);
+  for (auto& q : n->hT) release((void**)&q);
   release((void**)&n->dz[0]); release((void**)&n->dz[1]);
+  release((void**)&n->dzT[0]); release((void**)&n->dzT[1]);
   release((void**)&n->T); release((void**)&n->M);
   n->hp.assign(L, nullptr);
   n->zp.assign(L, nullptr);
+  n->hT.assign(L, nullptr);
+  const size_t bT = (size_t)pad16((int)B);
   int smax = 0;
   for (int s : n->sizes) smax = std::max(smax, pad16(s));
   int rc;
@@ -499,10 +483,12 @@ int mlp_train_buffers(xt_ctx* c, xt_mlp* n, int64_t B) {
     if ((rc = alloc(c, (void**)&n->hp[k], hb, "mlp activations"))) return rc;
     XT_CUDA(c, cudaMemsetAsync(n->hp[k], 0, hb, c->stream));
     if (k > 0 && (rc = alloc(c, (void**)&n->zp[k], (size_t)B * n->sizes[k] * 4, "mlp activations"))) return rc;
+    if ((rc = alloc(c, (void**)&n->hT[k], (size_t)(n->sizes[k] + 1) * bT * 2, "mlp activations"))) return rc;
   }
   for (int j = 0; j < 2; ++j) {
     if ((rc = alloc(c, (void**)&n->dz[j], (size_t)B * smax * 2, "mlp gradients"))) return rc;
     XT_CUDA(c, cudaMemsetAsync(n->dz[j], 0, (size_t)B * smax * 2, c->stream));
+    if ((rc = alloc(c, (void**)&n->dzT[j], (size_t)smax * bT * 2, "mlp gradients"))) return rc;
   }
   if ((rc = alloc(c, (void**)&n->T, (size_t)B * n->sizes[L] * 4, "mlp targets"))) return rc;
   if ((rc = alloc(c, (void**)&n->M, (size_t)B * n->sizes[L] * 4, "mlp mask"))) return rc;
@@ -532,6 +518,17 @@ int mlp_train_run(xt_ctx* c, xt_mlp* n, int64_t B, const TrainSrc& src, int64_t 
   a.Tb = n->T; a.Mb = n->M;
   for (int k = 0; k < L; ++k) { a.hp[k] = n->hp[k]; a.zp[k] = n->zp[k]; }
   a.dz[0] = n->dz[0]; a.dz[1] = n->dz[1];
+  // the transposed copies in rows of P(B), zero beyond the batch (a launch
+  // with another batch size may have left values there)
+  a.bT = pad16((int)B);
+  for (int k = 0; k < L; ++k) {
+    a.hT[k] = n->hT[k];
+    XT_CUDA(c, cudaMemsetAsync(n->hT[k], 0, (size_t)(n->sizes[k] + 1) * a.bT * 2, c->stream));
+  }
+  for (int j = 0; j < 2; ++j) {
+    a.dzT[j] = n->dzT[j];
+    XT_CUDA(c, cudaMemsetAsync(n->dzT[j], 0, (size_t)smax * a.bT * 2, c->stream));
+  }
   a.lr = (float)lr; a.b1 = 0.9f; a.b2 = 0.999f; a.eps = 1e-8f; a.update = update ? 1 : 0;
   a.msumv = msumv; a.lossv = lossv; a.nsteps = nsteps; a.st = n->st; a.bar = n->bar;
   const size_t smem = kTrSmemA + kTrSmemB;
