@@ -588,6 +588,27 @@ def nlte_bench(local, stream_ptr, n=64):
     return out
 
 
+def train_bench(local, stream_ptr, epochs=60):
+    """A9 training alone: the surrogate (4 layers: 333 -> 256 -> 256 -> 256 ->
+    406) on the 32^3 onion's populations (10 ions of 20-60 levels, J_ext
+    rates), batch 128, `epochs` passes over the 17,152 cells with matter, all
+    steps in launches of the fused training kernel.  Timed twice, the second
+    continuing from the first's weights; the faster is reported."""
+    import paper_2511_07539_gb300 as xt
+    import synth
+    w = synth.clumpy_onion(n=32, n_packets=2_000_000, seed=1, n_lines=5000, level_range=(20, 60),
+                           subdomains=(4, 4, 4))
+    ctx = xt.Context(local, stream_ptr)
+    ctx.load(w)
+    runs = [xt.train_surrogate(ctx.h, epochs=epochs, batch=128, lr=2e-3, rates=xt.XT_RATES_JBAR,
+                               jbar_W=5.6e-5, jbar_TR=8000.0) for _ in range(2)]
+    ctx.close()
+    tr = min(runs, key=lambda r: r["train_ms"])
+    return {"workload": w.name + " surrogate 333-256-256-256-406, batch 128", "epochs": epochs,
+            "steps": tr["steps"], "train_ms": tr["train_ms"], "us_per_step": tr["train_ms"] * 1e3 / tr["steps"],
+            "first_loss": runs[0]["first_loss"], "last_loss": runs[0]["last_loss"]}
+
+
 def coupled_bench(local, stream_ptr, n=32):
     """A10: the coupled loop to a relative population change <= 1e-3 on a
     clumpy onion of n^3 cells (10 ions of 20-60 levels, 5000 lines, 2e6
@@ -735,6 +756,8 @@ def main():
     ap.add_argument("--no-coupled", action="store_true", help="skip the coupled-loop measurement")
     ap.add_argument("--only-coupled", action="store_true", help="print the coupled-loop object alone")
     ap.add_argument("--coupled-n", type=int, default=32)
+    ap.add_argument("--only-train", action="store_true", help="print the surrogate-training object alone")
+    ap.add_argument("--train-epochs", type=int, default=60)
     ap.add_argument("--no-stream", action="store_true", help="skip the host-streamed store measurement")
     ap.add_argument("--no-scatter", action="store_true",
                     help="skip the scatter-mode and rates measurement")
@@ -822,6 +845,11 @@ def main():
         if rank == 0:
             print(json.dumps({"scatter_rates": scatter_rates_bench(
                 local, torch.cuda.current_stream().cuda_stream)}), flush=True)
+        return
+    if args.only_train:
+        if rank == 0:
+            print(json.dumps({"train": train_bench(local, torch.cuda.current_stream().cuda_stream,
+                                                   args.train_epochs)}), flush=True)
         return
     if args.only_coupled:
         if rank == 0:

@@ -31,7 +31,7 @@ constexpr int kTrMaxL = 8;                     // layers
 constexpr size_t kTrSmemA = 128 * kTrKC * 2;   // 64 KB
 constexpr size_t kTrSmemB = kTrN * kTrKC * 2;  // 16 KB
 constexpr long long kTrMmaSpin = 1ll << 24;    // polls of an MMA completion
-constexpr long long kTrBarSpin = 1ll << 22;    // polls of a grid barrier (256 ns sleeps: about a second)
+constexpr long long kTrBarSpin = 1ll << 24;    // polls of a grid barrier (64 ns sleeps: about a second)
 
 struct TrainArgs {
   int L, B, nout, dzld;
@@ -80,7 +80,7 @@ __device__ bool grid_barrier(unsigned* bar) {
         long long i = 0;
         while (vb[1] == g0) {
           if (vb[2] != 0 || ++i > kTrBarSpin) { atomicExch(bar + 2, 1u); ok = 0; break; }
-          __nanosleep(256);
+          __nanosleep(64);
         }
       }
       __threadfence();
@@ -537,9 +537,13 @@ int mlp_train_run(xt_ctx* c, xt_mlp* n, int64_t B, const TrainSrc& src, int64_t 
   XT_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_train, kTrThreads, smem));
   XT_CUDA(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
   if (per_sm < 1) return fail(c, XT_ECUDA, "surrogate training: the kernel does not fit an SM");
+  // one CTA per SM: the phases have up to a few dozen tiles, and the
+  // elementwise work (gather, Adam) takes every thread the launch has (fewer
+  // CTAs, sized to the largest phase, measured slower)
+  const int grid = nsm;
   XT_CUDA(c, cudaMemsetAsync(n->bar, 0, 4 * sizeof(unsigned), c->stream));
   void* args[] = {(void*)&a};
-  XT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_train, dim3(nsm), dim3(kTrThreads), args, smem, c->stream));
+  XT_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_train, dim3(grid), dim3(kTrThreads), args, smem, c->stream));
   unsigned err = 0;
   XT_CUDA(c, cudaMemcpyAsync(&err, n->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
