@@ -68,6 +68,41 @@ def test_gradients_vs_fp64_oracle(xt):
         o += n
 
 
+@pytest.mark.parametrize("sizes,B", [([35, 50, 7], 37), ([17, 129, 33, 300], 130)])
+def test_gradients_ragged_shapes(xt, sizes, B):
+    """The fused kernel pads every row to 16 elements and the batch to tiles
+    of 128: layer sizes and batches that fill neither (a second batch tile of
+    2 rows; 129 inputs, whose last weight row and the bias row spill into a
+    second 128-row tile; a 300-wide K in two chunks) give the FP64 oracle's
+    gradients."""
+    rng = np.random.default_rng(7)
+    flat = np.concatenate([np.concatenate([rng.standard_normal(a * b) * np.sqrt(2.0 / a),
+                                           rng.standard_normal(b) * 0.1])
+                           for a, b in zip(sizes[:-1], sizes[1:])]).astype(np.float32)
+    nin, nout = sizes[0], sizes[-1]
+    X = rng.standard_normal((B, nin)).astype(np.float32)
+    T = rng.standard_normal((B, nout)).astype(np.float32)
+    M = (rng.random((B, nout)) > 0.3).astype(np.float32)
+    with _ctx(xt) as ctx:
+        xt.surrogate_init(ctx.h, sizes)
+        xt.surrogate_weights(ctx.h, flat)
+        loss, g = xt.surrogate_train_step(ctx.h, X, T, M, update=False, n_param=flat.size)
+    params = [(_bf16(W), b) for W, b in mlp.unflatten(flat.astype(np.float64), sizes)]
+    l_o, g_o = mlp.loss_and_grads(params, _bf16(X), T.astype(np.float64), M.astype(np.float64))
+    go = np.concatenate([np.concatenate([gW.ravel(), gb.ravel()]) for gW, gb in g_o])
+    assert abs(loss - l_o) / l_o < 1e-2
+    o = 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        n = a * b + b
+        gl, gol = g[o:o + n], go[o:o + n]
+        cos = float(gl @ gol / (np.linalg.norm(gl) * np.linalg.norm(gol)))
+        assert cos >= 0.999 and np.linalg.norm(gl - gol) / np.linalg.norm(gol) < 2e-2, (a, b, cos)
+        # the bias part alone (the row of ones)
+        bl, bol = gl[a * b:], gol[a * b:]
+        assert np.linalg.norm(bl - bol) / np.linalg.norm(bol) < 2e-2, (a, b)
+        o += n
+
+
 def test_training_lowers_the_loss(xt):
     rng = np.random.default_rng(1)
     sizes = [16, 64, 64, 8]
