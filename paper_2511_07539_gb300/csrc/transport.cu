@@ -324,6 +324,23 @@ struct EmitOut {
 // viewer's centre direction, at its bin's start frequency, with the bin's
 // emission times dOmega_k / 4 pi.  E0 = 0 marks an empty ray (the cell has no
 // emission in the bin), which is not traced.  The walls are half a cell away.
+// The ray id a lane takes at id v of the launch's range, for the trace
+// kernels' refills: within every cell's block of nbin x nview ids that the
+// launch holds whole, the lanes take the ids bin by bin for one viewer after
+// another, so that a warp's rays share their start point and direction and
+// cross the same faces together (their frequencies, hence their line tests,
+// differ); ids in a block the launch holds only in part are taken in order.
+// A bijection of the launch's range onto itself: every ray is traced once and
+// keeps its id (records, tallies).
+__device__ __forceinline__ int64_t ray_id_of(const EmitArgs& a, int64_t v) {
+  const RayTables& T = a.ray;
+  const int64_t per_cell = T.nbin * T.nview;
+  const int64_t lo = (v / per_cell) * per_cell;
+  if (T.nview <= 1 || lo < a.p_begin || lo + per_cell > a.p_begin + a.n) return v;
+  const int64_t rem = v - lo, kv = rem / T.nbin;
+  return lo + (rem - kv * T.nbin) * T.nview + kv;
+}
+
 __device__ __forceinline__ void emit_ray(const EmitArgs& a, int64_t rid, EmitOut& o) {
   const Geometry& g = a.g;
   const RayTables& T = a.ray;
@@ -671,7 +688,7 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
             // emit the packet here: its state goes to registers; the pool keeps
             // what the escape tallies read (direction, lab frequency, id)
             i = (int)my;
-            const int64_t p = a.em.p_begin + (int64_t)my;
+            const int64_t p = RAYS ? ray_id_of(a.em, a.em.p_begin + (int64_t)my) : a.em.p_begin + (int64_t)my;
             EmitOut o;
             if constexpr (RAYS) emit_ray(a.em, p, o);
             else emit_packet(a.em, trig, p, o);
@@ -1404,7 +1421,7 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
         } else if (!have && my < (unsigned long long)a.n_list) {
           // ---- emission
           i = (int)my;
-          const int64_t p = em.p_begin + (int64_t)my;
+          const int64_t p = RAYS ? ray_id_of(em, em.p_begin + (int64_t)my) : em.p_begin + (int64_t)my;
           int64_t c;
           int idx[3];
           double E0;
@@ -2279,8 +2296,15 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       return fail(c, XT_EINVAL, "run_transport_domain: more than 2^27 packets in one call");
   }
   // one chunk of up to 2^27 packets (23 GB of pool): the whole emission of a
-  // paper-scale pass runs while the estimator store is being cleared
-  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
+  // paper-scale pass runs while the estimator store is being cleared; rays
+  // in chunks of whole cells' blocks of ids where a block fits (the trace
+  // kernels hand a warp the rays of one cell and viewer only within blocks a
+  // launch holds whole)
+  int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
+  if (rays && count > chunk) {
+    const int64_t per_cell = rtab_rays.nbin * rtab_rays.nview;
+    if (per_cell > 0 && per_cell <= chunk) chunk = (chunk / per_cell) * per_cell;
+  }
   if ((rc = ensure_buffers(c, chunk, nsd))) return rc;
   const int64_t cap = c->pool_cap;
   if (host_store && c->stream_q_cap < cap) {      // out, carry in, carry out queues
