@@ -324,14 +324,16 @@ struct EmitOut {
 // viewer's centre direction, at its bin's start frequency, with the bin's
 // emission times dOmega_k / 4 pi.  E0 = 0 marks an empty ray (the cell has no
 // emission in the bin), which is not traced.  The walls are half a cell away.
-// The ray id a lane takes at id v of the launch's range, for the trace
-// kernels' refills: within every cell's block of nbin x nview ids that the
-// launch holds whole, the lanes take the ids bin by bin for one viewer after
-// another, so that a warp's rays share their start point and direction and
-// cross the same faces together (their frequencies, hence their line tests,
-// differ); ids in a block the launch holds only in part are taken in order.
-// A bijection of the launch's range onto itself: every ray is traced once and
-// keeps its id (records, tallies).
+// The ray id a lane takes at id v of the launch's range, for the spherical
+// walk's refill: within every cell's block of nbin x nview ids that the
+// launch holds whole, the lanes take the rays of one viewer after another,
+// bin by bin, so that a warp's rays share their start point and direction and
+// cross the same faces together, and their neighbouring frequencies give them
+// line-test loops of similar length; ids in a block the launch holds only in
+// part are taken in order.  A bijection of the launch's range onto itself:
+// every ray is traced once and keeps its id.  (Bins spread across the band
+// instead, 1.7x slower; the same order on the cube, whose cell walk is cheap,
+// 1.8x slower than ids in order.)
 __device__ __forceinline__ int64_t ray_id_of(const EmitArgs& a, int64_t v) {
   const RayTables& T = a.ray;
   const int64_t per_cell = T.nbin * T.nview;
@@ -613,6 +615,10 @@ __device__ __forceinline__ bool pi_segment(const TraceArgs& a, const FixExpTable
 enum { T_ABS, T_DROP, T_ABSE, T_REEM, T_THERM, T_EMITN, T_EMITE, T_NACC, T_PIN = T_NACC, T_PIE };
 constexpr int kMaxSteps = 4;      // walls crossed per search before the lane yields
 constexpr int kRefillLanes = 24;  // empty lanes of a warp that trigger a refill with emission
+// Rays on the spherical grid: a warp is refilled only once all its lanes are
+// empty, so that it keeps walking one cell's and viewer's rays together
+// (ray_id_of)
+constexpr int kRayRefillLanes = 32;
 constexpr int kLogSegments = 4096; // touched-slot log segments (>= trace blocks per launch)
 
 template <int MODE, bool PI = false, bool RAYS = false, bool WR = false>
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(256, (MODE == XT_MODE_ATTEN && !PI) ? 4 : 2) k
             // emit the packet here: its state goes to registers; the pool keeps
             // what the escape tallies read (direction, lab frequency, id)
             i = (int)my;
-            const int64_t p = RAYS ? ray_id_of(a.em, a.em.p_begin + (int64_t)my) : a.em.p_begin + (int64_t)my;
+            const int64_t p = a.em.p_begin + (int64_t)my;
             EmitOut o;
             if constexpr (RAYS) emit_ray(a.em, p, o);
             else emit_packet(a.em, trig, p, o);
@@ -1379,7 +1385,8 @@ __global__ void __launch_bounds__(256) k_trace_sph(const TraceArgs a) {
       const unsigned full = 0xffffffffu;
       const unsigned m0 = __ballot_sync(full, !have);
       if (m0 == full && drained) break;
-      const unsigned m = (drained || (m0 != full && __popc(m0) < kSphRefill)) ? 0u : m0;
+      const unsigned m =
+          (drained || (m0 != full && __popc(m0) < (RAYS ? kRayRefillLanes : kSphRefill))) ? 0u : m0;
       if (m) {
         const int leader = __ffs(m) - 1;
         unsigned long long base = 0;
@@ -2297,8 +2304,8 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   }
   // one chunk of up to 2^27 packets (23 GB of pool): the whole emission of a
   // paper-scale pass runs while the estimator store is being cleared; rays
-  // in chunks of whole cells' blocks of ids where a block fits (the trace
-  // kernels hand a warp the rays of one cell and viewer only within blocks a
+  // in chunks of whole cells' blocks of ids where a block fits (the spherical
+  // walk hands a warp the rays of one cell and viewer only within blocks a
   // launch holds whole)
   int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 27);
   if (rays && count > chunk) {
