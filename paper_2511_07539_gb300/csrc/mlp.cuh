@@ -31,7 +31,7 @@ struct xt_mlp {
   // training buffers (batch capacity tcap), rows padded to P(s)
   int64_t tcap = 0;
   std::vector<__nv_bfloat16*> hp;     // [B][P(s_k)] activations, k = 0..L-1
-  std::vector<float*> zp;             // [B][s_k] pre-activations, k = 1..L-1 (index k)
+  std::vector<float*> zp;             // [B][P(s_k)] pre-activations, k = 1..L-1 (index k)
   __nv_bfloat16* dz[2] = {nullptr, nullptr};   // [B][P(max s)] output gradients, alternating
   // the same transposed, rows of P(B): hT_k [s_k + 1][P(B)] (the last row all
   // ones over the batch, for the bias gradients), dzT [max s][P(B)]

@@ -219,29 +219,41 @@ __device__ void phase_gather(const TrainArgs& a, int64_t t) {
 
 // Adam on the FP32 master weights after step t (nothing if its mask was
 // empty; `count` the steps taken, the same in every CTA), writing the BF16
-// copies: flat (prediction) and both operand layouts.
+// copies: flat (prediction) and both operand layouts.  The flat vector is one
+// range (per layer W_k then b_k), walked four parameters at a time per thread
+// so that their loads are in flight together.
 __device__ void phase_adam(const TrainArgs& a, int64_t t, int64_t& count) {
   if (!a.update || !(a.msumv[t] > 0)) return;
   ++count;
   const float c1 = 1.f - powf(a.b1, (float)count), c2 = 1.f - powf(a.b2, (float)count);
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-  for (int k = 1; k <= a.L; ++k) {
-    const int si = a.s[k - 1], so = a.s[k];
-    const int64_t nw = (int64_t)si * so;
-    for (int64_t e = tid; e < nw + so; e += nth) {
-      const int64_t q = e < nw ? a.woff[k - 1] + e : a.boff[k - 1] + (e - nw);
-      const float gi = a.g[q];
-      const float mi = a.b1 * a.m[q] + (1.f - a.b1) * gi, vi = a.b2 * a.v[q] + (1.f - a.b2) * gi * gi;
-      a.m[q] = mi;
-      a.v[q] = vi;
-      const float wi = a.w[q] - a.lr * (mi / c1) / (sqrtf(vi / c2) + a.eps);
-      a.w[q] = wi;
-      const __nv_bfloat16 wh = __float2bfloat16(wi);
+  const int64_t np = a.boff[a.L - 1] + a.s[a.L];
+  for (int64_t e0 = tid; e0 < np; e0 += 4 * nth) {
+    float gi[4], mi[4], vi[4], wi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t q = e0 + u * nth;
+      if (q < np) { gi[u] = a.g[q]; mi[u] = a.m[q]; vi[u] = a.v[q]; wi[u] = a.w[q]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t q = e0 + u * nth;
+      if (q >= np) break;
+      const float m1 = a.b1 * mi[u] + (1.f - a.b1) * gi[u], v1 = a.b2 * vi[u] + (1.f - a.b2) * gi[u] * gi[u];
+      a.m[q] = m1;
+      a.v[q] = v1;
+      const float w1 = wi[u] - a.lr * (m1 / c1) / (sqrtf(v1 / c2) + a.eps);
+      a.w[q] = w1;
+      const __nv_bfloat16 wh = __float2bfloat16(w1);
       a.wb[q] = wh;
-      if (e < nw) {
+      int k = 0;
+      while (k + 1 < a.L && q >= a.woff[k + 1]) ++k;
+      if (q < a.boff[k]) {
+        const int so = a.s[k + 1];
+        const int64_t e = q - a.woff[k];
         const int i = (int)(e / so), o = (int)(e - (int64_t)i * so);
-        a.wp[a.wpo[k - 1] + (int64_t)i * a.ps[k] + o] = wh;
-        a.wt[a.wto[k - 1] + (int64_t)o * a.ps[k - 1] + i] = wh;
+        a.wp[a.wpo[k] + (int64_t)i * a.ps[k + 1] + o] = wh;
+        a.wt[a.wto[k] + (int64_t)o * a.ps[k] + i] = wh;
       }
     }
   }
@@ -269,35 +281,45 @@ __device__ bool phase_forward(const TrainArgs& a, int k, int64_t t, TcCta& tc_, 
         [&](int kc, int kn) { stage_rows<kTrN>(sb, Wt, pi, n0, so, kc, kn); });
     if (!ok) return false;
     epilogue(tc_, [&](int row, int c0, const float* v) {
-      const int b = m0 + row;
-      if (b >= B) return;
+      const int b = m0 + row, o0 = n0 + c0;
+      if (b >= B || o0 >= po) return;           // (po a multiple of 16: the 16 columns are in the row)
+      uint32_t hw[8];
+      if (!last) {
+        float z[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int o = n0 + c0 + q;
-        if (!last) {
-          if (o < so) {
-            const float z = v[q] + bias[o];
-            a.zp[k][(int64_t)b * so + o] = z;
-            const __nv_bfloat16 h = __float2bfloat16(tr_gelu(z));
-            a.hp[k][(int64_t)b * po + o] = h;
-            a.hT[k][(int64_t)o * a.bT + b] = h;
-          } else if (o < po) {
-            a.hp[k][(int64_t)b * po + o] = __float2bfloat16(0.f);
-          }
-        } else {
-          __nv_bfloat16* dY = a.dz[k & 1] + (int64_t)b * a.dzld;
+        for (int q = 0; q < 16; ++q) {
+          const int o = o0 + q;
+          z[q] = o < so ? v[q] + bias[o] : 0.f;
+          const __nv_bfloat16 h = __float2bfloat16(o < so ? tr_gelu(z[q]) : 0.f);
+          if (o < so) a.hT[k][(int64_t)o * a.bT + b] = h;
+          const uint32_t hb = __bfloat16_as_ushort(h);
+          hw[q >> 1] = (q & 1) ? (hw[q >> 1] | (hb << 16)) : hb;
+        }
+        float4* zr = reinterpret_cast<float4*>(a.zp[k] + (int64_t)b * po + o0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) zr[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+        uint4* hr = reinterpret_cast<uint4*>(a.hp[k] + (int64_t)b * po + o0);
+        hr[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        hr[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int o = o0 + q;
+          __nv_bfloat16 gy = __float2bfloat16(0.f);
           if (o < so) {
             const float y = v[q] + bias[o];
             const float d = y - a.Tb[(int64_t)b * so + o];
             const float r = a.Mb[(int64_t)b * so + o] * d;
             loss += (double)r * (double)d;
-            const __nv_bfloat16 gy = __float2bfloat16((float)(2.0 * inv) * r);
-            dY[o] = gy;
+            gy = __float2bfloat16((float)(2.0 * inv) * r);
             a.dzT[k & 1][(int64_t)o * a.bT + b] = gy;
-          } else if (o < po) {
-            dY[o] = __float2bfloat16(0.f);
           }
+          const uint32_t gb = __bfloat16_as_ushort(gy);
+          hw[q >> 1] = (q & 1) ? (hw[q >> 1] | (gb << 16)) : gb;
         }
+        uint4* dr = reinterpret_cast<uint4*>(a.dz[k & 1] + (int64_t)b * a.dzld + o0);
+        dr[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        dr[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
       }
     });
   }
@@ -349,18 +371,27 @@ __device__ bool phase_backward(const TrainArgs& a, int k, TcCta& tc_, unsigned c
       __nv_bfloat16* dZnT = a.dzT[(k - 1) & 1];
       const float* Z = a.zp[k - 1];
       epilogue(tc_, [&](int row, int c0, const float* v) {
-        const int b = m0 + row;
-        if (b >= B) return;
+        const int b = m0 + row, i0 = n0 + c0;
+        if (b >= B || i0 >= pi) return;          // (pi a multiple of 16: the 16 columns are in the row)
+        const float4* zr = reinterpret_cast<const float4*>(Z + (int64_t)b * pi + i0);
+        float z[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 f = zr[q];
+          z[4 * q] = f.x; z[4 * q + 1] = f.y; z[4 * q + 2] = f.z; z[4 * q + 3] = f.w;
+        }
+        uint32_t dw[8];
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int i = n0 + c0 + q;
-          if (i < si) {
-            const __nv_bfloat16 d = __float2bfloat16(v[q] * tr_gelu_grad(Z[(int64_t)b * si + i]));
-            dZn[(int64_t)b * a.dzld + i] = d;
-            dZnT[(int64_t)i * a.bT + b] = d;
-          } else if (i < pi)
-            dZn[(int64_t)b * a.dzld + i] = __float2bfloat16(0.f);
+          const int i = i0 + q;
+          const __nv_bfloat16 d = __float2bfloat16(i < si ? v[q] * tr_gelu_grad(z[q]) : 0.f);
+          if (i < si) dZnT[(int64_t)i * a.bT + b] = d;
+          const uint32_t db = __bfloat16_as_ushort(d);
+          dw[q >> 1] = (q & 1) ? (dw[q >> 1] | (db << 16)) : db;
         }
+        uint4* dr = reinterpret_cast<uint4*>(dZn + (int64_t)b * a.dzld + i0);
+        dr[0] = make_uint4(dw[0], dw[1], dw[2], dw[3]);
+        dr[1] = make_uint4(dw[4], dw[5], dw[6], dw[7]);
       });
     }
   }
@@ -482,7 +513,7 @@ int mlp_train_buffers(xt_ctx* c, xt_mlp* n, int64_t B) {
     const size_t hb = (size_t)B * pad16(n->sizes[k]) * 2;
     if ((rc = alloc(c, (void**)&n->hp[k], hb, "mlp activations"))) return rc;
     XT_CUDA(c, cudaMemsetAsync(n->hp[k], 0, hb, c->stream));
-    if (k > 0 && (rc = alloc(c, (void**)&n->zp[k], (size_t)B * n->sizes[k] * 4, "mlp activations"))) return rc;
+    if (k > 0 && (rc = alloc(c, (void**)&n->zp[k], (size_t)B * pad16(n->sizes[k]) * 4, "mlp activations"))) return rc;
     if ((rc = alloc(c, (void**)&n->hT[k], (size_t)(n->sizes[k] + 1) * bT * 2, "mlp activations"))) return rc;
   }
   for (int j = 0; j < 2; ++j) {
