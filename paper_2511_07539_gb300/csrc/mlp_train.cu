@@ -60,30 +60,38 @@ __device__ __forceinline__ float tr_gelu_grad(float z) {
   return 0.5f * (1.0f + th) + 0.5f * z * (1.0f - th * th) * du;
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid barrier of a cooperative launch with bounded waits: false (and the
 // error flag set) if some CTA did not arrive within about a second or another
-// CTA already gave up; a CTA that sees the flag set does not arrive.
+// CTA already gave up; a CTA that sees the flag set does not arrive.  The
+// arrival is an acquire-release add (it publishes the CTA's writes, ordered
+// before it by the block barrier; the last arrival thereby sees every CTA's),
+// the last arrival advances the generation with a release, and the others
+// wait on it with acquires.
 __device__ bool grid_barrier(unsigned* bar) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vb = bar;
-    int ok = vb[2] == 0;
+    int ok = ld_acquire(bar + 2) == 0;
     if (ok) {
-      const unsigned g0 = vb[1];
-      __threadfence();
-      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
+      const unsigned g0 = ld_acquire(bar + 1);
+      unsigned old;
+      asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+      if (old == gridDim.x - 1) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
       } else {
         long long i = 0;
-        while (vb[1] == g0) {
-          if (vb[2] != 0 || ++i > kTrBarSpin) { atomicExch(bar + 2, 1u); ok = 0; break; }
+        while (ld_acquire(bar + 1) == g0) {
+          if (ld_acquire(bar + 2) != 0 || ++i > kTrBarSpin) { atomicExch(bar + 2, 1u); ok = 0; break; }
           __nanosleep(64);
         }
       }
-      __threadfence();
     }
     ok_s = ok;
   }
