@@ -542,8 +542,9 @@ int run_transport_noalloc(const xt_noalloc_transport *a, void *cuda_stream,
  * returned (call again with a larger buffer after the same inputs: the pass
  * is deterministic).  accumulate works as in run_transport (0 on a domain's
  * first call of a pass, 1 on the calls that resume its bundles).  Attenuation
- * mode with Monte Carlo packets, the estimator store on the device, no
- * packet records.  Results summed over the domains equal run_transport's on
+ * mode with Monte Carlo packets, or with rays (XT_SAMPLER_RAYS) on a
+ * spherical grid, where a domain emits the rays of its own emitting cells;
+ * the estimator store on the device, no packet records.  Results summed over the domains equal run_transport's on
  * the whole grid (up to the order of additions); a packet's trajectory does
  * not depend on the decomposition.  bundle_in and bundle_out may be host or
  * device memory.  An entry of bundle_in whose cell lies outside the grid, or

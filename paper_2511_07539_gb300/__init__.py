@@ -363,7 +363,7 @@ XT_BUNDLE_FIELDS, XT_BUNDLE_CELL = 24, 17
 def run_transport_domain(ctx, z_lo, z_hi, emit, bundle_in=None, bundle_out=None, n_packets=0, seed=0,
                          tau_min=1e-4, e_cut=1e-6, n_theta=20, n_phi=20, spec_lam0_A=1000.0,
                          spec_dlog=1e-3, spec_nbins=1, accumulate=False, max_events=1_000_000,
-                         flags=0):
+                         flags=0, sampler=None):
     """One call of a process's domain (see include/extrass.h): returns
     (stats, n_out); the leaving packets' states are in bundle_out[:n_out]
     (a [cap, XT_BUNDLE_FIELDS] float64 array or tensor, host or device)."""
@@ -374,7 +374,8 @@ def run_transport_domain(ctx, z_lo, z_hi, emit, bundle_in=None, bundle_out=None,
             raise ValueError(f"{name} must have shape [n, {XT_BUNDLE_FIELDS}]")
     p = TransportParams(int(n_packets), 0, -1, int(seed), XT_MODE_ATTEN, XT_EMIT_BAND, tau_min, e_cut,
                         int(n_theta), int(n_phi), spec_lam0_A, spec_dlog, int(spec_nbins),
-                        int(bool(accumulate)), int(max_events), 0, int(flags), None, XT_SAMPLER_MC)
+                        int(bool(accumulate)), int(max_events), 0, int(flags), None,
+                        XT_SAMPLER_MC if sampler is None else int(sampler))
     st = TransportStats()
     n_out = C.c_int64()
     rc = lib().run_transport_domain(ctx, C.byref(p), int(z_lo), int(z_hi), int(bool(emit)),

@@ -1952,7 +1952,7 @@ static int ensure_buffers(xt_ctx* c, int64_t cap, int nsd) {
 // the viewers' centre directions and solid-angle shares.  Returns the number
 // of rays in *n_rays.
 static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, const double*& Lc_nat,
-                      int64_t* n_rays) {
+                      int64_t* n_rays, std::vector<int>* rcell_out) {
   const Geometry& G = c->geo;
   const int nb = p->spec_nbins;
   const double lam0 = p->spec_lam0_A, dlog = p->spec_dlog;
@@ -2080,6 +2080,7 @@ static int build_rays(xt_ctx* c, const xt_transport_params* p, RayTables& T, con
   XT_CUDA(c, cudaStreamSynchronize(c->stream));
   T.nbin = nbin;
   T.nview = nview;
+  if (rcell_out) *rcell_out = rcell;
   T.rcell = (const int*)(B + o_rc);
   T.bin_nu = (const double*)(B + o_nu);
   T.bin_cursor = (const int*)(B + o_cur);
@@ -2111,12 +2112,13 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return fail(c, XT_EINVAL, "run_transport: a spherical grid takes attenuation mode, without subdomain "
                               "rounds, with the estimator store on the device");
   RayTables rtab_rays{};
+  std::vector<int> ray_cells;          // the emitting cells, natural order (rays)
   const double* ray_Lc = nullptr;
   int64_t n_total = p->n_packets;
   if (rays) {
     if (c->nline < 1) return fail(c, XT_ESTATE, "run_transport: no lines loaded");
     if (p->emission == XT_EMIT_BAND && !c->d_L) return fail(c, XT_ESTATE, "run_transport: band emission needs L_cell in init_grid");
-    int rcr = build_rays(c, p, rtab_rays, ray_Lc, &n_total);
+    int rcr = build_rays(c, p, rtab_rays, ray_Lc, &n_total, &ray_cells);
     if (rcr) return rcr;
   }
   const int64_t count_all = p->packet_count < 0 ? n_total - p->packet_begin : p->packet_count;
@@ -2124,9 +2126,11 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
     return fail(c, XT_EINVAL, rays ? "run_transport: ray range outside [0, rays)"
                                    : "run_transport: packet range outside [0, n_packets)");
   const bool dom = c->dom.active;
-  if (dom && (rays || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 || p->packet_records))
-    return fail(c, XT_EINVAL, "run_transport_domain: attenuation mode with Monte Carlo packets, the store "
-                              "on the device, no subdomain rounds and no packet records");
+  if (dom && ((rays && !sph) || p->mode != XT_MODE_ATTEN || p->subdomain_rounds || c->S_groups > 0 ||
+              p->packet_records))
+    return fail(c, XT_EINVAL, "run_transport_domain: attenuation mode with Monte Carlo packets (or rays on "
+                              "a spherical grid), the store on the device, no subdomain rounds and no "
+                              "packet records");
   int64_t count = count_all;
   if (p->mode != XT_MODE_ATTEN && p->mode != XT_MODE_SCATTER) return fail(c, XT_EINVAL, "run_transport: mode");
   if (p->emission != XT_EMIT_BAND && p->emission != XT_EMIT_LINES) return fail(c, XT_EINVAL, "run_transport: emission");
@@ -2294,7 +2298,20 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
   int64_t dom_e0 = 0, dom_emit = 0;
   if (dom) {
     const int64_t nxy = (int64_t)G.nx * G.ny;
-    const int64_t q0 = c->h_qoff[(size_t)(c->dom.z_lo * nxy)], q1 = c->h_qoff[(size_t)(c->dom.z_hi * nxy)];
+    int64_t q0, q1;
+    if (rays) {
+      // the rays of the domain's emitting cells: a contiguous range of the
+      // cells' blocks of nbin x nview ids (whole z layers are a contiguous
+      // range of natural cell indices)
+      const int64_t per_cell = rtab_rays.nbin * rtab_rays.nview;
+      const int64_t r0 = std::lower_bound(ray_cells.begin(), ray_cells.end(), (int)(c->dom.z_lo * nxy)) - ray_cells.begin();
+      const int64_t r1 = std::lower_bound(ray_cells.begin(), ray_cells.end(), (int)(c->dom.z_hi * nxy)) - ray_cells.begin();
+      q0 = r0 * per_cell;
+      q1 = r1 * per_cell;
+    } else {
+      q0 = c->h_qoff[(size_t)(c->dom.z_lo * nxy)];
+      q1 = c->h_qoff[(size_t)(c->dom.z_hi * nxy)];
+    }
     dom_e0 = std::max<int64_t>(q0, p->packet_begin);
     const int64_t e1 = std::min<int64_t>(q1, p->packet_begin + count_all);
     dom_emit = c->dom.emit && e1 > dom_e0 ? e1 - dom_e0 : 0;
@@ -2576,7 +2593,9 @@ extern "C" int run_transport(xt_ctx* c, const xt_transport_params* p, xt_transpo
       ta.out = qA;
       const int grid = (int)std::min<int64_t>(grid_max, (count + 255) / 256);
       sl = tick(1);
-      if (sph && pi) k_trace_sph<true, false, true><<<grid, 256, 0, c->stream>>>(ta);
+      if (sph && rays && pi) k_trace_sph<true, true, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph && rays) k_trace_sph<true, true><<<grid, 256, 0, c->stream>>>(ta);
+      else if (sph && pi) k_trace_sph<true, false, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (sph) k_trace_sph<true><<<grid, 256, 0, c->stream>>>(ta);
       else if (pi) k_trace<XT_MODE_ATTEN, true><<<grid, 256, 0, c->stream>>>(ta);
       else if (wr) k_trace<XT_MODE_ATTEN, false, false, true><<<grid, 256, 0, c->stream>>>(ta);

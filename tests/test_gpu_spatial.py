@@ -131,6 +131,75 @@ def test_phi_slab_domains_on_the_spherical_grid(xt, world, pi):
         _cmp(G, G_ref, 1e-10, "photoionization rates")
 
 
+@pytest.mark.parametrize("pi", [False, True])
+def test_rays_across_phi_slab_domains(xt, pi):
+    """The paper's own configuration (Secs. 2.3, 2.4.1): the RAYS sampler on
+    the spherical grid with domains of whole phi slices; a domain emits the
+    rays of its cells (a contiguous range of the cells' blocks of ray ids) and
+    hands on those that enter another domain.  The sums over the domains equal
+    one run_transport of the whole grid with the same rays."""
+    import torch
+    from paper_2511_07539_gb300 import spatial
+    w = synth.spherical_sphere(n_packets=1, seed=9, nr=6, nth=4, nph=6, subdomains=(1, 1, 3))
+    if pi:
+        synth.with_photoionization(w)
+    w.pops = w.pops * 1e-3
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = dict(n_packets=1, seed=w.seed, spec_lam0_A=w.spec_band_A[0], spec_nbins=w.spec_band_A[1],
+              sampler=xt.XT_SAMPLER_RAYS, n_theta=7, n_phi=7, spec_dlog=0.01)
+    ref = xt.Context(0, stream)
+    ref.load(w)
+    st = xt.run_transport(ref.h, **kw)
+    S_ref, spec_ref = ref.get_estimators(), ref.get_spectrum(0)
+    G_ref = ref.get_photoionization_rates()[0] if pi else None
+    ref.close()
+    world = 3
+    ctxs, trs = [], []
+    for r in range(world):
+        c = xt.Context(0, stream)
+        c.load(w)
+        ctxs.append(c)
+        trs.append(spatial.LibDomainTracer(c, *spatial.slab(r, w.nz, world), **kw))
+    rounds = spatial.run_local(trs, w.nz)
+    assert 1 <= rounds <= world - 1
+    S = np.zeros_like(S_ref)
+    spec = np.zeros_like(spec_ref)
+    G = np.zeros_like(G_ref) if pi else None
+    ev = tests = emitted = 0.0
+    nxy = w.nx * w.ny
+    for r, (c, t) in enumerate(zip(ctxs, trs)):
+        z0, z1 = spatial.slab(r, w.nz, world)
+        S[z0 * nxy:z1 * nxy] = c.get_estimators(z0 * nxy, (z1 - z0) * nxy)
+        spec += c.get_spectrum(0)
+        if pi:
+            G[z0 * nxy:z1 * nxy] = c.get_photoionization_rates(z0 * nxy, (z1 - z0) * nxy)[0]
+        ev += t.stats[-1]["events"]
+        tests += t.stats[-1]["tests"]
+        emitted += t.stats[-1]["emitted_E"]
+        c.close()
+    assert st["rays"] > 0 and st["events"] > 1000
+    assert ev == st["events"] and tests == st["tests"]
+    assert abs(emitted / st["emitted_E"] - 1) < 1e-12
+    _cmp(S, S_ref, 1e-10, "estimators")
+    _cmp(spec, spec_ref, 1e-9, "spectrum")
+    if pi:
+        _cmp(G, G_ref, 1e-10, "photoionization rates")
+
+
+def test_rays_domains_refused_on_the_cube(xt):
+    """Domains take rays on the spherical grid only (the cube's domain path
+    emits through the packet pool, which has no ray form)."""
+    import torch
+    w = synth.clumpy_onion(seed=2, n=8, n_packets=1000, n_lines=200, level_range=(20, 30),
+                           subdomains=(2, 2, 2))
+    with xt.Context(0, torch.cuda.current_stream().cuda_stream) as ctx:
+        ctx.load(w)
+        with pytest.raises(xt.XtError) as e:
+            xt.run_transport_domain(ctx.h, 0, 4, True, n_packets=1, seed=1, spec_lam0_A=w.spec_band_A[0],
+                                    spec_nbins=w.spec_band_A[1], sampler=xt.XT_SAMPLER_RAYS)
+        assert e.value.code == xt.XT_EINVAL
+
+
 def test_malformed_bundle_is_refused(xt):
     """A received state whose cell lies outside the grid, or whose line cursor
     lies outside the line list, is refused (XT_EINVAL) before it is traced."""
