@@ -256,17 +256,19 @@ STATE_Z = 4                # the z index of the cell the packet entered
 
 
 def transport_domain(w, z_lo, z_hi, emit, bundle_in=None, n_theta=20, n_phi=20, spec_dlog=1e-3,
-                     tau_min=1e-4, e_cut=1e-6, seed=None, max_events=1_000_000):
+                     tau_min=1e-4, e_cut=1e-6, seed=None, max_events=1_000_000, sampler="mc"):
     """One domain of a spatial decomposition (Sec. 2.4.1): the cells with z in
-    [z_lo, z_hi).  With emit, the workload's packets emitted in the domain
-    start; the packets of bundle_in (states from other domains, [n,
-    STATE_FIELDS]) resume.  Returns S [ncell, nline] (only the domain's cells
-    written), spec, ledger, S_pi and heat (with photoionization data), and the
-    states of the packets that entered another domain's cells."""
+    [z_lo, z_hi).  With emit, the workload's packets (or, sampler="rays", its
+    rays) emitted in the domain start; the packets of bundle_in (states from
+    other domains, [n, STATE_FIELDS]) resume.  Returns S [ncell, nline] (only
+    the domain's cells written), spec, ledger, S_pi and heat (with
+    photoionization data), and the states of the packets that entered another
+    domain's cells."""
     keep = _Keep(w)
     lam0, nbins = w.spec_band_A
-    pr = _params(w, w.n_packets, 0, w.n_packets, seed, "atten", "band", tau_min, e_cut, n_theta,
-                 n_phi, spec_dlog, max_events, "mc")
+    N = ray_count(w, "band", n_theta, n_phi, spec_dlog) if sampler == "rays" else w.n_packets
+    pr = _params(w, N, 0, N, seed, "atten", "band", tau_min, e_cut, n_theta, n_phi, spec_dlog,
+                 max_events, sampler)
     S = np.zeros((w.ncell, w.nline))
     spec = np.zeros((n_theta * n_phi, nbins))
     ledger = np.zeros(20)
@@ -285,6 +287,8 @@ def transport_domain(w, z_lo, z_hi, emit, bundle_in=None, n_theta=20, n_phi=20, 
                                        _ptr(spec), _ptr(ledger), _ptr(S_pi), _ptr(heat))
         if rc == 0:
             break
+        if rc == -2:
+            raise ValueError("an emitting line lies outside the output wavelength grid")
         cap = int(n_out[0])
     res = dict(S=S, spec=spec, ledger=dict(zip(LEDGER, ledger[:len(LEDGER)].tolist())),
                bundle=out[: int(n_out[0])])

@@ -623,7 +623,7 @@ static void transport_packet(const prep_t *P, int64_t p, double *S, double *spec
  * order over the emitting cells, the emitting bins and the viewers.  A ray
  * whose cell has no emission in its bin is empty: fate 4, nothing traced. */
 static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, double *ledger,
-                          double *pkt, double *S_pi, double *heat) {
+                          double *pkt, double *S_pi, double *heat, xo_domain *dom) {
     const xo_problem *pb = P->pb;
     const xo_params *pr = P->pr;
     int64_t nv = (int64_t)pr->n_theta * pr->n_phi;
@@ -661,7 +661,7 @@ static void transport_ray(const prep_t *P, int64_t r, double *S, double *spec, d
         rr[0] = rm * sin(th) * cos(ph); rr[1] = rm * sin(th) * sin(ph); rr[2] = rm * cos(th);
     }
     propagate(P, r, c, idx, rr, n, P->rbin_nu[jb], P->rbin_cursor[jb], E0, S, spec, ledger, pkt, S_pi, heat,
-              NULL);
+              dom);
 }
 
 /* The event loop of one packet or ray from its emission (Secs. 2.3, 2.3.2):
@@ -1087,7 +1087,7 @@ int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *s
     if (pr->sampler == 1 && rays_prep(&P) != 0) { unprep(&P); g_rec = NULL; return -2; }
     for (int64_t p = pr->p_begin; p < pr->p_end; p++) {
         double *pk = pkt ? pkt + (p - pr->p_begin) * XO_PKT_FIELDS : NULL;
-        if (pr->sampler == 1) transport_ray(&P, p, S, spec, ledger, pk, S_pi, heat);
+        if (pr->sampler == 1) transport_ray(&P, p, S, spec, ledger, pk, S_pi, heat, NULL);
         else transport_packet(&P, p, S, spec, ledger, pk, S_pi, heat, NULL);
     }
     unprep(&P);
@@ -1104,8 +1104,10 @@ int xo_transport(const xo_problem *pb, const xo_params *pr, double *S, double *s
  * another domain; the states of those are written to bundle_out (at most
  * out_cap, their number in *n_out).  Estimators, spectrum and ledger
  * accumulate as in xo_transport (emission is counted where the packet is
- * emitted).  Attenuation mode, Monte Carlo packets.  Returns 0, or -1 if
- * bundle_out was too small (its first out_cap states are written). */
+ * emitted).  Attenuation mode, Monte Carlo packets or rays (the rays of the
+ * domain's emitting cells).  Returns 0, -1 if bundle_out was too small (its
+ * first out_cap states are written), or -2 if an emitting line of the rays
+ * lies outside the output grid. */
 int xo_transport_domain(const xo_problem *pb, const xo_params *pr, int32_t z_lo, int32_t z_hi,
                         int32_t emit, const double *bundle_in, int64_t n_in, double *bundle_out,
                         int64_t out_cap, int64_t *n_out, double *S, double *spec, double *ledger,
@@ -1115,11 +1117,15 @@ int xo_transport_domain(const xo_problem *pb, const xo_params *pr, int32_t z_lo,
     prep(&P, pb, pr);
     xo_domain dom = {z_lo, z_hi, bundle_out, out_cap, 0};
     int64_t nxy = (int64_t)pb->nx * pb->ny;
+    if (pr->sampler == 1 && rays_prep(&P) != 0) { unprep(&P); return -2; }
+    int64_t per_cell = (int64_t)P.n_rbin * pr->n_theta * pr->n_phi;
     if (emit)
         for (int64_t p = pr->p_begin; p < pr->p_end; p++) {
-            int64_t c = cell_of_packet(&P, p);
+            int64_t c = pr->sampler == 1 ? P.rcell[p / per_cell] : cell_of_packet(&P, p);
             int32_t z = (int32_t)(c / nxy);
-            if (z >= z_lo && z < z_hi) transport_packet(&P, p, S, spec, ledger, NULL, S_pi, heat, &dom);
+            if (z < z_lo || z >= z_hi) continue;
+            if (pr->sampler == 1) transport_ray(&P, p, S, spec, ledger, NULL, S_pi, heat, &dom);
+            else transport_packet(&P, p, S, spec, ledger, NULL, S_pi, heat, &dom);
         }
     for (int64_t k = 0; k < n_in; k++) {
         xo_state st;

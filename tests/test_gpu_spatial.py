@@ -140,9 +140,9 @@ def test_rays_across_phi_slab_domains(xt, pi):
     one run_transport of the whole grid with the same rays."""
     import torch
     from paper_2511_07539_gb300 import spatial
-    w = synth.spherical_sphere(n_packets=1, seed=9, nr=6, nth=4, nph=6, subdomains=(1, 1, 3))
+    w = synth.spherical_sphere(n_packets=1, seed=72, nr=6, nth=4, nph=6, subdomains=(1, 1, 3))
     if pi:
-        synth.with_photoionization(w)
+        synth.with_photoionization(w, chi_eV=6.0, charge=0, pi_nlev=9)
     w.pops = w.pops * 1e-3
     stream = torch.cuda.current_stream().cuda_stream
     kw = dict(n_packets=1, seed=w.seed, spec_lam0_A=w.spec_band_A[0], spec_nbins=w.spec_band_A[1],
@@ -183,6 +183,7 @@ def test_rays_across_phi_slab_domains(xt, pi):
     _cmp(S, S_ref, 1e-10, "estimators")
     _cmp(spec, spec_ref, 1e-9, "spectrum")
     if pi:
+        assert (G_ref > 0).any()
         _cmp(G, G_ref, 1e-10, "photoionization rates")
 
 
