@@ -12,8 +12,8 @@
 // ([b][i]) and transposed ([i][b]), so that each product's operands are rows
 // with K contiguous; the CTA stages them through registers into the canonical
 // K-major layout of tc.cuh, in chunks of 256 K, and reads the accumulator with
-// tcgen05.ld.  Hidden activations
-// GELU (tanh form), loss and Adam as in the per-kernel reference of mlp.cu.
+// tcgen05.ld.  Hidden activations GELU (tanh form, Hendrycks & Gimpel 2016),
+// masked mean squared error, Adam (Kingma & Ba 2015) on FP32 master weights.
 #include <cuda_runtime.h>
 
 #include <algorithm>
