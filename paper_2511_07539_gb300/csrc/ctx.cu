@@ -6,6 +6,7 @@
 #include <numeric>
 
 #include "fixexp.cuh"
+#include "linesort.h"
 #include "xt_internal.cuh"
 
 namespace xt {
@@ -567,33 +568,7 @@ int load_atomic_data(xt_ctx* c, const xt_atom_desc* a) {
   std::vector<double> nu(nl);
   for (int l = 0; l < nl; ++l) nu[l] = kC / (lam[l] * 1e-8);
   std::vector<int> order(nl);
-  {
-    // a stable LSD radix sort (8-bit digits) of the complemented bit patterns
-    // of nu, starting from the caller order: positive doubles order as their
-    // bit patterns, so this is descending nu with ties in ascending caller
-    // index (passes whose digit is the same for every line are skipped)
-    std::vector<uint64_t> key(nl), key2(nl);
-    std::vector<int> o2(nl);
-    for (int l = 0; l < nl; ++l) {
-      uint64_t b;
-      std::memcpy(&b, &nu[l], sizeof(b));
-      key[l] = ~b;
-      order[l] = l;
-    }
-    for (int sh = 0; sh < 64; sh += 8) {
-      size_t cnt[257] = {0};
-      for (int i = 0; i < nl; ++i) cnt[((key[i] >> sh) & 255u) + 1]++;
-      if (nl == 0 || cnt[((key[0] >> sh) & 255u) + 1] == (size_t)nl) continue;
-      for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
-      for (int i = 0; i < nl; ++i) {
-        const size_t pos = cnt[(key[i] >> sh) & 255u]++;
-        key2[pos] = key[i];
-        o2[pos] = order[i];
-      }
-      key.swap(key2);
-      order.swap(o2);
-    }
-  }
+  sort_lines_by_frequency(nu.data(), nl, order.data());
   c->h_orig_of = order;
   c->h_sorted_of.assign(nl, 0);
   for (int s = 0; s < nl; ++s) c->h_sorted_of[order[s]] = s;

@@ -5,6 +5,7 @@
 #include "fixexp.cuh"
 #include "philox.cuh"
 #include "quota.h"
+#include "linesort.h"
 
 using namespace xt;
 
@@ -55,6 +56,8 @@ void h_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out, long n) {
 void h_u01(const uint64_t* x, double* out, long n) {
   for (long i = 0; i < n; ++i) out[i] = u01(x[i]);
 }
+
+void h_linesort(const double* nu, int n, int* order) { sort_lines_by_frequency(nu, n, order); }
 
 void h_quota(const double* L, long nc, long N, int64_t* qoff) {
   std::vector<double> Lv(L, L + nc);

@@ -1,7 +1,8 @@
 """The library's integer-pipe routines (fixexp.cuh: the quotient, the
 emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
 beta and its derivative, the scaled rounding to FP32 of the rate solve; and
-the Philox generator of philox.cuh; the packet quota of quota.h) compiled
+the Philox generator of philox.cuh; the packet quota of quota.h; the line
+order of linesort.h) compiled
 for the host from the same source and
 checked against mpmath on the CPU, so that they are pinned without a GPU.
 On the device the FP32 seeds of the two Newton-Raphson iterations come from
@@ -156,6 +157,23 @@ def test_philox_vs_numpy(fx):
     u = np.zeros(x.size)
     fx.h_u01(_p(x), _p(u), C.c_long(x.size))
     np.testing.assert_array_equal(u, (x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53)
+
+
+def test_line_order_is_a_stable_descending_frequency_sort(fx):
+    """The library's line order (a radix sort of the frequencies' bit
+    patterns) equals a stable sort by descending frequency: numpy's stable
+    argsort of -nu, with many ties, one line, none, and frequencies spanning
+    many binades."""
+    rng = np.random.default_rng(12)
+    cases = [np.zeros(0), np.array([3.0e15]),
+             2.99792458e18 / (1000.0 + rng.integers(0, 50, 20_000) * 0.5),    # many equal wavelengths
+             10.0 ** rng.uniform(10, 20, 100_003),                           # many binades
+             np.full(777, 5.0e14)]
+    for nu in cases:
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        order = np.zeros(len(nu), dtype=np.int32)
+        fx.h_linesort(_p(nu), C.c_int(len(nu)), _p(order))
+        np.testing.assert_array_equal(order, np.argsort(-nu, kind="stable"))
 
 
 def test_packet_quota_matches_the_oracle(fx):
