@@ -39,6 +39,7 @@
 #include "fixexp.cuh"
 #include "philox.cuh"
 #include "quota.h"
+#include "raysched.h"
 #include "xt_internal.cuh"
 
 namespace xt {
@@ -335,12 +336,7 @@ struct EmitOut {
 // instead, 1.7x slower; the same order on the cube, whose cell walk is cheap,
 // 1.8x slower than ids in order.)
 __device__ __forceinline__ int64_t ray_id_of(const EmitArgs& a, int64_t v) {
-  const RayTables& T = a.ray;
-  const int64_t per_cell = T.nbin * T.nview;
-  const int64_t lo = (v / per_cell) * per_cell;
-  if (T.nview <= 1 || lo < a.p_begin || lo + per_cell > a.p_begin + a.n) return v;
-  const int64_t rem = v - lo, kv = rem / T.nbin;
-  return lo + (rem - kv * T.nbin) * T.nview + kv;
+  return ray_id_in_range(v, a.p_begin, a.n, a.ray.nbin, a.ray.nview);
 }
 
 __device__ __forceinline__ void emit_ray(const EmitArgs& a, int64_t rid, EmitOut& o) {

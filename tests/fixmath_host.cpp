@@ -6,6 +6,7 @@
 #include "philox.cuh"
 #include "quota.h"
 #include "linesort.h"
+#include "raysched.h"
 
 using namespace xt;
 
@@ -58,6 +59,10 @@ void h_u01(const uint64_t* x, double* out, long n) {
 }
 
 void h_linesort(const double* nu, int n, int* order) { sort_lines_by_frequency(nu, n, order); }
+
+void h_rayids(int64_t p_begin, int64_t n, int64_t nbin, int64_t nview, int64_t* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = ray_id_in_range(p_begin + i, p_begin, n, nbin, nview);
+}
 
 void h_quota(const double* L, long nc, long N, int64_t* qoff) {
   std::vector<double> Lv(L, L + nc);

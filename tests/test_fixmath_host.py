@@ -2,7 +2,7 @@
 emission direction, e^-tau and 1 - e^-tau, sin/cos of the azimuth, Sobolev
 beta and its derivative, the scaled rounding to FP32 of the rate solve; and
 the Philox generator of philox.cuh; the packet quota of quota.h; the line
-order of linesort.h) compiled
+order of linesort.h; the ray hand-out order of raysched.h) compiled
 for the host from the same source and
 checked against mpmath on the CPU, so that they are pinned without a GPU.
 On the device the FP32 seeds of the two Newton-Raphson iterations come from
@@ -174,6 +174,27 @@ def test_line_order_is_a_stable_descending_frequency_sort(fx):
         order = np.zeros(len(nu), dtype=np.int32)
         fx.h_linesort(_p(nu), C.c_int(len(nu)), _p(order))
         np.testing.assert_array_equal(order, np.argsort(-nu, kind="stable"))
+
+
+@pytest.mark.parametrize("p_begin,n,nbin,nview", [(0, 3 * 5 * 7, 5, 7), (11, 3 * 5 * 7, 5, 7),
+                                                   (35, 70, 5, 7), (0, 40, 40, 1), (3, 1, 5, 7),
+                                                   (0, 0, 5, 7), (123, 4 * 36 * 49 + 17, 36, 49)])
+def test_ray_hand_out_order_is_a_bijection(fx, p_begin, n, nbin, nview):
+    """The refill's ray order permutes each launch's id range onto itself
+    (every ray traced once), takes a whole block's ids viewer by viewer and bin
+    after bin, and leaves the ids of blocks the range cuts in order."""
+    out = np.zeros(n, dtype=np.int64)
+    fx.h_rayids(C.c_int64(p_begin), C.c_int64(n), C.c_int64(nbin), C.c_int64(nview), _p(out))
+    ids = np.arange(p_begin, p_begin + n)
+    np.testing.assert_array_equal(np.sort(out), ids)
+    per = nbin * nview
+    for v, p in zip(ids, out):
+        lo = (v // per) * per
+        if nview > 1 and lo >= p_begin and lo + per <= p_begin + n:
+            rem = v - lo
+            assert p == lo + (rem % nbin) * nview + rem // nbin       # bin fastest, then viewer
+        else:
+            assert p == v
 
 
 def test_packet_quota_matches_the_oracle(fx):
