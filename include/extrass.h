@@ -369,7 +369,12 @@ int solve_nlte(xt_ctx *ctx, const xt_nlte_params *p, double *pops_out, int32_t *
  * tensor cores with FP32 accumulation.  Weights are one flat FP32 vector:
  * W_1 [n_in][h], b_1, W_2, b_2, ..., W_out, b_out (W row-major [fan_in][fan_out]).
  * A bad prediction costs only refinement or Newton steps: solve_nlte refines (or falls
- * back to FP64) whatever the warm start. */
+ * back to FP64) whatever the warm start.  Training (surrogate_train_step,
+ * train_surrogate) runs in one persistent cooperative kernel per call (every
+ * step of a call in one launch, one CTA per SM, tcgen05 BF16 products); its
+ * grid barriers and MMA completions are waited on with bounded polls, after
+ * which the call returns XT_ETIMEOUT.  Prediction uses BF16 products with FP32
+ * accumulation (mma.sync).  At most 8 layers (n_sizes <= 9): XT_EINVAL. */
 int surrogate_init(xt_ctx *ctx, const int32_t *sizes, int32_t n_sizes, uint64_t seed);
 /* set != 0: load weights from flat; else copy them out.  n_cap in floats. */
 int surrogate_weights(xt_ctx *ctx, int32_t set, float *flat, size_t n_cap);
