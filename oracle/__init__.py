@@ -110,6 +110,9 @@ def lib():
         _lib.xo_cell_volumes.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         _lib.xo_ray_count.restype = C.c_int64
         _lib.xo_ray_count.argtypes = [C.c_void_p, C.c_void_p]
+        _lib.xo_sph_walk.restype = C.c_int64
+        _lib.xo_sph_walk.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_int64, C.c_void_p, C.c_void_p]
         _lib.xo_tau_beta.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
         _lib.xo_packet_quota.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
         _lib.xo_philox4x64_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -171,6 +174,25 @@ def _params(w, N, p_begin, p_end, seed, mode, emission, tau_min, e_cut, n_theta,
                    0 if mode == "atten" else 1, 0 if emission == "band" else 1,
                    tau_min, e_cut, n_theta, n_phi, lam0, spec_dlog, nbins, max_events,
                    1 if sampler == "rays" else 0)
+
+
+def sph_walk(w, p0, n, idx0, max_cells=10_000):
+    """The spherical grid's walk alone (test entry): the natural indices of
+    the cells a straight path from p0 (cm, inside cell idx0 = (ir, ith, iph))
+    along the unit vector n crosses, and the path length at which it leaves
+    each; None if the path does not leave the outer sphere within max_cells."""
+    keep = _Keep(w)
+    pr = _params(w, 0, 0, 0, 0, "atten", "band", 1e-4, 1e-6, 20, 20, 1e-3, 1, "mc")
+    p0 = np.ascontiguousarray(p0, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    i0 = np.ascontiguousarray(idx0, dtype=np.int32)
+    cells = np.zeros(max_cells, dtype=np.int64)
+    s_exit = np.zeros(max_cells)
+    k = lib().xo_sph_walk(C.byref(keep.pb), C.byref(pr), _ptr(p0), _ptr(n), _ptr(i0), max_cells,
+                          _ptr(cells), _ptr(s_exit))
+    if k < 0:
+        return None
+    return cells[:k], s_exit[:k]
 
 
 def ray_count(w, emission="band", n_theta=20, n_phi=20, spec_dlog=1e-3):

@@ -777,6 +777,20 @@ static double sph_exit(const prep_t *P, const double p0[3], const double n[3], c
     return best;
 }
 
+/* The cell beyond the face of kind `kind` of cell idx (updated in place):
+ * returns 1 if that is the outside of the outer sphere (idx[0] = nx), -1 if
+ * there was no face (kind < 0), else 0.  Azimuthal indices wrap around. */
+static int sph_cross(const xo_problem *pb, int32_t idx[3], int kind) {
+    if (kind == 0) return ++idx[0] == pb->nx ? 1 : 0;
+    if (kind == 1) idx[0]--;
+    else if (kind == 2) idx[1]--;
+    else if (kind == 3) idx[1]++;
+    else if (kind == 4) idx[2] = idx[2] == 0 ? pb->nz - 1 : idx[2] - 1;
+    else if (kind == 5) idx[2] = idx[2] == pb->nz - 1 ? 0 : idx[2] + 1;
+    else return -1;
+    return 0;
+}
+
 /* The event loop on the spherical grid (attenuation mode): as in trace, with
  * the walk through (r, theta, phi) cells; the packet's position is p0 + s n. */
 static int pi_segment(const prep_t *P, int64_t cell, const double *pc, double nu_lab,
@@ -851,30 +865,19 @@ static void trace_sph(const prep_t *P, xo_state *st, double *S, double *spec, do
             goto done;
         }
         s = s_exit;
-        if (kind == 0) {
-            if (++idx[0] == pb->nx) {                     /* leaves the outer sphere */
-                double E = N * XO_H * nu_lab;
-                esc_E = E;
-                ledger[L_ESC_N] += N;
-                ledger[L_ESC_E] += E;
-                vbin = xo_viewer_bin(n, pr->n_theta, pr->n_phi);
-                lbin = xo_lambda_bin(XO_C / nu_lab * 1e8, pr->spec_lam0_A, pr->spec_dlog, pr->spec_nbins);
-                if (lbin >= 0) spec[(int64_t)vbin * pr->spec_nbins + lbin] += E;
-                else ledger[L_OOB_E] += E;
-                fate = 0;
-                goto done;
-            }
-        } else if (kind == 1) {
-            idx[0]--;
-        } else if (kind == 2) {
-            idx[1]--;
-        } else if (kind == 3) {
-            idx[1]++;
-        } else if (kind == 4) {
-            idx[2] = idx[2] == 0 ? pb->nz - 1 : idx[2] - 1;
-        } else if (kind == 5) {
-            idx[2] = idx[2] == pb->nz - 1 ? 0 : idx[2] + 1;
-        } else {
+        int crossed = sph_cross(pb, idx, kind);
+        if (crossed == 1) {                               /* leaves the outer sphere */
+            double E = N * XO_H * nu_lab;
+            esc_E = E;
+            ledger[L_ESC_N] += N;
+            ledger[L_ESC_E] += E;
+            vbin = xo_viewer_bin(n, pr->n_theta, pr->n_phi);
+            lbin = xo_lambda_bin(XO_C / nu_lab * 1e8, pr->spec_lam0_A, pr->spec_dlog, pr->spec_nbins);
+            if (lbin >= 0) spec[(int64_t)vbin * pr->spec_nbins + lbin] += E;
+            else ledger[L_OOB_E] += E;
+            fate = 0;
+            goto done;
+        } else if (crossed < 0) {
             fate = 3;                                      /* no face ahead (cannot happen inside) */
             ledger[L_GUARD] += 1.0;
             goto done;
@@ -1135,6 +1138,33 @@ int xo_transport_domain(const xo_problem *pb, const xo_params *pr, int32_t z_lo,
     unprep(&P);
     *n_out = dom.n;
     return dom.n > out_cap ? -1 : 0;
+}
+
+/* The walk alone, for a test: the cells a straight path from p0 (cm, inside
+ * cell idx0 of the spherical grid) along the unit vector n crosses, in order
+ * (natural indices), and the path length at which it leaves each, by the
+ * face solver and the cell step of the event loop; at most max cells.
+ * Returns the number of cells when the path leaves the outer sphere, or -1
+ * (max reached, or no face ahead). */
+int64_t xo_sph_walk(const xo_problem *pb, const xo_params *pr, const double *p0, const double *n,
+                    const int32_t *idx0, int64_t max, int64_t *cells, double *s_exit) {
+    prep_t P;
+    prep(&P, pb, pr);
+    int32_t idx[3] = {idx0[0], idx0[1], idx0[2]};
+    double s = 0.0;
+    int64_t ret = -1;
+    for (int64_t k = 0; k < max; k++) {
+        int kind;
+        double se = sph_exit(&P, p0, n, idx, s, &kind);
+        cells[k] = ((int64_t)idx[2] * pb->ny + idx[1]) * pb->nx + idx[0];
+        s_exit[k] = se;
+        int crossed = sph_cross(pb, idx, kind);
+        if (crossed == 1) { ret = k + 1; break; }
+        if (crossed < 0) break;
+        s = se;
+    }
+    unprep(&P);
+    return ret;
 }
 
 /* Number of rays of the RAYS sampler (emitting cells x emitting bins x

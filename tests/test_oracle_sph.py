@@ -15,6 +15,11 @@ GPU).
   from cell to cell (an event booked in the wrong cell would carry the wrong
   cell's population and break the per-cell mean intensity).
 - The photon ledger closes.
+- The walk alone (face solver and cell step): along random straight paths,
+  every cell the oracle lists contains the middle of its path piece, the
+  points just before and after each exit lie in the cell left and the cell
+  entered, and a fine sampling of the path meets the cells in the same order
+  (cell membership computed directly from r, theta and phi).
 """
 import numpy as np
 import pytest
@@ -284,3 +289,57 @@ def test_ledger_closes_with_photoionization_on_the_spherical_grid():
     assert L["pi_N"] > 0.05 * L["emit_N"] and L["abs_N"] > 0.05 * L["emit_N"] and L["events"] > 10_000
     assert L["esc_N"] + L["abs_N"] + L["pi_N"] + L["drop_N"] == pytest.approx(L["emit_N"], rel=1e-13)
     assert o["S_pi"].sum() == pytest.approx(L["pi_N"], rel=1e-12)
+
+
+def _cell_of(w, p):
+    """Natural index of the cell holding point p (cm), straight from the
+    edges in r, theta and phi (-1 outside the outer sphere)."""
+    r = float(np.sqrt(p @ p))
+    if r >= w.r_edges[-1] * w.t:
+        return -1
+    th = float(np.arccos(np.clip(p[2] / r, -1.0, 1.0)))
+    ph = float(np.arctan2(p[1], p[0])) % (2.0 * np.pi)
+    ir = min(int(np.searchsorted(w.r_edges * w.t, r, side="right")) - 1, w.nx - 1)
+    it = min(max(int(np.searchsorted(w.theta_edges, th, side="right")) - 1, 0), w.ny - 1)
+    ip = min(max(int(np.searchsorted(w.phi_edges, ph, side="right")) - 1, 0), w.nz - 1)
+    return (ip * w.ny + it) * w.nx + ir
+
+
+@pytest.mark.parametrize("nr,nth,nph", [(6, 4, 6), (9, 7, 5), (5, 6, 1)])
+def test_walk_against_cell_membership(nr, nth, nph):
+    w = synth.spherical_sphere(n_packets=1, seed=3, nr=nr, nth=nth, nph=nph)
+    rng = np.random.default_rng(nr * 100 + nth * 10 + nph)
+    R = w.r_edges[-1] * w.t
+    eps = 1e-9 * R
+    for _ in range(150):
+        # a point uniform in a random cell, a direction uniform on the sphere
+        ir, it, ip = rng.integers(nr), rng.integers(nth), rng.integers(nph)
+        r0, r1 = w.r_edges[ir] * w.t, w.r_edges[ir + 1] * w.t
+        r = (r0 ** 3 + rng.random() * (r1 ** 3 - r0 ** 3)) ** (1.0 / 3.0)
+        c0, c1 = np.cos(w.theta_edges[it]), np.cos(w.theta_edges[it + 1])
+        mu = c0 + rng.random() * (c1 - c0)
+        ph = w.phi_edges[ip] + rng.random() * (w.phi_edges[ip + 1] - w.phi_edges[ip])
+        st = np.sqrt(1.0 - mu * mu)
+        p0 = r * np.array([st * np.cos(ph), st * np.sin(ph), mu])
+        u, v = rng.random(2)
+        m = 2.0 * u - 1.0
+        n = np.array([np.sqrt(1 - m * m) * np.cos(2 * np.pi * v), np.sqrt(1 - m * m) * np.sin(2 * np.pi * v), m])
+        assert _cell_of(w, p0) == (ip * nth + it) * nr + ir
+        out = oracle.sph_walk(w, p0, n, (ir, it, ip))
+        assert out is not None
+        cells, s_exit = out
+        assert np.all(np.diff(s_exit) > 0) and s_exit[0] > 0
+        s_prev = 0.0
+        for k, (c, se) in enumerate(zip(cells, s_exit)):
+            assert _cell_of(w, p0 + 0.5 * (s_prev + se) * n) == c
+            assert _cell_of(w, p0 + (se - eps) * n) == c
+            nxt = cells[k + 1] if k + 1 < len(cells) else -1
+            assert _cell_of(w, p0 + (se + eps) * n) == nxt
+            s_prev = se
+        # a fine sampling meets the cells in the same order
+        ss = np.linspace(0.0, s_exit[-1] * (1 - 1e-12), 4000)
+        seen = [c for c in (_cell_of(w, p0 + s * n) for s in ss)]
+        dedup = [seen[0]] + [b for a, b in zip(seen[:-1], seen[1:]) if b != a]
+        it_cells = iter(cells.tolist())
+        assert all(any(c == x for x in it_cells) for c in dedup)      # a subsequence, in order
+
