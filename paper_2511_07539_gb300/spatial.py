@@ -34,8 +34,9 @@ def slab(rank, nz, world):
 class LibDomainTracer:
     """A process's domain traced by the CUDA library: run_transport_domain on
     the context `ctx` (grid, atoms and populations loaded), transport keyword
-    arguments as for run_transport (n_packets, seed, spectrum grid ...).
-    Bundles stay on the device (torch tensors)."""
+    arguments as for run_transport (n_packets, seed, spectrum grid, sampler:
+    rays take domains on the spherical grid ...).  Bundles stay on the device
+    (torch tensors)."""
 
     def __init__(self, ctx, z_lo, z_hi, device="cuda", **kw):
         import torch
